@@ -1,0 +1,245 @@
+"""ctypes front end of the plain FP64 CPU oracle (``jagp_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
+bench's CPU-baseline leg call it; the CUDA library never does.  It shares no
+code with the CUDA path.  ``build()`` compiles the C file with gcc into
+``oracle/_build`` (OpenMP when available, no FP contraction).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "jagp_oracle.c")
+_OUT = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_OUT, "libjagp_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+f64p = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+
+
+class _OrcSystem(C.Structure):
+    _fields_ = [
+        ("n_atoms", C.c_int), ("R", C.c_void_p), ("Z", C.c_void_p),
+        ("n_shells", C.c_int), ("shell_atom", C.c_void_p), ("shell_l", C.c_void_p),
+        ("shell_radial", C.c_void_p), ("shell_zeta", C.c_void_p),
+        ("L", C.c_int), ("lam", C.c_void_p), ("n_up", C.c_int), ("n_dn", C.c_int),
+        ("unpaired", C.c_void_p), ("b_ea", C.c_double), ("b_para", C.c_double),
+        ("b_anti", C.c_double), ("use_j1", C.c_int), ("use_j2", C.c_int),
+        ("j2_spin_independent", C.c_int),
+    ]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle (idempotent); returns the library path."""
+    with _lock:
+        if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+            return _LIB
+        os.makedirs(_OUT, exist_ok=True)
+        base = ["gcc", "-O2", "-fPIC", "-shared", "-ffp-contract=off", "-std=c11", _SRC, "-o", _LIB + ".tmp", "-lm"]
+        try:
+            subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True, capture_output=True)
+        except subprocess.CalledProcessError:
+            subprocess.run(base, check=True, capture_output=True)
+        os.replace(_LIB + ".tmp", _LIB)
+        return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = build()
+        L = C.CDLL(path)
+        vp, i, d = C.c_void_p, C.c_int, C.c_double
+        L.orc_philox4x32_10.argtypes = [vp, vp, vp]
+        L.orc_ao_full.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        L.orc_logpsi.argtypes = [vp, vp, vp]
+        L.orc_logpsi.restype = i
+        L.orc_local_energy_ex.argtypes = [vp, vp, vp, vp, vp]
+        L.orc_local_energy_ex.restype = i
+        L.orc_local_energy_batch.argtypes = [vp, vp, i, vp]
+        L.orc_local_energy_batch.restype = i
+        L.orc_logpsi_batch.argtypes = [vp, vp, i, vp, vp]
+        L.orc_logpsi_batch.restype = i
+        L.orc_det_inverse.argtypes = [i, vp, vp, vp, vp]
+        L.orc_det_inverse.restype = i
+        L.orc_geminal.argtypes = [vp, vp, vp]
+        L.orc_jastrow.argtypes = [vp, vp]
+        L.orc_jastrow.restype = d
+        L.orc_jastrow_derivs.argtypes = [vp, vp, vp, vp]
+        L.orc_sm_ratio_row.argtypes = [i, vp, i, vp]
+        L.orc_sm_ratio_row.restype = d
+        L.orc_sm_update_row.argtypes = [i, vp, i, vp]
+        L.orc_move_draws.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, d, vp, vp, vp]
+        L.orc_vmc.argtypes = [vp, vp, i, C.c_longlong, C.c_uint64, C.c_longlong, i, d, vp, vp, vp, i]
+        L.orc_vmc.restype = i
+        L.orc_grad_logpsi.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.orc_grad_logpsi.restype = i
+        L.orc_max_threads.restype = i
+        _lib = L
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data
+
+
+def philox4x32_10(ctr, key):
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    o = np.zeros(4, np.uint32)
+    lib().orc_philox4x32_10(_p(c), _p(k), _p(o))
+    return o
+
+
+def det_inverse(A):
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    n = A.shape[0]
+    la, sg = np.zeros(1), np.zeros(1)
+    inv = np.zeros((n, n))
+    ok = lib().orc_det_inverse(n, _p(A), _p(la), _p(sg), _p(inv))
+    return bool(ok), float(la[0]), float(sg[0]), inv
+
+
+def sm_ratio_row(Ginv, i, newrow):
+    Ginv = np.ascontiguousarray(Ginv, dtype=np.float64)
+    newrow = np.ascontiguousarray(newrow, dtype=np.float64)
+    return lib().orc_sm_ratio_row(Ginv.shape[0], _p(Ginv), int(i), _p(newrow))
+
+
+def sm_update_row(Ginv, i, newrow):
+    G = np.array(Ginv, dtype=np.float64, order="C")
+    newrow = np.ascontiguousarray(newrow, dtype=np.float64)
+    lib().orc_sm_update_row(G.shape[0], _p(G), int(i), _p(newrow))
+    return G
+
+
+def move_draws(seed, walker, sweep, electron, delta, r):
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    rp = np.zeros(3)
+    u = np.zeros(1)
+    lib().orc_move_draws(C.c_uint64(seed), walker, sweep, electron, float(delta), _p(r), _p(rp), _p(u))
+    return rp, float(u[0])
+
+
+def max_threads() -> int:
+    return int(lib().orc_max_threads())
+
+
+class Oracle:
+    """The oracle bound to one synthetic system (``synth.System``)."""
+
+    def __init__(self, sys):
+        self.sys = sys
+        self._keep = [sys.R, sys.Z, sys.shell_atom, sys.shell_l, sys.shell_radial,
+                      sys.shell_zeta, sys.lam, sys.unpaired]
+        s = _OrcSystem()
+        s.n_atoms = sys.n_atoms
+        s.R, s.Z = _p(sys.R), _p(sys.Z)
+        s.n_shells = sys.n_shells
+        s.shell_atom, s.shell_l = _p(sys.shell_atom), _p(sys.shell_l)
+        s.shell_radial, s.shell_zeta = _p(sys.shell_radial), _p(sys.shell_zeta)
+        s.L = sys.L
+        s.lam = _p(sys.lam)
+        s.n_up, s.n_dn = sys.n_up, sys.n_dn
+        s.unpaired = _p(sys.unpaired)
+        s.b_ea, s.b_para, s.b_anti = sys.b_ea, sys.b_para, sys.b_anti
+        s.use_j1, s.use_j2 = int(sys.use_j1), int(sys.use_j2)
+        s.j2_spin_independent = int(sys.j2_spin_independent)
+        self._s = s
+        self._ps = C.addressof(s)
+        self.N, self.L, self.nu = sys.N, sys.L, sys.n_up
+
+    # --- single configuration --------------------------------------------
+    def ao(self, r, hess=False):
+        r = np.ascontiguousarray(r, dtype=np.float64)
+        L = self.L
+        v, g, l = np.zeros(L), np.zeros((L, 3)), np.zeros(L)
+        H = np.zeros((L, 3, 3)) if hess else None
+        gl = np.zeros((L, 3)) if hess else None
+        lib().orc_ao_full(self._ps, _p(r), _p(v), _p(g), _p(l), _p(H), _p(gl))
+        return (v, g, l, H, gl) if hess else (v, g, l)
+
+    def geminal(self, x):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        phi = np.stack([self.ao(x[i])[0] for i in range(self.N)])
+        G = np.zeros((self.nu, self.nu))
+        lib().orc_geminal(self._ps, _p(phi), _p(G))
+        return G
+
+    def logpsi(self, x):
+        """(log|Psi|, sign, log|det G~|, J)"""
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        out = np.zeros(4)
+        ok = lib().orc_logpsi(self._ps, _p(x), _p(out))
+        if not ok:
+            raise ValueError("singular geminal matrix")
+        return tuple(float(v) for v in out)
+
+    def jastrow(self, x):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        return float(lib().orc_jastrow(self._ps, _p(x)))
+
+    def jastrow_derivs(self, x):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        g, l = np.zeros((self.N, 3)), np.zeros(self.N)
+        lib().orc_jastrow_derivs(self._ps, _p(x), _p(g), _p(l))
+        return g, l
+
+    def local_energy(self, x, parts=False):
+        """e_L (or (e_L, kinetic, V_ee, V_ei, V_ii, gradD/D, lapD/D) if parts)."""
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        out = np.zeros(5)
+        gD, lD = np.zeros((self.N, 3)), np.zeros(self.N)
+        ok = lib().orc_local_energy_ex(self._ps, _p(x), _p(out), _p(gD), _p(lD))
+        if not ok:
+            raise ValueError("singular geminal matrix")
+        return (tuple(float(v) for v in out) + (gD, lD)) if parts else float(out[0])
+
+    def grad_logpsi(self, x, want_lam=True):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        dlam = np.zeros((self.L, self.L)) if want_lam else None
+        djas = np.zeros(3)
+        dR = np.zeros((self.sys.n_atoms, 3))
+        dr = np.zeros((self.N, 3))
+        ok = lib().orc_grad_logpsi(self._ps, _p(x), _p(dlam), _p(djas), _p(dR), _p(dr))
+        if not ok:
+            raise ValueError("singular geminal matrix")
+        return {"lam": dlam, "jas": djas, "R": dR, "r": dr}
+
+    # --- batches ------------------------------------------------------------
+    def local_energy_batch(self, x):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        W = x.shape[0]
+        e = np.zeros(W)
+        lib().orc_local_energy_batch(self._ps, _p(x), W, _p(e))
+        return e
+
+    def logpsi_batch(self, x):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        W = x.shape[0]
+        la, sg = np.zeros(W), np.zeros(W)
+        lib().orc_logpsi_batch(self._ps, _p(x), W, _p(la), _p(sg))
+        return la, sg
+
+    def vmc(self, x, nsweeps, seed=0, sweep0=0, walker0=0, delta=None, record_eL=True,
+            nthreads=0):
+        """Run nsweeps Metropolis sweeps in place on x [W][N][3].
+        Returns (eL [nsweeps][W] or None, logpsi [W], n_accept [W])."""
+        assert x.dtype == np.float64 and x.flags["C_CONTIGUOUS"]
+        W = x.shape[0]
+        eL = np.zeros((nsweeps, W)) if record_eL else None
+        lp = np.zeros(W)
+        nacc = np.zeros(W, dtype=np.int64)
+        d = self.sys.delta if delta is None else delta
+        ok = lib().orc_vmc(self._ps, _p(x), W, walker0, C.c_uint64(seed), sweep0, nsweeps, float(d),
+                           _p(eL), _p(lp), _p(nacc), int(nthreads))
+        if not ok:
+            raise ValueError("singular geminal matrix at the start of a walker")
+        return eL, lp, nacc

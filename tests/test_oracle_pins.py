@@ -1,0 +1,401 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Every test here runs on the CPU (no GPU marker).  Each one would fail for a
+plausible mistake in the oracle: a wrong sign in a Jastrow derivative, a
+transposed lambda, a dropped cross term in the kinetic energy, a wrong
+pivot sign in the LU, a biased proposal in the sampler.
+"""
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _rand_cfg(sys, seed, spread=1.2):
+    rng = np.random.default_rng(seed)
+    x = synth.init_walkers(sys, 1, seed=seed)[0]
+    return np.ascontiguousarray(x + rng.uniform(-spread, spread, size=x.shape) * 0.3)
+
+
+# ----------------------------------------------------------------------------
+# Philox4x32-10: published known-answer vectors
+# ----------------------------------------------------------------------------
+
+def test_philox_known_answers():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt"))
+            if l.strip() and not l.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(t, 16) for t in r]
+        out = oracle.philox4x32_10(v[0:4], v[4:6])
+        assert [int(o) for o in out] == v[6:10]
+
+
+def test_move_draws_ranges():
+    """Proposals stay within delta of r in each coordinate and u_acc is in [0,1)."""
+    r = np.array([0.1, -0.2, 0.3])
+    for e in range(200):
+        rp, u = oracle.move_draws(0, 3, 5, e, 0.7, r)
+        assert np.all(np.abs(rp - r) < 0.7) and 0.0 <= u < 1.0
+
+
+# ----------------------------------------------------------------------------
+# local energy: closed forms per configuration (zero variance, Sec. VMC)
+# ----------------------------------------------------------------------------
+
+def test_hydrogen_zero_variance():
+    o = oracle.Oracle(synth.hydrogen_slater())
+    rng = np.random.default_rng(1)
+    for _ in range(50):
+        x = rng.normal(0, 1.5, size=(1, 3))
+        assert abs(o.local_energy(x) - (-0.5)) < 1e-12
+
+
+@pytest.mark.parametrize("beta", [0.6, 1.3])
+def test_slater_one_electron_per_config(beta):
+    o = oracle.Oracle(synth.one_electron_slater(beta))
+    rng = np.random.default_rng(2)
+    for _ in range(20):
+        x = rng.normal(0, 1.5, size=(1, 3))
+        r = np.linalg.norm(x)
+        assert abs(o.local_energy(x) - (-beta ** 2 / 2 + (beta - 1) / r)) < 1e-12 * (1 + 1 / r)
+
+
+@pytest.mark.parametrize("alpha", [0.2, 0.9])
+def test_gaussian_one_electron_per_config(alpha):
+    o = oracle.Oracle(synth.one_electron_gauss(alpha))
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        x = rng.normal(0, 1.0, size=(1, 3))
+        r = np.linalg.norm(x)
+        ref = 3 * alpha - 2 * alpha ** 2 * r * r - 1 / r
+        assert abs(o.local_energy(x) - ref) < 1e-11 * (1 + abs(ref))
+
+
+@pytest.mark.parametrize("Z", [1.0, 2.0])
+def test_hydrogenic_via_one_body_jastrow(Z):
+    """exp(J1) with b_ea -> 0 is exp(-Z r), an exact eigenstate: e_L = -Z^2/2."""
+    o = oracle.Oracle(synth.hydrogenic_gauss_j1(Z))
+    rng = np.random.default_rng(4)
+    for _ in range(20):
+        x = rng.normal(0, 1.0, size=(1, 3))
+        assert abs(o.local_energy(x) - (-Z * Z / 2)) < 1e-11
+
+
+def test_helium_product_per_config():
+    beta = 1.45
+    o = oracle.Oracle(synth.helium_slater(beta))
+    rng = np.random.default_rng(5)
+    for _ in range(20):
+        x = rng.normal(0, 1.0, size=(2, 3))
+        r1, r2 = np.linalg.norm(x[0]), np.linalg.norm(x[1])
+        r12 = np.linalg.norm(x[0] - x[1])
+        ref = -beta ** 2 + (beta - 2.0) * (1 / r1 + 1 / r2) + 1 / r12
+        assert abs(o.local_energy(x) - ref) < 1e-11 * (1 + abs(ref))
+
+
+# ----------------------------------------------------------------------------
+# the sampler: textbook variational energies within the statistical error
+# ----------------------------------------------------------------------------
+
+def _vmc_mean(sysm, W=1024, sweeps=120, equil=20, seed=11):
+    o = oracle.Oracle(sysm)
+    x = np.ascontiguousarray(synth.init_walkers(sysm, W, seed=seed))
+    eL, _, nacc = o.vmc(x, sweeps, seed=seed)
+    wm = eL[equil:].mean(axis=0)          # walkers are independent chains
+    return wm.mean(), wm.std(ddof=1) / math.sqrt(W), nacc.sum() / (W * sweeps * sysm.N)
+
+
+def test_vmc_slater_one_electron_mean():
+    beta = 0.8
+    m, err, acc = _vmc_mean(synth.one_electron_slater(beta))
+    assert 0.2 < acc < 0.95
+    assert abs(m - (beta ** 2 / 2 - beta)) < 4.5 * err, (m, err)
+
+
+def test_vmc_gaussian_one_electron_mean():
+    a = 0.3
+    m, err, _ = _vmc_mean(synth.one_electron_gauss(a))
+    assert abs(m - (1.5 * a - 2 * math.sqrt(2 * a / math.pi))) < 4.5 * err, (m, err)
+
+
+def test_vmc_helium_mean():
+    vals = dict(l.split() for l in open(os.path.join(GOLDEN, "closed_forms.txt"))
+                if l.strip() and not l.startswith("#"))
+    beta = float(vals["he_optimal_beta"])
+    m, err, _ = _vmc_mean(synth.helium_slater(beta), W=768, sweeps=100)
+    assert abs(m - float(vals["he_optimal_energy"])) < 4.5 * err, (m, err)
+    # a wrong sampler (e.g. sampling |Psi| instead of Psi^2) misses by far more
+    assert err < 0.02
+
+
+# ----------------------------------------------------------------------------
+# determinant: AGP <-> SD, Cauchy-Binet (seniority-zero expansion), LU
+# ----------------------------------------------------------------------------
+
+def test_lu_against_library():
+    rng = np.random.default_rng(6)
+    for n in (1, 2, 5, 17):
+        A = rng.normal(size=(n, n))
+        ok, la, sg, inv = oracle.det_inverse(A)
+        s_ref, la_ref = np.linalg.slogdet(A)
+        assert ok and abs(la - la_ref) < 1e-12 * max(1, abs(la_ref)) and sg == s_ref
+        assert np.allclose(inv @ A, np.eye(n), atol=1e-11)
+    ok, *_ = oracle.det_inverse(np.zeros((3, 3)))
+    assert not ok
+
+
+def test_agp_rank_n_equals_slater_determinant():
+    """lambda = C C^T of rank n gives det(Phi_up C) det(Phi_dn C) (Sec. SD)."""
+    s = synth.small_random(n_atoms=3, n_up=3, n_dn=3, per_atom=6, seed=8, use_j1=False, use_j2=False)
+    rng = np.random.default_rng(8)
+    Cm = rng.normal(size=(s.L, s.n_up))
+    s.lam = np.ascontiguousarray(Cm @ Cm.T)
+    o = oracle.Oracle(s)
+    x = _rand_cfg(s, 9)
+    G = o.geminal(x)
+    phi = np.stack([o.ao(x[i])[0] for i in range(s.N)])
+    ref = np.linalg.det(phi[:3] @ Cm) * np.linalg.det(phi[3:] @ Cm)
+    assert abs(np.linalg.det(G) - ref) < 1e-10 * abs(ref)
+    la, sg, ld, J = o.logpsi(x)
+    assert abs(ld - math.log(abs(ref))) < 1e-10 and sg == np.sign(ref)
+
+
+@pytest.mark.parametrize("n,L", [(2, 5), (3, 6)])
+def test_cauchy_binet_seniority_zero(n, L):
+    """Diagonal lambda: det G = sum over n-subsets S of prod lambda_S det Phi_up[:,S] det Phi_dn[:,S]
+    (the pair-occupation expansion of Sec. "Implicit multiconfigurational character")."""
+    s = synth.small_random(n_atoms=2, n_up=n, n_dn=n, per_atom=6, seed=10, use_j1=False, use_j2=False)
+    # keep the first L functions only (two atoms x 6)
+    keep = L
+    shells, tot = [], 0
+    for k, l in enumerate(s.shell_l):
+        if tot + 2 * l + 1 <= keep:
+            shells.append(k)
+            tot += 2 * l + 1
+    s.shell_atom, s.shell_l = s.shell_atom[shells].copy(), s.shell_l[shells].copy()
+    s.shell_radial, s.shell_zeta = s.shell_radial[shells].copy(), s.shell_zeta[shells].copy()
+    L = tot
+    d = np.random.default_rng(n).uniform(0.5, 1.5, size=L)
+    s.lam = np.ascontiguousarray(np.diag(d))
+    s.check()
+    o = oracle.Oracle(s)
+    x = _rand_cfg(s, 12)
+    phi = np.stack([o.ao(x[i])[0] for i in range(s.N)])
+    Pu, Pd = phi[:n], phi[n:]
+    tot_cb = 0.0
+    for S in itertools.combinations(range(L), n):
+        S = list(S)
+        tot_cb += np.prod(d[S]) * np.linalg.det(Pu[:, S]) * np.linalg.det(Pd[:, S])
+    la, sg, ld, J = o.logpsi(x)
+    assert abs(sg * math.exp(ld) - tot_cb) < 1e-11 * abs(tot_cb)
+
+
+def test_antisymmetry_same_spin_exchange():
+    s = synth.small_random(n_atoms=3, n_up=3, n_dn=2, per_atom=6, seed=13, slater_fraction=0.3)
+    o = oracle.Oracle(s)
+    x = _rand_cfg(s, 14)
+    la, sg, _, _ = o.logpsi(x)
+    e = o.local_energy(x)
+    for (i, j) in ((0, 2), (3, 4)):       # two up electrons, two down electrons
+        y = x.copy()
+        y[[i, j]] = y[[j, i]]
+        la2, sg2, _, _ = o.logpsi(y)
+        assert abs(la2 - la) < 1e-12 and sg2 == -sg
+        assert abs(o.local_energy(y) - e) < 1e-10 * (1 + abs(e))
+
+
+# ----------------------------------------------------------------------------
+# Sherman-Morrison against full recomputation
+# ----------------------------------------------------------------------------
+
+def test_sherman_morrison_ratio_and_drift():
+    rng = np.random.default_rng(15)
+    n = 12
+    G = rng.normal(size=(n, n)) + 3 * np.eye(n)
+    ok, la, sg, Ginv = oracle.det_inverse(G)
+    for step in range(100):
+        i = int(rng.integers(n))
+        row = G[i] + rng.normal(scale=0.3, size=n)
+        R = oracle.sm_ratio_row(Ginv, i, row)
+        G2 = G.copy()
+        G2[i] = row
+        ok2, la2, sg2, _ = oracle.det_inverse(G2)
+        assert abs(R - sg * sg2 * math.exp(la2 - la)) < 1e-12 * abs(R) * 10
+        Ginv = oracle.sm_update_row(Ginv, i, row)
+        G, la, sg = G2, la2, sg2
+    ok, _, _, fresh = oracle.det_inverse(G)
+    assert np.max(np.abs(Ginv - fresh)) < 1e-10 * np.max(np.abs(fresh))
+
+
+# ----------------------------------------------------------------------------
+# analytic derivatives against central finite differences
+# ----------------------------------------------------------------------------
+
+def test_orbital_derivatives_fd():
+    s = synth.small_random(n_atoms=2, n_up=2, n_dn=1, per_atom=24, seed=16, slater_fraction=0.4)
+    o = oracle.Oracle(s)
+    r = np.array([0.7, -0.4, 1.1])
+    v, g, l, H, gl = o.ao(r, hess=True)
+    h = 1e-4
+    for q in range(3):
+        dp, dm = r.copy(), r.copy()
+        dp[q] += h
+        dm[q] -= h
+        vp, gp, lp = o.ao(dp)
+        vm, gm, lm = o.ao(dm)
+        assert np.allclose((vp - vm) / (2 * h), g[:, q], rtol=1e-7, atol=1e-9)
+        assert np.allclose((gp - gm) / (2 * h), H[:, q, :], rtol=1e-6, atol=1e-8)
+        assert np.allclose((lp - lm) / (2 * h), gl[:, q], rtol=1e-6, atol=1e-8)
+    assert np.allclose(np.trace(H, axis1=1, axis2=2), l, rtol=1e-12, atol=1e-13)
+
+
+def _logpsi_signed(o, x):
+    la, sg, _, _ = o.logpsi(x)
+    return la, sg
+
+
+@pytest.mark.parametrize("seed,sym", [(17, True), (18, False)])
+def test_kinetic_and_gradient_fd(seed, sym):
+    """grad log|Psi| against h=1e-4 central differences; the kinetic energy
+    -1/2 sum lap Psi/Psi against h=1e-3 second differences of Psi."""
+    s = synth.small_random(n_atoms=3, n_up=3, n_dn=2, per_atom=6, seed=seed, symmetric=sym,
+                           slater_fraction=0.3)
+    o = oracle.Oracle(s)
+    x = _rand_cfg(s, seed + 100)
+    g = o.grad_logpsi(x, want_lam=False)["r"]
+    e, kin, vee, vei, vii, gD, lD = o.local_energy(x, parts=True)
+    la0, sg0 = _logpsi_signed(o, x)
+    h1, h2 = 1e-4, 1e-3
+    lap_sum = 0.0
+    for i in range(s.N):
+        for q in range(3):
+            xp, xm = x.copy(), x.copy()
+            xp[i, q] += h1
+            xm[i, q] -= h1
+            fd = (_logpsi_signed(o, xp)[0] - _logpsi_signed(o, xm)[0]) / (2 * h1)
+            assert abs(fd - g[i, q]) < 1e-7 * (1 + abs(g[i, q]))
+            xp, xm = x.copy(), x.copy()
+            xp[i, q] += h2
+            xm[i, q] -= h2
+            lp, sp = _logpsi_signed(o, xp)
+            lm, sm = _logpsi_signed(o, xm)
+            lap_sum += (sp * sg0 * math.exp(lp - la0) + sm * sg0 * math.exp(lm - la0) - 2.0) / h2 ** 2
+    assert abs(-0.5 * lap_sum - kin) < 1e-5 * (1 + abs(kin))
+
+
+def test_potential_terms_by_hand():
+    s = synth.small_random(n_atoms=2, n_up=2, n_dn=1, per_atom=6, seed=19)
+    o = oracle.Oracle(s)
+    x = _rand_cfg(s, 20)
+    _, _, vee, vei, vii, _, _ = o.local_energy(x, parts=True)
+    ref_ee = sum(1 / np.linalg.norm(x[i] - x[j]) for i in range(3) for j in range(i + 1, 3))
+    ref_ei = -sum(s.Z[a] / np.linalg.norm(x[i] - s.R[a]) for i in range(3) for a in range(2))
+    ref_ii = s.Z[0] * s.Z[1] / np.linalg.norm(s.R[0] - s.R[1])
+    assert abs(vee - ref_ee) < 1e-13 and abs(vei - ref_ei) < 1e-13 and abs(vii - ref_ii) < 1e-13
+
+
+def test_parameter_gradients_fd():
+    """d log|Psi| / d lambda, d/d b_ea, b_para, b_anti and d/d R_a by central FD."""
+    s = synth.small_random(n_atoms=2, n_up=2, n_dn=2, per_atom=6, seed=21, symmetric=False,
+                           slater_fraction=0.3)
+    o = oracle.Oracle(s)
+    x = _rand_cfg(s, 22)
+    gr = o.grad_logpsi(x)
+    h = 1e-5
+
+    def lp_with(mod):
+        t = synth.small_random(n_atoms=2, n_up=2, n_dn=2, per_atom=6, seed=21, symmetric=False,
+                               slater_fraction=0.3)
+        mod(t)
+        t.check()
+        return oracle.Oracle(t).logpsi(x)[0]
+
+    rng = np.random.default_rng(23)
+    for _ in range(6):
+        mu, nu = rng.integers(s.L, size=2)
+
+        def m(t, d):
+            t.lam = t.lam.copy()
+            t.lam[mu, nu] += d
+        fd = (lp_with(lambda t: m(t, h)) - lp_with(lambda t: m(t, -h))) / (2 * h)
+        assert abs(fd - gr["lam"][mu, nu]) < 1e-6 * (1 + abs(fd))
+    for k, name in enumerate(("b_ea", "b_para", "b_anti")):
+        b0 = getattr(s, name)
+        fd = (lp_with(lambda t: setattr(t, name, b0 + h)) - lp_with(lambda t: setattr(t, name, b0 - h))) / (2 * h)
+        assert abs(fd - gr["jas"][k]) < 1e-6 * (1 + abs(fd))
+    for a in range(2):
+        for q in range(3):
+            def mr(t, d):
+                t.R = t.R.copy()
+                t.R[a, q] += d
+            fd = (lp_with(lambda t: mr(t, h)) - lp_with(lambda t: mr(t, -h))) / (2 * h)
+            assert abs(fd - gr["R"][a, q]) < 1e-6 * (1 + abs(fd))
+
+
+# ----------------------------------------------------------------------------
+# invariants and cusps
+# ----------------------------------------------------------------------------
+
+def test_lambda_scale_invariance():
+    s = synth.small_random(n_atoms=3, n_up=3, n_dn=2, per_atom=6, seed=24)
+    o = oracle.Oracle(s)
+    x = _rand_cfg(s, 25)
+    la, _, _, _ = o.logpsi(x)
+    e = o.local_energy(x)
+    c = -2.5
+    s.lam = np.ascontiguousarray(c * s.lam)
+    o2 = oracle.Oracle(s)
+    la2, _, _, _ = o2.logpsi(x)
+    assert abs(la2 - (la + s.n_dn * math.log(abs(c)))) < 1e-11
+    assert abs(o2.local_energy(x) - e) < 1e-10 * (1 + abs(e))
+
+
+def test_translation_invariance():
+    s = synth.small_random(n_atoms=3, n_up=2, n_dn=2, per_atom=20, seed=26, slater_fraction=0.2)
+    o = oracle.Oracle(s)
+    x = _rand_cfg(s, 27)
+    la, sg, _, _ = o.logpsi(x)
+    e = o.local_energy(x)
+    t = np.array([0.37, -1.1, 0.52])
+    s.R = np.ascontiguousarray(s.R + t)
+    o2 = oracle.Oracle(s)
+    la2, sg2, _, _ = o2.logpsi(x + t)
+    assert abs(la2 - la) < 1e-10 and sg2 == sg
+    assert abs(o2.local_energy(x + t) - e) < 1e-9 * (1 + abs(e))
+    # the same statement, differentiated: sum_a dR_a + sum_i dr_i = 0
+    g = o.grad_logpsi(x, want_lam=False)
+    assert np.allclose(g["R"].sum(0) + g["r"].sum(0), 0.0, atol=1e-9)
+
+
+def test_cusp_conditions():
+    """Kato cusps carried by the Jastrow: dJ2/dr -> 1/2 (antiparallel), 1/4
+    (parallel); dJ1/dr -> -Z (Eqs. onebody_J_hom, onebody_u, twobody_v)."""
+    s = synth.small_random(n_atoms=1, n_up=2, n_dn=1, per_atom=6, seed=28, Z=2.0)
+    o = oracle.Oracle(s)
+    far = 1e5    # the third electron sits far away so that only one pair varies
+    base = np.array([[5.0, 5.0, 5.0], [far, far, far], [5.0, 5.0, 5.0]])
+
+    def slope(i, j, eps=1e-7):
+        x1, x2 = base.copy(), base.copy()
+        x1[i] = x1[j] + np.array([eps, 0, 0])
+        x2[i] = x2[j] + np.array([2 * eps, 0, 0])
+        return (o.jastrow(x2) - o.jastrow(x1)) / eps
+
+    s.use_j1 = False
+    o = oracle.Oracle(s)
+    assert abs(slope(2, 0) - 0.5) < 1e-5          # up-down pair
+    base[2] = [-far, far, -far]
+    assert abs(slope(1, 0) - 0.25) < 1e-5         # up-up pair
+    s.use_j1, s.use_j2 = True, False
+    o = oracle.Oracle(s)
+    x1 = np.array([s.R[0] + [1e-7, 0, 0], [far, far, far], [-far, far, -far]])
+    x2 = np.array([s.R[0] + [2e-7, 0, 0], [far, far, far], [-far, far, -far]])
+    assert abs((o.jastrow(x2) - o.jastrow(x1)) / 1e-7 - (-2.0)) < 1e-5
