@@ -1,0 +1,352 @@
+#!/usr/bin/env python
+"""Benchmark of the JAGP VMC hot path on one GB300 (or N, one process each).
+
+A step is one pass of the whole path over every walker: one Metropolis sweep
+(every electron proposed once: orbital evaluation, proposed rows/columns of
+G~, sequential Sherman-Morrison acceptance, lambda products of the accepted
+rows), the FP64 refresh of G~^{-1}, log|det| and J, the local energy of every
+walker and the per-sweep reductions.
+
+Workload (N=1): the plain-FP64 VMC configuration with 16 He atoms in a 10 bohr
+cube, N = 32 electrons (16 up, 16 down), 20 s/p/d Gaussians per atom (L = 320),
+dense random symmetric lambda, one- and two-body Jastrow, 4096 walkers.
+The walker state (~1 GB) is larger than L2, so no flush is needed between
+steps.  Under torchrun each rank runs its own 4096 walkers (weak scaling, no
+data-path collective; a barrier and a max-reduction of the timings only).
+
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "walker-electron moves/s and E_L+forces/s, mixed/batched vs plain FP64 on 1 GB300"
+UNIT = "walker-electron moves/s"
+WORKLOAD = ("plain FP64 VMC: 16 He atoms in a 10 bohr cube (min separation 1.5), N=32 (16 up, 16 down), "
+            "20 s/p/d Gaussians/atom (L=320), dense random symmetric lambda, J1 + J2, 4096 walkers/GPU")
+# FP64 CUDA-core peak of one GB300 (no measured value available): 1.25 TFLOP/s nominal
+FP64_PEAK_TFLOPS = 1.25
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "k_lambda_rows_C2_traffic.json")
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def emit(obj):
+    print(json.dumps(obj), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                p = [t.strip() for t in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    sm.append(float(p[1]))
+                    smax.append(float(p[2]))
+                except ValueError:
+                    continue
+                for name, v in zip(names, p[5:9]):
+                    if v.lower() in ("active", "0x1") or v == "1":
+                        reasons.add(name)
+        except OSError:
+            pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle (test infrastructure) timed on the host cores
+# ----------------------------------------------------------------------------
+def oracle_rate(sysm, target_s: float = 15.0, max_walkers: int = 4096):
+    """Oracle VMC sweep + local energy on a bounded walker sample; returns
+    (moves/s, e_L/s, cores, sample description, seconds)."""
+    import oracle
+    import synth
+    o = oracle.Oracle(sysm)
+    cores = oracle.max_threads()
+    Ws = max(cores, 8)
+    while True:
+        x = synth.init_walkers(sysm, Ws, seed=0)
+        t0 = time.perf_counter()
+        o.vmc(x, 1, seed=0, sweep0=0, walker0=0, record_eL=True, nthreads=cores)
+        dt = time.perf_counter() - t0
+        if dt >= target_s * 0.5 or Ws >= max_walkers:
+            break
+        Ws = min(max_walkers, int(Ws * min(8.0, max(2.0, target_s / max(dt, 1e-3)))))
+    moves = Ws * sysm.N
+    return moves / dt, Ws / dt, cores, f"{Ws} walkers x 1 sweep (+ e_L per walker) of the same system", dt
+
+
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return os.uname().machine
+
+
+# ----------------------------------------------------------------------------
+# reference arm: the CPU oracle as it stands
+# ----------------------------------------------------------------------------
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import synth
+    sysm = synth.config2()
+    import oracle
+    o = oracle.Oracle(sysm)
+    cores = oracle.max_threads()
+    # size one step so that the whole --steps/--warmup run stays near two minutes
+    per_step = max(1.0, 120.0 / (args.steps + args.warmup))
+    Ws = max(cores, 8)
+    x = synth.init_walkers(sysm, Ws, seed=0)
+    t0 = time.perf_counter()
+    o.vmc(x, 1, seed=0, record_eL=True, nthreads=cores)
+    dt = time.perf_counter() - t0
+    Ws = int(min(4096, max(Ws, Ws * per_step / max(dt, 1e-3))))
+    x = synth.init_walkers(sysm, Ws, seed=0)
+    for k in range(args.warmup):
+        o.vmc(x, 1, seed=0, sweep0=k, record_eL=True, nthreads=cores)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        o.vmc(x, 1, seed=0, sweep0=args.warmup + k, record_eL=True, nthreads=cores)
+    dt = time.perf_counter() - t0
+    value = Ws * sysm.N * args.steps / dt
+    sample = f"{Ws} walkers per step (of 4096), 1 sweep + e_L per walker, {cores} threads, {cpu_model()}"
+    emit({"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+          "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+          "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+          "config": {"workload": WORKLOAD, "sample_walkers": Ws},
+          "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+          "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}})
+    return 0
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("k_linalg.cu", "jagp_common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2002_07401_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(src_hash):
+    try:
+        d = json.load(open(PROFILE_TRAFFIC))
+    except (OSError, ValueError):
+        return None, None
+    if d.get("source_hash") != src_hash:
+        return None, None
+    return d.get("dram_bytes_per_accepted_row"), d
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_2002_07401_gb300 as pg
+    import synth
+
+    ws, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (the CPU oracle is not a fallback)")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    sysm = synth.config2()
+    W = args.walkers
+    N, L = sysm.N, sysm.L
+    x_all = synth.init_walkers(sysm, W * ws, seed=0)
+    x0 = np.ascontiguousarray(x_all[rank * W:(rank + 1) * W])
+    walker0 = rank * W
+
+    g = pg.JAGP(sysm, W, seed=0)
+    h = g.h
+    r = g.positions(x0)
+    stream = torch.cuda.current_stream()
+    eL = torch.empty((1, W), dtype=torch.float64, device=dev)
+    acc_steps = torch.empty((args.steps, 4), dtype=torch.float64, device=dev)
+    acc_tmp = torch.empty((1, 4), dtype=torch.float64, device=dev)
+    pg.jagp_eval(h, r, W, g.state)
+    for k in range(args.warmup):
+        pg.vmc_sweep(h, r, g.state, W, 1, walker0, k, eL, acc_tmp)
+    torch.cuda.synchronize()
+    bits = g.status()
+
+    pg.jagp_profile(h, pg.KERNEL_LAMBDA_ROWS, True)
+    pg.jagp_profile_read(h)  # clear
+    n0 = pg.jagp_launch_count(h)
+    e_start, e_stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e_start.record(stream)
+        for k in range(args.steps):
+            pg.vmc_sweep(h, r, g.state, W, 1, walker0, args.warmup + k, eL, acc_steps[k:k + 1])
+        e_stop.record(stream)
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+    launches = pg.jagp_launch_count(h) - n0
+    lam_ms, lam_n = pg.jagp_profile_read(h)
+    pg.jagp_profile(h, pg.KERNEL_LAMBDA_ROWS, False)
+    ms = e_start.elapsed_time(e_stop)
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    acc = acc_steps.cpu().numpy()
+    accepted = float(acc[:, 2].sum())
+    bits |= g.status()
+
+    # end to end through the public API with host buffers: pinned host positions
+    # in, e_L and positions out, every step (state rebuilt by jagp_eval)
+    hx = torch.from_numpy(x0.copy()).pin_memory()
+    he = torch.empty(W, dtype=torch.float64).pin_memory()
+    hr = torch.empty_like(hx).pin_memory()
+    e2e_steps = max(2, min(args.steps, 5))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(e2e_steps):
+        r.copy_(hx, non_blocking=True)
+        pg.jagp_eval(h, r, W, g.state)
+        pg.vmc_sweep(h, r, g.state, W, 1, walker0, 10_000 + k, eL, None)
+        he.copy_(eL[0], non_blocking=True)
+        hr.copy_(r, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+    if ws > 1:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_value = W * N * e2e_steps * ws / float(e2e_t.item())
+
+    if rank != 0:
+        if ws > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return 0
+
+    moves = W * N * args.steps * ws
+    value = moves / (ms_max / 1e3)
+    # dominant kernel: lambda products of accepted rows, 2 L^2 flops per row
+    flops = 2.0 * L * L * accepted
+    achieved = flops / (lam_ms / 1e3) / 1e12 if lam_ms > 0 else None
+    src_hash = kernel_source_hash()
+    traffic_per_row, _ = profiled_traffic(src_hash)
+    rows_per_launch = accepted / max(lam_n, 1)
+    traffic = traffic_per_row * rows_per_launch if traffic_per_row else None
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "walkers_per_gpu": W, "n_electrons": N, "basis_functions": L,
+                   "precision": "fp64", "l2": "inputs larger than L2 (walker state ~1 GB per GPU)",
+                   "parallelism": f"walker shards x{ws}"},
+        "el_per_s": W * args.steps * ws / (ms_max / 1e3),
+        "acceptance": accepted / (W * N * args.steps),
+        "status_bits": bits,
+        "roofline": {"kernel": "k_lambda_rows", "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
+                     "traffic": traffic, "peak_source": "nominal FP64 of GB300 (no measured FP64 peak)",
+                     "launches": lam_n, "avg_launch_ms": lam_ms / max(lam_n, 1),
+                     "share_of_step": lam_ms / ms if ms > 0 else None},
+        "gpu_launches": launches,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(hx.numel() * 8),
+                "d2h_bytes_per_step": int(he.numel() * 8 + hr.numel() * 8), "steps": e2e_steps},
+        "clocks": clk.summary(),
+    }
+    if ws == 1 and not args.no_cpu_baseline:
+        mv, els, cores, sample, secs = oracle_rate(sysm, target_s=args.cpu_seconds)
+        out["cpu_baseline"] = {"value": mv, "unit": UNIT, "cores": cores, "kind": "oracle",
+                               "sample": f"{sample}; {secs:.1f} s; {cpu_model()}"}
+    emit(out)
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--walkers", type=int, default=4096)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,162 @@
+/*
+ * jagp.h -- C ABI of libjagp, a GB300 (sm_103a) implementation of the
+ * data-parallel hot path of variational Monte Carlo (VMC) for
+ * Jastrow-correlated antisymmetrized-geminal-power (JAGP) wave functions,
+ * following TurboRVB (Nakano et al., arXiv 2002.07401).
+ *
+ * Wave function (Sec. "Wave functions"):  Psi(x) = det(G~(x)) * exp(J(x)), with
+ *   G~ = [G_ud | Phi] the N_up x N_up geminal matrix of Eq. wfAGPunpaired,
+ *   G_ud[i][j] = sum_{mu,nu} phi_mu(r_i^up) lambda_{mu,nu} phi_nu(r_j^dn)   (Eq. agp_expansion)
+ *   Phi[i][l]  = sum_mu c^{(l)}_mu phi_mu(r_i^up)     (k = N_up - N_dn unpaired orbitals)
+ *   phi_mu: Gaussian or Slater atomic orbitals, l <= 2 (Eqs. gaussian, slater),
+ *   J = J1 + J2 (Eqs. onebody_J_hom, onebody_u, twobody_jastrow, twobody_v).
+ * Local energy e_L = H Psi / Psi (Sec. VMC, Eq. 1); sampling by single-electron
+ * Metropolis moves (Sec. VMC).
+ *
+ * Conventions shared by every call:
+ *   - Electron positions r are float64 [W][N][3] (bohr), up electrons first.
+ *   - Pointers named d_* are DEVICE pointers owned by the caller; pointers named
+ *     h_* (and everything reached through jagp_system_t) are HOST pointers,
+ *     copied during the call.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Calls are asynchronous on that stream unless stated otherwise.
+ *   - Every call returns a jagp_status_t; JAGP_OK is 0.  Argument errors are
+ *     detected on the host before any launch.  Numerical failures inside the
+ *     kernels (a non-finite ratio, a singular geminal matrix at a refresh) set
+ *     per-walker status bits that jagp_walker_status() reads back.
+ *   - The library never synchronises the device except where a call says so.
+ */
+#ifndef JAGP_H
+#define JAGP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int jagp_status_t;
+#define JAGP_OK 0
+#define JAGP_ERR_INVALID_ARG 1  /* a size, pointer or option is out of range */
+#define JAGP_ERR_SINGULAR 2     /* |det G~| = 0 or non-finite at a refresh */
+#define JAGP_ERR_NONFINITE 3    /* NaN/Inf in a position or a ratio */
+#define JAGP_ERR_OOM 4          /* a device allocation inside jagp_create failed */
+#define JAGP_ERR_TIMEOUT 5      /* a bounded device wait expired */
+#define JAGP_ERR_UNSUPPORTED 6  /* e.g. l > 2, N_dn > N_up, too many walkers */
+#define JAGP_ERR_CUDA 7         /* a CUDA runtime call failed */
+
+/* per-walker status bits (jagp_walker_status) */
+#define JAGP_WS_NONFINITE 1
+#define JAGP_WS_SINGULAR 2
+#define JAGP_WS_DRIFT 4          /* Sherman-Morrison drift above tolerance at a refresh */
+
+#define JAGP_PREC_FP64 0         /* every step in float64 */
+#define JAGP_PREC_MIXED 1        /* basis fp32, lambda products bf16 tensor cores (fp32 accumulate),
+                                    fp64 refresh / log-det / energies */
+
+/* The system: atoms, basis, pairing matrix lambda, unpaired orbitals, Jastrow.
+ * All pointers are host pointers, read during jagp_create only. */
+typedef struct jagp_system {
+  int n_atoms;
+  const double *R;            /* [n_atoms][3] nuclear positions (bohr) */
+  const double *Z;            /* [n_atoms] nuclear charges */
+  int n_shells;
+  const int *shell_atom;      /* [n_shells] owning atom */
+  const int *shell_l;         /* [n_shells] angular momentum 0..2 (components: s; x,y,z;
+                                 xy,yz,zx,x^2-y^2,3z^2-r^2, relative to the atom) */
+  const int *shell_radial;    /* [n_shells] 0 = Gaussian e^{-zeta r^2}, 1 = Slater e^{-zeta r} */
+  const double *shell_zeta;   /* [n_shells] exponent */
+  const double *lambda;       /* [L][L] row-major, L = sum (2l+1); need not be symmetric */
+  int n_up, n_dn;             /* N_up >= N_dn >= 0, N_up >= 1 */
+  const double *unpaired;     /* [N_up-N_dn][L] unpaired-orbital coefficients, NULL if equal */
+  double b_ea;                /* J1 parameter (0 = the b -> 0 limit u = r/2) */
+  double b_para, b_anti;      /* J2 parameters */
+  int use_j1, use_j2;
+  int j2_spin_independent;    /* 1: r/(2(1+b_anti r)) for every pair */
+} jagp_system_t;
+
+typedef struct jagp_options {
+  int precision;              /* JAGP_PREC_FP64 or JAGP_PREC_MIXED */
+  int max_walkers;            /* upper bound on W for every later call */
+  double delta;               /* proposal half-width: r' = r + delta (2u - 1) per coordinate */
+  uint64_t seed;              /* Philox4x32-10 key */
+  double drift_tol;           /* Sherman-Morrison drift tolerance checked at each refresh */
+} jagp_options_t;
+
+typedef struct jagp_ctx *jagp_handle_t;
+
+/* Create a handle: validates the system, copies lambda, lambda^T, the shell
+ * table and the unpaired orbitals to the current device (the handle owns
+ * those copies; jagp_destroy frees them).  Synchronous.
+ * Errors: INVALID_ARG (bad sizes/pointers), UNSUPPORTED (l > 2, N_dn > N_up,
+ * N_up > 64 in this release), OOM, CUDA. */
+jagp_status_t jagp_create(jagp_handle_t *out, const jagp_system_t *sys, const jagp_options_t *opt);
+jagp_status_t jagp_destroy(jagp_handle_t h);
+
+/* Bytes of device workspace ("walker state") that W walkers need.  The caller
+ * allocates it (e.g. a torch uint8 tensor), 256-byte aligned, and passes it to
+ * the calls below; it holds G~^{-1}, the orbital tables, log|det| and the
+ * per-walker counters.  Returns 0 for an invalid W. */
+size_t jagp_state_bytes(jagp_handle_t h, int W);
+
+/* log|Psi| and sign(Psi) of W configurations, and (re)build the walker state
+ * for them (Sec. AGP: G~ = Phi_up lambda Phi_dn^T | Phi_up C; LU with partial
+ * pivoting; J).  d_r: [W][N][3]; d_logabs, d_sign: [W] (either may be NULL).
+ * Afterwards d_state is consistent with d_r and may be passed to vmc_sweep /
+ * local_energy.  A singular G~ sets JAGP_WS_SINGULAR for that walker. */
+jagp_status_t jagp_eval(jagp_handle_t h, const double *d_r, int W, void *d_state, double *d_logabs,
+                        double *d_sign, void *stream);
+
+/* nsweeps Metropolis sweeps (Sec. VMC) over W walkers whose state came from
+ * jagp_eval or an earlier vmc_sweep on the same d_r.  One sweep moves every
+ * electron once (up electrons 0..N_up-1, then down), each move drawing the
+ * Philox4x32-10 block counter = (walker0 + w, sweep0 + t, electron, 1),
+ * key = (seed lo, seed hi): x0..x2 give the proposal, x3 the acceptance draw
+ * u = x3 2^-32; accept iff u < |Psi(x')/Psi(x)|^2.  The ratio uses
+ * Sherman-Morrison updates of G~^{-1}; G~^{-1}, log|det| and J are refreshed
+ * in FP64 after every sweep.  d_r is updated in place.
+ * d_eL: [nsweeps][W] local energy after each sweep, or NULL (no energies).
+ * d_acc: [nsweeps][4] (sum e_L, sum e_L^2, accepted moves, max drift) or NULL. */
+jagp_status_t vmc_sweep(jagp_handle_t h, double *d_r, void *d_state, int W, int nsweeps,
+                        uint64_t walker0, uint64_t sweep0, double *d_eL, double *d_acc, void *stream);
+
+/* Local energy e_L = -1/2 sum_i lap_i Psi/Psi + V_ee + V_ei + V_ii (Sec. VMC,
+ * Eq. 1) of W configurations whose state is current.  d_eL: [W].
+ * d_parts: [W][4] (kinetic, V_ee, V_ei, V_ii) or NULL. */
+jagp_status_t local_energy(jagp_handle_t h, const double *d_r, void *d_state, int W, double *d_eL,
+                           double *d_parts, void *stream);
+
+/* Copy per-walker bookkeeping to device arrays (each may be NULL):
+ * log|Psi|, sign, accepted moves since jagp_eval, last drift, status bits. */
+jagp_status_t jagp_walker_info(jagp_handle_t h, const void *d_state, int W, double *d_logabs,
+                               double *d_sign, double *d_naccept, double *d_drift, int *d_status,
+                               void *stream);
+
+/* OR of the status bits of all W walkers.  Synchronises `stream`. */
+jagp_status_t jagp_walker_status(jagp_handle_t h, const void *d_state, int W, int *h_bits,
+                                 void *stream);
+
+/* Profiling hooks (Sec. "Derivatives of energy" aside, these are tooling, not
+ * part of the method).  jagp_profile(h, kernel, 1) makes later vmc_sweep /
+ * jagp_eval calls record a CUDA event pair on the launching stream around every
+ * launch of `kernel` (JAGP_KERNEL_*); jagp_profile_read synchronises those
+ * events, returns the summed device time (ms) and the number of launches, and
+ * clears the record.  jagp_launch_count returns how many kernels the handle
+ * has launched since jagp_create. */
+#define JAGP_KERNEL_LAMBDA_ROWS 1   /* lambda products of accepted orbital rows */
+#define JAGP_KERNEL_GEMM_ROWS 2     /* proposed rows / columns and the refresh G~ */
+#define JAGP_KERNEL_METROPOLIS 3
+#define JAGP_KERNEL_BASIS 4
+#define JAGP_KERNEL_ENERGY 5        /* kinetic contraction + local energy */
+jagp_status_t jagp_profile(jagp_handle_t h, int kernel, int enable);
+jagp_status_t jagp_profile_read(jagp_handle_t h, double *h_total_ms, long long *h_launches);
+long long jagp_launch_count(jagp_handle_t h);
+
+const char *jagp_status_string(jagp_status_t s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* JAGP_H */

@@ -1,0 +1,266 @@
+"""GB300 (sm_103a) JAGP variational Monte Carlo hot path -- Python binding.
+
+A thin ctypes layer over the C ABI in ``include/jagp.h``: the functions below
+carry the same names as the C entry points and only marshal arguments (torch
+tensors give device memory and streams; every step runs in libjagp's CUDA
+kernels).  There is no CPU fallback: without the built library or a CUDA
+device every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+JAGP_OK = 0
+JAGP_PREC_FP64 = 0
+JAGP_PREC_MIXED = 1
+WS_NONFINITE, WS_SINGULAR, WS_DRIFT = 1, 2, 4
+
+
+class JagpError(RuntimeError):
+    pass
+
+
+class _System(C.Structure):
+    _fields_ = [
+        ("n_atoms", C.c_int), ("R", C.c_void_p), ("Z", C.c_void_p),
+        ("n_shells", C.c_int), ("shell_atom", C.c_void_p), ("shell_l", C.c_void_p),
+        ("shell_radial", C.c_void_p), ("shell_zeta", C.c_void_p), ("lambda_", C.c_void_p),
+        ("n_up", C.c_int), ("n_dn", C.c_int), ("unpaired", C.c_void_p),
+        ("b_ea", C.c_double), ("b_para", C.c_double), ("b_anti", C.c_double),
+        ("use_j1", C.c_int), ("use_j2", C.c_int), ("j2_spin_independent", C.c_int),
+    ]
+
+
+class _Options(C.Structure):
+    _fields_ = [
+        ("precision", C.c_int), ("max_walkers", C.c_int), ("delta", C.c_double),
+        ("seed", C.c_uint64), ("drift_tol", C.c_double),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    """Load libjagp.so (building it first if the sources are newer)."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        if not os.path.exists(path):
+            raise JagpError(f"libjagp not found at {path}")
+        L = C.CDLL(path)
+        vp, i, d, u64 = C.c_void_p, C.c_int, C.c_double, C.c_uint64
+        L.jagp_create.argtypes = [C.POINTER(vp), C.POINTER(_System), C.POINTER(_Options)]
+        L.jagp_destroy.argtypes = [vp]
+        L.jagp_state_bytes.argtypes = [vp, i]
+        L.jagp_state_bytes.restype = C.c_size_t
+        L.jagp_eval.argtypes = [vp, vp, i, vp, vp, vp, vp]
+        L.vmc_sweep.argtypes = [vp, vp, vp, i, i, u64, u64, vp, vp, vp]
+        L.local_energy.argtypes = [vp, vp, vp, i, vp, vp, vp]
+        L.jagp_walker_info.argtypes = [vp, vp, i, vp, vp, vp, vp, vp, vp]
+        L.jagp_walker_status.argtypes = [vp, vp, i, C.POINTER(C.c_int), vp]
+        L.jagp_profile.argtypes = [vp, i, i]
+        L.jagp_profile.restype = i
+        L.jagp_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]
+        L.jagp_profile_read.restype = i
+        L.jagp_launch_count.argtypes = [vp]
+        L.jagp_launch_count.restype = C.c_longlong
+        L.jagp_status_string.argtypes = [i]
+        L.jagp_status_string.restype = C.c_char_p
+        for f in ("jagp_create", "jagp_destroy", "jagp_eval", "vmc_sweep", "local_energy",
+                  "jagp_walker_info", "jagp_walker_status"):
+            getattr(L, f).restype = i
+        _lib = L
+    return _lib
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def _check(status: int, what: str):
+    if status != JAGP_OK:
+        msg = lib().jagp_status_string(status).decode()
+        raise JagpError(f"{what} failed: {msg} (status {status})")
+
+
+def _ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    return t.data_ptr()
+
+
+def _stream(stream) -> Optional[int]:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+# --------------------------------------------------------------------------
+# C entry points under the same names (argument marshalling only)
+# --------------------------------------------------------------------------
+
+def jagp_create(sysm, precision: int = JAGP_PREC_FP64, max_walkers: int = 1, delta: Optional[float] = None,
+                seed: int = 0, drift_tol: float = 1e-8) -> int:
+    """sysm: a ``synth.System``-like object (numpy arrays).  Returns the handle."""
+    keep = []
+
+    def arr(a, dt):
+        if a is None:
+            return None
+        a = np.ascontiguousarray(a, dtype=dt)
+        keep.append(a)
+        return a.ctypes.data
+
+    s = _System()
+    s.n_atoms = int(sysm.R.shape[0])
+    s.R, s.Z = arr(sysm.R, np.float64), arr(sysm.Z, np.float64)
+    s.n_shells = int(len(sysm.shell_l))
+    s.shell_atom, s.shell_l = arr(sysm.shell_atom, np.int32), arr(sysm.shell_l, np.int32)
+    s.shell_radial, s.shell_zeta = arr(sysm.shell_radial, np.int32), arr(sysm.shell_zeta, np.float64)
+    s.lambda_ = arr(sysm.lam, np.float64)
+    s.n_up, s.n_dn = int(sysm.n_up), int(sysm.n_dn)
+    s.unpaired = arr(sysm.unpaired, np.float64)
+    s.b_ea, s.b_para, s.b_anti = float(sysm.b_ea), float(sysm.b_para), float(sysm.b_anti)
+    s.use_j1, s.use_j2 = int(sysm.use_j1), int(sysm.use_j2)
+    s.j2_spin_independent = int(sysm.j2_spin_independent)
+    o = _Options()
+    o.precision, o.max_walkers = int(precision), int(max_walkers)
+    o.delta = float(sysm.delta if delta is None else delta)
+    o.seed, o.drift_tol = int(seed), float(drift_tol)
+    h = C.c_void_p()
+    _check(lib().jagp_create(C.byref(h), C.byref(s), C.byref(o)), "jagp_create")
+    return h.value
+
+
+def jagp_destroy(h: int):
+    _check(lib().jagp_destroy(h), "jagp_destroy")
+
+
+def jagp_state_bytes(h: int, W: int) -> int:
+    return int(lib().jagp_state_bytes(h, int(W)))
+
+
+def jagp_eval(h, r, W, state, logabs=None, sign=None, stream=None):
+    _check(lib().jagp_eval(h, _ptr(r), int(W), _ptr(state), _ptr(logabs), _ptr(sign), _stream(stream)),
+           "jagp_eval")
+
+
+def vmc_sweep(h, r, state, W, nsweeps, walker0=0, sweep0=0, eL=None, acc=None, stream=None):
+    _check(lib().vmc_sweep(h, _ptr(r), _ptr(state), int(W), int(nsweeps), int(walker0), int(sweep0),
+                           _ptr(eL), _ptr(acc), _stream(stream)), "vmc_sweep")
+
+
+def local_energy(h, r, state, W, eL, parts=None, stream=None):
+    _check(lib().local_energy(h, _ptr(r), _ptr(state), int(W), _ptr(eL), _ptr(parts), _stream(stream)),
+           "local_energy")
+
+
+def jagp_walker_info(h, state, W, logabs=None, sign=None, naccept=None, drift=None, status=None, stream=None):
+    _check(lib().jagp_walker_info(h, _ptr(state), int(W), _ptr(logabs), _ptr(sign), _ptr(naccept), _ptr(drift),
+                                  _ptr(status), _stream(stream)), "jagp_walker_info")
+
+
+def jagp_walker_status(h, state, W, stream=None) -> int:
+    bits = C.c_int(0)
+    _check(lib().jagp_walker_status(h, _ptr(state), int(W), C.byref(bits), _stream(stream)),
+           "jagp_walker_status")
+    return bits.value
+
+
+KERNEL_LAMBDA_ROWS, KERNEL_GEMM_ROWS, KERNEL_METROPOLIS, KERNEL_BASIS, KERNEL_ENERGY = 1, 2, 3, 4, 5
+
+
+def jagp_profile(h, kernel: int, enable: bool = True):
+    _check(lib().jagp_profile(h, int(kernel), int(bool(enable))), "jagp_profile")
+
+
+def jagp_profile_read(h):
+    """(summed device milliseconds, launches) of the profiled kernel; synchronises its events."""
+    ms, n = C.c_double(0.0), C.c_longlong(0)
+    _check(lib().jagp_profile_read(h, C.byref(ms), C.byref(n)), "jagp_profile_read")
+    return ms.value, n.value
+
+
+def jagp_launch_count(h) -> int:
+    return int(lib().jagp_launch_count(h))
+
+
+# --------------------------------------------------------------------------
+# convenience owner of a handle plus the walker state (device memory from torch)
+# --------------------------------------------------------------------------
+
+class JAGP:
+    """One system on the current CUDA device with state for up to W walkers."""
+
+    def __init__(self, sysm, W: int, precision: int = JAGP_PREC_FP64, seed: int = 0,
+                 delta: Optional[float] = None, drift_tol: float = 1e-8, device: str = "cuda"):
+        import torch
+        if not torch.cuda.is_available():
+            raise JagpError("libjagp needs a CUDA device; there is no CPU fallback")
+        self.sys, self.W, self.device = sysm, int(W), torch.device(device)
+        with torch.cuda.device(self.device):
+            self.h = jagp_create(sysm, precision, W, delta, seed, drift_tol)
+            nbytes = jagp_state_bytes(self.h, W)
+            # 256-byte aligned: the caching allocator hands out 512-byte aligned blocks
+            self.state = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        assert self.state.data_ptr() % 256 == 0
+        self.N = sysm.n_up + sysm.n_dn
+
+    def close(self):
+        if getattr(self, "h", None):
+            jagp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def positions(self, x):
+        import torch
+        return torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float64, device=self.device).contiguous()
+
+    def eval(self, r):
+        import torch
+        W = r.shape[0]
+        la = torch.empty(W, dtype=torch.float64, device=self.device)
+        sg = torch.empty(W, dtype=torch.float64, device=self.device)
+        jagp_eval(self.h, r, W, self.state, la, sg)
+        return la, sg
+
+    def sweep(self, r, nsweeps, walker0=0, sweep0=0, energies=True, acc=False):
+        import torch
+        W = r.shape[0]
+        eL = torch.empty((nsweeps, W), dtype=torch.float64, device=self.device) if energies else None
+        ac = torch.empty((nsweeps, 4), dtype=torch.float64, device=self.device) if acc else None
+        vmc_sweep(self.h, r, self.state, W, nsweeps, walker0, sweep0, eL, ac)
+        return eL, ac
+
+    def local_energy(self, r, parts=False):
+        import torch
+        W = r.shape[0]
+        e = torch.empty(W, dtype=torch.float64, device=self.device)
+        p = torch.empty((W, 4), dtype=torch.float64, device=self.device) if parts else None
+        local_energy(self.h, r, self.state, W, e, p)
+        return (e, p) if parts else e
+
+    def info(self, W=None):
+        import torch
+        W = self.W if W is None else W
+        f = lambda: torch.empty(W, dtype=torch.float64, device=self.device)  # noqa: E731
+        la, sg, na, dr = f(), f(), f(), f()
+        st = torch.empty(W, dtype=torch.int32, device=self.device)
+        jagp_walker_info(self.h, self.state, W, la, sg, na, dr, st)
+        return {"logabs": la, "sign": sg, "naccept": na, "drift": dr, "status": st}
+
+    def status(self, W=None) -> int:
+        return jagp_walker_status(self.h, self.state, self.W if W is None else W)

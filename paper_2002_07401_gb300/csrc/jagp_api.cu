@@ -1,0 +1,383 @@
+// jagp_api.cu -- the C ABI of libjagp (declared in include/jagp.h): argument
+// checking, device copies of the system, and the launch sequence of each
+// entry point.  All per-walker memory is the caller's state buffer.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <mutex>
+#include <vector>
+
+#include "jagp_launch.h"
+
+using namespace jagp;
+
+struct jagp_ctx {
+  int device = 0;
+  DevSystem ds{};
+  int precision = JAGP_PREC_FP64;
+  int max_walkers = 0;
+  double drift_tol = 1e-8;
+  void *d_mem = nullptr;
+  long long launches = 0;
+  int prof_kernel = 0;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events;
+};
+
+namespace {
+
+std::once_flag g_attr_once;
+cudaError_t g_attr_err = cudaSuccess;
+
+#define JAGP_CU(call)                          \
+  do {                                         \
+    cudaError_t e_ = (call);                   \
+    if (e_ != cudaSuccess) return JAGP_ERR_CUDA; \
+  } while (0)
+
+// Launch bookkeeping: count the kernels a launcher issues and, when profiling
+// is on for that kernel class, bracket it with an event pair on its stream.
+struct LaunchScope {
+  jagp_ctx *h;
+  cudaStream_t st;
+  bool timed;
+  cudaEvent_t a = nullptr, b = nullptr;
+  LaunchScope(jagp_ctx *h_, int kernel, cudaStream_t st_, int nkernels = 1)
+      : h(h_), st(st_), timed(kernel != 0 && h_->prof_kernel == kernel) {
+    h->launches += nkernels;
+    if (timed && cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess)
+      cudaEventRecord(a, st);
+    else
+      timed = false;
+  }
+  ~LaunchScope() {
+    if (timed) {
+      cudaEventRecord(b, st);
+      h->prof_events.emplace_back(a, b);
+    }
+  }
+};
+
+#define LAUNCH(kernel_id, nk, call)             \
+  do {                                          \
+    LaunchScope ls_(h, (kernel_id), st, (nk));  \
+    JAGP_CU(call);                              \
+  } while (0)
+
+Layout layout_of(const jagp_ctx *h, int W) {
+  return make_layout((size_t)W, (size_t)h->ds.n_up, (size_t)h->ds.N, (size_t)h->ds.L);
+}
+
+template <typename T>
+T *at(void *base, size_t off) {
+  return reinterpret_cast<T *>(static_cast<char *>(base) + off);
+}
+
+jagp_status_t check_walkers(const jagp_ctx *h, int W, const void *state) {
+  if (!h) return JAGP_ERR_INVALID_ARG;
+  if (W <= 0 || W > h->max_walkers) return JAGP_ERR_INVALID_ARG;
+  if (!state || (reinterpret_cast<uintptr_t>(state) & 255u)) return JAGP_ERR_INVALID_ARG;
+  return JAGP_OK;
+}
+
+// the FP64 local-energy sequence on a current state
+jagp_status_t run_local_energy(jagp_ctx *h, const double *r, void *state, int W, double *eL, double *parts,
+                               cudaStream_t st) {
+  const Layout L = layout_of(h, W);
+  LAUNCH(JAGP_KERNEL_ENERGY, 1, launch_mmat(h->ds, at<double>(state, L.ginv), at<double>(state, L.bt), at<double>(state, L.a_up),
+                      at<double>(state, L.mbuf), W, st));
+  LAUNCH(JAGP_KERNEL_ENERGY, 1, launch_kinetic(h->ds, r, at<double>(state, L.mbuf), at<double>(state, L.kin), W, st));
+  LAUNCH(JAGP_KERNEL_ENERGY, 1, launch_elocal(h->ds, r, at<double>(state, L.kin), eL, parts, W, st));
+  return JAGP_OK;
+}
+
+// G~ = Phi_up Bt^T, its inverse, log|det| and J from the current tables
+jagp_status_t run_refresh(jagp_ctx *h, const double *r, void *state, int W, int check_drift, cudaStream_t st) {
+  const Layout L = layout_of(h, W);
+  const int n = h->ds.n_up, Lb = h->ds.L;
+  LAUNCH(JAGP_KERNEL_GEMM_ROWS, 1, launch_gemm_rows(at<double>(state, L.phi_up), (size_t)n * Lb, at<double>(state, L.bt), (size_t)n * Lb, n,
+                           n, Lb, at<double>(state, L.gprop), (size_t)n * n, n, W, st));
+  LAUNCH(0, 1, launch_refresh_inverse(at<double>(state, L.gprop), at<double>(state, L.ginv), at<double>(state, L.scal),
+                                 at<int>(state, L.status), n, W, check_drift, h->drift_tol, st));
+  LAUNCH(0, 1, launch_jastrow_full(h->ds, r, at<double>(state, L.scal), W, st));
+  return JAGP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *jagp_status_string(jagp_status_t s) {
+  switch (s) {
+    case JAGP_OK: return "ok";
+    case JAGP_ERR_INVALID_ARG: return "invalid argument";
+    case JAGP_ERR_SINGULAR: return "singular geminal matrix";
+    case JAGP_ERR_NONFINITE: return "non-finite position or ratio";
+    case JAGP_ERR_OOM: return "device allocation failed";
+    case JAGP_ERR_TIMEOUT: return "bounded device wait expired";
+    case JAGP_ERR_UNSUPPORTED: return "unsupported system or size";
+    case JAGP_ERR_CUDA: return "CUDA runtime error";
+    default: return "unknown status";
+  }
+}
+
+jagp_status_t jagp_create(jagp_handle_t *out, const jagp_system_t *sys, const jagp_options_t *opt) {
+  if (!out || !sys || !opt) return JAGP_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (sys->n_atoms <= 0 || !sys->R || !sys->Z) return JAGP_ERR_INVALID_ARG;
+  if (sys->n_shells <= 0 || !sys->shell_atom || !sys->shell_l || !sys->shell_radial || !sys->shell_zeta)
+    return JAGP_ERR_INVALID_ARG;
+  if (!sys->lambda || sys->n_up < 1 || sys->n_dn < 0) return JAGP_ERR_INVALID_ARG;
+  if (sys->n_dn > sys->n_up) return JAGP_ERR_UNSUPPORTED;
+  if (sys->n_up > kMaxUp) return JAGP_ERR_UNSUPPORTED;
+  if (sys->n_up > sys->n_dn && !sys->unpaired) return JAGP_ERR_INVALID_ARG;
+  if (opt->precision != JAGP_PREC_FP64) return JAGP_ERR_UNSUPPORTED;
+  if (opt->max_walkers <= 0 || !(opt->delta > 0.0) || !isfinite(opt->delta)) return JAGP_ERR_INVALID_ARG;
+  int L = 0;
+  std::vector<double4> geo(sys->n_shells);
+  std::vector<int> info(sys->n_shells);
+  for (int k = 0; k < sys->n_shells; ++k) {
+    const int l = sys->shell_l[k], a = sys->shell_atom[k], rad = sys->shell_radial[k];
+    if (l < 0 || l > 2 || rad < 0 || rad > 1) return JAGP_ERR_UNSUPPORTED;
+    if (a < 0 || a >= sys->n_atoms || !(sys->shell_zeta[k] >= 0.0)) return JAGP_ERR_INVALID_ARG;
+    geo[k] = make_double4(sys->R[3 * a], sys->R[3 * a + 1], sys->R[3 * a + 2], sys->shell_zeta[k]);
+    info[k] = l | (rad << 2) | (L << 8);
+    L += 2 * l + 1;
+  }
+  const int na = sys->n_atoms, k_unp = sys->n_up - sys->n_dn;
+  std::vector<double> c1(na), lamT((size_t)L * L);
+  double vii = 0.0;
+  for (int a = 0; a < na; ++a) {
+    c1[a] = pow(2.0 * sys->Z[a], 0.25);
+    for (int b = a + 1; b < na; ++b) {
+      const double dx = sys->R[3 * a] - sys->R[3 * b], dy = sys->R[3 * a + 1] - sys->R[3 * b + 1],
+                   dz = sys->R[3 * a + 2] - sys->R[3 * b + 2];
+      vii += sys->Z[a] * sys->Z[b] / sqrt(dx * dx + dy * dy + dz * dz);
+    }
+  }
+  for (int i = 0; i < L; ++i)
+    for (int j = 0; j < L; ++j) lamT[(size_t)j * L + i] = sys->lambda[(size_t)i * L + j];
+
+  jagp_ctx *h = new jagp_ctx();
+  if (cudaGetDevice(&h->device) != cudaSuccess) {
+    delete h;
+    return JAGP_ERR_CUDA;
+  }
+  std::call_once(g_attr_once, [] {
+    g_attr_err = setup_kernel_attributes();
+    if (g_attr_err == cudaSuccess) g_attr_err = setup_walker_attributes();
+    if (g_attr_err == cudaSuccess) g_attr_err = setup_energy_attributes();
+  });
+  if (g_attr_err != cudaSuccess) {
+    delete h;
+    return JAGP_ERR_CUDA;
+  }
+  // one allocation: R, Z, c1, shell geo, shell info, lambda, lambda^T, unpaired
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t r = off; off = align256(off + bytes); return r; };
+  const size_t oR = take(na * 3 * 8), oZ = take(na * 8), oC = take(na * 8);
+  const size_t oG = take(sys->n_shells * sizeof(double4)), oI = take(sys->n_shells * sizeof(int));
+  const size_t oL = take((size_t)L * L * 8), oT = take((size_t)L * L * 8);
+  const size_t oU = take((size_t)(k_unp > 0 ? k_unp : 1) * L * 8);
+  if (cudaMalloc(&h->d_mem, off) != cudaSuccess) {
+    delete h;
+    return JAGP_ERR_OOM;
+  }
+  char *b = static_cast<char *>(h->d_mem);
+  bool ok = cudaMemcpy(b + oR, sys->R, na * 3 * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy(b + oZ, sys->Z, na * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy(b + oC, c1.data(), na * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy(b + oG, geo.data(), sys->n_shells * sizeof(double4), cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy(b + oI, info.data(), sys->n_shells * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy(b + oL, sys->lambda, (size_t)L * L * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy(b + oT, lamT.data(), (size_t)L * L * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
+            (k_unp == 0 ||
+             cudaMemcpy(b + oU, sys->unpaired, (size_t)k_unp * L * 8, cudaMemcpyHostToDevice) == cudaSuccess);
+  if (!ok) {
+    cudaFree(h->d_mem);
+    delete h;
+    return JAGP_ERR_CUDA;
+  }
+  DevSystem &d = h->ds;
+  d.n_atoms = na;
+  d.n_shells = sys->n_shells;
+  d.L = L;
+  d.n_up = sys->n_up;
+  d.n_dn = sys->n_dn;
+  d.N = sys->n_up + sys->n_dn;
+  d.R = reinterpret_cast<const double *>(b + oR);
+  d.Z = reinterpret_cast<const double *>(b + oZ);
+  d.c1 = reinterpret_cast<const double *>(b + oC);
+  d.shell_geo = reinterpret_cast<const double4 *>(b + oG);
+  d.shell_info = reinterpret_cast<const int *>(b + oI);
+  d.lam = reinterpret_cast<const double *>(b + oL);
+  d.lamT = reinterpret_cast<const double *>(b + oT);
+  d.unpaired = reinterpret_cast<const double *>(b + oU);
+  d.b_ea = sys->b_ea;
+  d.b_para = sys->b_para;
+  d.b_anti = sys->b_anti;
+  d.use_j1 = sys->use_j1 ? 1 : 0;
+  d.use_j2 = sys->use_j2 ? 1 : 0;
+  d.j2_si = sys->j2_spin_independent ? 1 : 0;
+  d.v_ii = vii;
+  d.delta = opt->delta;
+  d.key0 = (uint32_t)(opt->seed & 0xffffffffu);
+  d.key1 = (uint32_t)(opt->seed >> 32);
+  h->precision = opt->precision;
+  h->max_walkers = opt->max_walkers;
+  h->drift_tol = opt->drift_tol > 0.0 ? opt->drift_tol : 1e-8;
+  *out = h;
+  return JAGP_OK;
+}
+
+jagp_status_t jagp_destroy(jagp_handle_t h) {
+  if (!h) return JAGP_ERR_INVALID_ARG;
+  for (auto &p : h->prof_events) {
+    cudaEventDestroy(p.first);
+    cudaEventDestroy(p.second);
+  }
+  cudaError_t e = cudaFree(h->d_mem);
+  delete h;
+  return e == cudaSuccess ? JAGP_OK : JAGP_ERR_CUDA;
+}
+
+size_t jagp_state_bytes(jagp_handle_t h, int W) {
+  if (!h || W <= 0 || W > h->max_walkers) return 0;
+  return layout_of(h, W).total;
+}
+
+jagp_status_t jagp_eval(jagp_handle_t h, const double *d_r, int W, void *d_state, double *d_logabs,
+                        double *d_sign, void *stream) {
+  jagp_status_t s = check_walkers(h, W, d_state);
+  if (s != JAGP_OK) return s;
+  if (!d_r) return JAGP_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const Layout L = layout_of(h, W);
+  const DevSystem &d = h->ds;
+  const int n = d.n_up, Lb = d.L;
+  double *phi_up = at<double>(d_state, L.phi_up), *pprop = at<double>(d_state, L.pprop);
+  LAUNCH(0, 1, launch_walker_init(at<double>(d_state, L.scal), at<int>(d_state, L.status), W, st));
+  LAUNCH(JAGP_KERNEL_BASIS, 1, launch_basis_points(d, false, d_r, W, 0, n, phi_up, nullptr, 0, 0, st));
+  LAUNCH(JAGP_KERNEL_BASIS, d.n_dn > 0, launch_basis_points(d, false, d_r, W, n, d.n_dn, pprop, nullptr, 0, 0, st));
+  // A_up = Phi_up lambda (every row); Bt rows j < n_dn = lambda phi(r_j^dn)
+  LAUNCH(JAGP_KERNEL_LAMBDA_ROWS, 1, launch_lambda_rows(phi_up, d.lam, at<double>(d_state, L.a_up), nullptr, nullptr, W * n, n, n, Lb, W * n,
+                             st));
+  if (d.n_dn > 0)
+    LAUNCH(JAGP_KERNEL_LAMBDA_ROWS, 1, launch_lambda_rows(pprop, d.lamT, at<double>(d_state, L.bt), nullptr, nullptr, W * d.n_dn, d.n_dn, n,
+                               Lb, W * d.n_dn, st));
+  LAUNCH(0, d.n_up > d.n_dn, launch_fill_unpaired(d, at<double>(d_state, L.bt), W, st));
+  s = run_refresh(h, d_r, d_state, W, 0, st);
+  if (s != JAGP_OK) return s;
+  LAUNCH(0, (d_logabs || d_sign), launch_logpsi_out(at<double>(d_state, L.scal), W, d_logabs, d_sign, st));
+  return JAGP_OK;
+}
+
+jagp_status_t vmc_sweep(jagp_handle_t h, double *d_r, void *d_state, int W, int nsweeps, uint64_t walker0,
+                        uint64_t sweep0, double *d_eL, double *d_acc, void *stream) {
+  jagp_status_t s = check_walkers(h, W, d_state);
+  if (s != JAGP_OK) return s;
+  if (!d_r || nsweeps < 0) return JAGP_ERR_INVALID_ARG;
+  if (walker0 + (uint64_t)W > 0x100000000ull || sweep0 + (uint64_t)nsweeps > 0x100000000ull)
+    return JAGP_ERR_INVALID_ARG;  // Philox counter words are 32-bit
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const Layout L = layout_of(h, W);
+  const DevSystem &d = h->ds;
+  const int n = d.n_up, Lb = d.L;
+  double *phi_up = at<double>(d_state, L.phi_up), *a_up = at<double>(d_state, L.a_up);
+  double *bt = at<double>(d_state, L.bt), *ginv = at<double>(d_state, L.ginv);
+  double *pprop = at<double>(d_state, L.pprop), *gprop = at<double>(d_state, L.gprop);
+  double *rprop = at<double>(d_state, L.rprop), *scal = at<double>(d_state, L.scal);
+  int *status = at<int>(d_state, L.status), *list = at<int>(d_state, L.list), *count = at<int>(d_state, L.count);
+  for (int t = 0; t < nsweeps; ++t) {
+    const uint32_t sw = (uint32_t)(sweep0 + (uint64_t)t);
+    JAGP_CU(cudaMemsetAsync(count, 0, 2 * sizeof(int), st));
+    // up electrons: rows of G~ against the frozen down-spin table Bt
+    LAUNCH(JAGP_KERNEL_BASIS, 1, launch_basis_points(d, true, d_r, W, 0, n, pprop, rprop, (uint32_t)walker0, sw, st));
+    LAUNCH(JAGP_KERNEL_GEMM_ROWS, 1, launch_gemm_rows(pprop, (size_t)n * Lb, bt, (size_t)n * Lb, n, n, Lb, gprop, (size_t)n * n, n, W, st));
+    LAUNCH(JAGP_KERNEL_METROPOLIS, 1, launch_metropolis(d, true, d_r, rprop, gprop, ginv, scal, status, pprop, phi_up, list, count, W, st));
+    LAUNCH(JAGP_KERNEL_LAMBDA_ROWS, 1, launch_lambda_rows(pprop, d.lam, a_up, list, count, 0, 1, 0, Lb, W * n, st));
+    if (d.n_dn > 0) {
+      // down electrons: columns of G~ against the updated up-spin table A_up
+      LAUNCH(JAGP_KERNEL_BASIS, 1, launch_basis_points(d, true, d_r, W, n, d.n_dn, pprop, rprop, (uint32_t)walker0, sw, st));
+      LAUNCH(JAGP_KERNEL_GEMM_ROWS, 1, launch_gemm_rows(pprop, (size_t)n * Lb, a_up, (size_t)n * Lb, d.n_dn, n, Lb, gprop, (size_t)n * n, n,
+                               W, st));
+      LAUNCH(JAGP_KERNEL_METROPOLIS, 1, launch_metropolis(d, false, d_r, rprop, gprop, ginv, scal, status, pprop, phi_up, list, count + 1, W,
+                                st));
+      LAUNCH(JAGP_KERNEL_LAMBDA_ROWS, 1, launch_lambda_rows(pprop, d.lamT, bt, list, count + 1, 0, 1, 0, Lb, W * d.n_dn, st));
+    }
+    s = run_refresh(h, d_r, d_state, W, 1, st);
+    if (s != JAGP_OK) return s;
+    double *eL = d_eL ? d_eL + (size_t)t * W : nullptr;
+    if (eL) {
+      s = run_local_energy(h, d_r, d_state, W, eL, nullptr, st);
+      if (s != JAGP_OK) return s;
+    }
+    if (d_acc) LAUNCH(0, 1, launch_reduce_acc(eL, scal, count, W, d_acc + (size_t)t * 4, st));
+  }
+  return JAGP_OK;
+}
+
+jagp_status_t local_energy(jagp_handle_t h, const double *d_r, void *d_state, int W, double *d_eL,
+                           double *d_parts, void *stream) {
+  jagp_status_t s = check_walkers(h, W, d_state);
+  if (s != JAGP_OK) return s;
+  if (!d_r || !d_eL) return JAGP_ERR_INVALID_ARG;
+  return run_local_energy(h, d_r, d_state, W, d_eL, d_parts, static_cast<cudaStream_t>(stream));
+}
+
+jagp_status_t jagp_profile(jagp_handle_t h, int kernel, int enable) {
+  if (!h || kernel < 1 || kernel > JAGP_KERNEL_ENERGY) return JAGP_ERR_INVALID_ARG;
+  h->prof_kernel = enable ? kernel : 0;
+  return JAGP_OK;
+}
+
+jagp_status_t jagp_profile_read(jagp_handle_t h, double *h_total_ms, long long *h_launches) {
+  if (!h || !h_total_ms || !h_launches) return JAGP_ERR_INVALID_ARG;
+  double tot = 0.0;
+  jagp_status_t rc = JAGP_OK;
+  for (auto &p : h->prof_events) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(p.second) != cudaSuccess || cudaEventElapsedTime(&ms, p.first, p.second) != cudaSuccess)
+      rc = JAGP_ERR_CUDA;
+    tot += ms;
+    cudaEventDestroy(p.first);
+    cudaEventDestroy(p.second);
+  }
+  *h_launches = (long long)h->prof_events.size();
+  *h_total_ms = tot;
+  h->prof_events.clear();
+  return rc;
+}
+
+long long jagp_launch_count(jagp_handle_t h) { return h ? h->launches : -1;
+}
+
+jagp_status_t jagp_walker_info(jagp_handle_t h, const void *d_state, int W, double *d_logabs, double *d_sign,
+                               double *d_naccept, double *d_drift, int *d_status, void *stream) {
+  jagp_status_t s = check_walkers(h, W, d_state);
+  if (s != JAGP_OK) return s;
+  const Layout L = layout_of(h, W);
+  void *sp = const_cast<void *>(d_state);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  LAUNCH(0, 1, launch_walker_info(at<double>(sp, L.scal), at<int>(sp, L.status), W, d_logabs, d_sign, d_naccept,
+                                  d_drift, d_status, st));
+  return JAGP_OK;
+}
+
+jagp_status_t jagp_walker_status(jagp_handle_t h, const void *d_state, int W, int *h_bits, void *stream) {
+  jagp_status_t s = check_walkers(h, W, d_state);
+  if (s != JAGP_OK) return s;
+  if (!h_bits) return JAGP_ERR_INVALID_ARG;
+  const Layout L = layout_of(h, W);
+  std::vector<int> bits(W);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  JAGP_CU(cudaMemcpyAsync(bits.data(), static_cast<const char *>(d_state) + L.status, (size_t)W * sizeof(int),
+                          cudaMemcpyDeviceToHost, st));
+  JAGP_CU(cudaStreamSynchronize(st));
+  int o = 0;
+  for (int w = 0; w < W; ++w) o |= bits[w];
+  *h_bits = o;
+  return JAGP_OK;
+}
+
+}  // extern "C"

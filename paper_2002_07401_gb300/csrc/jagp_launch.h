@@ -1,0 +1,68 @@
+// jagp_launch.h -- host-side launchers of the libjagp kernels (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "jagp_common.cuh"
+
+namespace jagp {
+
+// Orbital values at electron positions (PROPOSE = false) or at freshly drawn
+// proposals (PROPOSE = true, also writes rprop).  Rows go to
+// out[(w * n_up + i) * L], i < npts, for electrons e0 .. e0 + npts - 1.
+cudaError_t launch_basis_points(const DevSystem &s, bool propose, const double *r, int W, int e0,
+                                int npts, double *out, double *rprop, uint32_t walker0,
+                                uint32_t sweep, cudaStream_t st);
+
+// Sequential Metropolis over one spin species with Sherman-Morrison updates.
+cudaError_t launch_metropolis(const DevSystem &s, bool up, double *r, const double *rprop,
+                              const double *gprop, double *ginv, double *scal, int *status,
+                              const double *pprop, double *phi_up, int *list, int *count, int W,
+                              cudaStream_t st);
+
+// Out[w][a][b] = sum_k X[w][a][k] Y[w][b][k]  (a < ma, b < nb, k < K); row stride K.
+cudaError_t launch_gemm_rows(const double *X, size_t xw, const double *Y, size_t yw, int ma, int nb,
+                             int K, double *Out, size_t ow, int ldo, int W, cudaStream_t st);
+
+// Out[row] = P[row] * Lam (L x L).  Rows are list[0 .. *count) when list is
+// given, else rows r < nrows mapped to (r / nsub) * stride + r % nsub.
+cudaError_t launch_lambda_rows(const double *P, const double *Lam, double *Out, const int *list,
+                               const int *count, int nrows, int nsub, int stride, int L,
+                               int max_rows, cudaStream_t st);
+
+// Fill rows n_dn .. n_up - 1 of every walker's Bt block with the unpaired orbitals.
+cudaError_t launch_fill_unpaired(const DevSystem &s, double *bt, int W, cudaStream_t st);
+
+// Gauss-Jordan inverse with partial pivoting of G~ (in gm), log|det|, sign and
+// the Sherman-Morrison drift against the inverse held in ginv.
+cudaError_t launch_refresh_inverse(const double *gm, double *ginv, double *scal, int *status, int n,
+                                   int W, int check_drift, double drift_tol, cudaStream_t st);
+
+cudaError_t launch_jastrow_full(const DevSystem &s, const double *r, double *scal, int W,
+                                cudaStream_t st);
+
+// M vectors of the kinetic energy (see k_linalg.cu), then the orbital
+// derivative contractions and the final per-walker local energy.
+cudaError_t launch_mmat(const DevSystem &s, const double *ginv, const double *bt, const double *a_up,
+                        double *mbuf, int W, cudaStream_t st);
+cudaError_t launch_kinetic(const DevSystem &s, const double *r, const double *mbuf, double *kin, int W,
+                           cudaStream_t st);
+cudaError_t launch_elocal(const DevSystem &s, const double *r, const double *kin, double *eL,
+                          double *parts, int W, cudaStream_t st);
+
+cudaError_t launch_walker_init(double *scal, int *status, int W, cudaStream_t st);
+cudaError_t launch_logpsi_out(const double *scal, int W, double *logabs, double *sign,
+                              cudaStream_t st);
+cudaError_t launch_walker_info(const double *scal, const int *status, int W, double *logabs,
+                               double *sign, double *nacc, double *drift, int *st_out,
+                               cudaStream_t st);
+cudaError_t launch_reduce_acc(const double *eL, const double *scal, const int *count, int W,
+                              double *acc, cudaStream_t st);
+
+// one-time kernel attribute set-up (dynamic shared memory limits), per file
+cudaError_t setup_kernel_attributes();
+cudaError_t setup_walker_attributes();
+cudaError_t setup_energy_attributes();
+
+}  // namespace jagp

@@ -1,0 +1,351 @@
+// k_linalg.cu -- the dense contractions and the FP64 inverse refresh of the
+// geminal matrix (Sec. AGP, Eq. agp_expansion: G~ = Phi_up lambda Phi_dn^T | Phi_up C).
+#include <math.h>
+
+#include "jagp_launch.h"
+
+namespace jagp {
+
+// ---------------------------------------------------------------------------
+// Per-walker small GEMM against row-major operands sharing the contraction
+// index:  Out[w][a][b] = sum_k X[w][a][k] Y[w][b][k].
+// Used for the proposed rows (Phi'_up . Bt), the proposed columns
+// (Phi'_dn . A_up) and G~ at a refresh (Phi_up . Bt).  16 x 16 output tile per
+// CTA, one output per thread, operands staged through shared memory in
+// k-chunks of 64 (row pitch 65 doubles: conflict-free column reads).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_gemm_rows(const double *__restrict__ X, size_t xw,
+                                                   const double *__restrict__ Y, size_t yw, int ma, int nb,
+                                                   int K, double *__restrict__ Out, size_t ow, int ldo) {
+  __shared__ double Xs[16][65];
+  __shared__ double Ys[16][65];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int w = blockIdx.z, a0 = blockIdx.y * 16, b0 = blockIdx.x * 16;
+  const double *Xw = X + (size_t)w * xw;
+  const double *Yw = Y + (size_t)w * yw;
+  double acc = 0.0;
+  for (int k0 = 0; k0 < K; k0 += 64) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int idx = threadIdx.x + q * 256, row = idx >> 6, col = idx & 63;
+      const int k = k0 + col;
+      const int a = a0 + row, b = b0 + row;
+      Xs[row][col] = (a < ma && k < K) ? Xw[(size_t)a * K + k] : 0.0;
+      Ys[row][col] = (b < nb && k < K) ? Yw[(size_t)b * K + k] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 16
+    for (int k = 0; k < 64; ++k) acc = fma(Xs[ty][k], Ys[tx][k], acc);
+    __syncthreads();
+  }
+  if (a0 + ty < ma && b0 + tx < nb) Out[(size_t)w * ow + (size_t)(a0 + ty) * ldo + b0 + tx] = acc;
+}
+
+cudaError_t launch_gemm_rows(const double *X, size_t xw, const double *Y, size_t yw, int ma, int nb, int K,
+                             double *Out, size_t ow, int ldo, int W, cudaStream_t st) {
+  if (W <= 0 || ma <= 0 || nb <= 0) return cudaSuccess;
+  dim3 grid((nb + 15) / 16, (ma + 15) / 16, W);
+  k_gemm_rows<<<grid, 256, 0, st>>>(X, xw, Y, yw, ma, nb, K, Out, ow, ldo);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// lambda products of whole orbital rows, batched over walkers:
+//   Out[row][c] = sum_k P[row][k] Lam[k][c]
+// with Lam = lambda (A_up rows phi^T lambda) or lambda^T (Bt rows lambda phi).
+// In the sweep only the accepted moves' rows are listed, so the cost is
+// (accepted moves) x L^2.  64 x 64 output tile, 256 threads each holding a
+// 4 x 4 register block (rows ty + 16 i, columns tx + 16 j), k-chunks of 16.
+// FP64 CUDA-core arithmetic.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_lambda_rows(const double *__restrict__ P, const double *__restrict__ Lam,
+                                                     double *__restrict__ Out, const int *__restrict__ list,
+                                                     const int *__restrict__ count, int nrows, int nsub,
+                                                     int stride, int L) {
+  const int rows = count ? *count : nrows;
+  const int m0 = blockIdx.y * 64;
+  if (m0 >= rows) return;
+  const int n0 = blockIdx.x * 64;
+  __shared__ double As[16][64];
+  __shared__ double Bs[16][64];
+  __shared__ long rowoff[64];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  if (tid < 64) {
+    const int m = m0 + tid;
+    long phys = -1;
+    if (m < rows) phys = list ? (long)list[m] : (long)(m / nsub) * stride + (m % nsub);
+    rowoff[tid] = phys < 0 ? -1 : phys * (long)L;
+  }
+  __syncthreads();
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+  const int lm = tid >> 2, lk = (tid & 3) * 4;   // P tile loader: row lm, k lk..lk+3
+  const int bk = tid >> 4, bc = (tid & 15) * 4;  // Lam tile loader: k bk, columns bc..bc+3
+  for (int k0 = 0; k0 < L; k0 += 16) {
+    const long ro = rowoff[lm];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int k = k0 + lk + q;
+      As[lk + q][lm] = (ro >= 0 && k < L) ? P[ro + k] : 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int k = k0 + bk, c = n0 + bc + q;
+      Bs[bk][bc + q] = (k < L && c < L) ? Lam[(size_t)k * L + c] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const long ro = rowoff[ty + 16 * i];
+    if (ro < 0) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c = n0 + tx + 16 * j;
+      if (c < L) Out[ro + c] = acc[i][j];
+    }
+  }
+}
+
+cudaError_t launch_lambda_rows(const double *P, const double *Lam, double *Out, const int *list, const int *count,
+                               int nrows, int nsub, int stride, int L, int max_rows, cudaStream_t st) {
+  if (max_rows <= 0) return cudaSuccess;
+  dim3 grid((L + 63) / 64, (max_rows + 63) / 64);
+  k_lambda_rows<<<grid, 256, 0, st>>>(P, Lam, Out, list, count, nrows, nsub > 0 ? nsub : 1, stride, L);
+  return cudaGetLastError();
+}
+
+__global__ void k_fill_unpaired(const double *__restrict__ unp, double *__restrict__ bt, int W, int nu, int nd,
+                                int L) {
+  const int k = nu - nd;
+  const long total = (long)W * k * L;
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+    const int c = (int)(idx % L);
+    const long t = idx / L;
+    const int l = (int)(t % k);
+    const int w = (int)(t / k);
+    bt[((size_t)w * nu + nd + l) * L + c] = unp[(size_t)l * L + c];
+  }
+}
+
+cudaError_t launch_fill_unpaired(const DevSystem &s, double *bt, int W, cudaStream_t st) {
+  if (W <= 0 || s.n_up == s.n_dn) return cudaSuccess;
+  const long total = (long)W * (s.n_up - s.n_dn) * s.L;
+  long blocks = (total + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  k_fill_unpaired<<<(int)blocks, 256, 0, st>>>(s.unpaired, bt, W, s.n_up, s.n_dn, s.L);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// FP64 refresh: Gauss-Jordan elimination with partial pivoting on [G~ | I]
+// (one CTA per walker, the n x 2n block in shared memory).  log|det G~| is the
+// sum of log|pivot|, the sign the product of pivot signs and row swaps.  The
+// fresh inverse replaces the Sherman-Morrison one; their largest difference
+// times max|G~| is the walker's drift.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_refresh_inverse(const double *__restrict__ gm, double *__restrict__ ginv,
+                                                         double *__restrict__ scal, int *__restrict__ status,
+                                                         int n, int check_drift, double drift_tol) {
+  extern __shared__ double sm[];
+  const int ld = 2 * n + 1, tid = threadIdx.x, bs = blockDim.x, w = blockIdx.x;
+  double *A = sm;              // n x ld
+  double *f = A + n * ld;      // n
+  __shared__ int s_piv;
+  __shared__ double s_pv;
+  __shared__ double red[32];
+  const double *G = gm + (size_t)w * n * n;
+  double gmax = 0.0;
+  for (int idx = tid; idx < n * 2 * n; idx += bs) {
+    const int i = idx / (2 * n), j = idx - i * 2 * n;
+    double v;
+    if (j < n) {
+      v = G[i * n + j];
+      gmax = fmax(gmax, fabs(v));
+    } else {
+      v = (j - n == i) ? 1.0 : 0.0;
+    }
+    A[i * ld + j] = v;
+  }
+  double logdet = 0.0, sgn = 1.0;
+  bool ok = true;
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    if (tid < 32) {
+      double best = -1.0;
+      int bi = k;  // stays a valid row even if every candidate is NaN (then pv is NaN: singular)
+      for (int i = k + tid; i < n; i += 32) {
+        const double v = fabs(A[i * ld + k]);
+        if (v > best) {
+          best = v;
+          bi = i;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) {
+          best = ob;
+          bi = oi;
+        }
+      }
+      if (tid == 0) {
+        s_piv = bi;
+        s_pv = A[bi * ld + k];
+      }
+    }
+    __syncthreads();
+    const int p = s_piv;
+    const double pv = s_pv;
+    if (!(pv != 0.0) || !isfinite(pv)) {
+      ok = false;
+      break;
+    }
+    if (p != k) {
+      for (int j = tid; j < 2 * n; j += bs) {
+        const double t = A[k * ld + j];
+        A[k * ld + j] = A[p * ld + j];
+        A[p * ld + j] = t;
+      }
+      sgn = -sgn;
+    }
+    logdet += log(fabs(pv));
+    if (pv < 0.0) sgn = -sgn;
+    __syncthreads();
+    const double ip = 1.0 / pv;
+    for (int j = tid; j < 2 * n; j += bs) A[k * ld + j] *= ip;
+    __syncthreads();
+    for (int i = tid; i < n; i += bs) f[i] = A[i * ld + k];
+    __syncthreads();
+    for (int idx = tid; idx < n * 2 * n; idx += bs) {
+      const int i = idx / (2 * n), j = idx - i * 2 * n;
+      if (i != k && j >= k) A[i * ld + j] -= f[i] * A[k * ld + j];
+    }
+    __syncthreads();
+  }
+  double *gi = ginv + (size_t)w * n * n;
+  if (!ok) {
+    if (tid == 0) {
+      status[w] |= JAGP_WS_SINGULAR;
+      scal[(size_t)w * S_STRIDE + S_LOGDET] = -INFINITY;
+      scal[(size_t)w * S_STRIDE + S_SIGN] = 0.0;
+    }
+    return;
+  }
+  double dmax = 0.0;
+  for (int idx = tid; idx < n * n; idx += bs) {
+    const int i = idx / n, j = idx - i * n;
+    const double v = A[i * ld + n + j];
+    if (check_drift) dmax = fmax(dmax, fabs(v - gi[idx]));
+    gi[idx] = v;
+  }
+  // block max of dmax and gmax
+  for (int o = 16; o > 0; o >>= 1) {
+    dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+    gmax = fmax(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
+  }
+  if ((tid & 31) == 0) {
+    red[tid >> 5] = dmax;
+    red[16 + (tid >> 5)] = gmax;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double d = 0.0, g = 0.0;
+    for (int q = 0; q < (bs >> 5); ++q) {
+      d = fmax(d, red[q]);
+      g = fmax(g, red[16 + q]);
+    }
+    scal[(size_t)w * S_STRIDE + S_LOGDET] = logdet;
+    scal[(size_t)w * S_STRIDE + S_SIGN] = sgn;
+    if (check_drift) {
+      const double drift = d * g;
+      scal[(size_t)w * S_STRIDE + S_DRIFT] = drift;
+      if (!(drift <= drift_tol)) status[w] |= JAGP_WS_DRIFT;
+    }
+  }
+}
+
+cudaError_t launch_refresh_inverse(const double *gm, double *ginv, double *scal, int *status, int n, int W,
+                                   int check_drift, double drift_tol, cudaStream_t st) {
+  if (W <= 0) return cudaSuccess;
+  const size_t smem = (size_t)(n * (2 * n + 1) + n) * sizeof(double);
+  k_refresh_inverse<<<W, 256, smem, st>>>(gm, ginv, scal, status, n, check_drift, drift_tol);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Kinetic-energy contraction vectors.  D = det G~ is linear in row i (up
+// electron i) and in column j (down electron j), so
+//   grad_i D / D = sum_mu grad phi_mu(r_i) M[i][mu],
+//   up:   M[i]       = sum_j Ginv[j][i] Bt[j]      (Bt[j] = lambda phi(r_j^dn) or c^{(l)})
+//   down: M[n_up + j] = sum_i Ginv[j][i] A_up[i]   (A_up[i] = phi(r_i^up)^T lambda)
+// and the same M with the Laplacians.  One CTA per (walker, 64 columns).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_mmat(DevSystem s, const double *__restrict__ ginv,
+                                              const double *__restrict__ bt, const double *__restrict__ a_up,
+                                              double *__restrict__ mbuf) {
+  extern __shared__ double sm[];
+  const int n = s.n_up, nd = s.n_dn, N = s.N, L = s.L;
+  const int w = blockIdx.y, c0 = blockIdx.x * 64, tid = threadIdx.x;
+  double *Gs = sm;              // n*n
+  double *Bs = Gs + n * n;      // n*64
+  double *As = Bs + n * 64;     // n*64
+  for (int t = tid; t < n * n; t += 256) Gs[t] = ginv[(size_t)w * n * n + t];
+  for (int t = tid; t < n * 64; t += 256) {
+    const int j = t >> 6, c = t & 63;
+    const bool in = c0 + c < L;
+    Bs[t] = in ? bt[((size_t)w * n + j) * L + c0 + c] : 0.0;
+    As[t] = in ? a_up[((size_t)w * n + j) * L + c0 + c] : 0.0;
+  }
+  __syncthreads();
+  for (int idx = tid; idx < N * 64; idx += 256) {
+    const int e = idx >> 6, c = idx & 63;
+    if (c0 + c >= L) continue;
+    double acc = 0.0;
+    if (e < n) {
+      for (int j = 0; j < n; ++j) acc = fma(Gs[j * n + e], Bs[j * 64 + c], acc);
+    } else {
+      const int jj = e - n;
+      for (int i = 0; i < n; ++i) acc = fma(Gs[jj * n + i], As[i * 64 + c], acc);
+    }
+    (void)nd;
+    mbuf[((size_t)w * N + e) * L + c0 + c] = acc;
+  }
+}
+
+cudaError_t launch_mmat(const DevSystem &s, const double *ginv, const double *bt, const double *a_up, double *mbuf,
+                        int W, cudaStream_t st) {
+  if (W <= 0) return cudaSuccess;
+  const int n = s.n_up;
+  const size_t smem = (size_t)(n * n + 2 * n * 64) * sizeof(double);
+  dim3 grid((s.L + 63) / 64, W);
+  k_mmat<<<grid, 256, smem, st>>>(s, ginv, bt, a_up, mbuf);
+  return cudaGetLastError();
+}
+
+cudaError_t setup_kernel_attributes() {
+  const int big = 200 * 1024;
+  cudaError_t e = cudaFuncSetAttribute(k_refresh_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_mmat, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  return e;
+}
+
+}  // namespace jagp

@@ -1,0 +1,383 @@
+// k_walkers.cu -- per-electron and per-walker kernels of the VMC sweep:
+// orbital evaluation at electrons / proposals, the sequential Metropolis
+// acceptance with Sherman-Morrison updates, the full Jastrow, bookkeeping.
+#include <math.h>
+
+#include "jagp_launch.h"
+
+namespace jagp {
+
+// ---------------------------------------------------------------------------
+// Orbitals at points: one warp per point, lanes stride over shells.  The shell
+// table (32-byte centre+exponent records and packed info words) is staged in
+// shared memory once per CTA; CTAs then grid-stride over points.
+// (Sec. "Atomic basis set", Eqs. gaussian, slater.)
+// ---------------------------------------------------------------------------
+template <bool PROPOSE>
+__global__ void __launch_bounds__(256) k_basis_points(DevSystem s, const double *__restrict__ r, int W,
+                                                      int e0, int npts, double *__restrict__ out,
+                                                      double *__restrict__ rprop, uint32_t walker0,
+                                                      uint32_t sweep) {
+  extern __shared__ double4 sh_geo[];
+  int *sh_info = reinterpret_cast<int *>(sh_geo + s.n_shells);
+  for (int k = threadIdx.x; k < s.n_shells; k += blockDim.x) {
+    sh_geo[k] = s.shell_geo[k];
+    sh_info[k] = s.shell_info[k];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const long nwarps = (long)gridDim.x * (blockDim.x >> 5);
+  const long total = (long)W * npts;
+  for (long pt = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); pt < total; pt += nwarps) {
+    const int w = (int)(pt / npts), i = (int)(pt % npts);
+    const double *rr = r + ((size_t)w * s.N + e0 + i) * 3;
+    double p[3] = {rr[0], rr[1], rr[2]};
+    if (PROPOSE) {
+      double rp[3], u;
+      move_draw(s, walker0 + (uint32_t)w, sweep, (uint32_t)(e0 + i), p, rp, &u);
+      p[0] = rp[0];
+      p[1] = rp[1];
+      p[2] = rp[2];
+      if (lane < 4) rprop[((size_t)w * s.n_up + i) * 4 + lane] = lane < 3 ? rp[lane] : u;
+    }
+    double *o = out + ((size_t)w * s.n_up + i) * s.L;
+    for (int k = lane; k < s.n_shells; k += 32) {
+      const double4 g = sh_geo[k];
+      const int info = sh_info[k];
+      double v[5];
+      const int nc = shell_values<double>(info, g.w, p[0] - g.x, p[1] - g.y, p[2] - g.z, v);
+      const int off = shell_off(info);
+#pragma unroll
+      for (int c = 0; c < 5; ++c)
+        if (c < nc) o[off + c] = v[c];
+    }
+  }
+}
+
+cudaError_t launch_basis_points(const DevSystem &s, bool propose, const double *r, int W, int e0, int npts,
+                                double *out, double *rprop, uint32_t walker0, uint32_t sweep,
+                                cudaStream_t st) {
+  if (W <= 0 || npts <= 0) return cudaSuccess;
+  const long total = (long)W * npts;
+  const int warps = 8;
+  long blocks = (total + warps - 1) / warps;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  const size_t smem = (size_t)s.n_shells * (sizeof(double4) + sizeof(int));
+  if (propose)
+    k_basis_points<true><<<(int)blocks, warps * 32, smem, st>>>(s, r, W, e0, npts, out, rprop, walker0, sweep);
+  else
+    k_basis_points<false><<<(int)blocks, warps * 32, smem, st>>>(s, r, W, e0, npts, out, rprop, walker0, sweep);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Block reduction of two doubles (blockDim.x <= 1024); result valid in thread 0.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void block_sum2(double &a, double &b, double *red) {
+  a = warp_sum(a);
+  b = warp_sum(b);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0) {
+    red[2 * warp] = a;
+    red[2 * warp + 1] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int q = 1; q < nw; ++q) {
+      a += red[2 * q];
+      b += red[2 * q + 1];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Sequential single-electron Metropolis for one spin species (Sec. VMC).
+// One CTA per walker; G~^{-1} lives in shared memory for the whole
+// half-sweep.  Move m of an up electron replaces row m of G~ by the proposed
+// row g' (already computed from the frozen down-spin table):
+//   ratio R = g' . G~^{-1}[:, m],
+//   G~^{-1} <- G~^{-1} - G~^{-1}[:, m] (g'^T G~^{-1} - e_m^T) / R   (Sherman-Morrison);
+// a down electron replaces column m, with the transposed formulas.  The
+// Jastrow factor contributes exp(2 dJ), dJ summed over the atoms (J1) and the
+// other electrons at their current positions (J2).  Accept iff u < R^2 e^{2 dJ}.
+// ---------------------------------------------------------------------------
+template <bool UP>
+__global__ void __launch_bounds__(128) k_metropolis(DevSystem s, double *__restrict__ r,
+                                                    const double *__restrict__ rprop,
+                                                    const double *__restrict__ gprop,
+                                                    double *__restrict__ ginv, double *__restrict__ scal,
+                                                    int *__restrict__ status,
+                                                    const double *__restrict__ pprop,
+                                                    double *__restrict__ phi_up, int *__restrict__ list,
+                                                    int *__restrict__ count) {
+  extern __shared__ double sm[];
+  const int n = s.n_up, N = s.N, tid = threadIdx.x, bs = blockDim.x;
+  const int w = blockIdx.x;
+  double *Gi = sm;            // n * n
+  double *xs = Gi + n * n;    // N * 3
+  double *gp = xs + N * 3;    // n
+  double *vv = gp + n;        // n
+  double *cc = vv + n;        // n
+  __shared__ double red[64];
+  __shared__ int s_acc;
+  __shared__ double s_R;
+  double *gw = ginv + (size_t)w * n * n;
+  for (int t = tid; t < n * n; t += bs) Gi[t] = gw[t];
+  for (int t = tid; t < N * 3; t += bs) xs[t] = r[(size_t)w * N * 3 + t];
+  double logdet = 0.0, sgn = 1.0, J = 0.0, nacc = 0.0;
+  int st_bits = 0;
+  if (tid == 0) {
+    logdet = scal[(size_t)w * S_STRIDE + S_LOGDET];
+    sgn = scal[(size_t)w * S_STRIDE + S_SIGN];
+    J = scal[(size_t)w * S_STRIDE + S_J];
+    nacc = scal[(size_t)w * S_STRIDE + S_NACC];
+    st_bits = status[w];
+  }
+  const int nmoves = UP ? s.n_up : s.n_dn;
+  const int e0 = UP ? 0 : s.n_up;
+  __syncthreads();
+  for (int m = 0; m < nmoves; ++m) {
+    const int e = e0 + m;
+    const double *rp4 = rprop + ((size_t)w * n + m) * 4;
+    const double px = rp4[0], py = rp4[1], pz = rp4[2];
+    for (int t = tid; t < n; t += bs) gp[t] = gprop[((size_t)w * n + m) * n + t];
+    __syncthreads();
+    double pr = 0.0, pj = 0.0;
+    for (int t = tid; t < n; t += bs) pr += UP ? gp[t] * Gi[t * n + m] : Gi[m * n + t] * gp[t];
+    const double ox = xs[3 * e], oy = xs[3 * e + 1], oz = xs[3 * e + 2];
+    if (s.use_j1) {
+      for (int a = tid; a < s.n_atoms; a += bs) {
+        const double ax = s.R[3 * a], ay = s.R[3 * a + 1], az = s.R[3 * a + 2];
+        const double dn = sqrt((px - ax) * (px - ax) + (py - ay) * (py - ay) + (pz - az) * (pz - az));
+        const double d0 = sqrt((ox - ax) * (ox - ax) + (oy - ay) * (oy - ay) + (oz - az) * (oz - az));
+        pj += j1_val(s.c1[a], s.b_ea, dn) - j1_val(s.c1[a], s.b_ea, d0);
+      }
+    }
+    if (s.use_j2) {
+      for (int k = tid; k < N; k += bs) {
+        if (k == e) continue;
+        const bool same = (k < s.n_up) == UP;
+        double kk, bb;
+        j2_params(s, same, &kk, &bb);
+        const double qx = xs[3 * k], qy = xs[3 * k + 1], qz = xs[3 * k + 2];
+        const double dn = sqrt((px - qx) * (px - qx) + (py - qy) * (py - qy) + (pz - qz) * (pz - qz));
+        const double d0 = sqrt((ox - qx) * (ox - qx) + (oy - qy) * (oy - qy) + (oz - qz) * (oz - qz));
+        pj += j2_val(kk, bb, dn) - j2_val(kk, bb, d0);
+      }
+    }
+    block_sum2(pr, pj, red);
+    if (tid == 0) {
+      const double u = rp4[3];
+      const double p = pr * pr * exp(2.0 * pj);
+      int acc = 0;
+      if (!isfinite(p) || !isfinite(pr)) {
+        st_bits |= JAGP_WS_NONFINITE;
+      } else if (pr != 0.0 && u < p) {
+        acc = 1;
+        logdet += log(fabs(pr));
+        if (pr < 0.0) sgn = -sgn;
+        J += pj;
+        nacc += 1.0;
+        list[atomicAdd(count, 1)] = w * n + m;
+      }
+      s_acc = acc;
+      s_R = pr;
+    }
+    __syncthreads();
+    if (s_acc) {
+      for (int t = tid; t < n; t += bs) {
+        double a = 0.0;
+        if (UP) {
+          for (int j = 0; j < n; ++j) a += gp[j] * Gi[j * n + t];
+          cc[t] = Gi[t * n + m];
+        } else {
+          for (int i = 0; i < n; ++i) a += Gi[t * n + i] * gp[i];
+          cc[t] = Gi[m * n + t];
+        }
+        vv[t] = a;
+      }
+      __syncthreads();
+      const double invR = 1.0 / s_R;
+      for (int idx = tid; idx < n * n; idx += bs) {
+        const int j = idx / n, k = idx - j * n;
+        if (UP)
+          Gi[idx] -= cc[j] * (vv[k] - (k == m ? 1.0 : 0.0)) * invR;
+        else
+          Gi[idx] -= (vv[j] - (j == m ? 1.0 : 0.0)) * cc[k] * invR;
+      }
+      if (tid == 0) {
+        xs[3 * e] = px;
+        xs[3 * e + 1] = py;
+        xs[3 * e + 2] = pz;
+      }
+      if (UP) {
+        const double *src = pprop + ((size_t)w * n + m) * s.L;
+        double *dst = phi_up + ((size_t)w * n + m) * s.L;
+        for (int t = tid; t < s.L; t += bs) dst[t] = src[t];
+      }
+    }
+    __syncthreads();
+  }
+  for (int t = tid; t < n * n; t += bs) gw[t] = Gi[t];
+  for (int t = tid; t < N * 3; t += bs) r[(size_t)w * N * 3 + t] = xs[t];
+  if (tid == 0) {
+    scal[(size_t)w * S_STRIDE + S_LOGDET] = logdet;
+    scal[(size_t)w * S_STRIDE + S_SIGN] = sgn;
+    scal[(size_t)w * S_STRIDE + S_J] = J;
+    scal[(size_t)w * S_STRIDE + S_NACC] = nacc;
+    status[w] = st_bits;
+  }
+}
+
+cudaError_t launch_metropolis(const DevSystem &s, bool up, double *r, const double *rprop,
+                              const double *gprop, double *ginv, double *scal, int *status,
+                              const double *pprop, double *phi_up, int *list, int *count, int W,
+                              cudaStream_t st) {
+  if (W <= 0 || (!up && s.n_dn == 0)) return cudaSuccess;
+  const int n = s.n_up;
+  const size_t smem = (size_t)(n * n + s.N * 3 + 3 * n) * sizeof(double);
+  if (up)
+    k_metropolis<true><<<W, 128, smem, st>>>(s, r, rprop, gprop, ginv, scal, status, pprop, phi_up, list, count);
+  else
+    k_metropolis<false><<<W, 128, smem, st>>>(s, r, rprop, gprop, ginv, scal, status, pprop, phi_up, list, count);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// J = J1 + J2 of each walker from scratch (one CTA per walker).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_jastrow_full(DevSystem s, const double *__restrict__ r,
+                                                      double *__restrict__ scal) {
+  const int w = blockIdx.x, N = s.N;
+  const double *x = r + (size_t)w * N * 3;
+  __shared__ double red[64];
+  double j1 = 0.0, j2 = 0.0;
+  if (s.use_j1)
+    for (int idx = threadIdx.x; idx < N * s.n_atoms; idx += blockDim.x) {
+      const int i = idx / s.n_atoms, a = idx - i * s.n_atoms;
+      const double dx = x[3 * i] - s.R[3 * a], dy = x[3 * i + 1] - s.R[3 * a + 1], dz = x[3 * i + 2] - s.R[3 * a + 2];
+      j1 += j1_val(s.c1[a], s.b_ea, sqrt(dx * dx + dy * dy + dz * dz));
+    }
+  if (s.use_j2)
+    for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
+      const int i = idx / N, j = idx - i * N;
+      if (j <= i) continue;
+      double kk, bb;
+      j2_params(s, (i < s.n_up) == (j < s.n_up), &kk, &bb);
+      const double dx = x[3 * i] - x[3 * j], dy = x[3 * i + 1] - x[3 * j + 1], dz = x[3 * i + 2] - x[3 * j + 2];
+      j2 += j2_val(kk, bb, sqrt(dx * dx + dy * dy + dz * dz));
+    }
+  block_sum2(j1, j2, red);
+  if (threadIdx.x == 0) scal[(size_t)w * S_STRIDE + S_J] = j1 + j2;
+}
+
+cudaError_t launch_jastrow_full(const DevSystem &s, const double *r, double *scal, int W, cudaStream_t st) {
+  if (W <= 0) return cudaSuccess;
+  k_jastrow_full<<<W, 128, 0, st>>>(s, r, scal);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// bookkeeping
+// ---------------------------------------------------------------------------
+__global__ void k_walker_init(double *scal, int *status, int W) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= W) return;
+  scal[(size_t)w * S_STRIDE + S_NACC] = 0.0;
+  scal[(size_t)w * S_STRIDE + S_DRIFT] = 0.0;
+  status[w] = 0;
+}
+
+cudaError_t launch_walker_init(double *scal, int *status, int W, cudaStream_t st) {
+  if (W <= 0) return cudaSuccess;
+  k_walker_init<<<(W + 255) / 256, 256, 0, st>>>(scal, status, W);
+  return cudaGetLastError();
+}
+
+__global__ void k_logpsi_out(const double *scal, int W, double *logabs, double *sign) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= W) return;
+  const double *sw = scal + (size_t)w * S_STRIDE;
+  if (logabs) logabs[w] = sw[S_LOGDET] + sw[S_J];
+  if (sign) sign[w] = sw[S_SIGN];
+}
+
+cudaError_t launch_logpsi_out(const double *scal, int W, double *logabs, double *sign, cudaStream_t st) {
+  if (W <= 0 || (!logabs && !sign)) return cudaSuccess;
+  k_logpsi_out<<<(W + 255) / 256, 256, 0, st>>>(scal, W, logabs, sign);
+  return cudaGetLastError();
+}
+
+__global__ void k_walker_info(const double *scal, const int *status, int W, double *logabs, double *sign,
+                              double *nacc, double *drift, int *st_out) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= W) return;
+  const double *sw = scal + (size_t)w * S_STRIDE;
+  if (logabs) logabs[w] = sw[S_LOGDET] + sw[S_J];
+  if (sign) sign[w] = sw[S_SIGN];
+  if (nacc) nacc[w] = sw[S_NACC];
+  if (drift) drift[w] = sw[S_DRIFT];
+  if (st_out) st_out[w] = status[w];
+}
+
+cudaError_t launch_walker_info(const double *scal, const int *status, int W, double *logabs, double *sign,
+                               double *nacc, double *drift, int *st_out, cudaStream_t st) {
+  if (W <= 0) return cudaSuccess;
+  k_walker_info<<<(W + 255) / 256, 256, 0, st>>>(scal, status, W, logabs, sign, nacc, drift, st_out);
+  return cudaGetLastError();
+}
+
+// Per-sweep accumulators in a fixed reduction order (bitwise reproducible):
+// acc = (sum e_L, sum e_L^2, accepted moves of this sweep, max drift).
+__global__ void __launch_bounds__(1024) k_reduce_acc(const double *eL, const double *scal, const int *count,
+                                                     int W, double *acc) {
+  __shared__ double s1[1024], s2[1024], s3[1024];
+  double a = 0.0, b = 0.0, d = 0.0;
+  for (int w = threadIdx.x; w < W; w += blockDim.x) {
+    if (eL) {
+      const double e = eL[w];
+      a += e;
+      b += e * e;
+    }
+    d = fmax(d, scal[(size_t)w * S_STRIDE + S_DRIFT]);
+  }
+  s1[threadIdx.x] = a;
+  s2[threadIdx.x] = b;
+  s3[threadIdx.x] = d;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      s1[threadIdx.x] += s1[threadIdx.x + o];
+      s2[threadIdx.x] += s2[threadIdx.x + o];
+      s3[threadIdx.x] = fmax(s3[threadIdx.x], s3[threadIdx.x + o]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    acc[0] = s1[0];
+    acc[1] = s2[0];
+    acc[2] = (double)count[0] + (double)count[1];
+    acc[3] = s3[0];
+  }
+}
+
+cudaError_t launch_reduce_acc(const double *eL, const double *scal, const int *count, int W, double *acc,
+                              cudaStream_t st) {
+  k_reduce_acc<<<1, 1024, 0, st>>>(eL, scal, count, W, acc);
+  return cudaGetLastError();
+}
+
+}  // namespace jagp
+
+namespace jagp {
+cudaError_t setup_walker_attributes() {
+  cudaError_t e = cudaFuncSetAttribute(k_basis_points<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_basis_points<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_metropolis<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_metropolis<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+}
+}  // namespace jagp

@@ -1,0 +1,63 @@
+"""Host-side checks of the C ABI (no GPU needed): the library builds, loads and
+exports every function that include/jagp.h declares."""
+import ctypes
+import os
+import re
+import shutil
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER_DIR = os.path.join(ROOT, "include")
+
+
+def declared_functions():
+    names = []
+    for f in sorted(os.listdir(HEADER_DIR)):
+        if not f.endswith(".h"):
+            continue
+        txt = open(os.path.join(HEADER_DIR, f)).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*([a-z_0-9]+)\s*\(", txt, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.mark.skipif(shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"),
+                    reason="needs the CUDA toolkit to build")
+def test_library_exports_every_declared_symbol():
+    import paper_2002_07401_gb300 as pg
+    path = pg._build.build()
+    lib = ctypes.CDLL(path)
+    names = declared_functions()
+    assert {"jagp_create", "jagp_eval", "vmc_sweep", "local_energy"} <= set(names)
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings_and_bad_args_without_gpu():
+    """Argument validation happens on the host before any CUDA call."""
+    if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("needs the CUDA toolkit to build")
+    import paper_2002_07401_gb300 as pg
+    L = pg.lib()
+    assert L.jagp_status_string(0) == b"ok"
+    assert L.jagp_status_string(1) == b"invalid argument"
+    # null handle / bad sizes are rejected on the host
+    assert L.jagp_state_bytes(None, 4) == 0
+    assert L.jagp_eval(None, None, 1, None, None, None, None) == 1
+    assert L.vmc_sweep(None, None, None, 1, 1, 0, 0, None, None, None) == 1
+    assert L.local_energy(None, None, None, 1, None, None, None) == 1
+    h = ctypes.c_void_p()
+    assert L.jagp_create(ctypes.byref(h), None, None) == 1
+
+
+def test_oracle_and_product_share_no_code():
+    """Neither side imports or includes the other."""
+    pkg = os.path.join(ROOT, "paper_2002_07401_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "oracle" not in re.findall(r"(?:import|include)\s+[\"<]?([a-z_]+)", txt), f
+    txt = open(os.path.join(ROOT, "oracle", "jagp_oracle.c")).read()
+    assert "#include \"" not in txt
