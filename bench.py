@@ -37,7 +37,7 @@ WORKLOAD = ("plain FP64 VMC: 16 He atoms in a 10 bohr cube (min separation 1.5),
             "20 s/p/d Gaussians/atom (L=320), dense random symmetric lambda, J1 + J2, 4096 walkers/GPU")
 # FP64 CUDA-core peak of one GB300 (no measured value available): 1.25 TFLOP/s nominal
 FP64_PEAK_TFLOPS = 1.25
-PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "k_lambda_rows_C2_traffic.json")
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "k_lambda_rows_C2_traffic.txt")
 
 
 def dist_env():
@@ -186,7 +186,7 @@ def run_reference(args):
 # ----------------------------------------------------------------------------
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("k_linalg.cu", "jagp_common.cuh"):
+    for f in ("k_lambda.cu",):
         h.update(open(os.path.join(ROOT, "paper_2002_07401_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
