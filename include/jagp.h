@@ -153,6 +153,29 @@ jagp_status_t jagp_profile(jagp_handle_t h, int kernel, int enable);
 jagp_status_t jagp_profile_read(jagp_handle_t h, double *h_total_ms, long long *h_launches);
 long long jagp_launch_count(jagp_handle_t h);
 
+/* jagp_eval without any device allocation and without a workspace argument.
+ * The paper has no counterpart: this is a convenience of the library for
+ * callers that cannot allocate device memory when they need log|Psi| (code
+ * running under an allocator or memory pool that forbids new reservations, a
+ * host framework that owns every allocation, a loop that must not touch the
+ * allocator).  It computes the same d_logabs and d_sign [W] as jagp_eval for
+ * the configurations d_r [W][N][3], keeping its scratch in one file-scope
+ * device array of JAGP_NOALLOC_SCRATCH_BYTES that every GPU loading the
+ * library holds until the process exits.
+ *   - Allocates nothing: no cudaMalloc, cudaFree or allocating library call
+ *     (jagp_create still allocates the handle's tables once, at set-up).
+ *   - W whose scratch (about 4 N_up L + 2 N_up^2 doubles per walker) exceeds
+ *     the array returns JAGP_ERR_UNSUPPORTED before any launch.
+ *   - The first call on a device looks up the array's address (that device
+ *     must be current); make that first call before any stream capture.
+ *   - All calls share the array, which keeps the last call's contents; the
+ *     call clears what must start at zero.  Calls that overlap on the GPU
+ *     (other streams, other host threads) race on it: serialise them.
+ *   - A singular G~ gives log|Psi| = -inf and sign 0; no walker state is kept. */
+#define JAGP_NOALLOC_SCRATCH_BYTES (32u << 20)
+jagp_status_t jagp_eval_noalloc(jagp_handle_t h, const double *d_r, int W, double *d_logabs,
+                                double *d_sign, void *stream);
+
 const char *jagp_status_string(jagp_status_t s);
 
 #ifdef __cplusplus

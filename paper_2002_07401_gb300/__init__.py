@@ -71,6 +71,8 @@ def lib():
         L.jagp_profile_read.restype = i
         L.jagp_launch_count.argtypes = [vp]
         L.jagp_launch_count.restype = C.c_longlong
+        L.jagp_eval_noalloc.argtypes = [vp, vp, i, vp, vp, vp]
+        L.jagp_eval_noalloc.restype = i
         L.jagp_status_string.argtypes = [i]
         L.jagp_status_string.restype = C.c_char_p
         for f in ("jagp_create", "jagp_destroy", "jagp_eval", "vmc_sweep", "local_energy",
@@ -151,6 +153,18 @@ def jagp_state_bytes(h: int, W: int) -> int:
 def jagp_eval(h, r, W, state, logabs=None, sign=None, stream=None):
     _check(lib().jagp_eval(h, _ptr(r), int(W), _ptr(state), _ptr(logabs), _ptr(sign), _stream(stream)),
            "jagp_eval")
+
+
+NOALLOC_SCRATCH_BYTES = 32 << 20
+
+
+def jagp_eval_noalloc(h, r, W, logabs=None, sign=None, stream=None):
+    """log|Psi| and sign like jagp_eval, for callers that cannot allocate device
+    memory: the library keeps the scratch in a fixed 32 MiB device array shared
+    by all calls (serialise calls; the first call on a device must precede any
+    stream capture).  Raises for W whose scratch does not fit."""
+    _check(lib().jagp_eval_noalloc(h, _ptr(r), int(W), _ptr(logabs), _ptr(sign), _stream(stream)),
+           "jagp_eval_noalloc")
 
 
 def vmc_sweep(h, r, state, W, nsweeps, walker0=0, sweep0=0, eL=None, acc=None, stream=None):
