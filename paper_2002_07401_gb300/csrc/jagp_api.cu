@@ -123,17 +123,28 @@ jagp_status_t jagp_create(jagp_handle_t *out, const jagp_system_t *sys, const ja
   if (sys->n_up > sys->n_dn && !sys->unpaired) return JAGP_ERR_INVALID_ARG;
   if (opt->precision != JAGP_PREC_FP64) return JAGP_ERR_UNSUPPORTED;
   if (opt->max_walkers <= 0 || !(opt->delta > 0.0) || !isfinite(opt->delta)) return JAGP_ERR_INVALID_ARG;
+  // Shell table in evaluation order: grouped by (radial type, l) so that the 32
+  // lanes of a warp, which take consecutive shells, run the same branch; each
+  // record keeps the offset of its first function in the caller's order.
   int L = 0;
-  std::vector<double4> geo(sys->n_shells);
-  std::vector<int> info(sys->n_shells);
+  std::vector<double4> geo;
+  std::vector<int> info;
+  std::vector<int> offset(sys->n_shells);
   for (int k = 0; k < sys->n_shells; ++k) {
     const int l = sys->shell_l[k], a = sys->shell_atom[k], rad = sys->shell_radial[k];
     if (l < 0 || l > 2 || rad < 0 || rad > 1) return JAGP_ERR_UNSUPPORTED;
     if (a < 0 || a >= sys->n_atoms || !(sys->shell_zeta[k] >= 0.0)) return JAGP_ERR_INVALID_ARG;
-    geo[k] = make_double4(sys->R[3 * a], sys->R[3 * a + 1], sys->R[3 * a + 2], sys->shell_zeta[k]);
-    info[k] = l | (rad << 2) | (L << 8);
+    offset[k] = L;
     L += 2 * l + 1;
   }
+  for (int rad = 0; rad <= 1; ++rad)
+    for (int l = 0; l <= 2; ++l)
+      for (int k = 0; k < sys->n_shells; ++k) {
+        if (sys->shell_l[k] != l || sys->shell_radial[k] != rad) continue;
+        const int a = sys->shell_atom[k];
+        geo.push_back(make_double4(sys->R[3 * a], sys->R[3 * a + 1], sys->R[3 * a + 2], sys->shell_zeta[k]));
+        info.push_back(l | (rad << 2) | (offset[k] << 8));
+      }
   const int na = sys->n_atoms, k_unp = sys->n_up - sys->n_dn;
   std::vector<double> c1(na), lamT((size_t)L * L);
   double vii = 0.0;

@@ -12,6 +12,7 @@ namespace jagp {
 
 constexpr int kMaxUp = 64;          // N_up handled with G~^{-1} resident in shared memory
 constexpr int kWarp = 32;
+constexpr int kPropStride = 8;     // doubles per proposal record
 
 // Shell record packed for one 32-byte load: centre (x, y, z) and exponent.
 // info = l | radial << 2 | first-function-offset << 8.
@@ -40,7 +41,7 @@ struct Layout {
   size_t ginv;     // double [W][n_up][n_up] G~^{-1}
   size_t pprop;    // double [W][n_up][L]   orbitals at the proposals (scratch)
   size_t gprop;    // double [W][n_up][n_up] proposed rows / columns, or G~ at a refresh
-  size_t rprop;    // double [W][n_up][4]   proposal (x, y, z) and acceptance draw
+  size_t rprop;    // double [W][n_up][8]   proposal (x, y, z), acceptance draw, one-body Jastrow change
   size_t mbuf;     // double [W][N][L]      kinetic contraction vectors
   size_t kin;      // double [W][N][4]      grad_i D/D (3) and lap_i D/D
   size_t scal;     // double [W][8]         log|det|, sign, J, accepted, drift
@@ -64,7 +65,7 @@ inline Layout make_layout(size_t W, size_t nu, size_t N, size_t L) {
   l.ginv = take(W * nu * nu * 8);
   l.pprop = take(W * nu * L * 8);
   l.gprop = take(W * nu * nu * 8);
-  l.rprop = take(W * nu * 4 * 8);
+  l.rprop = take(W * nu * kPropStride * 8);
   l.mbuf = take(W * N * L * 8);
   l.kin = take(W * N * 4 * 8);
   l.scal = take(W * S_STRIDE * 8);

@@ -200,9 +200,126 @@ __global__ void __launch_bounds__(256) k_refresh_inverse(const double *__restric
   }
 }
 
+// The same elimination with one warp per walker (N_up <= 32): lane j owns the
+// columns j and j + 32 of [G~ | I]; pivot search by shuffles, no block barriers.
+constexpr int kRefreshWarps = 4;
+
+__global__ void __launch_bounds__(kRefreshWarps * 32) k_refresh_inverse_warp(
+    const double *__restrict__ gm, double *__restrict__ ginv, double *__restrict__ scal, int *__restrict__ status,
+    int n, int W, int check_drift, double drift_tol) {
+  extern __shared__ double sm[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int w = blockIdx.x * kRefreshWarps + warp;
+  if (w >= W) return;  // warp-uniform; no block-wide barrier below
+  const int ld = 2 * n + 1, n2 = 2 * n;
+  double *A = sm + (size_t)warp * (n * ld + n);
+  double *f = A + n * ld;
+  const double *G = gm + (size_t)w * n * n;
+  double gmax = 0.0;
+  for (int idx = lane; idx < n * n2; idx += 32) {
+    const int i = idx / n2, j = idx - i * n2;
+    double v;
+    if (j < n) {
+      v = G[i * n + j];
+      gmax = fmax(gmax, fabs(v));
+    } else {
+      v = (j - n == i) ? 1.0 : 0.0;
+    }
+    A[i * ld + j] = v;
+  }
+  __syncwarp();
+  double logdet = 0.0, sgn = 1.0;
+  bool ok = true;
+  for (int k = 0; k < n; ++k) {
+    double best = -1.0;
+    int bi = k;
+    for (int i = k + lane; i < n; i += 32) {
+      const double v = fabs(A[i * ld + k]);
+      if (v > best) {
+        best = v;
+        bi = i;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) {
+        best = ob;
+        bi = oi;
+      }
+    }
+    bi = __shfl_sync(0xffffffffu, bi, 0);
+    const double pv = A[bi * ld + k];
+    if (!(pv != 0.0) || !isfinite(pv)) {
+      ok = false;
+      break;
+    }
+    if (bi != k) {
+      for (int j = lane; j < n2; j += 32) {
+        const double t = A[k * ld + j];
+        A[k * ld + j] = A[bi * ld + j];
+        A[bi * ld + j] = t;
+      }
+      sgn = -sgn;
+    }
+    logdet += log(fabs(pv));
+    if (pv < 0.0) sgn = -sgn;
+    __syncwarp();
+    const double ip = 1.0 / pv;
+    for (int j = lane; j < n2; j += 32) A[k * ld + j] *= ip;
+    for (int i = lane; i < n; i += 32) f[i] = A[i * ld + k];
+    __syncwarp();
+    for (int i = 0; i < n; ++i) {
+      if (i == k) continue;
+      const double fi = f[i];
+      for (int j = lane; j < n2; j += 32)
+        if (j >= k) A[i * ld + j] = fma(-fi, A[k * ld + j], A[i * ld + j]);
+    }
+    __syncwarp();
+  }
+  double *gi = ginv + (size_t)w * n * n;
+  double *sw = scal + (size_t)w * S_STRIDE;
+  if (!ok) {
+    if (lane == 0) {
+      status[w] |= JAGP_WS_SINGULAR;
+      sw[S_LOGDET] = -INFINITY;
+      sw[S_SIGN] = 0.0;
+    }
+    return;
+  }
+  double dmax = 0.0;
+  for (int idx = lane; idx < n * n; idx += 32) {
+    const int i = idx / n, j = idx - i * n;
+    const double v = A[i * ld + n + j];
+    if (check_drift) dmax = fmax(dmax, fabs(v - gi[idx]));
+    gi[idx] = v;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+    gmax = fmax(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
+  }
+  if (lane == 0) {
+    sw[S_LOGDET] = logdet;
+    sw[S_SIGN] = sgn;
+    if (check_drift) {
+      const double drift = dmax * gmax;
+      sw[S_DRIFT] = drift;
+      if (!(drift <= drift_tol)) status[w] |= JAGP_WS_DRIFT;
+    }
+  }
+}
+
 cudaError_t launch_refresh_inverse(const double *gm, double *ginv, double *scal, int *status, int n, int W,
                                    int check_drift, double drift_tol, cudaStream_t st) {
   if (W <= 0) return cudaSuccess;
+  if (n <= 32) {
+    const size_t smem = (size_t)kRefreshWarps * (n * (2 * n + 1) + n) * sizeof(double);
+    k_refresh_inverse_warp<<<(W + kRefreshWarps - 1) / kRefreshWarps, kRefreshWarps * 32, smem, st>>>(
+        gm, ginv, scal, status, n, W, check_drift, drift_tol);
+    return cudaGetLastError();
+  }
   const size_t smem = (size_t)(n * (2 * n + 1) + n) * sizeof(double);
   k_refresh_inverse<<<W, 256, smem, st>>>(gm, ginv, scal, status, n, check_drift, drift_tol);
   return cudaGetLastError();
@@ -261,6 +378,8 @@ cudaError_t launch_mmat(const DevSystem &s, const double *ginv, const double *bt
 cudaError_t setup_kernel_attributes() {
   const int big = 200 * 1024;
   cudaError_t e = cudaFuncSetAttribute(k_refresh_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_refresh_inverse_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_mmat, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   return e;

@@ -38,7 +38,22 @@ __global__ void __launch_bounds__(256) k_basis_points(DevSystem s, const double 
       p[0] = rp[0];
       p[1] = rp[1];
       p[2] = rp[2];
-      if (lane < 4) rprop[((size_t)w * s.n_up + i) * 4 + lane] = lane < 3 ? rp[lane] : u;
+      // change of the one-body Jastrow for this move: it depends only on the
+      // electron's own old and new positions, so it is taken here, in parallel
+      // (lane pairs: even lanes take the new position, odd lanes the old one)
+      double dj1 = 0.0;
+      if (s.use_j1)
+        for (int q = lane; q < 2 * s.n_atoms; q += 32) {
+          const int a = q >> 1;
+          const double *pos = (q & 1) ? rr : rp;
+          const double ax = pos[0] - s.R[3 * a], ay = pos[1] - s.R[3 * a + 1], az = pos[2] - s.R[3 * a + 2];
+          const double v = j1_val(s.c1[a], s.b_ea, sqrt(ax * ax + ay * ay + az * az));
+          dj1 += (q & 1) ? -v : v;
+        }
+      dj1 = warp_sum(dj1);
+      double *rec = rprop + ((size_t)w * s.n_up + i) * kPropStride;
+      if (lane < 4) rec[lane] = lane < 3 ? rp[lane] : u;
+      if (lane == 0) rec[4] = dj1;
     }
     double *o = out + ((size_t)w * s.n_up + i) * s.L;
     for (int k = lane; k < s.n_shells; k += 32) {
@@ -139,21 +154,14 @@ __global__ void __launch_bounds__(128) k_metropolis(DevSystem s, double *__restr
   __syncthreads();
   for (int m = 0; m < nmoves; ++m) {
     const int e = e0 + m;
-    const double *rp4 = rprop + ((size_t)w * n + m) * 4;
+    const double *rp4 = rprop + ((size_t)w * n + m) * kPropStride;
     const double px = rp4[0], py = rp4[1], pz = rp4[2];
     for (int t = tid; t < n; t += bs) gp[t] = gprop[((size_t)w * n + m) * n + t];
     __syncthreads();
     double pr = 0.0, pj = 0.0;
     for (int t = tid; t < n; t += bs) pr += UP ? gp[t] * Gi[t * n + m] : Gi[m * n + t] * gp[t];
     const double ox = xs[3 * e], oy = xs[3 * e + 1], oz = xs[3 * e + 2];
-    if (s.use_j1) {
-      for (int a = tid; a < s.n_atoms; a += bs) {
-        const double ax = s.R[3 * a], ay = s.R[3 * a + 1], az = s.R[3 * a + 2];
-        const double dn = sqrt((px - ax) * (px - ax) + (py - ay) * (py - ay) + (pz - az) * (pz - az));
-        const double d0 = sqrt((ox - ax) * (ox - ax) + (oy - ay) * (oy - ay) + (oz - az) * (oz - az));
-        pj += j1_val(s.c1[a], s.b_ea, dn) - j1_val(s.c1[a], s.b_ea, d0);
-      }
-    }
+    if (tid == 0) pj = rp4[4];   // one-body Jastrow change, from the proposal kernel
     if (s.use_j2) {
       for (int k = tid; k < N; k += bs) {
         if (k == e) continue;
@@ -230,6 +238,118 @@ __global__ void __launch_bounds__(128) k_metropolis(DevSystem s, double *__restr
   }
 }
 
+// ---------------------------------------------------------------------------
+// The same acceptance loop with one warp per walker (N_up <= 32): G~^{-1} in
+// the warp's slice of shared memory, reductions by shuffles, no block barriers.
+// Every lane takes the accept decision from lane 0's sums so that it is uniform.
+// ---------------------------------------------------------------------------
+constexpr int kMetroWarps = 4;
+
+template <bool UP>
+__global__ void __launch_bounds__(kMetroWarps * 32) k_metropolis_warp(
+    DevSystem s, double *__restrict__ r, const double *__restrict__ rprop, const double *__restrict__ gprop,
+    double *__restrict__ ginv, double *__restrict__ scal, int *__restrict__ status,
+    const double *__restrict__ pprop, double *__restrict__ phi_up, int *__restrict__ list,
+    int *__restrict__ count, int W) {
+  extern __shared__ double sm[];
+  const int n = s.n_up, N = s.N, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int w = blockIdx.x * kMetroWarps + warp;
+  if (w >= W) return;  // warp-uniform; the kernel has no block-wide barrier
+  const int per = n * n + N * 3 + 3 * n;
+  double *Gi = sm + (size_t)warp * per;
+  double *xs = Gi + n * n;
+  double *gp = xs + N * 3;
+  double *vv = gp + n;
+  double *cc = vv + n;
+  double *gw = ginv + (size_t)w * n * n;
+  for (int t = lane; t < n * n; t += 32) Gi[t] = gw[t];
+  for (int t = lane; t < N * 3; t += 32) xs[t] = r[(size_t)w * N * 3 + t];
+  double *sw = scal + (size_t)w * S_STRIDE;
+  double logdet = sw[S_LOGDET], sgn = sw[S_SIGN], J = sw[S_J], nacc = sw[S_NACC];
+  int st_bits = status[w];
+  const int nmoves = UP ? s.n_up : s.n_dn;
+  const int e0 = UP ? 0 : s.n_up;
+  __syncwarp();
+  for (int m = 0; m < nmoves; ++m) {
+    const int e = e0 + m;
+    const double *rec = rprop + ((size_t)w * n + m) * kPropStride;
+    const double px = rec[0], py = rec[1], pz = rec[2];
+    const double *grow = gprop + ((size_t)w * n + m) * n;
+    double pr = 0.0, pj = 0.0;
+    for (int t = lane; t < n; t += 32) {
+      const double g = grow[t];
+      gp[t] = g;
+      pr += UP ? g * Gi[t * n + m] : Gi[m * n + t] * g;
+    }
+    if (lane == 0) pj = rec[4];
+    if (s.use_j2) {
+      const double ox = xs[3 * e], oy = xs[3 * e + 1], oz = xs[3 * e + 2];
+      for (int k = lane; k < N; k += 32) {
+        if (k == e) continue;
+        double kk, bb;
+        j2_params(s, (k < s.n_up) == UP, &kk, &bb);
+        const double qx = xs[3 * k], qy = xs[3 * k + 1], qz = xs[3 * k + 2];
+        const double dn = sqrt((px - qx) * (px - qx) + (py - qy) * (py - qy) + (pz - qz) * (pz - qz));
+        const double d0 = sqrt((ox - qx) * (ox - qx) + (oy - qy) * (oy - qy) + (oz - qz) * (oz - qz));
+        pj += j2_val(kk, bb, dn) - j2_val(kk, bb, d0);
+      }
+    }
+    pr = __shfl_sync(0xffffffffu, warp_sum(pr), 0);
+    pj = __shfl_sync(0xffffffffu, warp_sum(pj), 0);
+    const double p = pr * pr * exp(2.0 * pj);
+    int acc = 0;
+    if (!isfinite(p) || !isfinite(pr)) {
+      st_bits |= JAGP_WS_NONFINITE;
+    } else if (pr != 0.0 && rec[3] < p) {
+      acc = 1;
+    }
+    __syncwarp();
+    if (acc) {
+      logdet += log(fabs(pr));
+      if (pr < 0.0) sgn = -sgn;
+      J += pj;
+      nacc += 1.0;
+      if (lane == 0) list[atomicAdd(count, 1)] = w * n + m;
+      for (int t = lane; t < n; t += 32) {
+        double a = 0.0;
+        if (UP) {
+          for (int j = 0; j < n; ++j) a = fma(gp[j], Gi[j * n + t], a);
+          cc[t] = Gi[t * n + m];
+        } else {
+          for (int i = 0; i < n; ++i) a = fma(Gi[t * n + i], gp[i], a);
+          cc[t] = Gi[m * n + t];
+        }
+        vv[t] = a;
+      }
+      __syncwarp();
+      const double invR = 1.0 / pr;
+      for (int idx = lane; idx < n * n; idx += 32) {
+        const int j = idx / n, k = idx - j * n;
+        if (UP)
+          Gi[idx] -= cc[j] * (vv[k] - (k == m ? 1.0 : 0.0)) * invR;
+        else
+          Gi[idx] -= (vv[j] - (j == m ? 1.0 : 0.0)) * cc[k] * invR;
+      }
+      if (lane < 3) xs[3 * e + lane] = lane == 0 ? px : (lane == 1 ? py : pz);
+      if (UP) {
+        const double *src = pprop + ((size_t)w * n + m) * s.L;
+        double *dst = phi_up + ((size_t)w * n + m) * s.L;
+        for (int t = lane; t < s.L; t += 32) dst[t] = src[t];
+      }
+      __syncwarp();
+    }
+  }
+  for (int t = lane; t < n * n; t += 32) gw[t] = Gi[t];
+  for (int t = lane; t < N * 3; t += 32) r[(size_t)w * N * 3 + t] = xs[t];
+  if (lane == 0) {
+    sw[S_LOGDET] = logdet;
+    sw[S_SIGN] = sgn;
+    sw[S_J] = J;
+    sw[S_NACC] = nacc;
+    status[w] = st_bits;
+  }
+}
+
 cudaError_t launch_metropolis(const DevSystem &s, bool up, double *r, const double *rprop,
                               const double *gprop, double *ginv, double *scal, int *status,
                               const double *pprop, double *phi_up, int *list, int *count, int W,
@@ -237,6 +357,16 @@ cudaError_t launch_metropolis(const DevSystem &s, bool up, double *r, const doub
   if (W <= 0 || (!up && s.n_dn == 0)) return cudaSuccess;
   const int n = s.n_up;
   const size_t smem = (size_t)(n * n + s.N * 3 + 3 * n) * sizeof(double);
+  if (n <= 32) {
+    const int blocks = (W + kMetroWarps - 1) / kMetroWarps;
+    if (up)
+      k_metropolis_warp<true><<<blocks, kMetroWarps * 32, smem * kMetroWarps, st>>>(
+          s, r, rprop, gprop, ginv, scal, status, pprop, phi_up, list, count, W);
+    else
+      k_metropolis_warp<false><<<blocks, kMetroWarps * 32, smem * kMetroWarps, st>>>(
+          s, r, rprop, gprop, ginv, scal, status, pprop, phi_up, list, count, W);
+    return cudaGetLastError();
+  }
   if (up)
     k_metropolis<true><<<W, 128, smem, st>>>(s, r, rprop, gprop, ginv, scal, status, pprop, phi_up, list, count);
   else
@@ -377,6 +507,10 @@ cudaError_t setup_walker_attributes() {
   e = cudaFuncSetAttribute(k_basis_points<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_metropolis<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_metropolis_warp<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_metropolis_warp<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_metropolis<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
