@@ -137,6 +137,22 @@ jagp_status_t jagp_walker_info(jagp_handle_t h, const void *d_state, int W, doub
 jagp_status_t jagp_walker_status(jagp_handle_t h, const void *d_state, int W, int *h_bits,
                                  void *stream);
 
+/* The tensor-core contraction behind the lambda products of the mixed
+ * precision path (Sec. AGP, Eq. agp_expansion: rows phi^T lambda and
+ * lambda phi), exposed for direct use and testing:
+ *   C[rows[m]][n] = sum_{p < npairs} sum_{k < Kp} A[m][pair_a[p] Kp + k] * B[n][pair_b[p] Kp + k]
+ * d_A: BF16 bits [M][a_terms Kp], d_B: BF16 bits [N][b_terms Kp] (each row
+ * holds up to three BF16 terms of an FP32 row side by side; Kp % 64 == 0;
+ * 16-byte aligned bases); d_C: FP32 with row pitch ldc >= N; d_rows: [M]
+ * destination rows or NULL (identity); d_count: device int live row count
+ * (<= M) or NULL (= M).  tcgen05.mma (BF16 in, FP32 accumulate in tensor
+ * memory) fed by TMA.  h_pair_a/h_pair_b are host arrays of npairs (1..8) term
+ * indices.  *d_err (device int) is set non-zero if a pipeline wait timed out.
+ * Errors: INVALID_ARG for shapes, alignment or term indices. */
+jagp_status_t jagp_gemm_bf16x(const uint16_t *d_A, int M, int a_terms, const uint16_t *d_B, int N, int b_terms,
+                              int Kp, int npairs, const int *h_pair_a, const int *h_pair_b, float *d_C,
+                              long long ldc, const int *d_rows, const int *d_count, int *d_err, void *stream);
+
 /* Profiling hooks (Sec. "Derivatives of energy" aside, these are tooling, not
  * part of the method).  jagp_profile(h, kernel, 1) makes later vmc_sweep /
  * jagp_eval calls record a CUDA event pair on the launching stream around every

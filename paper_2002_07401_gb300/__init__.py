@@ -71,6 +71,8 @@ def lib():
         L.jagp_profile_read.restype = i
         L.jagp_launch_count.argtypes = [vp]
         L.jagp_launch_count.restype = C.c_longlong
+        L.jagp_gemm_bf16x.argtypes = [vp, i, i, vp, i, i, i, i, vp, vp, vp, C.c_longlong, vp, vp, vp, vp]
+        L.jagp_gemm_bf16x.restype = i
         L.jagp_eval_noalloc.argtypes = [vp, vp, i, vp, vp, vp]
         L.jagp_eval_noalloc.restype = i
         L.jagp_status_string.argtypes = [i]
@@ -187,6 +189,21 @@ def jagp_walker_status(h, state, W, stream=None) -> int:
     _check(lib().jagp_walker_status(h, _ptr(state), int(W), C.byref(bits), _stream(stream)),
            "jagp_walker_status")
     return bits.value
+
+
+def jagp_gemm_bf16x(A, a_terms, B, b_terms, Kp, pairs, out, rows=None, count=None, err=None, stream=None):
+    """Tensor-core contraction: out[rows[m]][n] = sum over (a, b) in pairs of
+    A[m, a*Kp:(a+1)*Kp] . B[n, b*Kp:(b+1)*Kp]  (A, B: bfloat16 tensors holding
+    a_terms / b_terms BF16 terms of width Kp; out: float32)."""
+    import torch
+    arr_a = (C.c_int * len(pairs))(*[int(a) for a, _ in pairs])
+    arr_b = (C.c_int * len(pairs))(*[int(b) for _, b in pairs])
+    if err is None:
+        err = torch.zeros(1, dtype=torch.int32, device=A.device)
+    _check(lib().jagp_gemm_bf16x(_ptr(A), int(A.shape[0]), int(a_terms), _ptr(B), int(B.shape[0]), int(b_terms),
+                                 int(Kp), len(pairs), arr_a, arr_b, _ptr(out), int(out.stride(0)), _ptr(rows),
+                                 _ptr(count), _ptr(err), _stream(stream)), "jagp_gemm_bf16x")
+    return err
 
 
 KERNEL_LAMBDA_ROWS, KERNEL_GEMM_ROWS, KERNEL_METROPOLIS, KERNEL_BASIS, KERNEL_ENERGY = 1, 2, 3, 4, 5

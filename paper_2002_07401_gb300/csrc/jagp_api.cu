@@ -168,6 +168,7 @@ jagp_status_t jagp_create(jagp_handle_t *out, const jagp_system_t *sys, const ja
     g_attr_err = setup_kernel_attributes();
     if (g_attr_err == cudaSuccess) g_attr_err = setup_walker_attributes();
     if (g_attr_err == cudaSuccess) g_attr_err = setup_energy_attributes();
+    if (g_attr_err == cudaSuccess) g_attr_err = setup_umma_attributes();
   });
   if (g_attr_err != cudaSuccess) {
     delete h;
@@ -324,6 +325,25 @@ jagp_status_t local_energy(jagp_handle_t h, const double *d_r, void *d_state, in
   if (s != JAGP_OK) return s;
   if (!d_r || !d_eL) return JAGP_ERR_INVALID_ARG;
   return run_local_energy(h, d_r, d_state, W, d_eL, d_parts, static_cast<cudaStream_t>(stream));
+}
+
+jagp_status_t jagp_gemm_bf16x(const uint16_t *d_A, int M, int a_terms, const uint16_t *d_B, int N, int b_terms,
+                              int Kp, int npairs, const int *h_pair_a, const int *h_pair_b, float *d_C,
+                              long long ldc, const int *d_rows, const int *d_count, int *d_err, void *stream) {
+  if (!d_A || !d_B || !d_C || !d_err || !h_pair_a || !h_pair_b) return JAGP_ERR_INVALID_ARG;
+  if (M <= 0 || N <= 0 || Kp <= 0 || Kp % 64 != 0 || ldc < N || npairs < 1 || npairs > 8) return JAGP_ERR_INVALID_ARG;
+  if (a_terms < 1 || a_terms > 3 || b_terms < 1 || b_terms > 3) return JAGP_ERR_INVALID_ARG;
+  std::call_once(g_attr_once, [] {
+    g_attr_err = setup_kernel_attributes();
+    if (g_attr_err == cudaSuccess) g_attr_err = setup_walker_attributes();
+    if (g_attr_err == cudaSuccess) g_attr_err = setup_energy_attributes();
+    if (g_attr_err == cudaSuccess) g_attr_err = setup_umma_attributes();
+  });
+  if (g_attr_err != cudaSuccess) return JAGP_ERR_CUDA;
+  const cudaError_t e = launch_umma_gemm(d_A, M, d_count, a_terms, d_B, N, b_terms, Kp, npairs, h_pair_a, h_pair_b,
+                                         d_C, ldc, d_rows, d_err, static_cast<cudaStream_t>(stream));
+  if (e == cudaErrorInvalidValue) return JAGP_ERR_INVALID_ARG;
+  return e == cudaSuccess ? JAGP_OK : JAGP_ERR_CUDA;
 }
 
 jagp_status_t jagp_profile(jagp_handle_t h, int kernel, int enable) {

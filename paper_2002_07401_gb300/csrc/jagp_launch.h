@@ -60,6 +60,16 @@ cudaError_t launch_walker_info(const double *scal, const int *status, int W, dou
 cudaError_t launch_reduce_acc(const double *eL, const double *scal, const int *count, int W,
                               double *acc, cudaStream_t st);
 
+// Tensor-core contraction (k_umma.cu):
+//   out[out_rows[m]][c] = sum_p sum_k A[m][pair_a[p] kp + k] B[c][pair_b[p] kp + k]
+// A: BF16 [m_max][a_terms kp], B: BF16 [n][b_terms kp] (kp % 64 == 0, 16-byte
+// aligned bases); rows m < *m_dev (or m_max) are written; out FP32, pitch ldo.
+int umma_pick_bn(int n);
+cudaError_t launch_umma_gemm(const uint16_t *A, int m_max, const int *m_dev, int a_terms, const uint16_t *B, int n,
+                             int b_terms, int kp, int npairs, const int *pair_a, const int *pair_b, float *out,
+                             long long ldo, const int *out_rows, int *err, cudaStream_t st);
+cudaError_t setup_umma_attributes();
+
 // one-time kernel attribute set-up (dynamic shared memory limits), per file
 cudaError_t setup_kernel_attributes();
 cudaError_t setup_walker_attributes();
