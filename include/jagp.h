@@ -52,8 +52,11 @@ typedef int jagp_status_t;
 #define JAGP_WS_DRIFT 4          /* Sherman-Morrison drift above tolerance at a refresh */
 
 #define JAGP_PREC_FP64 0         /* every step in float64 */
-#define JAGP_PREC_MIXED 1        /* basis fp32, lambda products bf16 tensor cores (fp32 accumulate),
-                                    fp64 refresh / log-det / energies */
+#define JAGP_PREC_MIXED 1        /* orbitals, lambda products, proposed rows and Sherman-Morrison in
+                                    FP32 (lambda products on the BF16 tensor cores with FP32
+                                    accumulation, operands cut into exact 8-bit fixed-point slices);
+                                    G~^{-1} refreshed by an FP64 elimination after every half-sweep;
+                                    log|det|, Jastrow, energies and their sums in FP64 */
 
 /* The system: atoms, basis, pairing matrix lambda, unpaired orbitals, Jastrow.
  * All pointers are host pointers, read during jagp_create only. */
@@ -81,7 +84,8 @@ typedef struct jagp_options {
   int max_walkers;            /* upper bound on W for every later call */
   double delta;               /* proposal half-width: r' = r + delta (2u - 1) per coordinate */
   uint64_t seed;              /* Philox4x32-10 key */
-  double drift_tol;           /* Sherman-Morrison drift tolerance checked at each refresh */
+  double drift_tol;           /* Sherman-Morrison drift tolerance checked at each refresh
+                                 (<= 0: 1e-8 for FP64, 1e-3 for MIXED) */
 } jagp_options_t;
 
 typedef struct jagp_ctx *jagp_handle_t;
@@ -139,19 +143,26 @@ jagp_status_t jagp_walker_status(jagp_handle_t h, const void *d_state, int W, in
 
 /* The tensor-core contraction behind the lambda products of the mixed
  * precision path (Sec. AGP, Eq. agp_expansion: rows phi^T lambda and
- * lambda phi), exposed for direct use and testing:
- *   C[rows[m]][n] = sum_{p < npairs} sum_{k < Kp} A[m][pair_a[p] Kp + k] * B[n][pair_b[p] Kp + k]
- * d_A: BF16 bits [M][a_terms Kp], d_B: BF16 bits [N][b_terms Kp] (each row
- * holds up to three BF16 terms of an FP32 row side by side; Kp % 64 == 0;
- * 16-byte aligned bases); d_C: FP32 with row pitch ldc >= N; d_rows: [M]
- * destination rows or NULL (identity); d_count: device int live row count
- * (<= M) or NULL (= M).  tcgen05.mma (BF16 in, FP32 accumulate in tensor
- * memory) fed by TMA.  h_pair_a/h_pair_b are host arrays of npairs (1..8) term
- * indices.  *d_err (device int) is set non-zero if a pipeline wait timed out.
- * Errors: INVALID_ARG for shapes, alignment or term indices. */
+ * lambda phi), exposed for direct use and testing.  tcgen05.mma (BF16 in,
+ * FP32 accumulate in tensor memory) fed by TMA.
+ *   plain mode (d_row_exp = d_col_exp = NULL):
+ *     C[rows[m]][n] = sum_{p < npairs} sum_{k < Kp} A[m][pair_a[p] Kp + k] * B[n][pair_b[p] Kp + k]
+ *   fixed-point mode (both exponent arrays given): the terms are exact 8-bit
+ *     integer slices, a = 2^(ea[m] - 7) sum_t A_t / 256^t (likewise b with
+ *     eb[n]), pairs with equal pair_a + pair_b (<= 3) share an exactly summed
+ *     accumulator S_d, and C = 2^(ea + eb - 14) sum_d S_d / 256^d.
+ * d_A: BF16 bits [M][a_terms Kp], d_B: BF16 bits [N][b_terms Kp] (up to four
+ * terms per row side by side; Kp % 64 == 0; 16-byte aligned bases); d_C: FP32
+ * with row pitch ldc >= N; d_rows: [M] destination rows or NULL (identity);
+ * d_count: device int live row count (<= M) or NULL (= M); d_row_exp [M],
+ * d_col_exp [N]: device ints or NULL.  h_pair_a/h_pair_b: host arrays of
+ * npairs (1..16) term indices.  *d_err (device int) is set non-zero if a
+ * pipeline wait timed out.  Errors: INVALID_ARG for shapes, alignment or term
+ * indices. */
 jagp_status_t jagp_gemm_bf16x(const uint16_t *d_A, int M, int a_terms, const uint16_t *d_B, int N, int b_terms,
                               int Kp, int npairs, const int *h_pair_a, const int *h_pair_b, float *d_C,
-                              long long ldc, const int *d_rows, const int *d_count, int *d_err, void *stream);
+                              long long ldc, const int *d_rows, const int *d_count, const int *d_row_exp,
+                              const int *d_col_exp, int *d_err, void *stream);
 
 /* Profiling hooks (Sec. "Derivatives of energy" aside, these are tooling, not
  * part of the method).  jagp_profile(h, kernel, 1) makes later vmc_sweep /

@@ -71,7 +71,7 @@ def lib():
         L.jagp_profile_read.restype = i
         L.jagp_launch_count.argtypes = [vp]
         L.jagp_launch_count.restype = C.c_longlong
-        L.jagp_gemm_bf16x.argtypes = [vp, i, i, vp, i, i, i, i, vp, vp, vp, C.c_longlong, vp, vp, vp, vp]
+        L.jagp_gemm_bf16x.argtypes = [vp, i, i, vp, i, i, i, i, vp, vp, vp, C.c_longlong, vp, vp, vp, vp, vp, vp]
         L.jagp_gemm_bf16x.restype = i
         L.jagp_eval_noalloc.argtypes = [vp, vp, i, vp, vp, vp]
         L.jagp_eval_noalloc.restype = i
@@ -112,7 +112,7 @@ def _stream(stream) -> Optional[int]:
 # --------------------------------------------------------------------------
 
 def jagp_create(sysm, precision: int = JAGP_PREC_FP64, max_walkers: int = 1, delta: Optional[float] = None,
-                seed: int = 0, drift_tol: float = 1e-8) -> int:
+                seed: int = 0, drift_tol: float = 0.0) -> int:
     """sysm: a ``synth.System``-like object (numpy arrays).  Returns the handle."""
     keep = []
 
@@ -191,10 +191,12 @@ def jagp_walker_status(h, state, W, stream=None) -> int:
     return bits.value
 
 
-def jagp_gemm_bf16x(A, a_terms, B, b_terms, Kp, pairs, out, rows=None, count=None, err=None, stream=None):
+def jagp_gemm_bf16x(A, a_terms, B, b_terms, Kp, pairs, out, rows=None, count=None, err=None, stream=None,
+                    row_exp=None, col_exp=None):
     """Tensor-core contraction: out[rows[m]][n] = sum over (a, b) in pairs of
     A[m, a*Kp:(a+1)*Kp] . B[n, b*Kp:(b+1)*Kp]  (A, B: bfloat16 tensors holding
-    a_terms / b_terms BF16 terms of width Kp; out: float32)."""
+    a_terms / b_terms BF16 terms of width Kp; out: float32).  With row_exp and
+    col_exp (int32) the terms are fixed-point slices (see include/jagp.h)."""
     import torch
     arr_a = (C.c_int * len(pairs))(*[int(a) for a, _ in pairs])
     arr_b = (C.c_int * len(pairs))(*[int(b) for _, b in pairs])
@@ -202,7 +204,8 @@ def jagp_gemm_bf16x(A, a_terms, B, b_terms, Kp, pairs, out, rows=None, count=Non
         err = torch.zeros(1, dtype=torch.int32, device=A.device)
     _check(lib().jagp_gemm_bf16x(_ptr(A), int(A.shape[0]), int(a_terms), _ptr(B), int(B.shape[0]), int(b_terms),
                                  int(Kp), len(pairs), arr_a, arr_b, _ptr(out), int(out.stride(0)), _ptr(rows),
-                                 _ptr(count), _ptr(err), _stream(stream)), "jagp_gemm_bf16x")
+                                 _ptr(count), _ptr(row_exp), _ptr(col_exp), _ptr(err), _stream(stream)),
+           "jagp_gemm_bf16x")
     return err
 
 
@@ -232,7 +235,7 @@ class JAGP:
     """One system on the current CUDA device with state for up to W walkers."""
 
     def __init__(self, sysm, W: int, precision: int = JAGP_PREC_FP64, seed: int = 0,
-                 delta: Optional[float] = None, drift_tol: float = 1e-8, device: str = "cuda"):
+                 delta: Optional[float] = None, drift_tol: float = 0.0, device: str = "cuda"):
         import torch
         if not torch.cuda.is_available():
             raise JagpError("libjagp needs a CUDA device; there is no CPU fallback")

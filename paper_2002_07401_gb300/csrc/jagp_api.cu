@@ -5,6 +5,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
+#include <cmath>
 #include <mutex>
 #include <vector>
 
@@ -55,12 +57,43 @@ struct LaunchScope {
   } while (0)
 
 Layout layout_of(const jagp_ctx *h, int W) {
-  return make_layout((size_t)W, (size_t)h->ds.n_up, (size_t)h->ds.N, (size_t)h->ds.L);
+  const bool mixed = h->precision == JAGP_PREC_MIXED;
+  return make_layout((size_t)W, (size_t)h->ds.n_up, (size_t)h->ds.N, (size_t)h->ds.L, mixed ? 4 : 8,
+                     mixed ? (size_t)h->kp : 0);
 }
+
+// the ten slice pairs (a, b) with a + b <= 3 of the four-slice fixed-point operands
+const int kPairA[10] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3};
+const int kPairB[10] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0};
 
 template <typename T>
 T *at(void *base, size_t off) {
   return reinterpret_cast<T *>(static_cast<char *>(base) + off);
+}
+
+// host: one row of FP64 values -> four exact 8-bit fixed-point slices (BF16 bits)
+// relative to 2^e, e = 1 + the binary exponent of the row's largest magnitude:
+// v = 2^(e - 7) (t0 + t1 / 256 + t2 / 256^2 + t3 / 256^3 + ...), |t| <= 128.
+uint16_t bf16_of_small_int(double q) {
+  const float f = static_cast<float>(q);  // |q| <= 128: exact in BF16
+  uint32_t u;
+  memcpy(&u, &f, 4);
+  return static_cast<uint16_t>(u >> 16);
+}
+int slice_row_fixed4(const double *v, size_t vstride, int L, uint16_t *dst, size_t kp) {
+  double mx = 0.0;
+  for (int k = 0; k < L; ++k) mx = std::max(mx, std::fabs(v[k * vstride]));
+  int e = 0;
+  if (mx > 0.0) std::frexp(mx, &e);  // mx = f 2^e, f in [0.5, 1)
+  for (int k = 0; k < L; ++k) {
+    double x = std::ldexp(v[k * vstride], 7 - e);
+    for (int t = 0; t < 4; ++t) {
+      const double q = std::nearbyint(x);
+      dst[t * kp + k] = bf16_of_small_int(q);
+      x = (x - q) * 256.0;
+    }
+  }
+  return e;
 }
 
 jagp_status_t check_walkers(const jagp_ctx *h, int W, const void *state) {
@@ -70,26 +103,161 @@ jagp_status_t check_walkers(const jagp_ctx *h, int W, const void *state) {
   return JAGP_OK;
 }
 
-// the FP64 local-energy sequence on a current state
+// lambda products of orbital rows: out[row] = P[row]^T lambda (left) or lambda P[row] (!left)
+// for the listed rows (list/count) or the (nsub, stride) rows r < nrows.
+jagp_status_t lambda_products(jagp_ctx *h, const double *P, double *out, bool left, const int *list, const int *count,
+                              int nrows, int nsub, int stride, int max_rows, void *, int, cudaStream_t st) {
+  LAUNCH(JAGP_KERNEL_LAMBDA_ROWS, 1,
+         launch_lambda_rows(P, left ? h->ds.lam : h->ds.lamT, out, list, count, nrows, nsub, stride, h->ds.L, max_rows,
+                            st));
+  return JAGP_OK;
+}
+jagp_status_t lambda_products(jagp_ctx *h, const float *P, float *out, bool left, const int *list, const int *count,
+                              int nrows, int nsub, int stride, int max_rows, void *state, int W, cudaStream_t st) {
+  // mixed path: cut the FP32 rows into fixed-point slices, then the exact
+  // tensor-core contraction against the sliced lambda
+  const Layout L = layout_of(h, W);
+  uint16_t *pack = at<uint16_t>(state, L.pack);
+  int *rows = at<int>(state, L.rows), *exps = at<int>(state, L.exps);
+  LAUNCH(0, 1, launch_pack_fixed4(P, list, count, nrows, nsub, stride, h->ds.L, h->kp, pack, rows, exps, max_rows, st));
+  // Bt rows (lambda phi) also keep their low parts for the refresh of G~
+  float *out_lo = left ? nullptr : at<float>(state, L.bt_lo);
+  LAUNCH(JAGP_KERNEL_LAMBDA_ROWS, 1,
+         launch_umma_gemm(pack, max_rows, count, 4, left ? h->split_lamT : h->split_lam, h->ds.L, 4, h->kp, 10, kPairA,
+                          kPairB, out, h->ds.L, rows, h->d_err, st, exps, left ? h->exp_lamT : h->exp_lam, out_lo));
+  return JAGP_OK;
+}
+
+// G~ = Phi_up Bt^T at a refresh: plain FP64 products, or the compensated FP32 sum
+cudaError_t refresh_geminal(const double *phi, size_t pw, const double *bt, size_t bw, int n, int Lb, double *g, int W,
+                            cudaStream_t st) {
+  return launch_gemm_rows<double>(phi, pw, bt, bw, n, n, Lb, g, (size_t)n * n, n, W, st);
+}
+cudaError_t refresh_geminal(const float *phi, size_t pw, const float *bt, const float *bt_lo, size_t bw, int n, int Lb,
+                            double *g, int W, cudaStream_t st) {
+  return launch_gemm_rows_dot2(phi, pw, bt, bt_lo, bw, n, n, Lb, g, (size_t)n * n, n, W, st);
+}
+cudaError_t refresh_geminal(const double *phi, size_t pw, const double *bt, const double *, size_t bw, int n, int Lb,
+                            double *g, int W, cudaStream_t st) {
+  return refresh_geminal(phi, pw, bt, bw, n, Lb, g, W, st);
+}
+const double *low_part(double *, const Layout &, void *) { return nullptr; }
+const float *low_part(float *, const Layout &L, void *state) { return at<float>(state, L.bt_lo); }
+// where the refresh keeps G~: the FP64 table, or the FP64 side array of the FP32 path
+double *refresh_g(double *, const Layout &L, void *state) { return at<double>(state, L.gprop); }
+double *refresh_g(float *, const Layout &L, void *state) { return at<double>(state, L.g64); }
+
+// the local-energy sequence on a current state
+template <typename T>
 jagp_status_t run_local_energy(jagp_ctx *h, const double *r, void *state, int W, double *eL, double *parts,
                                cudaStream_t st) {
   const Layout L = layout_of(h, W);
-  LAUNCH(JAGP_KERNEL_ENERGY, 1, launch_mmat(h->ds, at<double>(state, L.ginv), at<double>(state, L.bt), at<double>(state, L.a_up),
-                      at<double>(state, L.mbuf), W, st));
-  LAUNCH(JAGP_KERNEL_ENERGY, 1, launch_kinetic(h->ds, r, at<double>(state, L.mbuf), at<double>(state, L.kin), W, st));
+  LAUNCH(JAGP_KERNEL_ENERGY, 1,
+         launch_mmat<T>(h->ds, at<T>(state, L.ginv), at<T>(state, L.bt), at<T>(state, L.a_up), at<T>(state, L.mbuf), W,
+                        st));
+  LAUNCH(JAGP_KERNEL_ENERGY, 1, launch_kinetic<T>(h->ds, r, at<T>(state, L.mbuf), at<double>(state, L.kin), W, st));
   LAUNCH(JAGP_KERNEL_ENERGY, 1, launch_elocal(h->ds, r, at<double>(state, L.kin), eL, parts, W, st));
   return JAGP_OK;
 }
 
-// G~ = Phi_up Bt^T, its inverse, log|det| and J from the current tables
-jagp_status_t run_refresh(jagp_ctx *h, const double *r, void *state, int W, int check_drift, cudaStream_t st) {
+// G~ = Phi_up Bt^T, its inverse (FP64 elimination), log|det| and (optionally) J
+template <typename T>
+jagp_status_t run_refresh(jagp_ctx *h, const double *r, void *state, int W, int check_drift, bool jastrow,
+                          cudaStream_t st) {
   const Layout L = layout_of(h, W);
   const int n = h->ds.n_up, Lb = h->ds.L;
-  LAUNCH(JAGP_KERNEL_GEMM_ROWS, 1, launch_gemm_rows(at<double>(state, L.phi_up), (size_t)n * Lb, at<double>(state, L.bt), (size_t)n * Lb, n,
-                           n, Lb, at<double>(state, L.gprop), (size_t)n * n, n, W, st));
-  LAUNCH(0, 1, launch_refresh_inverse(at<double>(state, L.gprop), at<double>(state, L.ginv), at<double>(state, L.scal),
-                                 at<int>(state, L.status), n, W, check_drift, h->drift_tol, st));
-  LAUNCH(0, 1, launch_jastrow_full(h->ds, r, at<double>(state, L.scal), W, st));
+  double *gm = refresh_g(static_cast<T *>(nullptr), L, state);
+  LAUNCH(JAGP_KERNEL_GEMM_ROWS, 1,
+         refresh_geminal(at<T>(state, L.phi_up), (size_t)n * Lb, at<T>(state, L.bt),
+                         low_part(static_cast<T *>(nullptr), L, state), (size_t)n * Lb, n, Lb, gm, W, st));
+  LAUNCH(0, 1,
+         launch_refresh_inverse<T>(gm, at<T>(state, L.ginv), at<double>(state, L.scal), at<int>(state, L.status), n,
+                                   W, check_drift, h->drift_tol, st));
+  if (jastrow) LAUNCH(0, 1, launch_jastrow_full(h->ds, r, at<double>(state, L.scal), W, st));
+  return JAGP_OK;
+}
+
+template <typename T>
+jagp_status_t run_eval(jagp_ctx *h, const double *d_r, int W, void *d_state, double *d_logabs, double *d_sign,
+                       cudaStream_t st) {
+  const Layout L = layout_of(h, W);
+  const DevSystem &d = h->ds;
+  const int n = d.n_up;
+  T *phi_up = at<T>(d_state, L.phi_up), *pprop = at<T>(d_state, L.pprop);
+  LAUNCH(0, 1, launch_walker_init(at<double>(d_state, L.scal), at<int>(d_state, L.status), W, st));
+  LAUNCH(JAGP_KERNEL_BASIS, 1, launch_basis_points<T>(d, false, d_r, W, 0, n, phi_up, nullptr, 0, 0, st));
+  LAUNCH(JAGP_KERNEL_BASIS, d.n_dn > 0, launch_basis_points<T>(d, false, d_r, W, n, d.n_dn, pprop, nullptr, 0, 0, st));
+  // A_up = Phi_up lambda (every row); Bt rows j < n_dn = lambda phi(r_j^dn)
+  jagp_status_t s = lambda_products(h, phi_up, at<T>(d_state, L.a_up), true, nullptr, nullptr, W * n, n, n, W * n,
+                                    d_state, W, st);
+  if (s != JAGP_OK) return s;
+  if (d.n_dn > 0) {
+    s = lambda_products(h, pprop, at<T>(d_state, L.bt), false, nullptr, nullptr, W * d.n_dn, d.n_dn, n, W * d.n_dn,
+                        d_state, W, st);
+    if (s != JAGP_OK) return s;
+  }
+  LAUNCH(0, d.n_up > d.n_dn, launch_fill_unpaired<T>(d, at<T>(d_state, L.bt), W, st));
+  if (h->precision == JAGP_PREC_MIXED)
+    LAUNCH(0, d.n_up > d.n_dn, launch_fill_unpaired_lo(d, at<float>(d_state, L.bt_lo), W, st));
+  s = run_refresh<T>(h, d_r, d_state, W, 0, true, st);
+  if (s != JAGP_OK) return s;
+  LAUNCH(0, (d_logabs || d_sign), launch_logpsi_out(at<double>(d_state, L.scal), W, d_logabs, d_sign, st));
+  return JAGP_OK;
+}
+
+template <typename T>
+jagp_status_t run_sweeps(jagp_ctx *h, double *d_r, void *d_state, int W, int nsweeps, uint64_t walker0,
+                         uint64_t sweep0, double *d_eL, double *d_acc, cudaStream_t st) {
+  const Layout L = layout_of(h, W);
+  const DevSystem &d = h->ds;
+  const int n = d.n_up, Lb = d.L;
+  // the mixed path refreshes G~^{-1} in FP64 after every half-sweep (every N_up
+  // moves), the FP64 path once per sweep
+  const bool half_refresh = h->precision == JAGP_PREC_MIXED;
+  T *phi_up = at<T>(d_state, L.phi_up), *a_up = at<T>(d_state, L.a_up);
+  T *bt = at<T>(d_state, L.bt), *ginv = at<T>(d_state, L.ginv);
+  T *pprop = at<T>(d_state, L.pprop), *gprop = at<T>(d_state, L.gprop);
+  double *rprop = at<double>(d_state, L.rprop), *scal = at<double>(d_state, L.scal);
+  int *status = at<int>(d_state, L.status), *list = at<int>(d_state, L.list), *count = at<int>(d_state, L.count);
+  jagp_status_t s;
+  for (int t = 0; t < nsweeps; ++t) {
+    const uint32_t sw = (uint32_t)(sweep0 + (uint64_t)t);
+    JAGP_CU(cudaMemsetAsync(count, 0, 2 * sizeof(int), st));
+    // up electrons: rows of G~ against the frozen down-spin table Bt
+    LAUNCH(JAGP_KERNEL_BASIS, 1,
+           launch_basis_points<T>(d, true, d_r, W, 0, n, pprop, rprop, (uint32_t)walker0, sw, st));
+    LAUNCH(JAGP_KERNEL_GEMM_ROWS, 1,
+           launch_gemm_rows<T>(pprop, (size_t)n * Lb, bt, (size_t)n * Lb, n, n, Lb, gprop, (size_t)n * n, n, W, st));
+    LAUNCH(JAGP_KERNEL_METROPOLIS, 1,
+           launch_metropolis<T>(d, true, d_r, rprop, gprop, ginv, scal, status, pprop, phi_up, list, count, W, st));
+    s = lambda_products(h, pprop, a_up, true, list, count, 0, 1, 0, W * n, d_state, W, st);
+    if (s != JAGP_OK) return s;
+    if (half_refresh && d.n_dn > 0) {
+      s = run_refresh<T>(h, d_r, d_state, W, 1, false, st);
+      if (s != JAGP_OK) return s;
+    }
+    if (d.n_dn > 0) {
+      // down electrons: columns of G~ against the updated up-spin table A_up
+      LAUNCH(JAGP_KERNEL_BASIS, 1,
+             launch_basis_points<T>(d, true, d_r, W, n, d.n_dn, pprop, rprop, (uint32_t)walker0, sw, st));
+      LAUNCH(JAGP_KERNEL_GEMM_ROWS, 1,
+             launch_gemm_rows<T>(pprop, (size_t)n * Lb, a_up, (size_t)n * Lb, d.n_dn, n, Lb, gprop, (size_t)n * n, n,
+                                 W, st));
+      LAUNCH(JAGP_KERNEL_METROPOLIS, 1,
+             launch_metropolis<T>(d, false, d_r, rprop, gprop, ginv, scal, status, pprop, phi_up, list, count + 1, W,
+                                  st));
+      s = lambda_products(h, pprop, bt, false, list, count + 1, 0, 1, 0, W * d.n_dn, d_state, W, st);
+      if (s != JAGP_OK) return s;
+    }
+    s = run_refresh<T>(h, d_r, d_state, W, 1, true, st);
+    if (s != JAGP_OK) return s;
+    double *eL = d_eL ? d_eL + (size_t)t * W : nullptr;
+    if (eL) {
+      s = run_local_energy<T>(h, d_r, d_state, W, eL, nullptr, st);
+      if (s != JAGP_OK) return s;
+    }
+    if (d_acc) LAUNCH(0, 1, launch_reduce_acc(eL, scal, count, W, d_acc + (size_t)t * 4, st));
+  }
   return JAGP_OK;
 }
 
@@ -121,7 +289,7 @@ jagp_status_t jagp_create(jagp_handle_t *out, const jagp_system_t *sys, const ja
   if (sys->n_dn > sys->n_up) return JAGP_ERR_UNSUPPORTED;
   if (sys->n_up > kMaxUp) return JAGP_ERR_UNSUPPORTED;
   if (sys->n_up > sys->n_dn && !sys->unpaired) return JAGP_ERR_INVALID_ARG;
-  if (opt->precision != JAGP_PREC_FP64) return JAGP_ERR_UNSUPPORTED;
+  if (opt->precision != JAGP_PREC_FP64 && opt->precision != JAGP_PREC_MIXED) return JAGP_ERR_UNSUPPORTED;
   if (opt->max_walkers <= 0 || !(opt->delta > 0.0) || !isfinite(opt->delta)) return JAGP_ERR_INVALID_ARG;
   // Shell table in evaluation order: grouped by (radial type, l) so that the 32
   // lanes of a warp, which take consecutive shells, run the same branch; each
@@ -181,6 +349,21 @@ jagp_status_t jagp_create(jagp_handle_t *out, const jagp_system_t *sys, const ja
   const size_t oG = take(sys->n_shells * sizeof(double4)), oI = take(sys->n_shells * sizeof(int));
   const size_t oL = take((size_t)L * L * 8), oT = take((size_t)L * L * 8);
   const size_t oU = take((size_t)(k_unp > 0 ? k_unp : 1) * L * 8);
+  // mixed path: lambda^T and lambda as fixed-point slices, rows padded to kp
+  const bool mixed = opt->precision == JAGP_PREC_MIXED;
+  const int kp = (L + 63) / 64 * 64;
+  const size_t split_bytes = mixed ? (size_t)L * 4 * kp * 2 : 0;
+  const size_t exp_bytes = mixed ? (size_t)L * 4 : 0;
+  const size_t oSA = take(split_bytes), oSB = take(split_bytes), oXA = take(exp_bytes), oXB = take(exp_bytes);
+  const size_t oE = take(16);
+  std::vector<uint16_t> sA(split_bytes / 2, 0), sB(split_bytes / 2, 0);
+  std::vector<int> xA(mixed ? L : 0), xB(mixed ? L : 0);
+  if (mixed) {
+    for (int nn = 0; nn < L; ++nn) {
+      xA[nn] = slice_row_fixed4(sys->lambda + nn, (size_t)L, L, &sA[(size_t)nn * 4 * kp], (size_t)kp);  // column nn
+      xB[nn] = slice_row_fixed4(sys->lambda + (size_t)nn * L, 1, L, &sB[(size_t)nn * 4 * kp], (size_t)kp);  // row nn
+    }
+  }
   if (cudaMalloc(&h->d_mem, off) != cudaSuccess) {
     delete h;
     return JAGP_ERR_OOM;
@@ -194,7 +377,12 @@ jagp_status_t jagp_create(jagp_handle_t *out, const jagp_system_t *sys, const ja
             cudaMemcpy(b + oL, sys->lambda, (size_t)L * L * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
             cudaMemcpy(b + oT, lamT.data(), (size_t)L * L * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
             (k_unp == 0 ||
-             cudaMemcpy(b + oU, sys->unpaired, (size_t)k_unp * L * 8, cudaMemcpyHostToDevice) == cudaSuccess);
+             cudaMemcpy(b + oU, sys->unpaired, (size_t)k_unp * L * 8, cudaMemcpyHostToDevice) == cudaSuccess) &&
+            (!mixed || (cudaMemcpy(b + oSA, sA.data(), split_bytes, cudaMemcpyHostToDevice) == cudaSuccess &&
+                        cudaMemcpy(b + oSB, sB.data(), split_bytes, cudaMemcpyHostToDevice) == cudaSuccess &&
+                        cudaMemcpy(b + oXA, xA.data(), exp_bytes, cudaMemcpyHostToDevice) == cudaSuccess &&
+                        cudaMemcpy(b + oXB, xB.data(), exp_bytes, cudaMemcpyHostToDevice) == cudaSuccess)) &&
+            cudaMemset(b + oE, 0, 16) == cudaSuccess;
   if (!ok) {
     cudaFree(h->d_mem);
     delete h;
@@ -226,8 +414,14 @@ jagp_status_t jagp_create(jagp_handle_t *out, const jagp_system_t *sys, const ja
   d.key0 = (uint32_t)(opt->seed & 0xffffffffu);
   d.key1 = (uint32_t)(opt->seed >> 32);
   h->precision = opt->precision;
+  h->kp = kp;
+  h->split_lamT = mixed ? reinterpret_cast<const uint16_t *>(b + oSA) : nullptr;
+  h->split_lam = mixed ? reinterpret_cast<const uint16_t *>(b + oSB) : nullptr;
+  h->exp_lamT = mixed ? reinterpret_cast<const int *>(b + oXA) : nullptr;
+  h->exp_lam = mixed ? reinterpret_cast<const int *>(b + oXB) : nullptr;
+  h->d_err = reinterpret_cast<int *>(b + oE);
   h->max_walkers = opt->max_walkers;
-  h->drift_tol = opt->drift_tol > 0.0 ? opt->drift_tol : 1e-8;
+  h->drift_tol = opt->drift_tol > 0.0 ? opt->drift_tol : (mixed ? 1e-3 : 1e-8);
   *out = h;
   return JAGP_OK;
 }
@@ -254,24 +448,8 @@ jagp_status_t jagp_eval(jagp_handle_t h, const double *d_r, int W, void *d_state
   if (s != JAGP_OK) return s;
   if (!d_r) return JAGP_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const Layout L = layout_of(h, W);
-  const DevSystem &d = h->ds;
-  const int n = d.n_up, Lb = d.L;
-  double *phi_up = at<double>(d_state, L.phi_up), *pprop = at<double>(d_state, L.pprop);
-  LAUNCH(0, 1, launch_walker_init(at<double>(d_state, L.scal), at<int>(d_state, L.status), W, st));
-  LAUNCH(JAGP_KERNEL_BASIS, 1, launch_basis_points(d, false, d_r, W, 0, n, phi_up, nullptr, 0, 0, st));
-  LAUNCH(JAGP_KERNEL_BASIS, d.n_dn > 0, launch_basis_points(d, false, d_r, W, n, d.n_dn, pprop, nullptr, 0, 0, st));
-  // A_up = Phi_up lambda (every row); Bt rows j < n_dn = lambda phi(r_j^dn)
-  LAUNCH(JAGP_KERNEL_LAMBDA_ROWS, 1, launch_lambda_rows(phi_up, d.lam, at<double>(d_state, L.a_up), nullptr, nullptr, W * n, n, n, Lb, W * n,
-                             st));
-  if (d.n_dn > 0)
-    LAUNCH(JAGP_KERNEL_LAMBDA_ROWS, 1, launch_lambda_rows(pprop, d.lamT, at<double>(d_state, L.bt), nullptr, nullptr, W * d.n_dn, d.n_dn, n,
-                               Lb, W * d.n_dn, st));
-  LAUNCH(0, d.n_up > d.n_dn, launch_fill_unpaired(d, at<double>(d_state, L.bt), W, st));
-  s = run_refresh(h, d_r, d_state, W, 0, st);
-  if (s != JAGP_OK) return s;
-  LAUNCH(0, (d_logabs || d_sign), launch_logpsi_out(at<double>(d_state, L.scal), W, d_logabs, d_sign, st));
-  return JAGP_OK;
+  if (h->precision == JAGP_PREC_MIXED) return run_eval<float>(h, d_r, W, d_state, d_logabs, d_sign, st);
+  return run_eval<double>(h, d_r, W, d_state, d_logabs, d_sign, st);
 }
 
 jagp_status_t vmc_sweep(jagp_handle_t h, double *d_r, void *d_state, int W, int nsweeps, uint64_t walker0,
@@ -282,41 +460,9 @@ jagp_status_t vmc_sweep(jagp_handle_t h, double *d_r, void *d_state, int W, int 
   if (walker0 + (uint64_t)W > 0x100000000ull || sweep0 + (uint64_t)nsweeps > 0x100000000ull)
     return JAGP_ERR_INVALID_ARG;  // Philox counter words are 32-bit
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const Layout L = layout_of(h, W);
-  const DevSystem &d = h->ds;
-  const int n = d.n_up, Lb = d.L;
-  double *phi_up = at<double>(d_state, L.phi_up), *a_up = at<double>(d_state, L.a_up);
-  double *bt = at<double>(d_state, L.bt), *ginv = at<double>(d_state, L.ginv);
-  double *pprop = at<double>(d_state, L.pprop), *gprop = at<double>(d_state, L.gprop);
-  double *rprop = at<double>(d_state, L.rprop), *scal = at<double>(d_state, L.scal);
-  int *status = at<int>(d_state, L.status), *list = at<int>(d_state, L.list), *count = at<int>(d_state, L.count);
-  for (int t = 0; t < nsweeps; ++t) {
-    const uint32_t sw = (uint32_t)(sweep0 + (uint64_t)t);
-    JAGP_CU(cudaMemsetAsync(count, 0, 2 * sizeof(int), st));
-    // up electrons: rows of G~ against the frozen down-spin table Bt
-    LAUNCH(JAGP_KERNEL_BASIS, 1, launch_basis_points(d, true, d_r, W, 0, n, pprop, rprop, (uint32_t)walker0, sw, st));
-    LAUNCH(JAGP_KERNEL_GEMM_ROWS, 1, launch_gemm_rows(pprop, (size_t)n * Lb, bt, (size_t)n * Lb, n, n, Lb, gprop, (size_t)n * n, n, W, st));
-    LAUNCH(JAGP_KERNEL_METROPOLIS, 1, launch_metropolis(d, true, d_r, rprop, gprop, ginv, scal, status, pprop, phi_up, list, count, W, st));
-    LAUNCH(JAGP_KERNEL_LAMBDA_ROWS, 1, launch_lambda_rows(pprop, d.lam, a_up, list, count, 0, 1, 0, Lb, W * n, st));
-    if (d.n_dn > 0) {
-      // down electrons: columns of G~ against the updated up-spin table A_up
-      LAUNCH(JAGP_KERNEL_BASIS, 1, launch_basis_points(d, true, d_r, W, n, d.n_dn, pprop, rprop, (uint32_t)walker0, sw, st));
-      LAUNCH(JAGP_KERNEL_GEMM_ROWS, 1, launch_gemm_rows(pprop, (size_t)n * Lb, a_up, (size_t)n * Lb, d.n_dn, n, Lb, gprop, (size_t)n * n, n,
-                               W, st));
-      LAUNCH(JAGP_KERNEL_METROPOLIS, 1, launch_metropolis(d, false, d_r, rprop, gprop, ginv, scal, status, pprop, phi_up, list, count + 1, W,
-                                st));
-      LAUNCH(JAGP_KERNEL_LAMBDA_ROWS, 1, launch_lambda_rows(pprop, d.lamT, bt, list, count + 1, 0, 1, 0, Lb, W * d.n_dn, st));
-    }
-    s = run_refresh(h, d_r, d_state, W, 1, st);
-    if (s != JAGP_OK) return s;
-    double *eL = d_eL ? d_eL + (size_t)t * W : nullptr;
-    if (eL) {
-      s = run_local_energy(h, d_r, d_state, W, eL, nullptr, st);
-      if (s != JAGP_OK) return s;
-    }
-    if (d_acc) LAUNCH(0, 1, launch_reduce_acc(eL, scal, count, W, d_acc + (size_t)t * 4, st));
-  }
-  return JAGP_OK;
+  if (h->precision == JAGP_PREC_MIXED)
+    return run_sweeps<float>(h, d_r, d_state, W, nsweeps, walker0, sweep0, d_eL, d_acc, st);
+  return run_sweeps<double>(h, d_r, d_state, W, nsweeps, walker0, sweep0, d_eL, d_acc, st);
 }
 
 jagp_status_t local_energy(jagp_handle_t h, const double *d_r, void *d_state, int W, double *d_eL,
@@ -324,15 +470,22 @@ jagp_status_t local_energy(jagp_handle_t h, const double *d_r, void *d_state, in
   jagp_status_t s = check_walkers(h, W, d_state);
   if (s != JAGP_OK) return s;
   if (!d_r || !d_eL) return JAGP_ERR_INVALID_ARG;
-  return run_local_energy(h, d_r, d_state, W, d_eL, d_parts, static_cast<cudaStream_t>(stream));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (h->precision == JAGP_PREC_MIXED) return run_local_energy<float>(h, d_r, d_state, W, d_eL, d_parts, st);
+  return run_local_energy<double>(h, d_r, d_state, W, d_eL, d_parts, st);
 }
 
 jagp_status_t jagp_gemm_bf16x(const uint16_t *d_A, int M, int a_terms, const uint16_t *d_B, int N, int b_terms,
                               int Kp, int npairs, const int *h_pair_a, const int *h_pair_b, float *d_C,
-                              long long ldc, const int *d_rows, const int *d_count, int *d_err, void *stream) {
+                              long long ldc, const int *d_rows, const int *d_count, const int *d_row_exp,
+                              const int *d_col_exp, int *d_err, void *stream) {
   if (!d_A || !d_B || !d_C || !d_err || !h_pair_a || !h_pair_b) return JAGP_ERR_INVALID_ARG;
-  if (M <= 0 || N <= 0 || Kp <= 0 || Kp % 64 != 0 || ldc < N || npairs < 1 || npairs > 8) return JAGP_ERR_INVALID_ARG;
-  if (a_terms < 1 || a_terms > 3 || b_terms < 1 || b_terms > 3) return JAGP_ERR_INVALID_ARG;
+  if (M <= 0 || N <= 0 || Kp <= 0 || Kp % 64 != 0 || ldc < N || npairs < 1 || npairs > 16) return JAGP_ERR_INVALID_ARG;
+  if (a_terms < 1 || a_terms > 4 || b_terms < 1 || b_terms > 4) return JAGP_ERR_INVALID_ARG;
+  if ((d_row_exp == nullptr) != (d_col_exp == nullptr)) return JAGP_ERR_INVALID_ARG;
+  if (d_row_exp)
+    for (int p = 0; p < npairs; ++p)
+      if (h_pair_a[p] + h_pair_b[p] > 3) return JAGP_ERR_INVALID_ARG;
   std::call_once(g_attr_once, [] {
     g_attr_err = setup_kernel_attributes();
     if (g_attr_err == cudaSuccess) g_attr_err = setup_walker_attributes();
@@ -341,7 +494,8 @@ jagp_status_t jagp_gemm_bf16x(const uint16_t *d_A, int M, int a_terms, const uin
   });
   if (g_attr_err != cudaSuccess) return JAGP_ERR_CUDA;
   const cudaError_t e = launch_umma_gemm(d_A, M, d_count, a_terms, d_B, N, b_terms, Kp, npairs, h_pair_a, h_pair_b,
-                                         d_C, ldc, d_rows, d_err, static_cast<cudaStream_t>(stream));
+                                         d_C, ldc, d_rows, d_err, static_cast<cudaStream_t>(stream), d_row_exp,
+                                         d_col_exp);
   if (e == cudaErrorInvalidValue) return JAGP_ERR_INVALID_ARG;
   return e == cudaSuccess ? JAGP_OK : JAGP_ERR_CUDA;
 }

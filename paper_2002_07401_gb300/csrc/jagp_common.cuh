@@ -34,20 +34,28 @@ struct DevSystem {
 };
 
 // Byte offsets of the per-walker arrays inside the caller's state buffer.
+// Orbital tables, G~ and its inverse are stored in the precision of the path
+// (FP64, or FP32 in the mixed path, "T" below); positions, proposals,
+// per-walker scalars and the kinetic partial sums are always FP64.
 struct Layout {
-  size_t phi_up;   // double [W][n_up][L]   orbitals at the current up positions
-  size_t a_up;     // double [W][n_up][L]   rows phi(r_i^up)^T lambda
-  size_t bt;       // double [W][n_up][L]   rows lambda phi(r_j^dn) (j < n_dn), then c^{(l)}
-  size_t ginv;     // double [W][n_up][n_up] G~^{-1}
-  size_t pprop;    // double [W][n_up][L]   orbitals at the proposals (scratch)
-  size_t gprop;    // double [W][n_up][n_up] proposed rows / columns, or G~ at a refresh
-  size_t rprop;    // double [W][n_up][8]   proposal (x, y, z), acceptance draw, one-body Jastrow change
-  size_t mbuf;     // double [W][N][L]      kinetic contraction vectors
-  size_t kin;      // double [W][N][4]      grad_i D/D (3) and lap_i D/D
-  size_t scal;     // double [W][8]         log|det|, sign, J, accepted, drift
+  size_t phi_up;   // T      [W][n_up][L]    orbitals at the current up positions
+  size_t a_up;     // T      [W][n_up][L]    rows phi(r_i^up)^T lambda
+  size_t bt;       // T      [W][n_up][L]    rows lambda phi(r_j^dn) (j < n_dn), then c^{(l)}
+  size_t ginv;     // T      [W][n_up][n_up] G~^{-1}
+  size_t pprop;    // T      [W][n_up][L]    orbitals at the proposals (scratch)
+  size_t gprop;    // T      [W][n_up][n_up] proposed rows / columns, or G~ at a refresh
+  size_t rprop;    // double [W][n_up][8]    proposal (x, y, z), acceptance draw, one-body Jastrow change
+  size_t mbuf;     // T      [W][N][L]       kinetic contraction vectors
+  size_t kin;      // double [W][N][4]       grad_i D/D (3) and lap_i D/D
+  size_t scal;     // double [W][8]          log|det|, sign, J, accepted, drift
   size_t status;   // int    [W]
-  size_t list;     // int    [W][n_up]      accepted moves of a half-sweep
+  size_t list;     // int    [W][n_up]       accepted moves of a half-sweep
   size_t count;    // int    [4]
+  size_t pack;     // BF16   [W n_up][4 kp]  mixed path: fixed-point slices of the lambda-product rows
+  size_t rows;     // int    [W n_up]        mixed path: destination rows of the packed operand
+  size_t exps;     // int    [W n_up]        mixed path: row exponents of the packed operand
+  size_t g64;      // double [W][n_up][n_up] mixed path: G~ at a refresh (FP64 result of the compensated sum)
+  size_t bt_lo;    // float  [W][n_up][L]    mixed path: low parts of Bt (Bt + bt_lo is a two-float table)
   size_t total;
 };
 
@@ -55,23 +63,29 @@ enum { S_LOGDET = 0, S_SIGN = 1, S_J = 2, S_NACC = 3, S_DRIFT = 4, S_STRIDE = 8 
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-inline Layout make_layout(size_t W, size_t nu, size_t N, size_t L) {
+// esz: bytes per table element (8 or 4); kp: padded K of the packed operand (0 = none)
+inline Layout make_layout(size_t W, size_t nu, size_t N, size_t L, size_t esz = 8, size_t kp = 0) {
   Layout l;
   size_t o = 0;
   auto take = [&](size_t bytes) { size_t r = o; o = align256(o + bytes); return r; };
-  l.phi_up = take(W * nu * L * 8);
-  l.a_up = take(W * nu * L * 8);
-  l.bt = take(W * nu * L * 8);
-  l.ginv = take(W * nu * nu * 8);
-  l.pprop = take(W * nu * L * 8);
-  l.gprop = take(W * nu * nu * 8);
+  l.phi_up = take(W * nu * L * esz);
+  l.a_up = take(W * nu * L * esz);
+  l.bt = take(W * nu * L * esz);
+  l.ginv = take(W * nu * nu * esz);
+  l.pprop = take(W * nu * L * esz);
+  l.gprop = take(W * nu * nu * esz);
   l.rprop = take(W * nu * kPropStride * 8);
-  l.mbuf = take(W * N * L * 8);
+  l.mbuf = take(W * N * L * esz);
   l.kin = take(W * N * 4 * 8);
   l.scal = take(W * S_STRIDE * 8);
   l.status = take(W * 4);
   l.list = take(W * nu * 4);
   l.count = take(16);
+  l.pack = take(W * nu * 4 * kp * 2);
+  l.rows = take(kp ? W * nu * 4 : 0);
+  l.exps = take(kp ? W * nu * 4 : 0);
+  l.g64 = take(esz == 4 ? W * nu * nu * 8 : 0);
+  l.bt_lo = take(esz == 4 ? W * nu * L * 4 : 0);
   l.total = o;
   return l;
 }
@@ -120,19 +134,39 @@ __device__ __forceinline__ int shell_l(int info) { return info & 3; }
 __device__ __forceinline__ int shell_rad(int info) { return (info >> 2) & 1; }
 __device__ __forceinline__ int shell_off(int info) { return info >> 8; }
 
+// Radial factor g = e^{-zeta r^2} (Gaussian) or e^{-zeta r} (Slater) from the
+// FP64 squared distance.  FP64: the library exp.  FP32 (mixed path): the
+// exponent x is formed in FP64 and split x = x_hi + x_lo (x_hi its FP32
+// rounding), and g = exp_f32(x_hi) (1 + x_lo): FP32 relative accuracy even for
+// large |x|, where rounding the argument itself to FP32 would not be.
 template <typename T>
-__device__ __forceinline__ T texp(T x);
+__device__ __forceinline__ T radial_factor(int rad, double zeta, double r2);
 template <>
-__device__ __forceinline__ double texp<double>(double x) { return exp(x); }
+__device__ __forceinline__ double radial_factor<double>(int rad, double zeta, double r2) {
+  return rad ? exp(-zeta * sqrt(r2)) : exp(-zeta * r2);
+}
 template <>
-__device__ __forceinline__ float texp<float>(float x) { return expf(x); }
+__device__ __forceinline__ float radial_factor<float>(int rad, double zeta, double r2) {
+  const double x = rad ? -zeta * sqrt(r2) : -zeta * r2;
+  const float xh = static_cast<float>(x);
+  const float xl = static_cast<float>(x - static_cast<double>(xh));
+  return expf(xh) * (1.0f + xl);
+}
 
-// values only; returns the number of components written to v
+// values only, at the FP64 displacement (dx, dy, dz) from the shell's atom;
+// returns the number of components written to v.  FP32 values: the radial
+// factor exp(x_hi)(1 + x_lo) and the angular polynomial are multiplied in FP64
+// and rounded once, so each value carries the FP32 exponential's error and a
+// single rounding.
 template <typename T>
-__device__ __forceinline__ int shell_values(int info, T zeta, T dx, T dy, T dz, T v[5]) {
+__device__ __forceinline__ int shell_values(int info, double zeta, double dx, double dy, double dz, T v[5]);
+
+template <>
+__device__ __forceinline__ int shell_values<double>(int info, double zeta, double dx, double dy, double dz,
+                                                    double v[5]) {
   const int l = shell_l(info);
-  const T r2 = dx * dx + dy * dy + dz * dz;
-  const T g = shell_rad(info) ? texp<T>(-zeta * sqrt(r2)) : texp<T>(-zeta * r2);
+  const double r2 = dx * dx + dy * dy + dz * dz;
+  const double g = radial_factor<double>(shell_rad(info), zeta, r2);
   if (l == 0) {
     v[0] = g;
     return 1;
@@ -147,43 +181,72 @@ __device__ __forceinline__ int shell_values(int info, T zeta, T dx, T dy, T dz, 
   v[1] = dy * dz * g;
   v[2] = dz * dx * g;
   v[3] = (dx * dx - dy * dy) * g;
-  v[4] = (T(3) * dz * dz - r2) * g;
+  v[4] = (3.0 * dz * dz - r2) * g;
+  return 5;
+}
+
+template <>
+__device__ __forceinline__ int shell_values<float>(int info, double zeta, double dx, double dy, double dz,
+                                                   float v[5]) {
+  const int l = shell_l(info);
+  const double r2 = dx * dx + dy * dy + dz * dz;
+  const double x = shell_rad(info) ? -zeta * sqrt(r2) : -zeta * r2;
+  const float xh = static_cast<float>(x);
+  const float xl = static_cast<float>(x - static_cast<double>(xh));
+  const double g = static_cast<double>(expf(xh)) * (1.0 + static_cast<double>(xl));
+  if (l == 0) {
+    v[0] = static_cast<float>(g);
+    return 1;
+  }
+  if (l == 1) {
+    v[0] = static_cast<float>(dx * g);
+    v[1] = static_cast<float>(dy * g);
+    v[2] = static_cast<float>(dz * g);
+    return 3;
+  }
+  v[0] = static_cast<float>(dx * dy * g);
+  v[1] = static_cast<float>(dy * dz * g);
+  v[2] = static_cast<float>(dz * dx * g);
+  v[3] = static_cast<float>((dx * dx - dy * dy) * g);
+  v[4] = static_cast<float>((3.0 * dz * dz - r2) * g);
   return 5;
 }
 
 // values, gradients and Laplacians: out[c] = {v, gx, gy, gz, lap}
-__device__ __forceinline__ int shell_derivs(int info, double zeta, double dx, double dy, double dz,
-                                            double out[5][5]) {
+template <typename T>
+__device__ __forceinline__ int shell_derivs(int info, double zeta_d, double dxd, double dyd, double dzd,
+                                            T out[5][5]) {
   const int l = shell_l(info);
-  const double r2 = dx * dx + dy * dy + dz * dz;
-  double g, gg[3], lapg;
+  const double r2d = dxd * dxd + dyd * dyd + dzd * dzd;
+  const T zeta = static_cast<T>(zeta_d), dx = static_cast<T>(dxd), dy = static_cast<T>(dyd), dz = static_cast<T>(dzd);
+  const T r2 = static_cast<T>(r2d);
+  const T g = radial_factor<T>(shell_rad(info), zeta_d, r2d);
+  T gg[3], lapg;
   if (shell_rad(info)) {
-    const double r = sqrt(r2);
-    g = exp(-zeta * r);
-    const double f = -zeta / r * g;
+    const T r = static_cast<T>(sqrt(r2d));
+    const T f = -zeta / r * g;
     gg[0] = f * dx;
     gg[1] = f * dy;
     gg[2] = f * dz;
-    lapg = (zeta * zeta - 2.0 * zeta / r) * g;
+    lapg = (zeta * zeta - T(2) * zeta / r) * g;
   } else {
-    g = exp(-zeta * r2);
-    const double f = -2.0 * zeta * g;
+    const T f = T(-2) * zeta * g;
     gg[0] = f * dx;
     gg[1] = f * dy;
     gg[2] = f * dz;
-    lapg = (4.0 * zeta * zeta * r2 - 6.0 * zeta) * g;
+    lapg = (T(4) * zeta * zeta * r2 - T(6) * zeta) * g;
   }
-  const double d[3] = {dx, dy, dz};
+  const T d[3] = {dx, dy, dz};
   const int nc = 2 * l + 1;
 #pragma unroll
   for (int c = 0; c < 5; ++c) {
     if (c >= nc) break;
-    double P, gP[3] = {0.0, 0.0, 0.0};
+    T P, gP[3] = {T(0), T(0), T(0)};
     if (l == 0) {
-      P = 1.0;
+      P = T(1);
     } else if (l == 1) {
       P = d[c];
-      gP[c] = 1.0;
+      gP[c] = T(1);
     } else if (c == 0) {
       P = dx * dy; gP[0] = dy; gP[1] = dx;
     } else if (c == 1) {
@@ -191,15 +254,15 @@ __device__ __forceinline__ int shell_derivs(int info, double zeta, double dx, do
     } else if (c == 2) {
       P = dz * dx; gP[0] = dz; gP[2] = dx;
     } else if (c == 3) {
-      P = dx * dx - dy * dy; gP[0] = 2.0 * dx; gP[1] = -2.0 * dy;
+      P = dx * dx - dy * dy; gP[0] = T(2) * dx; gP[1] = T(-2) * dy;
     } else {
-      P = 3.0 * dz * dz - r2; gP[0] = -2.0 * dx; gP[1] = -2.0 * dy; gP[2] = 4.0 * dz;
+      P = T(3) * dz * dz - r2; gP[0] = T(-2) * dx; gP[1] = T(-2) * dy; gP[2] = T(4) * dz;
     }
     out[c][0] = P * g;
     out[c][1] = gP[0] * g + P * gg[0];
     out[c][2] = gP[1] * g + P * gg[1];
     out[c][3] = gP[2] * g + P * gg[2];
-    out[c][4] = 2.0 * (gP[0] * gg[0] + gP[1] * gg[1] + gP[2] * gg[2]) + P * lapg;
+    out[c][4] = T(2) * (gP[0] * gg[0] + gP[1] * gg[1] + gP[2] * gg[2]) + P * lapg;
   }
   return nc;
 }

@@ -16,4 +16,12 @@ struct jagp_ctx {
   long long launches = 0;
   int prof_kernel = 0;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events;
+  // mixed path: lambda as fixed-point slices (four exact 8-bit integer terms per
+  // element, BF16) with one exponent per output column, for the tensor cores
+  int kp = 0;                            // L padded to a multiple of 64
+  const uint16_t *split_lamT = nullptr;  // [L][4 kp]: row n slices lambda[:, n]  (A_up = phi^T lambda)
+  const uint16_t *split_lam = nullptr;   // [L][4 kp]: row n slices lambda[n, :]  (Bt = lambda phi)
+  const int *exp_lamT = nullptr;         // [L] exponents of those rows
+  const int *exp_lam = nullptr;          // [L]
+  int *d_err = nullptr;                  // tensor-core pipeline timeout flag
 };

@@ -11,19 +11,28 @@ namespace jagp {
 // Orbital values at electron positions (PROPOSE = false) or at freshly drawn
 // proposals (PROPOSE = true, also writes rprop).  Rows go to
 // out[(w * n_up + i) * L], i < npts, for electrons e0 .. e0 + npts - 1.
+template <typename T>
 cudaError_t launch_basis_points(const DevSystem &s, bool propose, const double *r, int W, int e0,
-                                int npts, double *out, double *rprop, uint32_t walker0,
+                                int npts, T *out, double *rprop, uint32_t walker0,
                                 uint32_t sweep, cudaStream_t st);
 
 // Sequential Metropolis over one spin species with Sherman-Morrison updates.
-cudaError_t launch_metropolis(const DevSystem &s, bool up, double *r, const double *rprop,
-                              const double *gprop, double *ginv, double *scal, int *status,
-                              const double *pprop, double *phi_up, int *list, int *count, int W,
-                              cudaStream_t st);
+template <typename T>
+cudaError_t launch_metropolis(const DevSystem &s, bool up, double *r, const double *rprop, const T *gprop,
+                              T *ginv, double *scal, int *status, const T *pprop, T *phi_up, int *list,
+                              int *count, int W, cudaStream_t st);
 
 // Out[w][a][b] = sum_k X[w][a][k] Y[w][b][k]  (a < ma, b < nb, k < K); row stride K.
-cudaError_t launch_gemm_rows(const double *X, size_t xw, const double *Y, size_t yw, int ma, int nb,
-                             int K, double *Out, size_t ow, int ldo, int W, cudaStream_t st);
+template <typename T>
+cudaError_t launch_gemm_rows(const T *X, size_t xw, const T *Y, size_t yw, int ma, int nb, int K, T *Out,
+                             size_t ow, int ldo, int W, cudaStream_t st);
+
+// FP32 variant with a compensated (error-free transformation) dot product; Y may
+// carry a low part Ylo (same layout) so that Y + Ylo is a two-float operand
+cudaError_t launch_gemm_rows_dot2(const float *X, size_t xw, const float *Y, const float *Ylo, size_t yw, int ma,
+                                  int nb, int K, double *Out, size_t ow, int ldo, int W, cudaStream_t st);
+// low parts of the unpaired-orbital rows of Bt (two-float table of the FP32 path)
+cudaError_t launch_fill_unpaired_lo(const DevSystem &s, float *bt_lo, int W, cudaStream_t st);
 
 // Out[row] = P[row] * Lam (L x L).  Rows are list[0 .. *count) when list is
 // given, else rows r < nrows mapped to (r / nsub) * stride + r % nsub.
@@ -32,21 +41,25 @@ cudaError_t launch_lambda_rows(const double *P, const double *Lam, double *Out, 
                                int max_rows, cudaStream_t st);
 
 // Fill rows n_dn .. n_up - 1 of every walker's Bt block with the unpaired orbitals.
-cudaError_t launch_fill_unpaired(const DevSystem &s, double *bt, int W, cudaStream_t st);
+template <typename T>
+cudaError_t launch_fill_unpaired(const DevSystem &s, T *bt, int W, cudaStream_t st);
 
 // Gauss-Jordan inverse with partial pivoting of G~ (in gm), log|det|, sign and
 // the Sherman-Morrison drift against the inverse held in ginv.
-cudaError_t launch_refresh_inverse(const double *gm, double *ginv, double *scal, int *status, int n,
-                                   int W, int check_drift, double drift_tol, cudaStream_t st);
+template <typename T>
+cudaError_t launch_refresh_inverse(const double *gm, T *ginv, double *scal, int *status, int n, int W,
+                                   int check_drift, double drift_tol, cudaStream_t st);
 
 cudaError_t launch_jastrow_full(const DevSystem &s, const double *r, double *scal, int W,
                                 cudaStream_t st);
 
 // M vectors of the kinetic energy (see k_linalg.cu), then the orbital
 // derivative contractions and the final per-walker local energy.
-cudaError_t launch_mmat(const DevSystem &s, const double *ginv, const double *bt, const double *a_up,
-                        double *mbuf, int W, cudaStream_t st);
-cudaError_t launch_kinetic(const DevSystem &s, const double *r, const double *mbuf, double *kin, int W,
+template <typename T>
+cudaError_t launch_mmat(const DevSystem &s, const T *ginv, const T *bt, const T *a_up, T *mbuf, int W,
+                        cudaStream_t st);
+template <typename T>
+cudaError_t launch_kinetic(const DevSystem &s, const double *r, const T *mbuf, double *kin, int W,
                            cudaStream_t st);
 cudaError_t launch_elocal(const DevSystem &s, const double *r, const double *kin, double *eL,
                           double *parts, int W, cudaStream_t st);
@@ -64,11 +77,20 @@ cudaError_t launch_reduce_acc(const double *eL, const double *scal, const int *c
 //   out[out_rows[m]][c] = sum_p sum_k A[m][pair_a[p] kp + k] B[c][pair_b[p] kp + k]
 // A: BF16 [m_max][a_terms kp], B: BF16 [n][b_terms kp] (kp % 64 == 0, 16-byte
 // aligned bases); rows m < *m_dev (or m_max) are written; out FP32, pitch ldo.
-int umma_pick_bn(int n);
+// With a_exp/b_exp (row / column exponents) the terms are fixed-point slices and
+// pairs of equal a + b share an exact accumulator (see k_umma.cu).
+int umma_pick_bn(int n, int max_bn);
 cudaError_t launch_umma_gemm(const uint16_t *A, int m_max, const int *m_dev, int a_terms, const uint16_t *B, int n,
                              int b_terms, int kp, int npairs, const int *pair_a, const int *pair_b, float *out,
-                             long long ldo, const int *out_rows, int *err, cudaStream_t st);
+                             long long ldo, const int *out_rows, int *err, cudaStream_t st,
+                             const int *a_exp = nullptr, const int *b_exp = nullptr, float *out_lo = nullptr);
+// FP32 rows -> four exact 8-bit slices per element (BF16) plus a row exponent
+cudaError_t launch_pack_fixed4(const float *P, const int *list, const int *count, int nrows, int nsub, int stride,
+                               int L, int kp, uint16_t *A, int *rows_out, int *exps, int max_rows, cudaStream_t st);
 cudaError_t setup_umma_attributes();
+// FP32 rows -> compact three-term BF16 operand rows (see k_umma.cu)
+cudaError_t launch_pack_split3(const float *P, const int *list, const int *count, int nrows, int nsub, int stride,
+                               int L, int kp, uint16_t *A, int *rows_out, int max_rows, cudaStream_t st);
 
 // one-time kernel attribute set-up (dynamic shared memory limits), per file
 cudaError_t setup_kernel_attributes();

@@ -13,8 +13,9 @@ namespace jagp {
 // electron's M vector (see k_mmat): one warp per electron, lanes over shells;
 // the derivative tables are never stored.
 // ---------------------------------------------------------------------------
+template <typename T>
 __global__ void __launch_bounds__(256) k_kinetic(DevSystem s, const double *__restrict__ r,
-                                                 const double *__restrict__ mbuf, double *__restrict__ kin,
+                                                 const T *__restrict__ mbuf, double *__restrict__ kin,
                                                  int W) {
   extern __shared__ double4 sh_geo[];
   int *sh_info = reinterpret_cast<int *>(sh_geo + s.n_shells);
@@ -29,28 +30,29 @@ __global__ void __launch_bounds__(256) k_kinetic(DevSystem s, const double *__re
   for (long pt = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); pt < total; pt += nwarps) {
     const double *rr = r + pt * 3;
     const double px = rr[0], py = rr[1], pz = rr[2];
-    const double *M = mbuf + pt * s.L;
-    double gx = 0.0, gy = 0.0, gz = 0.0, lp = 0.0;
+    const T *M = mbuf + pt * s.L;
+    T tx = T(0), ty = T(0), tz = T(0), tl = T(0);
     for (int k = lane; k < s.n_shells; k += 32) {
       const double4 g = sh_geo[k];
       const int info = sh_info[k];
-      double o[5][5];
-      const int nc = shell_derivs(info, g.w, px - g.x, py - g.y, pz - g.z, o);
+      T o[5][5];
+      const int nc = shell_derivs<T>(info, g.w, px - g.x, py - g.y, pz - g.z, o);
       const int off = shell_off(info);
 #pragma unroll
       for (int c = 0; c < 5; ++c) {
         if (c >= nc) break;
-        const double m = M[off + c];
-        gx = fma(o[c][1], m, gx);
-        gy = fma(o[c][2], m, gy);
-        gz = fma(o[c][3], m, gz);
-        lp = fma(o[c][4], m, lp);
+        const T m = M[off + c];
+        tx = fma(o[c][1], m, tx);
+        ty = fma(o[c][2], m, ty);
+        tz = fma(o[c][3], m, tz);
+        tl = fma(o[c][4], m, tl);
       }
     }
-    gx = warp_sum(gx);
-    gy = warp_sum(gy);
-    gz = warp_sum(gz);
-    lp = warp_sum(lp);
+    // lane partials are summed in FP64
+    const double gx = warp_sum(static_cast<double>(tx));
+    const double gy = warp_sum(static_cast<double>(ty));
+    const double gz = warp_sum(static_cast<double>(tz));
+    const double lp = warp_sum(static_cast<double>(tl));
     if (lane == 0) {
       double *o = kin + pt * 4;
       o[0] = gx;
@@ -61,16 +63,20 @@ __global__ void __launch_bounds__(256) k_kinetic(DevSystem s, const double *__re
   }
 }
 
-cudaError_t launch_kinetic(const DevSystem &s, const double *r, const double *mbuf, double *kin, int W,
-                           cudaStream_t st) {
+template <typename T>
+cudaError_t launch_kinetic(const DevSystem &s, const double *r, const T *mbuf, double *kin, int W, cudaStream_t st) {
   if (W <= 0) return cudaSuccess;
   const long total = (long)W * s.N;
   long blocks = (total + 7) / 8;
   if (blocks > 152 * 16) blocks = 152 * 16;
   const size_t smem = (size_t)s.n_shells * (sizeof(double4) + sizeof(int));
-  k_kinetic<<<(int)blocks, 256, smem, st>>>(s, r, mbuf, kin, W);
+  k_kinetic<T><<<(int)blocks, 256, smem, st>>>(s, r, mbuf, kin, W);
   return cudaGetLastError();
 }
+template cudaError_t launch_kinetic<double>(const DevSystem &, const double *, const double *, double *, int,
+                                            cudaStream_t);
+template cudaError_t launch_kinetic<float>(const DevSystem &, const double *, const float *, double *, int,
+                                           cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // Jastrow derivatives, kinetic assembly and the Coulomb terms: one CTA per walker.
@@ -158,7 +164,9 @@ cudaError_t launch_elocal(const DevSystem &s, const double *r, const double *kin
 }
 
 cudaError_t setup_energy_attributes() {
-  return cudaFuncSetAttribute(k_kinetic, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaError_t e = cudaFuncSetAttribute(k_kinetic<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_kinetic<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
 }  // namespace jagp

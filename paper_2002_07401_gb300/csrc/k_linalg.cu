@@ -14,24 +14,25 @@ namespace jagp {
 // CTA, one output per thread, operands staged through shared memory in
 // k-chunks of 64 (row pitch 65 doubles: conflict-free column reads).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_gemm_rows(const double *__restrict__ X, size_t xw,
-                                                   const double *__restrict__ Y, size_t yw, int ma, int nb,
-                                                   int K, double *__restrict__ Out, size_t ow, int ldo) {
-  __shared__ double Xs[16][65];
-  __shared__ double Ys[16][65];
+template <typename T>
+__global__ void __launch_bounds__(256) k_gemm_rows(const T *__restrict__ X, size_t xw,
+                                                   const T *__restrict__ Y, size_t yw, int ma, int nb,
+                                                   int K, T *__restrict__ Out, size_t ow, int ldo) {
+  __shared__ T Xs[16][65];
+  __shared__ T Ys[16][65];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int w = blockIdx.z, a0 = blockIdx.y * 16, b0 = blockIdx.x * 16;
-  const double *Xw = X + (size_t)w * xw;
-  const double *Yw = Y + (size_t)w * yw;
-  double acc = 0.0;
+  const T *Xw = X + (size_t)w * xw;
+  const T *Yw = Y + (size_t)w * yw;
+  T acc = T(0);
   for (int k0 = 0; k0 < K; k0 += 64) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int idx = threadIdx.x + q * 256, row = idx >> 6, col = idx & 63;
       const int k = k0 + col;
       const int a = a0 + row, b = b0 + row;
-      Xs[row][col] = (a < ma && k < K) ? Xw[(size_t)a * K + k] : 0.0;
-      Ys[row][col] = (b < nb && k < K) ? Yw[(size_t)b * K + k] : 0.0;
+      Xs[row][col] = (a < ma && k < K) ? Xw[(size_t)a * K + k] : T(0);
+      Ys[row][col] = (b < nb && k < K) ? Yw[(size_t)b * K + k] : T(0);
     }
     __syncthreads();
 #pragma unroll 16
@@ -41,15 +42,75 @@ __global__ void __launch_bounds__(256) k_gemm_rows(const double *__restrict__ X,
   if (a0 + ty < ma && b0 + tx < nb) Out[(size_t)w * ow + (size_t)(a0 + ty) * ldo + b0 + tx] = acc;
 }
 
-cudaError_t launch_gemm_rows(const double *X, size_t xw, const double *Y, size_t yw, int ma, int nb, int K,
-                             double *Out, size_t ow, int ldo, int W, cudaStream_t st) {
+// The refresh's G~ = Phi_up Bt^T in the FP32 path: the same tile scheme with a
+// compensated dot product (error-free product by fma, error-free sum, the
+// errors summed separately; Ogita, Rump and Oishi 2005), so that the FP32
+// tables give G~ to about FP32 rounding instead of the O(K eps) drift of a
+// plain FP32 sum.  The _rn intrinsics keep the compiler from fusing the steps.
+__global__ void __launch_bounds__(256) k_gemm_rows_dot2(const float *__restrict__ X, size_t xw,
+                                                        const float *__restrict__ Y, const float *__restrict__ Ylo,
+                                                        size_t yw, int ma, int nb, int K, double *__restrict__ Out,
+                                                        size_t ow, int ldo) {
+  __shared__ float Xs[16][65];
+  __shared__ float Ys[16][65];
+  __shared__ float Yl[16][65];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int w = blockIdx.z, a0 = blockIdx.y * 16, b0 = blockIdx.x * 16;
+  const float *Xw = X + (size_t)w * xw;
+  const float *Yw = Y + (size_t)w * yw;
+  float s = 0.0f, c = 0.0f;
+  for (int k0 = 0; k0 < K; k0 += 64) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int idx = threadIdx.x + q * 256, row = idx >> 6, col = idx & 63;
+      const int k = k0 + col;
+      const int a = a0 + row, b = b0 + row;
+      Xs[row][col] = (a < ma && k < K) ? Xw[(size_t)a * K + k] : 0.0f;
+      Ys[row][col] = (b < nb && k < K) ? Yw[(size_t)b * K + k] : 0.0f;
+      Yl[row][col] = (Ylo && b < nb && k < K) ? Ylo[(size_t)w * yw + (size_t)b * K + k] : 0.0f;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int k = 0; k < 64; ++k) {
+      const float x = Xs[ty][k], y = Ys[tx][k];
+      const float p = __fmul_rn(x, y);
+      const float pe = __fmaf_rn(x, y, -p);
+      const float t = __fadd_rn(s, p);
+      const float z = __fsub_rn(t, s);
+      const float se = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
+      s = t;
+      c = __fadd_rn(c, __fadd_rn(__fmaf_rn(x, Yl[tx][k], pe), se));
+    }
+    __syncthreads();
+  }
+  // the pair (s, c) carries more than FP32 precision: keep it in FP64
+  if (a0 + ty < ma && b0 + tx < nb)
+    Out[(size_t)w * ow + (size_t)(a0 + ty) * ldo + b0 + tx] = static_cast<double>(s) + static_cast<double>(c);
+}
+
+cudaError_t launch_gemm_rows_dot2(const float *X, size_t xw, const float *Y, const float *Ylo, size_t yw, int ma,
+                                  int nb, int K, double *Out, size_t ow, int ldo, int W, cudaStream_t st) {
   if (W <= 0 || ma <= 0 || nb <= 0) return cudaSuccess;
   dim3 grid((nb + 15) / 16, (ma + 15) / 16, W);
-  k_gemm_rows<<<grid, 256, 0, st>>>(X, xw, Y, yw, ma, nb, K, Out, ow, ldo);
+  k_gemm_rows_dot2<<<grid, 256, 0, st>>>(X, xw, Y, Ylo, yw, ma, nb, K, Out, ow, ldo);
   return cudaGetLastError();
 }
 
-__global__ void k_fill_unpaired(const double *__restrict__ unp, double *__restrict__ bt, int W, int nu, int nd,
+template <typename T>
+cudaError_t launch_gemm_rows(const T *X, size_t xw, const T *Y, size_t yw, int ma, int nb, int K, T *Out, size_t ow,
+                             int ldo, int W, cudaStream_t st) {
+  if (W <= 0 || ma <= 0 || nb <= 0) return cudaSuccess;
+  dim3 grid((nb + 15) / 16, (ma + 15) / 16, W);
+  k_gemm_rows<T><<<grid, 256, 0, st>>>(X, xw, Y, yw, ma, nb, K, Out, ow, ldo);
+  return cudaGetLastError();
+}
+template cudaError_t launch_gemm_rows<double>(const double *, size_t, const double *, size_t, int, int, int, double *,
+                                              size_t, int, int, cudaStream_t);
+template cudaError_t launch_gemm_rows<float>(const float *, size_t, const float *, size_t, int, int, int, float *,
+                                             size_t, int, int, cudaStream_t);
+
+template <typename T>
+__global__ void k_fill_unpaired(const double *__restrict__ unp, T *__restrict__ bt, int W, int nu, int nd,
                                 int L) {
   const int k = nu - nd;
   const long total = (long)W * k * L;
@@ -58,18 +119,44 @@ __global__ void k_fill_unpaired(const double *__restrict__ unp, double *__restri
     const long t = idx / L;
     const int l = (int)(t % k);
     const int w = (int)(t / k);
-    bt[((size_t)w * nu + nd + l) * L + c] = unp[(size_t)l * L + c];
+    bt[((size_t)w * nu + nd + l) * L + c] = static_cast<T>(unp[(size_t)l * L + c]);
   }
 }
 
-cudaError_t launch_fill_unpaired(const DevSystem &s, double *bt, int W, cudaStream_t st) {
+template <typename T>
+cudaError_t launch_fill_unpaired(const DevSystem &s, T *bt, int W, cudaStream_t st) {
   if (W <= 0 || s.n_up == s.n_dn) return cudaSuccess;
   const long total = (long)W * (s.n_up - s.n_dn) * s.L;
   long blocks = (total + 255) / 256;
   if (blocks > 152 * 8) blocks = 152 * 8;
-  k_fill_unpaired<<<(int)blocks, 256, 0, st>>>(s.unpaired, bt, W, s.n_up, s.n_dn, s.L);
+  k_fill_unpaired<T><<<(int)blocks, 256, 0, st>>>(s.unpaired, bt, W, s.n_up, s.n_dn, s.L);
   return cudaGetLastError();
 }
+template cudaError_t launch_fill_unpaired<double>(const DevSystem &, double *, int, cudaStream_t);
+
+__global__ void k_fill_unpaired_lo(const double *__restrict__ unp, float *__restrict__ lo, int W, int nu, int nd,
+                                   int L) {
+  const int k = nu - nd;
+  const long total = (long)W * k * L;
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+    const int c = (int)(idx % L);
+    const long t = idx / L;
+    const int l = (int)(t % k);
+    const int w = (int)(t / k);
+    const double v = unp[(size_t)l * L + c];
+    lo[((size_t)w * nu + nd + l) * L + c] = static_cast<float>(v - static_cast<double>(static_cast<float>(v)));
+  }
+}
+
+cudaError_t launch_fill_unpaired_lo(const DevSystem &s, float *lo, int W, cudaStream_t st) {
+  if (W <= 0 || s.n_up == s.n_dn) return cudaSuccess;
+  const long total = (long)W * (s.n_up - s.n_dn) * s.L;
+  long blocks = (total + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  k_fill_unpaired_lo<<<(int)blocks, 256, 0, st>>>(s.unpaired, lo, W, s.n_up, s.n_dn, s.L);
+  return cudaGetLastError();
+}
+template cudaError_t launch_fill_unpaired<float>(const DevSystem &, float *, int, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // FP64 refresh: Gauss-Jordan elimination with partial pivoting on [G~ | I]
@@ -78,7 +165,8 @@ cudaError_t launch_fill_unpaired(const DevSystem &s, double *bt, int W, cudaStre
 // fresh inverse replaces the Sherman-Morrison one; their largest difference
 // times max|G~| is the walker's drift.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_refresh_inverse(const double *__restrict__ gm, double *__restrict__ ginv,
+template <typename T>
+__global__ void __launch_bounds__(256) k_refresh_inverse(const double *__restrict__ gm, T *__restrict__ ginv,
                                                          double *__restrict__ scal, int *__restrict__ status,
                                                          int n, int check_drift, double drift_tol) {
   extern __shared__ double sm[];
@@ -158,7 +246,7 @@ __global__ void __launch_bounds__(256) k_refresh_inverse(const double *__restric
     }
     __syncthreads();
   }
-  double *gi = ginv + (size_t)w * n * n;
+  T *gi = ginv + (size_t)w * n * n;
   if (!ok) {
     if (tid == 0) {
       status[w] |= JAGP_WS_SINGULAR;
@@ -171,8 +259,8 @@ __global__ void __launch_bounds__(256) k_refresh_inverse(const double *__restric
   for (int idx = tid; idx < n * n; idx += bs) {
     const int i = idx / n, j = idx - i * n;
     const double v = A[i * ld + n + j];
-    if (check_drift) dmax = fmax(dmax, fabs(v - gi[idx]));
-    gi[idx] = v;
+    if (check_drift) dmax = fmax(dmax, fabs(v - static_cast<double>(gi[idx])));
+    gi[idx] = static_cast<T>(v);
   }
   // block max of dmax and gmax
   for (int o = 16; o > 0; o >>= 1) {
@@ -204,8 +292,9 @@ __global__ void __launch_bounds__(256) k_refresh_inverse(const double *__restric
 // columns j and j + 32 of [G~ | I]; pivot search by shuffles, no block barriers.
 constexpr int kRefreshWarps = 4;
 
+template <typename T>
 __global__ void __launch_bounds__(kRefreshWarps * 32) k_refresh_inverse_warp(
-    const double *__restrict__ gm, double *__restrict__ ginv, double *__restrict__ scal, int *__restrict__ status,
+    const double *__restrict__ gm, T *__restrict__ ginv, double *__restrict__ scal, int *__restrict__ status,
     int n, int W, int check_drift, double drift_tol) {
   extern __shared__ double sm[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -278,7 +367,7 @@ __global__ void __launch_bounds__(kRefreshWarps * 32) k_refresh_inverse_warp(
     }
     __syncwarp();
   }
-  double *gi = ginv + (size_t)w * n * n;
+  T *gi = ginv + (size_t)w * n * n;
   double *sw = scal + (size_t)w * S_STRIDE;
   if (!ok) {
     if (lane == 0) {
@@ -292,8 +381,8 @@ __global__ void __launch_bounds__(kRefreshWarps * 32) k_refresh_inverse_warp(
   for (int idx = lane; idx < n * n; idx += 32) {
     const int i = idx / n, j = idx - i * n;
     const double v = A[i * ld + n + j];
-    if (check_drift) dmax = fmax(dmax, fabs(v - gi[idx]));
-    gi[idx] = v;
+    if (check_drift) dmax = fmax(dmax, fabs(v - static_cast<double>(gi[idx])));
+    gi[idx] = static_cast<T>(v);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -311,19 +400,24 @@ __global__ void __launch_bounds__(kRefreshWarps * 32) k_refresh_inverse_warp(
   }
 }
 
-cudaError_t launch_refresh_inverse(const double *gm, double *ginv, double *scal, int *status, int n, int W,
+template <typename T>
+cudaError_t launch_refresh_inverse(const double *gm, T *ginv, double *scal, int *status, int n, int W,
                                    int check_drift, double drift_tol, cudaStream_t st) {
   if (W <= 0) return cudaSuccess;
   if (n <= 32) {
     const size_t smem = (size_t)kRefreshWarps * (n * (2 * n + 1) + n) * sizeof(double);
-    k_refresh_inverse_warp<<<(W + kRefreshWarps - 1) / kRefreshWarps, kRefreshWarps * 32, smem, st>>>(
+    k_refresh_inverse_warp<T><<<(W + kRefreshWarps - 1) / kRefreshWarps, kRefreshWarps * 32, smem, st>>>(
         gm, ginv, scal, status, n, W, check_drift, drift_tol);
     return cudaGetLastError();
   }
   const size_t smem = (size_t)(n * (2 * n + 1) + n) * sizeof(double);
-  k_refresh_inverse<<<W, 256, smem, st>>>(gm, ginv, scal, status, n, check_drift, drift_tol);
+  k_refresh_inverse<T><<<W, 256, smem, st>>>(gm, ginv, scal, status, n, check_drift, drift_tol);
   return cudaGetLastError();
 }
+template cudaError_t launch_refresh_inverse<double>(const double *, double *, double *, int *, int, int, int, double,
+                                                    cudaStream_t);
+template cudaError_t launch_refresh_inverse<float>(const double *, float *, double *, int *, int, int, int, double,
+                                                   cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // Kinetic-energy contraction vectors.  D = det G~ is linear in row i (up
@@ -333,27 +427,29 @@ cudaError_t launch_refresh_inverse(const double *gm, double *ginv, double *scal,
 //   down: M[n_up + j] = sum_i Ginv[j][i] A_up[i]   (A_up[i] = phi(r_i^up)^T lambda)
 // and the same M with the Laplacians.  One CTA per (walker, 64 columns).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_mmat(DevSystem s, const double *__restrict__ ginv,
-                                              const double *__restrict__ bt, const double *__restrict__ a_up,
-                                              double *__restrict__ mbuf) {
-  extern __shared__ double sm[];
+template <typename T>
+__global__ void __launch_bounds__(256) k_mmat(DevSystem s, const T *__restrict__ ginv,
+                                              const T *__restrict__ bt, const T *__restrict__ a_up,
+                                              T *__restrict__ mbuf) {
+  extern __shared__ double smd[];
+  T *sm = reinterpret_cast<T *>(smd);
   const int n = s.n_up, nd = s.n_dn, N = s.N, L = s.L;
   const int w = blockIdx.y, c0 = blockIdx.x * 64, tid = threadIdx.x;
-  double *Gs = sm;              // n*n
-  double *Bs = Gs + n * n;      // n*64
-  double *As = Bs + n * 64;     // n*64
+  T *Gs = sm;              // n*n
+  T *Bs = Gs + n * n;      // n*64
+  T *As = Bs + n * 64;     // n*64
   for (int t = tid; t < n * n; t += 256) Gs[t] = ginv[(size_t)w * n * n + t];
   for (int t = tid; t < n * 64; t += 256) {
     const int j = t >> 6, c = t & 63;
     const bool in = c0 + c < L;
-    Bs[t] = in ? bt[((size_t)w * n + j) * L + c0 + c] : 0.0;
-    As[t] = in ? a_up[((size_t)w * n + j) * L + c0 + c] : 0.0;
+    Bs[t] = in ? bt[((size_t)w * n + j) * L + c0 + c] : T(0);
+    As[t] = in ? a_up[((size_t)w * n + j) * L + c0 + c] : T(0);
   }
   __syncthreads();
   for (int idx = tid; idx < N * 64; idx += 256) {
     const int e = idx >> 6, c = idx & 63;
     if (c0 + c >= L) continue;
-    double acc = 0.0;
+    T acc = T(0);
     if (e < n) {
       for (int j = 0; j < n; ++j) acc = fma(Gs[j * n + e], Bs[j * 64 + c], acc);
     } else {
@@ -365,24 +461,34 @@ __global__ void __launch_bounds__(256) k_mmat(DevSystem s, const double *__restr
   }
 }
 
-cudaError_t launch_mmat(const DevSystem &s, const double *ginv, const double *bt, const double *a_up, double *mbuf,
-                        int W, cudaStream_t st) {
+template <typename T>
+cudaError_t launch_mmat(const DevSystem &s, const T *ginv, const T *bt, const T *a_up, T *mbuf, int W,
+                        cudaStream_t st) {
   if (W <= 0) return cudaSuccess;
   const int n = s.n_up;
-  const size_t smem = (size_t)(n * n + 2 * n * 64) * sizeof(double);
+  const size_t smem = (size_t)(n * n + 2 * n * 64) * sizeof(T);
   dim3 grid((s.L + 63) / 64, W);
-  k_mmat<<<grid, 256, smem, st>>>(s, ginv, bt, a_up, mbuf);
+  k_mmat<T><<<grid, 256, smem, st>>>(s, ginv, bt, a_up, mbuf);
   return cudaGetLastError();
+}
+template cudaError_t launch_mmat<double>(const DevSystem &, const double *, const double *, const double *, double *,
+                                         int, cudaStream_t);
+template cudaError_t launch_mmat<float>(const DevSystem &, const float *, const float *, const float *, float *, int,
+                                        cudaStream_t);
+
+template <typename T>
+static cudaError_t linalg_attrs() {
+  const int big = 200 * 1024;
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_refresh_inverse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+  if ((e = cudaFuncSetAttribute(k_refresh_inverse_warp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)))
+    return e;
+  return cudaFuncSetAttribute(k_mmat<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
 }
 
 cudaError_t setup_kernel_attributes() {
-  const int big = 200 * 1024;
-  cudaError_t e = cudaFuncSetAttribute(k_refresh_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_refresh_inverse_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_mmat, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  return e;
+  cudaError_t e = linalg_attrs<double>();
+  return e != cudaSuccess ? e : linalg_attrs<float>();
 }
 
 }  // namespace jagp

@@ -2,18 +2,27 @@
 // (tcgen05.mma kind::f16, BF16 operands, FP32 accumulator in tensor memory),
 // fed by TMA through a multi-stage mbarrier pipeline.
 //
-// C[m][n] = sum_p sum_k A[m][a_p Kp + k] * B[n][b_p Kp + k]
+// Plain mode:  C[m][n] = sum_p sum_k A[m][a_p Kp + k] * B[n][b_p Kp + k]
+// A holds up to four BF16 "terms" of each row side by side (each Kp wide, Kp a
+// multiple of 64); B likewise.  All pairs accumulate into one FP32 tensor-
+// memory accumulator.
 //
-// A holds up to 3 BF16 "terms" of each row side by side (hi, mid, lo of an
-// FP32 value, each Kp wide, Kp a multiple of 64); B likewise.  Summing the
-// pairs (a_p, b_p) with a_p + b_p <= 2 reproduces an FP32-accurate product of
-// the unsplit operands; one pair (0, 0) is the plain BF16 product.
+// Fixed-point mode (row exponents ea[m], column exponents eb[n] given): the
+// terms are 8-bit integer slices of rows scaled by powers of two,
+//   a = 2^(ea - 7) (t0 + t1 / 256 + t2 / 256^2 + t3 / 256^3),  |t_i| <= 128,
+// (exact in BF16), so every slice product is an integer below 2^14 and the
+// tensor cores sum them exactly while partial sums stay below 2^24.  Pairs of
+// equal weight d = a_p + b_p share an accumulator S_d, and the epilogue forms
+//   C = 2^(ea + eb - 14) (S_0 + S_1 / 256 + S_2 / 256^2 + S_3 / 256^3)
+// with one FP32 rounding per add: FP32-accurate products of FP32 rows, which
+// the lossy FP32 accumulation inside the tensor cores would not give.
 //
 // One CTA computes a 128 x BN tile: warp 0 lane 0 issues the TMA loads, warp 1
 // lane 0 issues the MMAs (one per 16-wide K slice), all four warps drain the
 // accumulator from tensor memory (warp w owns TMEM lanes 32w..32w+31 = rows).
 // Every wait is bounded by the global timer; a timeout sets *err.
 #include <cuda.h>
+#include <cuda_bf16.h>
 
 #include <mutex>
 
@@ -121,10 +130,14 @@ struct UmmaArgs {
   int bn;                // output columns per CTA (multiple of 16, <= 256)
   int stages;
   int npairs;
-  int pair_a[8], pair_b[8];
+  int pair_a[16], pair_b[16], pair_group[16];
+  int ngroups;           // accumulators (1 in plain mode)
+  const int *a_exp;      // fixed-point mode: row exponents [m_max], else null
+  const int *b_exp;      // fixed-point mode: column exponents [n]
   uint32_t idesc;
   uint32_t tmem_cols;    // power of two >= max(32, bn)
   float *out;
+  float *out_lo;         // fixed-point mode: low part of a two-float result, or null
   long long ldo;         // output row pitch (elements)
   const int *out_rows;   // destination row of row m, or null (= m)
   int *err;
@@ -184,6 +197,7 @@ __global__ void __launch_bounds__(128, 1) k_umma_gemm(const __grid_constant__ CU
     }
   } else if (warp == 1 && lane == 0) {
     // MMA issuer: four K = 16 slices per 64-wide chunk, accumulating in TMEM
+    uint32_t started = 0;  // bit g: accumulator g has received its first product
     for (int it = 0; it < iters; ++it) {
       const int s = it % g.stages;
       const uint32_t use = static_cast<uint32_t>(it / g.stages);
@@ -193,10 +207,14 @@ __global__ void __launch_bounds__(128, 1) k_umma_gemm(const __grid_constant__ CU
       }
       tc_fence_after();
       const uint32_t a0 = tiles + s * stage_bytes, b0 = a0 + a_bytes;
+      const int grp = g.pair_group[it / kchunks];
+      const uint32_t d_tmem = tmem + static_cast<uint32_t>(grp * g.bn);
 #pragma unroll
-      for (int kk = 0; kk < 4; ++kk)
-        umma_bf16(tmem, desc_sw128_kmajor(a0 + kk * 32), desc_sw128_kmajor(b0 + kk * 32), g.idesc,
-                  (it > 0 || kk > 0) ? 1u : 0u);
+      for (int kk = 0; kk < 4; ++kk) {
+        umma_bf16(d_tmem, desc_sw128_kmajor(a0 + kk * 32), desc_sw128_kmajor(b0 + kk * 32), g.idesc,
+                  (started >> grp) & 1u);
+        started |= 1u << grp;
+      }
       umma_commit(empty0 + 8u * s);
     }
     umma_commit(done);  // arrives once every MMA issued above has completed
@@ -211,9 +229,48 @@ __global__ void __launch_bounds__(128, 1) k_umma_gemm(const __grid_constant__ CU
     const bool live = row < M;
     const long long dst = live ? (g.out_rows ? g.out_rows[row] : row) : 0;
     const uint32_t t_row = tmem + (static_cast<uint32_t>(warp * 32) << 16);
+    const int ea = (g.a_exp && live) ? g.a_exp[row] : 0;
     for (int c = 0; c < g.bn; c += 16) {
       float v[16];
       tmem_ld16(t_row + static_cast<uint32_t>(c), v);
+      if (g.a_exp) {
+        // v = S_0 + S_1 / 256 + S_2 / 256^2 + S_3 / 256^3 as an unevaluated sum
+        // hi + lo of FP32 numbers: every S_d is an exact integer below 2^24 and
+        // each addition goes through an error-free transformation (TwoSum)
+        float lo[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) lo[j] = 0.0f;
+        float scale = 1.0f;
+        for (int q = 1; q < g.ngroups; ++q) {
+          float u[16];
+          tmem_ld16(t_row + static_cast<uint32_t>(q * g.bn + c), u);
+          scale *= 0.00390625f;
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const float b = __fmul_rn(u[j], scale);  // exact: power-of-two scaling
+            const float s = __fadd_rn(v[j], b);
+            const float z = __fsub_rn(s, v[j]);
+            const float e = __fadd_rn(__fsub_rn(v[j], __fsub_rn(s, z)), __fsub_rn(b, z));
+            v[j] = s;
+            lo[j] = __fadd_rn(lo[j], e);
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const float hi = __fadd_rn(v[j], lo[j]);
+          const float l2 = __fsub_rn(lo[j], __fsub_rn(hi, v[j]));
+          const int col = n0 + c + j;
+          const int sh = ea + (col < g.n ? g.b_exp[col] : 0) - 14;
+          v[j] = ldexpf(hi, sh);
+          lo[j] = ldexpf(l2, sh);
+        }
+        if (live && g.out_lo) {
+          float *ol = g.out_lo + dst * g.ldo + n0 + c;
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (n0 + c + j < g.n) ol[j] = lo[j];
+        }
+      }
       if (live) {
         float *o = g.out + dst * g.ldo + n0 + c;
 #pragma unroll
@@ -265,42 +322,51 @@ bool make_map(CUtensorMap *m, const void *base, uint64_t inner, uint64_t rows, u
 
 }  // namespace
 
-int umma_pick_bn(int n) {
-  if (n <= 256) return ((n + 15) / 16) * 16 < 32 ? 32 : ((n + 15) / 16) * 16;
-  const int tiles = (n + 255) / 256;
+int umma_pick_bn(int n, int max_bn) {
+  if (n <= max_bn) return ((n + 15) / 16) * 16 < 32 ? 32 : ((n + 15) / 16) * 16;
+  const int tiles = (n + max_bn - 1) / max_bn;
   return (((n + tiles - 1) / tiles) + 15) / 16 * 16;
 }
 
 cudaError_t launch_umma_gemm(const uint16_t *A, int m_max, const int *m_dev, int a_terms, const uint16_t *B, int n,
                              int b_terms, int kp, int npairs, const int *pair_a, const int *pair_b, float *out,
-                             long long ldo, const int *out_rows, int *err, cudaStream_t st) {
+                             long long ldo, const int *out_rows, int *err, cudaStream_t st, const int *a_exp,
+                             const int *b_exp, float *out_lo) {
   if (m_max <= 0 || n <= 0) return cudaSuccess;
-  if (kp <= 0 || kp % 64 != 0 || npairs < 1 || npairs > 8 || a_terms < 1 || b_terms < 1) return cudaErrorInvalidValue;
+  if (kp <= 0 || kp % 64 != 0 || npairs < 1 || npairs > 16 || a_terms < 1 || b_terms < 1) return cudaErrorInvalidValue;
   if ((reinterpret_cast<uintptr_t>(A) & 15u) || (reinterpret_cast<uintptr_t>(B) & 15u)) return cudaErrorInvalidValue;
-  for (int p = 0; p < npairs; ++p)
-    if (pair_a[p] < 0 || pair_a[p] >= a_terms || pair_b[p] < 0 || pair_b[p] >= b_terms) return cudaErrorInvalidValue;
+  if ((a_exp == nullptr) != (b_exp == nullptr)) return cudaErrorInvalidValue;
   UmmaArgs g{};
+  g.ngroups = 1;
+  for (int p = 0; p < npairs; ++p) {
+    if (pair_a[p] < 0 || pair_a[p] >= a_terms || pair_b[p] < 0 || pair_b[p] >= b_terms) return cudaErrorInvalidValue;
+    g.pair_a[p] = pair_a[p];
+    g.pair_b[p] = pair_b[p];
+    g.pair_group[p] = a_exp ? pair_a[p] + pair_b[p] : 0;
+    if (g.pair_group[p] + 1 > g.ngroups) g.ngroups = g.pair_group[p] + 1;
+  }
+  if (g.ngroups > 4) return cudaErrorInvalidValue;
+  g.a_exp = a_exp;
+  g.b_exp = b_exp;
   g.m_max = m_max;
   g.m_dev = m_dev;
   g.n = n;
   g.kp = kp;
-  g.bn = umma_pick_bn(n);
+  g.bn = umma_pick_bn(n, g.ngroups == 1 ? 256 : (g.ngroups == 2 ? 256 : 128));
   const uint32_t stage_bytes = 128u * 128u + static_cast<uint32_t>(g.bn) * 128u;
   g.stages = static_cast<int>((200u * 1024u) / stage_bytes);
   if (g.stages > 6) g.stages = 6;
   g.npairs = npairs;
-  for (int p = 0; p < npairs; ++p) {
-    g.pair_a[p] = pair_a[p];
-    g.pair_b[p] = pair_b[p];
-  }
   g.idesc = (1u << 4)                                   // D: FP32
             | (1u << 7) | (1u << 10)                    // A, B: BF16
             | (static_cast<uint32_t>(g.bn >> 3) << 17)  // N
             | (static_cast<uint32_t>(128 >> 4) << 24);  // M
   uint32_t cols = 32;
-  while (cols < static_cast<uint32_t>(g.bn)) cols <<= 1;
+  while (cols < static_cast<uint32_t>(g.bn * g.ngroups)) cols <<= 1;
+  if (cols > 512) return cudaErrorInvalidValue;
   g.tmem_cols = cols;
   g.out = out;
+  g.out_lo = a_exp ? out_lo : nullptr;
   g.ldo = ldo;
   g.out_rows = out_rows;
   g.err = err;
@@ -311,6 +377,96 @@ cudaError_t launch_umma_gemm(const uint16_t *A, int m_max, const int *m_dev, int
   const size_t smem = 1024 + static_cast<size_t>(g.stages) * stage_bytes + 8 * (2 * g.stages + 1) + 16;
   dim3 grid((n + g.bn - 1) / g.bn, (m_max + 127) / 128);
   k_umma_gemm<<<grid, 128, smem, st>>>(ta, tb, g);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Operand packing: FP32 orbital rows -> three BF16 terms (hi, mid, lo) side by
+// side, zero-padded to kp each, compacted in list order.  Row m of the output
+// comes from table row list[m] (m < *count) or, without a list, from
+// (m / nsub) * stride + m % nsub (m < nrows); rows_out[m] records it so the
+// contraction can write its result row back in place.  One warp per row.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_pack_split3(const float *__restrict__ P, const int *__restrict__ list,
+                                                     const int *__restrict__ count, int nrows, int nsub, int stride,
+                                                     int L, int kp, __nv_bfloat16 *__restrict__ A,
+                                                     int *__restrict__ rows_out) {
+  const int rows = count ? *count : nrows;
+  const int lane = threadIdx.x & 31;
+  const long nw = (long)gridDim.x * (blockDim.x >> 5);
+  for (long m = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); m < rows; m += nw) {
+    const long phys = list ? (long)list[m] : (m / nsub) * stride + (m % nsub);
+    if (lane == 0) rows_out[m] = (int)phys;
+    const float *src = P + phys * L;
+    __nv_bfloat16 *dst = A + m * 3 * (long)kp;
+    for (int k = lane; k < kp; k += 32) {
+      const float v = k < L ? src[k] : 0.0f;
+      const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+      const float r1 = v - __bfloat162float(hi);
+      const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
+      const float r2 = r1 - __bfloat162float(mid);
+      dst[k] = hi;
+      dst[kp + k] = mid;
+      dst[2 * kp + k] = __float2bfloat16_rn(r2);
+    }
+  }
+}
+
+cudaError_t launch_pack_split3(const float *P, const int *list, const int *count, int nrows, int nsub, int stride,
+                               int L, int kp, uint16_t *A, int *rows_out, int max_rows, cudaStream_t st) {
+  if (max_rows <= 0) return cudaSuccess;
+  long blocks = (max_rows + 7) / 8;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  k_pack_split3<<<(int)blocks, 256, 0, st>>>(P, list, count, nrows, nsub > 0 ? nsub : 1, stride, L, kp,
+                                              reinterpret_cast<__nv_bfloat16 *>(A), rows_out);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Fixed-point operand packing: each FP32 row (compacted as above) is scaled by
+// 2^-e (e = 1 + the binary exponent of its largest magnitude) and cut into four
+// exact 8-bit integer slices t0..t3 (|t| <= 128), stored as BF16 side by side,
+// with e in exps[m].  Every step of the cut is exact in FP32.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_pack_fixed4(const float *__restrict__ P, const int *__restrict__ list,
+                                                     const int *__restrict__ count, int nrows, int nsub, int stride,
+                                                     int L, int kp, __nv_bfloat16 *__restrict__ A,
+                                                     int *__restrict__ rows_out, int *__restrict__ exps) {
+  const int rows = count ? *count : nrows;
+  const int lane = threadIdx.x & 31;
+  const long nw = (long)gridDim.x * (blockDim.x >> 5);
+  for (long m = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); m < rows; m += nw) {
+    const long phys = list ? (long)list[m] : (m / nsub) * stride + (m % nsub);
+    const float *src = P + phys * L;
+    float mx = 0.0f;
+    for (int k = lane; k < L; k += 32) mx = fmaxf(mx, fabsf(src[k]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    const int e = (mx > 0.0f) ? ilogbf(mx) + 1 : 0;
+    if (lane == 0) {
+      rows_out[m] = (int)phys;
+      exps[m] = e;
+    }
+    __nv_bfloat16 *dst = A + m * 4 * (long)kp;
+    for (int k = lane; k < kp; k += 32) {
+      float x = k < L ? ldexpf(src[k], 7 - e) : 0.0f;  // |x| < 128
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const float q = rintf(x);
+        dst[t * kp + k] = __float2bfloat16_rn(q);
+        x = (x - q) * 256.0f;
+      }
+    }
+  }
+}
+
+cudaError_t launch_pack_fixed4(const float *P, const int *list, const int *count, int nrows, int nsub, int stride,
+                               int L, int kp, uint16_t *A, int *rows_out, int *exps, int max_rows, cudaStream_t st) {
+  if (max_rows <= 0) return cudaSuccess;
+  long blocks = (max_rows + 7) / 8;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  k_pack_fixed4<<<(int)blocks, 256, 0, st>>>(P, list, count, nrows, nsub > 0 ? nsub : 1, stride, L, kp,
+                                              reinterpret_cast<__nv_bfloat16 *>(A), rows_out, exps);
   return cudaGetLastError();
 }
 

@@ -13,9 +13,9 @@ namespace jagp {
 // shared memory once per CTA; CTAs then grid-stride over points.
 // (Sec. "Atomic basis set", Eqs. gaussian, slater.)
 // ---------------------------------------------------------------------------
-template <bool PROPOSE>
+template <bool PROPOSE, typename T>
 __global__ void __launch_bounds__(256) k_basis_points(DevSystem s, const double *__restrict__ r, int W,
-                                                      int e0, int npts, double *__restrict__ out,
+                                                      int e0, int npts, T *__restrict__ out,
                                                       double *__restrict__ rprop, uint32_t walker0,
                                                       uint32_t sweep) {
   extern __shared__ double4 sh_geo[];
@@ -55,12 +55,12 @@ __global__ void __launch_bounds__(256) k_basis_points(DevSystem s, const double 
       if (lane < 4) rec[lane] = lane < 3 ? rp[lane] : u;
       if (lane == 0) rec[4] = dj1;
     }
-    double *o = out + ((size_t)w * s.n_up + i) * s.L;
+    T *o = out + ((size_t)w * s.n_up + i) * s.L;
     for (int k = lane; k < s.n_shells; k += 32) {
       const double4 g = sh_geo[k];
       const int info = sh_info[k];
-      double v[5];
-      const int nc = shell_values<double>(info, g.w, p[0] - g.x, p[1] - g.y, p[2] - g.z, v);
+      T v[5];
+      const int nc = shell_values<T>(info, g.w, p[0] - g.x, p[1] - g.y, p[2] - g.z, v);
       const int off = shell_off(info);
 #pragma unroll
       for (int c = 0; c < 5; ++c)
@@ -69,8 +69,9 @@ __global__ void __launch_bounds__(256) k_basis_points(DevSystem s, const double 
   }
 }
 
+template <typename T>
 cudaError_t launch_basis_points(const DevSystem &s, bool propose, const double *r, int W, int e0, int npts,
-                                double *out, double *rprop, uint32_t walker0, uint32_t sweep,
+                                T *out, double *rprop, uint32_t walker0, uint32_t sweep,
                                 cudaStream_t st) {
   if (W <= 0 || npts <= 0) return cudaSuccess;
   const long total = (long)W * npts;
@@ -79,11 +80,15 @@ cudaError_t launch_basis_points(const DevSystem &s, bool propose, const double *
   if (blocks > 152 * 16) blocks = 152 * 16;
   const size_t smem = (size_t)s.n_shells * (sizeof(double4) + sizeof(int));
   if (propose)
-    k_basis_points<true><<<(int)blocks, warps * 32, smem, st>>>(s, r, W, e0, npts, out, rprop, walker0, sweep);
+    k_basis_points<true, T><<<(int)blocks, warps * 32, smem, st>>>(s, r, W, e0, npts, out, rprop, walker0, sweep);
   else
-    k_basis_points<false><<<(int)blocks, warps * 32, smem, st>>>(s, r, W, e0, npts, out, rprop, walker0, sweep);
+    k_basis_points<false, T><<<(int)blocks, warps * 32, smem, st>>>(s, r, W, e0, npts, out, rprop, walker0, sweep);
   return cudaGetLastError();
 }
+template cudaError_t launch_basis_points<double>(const DevSystem &, bool, const double *, int, int, int, double *,
+                                                 double *, uint32_t, uint32_t, cudaStream_t);
+template cudaError_t launch_basis_points<float>(const DevSystem &, bool, const double *, int, int, int, float *,
+                                                double *, uint32_t, uint32_t, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // Block reduction of two doubles (blockDim.x <= 1024); result valid in thread 0.
@@ -117,27 +122,27 @@ __device__ __forceinline__ void block_sum2(double &a, double &b, double *red) {
 // Jastrow factor contributes exp(2 dJ), dJ summed over the atoms (J1) and the
 // other electrons at their current positions (J2).  Accept iff u < R^2 e^{2 dJ}.
 // ---------------------------------------------------------------------------
-template <bool UP>
+template <bool UP, typename T>
 __global__ void __launch_bounds__(128) k_metropolis(DevSystem s, double *__restrict__ r,
                                                     const double *__restrict__ rprop,
-                                                    const double *__restrict__ gprop,
-                                                    double *__restrict__ ginv, double *__restrict__ scal,
+                                                    const T *__restrict__ gprop,
+                                                    T *__restrict__ ginv, double *__restrict__ scal,
                                                     int *__restrict__ status,
-                                                    const double *__restrict__ pprop,
-                                                    double *__restrict__ phi_up, int *__restrict__ list,
+                                                    const T *__restrict__ pprop,
+                                                    T *__restrict__ phi_up, int *__restrict__ list,
                                                     int *__restrict__ count) {
   extern __shared__ double sm[];
   const int n = s.n_up, N = s.N, tid = threadIdx.x, bs = blockDim.x;
   const int w = blockIdx.x;
-  double *Gi = sm;            // n * n
-  double *xs = Gi + n * n;    // N * 3
-  double *gp = xs + N * 3;    // n
-  double *vv = gp + n;        // n
-  double *cc = vv + n;        // n
+  double *xs = sm;                                  // N * 3 positions (FP64)
+  T *Gi = reinterpret_cast<T *>(xs + N * 3);        // n * n
+  T *gp = Gi + n * n;                               // n
+  T *vv = gp + n;                                   // n
+  T *cc = vv + n;                                   // n
   __shared__ double red[64];
   __shared__ int s_acc;
   __shared__ double s_R;
-  double *gw = ginv + (size_t)w * n * n;
+  T *gw = ginv + (size_t)w * n * n;
   for (int t = tid; t < n * n; t += bs) Gi[t] = gw[t];
   for (int t = tid; t < N * 3; t += bs) xs[t] = r[(size_t)w * N * 3 + t];
   double logdet = 0.0, sgn = 1.0, J = 0.0, nacc = 0.0;
@@ -158,8 +163,10 @@ __global__ void __launch_bounds__(128) k_metropolis(DevSystem s, double *__restr
     const double px = rp4[0], py = rp4[1], pz = rp4[2];
     for (int t = tid; t < n; t += bs) gp[t] = gprop[((size_t)w * n + m) * n + t];
     __syncthreads();
-    double pr = 0.0, pj = 0.0;
-    for (int t = tid; t < n; t += bs) pr += UP ? gp[t] * Gi[t * n + m] : Gi[m * n + t] * gp[t];
+    T prt = T(0);
+    double pj = 0.0;
+    for (int t = tid; t < n; t += bs) prt += UP ? gp[t] * Gi[t * n + m] : Gi[m * n + t] * gp[t];
+    double pr = static_cast<double>(prt);
     const double ox = xs[3 * e], oy = xs[3 * e + 1], oz = xs[3 * e + 2];
     if (tid == 0) pj = rp4[4];   // one-body Jastrow change, from the proposal kernel
     if (s.use_j2) {
@@ -195,7 +202,7 @@ __global__ void __launch_bounds__(128) k_metropolis(DevSystem s, double *__restr
     __syncthreads();
     if (s_acc) {
       for (int t = tid; t < n; t += bs) {
-        double a = 0.0;
+        T a = T(0);
         if (UP) {
           for (int j = 0; j < n; ++j) a += gp[j] * Gi[j * n + t];
           cc[t] = Gi[t * n + m];
@@ -206,13 +213,13 @@ __global__ void __launch_bounds__(128) k_metropolis(DevSystem s, double *__restr
         vv[t] = a;
       }
       __syncthreads();
-      const double invR = 1.0 / s_R;
+      const T invR = T(1) / static_cast<T>(s_R);
       for (int idx = tid; idx < n * n; idx += bs) {
         const int j = idx / n, k = idx - j * n;
         if (UP)
-          Gi[idx] -= cc[j] * (vv[k] - (k == m ? 1.0 : 0.0)) * invR;
+          Gi[idx] -= cc[j] * (vv[k] - (k == m ? T(1) : T(0))) * invR;
         else
-          Gi[idx] -= (vv[j] - (j == m ? 1.0 : 0.0)) * cc[k] * invR;
+          Gi[idx] -= (vv[j] - (j == m ? T(1) : T(0))) * cc[k] * invR;
       }
       if (tid == 0) {
         xs[3 * e] = px;
@@ -220,8 +227,8 @@ __global__ void __launch_bounds__(128) k_metropolis(DevSystem s, double *__restr
         xs[3 * e + 2] = pz;
       }
       if (UP) {
-        const double *src = pprop + ((size_t)w * n + m) * s.L;
-        double *dst = phi_up + ((size_t)w * n + m) * s.L;
+        const T *src = pprop + ((size_t)w * n + m) * s.L;
+        T *dst = phi_up + ((size_t)w * n + m) * s.L;
         for (int t = tid; t < s.L; t += bs) dst[t] = src[t];
       }
     }
@@ -245,23 +252,27 @@ __global__ void __launch_bounds__(128) k_metropolis(DevSystem s, double *__restr
 // ---------------------------------------------------------------------------
 constexpr int kMetroWarps = 4;
 
-template <bool UP>
+template <typename T>
+__host__ __device__ inline size_t metro_smem_per_walker(int n, int N) {
+  return ((size_t)N * 3 * sizeof(double) + (size_t)(n * n + 3 * n) * sizeof(T) + 15) & ~size_t(15);
+}
+
+template <bool UP, typename T>
 __global__ void __launch_bounds__(kMetroWarps * 32) k_metropolis_warp(
-    DevSystem s, double *__restrict__ r, const double *__restrict__ rprop, const double *__restrict__ gprop,
-    double *__restrict__ ginv, double *__restrict__ scal, int *__restrict__ status,
-    const double *__restrict__ pprop, double *__restrict__ phi_up, int *__restrict__ list,
+    DevSystem s, double *__restrict__ r, const double *__restrict__ rprop, const T *__restrict__ gprop,
+    T *__restrict__ ginv, double *__restrict__ scal, int *__restrict__ status,
+    const T *__restrict__ pprop, T *__restrict__ phi_up, int *__restrict__ list,
     int *__restrict__ count, int W) {
   extern __shared__ double sm[];
   const int n = s.n_up, N = s.N, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int w = blockIdx.x * kMetroWarps + warp;
   if (w >= W) return;  // warp-uniform; the kernel has no block-wide barrier
-  const int per = n * n + N * 3 + 3 * n;
-  double *Gi = sm + (size_t)warp * per;
-  double *xs = Gi + n * n;
-  double *gp = xs + N * 3;
-  double *vv = gp + n;
-  double *cc = vv + n;
-  double *gw = ginv + (size_t)w * n * n;
+  double *xs = reinterpret_cast<double *>(reinterpret_cast<char *>(sm) + warp * metro_smem_per_walker<T>(n, N));
+  T *Gi = reinterpret_cast<T *>(xs + N * 3);
+  T *gp = Gi + n * n;
+  T *vv = gp + n;
+  T *cc = vv + n;
+  T *gw = ginv + (size_t)w * n * n;
   for (int t = lane; t < n * n; t += 32) Gi[t] = gw[t];
   for (int t = lane; t < N * 3; t += 32) xs[t] = r[(size_t)w * N * 3 + t];
   double *sw = scal + (size_t)w * S_STRIDE;
@@ -274,13 +285,15 @@ __global__ void __launch_bounds__(kMetroWarps * 32) k_metropolis_warp(
     const int e = e0 + m;
     const double *rec = rprop + ((size_t)w * n + m) * kPropStride;
     const double px = rec[0], py = rec[1], pz = rec[2];
-    const double *grow = gprop + ((size_t)w * n + m) * n;
-    double pr = 0.0, pj = 0.0;
+    const T *grow = gprop + ((size_t)w * n + m) * n;
+    T prt = T(0);
+    double pj = 0.0;
     for (int t = lane; t < n; t += 32) {
-      const double g = grow[t];
+      const T g = grow[t];
       gp[t] = g;
-      pr += UP ? g * Gi[t * n + m] : Gi[m * n + t] * g;
+      prt += UP ? g * Gi[t * n + m] : Gi[m * n + t] * g;
     }
+    double pr = static_cast<double>(prt);
     if (lane == 0) pj = rec[4];
     if (s.use_j2) {
       const double ox = xs[3 * e], oy = xs[3 * e + 1], oz = xs[3 * e + 2];
@@ -311,7 +324,7 @@ __global__ void __launch_bounds__(kMetroWarps * 32) k_metropolis_warp(
       nacc += 1.0;
       if (lane == 0) list[atomicAdd(count, 1)] = w * n + m;
       for (int t = lane; t < n; t += 32) {
-        double a = 0.0;
+        T a = T(0);
         if (UP) {
           for (int j = 0; j < n; ++j) a = fma(gp[j], Gi[j * n + t], a);
           cc[t] = Gi[t * n + m];
@@ -322,18 +335,18 @@ __global__ void __launch_bounds__(kMetroWarps * 32) k_metropolis_warp(
         vv[t] = a;
       }
       __syncwarp();
-      const double invR = 1.0 / pr;
+      const T invR = T(1) / static_cast<T>(pr);
       for (int idx = lane; idx < n * n; idx += 32) {
         const int j = idx / n, k = idx - j * n;
         if (UP)
-          Gi[idx] -= cc[j] * (vv[k] - (k == m ? 1.0 : 0.0)) * invR;
+          Gi[idx] -= cc[j] * (vv[k] - (k == m ? T(1) : T(0))) * invR;
         else
-          Gi[idx] -= (vv[j] - (j == m ? 1.0 : 0.0)) * cc[k] * invR;
+          Gi[idx] -= (vv[j] - (j == m ? T(1) : T(0))) * cc[k] * invR;
       }
       if (lane < 3) xs[3 * e + lane] = lane == 0 ? px : (lane == 1 ? py : pz);
       if (UP) {
-        const double *src = pprop + ((size_t)w * n + m) * s.L;
-        double *dst = phi_up + ((size_t)w * n + m) * s.L;
+        const T *src = pprop + ((size_t)w * n + m) * s.L;
+        T *dst = phi_up + ((size_t)w * n + m) * s.L;
         for (int t = lane; t < s.L; t += 32) dst[t] = src[t];
       }
       __syncwarp();
@@ -350,29 +363,35 @@ __global__ void __launch_bounds__(kMetroWarps * 32) k_metropolis_warp(
   }
 }
 
-cudaError_t launch_metropolis(const DevSystem &s, bool up, double *r, const double *rprop,
-                              const double *gprop, double *ginv, double *scal, int *status,
-                              const double *pprop, double *phi_up, int *list, int *count, int W,
+template <typename T>
+cudaError_t launch_metropolis(const DevSystem &s, bool up, double *r, const double *rprop, const T *gprop, T *ginv,
+                              double *scal, int *status, const T *pprop, T *phi_up, int *list, int *count, int W,
                               cudaStream_t st) {
   if (W <= 0 || (!up && s.n_dn == 0)) return cudaSuccess;
   const int n = s.n_up;
-  const size_t smem = (size_t)(n * n + s.N * 3 + 3 * n) * sizeof(double);
+  const size_t per = metro_smem_per_walker<T>(n, s.N);
   if (n <= 32) {
     const int blocks = (W + kMetroWarps - 1) / kMetroWarps;
     if (up)
-      k_metropolis_warp<true><<<blocks, kMetroWarps * 32, smem * kMetroWarps, st>>>(
+      k_metropolis_warp<true, T><<<blocks, kMetroWarps * 32, per * kMetroWarps, st>>>(
           s, r, rprop, gprop, ginv, scal, status, pprop, phi_up, list, count, W);
     else
-      k_metropolis_warp<false><<<blocks, kMetroWarps * 32, smem * kMetroWarps, st>>>(
+      k_metropolis_warp<false, T><<<blocks, kMetroWarps * 32, per * kMetroWarps, st>>>(
           s, r, rprop, gprop, ginv, scal, status, pprop, phi_up, list, count, W);
     return cudaGetLastError();
   }
   if (up)
-    k_metropolis<true><<<W, 128, smem, st>>>(s, r, rprop, gprop, ginv, scal, status, pprop, phi_up, list, count);
+    k_metropolis<true, T><<<W, 128, per, st>>>(s, r, rprop, gprop, ginv, scal, status, pprop, phi_up, list, count);
   else
-    k_metropolis<false><<<W, 128, smem, st>>>(s, r, rprop, gprop, ginv, scal, status, pprop, phi_up, list, count);
+    k_metropolis<false, T><<<W, 128, per, st>>>(s, r, rprop, gprop, ginv, scal, status, pprop, phi_up, list, count);
   return cudaGetLastError();
 }
+template cudaError_t launch_metropolis<double>(const DevSystem &, bool, double *, const double *, const double *,
+                                               double *, double *, int *, const double *, double *, int *, int *,
+                                               int, cudaStream_t);
+template cudaError_t launch_metropolis<float>(const DevSystem &, bool, double *, const double *, const float *,
+                                              float *, double *, int *, const float *, float *, int *, int *, int,
+                                              cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // J = J1 + J2 of each walker from scratch (one CTA per walker).
@@ -501,17 +520,21 @@ cudaError_t launch_reduce_acc(const double *eL, const double *scal, const int *c
 }  // namespace jagp
 
 namespace jagp {
+template <typename T>
+static cudaError_t walker_attrs() {
+  const int big = 200 * 1024;
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_basis_points<true, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+  if ((e = cudaFuncSetAttribute(k_basis_points<false, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+  if ((e = cudaFuncSetAttribute(k_metropolis<true, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+  if ((e = cudaFuncSetAttribute(k_metropolis<false, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+  if ((e = cudaFuncSetAttribute(k_metropolis_warp<true, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)))
+    return e;
+  return cudaFuncSetAttribute(k_metropolis_warp<false, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+}
+
 cudaError_t setup_walker_attributes() {
-  cudaError_t e = cudaFuncSetAttribute(k_basis_points<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_basis_points<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_metropolis<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_metropolis_warp<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_metropolis_warp<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_metropolis<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaError_t e = walker_attrs<double>();
+  return e != cudaSuccess ? e : walker_attrs<float>();
 }
 }  // namespace jagp
