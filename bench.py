@@ -37,6 +37,8 @@ WORKLOAD = ("plain FP64 VMC: 16 He atoms in a 10 bohr cube (min separation 1.5),
             "20 s/p/d Gaussians/atom (L=320), dense random symmetric lambda, J1 + J2, 4096 walkers/GPU")
 # FP64 CUDA-core peak of one GB300 (no measured value available): 1.25 TFLOP/s nominal
 FP64_PEAK_TFLOPS = 1.25
+# BF16 dense tensor-core peak, sustained (the machine's fallback figure; no measured file)
+BF16_SUSTAINED_TFLOPS = 1700.0
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "k_lambda_rows_C2_traffic.txt")
 
 
@@ -114,23 +116,29 @@ class ClockSampler:
 # CPU oracle (test infrastructure) timed on the host cores
 # ----------------------------------------------------------------------------
 def oracle_rate(sysm, target_s: float = 15.0, max_walkers: int = 4096):
-    """Oracle VMC sweep + local energy on a bounded walker sample; returns
-    (moves/s, e_L/s, cores, sample description, seconds)."""
+    """Oracle VMC sweeps + local energies on a bounded sample of the same
+    workload (up to all of its walkers, then more sweeps) sized to roughly
+    target_s seconds; returns (moves/s, e_L/s, cores, sample description, seconds)."""
     import oracle
     import synth
     o = oracle.Oracle(sysm)
     cores = oracle.max_threads()
-    Ws = max(cores, 8)
+    Ws, sweeps = max(cores, 8), 1
     while True:
         x = synth.init_walkers(sysm, Ws, seed=0)
         t0 = time.perf_counter()
-        o.vmc(x, 1, seed=0, sweep0=0, walker0=0, record_eL=True, nthreads=cores)
+        o.vmc(x, sweeps, seed=0, sweep0=0, walker0=0, record_eL=True, nthreads=cores)
         dt = time.perf_counter() - t0
-        if dt >= target_s * 0.5 or Ws >= max_walkers:
+        if dt >= target_s * 0.5:
             break
-        Ws = min(max_walkers, int(Ws * min(8.0, max(2.0, target_s / max(dt, 1e-3)))))
-    moves = Ws * sysm.N
-    return moves / dt, Ws / dt, cores, f"{Ws} walkers x 1 sweep (+ e_L per walker) of the same system", dt
+        grow = min(8.0, max(2.0, target_s / max(dt, 1e-3)))
+        if Ws < max_walkers:
+            Ws = min(max_walkers, int(Ws * grow))
+        else:
+            sweeps = int(sweeps * grow) + 1
+    moves = Ws * sweeps * sysm.N
+    return (moves / dt, Ws * sweeps / dt, cores,
+            f"{Ws} walkers x {sweeps} sweep(s) (+ e_L per walker and sweep) of the same system", dt)
 
 
 def cpu_model():
@@ -201,6 +209,50 @@ def profiled_traffic(src_hash):
     return d.get("dram_bytes_per_accepted_row"), d
 
 
+def timed_sweeps(pg, torch, dist, sysm, W, walker0, x0, prec, steps, warmup, ws, dev, local, profile_kernel):
+    """Warm up, then time `steps` sweeps (+ local energies) with CUDA events on the
+    launching stream; the profiled kernel class is bracketed by event pairs."""
+    g = pg.JAGP(sysm, W, seed=0, precision=prec)
+    h = g.h
+    r = g.positions(x0)
+    stream = torch.cuda.current_stream()
+    eL = torch.empty((1, W), dtype=torch.float64, device=dev)
+    acc_steps = torch.empty((steps, 4), dtype=torch.float64, device=dev)
+    acc_tmp = torch.empty((1, 4), dtype=torch.float64, device=dev)
+    pg.jagp_eval(h, r, W, g.state)
+    for k in range(warmup):
+        pg.vmc_sweep(h, r, g.state, W, 1, walker0, k, eL, acc_tmp)
+    torch.cuda.synchronize()
+    bits = g.status()
+    pg.jagp_profile(h, profile_kernel, True)
+    pg.jagp_profile_read(h)  # clear
+    n0 = pg.jagp_launch_count(h)
+    e_start, e_stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e_start.record(stream)
+        for k in range(steps):
+            pg.vmc_sweep(h, r, g.state, W, 1, walker0, warmup + k, eL, acc_steps[k:k + 1])
+        e_stop.record(stream)
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+    launches = pg.jagp_launch_count(h) - n0
+    prof_ms, prof_n = pg.jagp_profile_read(h)
+    pg.jagp_profile(h, profile_kernel, False)
+    ms = e_start.elapsed_time(e_stop)
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    acc = acc_steps.cpu().numpy()
+    bits |= g.status()
+    return {"g": g, "r": r, "eL": eL, "ms": ms, "ms_max": float(t.item()), "launches": launches,
+            "prof_ms": prof_ms, "prof_n": prof_n, "accepted": float(acc[:, 2].sum()), "bits": bits,
+            "clocks": clk.summary()}
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -223,46 +275,13 @@ def run_gpu(args):
     x_all = synth.init_walkers(sysm, W * ws, seed=0)
     x0 = np.ascontiguousarray(x_all[rank * W:(rank + 1) * W])
     walker0 = rank * W
+    mixed_primary = args.precision == "mixed"
+    prec = pg.JAGP_PREC_MIXED if mixed_primary else pg.JAGP_PREC_FP64
 
-    g = pg.JAGP(sysm, W, seed=0)
+    run = timed_sweeps(pg, torch, dist, sysm, W, walker0, x0, prec, args.steps, args.warmup, ws, dev, local,
+                       pg.KERNEL_LAMBDA_ROWS)
+    g, r, eL = run["g"], run["r"], run["eL"]
     h = g.h
-    r = g.positions(x0)
-    stream = torch.cuda.current_stream()
-    eL = torch.empty((1, W), dtype=torch.float64, device=dev)
-    acc_steps = torch.empty((args.steps, 4), dtype=torch.float64, device=dev)
-    acc_tmp = torch.empty((1, 4), dtype=torch.float64, device=dev)
-    pg.jagp_eval(h, r, W, g.state)
-    for k in range(args.warmup):
-        pg.vmc_sweep(h, r, g.state, W, 1, walker0, k, eL, acc_tmp)
-    torch.cuda.synchronize()
-    bits = g.status()
-
-    pg.jagp_profile(h, pg.KERNEL_LAMBDA_ROWS, True)
-    pg.jagp_profile_read(h)  # clear
-    n0 = pg.jagp_launch_count(h)
-    e_start, e_stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
-        if ws > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
-        e_start.record(stream)
-        for k in range(args.steps):
-            pg.vmc_sweep(h, r, g.state, W, 1, walker0, args.warmup + k, eL, acc_steps[k:k + 1])
-        e_stop.record(stream)
-        torch.cuda.synchronize()
-        if ws > 1:
-            dist.barrier()
-    launches = pg.jagp_launch_count(h) - n0
-    lam_ms, lam_n = pg.jagp_profile_read(h)
-    pg.jagp_profile(h, pg.KERNEL_LAMBDA_ROWS, False)
-    ms = e_start.elapsed_time(e_stop)
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if ws > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    acc = acc_steps.cpu().numpy()
-    accepted = float(acc[:, 2].sum())
-    bits |= g.status()
 
     # end to end through the public API with host buffers: pinned host positions
     # in, e_L and positions out, every step (state rebuilt by jagp_eval)
@@ -284,6 +303,15 @@ def run_gpu(args):
     if ws > 1:
         dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
     e2e_value = W * N * e2e_steps * ws / float(e2e_t.item())
+    g.close()
+
+    # the other precision on the same workload, beside the primary
+    other = None
+    if not args.no_other:
+        oprec = pg.JAGP_PREC_FP64 if mixed_primary else pg.JAGP_PREC_MIXED
+        other = timed_sweeps(pg, torch, dist, sysm, W, walker0, x0, oprec, args.steps, args.warmup, ws, dev, local,
+                             pg.KERNEL_LAMBDA_ROWS)
+        other["g"].close()
 
     if rank != 0:
         if ws > 1:
@@ -291,35 +319,59 @@ def run_gpu(args):
             dist.destroy_process_group()
         return 0
 
-    moves = W * N * args.steps * ws
-    value = moves / (ms_max / 1e3)
-    # dominant kernel: lambda products of accepted rows, 2 L^2 flops per row
-    flops = 2.0 * L * L * accepted
-    achieved = flops / (lam_ms / 1e3) / 1e12 if lam_ms > 0 else None
-    src_hash = kernel_source_hash()
-    traffic_per_row, _ = profiled_traffic(src_hash)
-    rows_per_launch = accepted / max(lam_n, 1)
-    traffic = traffic_per_row * rows_per_launch if traffic_per_row else None
+    def summary(rr, mixed):
+        moves = W * N * args.steps * ws
+        value = moves / (rr["ms_max"] / 1e3)
+        flops = 2.0 * L * L * rr["accepted"]  # lambda products: 2 L^2 flops per accepted row
+        secs = rr["prof_ms"] / 1e3
+        achieved = flops / secs / 1e12 if secs > 0 else None
+        d = {"value": value, "ms_per_step": rr["ms_max"] / args.steps,
+             "el_per_s": W * args.steps * ws / (rr["ms_max"] / 1e3),
+             "acceptance": rr["accepted"] / (W * N * args.steps), "status_bits": rr["bits"],
+             "gpu_launches": rr["launches"], "clocks": rr["clocks"]}
+        if mixed:
+            kp = (L + 63) // 64 * 64
+            issued = 10 * 2.0 * kp * L * rr["accepted"]  # ten BF16 slice-pair products per row
+            tc = issued / secs / 1e12 if secs > 0 else None
+            d["roofline"] = {"kernel": "k_umma_gemm (tcgen05, BF16 fixed-point slices)", "bound": "tensor",
+                             "achieved": tc, "peak": BF16_SUSTAINED_TFLOPS, "unit": "TFLOP/s",
+                             "frac": tc / BF16_SUSTAINED_TFLOPS if tc else None, "traffic": None,
+                             "algorithmic_tflops": achieved, "peak_source": "fallback BF16 sustained (no "
+                             "MEASURED_PEAKS file)", "launches": rr["prof_n"],
+                             "avg_launch_ms": rr["prof_ms"] / max(rr["prof_n"], 1),
+                             "share_of_step": rr["prof_ms"] / rr["ms"] if rr["ms"] > 0 else None}
+        else:
+            traffic_per_row, _ = profiled_traffic(kernel_source_hash())
+            rows_per_launch = rr["accepted"] / max(rr["prof_n"], 1)
+            d["roofline"] = {"kernel": "k_lambda_rows", "bound": "alu", "achieved": achieved,
+                             "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                             "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
+                             "traffic": traffic_per_row * rows_per_launch if traffic_per_row else None,
+                             "peak_source": "nominal FP64 of GB300 (152 SM x 2 DFMA/clk x 2.07 GHz; "
+                                            "measured register probe 1.19)",
+                             "launches": rr["prof_n"], "avg_launch_ms": rr["prof_ms"] / max(rr["prof_n"], 1),
+                             "share_of_step": rr["prof_ms"] / rr["ms"] if rr["ms"] > 0 else None}
+        return d
+
+    prim = summary(run, mixed_primary)
     out = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic",
+        "metric": METRIC, "value": prim["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": prim["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+bf16 (f64 refresh)" if mixed_primary else "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "walkers_per_gpu": W, "n_electrons": N, "basis_functions": L,
-                   "precision": "fp64", "l2": "inputs larger than L2 (walker state ~1 GB per GPU)",
+                   "precision": args.precision, "l2": "inputs larger than L2 (walker state ~1 GB per GPU)",
                    "parallelism": f"walker shards x{ws}"},
-        "el_per_s": W * args.steps * ws / (ms_max / 1e3),
-        "acceptance": accepted / (W * N * args.steps),
-        "status_bits": bits,
-        "roofline": {"kernel": "k_lambda_rows", "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
-                     "traffic": traffic, "peak_source": "nominal FP64 of GB300 (no measured FP64 peak)",
-                     "launches": lam_n, "avg_launch_ms": lam_ms / max(lam_n, 1),
-                     "share_of_step": lam_ms / ms if ms > 0 else None},
-        "gpu_launches": launches,
+        "el_per_s": prim["el_per_s"], "acceptance": prim["acceptance"], "status_bits": prim["status_bits"],
+        "roofline": prim["roofline"], "gpu_launches": prim["gpu_launches"],
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(hx.numel() * 8),
                 "d2h_bytes_per_step": int(he.numel() * 8 + hr.numel() * 8), "steps": e2e_steps},
-        "clocks": clk.summary(),
+        "clocks": prim["clocks"],
     }
+    if other is not None:
+        o = summary(other, not mixed_primary)
+        o["precision"] = "fp64" if mixed_primary else "mixed"
+        o["speedup_vs_primary"] = o["value"] / prim["value"]
+        out["mixed" if not mixed_primary else "fp64"] = o
     if ws == 1 and not args.no_cpu_baseline:
         mv, els, cores, sample, secs = oracle_rate(sysm, target_s=args.cpu_seconds)
         out["cpu_baseline"] = {"value": mv, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -338,6 +390,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--walkers", type=int, default=4096)
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--no-other", action="store_true", help="skip timing the other precision")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     args = ap.parse_args()
