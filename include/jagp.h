@@ -131,6 +131,27 @@ jagp_status_t vmc_sweep(jagp_handle_t h, double *d_r, void *d_state, int W, int 
 jagp_status_t local_energy(jagp_handle_t h, const double *d_r, void *d_state, int W, double *d_eL,
                            double *d_parts, void *stream);
 
+/* Reverse-mode (adjoint) derivatives, Sec. "Derivatives of energy" (AAD) and
+ * Eqs. eq_general_force, forces:aad (without the space warp):  for W walkers
+ * whose state is current (jagp_eval / vmc_sweep on d_r) and per-walker seeds
+ * sL = d_seed_logpsi[w], sE = d_seed_eL[w] (either array may be NULL = 0),
+ * the vector-Jacobian products
+ *   d_dlambda[mu][nu] = sum_w (sL d log|Psi_w|/d lambda_{mu,nu} + sE d e_L,w/d lambda_{mu,nu})
+ *                        (every entry of lambda taken as independent)          [L][L] or NULL
+ *   d_djas[3]         = sum_w sL d log|Psi_w| / d (b_ea, b_para, b_anti)       (log|Psi| part only)
+ *   d_dR[a][3]        = sum_w (sL d log|Psi_w|/dR_a + sE d e_L,w/dR_a)          or NULL
+ *   d_dR_walker[w][a][3]  the same per walker                                 or NULL
+ *   d_dr[w][i][3]     = sL d log|Psi_w|/dr_i + sE d e_L,w/dr_i                  or NULL
+ * and d_eL[w] (the local energies the derivatives belong to, or NULL).  With
+ * sL = 2 (e_L - <e_L>) / M and sE = 1 / M, d_dR is minus the Hellmann-Feynman +
+ * Pulay force -<de_L/dR> - 2 cov(e_L, d log|Psi|/dR).  d_work: caller-owned
+ * device workspace of jagp_grad_workspace_bytes(h, W) bytes, 256-byte aligned.
+ * The jagp_grad call leaves d_state valid.  FP64 handles only (UNSUPPORTED otherwise). */
+size_t jagp_grad_workspace_bytes(jagp_handle_t h, int W);
+jagp_status_t jagp_grad(jagp_handle_t h, const double *d_r, void *d_state, int W, const double *d_seed_logpsi,
+                        const double *d_seed_eL, void *d_work, double *d_eL, double *d_dlambda, double *d_djas,
+                        double *d_dR, double *d_dR_walker, double *d_dr, void *stream);
+
 /* Copy per-walker bookkeeping to device arrays (each may be NULL):
  * log|Psi|, sign, accepted moves since jagp_eval, last drift, status bits. */
 jagp_status_t jagp_walker_info(jagp_handle_t h, const void *d_state, int W, double *d_logabs,

@@ -82,6 +82,10 @@ def lib():
         L.orc_grad_logpsi.argtypes = [vp, vp, vp, vp, vp, vp]
         L.orc_grad_logpsi.restype = i
         L.orc_max_threads.restype = i
+        L.orc_elocal_grad_fd.argtypes = [vp, vp, d, vp, vp]
+        L.orc_elocal_grad_fd.restype = i
+        L.orc_elocal_dlambda_fd.argtypes = [vp, vp, i, i, d]
+        L.orc_elocal_dlambda_fd.restype = d
         _lib = L
     return _lib
 
@@ -212,6 +216,19 @@ class Oracle:
         if not ok:
             raise ValueError("singular geminal matrix")
         return {"lam": dlam, "jas": djas, "R": dR, "r": dr}
+
+    def elocal_grad(self, x, h=1e-3, want_R=True, want_r=True):
+        """Reference d e_L / d R_a and d e_L / d r_i (Richardson-extrapolated
+        central differences of the local energy, error O(h^4))."""
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        dR = np.zeros((self.sys.n_atoms, 3)) if want_R else None
+        dr = np.zeros((self.N, 3)) if want_r else None
+        lib().orc_elocal_grad_fd(self._ps, _p(x), float(h), _p(dR), _p(dr))
+        return dR, dr
+
+    def elocal_dlambda(self, x, mu, nu, h=1e-4):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        return float(lib().orc_elocal_dlambda_fd(self._ps, _p(x), int(mu), int(nu), float(h)))
 
     # --- batches ------------------------------------------------------------
     def local_energy_batch(self, x):

@@ -820,3 +820,78 @@ done:
   free(phi); free(gphi); free(lphi); free(G); free(Ginv); free(a); free(col); free(owner);
   return ok;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Reference derivatives of the local energy with respect to the nuclear     */
+/* positions R_a and the electron positions r_i (the ingredients of the      */
+/* Hellmann-Feynman + Pulay force of Eq. forces:aad without the space warp): */
+/* central differences of orc_local_energy, Richardson-extrapolated          */
+/*   D(h) = (e(+h) - e(-h)) / 2h,  D = (4 D(h/2) - D(h)) / 3   (error O(h^4)) */
+/* dR: [n_atoms][3] (may be NULL), dr: [N][3] (may be NULL).                 */
+/* ------------------------------------------------------------------------ */
+static double el_at(const orc_system *s, const double *x) {
+  double out[5];
+  orc_local_energy(s, x, out);
+  return out[0];
+}
+
+int orc_elocal_grad_fd(const orc_system *s, const double *x, double h, double *dR, double *dr) {
+  int N = s->n_up + s->n_dn;
+  double *xx = (double *)malloc(sizeof(double) * 3 * N);
+  double *RR = (double *)malloc(sizeof(double) * 3 * s->n_atoms);
+  orc_system t = *s;
+  t.R = RR;
+  memcpy(xx, x, sizeof(double) * 3 * N);
+  memcpy(RR, s->R, sizeof(double) * 3 * s->n_atoms);
+  const double hs[2] = {h, 0.5 * h};
+  if (dr)
+    for (int q = 0; q < 3 * N; ++q) {
+      double D[2];
+      for (int k = 0; k < 2; ++k) {
+        xx[q] = x[q] + hs[k];
+        double ep = el_at(s, xx);
+        xx[q] = x[q] - hs[k];
+        double em = el_at(s, xx);
+        xx[q] = x[q];
+        D[k] = (ep - em) / (2.0 * hs[k]);
+      }
+      dr[q] = (4.0 * D[1] - D[0]) / 3.0;
+    }
+  if (dR)
+    for (int q = 0; q < 3 * s->n_atoms; ++q) {
+      double D[2];
+      for (int k = 0; k < 2; ++k) {
+        RR[q] = s->R[q] + hs[k];
+        double ep = el_at(&t, x);
+        RR[q] = s->R[q] - hs[k];
+        double em = el_at(&t, x);
+        RR[q] = s->R[q];
+        D[k] = (ep - em) / (2.0 * hs[k]);
+      }
+      dR[q] = (4.0 * D[1] - D[0]) / 3.0;
+    }
+  free(xx);
+  free(RR);
+  return 1;
+}
+
+/* the same for one entry lambda_{mu,nu} (every entry independent) */
+double orc_elocal_dlambda_fd(const orc_system *s, const double *x, int mu, int nu, double h) {
+  int L = s->L;
+  double *lam = (double *)malloc(sizeof(double) * (size_t)L * L);
+  memcpy(lam, s->lam, sizeof(double) * (size_t)L * L);
+  orc_system t = *s;
+  t.lam = lam;
+  const double hs[2] = {h, 0.5 * h};
+  double D[2];
+  for (int k = 0; k < 2; ++k) {
+    lam[(size_t)mu * L + nu] = s->lam[(size_t)mu * L + nu] + hs[k];
+    double ep = el_at(&t, x);
+    lam[(size_t)mu * L + nu] = s->lam[(size_t)mu * L + nu] - hs[k];
+    double em = el_at(&t, x);
+    lam[(size_t)mu * L + nu] = s->lam[(size_t)mu * L + nu];
+    D[k] = (ep - em) / (2.0 * hs[k]);
+  }
+  free(lam);
+  return (4.0 * D[1] - D[0]) / 3.0;
+}

@@ -73,6 +73,10 @@ def lib():
         L.jagp_launch_count.restype = C.c_longlong
         L.jagp_gemm_bf16x.argtypes = [vp, i, i, vp, i, i, i, i, vp, vp, vp, C.c_longlong, vp, vp, vp, vp, vp, vp]
         L.jagp_gemm_bf16x.restype = i
+        L.jagp_grad_workspace_bytes.argtypes = [vp, i]
+        L.jagp_grad_workspace_bytes.restype = C.c_size_t
+        L.jagp_grad.argtypes = [vp, vp, vp, i, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.jagp_grad.restype = i
         L.jagp_eval_noalloc.argtypes = [vp, vp, i, vp, vp, vp]
         L.jagp_eval_noalloc.restype = i
         L.jagp_status_string.argtypes = [i]
@@ -177,6 +181,17 @@ def vmc_sweep(h, r, state, W, nsweeps, walker0=0, sweep0=0, eL=None, acc=None, s
 def local_energy(h, r, state, W, eL, parts=None, stream=None):
     _check(lib().local_energy(h, _ptr(r), _ptr(state), int(W), _ptr(eL), _ptr(parts), _stream(stream)),
            "local_energy")
+
+
+def jagp_grad_workspace_bytes(h, W) -> int:
+    return int(lib().jagp_grad_workspace_bytes(h, int(W)))
+
+
+def jagp_grad(h, r, state, W, work, seed_logpsi=None, seed_eL=None, eL=None, dlambda=None, djas=None, dR=None,
+              dR_walker=None, dr=None, stream=None):
+    _check(lib().jagp_grad(h, _ptr(r), _ptr(state), int(W), _ptr(seed_logpsi), _ptr(seed_eL), _ptr(work), _ptr(eL),
+                           _ptr(dlambda), _ptr(djas), _ptr(dR), _ptr(dR_walker), _ptr(dr), _stream(stream)),
+           "jagp_grad")
 
 
 def jagp_walker_info(h, state, W, logabs=None, sign=None, naccept=None, drift=None, status=None, stream=None):
@@ -298,3 +313,55 @@ class JAGP:
 
     def status(self, W=None) -> int:
         return jagp_walker_status(self.h, self.state, self.W if W is None else W)
+
+    def grad(self, r, seed_logpsi=None, seed_eL=None, want_lambda=True):
+        """Vector-Jacobian products of (log|Psi|, e_L) at the current state (see
+        jagp_grad in include/jagp.h).  Returns a dict of device tensors."""
+        import torch
+        W = r.shape[0]
+        work = torch.empty(jagp_grad_workspace_bytes(self.h, W), dtype=torch.uint8, device=self.device)
+        f64 = dict(dtype=torch.float64, device=self.device)
+        L, na = self.sys.L, self.sys.R.shape[0]
+        out = {"eL": torch.empty(W, **f64), "lam": torch.empty((L, L), **f64) if want_lambda else None,
+               "jas": torch.empty(3, **f64), "R": torch.empty((na, 3), **f64),
+               "R_walker": torch.empty((W, na, 3), **f64), "r": torch.empty((W, self.N, 3), **f64)}
+        sl = None if seed_logpsi is None else seed_logpsi.to(**f64).contiguous()
+        se = None if seed_eL is None else seed_eL.to(**f64).contiguous()
+        jagp_grad(self.h, r, self.state, W, work, sl, se, out["eL"], out["lam"], out["jas"], out["R"],
+                  out["R_walker"], out["r"])
+        return out
+
+
+def _autograd_function():
+    import torch
+
+    class LogPsiLocalEnergy(torch.autograd.Function):
+        """(log|Psi|, e_L) of W configurations as a differentiable function of
+        (lambda, Jastrow parameters, R, r); the backward pass is the library's
+        adjoint (jagp_grad).  The Jastrow-parameter gradient is that of log|Psi|
+        only (d e_L / d b is not formed).  The tensors lam, jas, R must hold the
+        values the JAGP object was created with."""
+
+        @staticmethod
+        def forward(ctx, g, lam, jas, R, r):
+            r = r.detach().contiguous()
+            la, _ = g.eval(r)
+            eL = g.local_energy(r)
+            ctx.g = g
+            ctx.save_for_backward(r)
+            return la, eL
+
+        @staticmethod
+        def backward(ctx, g_log, g_el):
+            (r,) = ctx.saved_tensors
+            g = ctx.g
+            g.eval(r)
+            out = g.grad(r, seed_logpsi=g_log, seed_eL=g_el, want_lambda=ctx.needs_input_grad[1])
+            return None, out["lam"], out["jas"], out["R"], out["r"]
+
+    return LogPsiLocalEnergy
+
+
+def logpsi_and_local_energy(g, lam, jas, R, r):
+    """Differentiable (log|Psi|, e_L); see LogPsiLocalEnergy."""
+    return _autograd_function().apply(g, lam, jas, R, r)

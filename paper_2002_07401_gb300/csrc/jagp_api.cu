@@ -261,9 +261,104 @@ jagp_status_t run_sweeps(jagp_ctx *h, double *d_r, void *d_state, int W, int nsw
   return JAGP_OK;
 }
 
+// workspace of jagp_grad (byte offsets)
+struct GradLayout {
+  size_t jg, kbar, dnphi, h1, h2, gbar, btbar, abar, phibar_a, phibar_b, phibar_dn, part, rbar, rbar_at, jpar, eL,
+      lam_part, total;
+  int nparts, nz;
+};
+GradLayout grad_layout(const jagp_ctx *h, int W) {
+  const size_t w = (size_t)W, n = h->ds.n_up, N = h->ds.N, L = h->ds.L, na = h->ds.n_atoms;
+  GradLayout g;
+  g.nparts = adj_position_parts(h->ds);
+  const size_t rows = w * (n + h->ds.n_dn);
+  g.nz = (int)std::max<size_t>(1, std::min<size_t>(64, rows / 1024));
+  size_t o = 0;
+  auto take = [&](size_t bytes) { size_t r = o; o = align256(o + bytes); return r; };
+  g.jg = take(w * N * 3 * 8);
+  g.kbar = take(w * N * L * 8);
+  g.dnphi = take(w * n * L * 8);
+  g.h1 = take(w * n * n * 8);
+  g.h2 = take(w * n * n * 8);
+  g.gbar = take(w * n * n * 8);
+  g.btbar = take(w * n * L * 8);
+  g.abar = take(w * n * L * 8);
+  g.phibar_a = take(w * n * L * 8);
+  g.phibar_b = take(w * n * L * 8);
+  g.phibar_dn = take(w * n * L * 8);
+  g.part = take(w * g.nparts * na * 3 * 8);
+  g.rbar = take(w * N * 3 * 8);
+  g.rbar_at = take(w * na * 3 * 8);
+  g.jpar = take(w * 3 * 8);
+  g.eL = take(w * 8);
+  g.lam_part = take((size_t)g.nz * L * L * 8);
+  g.total = o;
+  return g;
+}
+
 }  // namespace
 
 extern "C" {
+
+size_t jagp_grad_workspace_bytes(jagp_handle_t h, int W) {
+  if (!h || W <= 0 || W > h->max_walkers) return 0;
+  return grad_layout(h, W).total;
+}
+
+jagp_status_t jagp_grad(jagp_handle_t h, const double *d_r, void *d_state, int W, const double *d_seed_logpsi,
+                        const double *d_seed_eL, void *d_work, double *d_eL, double *d_dlambda, double *d_djas,
+                        double *d_dR, double *d_dR_walker, double *d_dr, void *stream) {
+  jagp_status_t s = check_walkers(h, W, d_state);
+  if (s != JAGP_OK) return s;
+  if (!d_r || !d_work || (reinterpret_cast<uintptr_t>(d_work) & 255u)) return JAGP_ERR_INVALID_ARG;
+  if (h->precision != JAGP_PREC_FP64) return JAGP_ERR_UNSUPPORTED;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const DevSystem &d = h->ds;
+  const int n = d.n_up, nd = d.n_dn, N = d.N, Lb = d.L;
+  const Layout L = layout_of(h, W);
+  const GradLayout G = grad_layout(h, W);
+  char *wk = static_cast<char *>(d_work);
+  auto wp = [&](size_t off) { return reinterpret_cast<double *>(wk + off); };
+  double *eL = d_eL ? d_eL : wp(G.eL);
+  // forward: M vectors and grad D / D at the current state
+  s = run_local_energy<double>(h, d_r, d_state, W, eL, nullptr, st);
+  if (s != JAGP_OK) return s;
+  double *kbar = wp(G.kbar), *dnphi = wp(G.dnphi);
+  LAUNCH(0, 1, launch_adj_kvec(d, d_r, d_seed_eL, wp(G.jg), kbar, dnphi, W, st));
+  LAUNCH(JAGP_KERNEL_GEMM_ROWS, 1,
+         launch_gemm_rows<double>(kbar, (size_t)N * Lb, at<double>(d_state, L.bt), (size_t)n * Lb, n, n, Lb,
+                                  wp(G.h1), (size_t)n * n, n, W, st));
+  if (nd > 0)
+    LAUNCH(JAGP_KERNEL_GEMM_ROWS, 1,
+           launch_gemm_rows<double>(at<double>(d_state, L.a_up), (size_t)n * Lb, kbar + (size_t)n * Lb,
+                                    (size_t)N * Lb, n, nd, Lb, wp(G.h2), (size_t)n * n, n, W, st));
+  LAUNCH(0, 1, launch_adj_gbar(at<double>(d_state, L.ginv), wp(G.h1), wp(G.h2), d_seed_logpsi, n, nd, wp(G.gbar), W,
+                               st));
+  LAUNCH(0, 1,
+         launch_adj_rows(d, at<double>(d_state, L.ginv), wp(G.gbar), at<double>(d_state, L.phi_up),
+                         at<double>(d_state, L.bt), kbar, wp(G.btbar), wp(G.abar), wp(G.phibar_a), W, st));
+  if (nd > 0)
+    LAUNCH(JAGP_KERNEL_LAMBDA_ROWS, 1,
+           launch_lambda_rows(wp(G.btbar), d.lam, wp(G.phibar_dn), nullptr, nullptr, W * nd, nd, n, Lb, W * nd, st));
+  LAUNCH(JAGP_KERNEL_LAMBDA_ROWS, 1,
+         launch_lambda_rows(wp(G.abar), d.lamT, wp(G.phibar_b), nullptr, nullptr, W * n, n, n, Lb, W * n, st));
+  LAUNCH(0, 1,
+         launch_adj_positions(d, d_r, d_seed_eL, wp(G.jg), at<double>(d_state, L.mbuf), wp(G.phibar_a),
+                              wp(G.phibar_b), wp(G.phibar_dn), d.shell_atom, wp(G.rbar), wp(G.part), W, st));
+  LAUNCH(0, 1,
+         launch_adj_jastrow(d, d_r, d_seed_logpsi, d_seed_eL, wp(G.jg), at<double>(d_state, L.kin), wp(G.rbar),
+                            wp(G.rbar_at), wp(G.jpar), W, st));
+  LAUNCH(0, 1, launch_adj_reduce(wp(G.part), G.nparts, d.n_atoms, wp(G.rbar_at), wp(G.jpar), W, d_dR, d_djas, st));
+  if (d_dlambda)
+    LAUNCH(0, 1,
+           launch_adj_lambda(wp(G.btbar), dnphi, at<double>(d_state, L.phi_up), wp(G.abar), W, n, nd, Lb,
+                             wp(G.lam_part), G.nz, d_dlambda, st));
+  if (d_dr) JAGP_CU(cudaMemcpyAsync(d_dr, wp(G.rbar), (size_t)W * N * 3 * 8, cudaMemcpyDeviceToDevice, st));
+  if (d_dR_walker)
+    JAGP_CU(cudaMemcpyAsync(d_dR_walker, wp(G.rbar_at), (size_t)W * d.n_atoms * 3 * 8, cudaMemcpyDeviceToDevice, st));
+  return JAGP_OK;
+}
+
 
 const char *jagp_status_string(jagp_status_t s) {
   switch (s) {
@@ -296,7 +391,7 @@ jagp_status_t jagp_create(jagp_handle_t *out, const jagp_system_t *sys, const ja
   // record keeps the offset of its first function in the caller's order.
   int L = 0;
   std::vector<double4> geo;
-  std::vector<int> info;
+  std::vector<int> info, satom;
   std::vector<int> offset(sys->n_shells);
   for (int k = 0; k < sys->n_shells; ++k) {
     const int l = sys->shell_l[k], a = sys->shell_atom[k], rad = sys->shell_radial[k];
@@ -312,6 +407,7 @@ jagp_status_t jagp_create(jagp_handle_t *out, const jagp_system_t *sys, const ja
         const int a = sys->shell_atom[k];
         geo.push_back(make_double4(sys->R[3 * a], sys->R[3 * a + 1], sys->R[3 * a + 2], sys->shell_zeta[k]));
         info.push_back(l | (rad << 2) | (offset[k] << 8));
+        satom.push_back(a);
       }
   const int na = sys->n_atoms, k_unp = sys->n_up - sys->n_dn;
   std::vector<double> c1(na), lamT((size_t)L * L);
@@ -337,6 +433,7 @@ jagp_status_t jagp_create(jagp_handle_t *out, const jagp_system_t *sys, const ja
     if (g_attr_err == cudaSuccess) g_attr_err = setup_walker_attributes();
     if (g_attr_err == cudaSuccess) g_attr_err = setup_energy_attributes();
     if (g_attr_err == cudaSuccess) g_attr_err = setup_umma_attributes();
+    if (g_attr_err == cudaSuccess) g_attr_err = setup_adjoint_attributes();
   });
   if (g_attr_err != cudaSuccess) {
     delete h;
@@ -347,6 +444,7 @@ jagp_status_t jagp_create(jagp_handle_t *out, const jagp_system_t *sys, const ja
   auto take = [&](size_t bytes) { size_t r = off; off = align256(off + bytes); return r; };
   const size_t oR = take(na * 3 * 8), oZ = take(na * 8), oC = take(na * 8);
   const size_t oG = take(sys->n_shells * sizeof(double4)), oI = take(sys->n_shells * sizeof(int));
+  const size_t oSa = take(sys->n_shells * sizeof(int));
   const size_t oL = take((size_t)L * L * 8), oT = take((size_t)L * L * 8);
   const size_t oU = take((size_t)(k_unp > 0 ? k_unp : 1) * L * 8);
   // mixed path: lambda^T and lambda as fixed-point slices, rows padded to kp
@@ -374,6 +472,7 @@ jagp_status_t jagp_create(jagp_handle_t *out, const jagp_system_t *sys, const ja
             cudaMemcpy(b + oC, c1.data(), na * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
             cudaMemcpy(b + oG, geo.data(), sys->n_shells * sizeof(double4), cudaMemcpyHostToDevice) == cudaSuccess &&
             cudaMemcpy(b + oI, info.data(), sys->n_shells * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy(b + oSa, satom.data(), sys->n_shells * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess &&
             cudaMemcpy(b + oL, sys->lambda, (size_t)L * L * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
             cudaMemcpy(b + oT, lamT.data(), (size_t)L * L * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
             (k_unp == 0 ||
@@ -400,6 +499,7 @@ jagp_status_t jagp_create(jagp_handle_t *out, const jagp_system_t *sys, const ja
   d.c1 = reinterpret_cast<const double *>(b + oC);
   d.shell_geo = reinterpret_cast<const double4 *>(b + oG);
   d.shell_info = reinterpret_cast<const int *>(b + oI);
+  d.shell_atom = reinterpret_cast<const int *>(b + oSa);
   d.lam = reinterpret_cast<const double *>(b + oL);
   d.lamT = reinterpret_cast<const double *>(b + oT);
   d.unpaired = reinterpret_cast<const double *>(b + oU);
@@ -491,6 +591,7 @@ jagp_status_t jagp_gemm_bf16x(const uint16_t *d_A, int M, int a_terms, const uin
     if (g_attr_err == cudaSuccess) g_attr_err = setup_walker_attributes();
     if (g_attr_err == cudaSuccess) g_attr_err = setup_energy_attributes();
     if (g_attr_err == cudaSuccess) g_attr_err = setup_umma_attributes();
+    if (g_attr_err == cudaSuccess) g_attr_err = setup_adjoint_attributes();
   });
   if (g_attr_err != cudaSuccess) return JAGP_ERR_CUDA;
   const cudaError_t e = launch_umma_gemm(d_A, M, d_count, a_terms, d_B, N, b_terms, Kp, npairs, h_pair_a, h_pair_b,

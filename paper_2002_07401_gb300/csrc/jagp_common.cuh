@@ -23,6 +23,7 @@ struct DevSystem {
   const double *c1;         // (2 Z_a)^{1/4}
   const double4 *shell_geo; // [n_shells]
   const int *shell_info;    // [n_shells]
+  const int *shell_atom;    // [n_shells] owning atom, in the same (evaluation) order
   const double *lam;        // [L][L]
   const double *lamT;       // [L][L] = lambda^T
   const double *unpaired;   // [n_up - n_dn][L]

@@ -92,6 +92,28 @@ cudaError_t setup_umma_attributes();
 cudaError_t launch_pack_split3(const float *P, const int *list, const int *count, int nrows, int nsub, int stride,
                                int L, int kp, uint16_t *A, int *rows_out, int max_rows, cudaStream_t st);
 
+// Reverse-mode derivatives (k_adjoint.cu); see that file for the formulas.
+cudaError_t launch_adj_kvec(const DevSystem &s, const double *r, const double *sE, double *jg, double *kbar,
+                            double *dnphi, int W, cudaStream_t st);
+cudaError_t launch_adj_gbar(const double *ginv, const double *h1, const double *h2, const double *sL, int n, int nd,
+                            double *gbar, int W, cudaStream_t st);
+cudaError_t launch_adj_rows(const DevSystem &s, const double *ginv, const double *gbar, const double *phi_up,
+                            const double *bt, const double *kbar, double *btbar, double *abar, double *phibar, int W,
+                            cudaStream_t st);
+int adj_position_parts(const DevSystem &s);
+cudaError_t launch_adj_positions(const DevSystem &s, const double *r, const double *sE, const double *jg,
+                                 const double *mbuf, const double *phibar_a, const double *phibar_b,
+                                 const double *phibar_dn, const int *shell_atom, double *rbar, double *part, int W,
+                                 cudaStream_t st);
+cudaError_t launch_adj_jastrow(const DevSystem &s, const double *r, const double *sL, const double *sE,
+                               const double *jg, const double *kin, double *rbar, double *rbar_at, double *jpar, int W,
+                               cudaStream_t st);
+cudaError_t launch_adj_reduce(const double *part, int nparts, int n_atoms, double *rbar_at, const double *jpar,
+                              int W, double *dR, double *djas, cudaStream_t st);
+cudaError_t launch_adj_lambda(const double *btbar, const double *dnphi, const double *phi_up, const double *abar,
+                              int W, int n, int nd, int L, double *part, int nz, double *dlam, cudaStream_t st);
+cudaError_t setup_adjoint_attributes();
+
 // one-time kernel attribute set-up (dynamic shared memory limits), per file
 cudaError_t setup_kernel_attributes();
 cudaError_t setup_walker_attributes();

@@ -1,0 +1,163 @@
+"""Adjoint derivatives (jagp_grad) against the FP64 oracle.
+
+log|Psi| parts: the oracle's analytic gradients (themselves pinned by central
+differences), tolerance 1e-9 relative to the largest component.  e_L parts:
+the oracle's Richardson-extrapolated central differences of its own local
+energy (h = 5e-4 bohr, error O(h^4)), tolerance 1e-7 relative to the largest
+component.  Properties: translation invariance (sum over nuclei and electrons
+of the derivative vanishes for both log|Psi| and e_L) and zero e_L derivatives
+of exact eigenstates.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+SYSTEMS = {
+    "small-unpaired-slater": lambda: synth.small_random(n_atoms=3, n_up=4, n_dn=2, per_atom=20, seed=31,
+                                                        slater_fraction=0.3),
+    "small-nonsym": lambda: synth.small_random(n_atoms=4, n_up=5, n_dn=5, per_atom=16, seed=32, symmetric=False),
+    "C1": lambda: synth.config1(),
+    "mid-n40": lambda: synth.small_random(n_atoms=20, n_up=40, n_dn=37, per_atom=6, seed=33, side=7.0, Z=2.0),
+}
+
+
+def _cfgs(sysm, W, seed=5):
+    return synth.jitter_walkers(synth.init_walkers(sysm, W, seed=seed), seed + 1, 0.3)
+
+
+def _close(a, b, rel):
+    a, b = np.asarray(a), np.asarray(b)
+    scale = max(1.0, float(np.abs(b).max()))
+    return float(np.abs(a - b).max()) <= rel * scale, float(np.abs(a - b).max()) / scale
+
+
+@pytest.mark.parametrize("name", list(SYSTEMS))
+def test_logpsi_gradients_match_oracle(torch_cuda, name):
+    torch = torch_cuda
+    import paper_2002_07401_gb300 as pg
+    sysm = SYSTEMS[name]()
+    W = 5
+    x = _cfgs(sysm, W)
+    o = oracle.Oracle(sysm)
+    seeds = np.random.default_rng(1).normal(size=W)
+    g = pg.JAGP(sysm, W)
+    r = g.positions(x)
+    g.eval(r)
+    out = g.grad(r, seed_logpsi=torch.tensor(seeds, device="cuda"))
+    ref = [o.grad_logpsi(x[w]) for w in range(W)]
+    lam_ref = sum(s * d["lam"] for s, d in zip(seeds, ref))
+    jas_ref = sum(s * d["jas"] for s, d in zip(seeds, ref))
+    R_ref = sum(s * d["R"] for s, d in zip(seeds, ref))
+    r_ref = np.stack([s * d["r"] for s, d in zip(seeds, ref)])
+    for got, want, what in ((out["lam"], lam_ref, "lambda"), (out["jas"], jas_ref, "jastrow"), (out["R"], R_ref, "R"),
+                            (out["r"], r_ref, "r")):
+        ok, err = _close(got.cpu().numpy(), want, 1e-9)
+        assert ok, (what, err)
+    Rw = out["R_walker"].cpu().numpy()
+    for w in range(W):
+        assert _close(Rw[w], seeds[w] * ref[w]["R"], 1e-9)[0]
+
+
+@pytest.mark.parametrize("name", ["small-unpaired-slater", "small-nonsym", "C1"])
+def test_local_energy_gradients_match_fd(torch_cuda, name):
+    torch = torch_cuda
+    import paper_2002_07401_gb300 as pg
+    sysm = SYSTEMS[name]()
+    W = 3
+    x = _cfgs(sysm, W, seed=9)
+    o = oracle.Oracle(sysm)
+    seeds = np.array([1.0, -0.7, 0.4])
+    g = pg.JAGP(sysm, W)
+    r = g.positions(x)
+    g.eval(r)
+    out = g.grad(r, seed_eL=torch.tensor(seeds, device="cuda"))
+    Rw = out["R_walker"].cpu().numpy()
+    rr = out["r"].cpu().numpy()
+    for w in range(W):
+        dR, dr = o.elocal_grad(x[w], h=5e-4)
+        ok, err = _close(Rw[w], seeds[w] * dR, 1e-7)
+        assert ok, ("R", w, err)
+        ok, err = _close(rr[w], seeds[w] * dr, 1e-7)
+        assert ok, ("r", w, err)
+    # lambda: a few entries by central differences of the oracle's e_L
+    lam = out["lam"].cpu().numpy()
+    rng = np.random.default_rng(2)
+    for _ in range(4):
+        mu, nu = rng.integers(sysm.L, size=2)
+        fd = sum(seeds[w] * o.elocal_dlambda(x[w], mu, nu) for w in range(W))
+        assert abs(lam[mu, nu] - fd) <= 1e-6 * max(1.0, abs(fd)), (mu, nu, lam[mu, nu], fd)
+
+
+@pytest.mark.parametrize("name", list(SYSTEMS))
+def test_translation_invariance_of_force_vjp(torch_cuda, name):
+    torch = torch_cuda
+    import paper_2002_07401_gb300 as pg
+    sysm = SYSTEMS[name]()
+    W = 4
+    x = _cfgs(sysm, W, seed=11)
+    g = pg.JAGP(sysm, W)
+    r = g.positions(x)
+    g.eval(r)
+    eL = g.local_energy(r)
+    # the force estimator's seeds: sL = 2 (e_L - <e_L>) / W, sE = 1 / W
+    sL = 2.0 * (eL - eL.mean()) / W
+    sE = torch.full((W,), 1.0 / W, dtype=torch.float64, device="cuda")
+    out = g.grad(r, seed_logpsi=sL, seed_eL=sE, want_lambda=False)
+    Rw, rr = out["R_walker"].cpu().numpy(), out["r"].cpu().numpy()
+    for w in range(W):
+        tot = Rw[w].sum(0) + rr[w].sum(0)
+        scale = max(1.0, np.abs(Rw[w]).max(), np.abs(rr[w]).max())
+        assert np.abs(tot).max() <= 1e-9 * scale, (w, tot)
+
+
+def test_exact_eigenstates_have_zero_local_energy_derivatives(torch_cuda):
+    torch = torch_cuda
+    import paper_2002_07401_gb300 as pg
+    for sysm in (synth.hydrogen_slater(), synth.hydrogenic_gauss_j1(2.0)):
+        W = 8
+        g = pg.JAGP(sysm, W)
+        r = g.positions(_cfgs(sysm, W, seed=3))
+        g.eval(r)
+        out = g.grad(r, seed_eL=torch.ones(W, dtype=torch.float64, device="cuda"), want_lambda=False)
+        assert np.abs(out["r"].cpu().numpy()).max() < 1e-11
+        assert np.abs(out["R"].cpu().numpy()).max() < 1e-10
+
+
+def test_autograd_function_force(torch_cuda):
+    """The force estimator through torch.autograd: -dE/dR with E = <e_L> and the
+    Pulay term from the log|Psi| dependence of the sampling distribution."""
+    torch = torch_cuda
+    import paper_2002_07401_gb300 as pg
+    sysm = SYSTEMS["small-nonsym"]()
+    W = 6
+    x = _cfgs(sysm, W, seed=13)
+    g = pg.JAGP(sysm, W)
+    lam = torch.tensor(sysm.lam, device="cuda", requires_grad=True)
+    jas = torch.tensor([sysm.b_ea, sysm.b_para, sysm.b_anti], dtype=torch.float64, device="cuda", requires_grad=True)
+    R = torch.tensor(sysm.R, device="cuda", requires_grad=True)
+    r = g.positions(x).requires_grad_(True)
+    logpsi, eL = pg.logpsi_and_local_energy(g, lam, jas, R, r)
+    E = eL.mean()
+    surrogate = E + 2.0 * ((eL - E).detach() * logpsi).mean()
+    surrogate.backward()
+    o = oracle.Oracle(sysm)
+    el = np.array([o.local_energy(x[w]) for w in range(W)])
+    want = np.zeros_like(sysm.R)
+    for w in range(W):
+        dR, _ = o.elocal_grad(x[w], h=5e-4)
+        want += dR / W + 2.0 * (el[w] - el.mean()) / W * o.grad_logpsi(x[w], want_lam=False)["R"]
+    ok, err = _close(R.grad.cpu().numpy(), want, 1e-7)
+    assert ok, err
