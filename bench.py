@@ -253,6 +253,70 @@ def timed_sweeps(pg, torch, dist, sysm, W, walker0, x0, prec, steps, warmup, ws,
             "clocks": clk.summary()}
 
 
+FORCES_WORKLOAD = ("adjoint gradients: 64 He atoms in a 16 bohr cube, N=128 (64 up, 64 down), 24 s/p/d Gaussians/"
+                   "atom (L=1536), 2048 walkers/GPU; per configuration e_L, the ionic force vector (Hellmann-Feynman "
+                   "+ Pulay, Eq. forces:aad without space warp), d log|Psi|/d lambda and d log|Psi|/d b")
+
+
+def forces_bench(pg, torch, dist, args, dev, rank, ws, local):
+    """E_L + forces per second: one step = jagp_grad over all walkers with the
+    force-estimator seeds (sE = 1/M, sL = 2 (e_L - <e_L>)/M from the walkers'
+    local energies), producing e_L, dE/dR, d log|Psi|/d lambda and d/d b."""
+    import numpy as np
+    import synth
+    sysm = synth.config4()
+    W = args.force_walkers
+    x0 = np.ascontiguousarray(synth.init_walkers(sysm, W * ws, seed=0)[rank * W:(rank + 1) * W])
+    g = pg.JAGP(sysm, W, seed=0)
+    r = g.positions(x0)
+    g.eval(r)
+    eL, _ = g.sweep(r, 1, walker0=rank * W, sweep0=0)
+    e = eL[0]
+    sE = torch.full((W,), 1.0 / W, dtype=torch.float64, device=dev)
+    sL = 2.0 * (e - e.mean()) / W
+    work = torch.empty(pg.jagp_grad_workspace_bytes(g.h, W), dtype=torch.uint8, device=dev)
+    f64 = dict(dtype=torch.float64, device=dev)
+    L, na = sysm.L, sysm.n_atoms
+    out = dict(eL=torch.empty(W, **f64), lam=torch.empty((L, L), **f64), jas=torch.empty(3, **f64),
+               R=torch.empty((na, 3), **f64))
+    call = lambda: pg.jagp_grad(g.h, r, g.state, W, work, sL, sE, out["eL"], out["lam"], out["jas"], out["R"])  # noqa
+    for _ in range(args.force_warmup):
+        call()
+    torch.cuda.synchronize()
+    pg.jagp_profile(g.h, pg.KERNEL_LAMBDA_ROWS, True)
+    pg.jagp_profile_read(g.h)
+    n0 = pg.jagp_launch_count(g.h)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(args.force_steps):
+        call()
+    e1.record()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    launches = pg.jagp_launch_count(g.h) - n0
+    lam_ms, lam_n = pg.jagp_profile_read(g.h)
+    ms = e0.elapsed_time(e1)
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    g.close()
+    n, nd = sysm.n_up, sysm.n_dn
+    flops = 2.0 * L * L * W * (n + nd)  # the two lambda-product launches: 2 L^2 per orbital row
+    achieved = flops * args.force_steps / (lam_ms / 1e3) / 1e12 if lam_ms > 0 else None
+    return {"metric": "E_L+forces/s", "value": W * ws * args.force_steps / (ms_max / 1e3), "unit": "configurations/s",
+            "ms_per_step": ms_max / args.force_steps, "steps": args.force_steps, "warmup": args.force_warmup,
+            "dtype": "f64", "workload": FORCES_WORKLOAD, "walkers_per_gpu": W, "gpu_launches": launches,
+            "roofline": {"kernel": "k_lambda_rows (adjoint orbital rows)", "bound": "alu", "achieved": achieved,
+                         "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP64_PEAK_TFLOPS if achieved else None, "traffic": None,
+                         "launches": lam_n, "share_of_step": lam_ms / ms if ms > 0 else None}}
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -313,6 +377,8 @@ def run_gpu(args):
                              pg.KERNEL_LAMBDA_ROWS)
         other["g"].close()
 
+    forces = None if args.no_forces else forces_bench(pg, torch, dist, args, dev, rank, ws, local)
+
     if rank != 0:
         if ws > 1:
             dist.barrier()
@@ -372,6 +438,8 @@ def run_gpu(args):
         o["precision"] = "fp64" if mixed_primary else "mixed"
         o["speedup_vs_primary"] = o["value"] / prim["value"]
         out["mixed" if not mixed_primary else "fp64"] = o
+    if forces is not None:
+        out["forces"] = forces
     if ws == 1 and not args.no_cpu_baseline:
         mv, els, cores, sample, secs = oracle_rate(sysm, target_s=args.cpu_seconds)
         out["cpu_baseline"] = {"value": mv, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -392,6 +460,10 @@ def main():
     ap.add_argument("--walkers", type=int, default=4096)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--no-other", action="store_true", help="skip timing the other precision")
+    ap.add_argument("--no-forces", action="store_true", help="skip the E_L + forces measurement")
+    ap.add_argument("--force-walkers", type=int, default=2048)
+    ap.add_argument("--force-steps", type=int, default=2)
+    ap.add_argument("--force-warmup", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     args = ap.parse_args()
