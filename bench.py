@@ -317,6 +317,57 @@ def forces_bench(pg, torch, dist, args, dev, rank, ws, local):
                          "launches": lam_n, "share_of_step": lam_ms / ms if ms > 0 else None}}
 
 
+BATCH_WORKLOAD = ("batched uneven systems, mixed precision: 64 independent neutral He systems, N uniform in "
+                  "{8,...,128} (N/2 up, N/2 down, N/2 atoms), 16 Gaussians/atom, 512 walkers per system, every sweep "
+                  "one replay of a captured CUDA graph over all systems; FP64 refresh of G^-1 every N_up moves")
+
+
+def batch_bench(pg, torch, dist, args, dev, rank, ws):
+    """Walker-electron moves/s of the batched mixed-precision path."""
+    import synth
+    systems = synth.config3_systems(seed=0, n_systems=args.batch_systems)
+    W = args.batch_walkers
+    members, pos = [], []
+    for s in systems:
+        m = pg.JAGP(s, W, seed=0, precision=pg.JAGP_PREC_MIXED)
+        p = m.positions(synth.init_walkers(s, W * ws, seed=0)[rank * W:(rank + 1) * W])
+        m.eval(p)
+        members.append(m)
+        pos.append(p)
+    b = pg.Batch(members, pos, walker0=[rank * W] * len(members), n_streams=args.batch_streams)
+    b.sweep(args.warmup, sweep0=0)
+    torch.cuda.synchronize()
+    b.acc.zero_()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0.record()
+    b.sweep(args.batch_sweeps, sweep0=args.warmup)
+    e1.record()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    bits = 0
+    for m in members:
+        bits |= m.status()
+    acc = b.acc.cpu().numpy()
+    b.close()
+    for m in members:
+        m.close()
+    moves = W * sum(s.N for s in systems) * args.batch_sweeps * ws
+    return {"metric": "walker-electron moves/s", "value": moves / (ms_max / 1e3), "unit": "walker-electron moves/s",
+            "ms_per_sweep": ms_max / args.batch_sweeps, "sweeps": args.batch_sweeps, "warmup": args.warmup,
+            "systems": len(systems), "walkers_per_system": W, "moves_per_sweep": moves // args.batch_sweeps // ws,
+            "acceptance": float(acc[:, 2].sum()) / (moves / ws), "status_bits": bits,
+            "dtype": "f32+bf16 (f64 refresh)", "workload": BATCH_WORKLOAD}
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -378,6 +429,7 @@ def run_gpu(args):
         other["g"].close()
 
     forces = None if args.no_forces else forces_bench(pg, torch, dist, args, dev, rank, ws, local)
+    batched = None if args.no_batch else batch_bench(pg, torch, dist, args, dev, rank, ws)
 
     if rank != 0:
         if ws > 1:
@@ -440,6 +492,8 @@ def run_gpu(args):
         out["mixed" if not mixed_primary else "fp64"] = o
     if forces is not None:
         out["forces"] = forces
+    if batched is not None:
+        out["batched"] = batched
     if ws == 1 and not args.no_cpu_baseline:
         mv, els, cores, sample, secs = oracle_rate(sysm, target_s=args.cpu_seconds)
         out["cpu_baseline"] = {"value": mv, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -464,6 +518,11 @@ def main():
     ap.add_argument("--force-walkers", type=int, default=2048)
     ap.add_argument("--force-steps", type=int, default=2)
     ap.add_argument("--force-warmup", type=int, default=1)
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched uneven-systems measurement")
+    ap.add_argument("--batch-systems", type=int, default=64)
+    ap.add_argument("--batch-walkers", type=int, default=512)
+    ap.add_argument("--batch-sweeps", type=int, default=20)
+    ap.add_argument("--batch-streams", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     args = ap.parse_args()

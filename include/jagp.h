@@ -131,6 +131,25 @@ jagp_status_t vmc_sweep(jagp_handle_t h, double *d_r, void *d_state, int W, int 
 jagp_status_t local_energy(jagp_handle_t h, const double *d_r, void *d_state, int W, double *d_eL,
                            double *d_parts, void *stream);
 
+/* Batches of independent systems (uneven electron counts, each with its own
+ * handle and walker state): jagp_batch_sweep runs nsweeps sweeps of every
+ * system, exactly as vmc_sweep would (same Philox counters, walker indices
+ * walker0[s] + w, sweep indices sweep0 + t), with local energies after each
+ * sweep written to d_eL[s] ([W[s]], the last sweep's) and accumulated into
+ * d_acc[s][4] (sum e_L, sum e_L^2, accepted moves, max drift; the caller
+ * zeroes it).  The first jagp_batch_sweep captures one sweep of all systems
+ * (their launches forked over n_streams concurrent streams, largest systems
+ * first) into a CUDA graph, which every later sweep replays; the sweep index
+ * is read from a device counter, so the states, positions and output arrays
+ * must stay where they were when the batch was created.  Handles, states and
+ * arrays are borrowed, not copied.  d_eL and d_acc may be NULL. */
+typedef struct jagp_batch *jagp_batch_t;
+jagp_status_t jagp_batch_create(jagp_batch_t *out, int S, const jagp_handle_t *handles, void *const *d_states,
+                                double *const *d_r, const int *W, const uint64_t *walker0, double *const *d_eL,
+                                double *d_acc, int n_streams);
+jagp_status_t jagp_batch_sweep(jagp_batch_t b, int nsweeps, uint64_t sweep0, void *stream);
+jagp_status_t jagp_batch_destroy(jagp_batch_t b);
+
 /* Reverse-mode (adjoint) derivatives, Sec. "Derivatives of energy" (AAD) and
  * Eqs. eq_general_force, forces:aad (without the space warp):  for W walkers
  * whose state is current (jagp_eval / vmc_sweep on d_r) and per-walker seeds
@@ -225,6 +244,8 @@ jagp_status_t jagp_eval_noalloc(jagp_handle_t h, const double *d_r, int W, doubl
                                 double *d_sign, void *stream);
 
 const char *jagp_status_string(jagp_status_t s);
+/* The text of the last CUDA runtime error behind a JAGP_ERR_CUDA of this thread. */
+const char *jagp_last_cuda_error(void);
 
 #ifdef __cplusplus
 }

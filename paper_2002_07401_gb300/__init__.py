@@ -77,8 +77,16 @@ def lib():
         L.jagp_grad_workspace_bytes.restype = C.c_size_t
         L.jagp_grad.argtypes = [vp, vp, vp, i, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.jagp_grad.restype = i
+        L.jagp_batch_create.argtypes = [C.POINTER(vp), i, vp, vp, vp, vp, vp, vp, vp, i]
+        L.jagp_batch_create.restype = i
+        L.jagp_batch_sweep.argtypes = [vp, i, u64, vp]
+        L.jagp_batch_sweep.restype = i
+        L.jagp_batch_destroy.argtypes = [vp]
+        L.jagp_batch_destroy.restype = i
         L.jagp_eval_noalloc.argtypes = [vp, vp, i, vp, vp, vp]
         L.jagp_eval_noalloc.restype = i
+        L.jagp_last_cuda_error.argtypes = []
+        L.jagp_last_cuda_error.restype = C.c_char_p
         L.jagp_status_string.argtypes = [i]
         L.jagp_status_string.restype = C.c_char_p
         for f in ("jagp_create", "jagp_destroy", "jagp_eval", "vmc_sweep", "local_energy",
@@ -95,6 +103,8 @@ def library_path() -> str:
 def _check(status: int, what: str):
     if status != JAGP_OK:
         msg = lib().jagp_status_string(status).decode()
+        if status == 7:
+            msg += ": " + lib().jagp_last_cuda_error().decode()
         raise JagpError(f"{what} failed: {msg} (status {status})")
 
 
@@ -330,6 +340,46 @@ class JAGP:
         jagp_grad(self.h, r, self.state, W, work, sl, se, out["eL"], out["lam"], out["jas"], out["R"],
                   out["R_walker"], out["r"])
         return out
+
+
+class Batch:
+    """Independent systems swept together (jagp_batch_*): members are JAGP
+    objects with their positions; every sweep is one replay of a captured CUDA
+    graph.  eL[s] holds the last sweep's local energies, acc[s] the running
+    (sum e_L, sum e_L^2, accepted moves, max drift)."""
+
+    def __init__(self, members, positions, walker0=None, n_streams=8):
+        import torch
+        self.members, self.r = list(members), list(positions)
+        S = len(self.members)
+        dev = self.members[0].device
+        self.eL = [torch.zeros(p.shape[0], dtype=torch.float64, device=dev) for p in self.r]
+        self.acc = torch.zeros((S, 4), dtype=torch.float64, device=dev)
+        vp = C.c_void_p
+        hs = (vp * S)(*[m.h for m in self.members])
+        st = (vp * S)(*[m.state.data_ptr() for m in self.members])
+        rp = (vp * S)(*[p.data_ptr() for p in self.r])
+        ep = (vp * S)(*[e.data_ptr() for e in self.eL])
+        W = (C.c_int * S)(*[int(p.shape[0]) for p in self.r])
+        w0 = (C.c_uint64 * S)(*([0] * S if walker0 is None else [int(v) for v in walker0]))
+        b = vp()
+        _check(lib().jagp_batch_create(C.byref(b), S, hs, st, rp, W, w0, ep, self.acc.data_ptr(), int(n_streams)),
+               "jagp_batch_create")
+        self.b = b.value
+
+    def sweep(self, nsweeps, sweep0=0, stream=None):
+        _check(lib().jagp_batch_sweep(self.b, int(nsweeps), int(sweep0), _stream(stream)), "jagp_batch_sweep")
+
+    def close(self):
+        if getattr(self, "b", None):
+            lib().jagp_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def _autograd_function():

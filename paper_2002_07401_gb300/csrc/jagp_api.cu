@@ -21,10 +21,15 @@ namespace {
 std::once_flag g_attr_once;
 cudaError_t g_attr_err = cudaSuccess;
 
-#define JAGP_CU(call)                          \
-  do {                                         \
-    cudaError_t e_ = (call);                   \
-    if (e_ != cudaSuccess) return JAGP_ERR_CUDA; \
+thread_local const char *g_last_cuda_error = "no error";
+
+#define JAGP_CU(call)                                  \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) {                           \
+      g_last_cuda_error = cudaGetErrorString(e_);      \
+      return JAGP_ERR_CUDA;                            \
+    }                                                  \
   } while (0)
 
 // Launch bookkeeping: count the kernels a launcher issues and, when profiling
@@ -207,7 +212,8 @@ jagp_status_t run_eval(jagp_ctx *h, const double *d_r, int W, void *d_state, dou
 
 template <typename T>
 jagp_status_t run_sweeps(jagp_ctx *h, double *d_r, void *d_state, int W, int nsweeps, uint64_t walker0,
-                         uint64_t sweep0, double *d_eL, double *d_acc, cudaStream_t st) {
+                         uint64_t sweep0, double *d_eL, double *d_acc, cudaStream_t st,
+                         const uint32_t *sweep_dev = nullptr, int accumulate = 0) {
   const Layout L = layout_of(h, W);
   const DevSystem &d = h->ds;
   const int n = d.n_up, Lb = d.L;
@@ -225,7 +231,7 @@ jagp_status_t run_sweeps(jagp_ctx *h, double *d_r, void *d_state, int W, int nsw
     JAGP_CU(cudaMemsetAsync(count, 0, 2 * sizeof(int), st));
     // up electrons: rows of G~ against the frozen down-spin table Bt
     LAUNCH(JAGP_KERNEL_BASIS, 1,
-           launch_basis_points<T>(d, true, d_r, W, 0, n, pprop, rprop, (uint32_t)walker0, sw, st));
+           launch_basis_points<T>(d, true, d_r, W, 0, n, pprop, rprop, (uint32_t)walker0, sw, st, sweep_dev));
     LAUNCH(JAGP_KERNEL_GEMM_ROWS, 1,
            launch_gemm_rows<T>(pprop, (size_t)n * Lb, bt, (size_t)n * Lb, n, n, Lb, gprop, (size_t)n * n, n, W, st));
     LAUNCH(JAGP_KERNEL_METROPOLIS, 1,
@@ -239,7 +245,7 @@ jagp_status_t run_sweeps(jagp_ctx *h, double *d_r, void *d_state, int W, int nsw
     if (d.n_dn > 0) {
       // down electrons: columns of G~ against the updated up-spin table A_up
       LAUNCH(JAGP_KERNEL_BASIS, 1,
-             launch_basis_points<T>(d, true, d_r, W, n, d.n_dn, pprop, rprop, (uint32_t)walker0, sw, st));
+             launch_basis_points<T>(d, true, d_r, W, n, d.n_dn, pprop, rprop, (uint32_t)walker0, sw, st, sweep_dev));
       LAUNCH(JAGP_KERNEL_GEMM_ROWS, 1,
              launch_gemm_rows<T>(pprop, (size_t)n * Lb, a_up, (size_t)n * Lb, d.n_dn, n, Lb, gprop, (size_t)n * n, n,
                                  W, st));
@@ -251,12 +257,13 @@ jagp_status_t run_sweeps(jagp_ctx *h, double *d_r, void *d_state, int W, int nsw
     }
     s = run_refresh<T>(h, d_r, d_state, W, 1, true, st);
     if (s != JAGP_OK) return s;
-    double *eL = d_eL ? d_eL + (size_t)t * W : nullptr;
+    double *eL = d_eL ? d_eL + (accumulate ? 0 : (size_t)t * W) : nullptr;
     if (eL) {
       s = run_local_energy<T>(h, d_r, d_state, W, eL, nullptr, st);
       if (s != JAGP_OK) return s;
     }
-    if (d_acc) LAUNCH(0, 1, launch_reduce_acc(eL, scal, count, W, d_acc + (size_t)t * 4, st));
+    if (d_acc)
+      LAUNCH(0, 1, launch_reduce_acc(eL, scal, count, W, d_acc + (accumulate ? 0 : (size_t)t * 4), st, accumulate));
   }
   return JAGP_OK;
 }
@@ -359,6 +366,8 @@ jagp_status_t jagp_grad(jagp_handle_t h, const double *d_r, void *d_state, int W
   return JAGP_OK;
 }
 
+
+const char *jagp_last_cuda_error(void) { return g_last_cuda_error; }
 
 const char *jagp_status_string(jagp_status_t s) {
   switch (s) {
@@ -653,6 +662,158 @@ jagp_status_t jagp_walker_status(jagp_handle_t h, const void *d_state, int W, in
   int o = 0;
   for (int w = 0; w < W; ++w) o |= bits[w];
   *h_bits = o;
+  return JAGP_OK;
+}
+
+
+// ---------------------------------------------------------------------------
+// Batches of independent systems: one sweep of every system captured once into
+// a CUDA graph (the systems' launch sequences forked over concurrent streams),
+// replayed once per sweep; the Philox sweep index comes from a device counter
+// that the graph advances at its end.
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+struct jagp_batch {
+  int S = 0;
+  std::vector<jagp_ctx *> h;
+  std::vector<void *> state;
+  std::vector<double *> r, eL;
+  std::vector<int> W;
+  std::vector<uint64_t> walker0;
+  std::vector<int> order;  // systems by decreasing cost
+  double *acc = nullptr;
+  uint32_t *counter = nullptr;
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> ev;
+  cudaEvent_t ev0 = nullptr;
+  cudaStream_t cap = nullptr;  // capture stream (capture is not allowed on the legacy default stream)
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+__global__ void k_set_counter(uint32_t *c, uint32_t v) {
+  if (threadIdx.x == 0) *c = v;
+}
+
+jagp_status_t batch_capture(jagp_batch *b) {
+  cudaStream_t st = b->cap;
+  JAGP_CU(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  jagp_status_t rc = JAGP_OK;
+  cudaEventRecord(b->ev0, st);
+  const int K = (int)b->streams.size();
+  for (int k = 0; k < K; ++k) cudaStreamWaitEvent(b->streams[k], b->ev0, 0);
+  for (int q = 0; q < b->S && rc == JAGP_OK; ++q) {
+    const int sidx = b->order[q];
+    jagp_ctx *h = b->h[sidx];
+    const int prof = h->prof_kernel;
+    h->prof_kernel = 0;  // no event pairs inside a graph
+    cudaStream_t ss = b->streams[q % K];
+    double *acc = b->acc ? b->acc + 4 * (size_t)sidx : nullptr;
+    if (h->precision == JAGP_PREC_MIXED)
+      rc = run_sweeps<float>(h, b->r[sidx], b->state[sidx], b->W[sidx], 1, b->walker0[sidx], 0, b->eL[sidx], acc, ss,
+                             b->counter, 1);
+    else
+      rc = run_sweeps<double>(h, b->r[sidx], b->state[sidx], b->W[sidx], 1, b->walker0[sidx], 0, b->eL[sidx], acc,
+                              ss, b->counter, 1);
+    h->prof_kernel = prof;
+  }
+  for (int k = 0; k < K; ++k) {
+    cudaEventRecord(b->ev[k], b->streams[k]);
+    cudaStreamWaitEvent(st, b->ev[k], 0);
+  }
+  if (rc == JAGP_OK && launch_increment(b->counter, 1, st) != cudaSuccess) rc = JAGP_ERR_CUDA;
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(st, &g);
+  if (rc != JAGP_OK || e != cudaSuccess || !g) {
+    if (e != cudaSuccess) g_last_cuda_error = cudaGetErrorString(e);
+    if (g) cudaGraphDestroy(g);
+    return rc != JAGP_OK ? rc : JAGP_ERR_CUDA;
+  }
+  b->graph = g;
+  JAGP_CU(cudaGraphInstantiate(&b->exec, g, 0));
+  return JAGP_OK;
+}
+}  // namespace
+
+extern "C" {
+
+jagp_status_t jagp_batch_create(jagp_batch_t *out, int S, const jagp_handle_t *handles, void *const *d_states,
+                                double *const *d_r, const int *W, const uint64_t *walker0, double *const *d_eL,
+                                double *d_acc, int n_streams) {
+  if (!out || S <= 0 || !handles || !d_states || !d_r || !W) return JAGP_ERR_INVALID_ARG;
+  *out = nullptr;
+  for (int q = 0; q < S; ++q) {
+    const jagp_status_t s = check_walkers(handles[q], W[q], d_states[q]);
+    if (s != JAGP_OK || !d_r[q]) return JAGP_ERR_INVALID_ARG;
+    if (handles[q]->device != handles[0]->device) return JAGP_ERR_INVALID_ARG;
+    if (walker0 && walker0[q] + (uint64_t)W[q] > 0x100000000ull) return JAGP_ERR_INVALID_ARG;
+  }
+  jagp_batch *b = new jagp_batch();
+  b->S = S;
+  for (int q = 0; q < S; ++q) {
+    b->h.push_back(handles[q]);
+    b->state.push_back(d_states[q]);
+    b->r.push_back(d_r[q]);
+    b->eL.push_back(d_eL ? d_eL[q] : nullptr);
+    b->W.push_back(W[q]);
+    b->walker0.push_back(walker0 ? walker0[q] : 0);
+    b->order.push_back(q);
+  }
+  // largest systems first so that the concurrent streams finish together
+  auto cost = [&](int q) {
+    const double n = b->h[q]->ds.n_up, L = b->h[q]->ds.L;
+    return (double)b->W[q] * (n * L * L + n * n * L);
+  };
+  std::stable_sort(b->order.begin(), b->order.end(), [&](int a, int c) { return cost(a) > cost(c); });
+  b->acc = d_acc;
+  const int K = std::max(1, std::min(n_streams > 0 ? n_streams : 8, S));
+  bool ok = cudaMalloc(&b->counter, sizeof(uint32_t)) == cudaSuccess &&
+            cudaMemset(b->counter, 0, sizeof(uint32_t)) == cudaSuccess &&
+            cudaEventCreateWithFlags(&b->ev0, cudaEventDisableTiming) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) == cudaSuccess;
+  for (int k = 0; ok && k < K; ++k) {
+    cudaStream_t s2;
+    cudaEvent_t e2;
+    ok = cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&e2, cudaEventDisableTiming) == cudaSuccess;
+    if (ok) {
+      b->streams.push_back(s2);
+      b->ev.push_back(e2);
+    }
+  }
+  if (!ok) {
+    jagp_batch_destroy(b);
+    return JAGP_ERR_CUDA;
+  }
+  *out = b;
+  return JAGP_OK;
+}
+
+jagp_status_t jagp_batch_sweep(jagp_batch_t b, int nsweeps, uint64_t sweep0, void *stream) {
+  if (!b || nsweeps < 0 || sweep0 + (uint64_t)nsweeps > 0x100000000ull) return JAGP_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!b->exec) {
+    const jagp_status_t rc = batch_capture(b);
+    if (rc != JAGP_OK) return rc;
+  }
+  k_set_counter<<<1, 32, 0, st>>>(b->counter, (uint32_t)sweep0);
+  JAGP_CU(cudaGetLastError());
+  for (int t = 0; t < nsweeps; ++t) JAGP_CU(cudaGraphLaunch(b->exec, st));
+  return JAGP_OK;
+}
+
+jagp_status_t jagp_batch_destroy(jagp_batch_t b) {
+  if (!b) return JAGP_ERR_INVALID_ARG;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  for (auto s2 : b->streams) cudaStreamDestroy(s2);
+  for (auto e2 : b->ev) cudaEventDestroy(e2);
+  if (b->ev0) cudaEventDestroy(b->ev0);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  if (b->counter) cudaFree(b->counter);
+  delete b;
   return JAGP_OK;
 }
 

@@ -14,7 +14,7 @@ namespace jagp {
 template <typename T>
 cudaError_t launch_basis_points(const DevSystem &s, bool propose, const double *r, int W, int e0,
                                 int npts, T *out, double *rprop, uint32_t walker0,
-                                uint32_t sweep, cudaStream_t st);
+                                uint32_t sweep, cudaStream_t st, const uint32_t *sweep_dev = nullptr);
 
 // Sequential Metropolis over one spin species with Sherman-Morrison updates.
 template <typename T>
@@ -71,7 +71,9 @@ cudaError_t launch_walker_info(const double *scal, const int *status, int W, dou
                                double *sign, double *nacc, double *drift, int *st_out,
                                cudaStream_t st);
 cudaError_t launch_reduce_acc(const double *eL, const double *scal, const int *count, int W,
-                              double *acc, cudaStream_t st);
+                              double *acc, cudaStream_t st, int accumulate = 0);
+// *c += by (one thread): advances a device-side sweep counter between graph replays
+cudaError_t launch_increment(uint32_t *c, uint32_t by, cudaStream_t st);
 
 // Tensor-core contraction (k_umma.cu):
 //   out[out_rows[m]][c] = sum_p sum_k A[m][pair_a[p] kp + k] B[c][pair_b[p] kp + k]

@@ -17,7 +17,8 @@ template <bool PROPOSE, typename T>
 __global__ void __launch_bounds__(256) k_basis_points(DevSystem s, const double *__restrict__ r, int W,
                                                       int e0, int npts, T *__restrict__ out,
                                                       double *__restrict__ rprop, uint32_t walker0,
-                                                      uint32_t sweep) {
+                                                      uint32_t sweep, const uint32_t *__restrict__ sweep_dev) {
+  if (PROPOSE && sweep_dev) sweep += *sweep_dev;  // graph replays read the sweep index from the device
   extern __shared__ double4 sh_geo[];
   int *sh_info = reinterpret_cast<int *>(sh_geo + s.n_shells);
   for (int k = threadIdx.x; k < s.n_shells; k += blockDim.x) {
@@ -72,7 +73,7 @@ __global__ void __launch_bounds__(256) k_basis_points(DevSystem s, const double 
 template <typename T>
 cudaError_t launch_basis_points(const DevSystem &s, bool propose, const double *r, int W, int e0, int npts,
                                 T *out, double *rprop, uint32_t walker0, uint32_t sweep,
-                                cudaStream_t st) {
+                                cudaStream_t st, const uint32_t *sweep_dev) {
   if (W <= 0 || npts <= 0) return cudaSuccess;
   const long total = (long)W * npts;
   const int warps = 8;
@@ -80,15 +81,17 @@ cudaError_t launch_basis_points(const DevSystem &s, bool propose, const double *
   if (blocks > 152 * 16) blocks = 152 * 16;
   const size_t smem = (size_t)s.n_shells * (sizeof(double4) + sizeof(int));
   if (propose)
-    k_basis_points<true, T><<<(int)blocks, warps * 32, smem, st>>>(s, r, W, e0, npts, out, rprop, walker0, sweep);
+    k_basis_points<true, T><<<(int)blocks, warps * 32, smem, st>>>(s, r, W, e0, npts, out, rprop, walker0, sweep,
+                                                                    sweep_dev);
   else
-    k_basis_points<false, T><<<(int)blocks, warps * 32, smem, st>>>(s, r, W, e0, npts, out, rprop, walker0, sweep);
+    k_basis_points<false, T><<<(int)blocks, warps * 32, smem, st>>>(s, r, W, e0, npts, out, rprop, walker0, sweep,
+                                                                     nullptr);
   return cudaGetLastError();
 }
 template cudaError_t launch_basis_points<double>(const DevSystem &, bool, const double *, int, int, int, double *,
-                                                 double *, uint32_t, uint32_t, cudaStream_t);
+                                                 double *, uint32_t, uint32_t, cudaStream_t, const uint32_t *);
 template cudaError_t launch_basis_points<float>(const DevSystem &, bool, const double *, int, int, int, float *,
-                                                double *, uint32_t, uint32_t, cudaStream_t);
+                                                double *, uint32_t, uint32_t, cudaStream_t, const uint32_t *);
 
 // ---------------------------------------------------------------------------
 // Block reduction of two doubles (blockDim.x <= 1024); result valid in thread 0.
@@ -480,7 +483,7 @@ cudaError_t launch_walker_info(const double *scal, const int *status, int W, dou
 // Per-sweep accumulators in a fixed reduction order (bitwise reproducible):
 // acc = (sum e_L, sum e_L^2, accepted moves of this sweep, max drift).
 __global__ void __launch_bounds__(1024) k_reduce_acc(const double *eL, const double *scal, const int *count,
-                                                     int W, double *acc) {
+                                                     int W, double *acc, int accumulate) {
   __shared__ double s1[1024], s2[1024], s3[1024];
   double a = 0.0, b = 0.0, d = 0.0;
   for (int w = threadIdx.x; w < W; w += blockDim.x) {
@@ -504,16 +507,33 @@ __global__ void __launch_bounds__(1024) k_reduce_acc(const double *eL, const dou
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    acc[0] = s1[0];
-    acc[1] = s2[0];
-    acc[2] = (double)count[0] + (double)count[1];
-    acc[3] = s3[0];
+    const double c = (double)count[0] + (double)count[1];
+    if (accumulate) {
+      acc[0] += s1[0];
+      acc[1] += s2[0];
+      acc[2] += c;
+      acc[3] = fmax(acc[3], s3[0]);
+    } else {
+      acc[0] = s1[0];
+      acc[1] = s2[0];
+      acc[2] = c;
+      acc[3] = s3[0];
+    }
   }
 }
 
 cudaError_t launch_reduce_acc(const double *eL, const double *scal, const int *count, int W, double *acc,
-                              cudaStream_t st) {
-  k_reduce_acc<<<1, 1024, 0, st>>>(eL, scal, count, W, acc);
+                              cudaStream_t st, int accumulate) {
+  k_reduce_acc<<<1, 1024, 0, st>>>(eL, scal, count, W, acc, accumulate);
+  return cudaGetLastError();
+}
+
+__global__ void k_increment(uint32_t *c, uint32_t by) {
+  if (threadIdx.x == 0) *c += by;
+}
+
+cudaError_t launch_increment(uint32_t *c, uint32_t by, cudaStream_t st) {
+  k_increment<<<1, 32, 0, st>>>(c, by);
   return cudaGetLastError();
 }
 
