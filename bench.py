@@ -375,6 +375,7 @@ def run_gpu(args):
 
     import paper_2002_07401_gb300 as pg
     import synth
+    from paper_2002_07401_gb300 import shard
 
     ws, rank, local = dist_env()
     if not torch.cuda.is_available():
@@ -388,8 +389,8 @@ def run_gpu(args):
     W = args.walkers
     N, L = sysm.N, sysm.L
     x_all = synth.init_walkers(sysm, W * ws, seed=0)
-    x0 = np.ascontiguousarray(x_all[rank * W:(rank + 1) * W])
-    walker0 = rank * W
+    walker0 = shard.walker_offset(W, rank)
+    x0 = np.ascontiguousarray(x_all[walker0:walker0 + W])
     mixed_primary = args.precision == "mixed"
     prec = pg.JAGP_PREC_MIXED if mixed_primary else pg.JAGP_PREC_FP64
 
