@@ -155,13 +155,15 @@ double *refresh_g(float *, const Layout &L, void *state) { return at<double>(sta
 // the local-energy sequence on a current state
 template <typename T>
 jagp_status_t run_local_energy(jagp_ctx *h, const double *r, void *state, int W, double *eL, double *parts,
-                               cudaStream_t st) {
+                               cudaStream_t st, bool write_jastrow = false) {
   const Layout L = layout_of(h, W);
   LAUNCH(JAGP_KERNEL_ENERGY, 1,
          launch_mmat<T>(h->ds, at<T>(state, L.ginv), at<T>(state, L.bt), at<T>(state, L.a_up), at<T>(state, L.mbuf), W,
                         st));
   LAUNCH(JAGP_KERNEL_ENERGY, 1, launch_kinetic<T>(h->ds, r, at<T>(state, L.mbuf), at<double>(state, L.kin), W, st));
-  LAUNCH(JAGP_KERNEL_ENERGY, 1, launch_elocal(h->ds, r, at<double>(state, L.kin), eL, parts, W, st));
+  LAUNCH(JAGP_KERNEL_ENERGY, 1,
+         launch_elocal(h->ds, r, at<double>(state, L.kin), eL, parts, W, st,
+                       write_jastrow ? at<double>(state, L.scal) : nullptr));
   return JAGP_OK;
 }
 
@@ -255,11 +257,12 @@ jagp_status_t run_sweeps(jagp_ctx *h, double *d_r, void *d_state, int W, int nsw
       s = lambda_products(h, pprop, bt, false, list, count + 1, 0, 1, 0, W * d.n_dn, d_state, W, st);
       if (s != JAGP_OK) return s;
     }
-    s = run_refresh<T>(h, d_r, d_state, W, 1, true, st);
-    if (s != JAGP_OK) return s;
     double *eL = d_eL ? d_eL + (accumulate ? 0 : (size_t)t * W) : nullptr;
+    // the local-energy pass also forms J, so the refresh skips its Jastrow pass then
+    s = run_refresh<T>(h, d_r, d_state, W, 1, eL == nullptr, st);
+    if (s != JAGP_OK) return s;
     if (eL) {
-      s = run_local_energy<T>(h, d_r, d_state, W, eL, nullptr, st);
+      s = run_local_energy<T>(h, d_r, d_state, W, eL, nullptr, st, true);
       if (s != JAGP_OK) return s;
     }
     if (d_acc)

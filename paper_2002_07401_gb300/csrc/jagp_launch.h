@@ -62,7 +62,7 @@ template <typename T>
 cudaError_t launch_kinetic(const DevSystem &s, const double *r, const T *mbuf, double *kin, int W,
                            cudaStream_t st);
 cudaError_t launch_elocal(const DevSystem &s, const double *r, const double *kin, double *eL,
-                          double *parts, int W, cudaStream_t st);
+                          double *parts, int W, cudaStream_t st, double *scal = nullptr);
 
 cudaError_t launch_walker_init(double *scal, int *status, int W, cudaStream_t st);
 cudaError_t launch_logpsi_out(const double *scal, int W, double *logabs, double *sign,

@@ -12,6 +12,15 @@ namespace jagp {
 // Orbital gradients and Laplacians at every electron contracted with that
 // electron's M vector (see k_mmat): one warp per electron, lanes over shells;
 // the derivative tables are never stored.
+//
+// Per shell the contraction needs only S0 = sum_c M_c P_c and Sg = sum_c M_c
+// grad P_c: the angular polynomials are harmonic and homogeneous of degree l
+// (grad P . d = l P), so for the Gaussian g = e^{-zeta r^2}
+//   sum_c M_c grad(P_c g) = g (Sg - 2 zeta S0 d),
+//   sum_c M_c lap(P_c g)  = g S0 (4 zeta^2 r^2 - (4l + 6) zeta),
+// and for the Slater g = e^{-zeta r}
+//   sum_c M_c grad(P_c g) = g (Sg - zeta S0 d / r),
+//   sum_c M_c lap(P_c g)  = g S0 (zeta^2 - 2 zeta (l + 1) / r).
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(256) k_kinetic(DevSystem s, const double *__restrict__ r,
@@ -33,20 +42,44 @@ __global__ void __launch_bounds__(256) k_kinetic(DevSystem s, const double *__re
     const T *M = mbuf + pt * s.L;
     T tx = T(0), ty = T(0), tz = T(0), tl = T(0);
     for (int k = lane; k < s.n_shells; k += 32) {
-      const double4 g = sh_geo[k];
+      const double4 g4 = sh_geo[k];
       const int info = sh_info[k];
-      T o[5][5];
-      const int nc = shell_derivs<T>(info, g.w, px - g.x, py - g.y, pz - g.z, o);
-      const int off = shell_off(info);
-#pragma unroll
-      for (int c = 0; c < 5; ++c) {
-        if (c >= nc) break;
-        const T m = M[off + c];
-        tx = fma(o[c][1], m, tx);
-        ty = fma(o[c][2], m, ty);
-        tz = fma(o[c][3], m, tz);
-        tl = fma(o[c][4], m, tl);
+      const int l = shell_l(info), off = shell_off(info);
+      const double dxd = px - g4.x, dyd = py - g4.y, dzd = pz - g4.z;
+      const double r2d = dxd * dxd + dyd * dyd + dzd * dzd;
+      const T g = radial_factor<T>(shell_rad(info), g4.w, r2d);
+      const T dx = static_cast<T>(dxd), dy = static_cast<T>(dyd), dz = static_cast<T>(dzd);
+      const T r2 = static_cast<T>(r2d), zeta = static_cast<T>(g4.w);
+      T S0, Sx, Sy, Sz;
+      if (l == 0) {
+        S0 = M[off];
+        Sx = Sy = Sz = T(0);
+      } else if (l == 1) {
+        const T m0 = M[off], m1 = M[off + 1], m2 = M[off + 2];
+        S0 = m0 * dx + m1 * dy + m2 * dz;
+        Sx = m0;
+        Sy = m1;
+        Sz = m2;
+      } else {
+        const T m0 = M[off], m1 = M[off + 1], m2 = M[off + 2], m3 = M[off + 3], m4 = M[off + 4];
+        S0 = m0 * dx * dy + m1 * dy * dz + m2 * dz * dx + m3 * (dx * dx - dy * dy) + m4 * (T(3) * dz * dz - r2);
+        Sx = m0 * dy + m2 * dz + T(2) * (m3 - m4) * dx;
+        Sy = m0 * dx + m1 * dz - T(2) * (m3 + m4) * dy;
+        Sz = m1 * dy + m2 * dx + T(4) * m4 * dz;
       }
+      T f, lapfac;
+      if (shell_rad(info)) {
+        const T rinv = T(1) / static_cast<T>(sqrt(r2d));
+        f = -zeta * S0 * rinv;
+        lapfac = zeta * zeta - T(2) * zeta * static_cast<T>(l + 1) * rinv;
+      } else {
+        f = T(-2) * zeta * S0;
+        lapfac = T(4) * zeta * zeta * r2 - static_cast<T>(4 * l + 6) * zeta;
+      }
+      tx = fma(g, fma(f, dx, Sx), tx);
+      ty = fma(g, fma(f, dy, Sy), ty);
+      tz = fma(g, fma(f, dz, Sz), tz);
+      tl = fma(g * S0, lapfac, tl);
     }
     // lane partials are summed in FP64
     const double gx = warp_sum(static_cast<double>(tx));
@@ -79,27 +112,42 @@ template cudaError_t launch_kinetic<float>(const DevSystem &, const double *, co
                                            cudaStream_t);
 
 // ---------------------------------------------------------------------------
-// Jastrow derivatives, kinetic assembly and the Coulomb terms: one CTA per walker.
+// Jastrow value and derivatives, kinetic assembly and the Coulomb terms: one
+// CTA per walker.  With scal given, J = J1 + J2 is written too (the sweep then
+// needs no separate Jastrow pass).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(128) k_elocal(DevSystem s, const double *__restrict__ r,
                                                 const double *__restrict__ kin, double *__restrict__ eL,
-                                                double *__restrict__ parts) {
+                                                double *__restrict__ parts, double *__restrict__ scal) {
   const int w = blockIdx.x, N = s.N, tid = threadIdx.x;
   extern __shared__ double xs[];
   for (int t = tid; t < N * 3; t += blockDim.x) xs[t] = r[(size_t)w * N * 3 + t];
   __syncthreads();
-  double tkin = 0.0, vee = 0.0, vei = 0.0;
+  double tkin = 0.0, vee = 0.0, vei = 0.0, jv = 0.0;
   for (int e = tid; e < N; e += blockDim.x) {
     const double ex = xs[3 * e], ey = xs[3 * e + 1], ez = xs[3 * e + 2];
     double gJx = 0.0, gJy = 0.0, gJz = 0.0, lJ = 0.0;
     for (int a = 0; a < s.n_atoms; ++a) {
       const double dx = ex - s.R[3 * a], dy = ey - s.R[3 * a + 1], dz = ez - s.R[3 * a + 2];
-      const double rr = sqrt(dx * dx + dy * dy + dz * dz);
-      vei -= s.Z[a] / rr;
+      const double r2 = dx * dx + dy * dy + dz * dz;
+      const double rinv = rsqrt(r2), rr = r2 * rinv;
+      vei -= s.Z[a] * rinv;
       if (s.use_j1) {
-        double fp, fpp;
-        j1_d(s.c1[a], s.b_ea, rr, &fp, &fpp);
-        const double q = fp / rr;
+        // f = -c^3 u(c r), u = (1 - e^{-b s}) / (2b); f' = -c^4 e / 2, f'' = c^5 b e / 2
+        const double c = s.c1[a], c3 = c * c * c, c4 = c3 * c, b = s.b_ea;
+        double f, fp, fpp;
+        if (b == 0.0) {
+          f = -0.5 * c4 * rr;
+          fp = -0.5 * c4;
+          fpp = 0.0;
+        } else {
+          const double ex1 = exp(-b * c * rr);
+          f = -c3 * (1.0 - ex1) / (2.0 * b);
+          fp = -0.5 * c4 * ex1;
+          fpp = 0.5 * c4 * c * b * ex1;
+        }
+        jv += f;
+        const double q = fp * rinv;
         gJx += q * dx;
         gJy += q * dy;
         gJz += q * dz;
@@ -109,15 +157,18 @@ __global__ void __launch_bounds__(128) k_elocal(DevSystem s, const double *__res
     for (int k = 0; k < N; ++k) {
       if (k == e) continue;
       const double dx = ex - xs[3 * k], dy = ey - xs[3 * k + 1], dz = ez - xs[3 * k + 2];
-      const double rr = sqrt(dx * dx + dy * dy + dz * dz);
-      if (k > e) vee += 1.0 / rr;
+      const double r2 = dx * dx + dy * dy + dz * dz;
+      const double rinv = rsqrt(r2), rr = r2 * rinv;
+      if (k > e) vee += rinv;
       if (s.use_j2) {
         double kk, bb;
         j2_params(s, (e < s.n_up) == (k < s.n_up), &kk, &bb);
-        const double q1 = 1.0 + bb * rr;
-        const double vp = 1.0 / (kk * q1 * q1);
-        const double vpp = -2.0 * bb / (kk * q1 * q1 * q1);
-        const double q = vp / rr;
+        const double ik = 1.0 / kk;  // exact: k is 2 or 4
+        const double iq = 1.0 / (1.0 + bb * rr);
+        const double vp = ik * iq * iq;
+        const double vpp = -2.0 * bb * vp * iq;
+        if (k > e) jv += rr * ik * iq;
+        const double q = vp * rinv;
         gJx += q * dx;
         gJy += q * dy;
         gJz += q * dz;
@@ -129,22 +180,25 @@ __global__ void __launch_bounds__(128) k_elocal(DevSystem s, const double *__res
                      (gJx * gJx + gJy * gJy + gJz * gJz);
     tkin += -0.5 * t;
   }
-  __shared__ double red[3][4];
+  __shared__ double red[4][4];
   tkin = warp_sum(tkin);
   vee = warp_sum(vee);
   vei = warp_sum(vei);
+  jv = warp_sum(jv);
   if ((tid & 31) == 0) {
     red[0][tid >> 5] = tkin;
     red[1][tid >> 5] = vee;
     red[2][tid >> 5] = vei;
+    red[3][tid >> 5] = jv;
   }
   __syncthreads();
   if (tid == 0) {
-    double a = 0.0, b = 0.0, c = 0.0;
+    double a = 0.0, b = 0.0, c = 0.0, j = 0.0;
     for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
       a += red[0][q];
       b += red[1][q];
       c += red[2][q];
+      j += red[3][q];
     }
     eL[w] = a + b + c + s.v_ii;
     if (parts) {
@@ -153,13 +207,14 @@ __global__ void __launch_bounds__(128) k_elocal(DevSystem s, const double *__res
       parts[(size_t)w * 4 + 2] = c;
       parts[(size_t)w * 4 + 3] = s.v_ii;
     }
+    if (scal) scal[(size_t)w * S_STRIDE + S_J] = j;
   }
 }
 
 cudaError_t launch_elocal(const DevSystem &s, const double *r, const double *kin, double *eL, double *parts, int W,
-                          cudaStream_t st) {
+                          cudaStream_t st, double *scal) {
   if (W <= 0) return cudaSuccess;
-  k_elocal<<<W, 128, (size_t)s.N * 3 * sizeof(double), st>>>(s, r, kin, eL, parts);
+  k_elocal<<<W, 128, (size_t)s.N * 3 * sizeof(double), st>>>(s, r, kin, eL, parts, scal);
   return cudaGetLastError();
 }
 
