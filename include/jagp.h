@@ -189,9 +189,9 @@ jagp_status_t jagp_walker_status(jagp_handle_t h, const void *d_state, int W, in
  *     C[rows[m]][n] = sum_{p < npairs} sum_{k < Kp} A[m][pair_a[p] Kp + k] * B[n][pair_b[p] Kp + k]
  *   fixed-point mode (both exponent arrays given): the terms are exact 8-bit
  *     integer slices, a = 2^(ea[m] - 7) sum_t A_t / 256^t (likewise b with
- *     eb[n]), pairs with equal pair_a + pair_b (<= 3) share an exactly summed
+ *     eb[n]), pairs with equal pair_a + pair_b (<= 4) share an exactly summed
  *     accumulator S_d, and C = 2^(ea + eb - 14) sum_d S_d / 256^d.
- * d_A: BF16 bits [M][a_terms Kp], d_B: BF16 bits [N][b_terms Kp] (up to four
+ * d_A: BF16 bits [M][a_terms Kp], d_B: BF16 bits [N][b_terms Kp] (up to five
  * terms per row side by side; Kp % 64 == 0; 16-byte aligned bases); d_C: FP32
  * with row pitch ldc >= N; d_rows: [M] destination rows or NULL (identity);
  * d_count: device int live row count (<= M) or NULL (= M); d_row_exp [M],

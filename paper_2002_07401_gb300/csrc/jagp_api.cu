@@ -67,32 +67,33 @@ Layout layout_of(const jagp_ctx *h, int W) {
                      mixed ? (size_t)h->kp : 0);
 }
 
-// the ten slice pairs (a, b) with a + b <= 3 of the four-slice fixed-point operands
-const int kPairA[10] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3};
-const int kPairB[10] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0};
+// the fifteen slice pairs (a, b) with a + b <= 4 of the five-slice fixed-point
+// operands (each row kept to 2^-39 of its largest magnitude)
+const int kPairA[kFixedPairs] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3, 0, 1, 2, 3, 4};
+const int kPairB[kFixedPairs] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0, 4, 3, 2, 1, 0};
 
 template <typename T>
 T *at(void *base, size_t off) {
   return reinterpret_cast<T *>(static_cast<char *>(base) + off);
 }
 
-// host: one row of FP64 values -> four exact 8-bit fixed-point slices (BF16 bits)
-// relative to 2^e, e = 1 + the binary exponent of the row's largest magnitude:
-// v = 2^(e - 7) (t0 + t1 / 256 + t2 / 256^2 + t3 / 256^3 + ...), |t| <= 128.
+// host: one row of FP64 values -> kFixedSlices exact 8-bit fixed-point slices
+// (BF16 bits) relative to 2^e, e = 1 + the binary exponent of the row's largest
+// magnitude: v = 2^(e - 7) (t0 + t1 / 256 + t2 / 256^2 + ...), |t| <= 128.
 uint16_t bf16_of_small_int(double q) {
   const float f = static_cast<float>(q);  // |q| <= 128: exact in BF16
   uint32_t u;
   memcpy(&u, &f, 4);
   return static_cast<uint16_t>(u >> 16);
 }
-int slice_row_fixed4(const double *v, size_t vstride, int L, uint16_t *dst, size_t kp) {
+int slice_row_fixed(const double *v, size_t vstride, int L, uint16_t *dst, size_t kp) {
   double mx = 0.0;
   for (int k = 0; k < L; ++k) mx = std::max(mx, std::fabs(v[k * vstride]));
   int e = 0;
   if (mx > 0.0) std::frexp(mx, &e);  // mx = f 2^e, f in [0.5, 1)
   for (int k = 0; k < L; ++k) {
     double x = std::ldexp(v[k * vstride], 7 - e);
-    for (int t = 0; t < 4; ++t) {
+    for (int t = 0; t < kFixedSlices; ++t) {
       const double q = std::nearbyint(x);
       dst[t * kp + k] = bf16_of_small_int(q);
       x = (x - q) * 256.0;
@@ -110,44 +111,47 @@ jagp_status_t check_walkers(const jagp_ctx *h, int W, const void *state) {
 
 // lambda products of orbital rows: out[row] = P[row]^T lambda (left) or lambda P[row] (!left)
 // for the listed rows (list/count) or the (nsub, stride) rows r < nrows.
-jagp_status_t lambda_products(jagp_ctx *h, const double *P, double *out, bool left, const int *list, const int *count,
-                              int nrows, int nsub, int stride, int max_rows, void *, int, cudaStream_t st) {
+jagp_status_t lambda_products(jagp_ctx *h, const double *P, const float *, double *out, bool left, const int *list,
+                              const int *count, int nrows, int nsub, int stride, int max_rows, void *, int,
+                              cudaStream_t st) {
   LAUNCH(JAGP_KERNEL_LAMBDA_ROWS, 1,
          launch_lambda_rows(P, left ? h->ds.lam : h->ds.lamT, out, list, count, nrows, nsub, stride, h->ds.L, max_rows,
                             st));
   return JAGP_OK;
 }
-jagp_status_t lambda_products(jagp_ctx *h, const float *P, float *out, bool left, const int *list, const int *count,
-                              int nrows, int nsub, int stride, int max_rows, void *state, int W, cudaStream_t st) {
-  // mixed path: cut the FP32 rows into fixed-point slices, then the exact
-  // tensor-core contraction against the sliced lambda
+jagp_status_t lambda_products(jagp_ctx *h, const float *P, const float *P_lo, float *out, bool left, const int *list,
+                              const int *count, int nrows, int nsub, int stride, int max_rows, void *state, int W,
+                              cudaStream_t st) {
+  // mixed path: cut the two-float rows P + P_lo into fixed-point slices, then
+  // the exact tensor-core contraction against the sliced lambda
   const Layout L = layout_of(h, W);
   uint16_t *pack = at<uint16_t>(state, L.pack);
   int *rows = at<int>(state, L.rows), *exps = at<int>(state, L.exps);
-  LAUNCH(0, 1, launch_pack_fixed4(P, list, count, nrows, nsub, stride, h->ds.L, h->kp, pack, rows, exps, max_rows, st));
+  LAUNCH(0, 1,
+         launch_pack_fixed(P, P_lo, list, count, nrows, nsub, stride, h->ds.L, h->kp, pack, rows, exps, max_rows,
+                            st));
   // Bt rows (lambda phi) also keep their low parts for the refresh of G~
   float *out_lo = left ? nullptr : at<float>(state, L.bt_lo);
   LAUNCH(JAGP_KERNEL_LAMBDA_ROWS, 1,
-         launch_umma_gemm(pack, max_rows, count, 4, left ? h->split_lamT : h->split_lam, h->ds.L, 4, h->kp, 10, kPairA,
-                          kPairB, out, h->ds.L, rows, h->d_err, st, exps, left ? h->exp_lamT : h->exp_lam, out_lo));
+         launch_umma_gemm(pack, max_rows, count, kFixedSlices, left ? h->split_lamT : h->split_lam, h->ds.L,
+                          kFixedSlices, h->kp, kFixedPairs, kPairA, kPairB, out, h->ds.L, rows, h->d_err, st, exps,
+                          left ? h->exp_lamT : h->exp_lam, out_lo));
   return JAGP_OK;
 }
 
 // G~ = Phi_up Bt^T at a refresh: plain FP64 products, or the compensated FP32 sum
-cudaError_t refresh_geminal(const double *phi, size_t pw, const double *bt, size_t bw, int n, int Lb, double *g, int W,
-                            cudaStream_t st) {
+cudaError_t refresh_geminal(const double *phi, const float *, size_t pw, const double *bt, const float *, size_t bw,
+                            int n, int Lb, double *g, int W, cudaStream_t st) {
   return launch_gemm_rows<double>(phi, pw, bt, bw, n, n, Lb, g, (size_t)n * n, n, W, st);
 }
-cudaError_t refresh_geminal(const float *phi, size_t pw, const float *bt, const float *bt_lo, size_t bw, int n, int Lb,
-                            double *g, int W, cudaStream_t st) {
-  return launch_gemm_rows_dot2(phi, pw, bt, bt_lo, bw, n, n, Lb, g, (size_t)n * n, n, W, st);
+cudaError_t refresh_geminal(const float *phi, const float *phi_lo, size_t pw, const float *bt, const float *bt_lo,
+                            size_t bw, int n, int Lb, double *g, int W, cudaStream_t st) {
+  return launch_gemm_rows_dot2(phi, phi_lo, pw, bt, bt_lo, bw, n, n, Lb, g, (size_t)n * n, n, W, st);
 }
-cudaError_t refresh_geminal(const double *phi, size_t pw, const double *bt, const double *, size_t bw, int n, int Lb,
-                            double *g, int W, cudaStream_t st) {
-  return refresh_geminal(phi, pw, bt, bw, n, Lb, g, W, st);
+// low parts of the two-float tables of the mixed path (none in the FP64 path)
+float *lo_table(const jagp_ctx *h, void *state, size_t off) {
+  return h->precision == JAGP_PREC_MIXED ? at<float>(state, off) : nullptr;
 }
-const double *low_part(double *, const Layout &, void *) { return nullptr; }
-const float *low_part(float *, const Layout &L, void *state) { return at<float>(state, L.bt_lo); }
 // where the refresh keeps G~: the FP64 table, or the FP64 side array of the FP32 path
 double *refresh_g(double *, const Layout &L, void *state) { return at<double>(state, L.gprop); }
 double *refresh_g(float *, const Layout &L, void *state) { return at<double>(state, L.g64); }
@@ -175,8 +179,8 @@ jagp_status_t run_refresh(jagp_ctx *h, const double *r, void *state, int W, int 
   const int n = h->ds.n_up, Lb = h->ds.L;
   double *gm = refresh_g(static_cast<T *>(nullptr), L, state);
   LAUNCH(JAGP_KERNEL_GEMM_ROWS, 1,
-         refresh_geminal(at<T>(state, L.phi_up), (size_t)n * Lb, at<T>(state, L.bt),
-                         low_part(static_cast<T *>(nullptr), L, state), (size_t)n * Lb, n, Lb, gm, W, st));
+         refresh_geminal(at<T>(state, L.phi_up), lo_table(h, state, L.phi_lo), (size_t)n * Lb, at<T>(state, L.bt),
+                         lo_table(h, state, L.bt_lo), (size_t)n * Lb, n, Lb, gm, W, st));
   LAUNCH(0, 1,
          launch_refresh_inverse<T>(gm, at<T>(state, L.ginv), at<double>(state, L.scal), at<int>(state, L.status), n,
                                    W, check_drift, h->drift_tol, st));
@@ -191,16 +195,18 @@ jagp_status_t run_eval(jagp_ctx *h, const double *d_r, int W, void *d_state, dou
   const DevSystem &d = h->ds;
   const int n = d.n_up;
   T *phi_up = at<T>(d_state, L.phi_up), *pprop = at<T>(d_state, L.pprop);
+  float *phi_lo = lo_table(h, d_state, L.phi_lo), *pprop_lo = lo_table(h, d_state, L.pprop_lo);
   LAUNCH(0, 1, launch_walker_init(at<double>(d_state, L.scal), at<int>(d_state, L.status), W, st));
-  LAUNCH(JAGP_KERNEL_BASIS, 1, launch_basis_points<T>(d, false, d_r, W, 0, n, phi_up, nullptr, 0, 0, st));
-  LAUNCH(JAGP_KERNEL_BASIS, d.n_dn > 0, launch_basis_points<T>(d, false, d_r, W, n, d.n_dn, pprop, nullptr, 0, 0, st));
+  LAUNCH(JAGP_KERNEL_BASIS, 1, launch_basis_points<T>(d, false, d_r, W, 0, n, phi_up, phi_lo, nullptr, 0, 0, st));
+  LAUNCH(JAGP_KERNEL_BASIS, d.n_dn > 0,
+         launch_basis_points<T>(d, false, d_r, W, n, d.n_dn, pprop, pprop_lo, nullptr, 0, 0, st));
   // A_up = Phi_up lambda (every row); Bt rows j < n_dn = lambda phi(r_j^dn)
-  jagp_status_t s = lambda_products(h, phi_up, at<T>(d_state, L.a_up), true, nullptr, nullptr, W * n, n, n, W * n,
-                                    d_state, W, st);
+  jagp_status_t s = lambda_products(h, phi_up, phi_lo, at<T>(d_state, L.a_up), true, nullptr, nullptr, W * n, n, n,
+                                    W * n, d_state, W, st);
   if (s != JAGP_OK) return s;
   if (d.n_dn > 0) {
-    s = lambda_products(h, pprop, at<T>(d_state, L.bt), false, nullptr, nullptr, W * d.n_dn, d.n_dn, n, W * d.n_dn,
-                        d_state, W, st);
+    s = lambda_products(h, pprop, pprop_lo, at<T>(d_state, L.bt), false, nullptr, nullptr, W * d.n_dn, d.n_dn, n,
+                        W * d.n_dn, d_state, W, st);
     if (s != JAGP_OK) return s;
   }
   LAUNCH(0, d.n_up > d.n_dn, launch_fill_unpaired<T>(d, at<T>(d_state, L.bt), W, st));
@@ -227,18 +233,21 @@ jagp_status_t run_sweeps(jagp_ctx *h, double *d_r, void *d_state, int W, int nsw
   T *pprop = at<T>(d_state, L.pprop), *gprop = at<T>(d_state, L.gprop);
   double *rprop = at<double>(d_state, L.rprop), *scal = at<double>(d_state, L.scal);
   int *status = at<int>(d_state, L.status), *list = at<int>(d_state, L.list), *count = at<int>(d_state, L.count);
+  float *phi_lo = lo_table(h, d_state, L.phi_lo), *pprop_lo = lo_table(h, d_state, L.pprop_lo);
   jagp_status_t s;
   for (int t = 0; t < nsweeps; ++t) {
     const uint32_t sw = (uint32_t)(sweep0 + (uint64_t)t);
     JAGP_CU(cudaMemsetAsync(count, 0, 2 * sizeof(int), st));
     // up electrons: rows of G~ against the frozen down-spin table Bt
     LAUNCH(JAGP_KERNEL_BASIS, 1,
-           launch_basis_points<T>(d, true, d_r, W, 0, n, pprop, rprop, (uint32_t)walker0, sw, st, sweep_dev));
+           launch_basis_points<T>(d, true, d_r, W, 0, n, pprop, pprop_lo, rprop, (uint32_t)walker0, sw, st,
+                                  sweep_dev));
     LAUNCH(JAGP_KERNEL_GEMM_ROWS, 1,
            launch_gemm_rows<T>(pprop, (size_t)n * Lb, bt, (size_t)n * Lb, n, n, Lb, gprop, (size_t)n * n, n, W, st));
     LAUNCH(JAGP_KERNEL_METROPOLIS, 1,
-           launch_metropolis<T>(d, true, d_r, rprop, gprop, ginv, scal, status, pprop, phi_up, list, count, W, st));
-    s = lambda_products(h, pprop, a_up, true, list, count, 0, 1, 0, W * n, d_state, W, st);
+           launch_metropolis<T>(d, true, d_r, rprop, gprop, ginv, scal, status, pprop, phi_up, list, count, W, st,
+                                pprop_lo, phi_lo));
+    s = lambda_products(h, pprop, pprop_lo, a_up, true, list, count, 0, 1, 0, W * n, d_state, W, st);
     if (s != JAGP_OK) return s;
     if (half_refresh && d.n_dn > 0) {
       s = run_refresh<T>(h, d_r, d_state, W, 1, false, st);
@@ -247,14 +256,15 @@ jagp_status_t run_sweeps(jagp_ctx *h, double *d_r, void *d_state, int W, int nsw
     if (d.n_dn > 0) {
       // down electrons: columns of G~ against the updated up-spin table A_up
       LAUNCH(JAGP_KERNEL_BASIS, 1,
-             launch_basis_points<T>(d, true, d_r, W, n, d.n_dn, pprop, rprop, (uint32_t)walker0, sw, st, sweep_dev));
+             launch_basis_points<T>(d, true, d_r, W, n, d.n_dn, pprop, pprop_lo, rprop, (uint32_t)walker0, sw, st,
+                                    sweep_dev));
       LAUNCH(JAGP_KERNEL_GEMM_ROWS, 1,
              launch_gemm_rows<T>(pprop, (size_t)n * Lb, a_up, (size_t)n * Lb, d.n_dn, n, Lb, gprop, (size_t)n * n, n,
                                  W, st));
       LAUNCH(JAGP_KERNEL_METROPOLIS, 1,
              launch_metropolis<T>(d, false, d_r, rprop, gprop, ginv, scal, status, pprop, phi_up, list, count + 1, W,
                                   st));
-      s = lambda_products(h, pprop, bt, false, list, count + 1, 0, 1, 0, W * d.n_dn, d_state, W, st);
+      s = lambda_products(h, pprop, pprop_lo, bt, false, list, count + 1, 0, 1, 0, W * d.n_dn, d_state, W, st);
       if (s != JAGP_OK) return s;
     }
     double *eL = d_eL ? d_eL + (accumulate ? 0 : (size_t)t * W) : nullptr;
@@ -321,7 +331,7 @@ jagp_status_t jagp_grad(jagp_handle_t h, const double *d_r, void *d_state, int W
   jagp_status_t s = check_walkers(h, W, d_state);
   if (s != JAGP_OK) return s;
   if (!d_r || !d_work || (reinterpret_cast<uintptr_t>(d_work) & 255u)) return JAGP_ERR_INVALID_ARG;
-  if (h->precision != JAGP_PREC_FP64) return JAGP_ERR_UNSUPPORTED;
+  if (h->precision != JAGP_PREC_FP64 || h->ds.n_up > kMaxUpGrad) return JAGP_ERR_UNSUPPORTED;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const DevSystem &d = h->ds;
   const int n = d.n_up, nd = d.n_dn, N = d.N, Lb = d.L;
@@ -403,6 +413,7 @@ jagp_status_t jagp_create(jagp_handle_t *out, const jagp_system_t *sys, const ja
   // record keeps the offset of its first function in the caller's order.
   int L = 0;
   std::vector<double4> geo;
+  std::vector<float4> geo_dw;
   std::vector<int> info, satom;
   std::vector<int> offset(sys->n_shells);
   for (int k = 0; k < sys->n_shells; ++k) {
@@ -418,6 +429,15 @@ jagp_status_t jagp_create(jagp_handle_t *out, const jagp_system_t *sys, const ja
         if (sys->shell_l[k] != l || sys->shell_radial[k] != rad) continue;
         const int a = sys->shell_atom[k];
         geo.push_back(make_double4(sys->R[3 * a], sys->R[3 * a + 1], sys->R[3 * a + 2], sys->shell_zeta[k]));
+        // the same record as double-words for the FP32 path: FP32 roundings, then the remainders
+        const double v4[4] = {sys->R[3 * a], sys->R[3 * a + 1], sys->R[3 * a + 2], sys->shell_zeta[k]};
+        float hi[4], lo[4];
+        for (int c = 0; c < 4; ++c) {
+          hi[c] = static_cast<float>(v4[c]);
+          lo[c] = static_cast<float>(v4[c] - static_cast<double>(hi[c]));
+        }
+        geo_dw.push_back(make_float4(hi[0], hi[1], hi[2], hi[3]));
+        geo_dw.push_back(make_float4(lo[0], lo[1], lo[2], lo[3]));
         info.push_back(l | (rad << 2) | (offset[k] << 8));
         satom.push_back(a);
       }
@@ -456,13 +476,14 @@ jagp_status_t jagp_create(jagp_handle_t *out, const jagp_system_t *sys, const ja
   auto take = [&](size_t bytes) { size_t r = off; off = align256(off + bytes); return r; };
   const size_t oR = take(na * 3 * 8), oZ = take(na * 8), oC = take(na * 8);
   const size_t oG = take(sys->n_shells * sizeof(double4)), oI = take(sys->n_shells * sizeof(int));
+  const size_t oGd = take(sys->n_shells * 2 * sizeof(float4));
   const size_t oSa = take(sys->n_shells * sizeof(int));
   const size_t oL = take((size_t)L * L * 8), oT = take((size_t)L * L * 8);
   const size_t oU = take((size_t)(k_unp > 0 ? k_unp : 1) * L * 8);
   // mixed path: lambda^T and lambda as fixed-point slices, rows padded to kp
   const bool mixed = opt->precision == JAGP_PREC_MIXED;
   const int kp = (L + 63) / 64 * 64;
-  const size_t split_bytes = mixed ? (size_t)L * 4 * kp * 2 : 0;
+  const size_t split_bytes = mixed ? (size_t)L * kFixedSlices * kp * 2 : 0;
   const size_t exp_bytes = mixed ? (size_t)L * 4 : 0;
   const size_t oSA = take(split_bytes), oSB = take(split_bytes), oXA = take(exp_bytes), oXB = take(exp_bytes);
   const size_t oE = take(16);
@@ -470,8 +491,9 @@ jagp_status_t jagp_create(jagp_handle_t *out, const jagp_system_t *sys, const ja
   std::vector<int> xA(mixed ? L : 0), xB(mixed ? L : 0);
   if (mixed) {
     for (int nn = 0; nn < L; ++nn) {
-      xA[nn] = slice_row_fixed4(sys->lambda + nn, (size_t)L, L, &sA[(size_t)nn * 4 * kp], (size_t)kp);  // column nn
-      xB[nn] = slice_row_fixed4(sys->lambda + (size_t)nn * L, 1, L, &sB[(size_t)nn * 4 * kp], (size_t)kp);  // row nn
+      // column nn, then row nn
+      xA[nn] = slice_row_fixed(sys->lambda + nn, (size_t)L, L, &sA[(size_t)nn * kFixedSlices * kp], (size_t)kp);
+      xB[nn] = slice_row_fixed(sys->lambda + (size_t)nn * L, 1, L, &sB[(size_t)nn * kFixedSlices * kp], (size_t)kp);
     }
   }
   if (cudaMalloc(&h->d_mem, off) != cudaSuccess) {
@@ -483,6 +505,8 @@ jagp_status_t jagp_create(jagp_handle_t *out, const jagp_system_t *sys, const ja
             cudaMemcpy(b + oZ, sys->Z, na * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
             cudaMemcpy(b + oC, c1.data(), na * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
             cudaMemcpy(b + oG, geo.data(), sys->n_shells * sizeof(double4), cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy(b + oGd, geo_dw.data(), sys->n_shells * 2 * sizeof(float4), cudaMemcpyHostToDevice) ==
+                cudaSuccess &&
             cudaMemcpy(b + oI, info.data(), sys->n_shells * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess &&
             cudaMemcpy(b + oSa, satom.data(), sys->n_shells * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess &&
             cudaMemcpy(b + oL, sys->lambda, (size_t)L * L * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
@@ -510,6 +534,7 @@ jagp_status_t jagp_create(jagp_handle_t *out, const jagp_system_t *sys, const ja
   d.Z = reinterpret_cast<const double *>(b + oZ);
   d.c1 = reinterpret_cast<const double *>(b + oC);
   d.shell_geo = reinterpret_cast<const double4 *>(b + oG);
+  d.shell_dw = reinterpret_cast<const float4 *>(b + oGd);
   d.shell_info = reinterpret_cast<const int *>(b + oI);
   d.shell_atom = reinterpret_cast<const int *>(b + oSa);
   d.lam = reinterpret_cast<const double *>(b + oL);
@@ -593,11 +618,11 @@ jagp_status_t jagp_gemm_bf16x(const uint16_t *d_A, int M, int a_terms, const uin
                               const int *d_col_exp, int *d_err, void *stream) {
   if (!d_A || !d_B || !d_C || !d_err || !h_pair_a || !h_pair_b) return JAGP_ERR_INVALID_ARG;
   if (M <= 0 || N <= 0 || Kp <= 0 || Kp % 64 != 0 || ldc < N || npairs < 1 || npairs > 16) return JAGP_ERR_INVALID_ARG;
-  if (a_terms < 1 || a_terms > 4 || b_terms < 1 || b_terms > 4) return JAGP_ERR_INVALID_ARG;
+  if (a_terms < 1 || a_terms > 5 || b_terms < 1 || b_terms > 5) return JAGP_ERR_INVALID_ARG;
   if ((d_row_exp == nullptr) != (d_col_exp == nullptr)) return JAGP_ERR_INVALID_ARG;
   if (d_row_exp)
     for (int p = 0; p < npairs; ++p)
-      if (h_pair_a[p] + h_pair_b[p] > 3) return JAGP_ERR_INVALID_ARG;
+      if (h_pair_a[p] + h_pair_b[p] > 4) return JAGP_ERR_INVALID_ARG;
   std::call_once(g_attr_once, [] {
     g_attr_err = setup_kernel_attributes();
     if (g_attr_err == cudaSuccess) g_attr_err = setup_walker_attributes();

@@ -7,12 +7,16 @@
 #include <stdint.h>
 
 #include "../../include/jagp.h"
+#include "dword.cuh"
 
 namespace jagp {
 
-constexpr int kMaxUp = 64;          // N_up handled with G~^{-1} resident in shared memory
+constexpr int kMaxUp = 1024;        // largest N_up accepted (G~^{-1} leaves shared memory above ~160)
+constexpr int kMaxUpGrad = 64;     // largest N_up of the adjoint (its G~-sized tables stay in shared memory)
 constexpr int kWarp = 32;
 constexpr int kPropStride = 8;     // doubles per proposal record
+constexpr int kFixedSlices = 5;    // 8-bit slices per element of the fixed-point lambda products (mixed path)
+constexpr int kFixedPairs = 15;    // slice pairs (a, b) with a + b < kFixedSlices
 
 // Shell record packed for one 32-byte load: centre (x, y, z) and exponent.
 // info = l | radial << 2 | first-function-offset << 8.
@@ -22,6 +26,7 @@ struct DevSystem {
   const double *Z;          // [n_atoms]
   const double *c1;         // (2 Z_a)^{1/4}
   const double4 *shell_geo; // [n_shells]
+  const float4 *shell_dw;   // [n_shells][2]: (x, y, z, zeta) rounded to FP32, then the remainders
   const int *shell_info;    // [n_shells]
   const int *shell_atom;    // [n_shells] owning atom, in the same (evaluation) order
   const double *lam;        // [L][L]
@@ -52,11 +57,13 @@ struct Layout {
   size_t status;   // int    [W]
   size_t list;     // int    [W][n_up]       accepted moves of a half-sweep
   size_t count;    // int    [4]
-  size_t pack;     // BF16   [W n_up][4 kp]  mixed path: fixed-point slices of the lambda-product rows
+  size_t pack;     // BF16   [W n_up][5 kp]  mixed path: fixed-point slices of the lambda-product rows
   size_t rows;     // int    [W n_up]        mixed path: destination rows of the packed operand
   size_t exps;     // int    [W n_up]        mixed path: row exponents of the packed operand
   size_t g64;      // double [W][n_up][n_up] mixed path: G~ at a refresh (FP64 result of the compensated sum)
   size_t bt_lo;    // float  [W][n_up][L]    mixed path: low parts of Bt (Bt + bt_lo is a two-float table)
+  size_t phi_lo;   // float  [W][n_up][L]    mixed path: low parts of phi_up
+  size_t pprop_lo; // float  [W][n_up][L]    mixed path: low parts of pprop
   size_t total;
 };
 
@@ -82,11 +89,13 @@ inline Layout make_layout(size_t W, size_t nu, size_t N, size_t L, size_t esz = 
   l.status = take(W * 4);
   l.list = take(W * nu * 4);
   l.count = take(16);
-  l.pack = take(W * nu * 4 * kp * 2);
+  l.pack = take(W * nu * kFixedSlices * kp * 2);
   l.rows = take(kp ? W * nu * 4 : 0);
   l.exps = take(kp ? W * nu * 4 : 0);
   l.g64 = take(esz == 4 ? W * nu * nu * 8 : 0);
   l.bt_lo = take(esz == 4 ? W * nu * L * 4 : 0);
+  l.phi_lo = take(esz == 4 ? W * nu * L * 4 : 0);
+  l.pprop_lo = take(esz == 4 ? W * nu * L * 4 : 0);
   l.total = o;
   return l;
 }
@@ -136,38 +145,17 @@ __device__ __forceinline__ int shell_rad(int info) { return (info >> 2) & 1; }
 __device__ __forceinline__ int shell_off(int info) { return info >> 8; }
 
 // Radial factor g = e^{-zeta r^2} (Gaussian) or e^{-zeta r} (Slater) from the
-// FP64 squared distance.  FP64: the library exp.  FP32 (mixed path): the
-// exponent x is formed in FP64 and split x = x_hi + x_lo (x_hi its FP32
-// rounding), and g = exp_f32(x_hi) (1 + x_lo): FP32 relative accuracy even for
-// large |x|, where rounding the argument itself to FP32 would not be.
-template <typename T>
-__device__ __forceinline__ T radial_factor(int rad, double zeta, double r2);
-template <>
-__device__ __forceinline__ double radial_factor<double>(int rad, double zeta, double r2) {
+// FP64 squared distance (FP64 path).
+__device__ __forceinline__ double radial_factor(int rad, double zeta, double r2) {
   return rad ? exp(-zeta * sqrt(r2)) : exp(-zeta * r2);
 }
-template <>
-__device__ __forceinline__ float radial_factor<float>(int rad, double zeta, double r2) {
-  const double x = rad ? -zeta * sqrt(r2) : -zeta * r2;
-  const float xh = static_cast<float>(x);
-  const float xl = static_cast<float>(x - static_cast<double>(xh));
-  return expf(xh) * (1.0f + xl);
-}
 
-// values only, at the FP64 displacement (dx, dy, dz) from the shell's atom;
-// returns the number of components written to v.  FP32 values: the radial
-// factor exp(x_hi)(1 + x_lo) and the angular polynomial are multiplied in FP64
-// and rounded once, so each value carries the FP32 exponential's error and a
-// single rounding.
-template <typename T>
-__device__ __forceinline__ int shell_values(int info, double zeta, double dx, double dy, double dz, T v[5]);
-
-template <>
-__device__ __forceinline__ int shell_values<double>(int info, double zeta, double dx, double dy, double dz,
-                                                    double v[5]) {
+// FP64 path: values only, at the displacement (dx, dy, dz) from the shell's
+// atom; returns the number of components written to v.
+__device__ __forceinline__ int shell_values(int info, double zeta, double dx, double dy, double dz, double v[5]) {
   const int l = shell_l(info);
   const double r2 = dx * dx + dy * dy + dz * dz;
-  const double g = radial_factor<double>(shell_rad(info), zeta, r2);
+  const double g = radial_factor(shell_rad(info), zeta, r2);
   if (l == 0) {
     v[0] = g;
     return 1;
@@ -186,68 +174,95 @@ __device__ __forceinline__ int shell_values<double>(int info, double zeta, doubl
   return 5;
 }
 
-template <>
-__device__ __forceinline__ int shell_values<float>(int info, double zeta, double dx, double dy, double dz,
-                                                   float v[5]) {
-  const int l = shell_l(info);
-  const double r2 = dx * dx + dy * dy + dz * dz;
-  const double x = shell_rad(info) ? -zeta * sqrt(r2) : -zeta * r2;
-  const float xh = static_cast<float>(x);
-  const float xl = static_cast<float>(x - static_cast<double>(xh));
-  const double g = static_cast<double>(expf(xh)) * (1.0 + static_cast<double>(xl));
-  if (l == 0) {
-    v[0] = static_cast<float>(g);
-    return 1;
-  }
-  if (l == 1) {
-    v[0] = static_cast<float>(dx * g);
-    v[1] = static_cast<float>(dy * g);
-    v[2] = static_cast<float>(dz * g);
-    return 3;
-  }
-  v[0] = static_cast<float>(dx * dy * g);
-  v[1] = static_cast<float>(dy * dz * g);
-  v[2] = static_cast<float>(dz * dx * g);
-  v[3] = static_cast<float>((dx * dx - dy * dy) * g);
-  v[4] = static_cast<float>((3.0 * dz * dz - r2) * g);
-  return 5;
+// FP32 path: the displacement d = r - R_a of a point from the shell's atom in
+// double-word, from the point's and the atom's double-word coordinates (the
+// atom's split once on the host: geo_hi = (x, y, z, zeta) rounded to FP32,
+// geo_lo = the remainders).
+struct DwDisp {
+  fdw x, y, z, r2;
+};
+__device__ __forceinline__ DwDisp dw_displacement(const fdw p[3], float4 geo_hi, float4 geo_lo) {
+  DwDisp d;
+  d.x = dw_add(p[0], fdw{-geo_hi.x, -geo_lo.x});
+  d.y = dw_add(p[1], fdw{-geo_hi.y, -geo_lo.y});
+  d.z = dw_add(p[2], fdw{-geo_hi.z, -geo_lo.z});
+  d.r2 = dw_add(dw_add(dw_mul(d.x, d.x), dw_mul(d.y, d.y)), dw_mul(d.z, d.z));
+  return d;
 }
 
-// values, gradients and Laplacians: out[c] = {v, gx, gy, gz, lap}
-template <typename T>
-__device__ __forceinline__ int shell_derivs(int info, double zeta_d, double dxd, double dyd, double dzd,
-                                            T out[5][5]) {
+// the radial factor as a double-word (relative error ~2e-9)
+__device__ __forceinline__ fdw radial_dw(int rad, fdw zeta, fdw r2) {
+  return dw_exp_neg(dw_neg(dw_mul(zeta, rad ? dw_sqrt(r2) : r2)));
+}
+
+// FP32 path: the shell's values as double-words; v[c] (hi) is the value
+// rounded to FP32 (within half an ulp plus ~2e-9 relative), vlo[c] the rest.
+__device__ __forceinline__ int shell_values_dw(int info, fdw zeta, const DwDisp &d, float v[5], float vlo[5]) {
   const int l = shell_l(info);
-  const double r2d = dxd * dxd + dyd * dyd + dzd * dzd;
-  const T zeta = static_cast<T>(zeta_d), dx = static_cast<T>(dxd), dy = static_cast<T>(dyd), dz = static_cast<T>(dzd);
-  const T r2 = static_cast<T>(r2d);
-  const T g = radial_factor<T>(shell_rad(info), zeta_d, r2d);
-  T gg[3], lapg;
-  if (shell_rad(info)) {
-    const T r = static_cast<T>(sqrt(r2d));
-    const T f = -zeta / r * g;
-    gg[0] = f * dx;
-    gg[1] = f * dy;
-    gg[2] = f * dz;
-    lapg = (zeta * zeta - T(2) * zeta / r) * g;
-  } else {
-    const T f = T(-2) * zeta * g;
-    gg[0] = f * dx;
-    gg[1] = f * dy;
-    gg[2] = f * dz;
-    lapg = (T(4) * zeta * zeta * r2 - T(6) * zeta) * g;
+  const fdw g = radial_dw(shell_rad(info), zeta, d.r2);
+  if (l == 0) {
+    v[0] = g.hi;
+    vlo[0] = g.lo;
+    return 1;
   }
-  const T d[3] = {dx, dy, dz};
+  fdw p[5];
+  int nc;
+  if (l == 1) {
+    p[0] = d.x;
+    p[1] = d.y;
+    p[2] = d.z;
+    nc = 3;
+  } else {
+    const fdw xx = dw_mul(d.x, d.x), yy = dw_mul(d.y, d.y), zz = dw_mul(d.z, d.z);
+    p[0] = dw_mul(d.x, d.y);
+    p[1] = dw_mul(d.y, d.z);
+    p[2] = dw_mul(d.z, d.x);
+    p[3] = dw_add(xx, dw_neg(yy));
+    p[4] = dw_add(dw_mul_f(zz, 3.0f), dw_neg(d.r2));
+    nc = 5;
+  }
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    if (c >= nc) break;
+    const fdw t = dw_mul(p[c], g);
+    v[c] = t.hi;
+    vlo[c] = t.lo;
+  }
+  return nc;
+}
+
+// FP64 path: values, gradients and Laplacians: out[c] = {v, gx, gy, gz, lap}
+__device__ __forceinline__ int shell_derivs(int info, double zeta, double dx, double dy, double dz,
+                                            double out[5][5]) {
+  const int l = shell_l(info);
+  const double r2 = dx * dx + dy * dy + dz * dz;
+  const double g = radial_factor(shell_rad(info), zeta, r2);
+  double gg[3], lapg;
+  if (shell_rad(info)) {
+    const double r = sqrt(r2);
+    const double f = -zeta / r * g;
+    gg[0] = f * dx;
+    gg[1] = f * dy;
+    gg[2] = f * dz;
+    lapg = (zeta * zeta - 2.0 * zeta / r) * g;
+  } else {
+    const double f = -2.0 * zeta * g;
+    gg[0] = f * dx;
+    gg[1] = f * dy;
+    gg[2] = f * dz;
+    lapg = (4.0 * zeta * zeta * r2 - 6.0 * zeta) * g;
+  }
+  const double d[3] = {dx, dy, dz};
   const int nc = 2 * l + 1;
 #pragma unroll
   for (int c = 0; c < 5; ++c) {
     if (c >= nc) break;
-    T P, gP[3] = {T(0), T(0), T(0)};
+    double P, gP[3] = {0.0, 0.0, 0.0};
     if (l == 0) {
-      P = T(1);
+      P = 1.0;
     } else if (l == 1) {
       P = d[c];
-      gP[c] = T(1);
+      gP[c] = 1.0;
     } else if (c == 0) {
       P = dx * dy; gP[0] = dy; gP[1] = dx;
     } else if (c == 1) {
@@ -255,15 +270,15 @@ __device__ __forceinline__ int shell_derivs(int info, double zeta_d, double dxd,
     } else if (c == 2) {
       P = dz * dx; gP[0] = dz; gP[2] = dx;
     } else if (c == 3) {
-      P = dx * dx - dy * dy; gP[0] = T(2) * dx; gP[1] = T(-2) * dy;
+      P = dx * dx - dy * dy; gP[0] = 2.0 * dx; gP[1] = -2.0 * dy;
     } else {
-      P = T(3) * dz * dz - r2; gP[0] = T(-2) * dx; gP[1] = T(-2) * dy; gP[2] = T(4) * dz;
+      P = 3.0 * dz * dz - r2; gP[0] = -2.0 * dx; gP[1] = -2.0 * dy; gP[2] = 4.0 * dz;
     }
     out[c][0] = P * g;
     out[c][1] = gP[0] * g + P * gg[0];
     out[c][2] = gP[1] * g + P * gg[1];
     out[c][3] = gP[2] * g + P * gg[2];
-    out[c][4] = T(2) * (gP[0] * gg[0] + gP[1] * gg[1] + gP[2] * gg[2]) + P * lapg;
+    out[c][4] = 2.0 * (gP[0] * gg[0] + gP[1] * gg[1] + gP[2] * gg[2]) + P * lapg;
   }
   return nc;
 }
@@ -300,6 +315,34 @@ __device__ __forceinline__ void j2_params(const DevSystem &s, bool same, double 
   }
 }
 __device__ __forceinline__ double j2_val(double k, double b, double r) { return r / (k * (1.0 + b * r)); }
+
+// Two-body Jastrow change when electron e (spin UP) moves from (ox, oy, oz) to
+// (px, py, pz), summed over the other electrons k = k0, k0 + dk, ... < N at
+// positions xs.  FP64 path in FP64; FP32 path with FP32 distances (the value
+// only enters the acceptance test; J itself is recomputed in FP64).
+template <typename T, bool UP>
+__device__ __forceinline__ double j2_move_change(const DevSystem &s, const double *xs, int e, double px, double py,
+                                                 double pz, double ox, double oy, double oz, int k0, int dk) {
+  double pj = 0.0;
+  for (int k = k0; k < s.N; k += dk) {
+    if (k == e) continue;
+    double kk, bb;
+    j2_params(s, (k < s.n_up) == UP, &kk, &bb);
+    const double qx = xs[3 * k], qy = xs[3 * k + 1], qz = xs[3 * k + 2];
+    if constexpr (sizeof(T) == 8) {
+      const double dn = sqrt((px - qx) * (px - qx) + (py - qy) * (py - qy) + (pz - qz) * (pz - qz));
+      const double d0 = sqrt((ox - qx) * (ox - qx) + (oy - qy) * (oy - qy) + (oz - qz) * (oz - qz));
+      pj += j2_val(kk, bb, dn) - j2_val(kk, bb, d0);
+    } else {
+      const float ax = static_cast<float>(px - qx), ay = static_cast<float>(py - qy), az = static_cast<float>(pz - qz);
+      const float bx = static_cast<float>(ox - qx), by = static_cast<float>(oy - qy), bz = static_cast<float>(oz - qz);
+      const float dn = sqrtf(ax * ax + ay * ay + az * az), d0 = sqrtf(bx * bx + by * by + bz * bz);
+      const float ik = static_cast<float>(1.0 / kk), b = static_cast<float>(bb);
+      pj += static_cast<double>(ik * (__fdividef(dn, 1.0f + b * dn) - __fdividef(d0, 1.0f + b * d0)));
+    }
+  }
+  return pj;
+}
 
 // ---------------------------------------------------------------------------
 // reductions

@@ -10,27 +10,32 @@ namespace jagp {
 
 // Orbital values at electron positions (PROPOSE = false) or at freshly drawn
 // proposals (PROPOSE = true, also writes rprop).  Rows go to
-// out[(w * n_up + i) * L], i < npts, for electrons e0 .. e0 + npts - 1.
+// out[(w * n_up + i) * L], i < npts, for electrons e0 .. e0 + npts - 1; in the
+// FP32 path out_lo (same layout, may be null) gets the low parts.
 template <typename T>
 cudaError_t launch_basis_points(const DevSystem &s, bool propose, const double *r, int W, int e0,
-                                int npts, T *out, double *rprop, uint32_t walker0,
+                                int npts, T *out, float *out_lo, double *rprop, uint32_t walker0,
                                 uint32_t sweep, cudaStream_t st, const uint32_t *sweep_dev = nullptr);
 
 // Sequential Metropolis over one spin species with Sherman-Morrison updates.
+// Accepted up moves copy their proposal row of pprop (and pprop_lo, when given)
+// into phi_up (phi_lo).
 template <typename T>
 cudaError_t launch_metropolis(const DevSystem &s, bool up, double *r, const double *rprop, const T *gprop,
                               T *ginv, double *scal, int *status, const T *pprop, T *phi_up, int *list,
-                              int *count, int W, cudaStream_t st);
+                              int *count, int W, cudaStream_t st, const float *pprop_lo = nullptr,
+                              float *phi_lo = nullptr);
 
 // Out[w][a][b] = sum_k X[w][a][k] Y[w][b][k]  (a < ma, b < nb, k < K); row stride K.
 template <typename T>
 cudaError_t launch_gemm_rows(const T *X, size_t xw, const T *Y, size_t yw, int ma, int nb, int K, T *Out,
                              size_t ow, int ldo, int W, cudaStream_t st);
 
-// FP32 variant with a compensated (error-free transformation) dot product; Y may
-// carry a low part Ylo (same layout) so that Y + Ylo is a two-float operand
-cudaError_t launch_gemm_rows_dot2(const float *X, size_t xw, const float *Y, const float *Ylo, size_t yw, int ma,
-                                  int nb, int K, double *Out, size_t ow, int ldo, int W, cudaStream_t st);
+// FP32 variant with a compensated (error-free transformation) dot product; X and
+// Y may carry low parts Xlo, Ylo (same layouts) so that they are two-float operands
+cudaError_t launch_gemm_rows_dot2(const float *X, const float *Xlo, size_t xw, const float *Y, const float *Ylo,
+                                  size_t yw, int ma, int nb, int K, double *Out, size_t ow, int ldo, int W,
+                                  cudaStream_t st);
 // low parts of the unpaired-orbital rows of Bt (two-float table of the FP32 path)
 cudaError_t launch_fill_unpaired_lo(const DevSystem &s, float *bt_lo, int W, cudaStream_t st);
 
@@ -47,7 +52,7 @@ cudaError_t launch_fill_unpaired(const DevSystem &s, T *bt, int W, cudaStream_t 
 // Gauss-Jordan inverse with partial pivoting of G~ (in gm), log|det|, sign and
 // the Sherman-Morrison drift against the inverse held in ginv.
 template <typename T>
-cudaError_t launch_refresh_inverse(const double *gm, T *ginv, double *scal, int *status, int n, int W,
+cudaError_t launch_refresh_inverse(double *gm, T *ginv, double *scal, int *status, int n, int W,
                                    int check_drift, double drift_tol, cudaStream_t st);
 
 cudaError_t launch_jastrow_full(const DevSystem &s, const double *r, double *scal, int W,
@@ -86,9 +91,11 @@ cudaError_t launch_umma_gemm(const uint16_t *A, int m_max, const int *m_dev, int
                              int b_terms, int kp, int npairs, const int *pair_a, const int *pair_b, float *out,
                              long long ldo, const int *out_rows, int *err, cudaStream_t st,
                              const int *a_exp = nullptr, const int *b_exp = nullptr, float *out_lo = nullptr);
-// FP32 rows -> four exact 8-bit slices per element (BF16) plus a row exponent
-cudaError_t launch_pack_fixed4(const float *P, const int *list, const int *count, int nrows, int nsub, int stride,
-                               int L, int kp, uint16_t *A, int *rows_out, int *exps, int max_rows, cudaStream_t st);
+// FP32 rows (two-float rows P + P_lo when P_lo is given) -> kFixedSlices exact
+// 8-bit slices per element (BF16) plus a row exponent
+cudaError_t launch_pack_fixed(const float *P, const float *P_lo, const int *list, const int *count, int nrows,
+                               int nsub, int stride, int L, int kp, uint16_t *A, int *rows_out, int *exps,
+                               int max_rows, cudaStream_t st);
 cudaError_t setup_umma_attributes();
 // FP32 rows -> compact three-term BF16 operand rows (see k_umma.cu)
 cudaError_t launch_pack_split3(const float *P, const int *list, const int *count, int nrows, int nsub, int stride,

@@ -106,8 +106,8 @@ extern "C" jagp_status_t jagp_eval_noalloc(jagp_handle_t h, const double *d_r, i
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   // the same sequence as jagp_eval, on the static scratch
   NA_CU(launch_walker_init(scal, status, W, st));
-  NA_CU(launch_basis_points(d, false, d_r, W, 0, n, phi_up, nullptr, 0, 0, st));
-  NA_CU(launch_basis_points(d, false, d_r, W, n, d.n_dn, pprop, nullptr, 0, 0, st));
+  NA_CU(launch_basis_points(d, false, d_r, W, 0, n, phi_up, nullptr, nullptr, 0, 0, st));
+  NA_CU(launch_basis_points(d, false, d_r, W, n, d.n_dn, pprop, nullptr, nullptr, 0, 0, st));
   NA_CU(launch_lambda_rows(phi_up, d.lam, a_up, nullptr, nullptr, W * n, n, n, Lb, W * n, st));
   if (d.n_dn > 0)
     NA_CU(launch_lambda_rows(pprop, d.lamT, bt, nullptr, nullptr, W * d.n_dn, d.n_dn, n, Lb, W * d.n_dn, st));

@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(256) k_adj_kvec(DevSystem s, const double *__r
       const double4 g = sh_geo[k];
       const int info = sh_info[k];
       double o[5][5];
-      const int nc = shell_derivs<double>(info, g.w, ex - g.x, ey - g.y, ez - g.z, o);
+      const int nc = shell_derivs(info, g.w, ex - g.x, ey - g.y, ez - g.z, o);
       const int off = shell_off(info);
       for (int c = 0; c < nc; ++c) {
         kb[off + c] = se * (-0.5 * o[c][4] - (o[c][1] * gx + o[c][2] * gy + o[c][3] * gz));

@@ -4,6 +4,8 @@
 //   e_L = -1/2 sum_i lap_i Psi/Psi - sum_{i,a} Z_a/r_ia + sum_{i<j} 1/r_ij + sum_{a<b} Z_a Z_b/R_ab.
 #include <math.h>
 
+#include <type_traits>
+
 #include "jagp_launch.h"
 
 namespace jagp {
@@ -21,15 +23,26 @@ namespace jagp {
 // and for the Slater g = e^{-zeta r}
 //   sum_c M_c grad(P_c g) = g (Sg - zeta S0 d / r),
 //   sum_c M_c lap(P_c g)  = g S0 (zeta^2 - 2 zeta (l + 1) / r).
+//
+// FP64 path: FP64 throughout.  FP32 path: the displacement, r^2 and the radial
+// factor in double-word (FP32 instructions only, see dword.cuh) so that g is
+// accurate before its rounding; the polynomial contraction in FP32.
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(256) k_kinetic(DevSystem s, const double *__restrict__ r,
                                                  const T *__restrict__ mbuf, double *__restrict__ kin,
                                                  int W) {
+  constexpr bool kDw = std::is_same<T, float>::value;
   extern __shared__ double4 sh_geo[];
   int *sh_info = reinterpret_cast<int *>(sh_geo + s.n_shells);
+  float4 *sh_dw = reinterpret_cast<float4 *>(sh_geo);
   for (int k = threadIdx.x; k < s.n_shells; k += blockDim.x) {
-    sh_geo[k] = s.shell_geo[k];
+    if constexpr (kDw) {
+      sh_dw[2 * k] = s.shell_dw[2 * k];
+      sh_dw[2 * k + 1] = s.shell_dw[2 * k + 1];
+    } else {
+      sh_geo[k] = s.shell_geo[k];
+    }
     sh_info[k] = s.shell_info[k];
   }
   __syncthreads();
@@ -39,17 +52,40 @@ __global__ void __launch_bounds__(256) k_kinetic(DevSystem s, const double *__re
   for (long pt = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); pt < total; pt += nwarps) {
     const double *rr = r + pt * 3;
     const double px = rr[0], py = rr[1], pz = rr[2];
+    fdw pd[3];
+    if constexpr (kDw) {
+      pd[0] = dw_of(px);
+      pd[1] = dw_of(py);
+      pd[2] = dw_of(pz);
+    }
     const T *M = mbuf + pt * s.L;
     T tx = T(0), ty = T(0), tz = T(0), tl = T(0);
     for (int k = lane; k < s.n_shells; k += 32) {
-      const double4 g4 = sh_geo[k];
       const int info = sh_info[k];
-      const int l = shell_l(info), off = shell_off(info);
-      const double dxd = px - g4.x, dyd = py - g4.y, dzd = pz - g4.z;
-      const double r2d = dxd * dxd + dyd * dyd + dzd * dzd;
-      const T g = radial_factor<T>(shell_rad(info), g4.w, r2d);
-      const T dx = static_cast<T>(dxd), dy = static_cast<T>(dyd), dz = static_cast<T>(dzd);
-      const T r2 = static_cast<T>(r2d), zeta = static_cast<T>(g4.w);
+      const int l = shell_l(info), off = shell_off(info), rad = shell_rad(info);
+      T g, dx, dy, dz, r2, zeta, rinv = T(0);
+      if constexpr (kDw) {
+        const float4 gh = sh_dw[2 * k], gl = sh_dw[2 * k + 1];
+        const DwDisp d = dw_displacement(pd, gh, gl);
+        const fdw zw{gh.w, gl.w};
+        const fdw rw = rad ? dw_sqrt(d.r2) : fdw{0.0f, 0.0f};
+        g = dw_exp_neg(dw_neg(dw_mul(zw, rad ? rw : d.r2))).hi;
+        dx = d.x.hi;
+        dy = d.y.hi;
+        dz = d.z.hi;
+        r2 = d.r2.hi;
+        zeta = gh.w;
+        if (rad) rinv = 1.0f / rw.hi;
+      } else {
+        const double4 g4 = sh_geo[k];
+        dx = px - g4.x;
+        dy = py - g4.y;
+        dz = pz - g4.z;
+        r2 = dx * dx + dy * dy + dz * dz;
+        zeta = g4.w;
+        g = radial_factor(rad, zeta, r2);
+        if (rad) rinv = 1.0 / sqrt(r2);
+      }
       T S0, Sx, Sy, Sz;
       if (l == 0) {
         S0 = M[off];
@@ -68,8 +104,7 @@ __global__ void __launch_bounds__(256) k_kinetic(DevSystem s, const double *__re
         Sz = m1 * dy + m2 * dx + T(4) * m4 * dz;
       }
       T f, lapfac;
-      if (shell_rad(info)) {
-        const T rinv = T(1) / static_cast<T>(sqrt(r2d));
+      if (rad) {
         f = -zeta * S0 * rinv;
         lapfac = zeta * zeta - T(2) * zeta * static_cast<T>(l + 1) * rinv;
       } else {

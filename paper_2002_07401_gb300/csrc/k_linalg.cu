@@ -44,20 +44,21 @@ __global__ void __launch_bounds__(256) k_gemm_rows(const T *__restrict__ X, size
 
 // The refresh's G~ = Phi_up Bt^T in the FP32 path: the same tile scheme with a
 // compensated dot product (error-free product by fma, error-free sum, the
-// errors summed separately; Ogita, Rump and Oishi 2005), so that the FP32
-// tables give G~ to about FP32 rounding instead of the O(K eps) drift of a
-// plain FP32 sum.  The _rn intrinsics keep the compiler from fusing the steps.
-__global__ void __launch_bounds__(256) k_gemm_rows_dot2(const float *__restrict__ X, size_t xw,
-                                                        const float *__restrict__ Y, const float *__restrict__ Ylo,
-                                                        size_t yw, int ma, int nb, int K, double *__restrict__ Out,
-                                                        size_t ow, int ldo) {
+// errors summed separately; Ogita, Rump and Oishi 2005) over two-float
+// operands X + Xlo and Y + Ylo (the low parts' products with the high parts go
+// into the error sum; lo * lo is below the result's precision), so that G~ is
+// as accurate as the double-word tables rather than FP32.  The _rn intrinsics
+// keep the compiler from fusing the steps.
+__global__ void __launch_bounds__(256) k_gemm_rows_dot2(const float *__restrict__ X, const float *__restrict__ Xlo,
+                                                        size_t xw, const float *__restrict__ Y,
+                                                        const float *__restrict__ Ylo, size_t yw, int ma, int nb,
+                                                        int K, double *__restrict__ Out, size_t ow, int ldo) {
   __shared__ float Xs[16][65];
+  __shared__ float Xl[16][65];
   __shared__ float Ys[16][65];
   __shared__ float Yl[16][65];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int w = blockIdx.z, a0 = blockIdx.y * 16, b0 = blockIdx.x * 16;
-  const float *Xw = X + (size_t)w * xw;
-  const float *Yw = Y + (size_t)w * yw;
   float s = 0.0f, c = 0.0f;
   for (int k0 = 0; k0 < K; k0 += 64) {
 #pragma unroll
@@ -65,9 +66,12 @@ __global__ void __launch_bounds__(256) k_gemm_rows_dot2(const float *__restrict_
       const int idx = threadIdx.x + q * 256, row = idx >> 6, col = idx & 63;
       const int k = k0 + col;
       const int a = a0 + row, b = b0 + row;
-      Xs[row][col] = (a < ma && k < K) ? Xw[(size_t)a * K + k] : 0.0f;
-      Ys[row][col] = (b < nb && k < K) ? Yw[(size_t)b * K + k] : 0.0f;
-      Yl[row][col] = (Ylo && b < nb && k < K) ? Ylo[(size_t)w * yw + (size_t)b * K + k] : 0.0f;
+      const bool xa = a < ma && k < K, yb = b < nb && k < K;
+      const size_t xi = (size_t)w * xw + (size_t)a * K + k, yi = (size_t)w * yw + (size_t)b * K + k;
+      Xs[row][col] = xa ? X[xi] : 0.0f;
+      Xl[row][col] = (Xlo && xa) ? Xlo[xi] : 0.0f;
+      Ys[row][col] = yb ? Y[yi] : 0.0f;
+      Yl[row][col] = (Ylo && yb) ? Ylo[yi] : 0.0f;
     }
     __syncthreads();
 #pragma unroll 8
@@ -79,7 +83,8 @@ __global__ void __launch_bounds__(256) k_gemm_rows_dot2(const float *__restrict_
       const float z = __fsub_rn(t, s);
       const float se = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
       s = t;
-      c = __fadd_rn(c, __fadd_rn(__fmaf_rn(x, Yl[tx][k], pe), se));
+      const float cross = __fmaf_rn(Xl[ty][k], y, __fmul_rn(x, Yl[tx][k]));
+      c = __fadd_rn(c, __fadd_rn(__fadd_rn(cross, pe), se));
     }
     __syncthreads();
   }
@@ -88,11 +93,12 @@ __global__ void __launch_bounds__(256) k_gemm_rows_dot2(const float *__restrict_
     Out[(size_t)w * ow + (size_t)(a0 + ty) * ldo + b0 + tx] = static_cast<double>(s) + static_cast<double>(c);
 }
 
-cudaError_t launch_gemm_rows_dot2(const float *X, size_t xw, const float *Y, const float *Ylo, size_t yw, int ma,
-                                  int nb, int K, double *Out, size_t ow, int ldo, int W, cudaStream_t st) {
+cudaError_t launch_gemm_rows_dot2(const float *X, const float *Xlo, size_t xw, const float *Y, const float *Ylo,
+                                  size_t yw, int ma, int nb, int K, double *Out, size_t ow, int ldo, int W,
+                                  cudaStream_t st) {
   if (W <= 0 || ma <= 0 || nb <= 0) return cudaSuccess;
   dim3 grid((nb + 15) / 16, (ma + 15) / 16, W);
-  k_gemm_rows_dot2<<<grid, 256, 0, st>>>(X, xw, Y, Ylo, yw, ma, nb, K, Out, ow, ldo);
+  k_gemm_rows_dot2<<<grid, 256, 0, st>>>(X, Xlo, xw, Y, Ylo, yw, ma, nb, K, Out, ow, ldo);
   return cudaGetLastError();
 }
 
@@ -291,6 +297,8 @@ __global__ void __launch_bounds__(256) k_refresh_inverse(const double *__restric
 // The same elimination with one warp per walker (N_up <= 32): lane j owns the
 // columns j and j + 32 of [G~ | I]; pivot search by shuffles, no block barriers.
 constexpr int kRefreshWarps = 4;
+constexpr size_t kMmatSmemMax = 200 * 1024;  // k_mmat stages G~^{-1} whole up to this footprint
+constexpr size_t kRefreshSmemMax = 200 * 1024;  // [G~ | I] kept in shared memory up to this footprint
 
 template <typename T>
 __global__ void __launch_bounds__(kRefreshWarps * 32) k_refresh_inverse_warp(
@@ -400,23 +408,160 @@ __global__ void __launch_bounds__(kRefreshWarps * 32) k_refresh_inverse_warp(
   }
 }
 
+// In-place Gauss-Jordan for N_up too large for shared memory: the FP64 G~ of
+// the walker is overwritten by its inverse in global memory (L2-resident while
+// the CTA works on it).  Step k scales the pivot row, stores -f_i / p in column
+// k and updates the rest; the row swaps of the partial pivoting become column
+// swaps of the result, undone in reverse order at the end.
 template <typename T>
-cudaError_t launch_refresh_inverse(const double *gm, T *ginv, double *scal, int *status, int n, int W,
+__global__ void __launch_bounds__(512) k_refresh_inverse_global(double *__restrict__ gm, T *__restrict__ ginv,
+                                                                double *__restrict__ scal, int *__restrict__ status,
+                                                                int n, int check_drift, double drift_tol) {
+  extern __shared__ double sm[];
+  double *prow = sm;                                // n: the scaled pivot row
+  double *f = prow + n;                             // n: column k before the step
+  int *perm = reinterpret_cast<int *>(f + n);       // n: pivot row of each step
+  __shared__ int s_piv;
+  __shared__ double s_pv;
+  __shared__ double red[32];
+  const int tid = threadIdx.x, bs = blockDim.x, w = blockIdx.x, lane = tid & 31, warp = tid >> 5, nw = bs >> 5;
+  double *A = gm + (size_t)w * n * n;
+  double gmax = 0.0;
+  for (int idx = tid; idx < n * n; idx += bs) gmax = fmax(gmax, fabs(A[idx]));
+  double logdet = 0.0, sgn = 1.0;
+  bool ok = true;
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    if (warp == 0) {
+      double best = -1.0;
+      int bi = k;
+      for (int i = k + lane; i < n; i += 32) {
+        const double v = fabs(A[(size_t)i * n + k]);
+        if (v > best) {
+          best = v;
+          bi = i;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) {
+          best = ob;
+          bi = oi;
+        }
+      }
+      if (lane == 0) {
+        s_piv = bi;
+        s_pv = A[(size_t)bi * n + k];
+      }
+    }
+    __syncthreads();
+    const int p = s_piv;
+    const double pv = s_pv;
+    if (!(pv != 0.0) || !isfinite(pv)) {
+      ok = false;
+      break;
+    }
+    if (p != k) {
+      for (int j = tid; j < n; j += bs) {
+        const double t = A[(size_t)k * n + j];
+        A[(size_t)k * n + j] = A[(size_t)p * n + j];
+        A[(size_t)p * n + j] = t;
+      }
+      sgn = -sgn;
+    }
+    logdet += log(fabs(pv));
+    if (pv < 0.0) sgn = -sgn;
+    if (tid == 0) perm[k] = p;
+    __syncthreads();
+    const double ip = 1.0 / pv;
+    for (int j = tid; j < n; j += bs) prow[j] = j == k ? ip : A[(size_t)k * n + j] * ip;
+    for (int i = tid; i < n; i += bs) f[i] = i == k ? 0.0 : A[(size_t)i * n + k];
+    __syncthreads();
+    for (int i = warp; i < n; i += nw) {
+      double *Ai = A + (size_t)i * n;
+      if (i == k) {
+        for (int j = lane; j < n; j += 32) Ai[j] = prow[j];
+      } else {
+        const double fi = f[i];
+        for (int j = lane; j < n; j += 32) Ai[j] = j == k ? -fi * ip : fma(-fi, prow[j], Ai[j]);
+      }
+    }
+    __syncthreads();
+  }
+  T *gi = ginv + (size_t)w * n * n;
+  if (!ok) {
+    if (tid == 0) {
+      status[w] |= JAGP_WS_SINGULAR;
+      scal[(size_t)w * S_STRIDE + S_LOGDET] = -INFINITY;
+      scal[(size_t)w * S_STRIDE + S_SIGN] = 0.0;
+    }
+    return;
+  }
+  for (int k = n - 1; k >= 0; --k) {
+    const int p = perm[k];
+    if (p != k)
+      for (int i = tid; i < n; i += bs) {
+        const double t = A[(size_t)i * n + k];
+        A[(size_t)i * n + k] = A[(size_t)i * n + p];
+        A[(size_t)i * n + p] = t;
+      }
+    __syncthreads();
+  }
+  double dmax = 0.0;
+  for (int idx = tid; idx < n * n; idx += bs) {
+    const double v = A[idx];
+    if (check_drift) dmax = fmax(dmax, fabs(v - static_cast<double>(gi[idx])));
+    gi[idx] = static_cast<T>(v);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+    gmax = fmax(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
+  }
+  if (lane == 0) {
+    red[warp] = dmax;
+    red[16 + warp] = gmax;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double d = 0.0, g = 0.0;
+    for (int q = 0; q < nw; ++q) {
+      d = fmax(d, red[q]);
+      g = fmax(g, red[16 + q]);
+    }
+    scal[(size_t)w * S_STRIDE + S_LOGDET] = logdet;
+    scal[(size_t)w * S_STRIDE + S_SIGN] = sgn;
+    if (check_drift) {
+      const double drift = d * g;
+      scal[(size_t)w * S_STRIDE + S_DRIFT] = drift;
+      if (!(drift <= drift_tol)) status[w] |= JAGP_WS_DRIFT;
+    }
+  }
+}
+
+template <typename T>
+cudaError_t launch_refresh_inverse(double *gm, T *ginv, double *scal, int *status, int n, int W,
                                    int check_drift, double drift_tol, cudaStream_t st) {
   if (W <= 0) return cudaSuccess;
+  const size_t block_smem = (size_t)(n * (2 * n + 1) + n) * sizeof(double);
+  if (n > 32 && block_smem > kRefreshSmemMax) {
+    const size_t smem = (size_t)n * (2 * sizeof(double) + sizeof(int));
+    k_refresh_inverse_global<T><<<W, 512, smem, st>>>(gm, ginv, scal, status, n, check_drift, drift_tol);
+    return cudaGetLastError();
+  }
   if (n <= 32) {
     const size_t smem = (size_t)kRefreshWarps * (n * (2 * n + 1) + n) * sizeof(double);
     k_refresh_inverse_warp<T><<<(W + kRefreshWarps - 1) / kRefreshWarps, kRefreshWarps * 32, smem, st>>>(
         gm, ginv, scal, status, n, W, check_drift, drift_tol);
     return cudaGetLastError();
   }
-  const size_t smem = (size_t)(n * (2 * n + 1) + n) * sizeof(double);
-  k_refresh_inverse<T><<<W, 256, smem, st>>>(gm, ginv, scal, status, n, check_drift, drift_tol);
+  k_refresh_inverse<T><<<W, 256, block_smem, st>>>(gm, ginv, scal, status, n, check_drift, drift_tol);
   return cudaGetLastError();
 }
-template cudaError_t launch_refresh_inverse<double>(const double *, double *, double *, int *, int, int, int, double,
+template cudaError_t launch_refresh_inverse<double>(double *, double *, double *, int *, int, int, int, double,
                                                     cudaStream_t);
-template cudaError_t launch_refresh_inverse<float>(const double *, float *, double *, int *, int, int, int, double,
+template cudaError_t launch_refresh_inverse<float>(double *, float *, double *, int *, int, int, int, double,
                                                    cudaStream_t);
 
 // ---------------------------------------------------------------------------
@@ -461,12 +606,84 @@ __global__ void __launch_bounds__(256) k_mmat(DevSystem s, const T *__restrict__
   }
 }
 
+// The same contraction for N_up too large to stage G~^{-1} whole: 64 x 64
+// output tiles (electrons x basis functions), 4 x 4 per thread, the sum over
+// j (or i) in chunks of 16 in the same order as above.  Up tiles come first in
+// blockIdx.y, then down tiles, so that no tile mixes the two formulas.
+template <typename T>
+__global__ void __launch_bounds__(256) k_mmat_tiled(DevSystem s, const T *__restrict__ ginv,
+                                                    const T *__restrict__ bt, const T *__restrict__ a_up,
+                                                    T *__restrict__ mbuf) {
+  __shared__ T Xs[16][64];  // Xs[k][e]: G~^{-1}[k][e] (up) or G~^{-1}[e][k] (down)
+  __shared__ T Ys[16][64];  // Ys[k][c]: Bt[k][c] (up) or A_up[k][c] (down)
+  const int n = s.n_up, N = s.N, L = s.L;
+  const int w = blockIdx.z, c0 = blockIdx.x * 64, tid = threadIdx.x;
+  const int up_tiles = (n + 63) / 64;
+  const bool up = (int)blockIdx.y < up_tiles;
+  const int e0 = up ? blockIdx.y * 64 : (blockIdx.y - up_tiles) * 64;  // within the species
+  const int ne = up ? n : s.n_dn;
+  const T *G = ginv + (size_t)w * n * n;
+  const T *Y = (up ? bt : a_up) + (size_t)w * n * L;
+  const int tx = tid & 15, ty = tid >> 4;
+  T acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+  for (int k0 = 0; k0 < n; k0 += 16) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int idx = tid + q * 256;
+      const int kk = idx >> 6, col = idx & 63, k = k0 + kk;
+      T xv = T(0), yv = T(0);
+      if (k < n) {
+        const int e = e0 + col;
+        if (e < ne) xv = up ? G[(size_t)k * n + e] : G[(size_t)e * n + k];
+        if (c0 + col < L) yv = Y[(size_t)k * L + c0 + col];
+      }
+      Xs[kk][col] = xv;
+      Ys[kk][col] = yv;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      T xa[4], yb[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) xa[a] = Xs[kk][ty * 4 + a];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) yb[b] = Ys[kk][tx * 4 + b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = fma(xa[a], yb[b], acc[a][b]);
+    }
+    __syncthreads();
+  }
+  const int ebase = up ? 0 : n;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int e = e0 + ty * 4 + a;
+    if (e >= ne) continue;
+    T *o = mbuf + ((size_t)w * N + ebase + e) * L;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int c = c0 + tx * 4 + b;
+      if (c < L) o[c] = acc[a][b];
+    }
+  }
+}
+
 template <typename T>
 cudaError_t launch_mmat(const DevSystem &s, const T *ginv, const T *bt, const T *a_up, T *mbuf, int W,
                         cudaStream_t st) {
   if (W <= 0) return cudaSuccess;
   const int n = s.n_up;
   const size_t smem = (size_t)(n * n + 2 * n * 64) * sizeof(T);
+  if (smem > kMmatSmemMax) {
+    dim3 grid((s.L + 63) / 64, (n + 63) / 64 + (s.n_dn + 63) / 64, W);
+    k_mmat_tiled<T><<<grid, 256, 0, st>>>(s, ginv, bt, a_up, mbuf);
+    return cudaGetLastError();
+  }
   dim3 grid((s.L + 63) / 64, W);
   k_mmat<T><<<grid, 256, smem, st>>>(s, ginv, bt, a_up, mbuf);
   return cudaGetLastError();
@@ -482,6 +699,8 @@ static cudaError_t linalg_attrs() {
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(k_refresh_inverse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
   if ((e = cudaFuncSetAttribute(k_refresh_inverse_warp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)))
+    return e;
+  if ((e = cudaFuncSetAttribute(k_refresh_inverse_global<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)))
     return e;
   return cudaFuncSetAttribute(k_mmat<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
 }

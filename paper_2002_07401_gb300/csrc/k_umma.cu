@@ -9,13 +9,14 @@
 //
 // Fixed-point mode (row exponents ea[m], column exponents eb[n] given): the
 // terms are 8-bit integer slices of rows scaled by powers of two,
-//   a = 2^(ea - 7) (t0 + t1 / 256 + t2 / 256^2 + t3 / 256^3),  |t_i| <= 128,
+//   a = 2^(ea - 7) (t0 + t1 / 256 + t2 / 256^2 + ...),  |t_i| <= 128,
 // (exact in BF16), so every slice product is an integer below 2^14 and the
 // tensor cores sum them exactly while partial sums stay below 2^24.  Pairs of
-// equal weight d = a_p + b_p share an accumulator S_d, and the epilogue forms
-//   C = 2^(ea + eb - 14) (S_0 + S_1 / 256 + S_2 / 256^2 + S_3 / 256^3)
-// with one FP32 rounding per add: FP32-accurate products of FP32 rows, which
-// the lossy FP32 accumulation inside the tensor cores would not give.
+// equal weight d = a_p + b_p share an accumulator S_d (up to five), and the
+// epilogue forms C = 2^(ea + eb - 14) (S_0 + S_1 / 256 + S_2 / 256^2 + ...) as
+// an unevaluated two-float sum: products of two-float rows far beyond FP32
+// accuracy, which the lossy FP32 accumulation inside the tensor cores would
+// not give.
 //
 // One CTA computes a 128 x BN tile: warp 0 lane 0 issues the TMA loads, warp 1
 // lane 0 issues the MMAs (one per 16-wide K slice), all four warps drain the
@@ -234,7 +235,7 @@ __global__ void __launch_bounds__(128, 1) k_umma_gemm(const __grid_constant__ CU
       float v[16];
       tmem_ld16(t_row + static_cast<uint32_t>(c), v);
       if (g.a_exp) {
-        // v = S_0 + S_1 / 256 + S_2 / 256^2 + S_3 / 256^3 as an unevaluated sum
+        // v = S_0 + S_1 / 256 + S_2 / 256^2 + ... as an unevaluated sum
         // hi + lo of FP32 numbers: every S_d is an exact integer below 2^24 and
         // each addition goes through an error-free transformation (TwoSum)
         float lo[16];
@@ -345,14 +346,15 @@ cudaError_t launch_umma_gemm(const uint16_t *A, int m_max, const int *m_dev, int
     g.pair_group[p] = a_exp ? pair_a[p] + pair_b[p] : 0;
     if (g.pair_group[p] + 1 > g.ngroups) g.ngroups = g.pair_group[p] + 1;
   }
-  if (g.ngroups > 4) return cudaErrorInvalidValue;
+  if (g.ngroups > 5) return cudaErrorInvalidValue;
   g.a_exp = a_exp;
   g.b_exp = b_exp;
   g.m_max = m_max;
   g.m_dev = m_dev;
   g.n = n;
   g.kp = kp;
-  g.bn = umma_pick_bn(n, g.ngroups == 1 ? 256 : (g.ngroups == 2 ? 256 : 128));
+  // the ngroups accumulators of bn columns share the 512 tensor-memory columns
+  g.bn = umma_pick_bn(n, g.ngroups <= 2 ? 256 : (g.ngroups <= 4 ? 128 : 96));
   const uint32_t stage_bytes = 128u * 128u + static_cast<uint32_t>(g.bn) * 128u;
   g.stages = static_cast<int>((200u * 1024u) / stage_bytes);
   if (g.stages > 6) g.stages = 6;
@@ -424,20 +426,25 @@ cudaError_t launch_pack_split3(const float *P, const int *list, const int *count
 
 // ---------------------------------------------------------------------------
 // Fixed-point operand packing: each FP32 row (compacted as above) is scaled by
-// 2^-e (e = 1 + the binary exponent of its largest magnitude) and cut into four
-// exact 8-bit integer slices t0..t3 (|t| <= 128), stored as BF16 side by side,
-// with e in exps[m].  Every step of the cut is exact in FP32.
+// 2^-e (e = 1 + the binary exponent of its largest magnitude) and cut into
+// kFixedSlices exact 8-bit integer slices t0, t1, ... (|t| <= 128), stored as
+// BF16 side by side, with e in exps[m].  Every step of the cut is exact in
+// FP32.  A two-float row P + P_lo is cut the same way, its remainder carried
+// from slice to slice as an exact two-float sum (TwoSum), so that the slices
+// take the low part's bits as well.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_pack_fixed4(const float *__restrict__ P, const int *__restrict__ list,
-                                                     const int *__restrict__ count, int nrows, int nsub, int stride,
-                                                     int L, int kp, __nv_bfloat16 *__restrict__ A,
-                                                     int *__restrict__ rows_out, int *__restrict__ exps) {
+__global__ void __launch_bounds__(256) k_pack_fixed(const float *__restrict__ P, const float *__restrict__ P_lo,
+                                                     const int *__restrict__ list, const int *__restrict__ count,
+                                                     int nrows, int nsub, int stride, int L, int kp,
+                                                     __nv_bfloat16 *__restrict__ A, int *__restrict__ rows_out,
+                                                     int *__restrict__ exps) {
   const int rows = count ? *count : nrows;
   const int lane = threadIdx.x & 31;
   const long nw = (long)gridDim.x * (blockDim.x >> 5);
   for (long m = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); m < rows; m += nw) {
     const long phys = list ? (long)list[m] : (m / nsub) * stride + (m % nsub);
     const float *src = P + phys * L;
+    const float *srl = P_lo ? P_lo + phys * L : nullptr;
     float mx = 0.0f;
     for (int k = lane; k < L; k += 32) mx = fmaxf(mx, fabsf(src[k]));
 #pragma unroll
@@ -447,25 +454,30 @@ __global__ void __launch_bounds__(256) k_pack_fixed4(const float *__restrict__ P
       rows_out[m] = (int)phys;
       exps[m] = e;
     }
-    __nv_bfloat16 *dst = A + m * 4 * (long)kp;
+    __nv_bfloat16 *dst = A + m * kFixedSlices * (long)kp;
     for (int k = lane; k < kp; k += 32) {
       float x = k < L ? ldexpf(src[k], 7 - e) : 0.0f;  // |x| < 128
+      // the low part, in the same scale
+      float xl = (srl && k < L) ? ldexpf(srl[k], 7 - e) : 0.0f;
 #pragma unroll
-      for (int t = 0; t < 4; ++t) {
+      for (int t = 0; t < kFixedSlices; ++t) {
         const float q = rintf(x);
         dst[t * kp + k] = __float2bfloat16_rn(q);
-        x = (x - q) * 256.0f;
+        const fdw r = two_sum(__fsub_rn(x, q), xl);  // remainder + low part, exactly
+        x = __fmul_rn(r.hi, 256.0f);
+        xl = __fmul_rn(r.lo, 256.0f);
       }
     }
   }
 }
 
-cudaError_t launch_pack_fixed4(const float *P, const int *list, const int *count, int nrows, int nsub, int stride,
-                               int L, int kp, uint16_t *A, int *rows_out, int *exps, int max_rows, cudaStream_t st) {
+cudaError_t launch_pack_fixed(const float *P, const float *P_lo, const int *list, const int *count, int nrows,
+                               int nsub, int stride, int L, int kp, uint16_t *A, int *rows_out, int *exps,
+                               int max_rows, cudaStream_t st) {
   if (max_rows <= 0) return cudaSuccess;
   long blocks = (max_rows + 7) / 8;
   if (blocks > 152 * 16) blocks = 152 * 16;
-  k_pack_fixed4<<<(int)blocks, 256, 0, st>>>(P, list, count, nrows, nsub > 0 ? nsub : 1, stride, L, kp,
+  k_pack_fixed<<<(int)blocks, 256, 0, st>>>(P, P_lo, list, count, nrows, nsub > 0 ? nsub : 1, stride, L, kp,
                                               reinterpret_cast<__nv_bfloat16 *>(A), rows_out, exps);
   return cudaGetLastError();
 }

@@ -3,26 +3,66 @@
 // acceptance with Sherman-Morrison updates, the full Jastrow, bookkeeping.
 #include <math.h>
 
+#include <type_traits>
+
 #include "jagp_launch.h"
 
 namespace jagp {
 
 // ---------------------------------------------------------------------------
 // Orbitals at points: one warp per point, lanes stride over shells.  The shell
-// table (32-byte centre+exponent records and packed info words) is staged in
-// shared memory once per CTA; CTAs then grid-stride over points.
+// table (32-byte centre+exponent records and packed info words; in the FP32
+// path the double-word split records instead) is staged in shared memory once
+// per CTA; CTAs then grid-stride over points.
 // (Sec. "Atomic basis set", Eqs. gaussian, slater.)
+// FP64 path: FP64 values.  FP32 path: double-word values (FP32 arithmetic
+// only, see shell_values_dw); the FP32 table gets hi, out_lo (when given) lo.
+// With PROPOSE the point is the Metropolis proposal of the electron, and the
+// one-body Jastrow change of the move is taken here as well (FP32 distances in
+// the FP32 path: it only enters the acceptance test).
 // ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ double j1_move_change(const DevSystem &s, const double *rp, const double *rr, int lane) {
+  double dj1 = 0.0;
+  // lane pairs: even lanes take the new position, odd lanes the old one
+  for (int q = lane; q < 2 * s.n_atoms; q += 32) {
+    const int a = q >> 1;
+    const double *pos = (q & 1) ? rr : rp;
+    if constexpr (std::is_same<T, double>::value) {
+      const double ax = pos[0] - s.R[3 * a], ay = pos[1] - s.R[3 * a + 1], az = pos[2] - s.R[3 * a + 2];
+      const double v = j1_val(s.c1[a], s.b_ea, sqrt(ax * ax + ay * ay + az * az));
+      dj1 += (q & 1) ? -v : v;
+    } else {
+      const float ax = static_cast<float>(pos[0] - s.R[3 * a]), ay = static_cast<float>(pos[1] - s.R[3 * a + 1]),
+                  az = static_cast<float>(pos[2] - s.R[3 * a + 2]);
+      const float c = static_cast<float>(s.c1[a]), b = static_cast<float>(s.b_ea);
+      const float sc = c * sqrtf(ax * ax + ay * ay + az * az);
+      const float u = (b == 0.0f) ? 0.5f * sc : -expm1f(-b * sc) / (2.0f * b);
+      const float v = -c * c * c * u;
+      dj1 += (q & 1) ? -static_cast<double>(v) : static_cast<double>(v);
+    }
+  }
+  return warp_sum(dj1);
+}
+
 template <bool PROPOSE, typename T>
 __global__ void __launch_bounds__(256) k_basis_points(DevSystem s, const double *__restrict__ r, int W,
                                                       int e0, int npts, T *__restrict__ out,
-                                                      double *__restrict__ rprop, uint32_t walker0,
-                                                      uint32_t sweep, const uint32_t *__restrict__ sweep_dev) {
+                                                      float *__restrict__ out_lo, double *__restrict__ rprop,
+                                                      uint32_t walker0, uint32_t sweep,
+                                                      const uint32_t *__restrict__ sweep_dev) {
+  constexpr bool kDw = std::is_same<T, float>::value;
   if (PROPOSE && sweep_dev) sweep += *sweep_dev;  // graph replays read the sweep index from the device
   extern __shared__ double4 sh_geo[];
   int *sh_info = reinterpret_cast<int *>(sh_geo + s.n_shells);
+  float4 *sh_dw = reinterpret_cast<float4 *>(sh_geo);  // FP32 path: two float4 per shell in place of the double4
   for (int k = threadIdx.x; k < s.n_shells; k += blockDim.x) {
-    sh_geo[k] = s.shell_geo[k];
+    if constexpr (kDw) {
+      sh_dw[2 * k] = s.shell_dw[2 * k];
+      sh_dw[2 * k + 1] = s.shell_dw[2 * k + 1];
+    } else {
+      sh_geo[k] = s.shell_geo[k];
+    }
     sh_info[k] = s.shell_info[k];
   }
   __syncthreads();
@@ -41,38 +81,47 @@ __global__ void __launch_bounds__(256) k_basis_points(DevSystem s, const double 
       p[2] = rp[2];
       // change of the one-body Jastrow for this move: it depends only on the
       // electron's own old and new positions, so it is taken here, in parallel
-      // (lane pairs: even lanes take the new position, odd lanes the old one)
-      double dj1 = 0.0;
-      if (s.use_j1)
-        for (int q = lane; q < 2 * s.n_atoms; q += 32) {
-          const int a = q >> 1;
-          const double *pos = (q & 1) ? rr : rp;
-          const double ax = pos[0] - s.R[3 * a], ay = pos[1] - s.R[3 * a + 1], az = pos[2] - s.R[3 * a + 2];
-          const double v = j1_val(s.c1[a], s.b_ea, sqrt(ax * ax + ay * ay + az * az));
-          dj1 += (q & 1) ? -v : v;
-        }
-      dj1 = warp_sum(dj1);
+      const double dj1 = s.use_j1 ? j1_move_change<T>(s, rp, rr, lane) : 0.0;
       double *rec = rprop + ((size_t)w * s.n_up + i) * kPropStride;
       if (lane < 4) rec[lane] = lane < 3 ? rp[lane] : u;
       if (lane == 0) rec[4] = dj1;
     }
     T *o = out + ((size_t)w * s.n_up + i) * s.L;
-    for (int k = lane; k < s.n_shells; k += 32) {
-      const double4 g = sh_geo[k];
-      const int info = sh_info[k];
-      T v[5];
-      const int nc = shell_values<T>(info, g.w, p[0] - g.x, p[1] - g.y, p[2] - g.z, v);
-      const int off = shell_off(info);
+    if constexpr (kDw) {
+      const fdw pd[3] = {dw_of(p[0]), dw_of(p[1]), dw_of(p[2])};
+      float *ol = out_lo ? out_lo + ((size_t)w * s.n_up + i) * s.L : nullptr;
+      for (int k = lane; k < s.n_shells; k += 32) {
+        const float4 gh = sh_dw[2 * k], gl = sh_dw[2 * k + 1];
+        const int info = sh_info[k];
+        const DwDisp d = dw_displacement(pd, gh, gl);
+        float v[5], vl[5];
+        const int nc = shell_values_dw(info, fdw{gh.w, gl.w}, d, v, vl);
+        const int off = shell_off(info);
 #pragma unroll
-      for (int c = 0; c < 5; ++c)
-        if (c < nc) o[off + c] = v[c];
+        for (int c = 0; c < 5; ++c)
+          if (c < nc) {
+            o[off + c] = v[c];
+            if (ol) ol[off + c] = vl[c];
+          }
+      }
+    } else {
+      for (int k = lane; k < s.n_shells; k += 32) {
+        const double4 g = sh_geo[k];
+        const int info = sh_info[k];
+        double v[5];
+        const int nc = shell_values(info, g.w, p[0] - g.x, p[1] - g.y, p[2] - g.z, v);
+        const int off = shell_off(info);
+#pragma unroll
+        for (int c = 0; c < 5; ++c)
+          if (c < nc) o[off + c] = v[c];
+      }
     }
   }
 }
 
 template <typename T>
 cudaError_t launch_basis_points(const DevSystem &s, bool propose, const double *r, int W, int e0, int npts,
-                                T *out, double *rprop, uint32_t walker0, uint32_t sweep,
+                                T *out, float *out_lo, double *rprop, uint32_t walker0, uint32_t sweep,
                                 cudaStream_t st, const uint32_t *sweep_dev) {
   if (W <= 0 || npts <= 0) return cudaSuccess;
   const long total = (long)W * npts;
@@ -81,17 +130,19 @@ cudaError_t launch_basis_points(const DevSystem &s, bool propose, const double *
   if (blocks > 152 * 16) blocks = 152 * 16;
   const size_t smem = (size_t)s.n_shells * (sizeof(double4) + sizeof(int));
   if (propose)
-    k_basis_points<true, T><<<(int)blocks, warps * 32, smem, st>>>(s, r, W, e0, npts, out, rprop, walker0, sweep,
-                                                                    sweep_dev);
+    k_basis_points<true, T><<<(int)blocks, warps * 32, smem, st>>>(s, r, W, e0, npts, out, out_lo, rprop, walker0,
+                                                                    sweep, sweep_dev);
   else
-    k_basis_points<false, T><<<(int)blocks, warps * 32, smem, st>>>(s, r, W, e0, npts, out, rprop, walker0, sweep,
-                                                                     nullptr);
+    k_basis_points<false, T><<<(int)blocks, warps * 32, smem, st>>>(s, r, W, e0, npts, out, out_lo, rprop,
+                                                                     walker0, sweep, nullptr);
   return cudaGetLastError();
 }
 template cudaError_t launch_basis_points<double>(const DevSystem &, bool, const double *, int, int, int, double *,
-                                                 double *, uint32_t, uint32_t, cudaStream_t, const uint32_t *);
+                                                 float *, double *, uint32_t, uint32_t, cudaStream_t,
+                                                 const uint32_t *);
 template cudaError_t launch_basis_points<float>(const DevSystem &, bool, const double *, int, int, int, float *,
-                                                double *, uint32_t, uint32_t, cudaStream_t, const uint32_t *);
+                                                float *, double *, uint32_t, uint32_t, cudaStream_t,
+                                                const uint32_t *);
 
 // ---------------------------------------------------------------------------
 // Block reduction of two doubles (blockDim.x <= 1024); result valid in thread 0.
@@ -117,7 +168,7 @@ __device__ __forceinline__ void block_sum2(double &a, double &b, double *red) {
 // ---------------------------------------------------------------------------
 // Sequential single-electron Metropolis for one spin species (Sec. VMC).
 // One CTA per walker; G~^{-1} lives in shared memory for the whole
-// half-sweep.  Move m of an up electron replaces row m of G~ by the proposed
+// half-sweep (in global memory, L2-resident, when it does not fit).  Move m of an up electron replaces row m of G~ by the proposed
 // row g' (already computed from the frozen down-spin table):
 //   ratio R = g' . G~^{-1}[:, m],
 //   G~^{-1} <- G~^{-1} - G~^{-1}[:, m] (g'^T G~^{-1} - e_m^T) / R   (Sherman-Morrison);
@@ -125,28 +176,33 @@ __device__ __forceinline__ void block_sum2(double &a, double &b, double *red) {
 // Jastrow factor contributes exp(2 dJ), dJ summed over the atoms (J1) and the
 // other electrons at their current positions (J2).  Accept iff u < R^2 e^{2 dJ}.
 // ---------------------------------------------------------------------------
-template <bool UP, typename T>
-__global__ void __launch_bounds__(128) k_metropolis(DevSystem s, double *__restrict__ r,
+template <bool UP, typename T, bool GLOB>
+__global__ void __launch_bounds__(512) k_metropolis(DevSystem s, double *__restrict__ r,
                                                     const double *__restrict__ rprop,
                                                     const T *__restrict__ gprop,
                                                     T *__restrict__ ginv, double *__restrict__ scal,
                                                     int *__restrict__ status,
                                                     const T *__restrict__ pprop,
                                                     T *__restrict__ phi_up, int *__restrict__ list,
-                                                    int *__restrict__ count) {
+                                                    int *__restrict__ count,
+                                                    const float *__restrict__ pprop_lo,
+                                                    float *__restrict__ phi_lo) {
   extern __shared__ double sm[];
   const int n = s.n_up, N = s.N, tid = threadIdx.x, bs = blockDim.x;
   const int w = blockIdx.x;
+  T *gw = ginv + (size_t)w * n * n;
   double *xs = sm;                                  // N * 3 positions (FP64)
-  T *Gi = reinterpret_cast<T *>(xs + N * 3);        // n * n
-  T *gp = Gi + n * n;                               // n
+  // G~^{-1} in shared memory, or (GLOB, too large for it) in place in global
+  // memory, where a CTA's n x n block stays resident in L2 for the half-sweep
+  T *Gi = GLOB ? gw : reinterpret_cast<T *>(xs + N * 3);
+  T *gp = GLOB ? reinterpret_cast<T *>(xs + N * 3) : Gi + n * n;  // n
   T *vv = gp + n;                                   // n
   T *cc = vv + n;                                   // n
   __shared__ double red[64];
   __shared__ int s_acc;
   __shared__ double s_R;
-  T *gw = ginv + (size_t)w * n * n;
-  for (int t = tid; t < n * n; t += bs) Gi[t] = gw[t];
+  if (!GLOB)
+    for (int t = tid; t < n * n; t += bs) Gi[t] = gw[t];
   for (int t = tid; t < N * 3; t += bs) xs[t] = r[(size_t)w * N * 3 + t];
   double logdet = 0.0, sgn = 1.0, J = 0.0, nacc = 0.0;
   int st_bits = 0;
@@ -172,18 +228,7 @@ __global__ void __launch_bounds__(128) k_metropolis(DevSystem s, double *__restr
     double pr = static_cast<double>(prt);
     const double ox = xs[3 * e], oy = xs[3 * e + 1], oz = xs[3 * e + 2];
     if (tid == 0) pj = rp4[4];   // one-body Jastrow change, from the proposal kernel
-    if (s.use_j2) {
-      for (int k = tid; k < N; k += bs) {
-        if (k == e) continue;
-        const bool same = (k < s.n_up) == UP;
-        double kk, bb;
-        j2_params(s, same, &kk, &bb);
-        const double qx = xs[3 * k], qy = xs[3 * k + 1], qz = xs[3 * k + 2];
-        const double dn = sqrt((px - qx) * (px - qx) + (py - qy) * (py - qy) + (pz - qz) * (pz - qz));
-        const double d0 = sqrt((ox - qx) * (ox - qx) + (oy - qy) * (oy - qy) + (oz - qz) * (oz - qz));
-        pj += j2_val(kk, bb, dn) - j2_val(kk, bb, d0);
-      }
-    }
+    if (s.use_j2) pj += j2_move_change<T, UP>(s, xs, e, px, py, pz, ox, oy, oz, tid, bs);
     block_sum2(pr, pj, red);
     if (tid == 0) {
       const double u = rp4[3];
@@ -204,16 +249,28 @@ __global__ void __launch_bounds__(128) k_metropolis(DevSystem s, double *__restr
     }
     __syncthreads();
     if (s_acc) {
-      for (int t = tid; t < n; t += bs) {
-        T a = T(0);
-        if (UP) {
-          for (int j = 0; j < n; ++j) a += gp[j] * Gi[j * n + t];
-          cc[t] = Gi[t * n + m];
-        } else {
-          for (int i = 0; i < n; ++i) a += Gi[t * n + i] * gp[i];
-          cc[t] = Gi[m * n + t];
+      if (GLOB && !UP) {
+        // rows of G~^{-1} against g': one warp per row, coalesced loads
+        const int lane = tid & 31, nw = bs >> 5;
+        for (int t = tid >> 5; t < n; t += nw) {
+          T a = T(0);
+          for (int i = lane; i < n; i += 32) a += Gi[t * n + i] * gp[i];
+          a = warp_sum(a);
+          if (lane == 0) vv[t] = a;
         }
-        vv[t] = a;
+        for (int t = tid; t < n; t += bs) cc[t] = Gi[m * n + t];
+      } else {
+        for (int t = tid; t < n; t += bs) {
+          T a = T(0);
+          if (UP) {
+            for (int j = 0; j < n; ++j) a += gp[j] * Gi[j * n + t];
+            cc[t] = Gi[t * n + m];
+          } else {
+            for (int i = 0; i < n; ++i) a += Gi[t * n + i] * gp[i];
+            cc[t] = Gi[m * n + t];
+          }
+          vv[t] = a;
+        }
       }
       __syncthreads();
       const T invR = T(1) / static_cast<T>(s_R);
@@ -230,14 +287,16 @@ __global__ void __launch_bounds__(128) k_metropolis(DevSystem s, double *__restr
         xs[3 * e + 2] = pz;
       }
       if (UP) {
-        const T *src = pprop + ((size_t)w * n + m) * s.L;
-        T *dst = phi_up + ((size_t)w * n + m) * s.L;
-        for (int t = tid; t < s.L; t += bs) dst[t] = src[t];
+        const size_t row = ((size_t)w * n + m) * s.L;
+        for (int t = tid; t < s.L; t += bs) phi_up[row + t] = pprop[row + t];
+        if (phi_lo)
+          for (int t = tid; t < s.L; t += bs) phi_lo[row + t] = pprop_lo[row + t];
       }
     }
     __syncthreads();
   }
-  for (int t = tid; t < n * n; t += bs) gw[t] = Gi[t];
+  if (!GLOB)
+    for (int t = tid; t < n * n; t += bs) gw[t] = Gi[t];
   for (int t = tid; t < N * 3; t += bs) r[(size_t)w * N * 3 + t] = xs[t];
   if (tid == 0) {
     scal[(size_t)w * S_STRIDE + S_LOGDET] = logdet;
@@ -254,6 +313,7 @@ __global__ void __launch_bounds__(128) k_metropolis(DevSystem s, double *__restr
 // Every lane takes the accept decision from lane 0's sums so that it is uniform.
 // ---------------------------------------------------------------------------
 constexpr int kMetroWarps = 4;
+constexpr size_t kMetroSmemMax = 200 * 1024;  // G~^{-1} kept in shared memory up to this footprint
 
 template <typename T>
 __host__ __device__ inline size_t metro_smem_per_walker(int n, int N) {
@@ -265,7 +325,7 @@ __global__ void __launch_bounds__(kMetroWarps * 32) k_metropolis_warp(
     DevSystem s, double *__restrict__ r, const double *__restrict__ rprop, const T *__restrict__ gprop,
     T *__restrict__ ginv, double *__restrict__ scal, int *__restrict__ status,
     const T *__restrict__ pprop, T *__restrict__ phi_up, int *__restrict__ list,
-    int *__restrict__ count, int W) {
+    int *__restrict__ count, int W, const float *__restrict__ pprop_lo, float *__restrict__ phi_lo) {
   extern __shared__ double sm[];
   const int n = s.n_up, N = s.N, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int w = blockIdx.x * kMetroWarps + warp;
@@ -298,18 +358,8 @@ __global__ void __launch_bounds__(kMetroWarps * 32) k_metropolis_warp(
     }
     double pr = static_cast<double>(prt);
     if (lane == 0) pj = rec[4];
-    if (s.use_j2) {
-      const double ox = xs[3 * e], oy = xs[3 * e + 1], oz = xs[3 * e + 2];
-      for (int k = lane; k < N; k += 32) {
-        if (k == e) continue;
-        double kk, bb;
-        j2_params(s, (k < s.n_up) == UP, &kk, &bb);
-        const double qx = xs[3 * k], qy = xs[3 * k + 1], qz = xs[3 * k + 2];
-        const double dn = sqrt((px - qx) * (px - qx) + (py - qy) * (py - qy) + (pz - qz) * (pz - qz));
-        const double d0 = sqrt((ox - qx) * (ox - qx) + (oy - qy) * (oy - qy) + (oz - qz) * (oz - qz));
-        pj += j2_val(kk, bb, dn) - j2_val(kk, bb, d0);
-      }
-    }
+    if (s.use_j2)
+      pj += j2_move_change<T, UP>(s, xs, e, px, py, pz, xs[3 * e], xs[3 * e + 1], xs[3 * e + 2], lane, 32);
     pr = __shfl_sync(0xffffffffu, warp_sum(pr), 0);
     pj = __shfl_sync(0xffffffffu, warp_sum(pj), 0);
     const double p = pr * pr * exp(2.0 * pj);
@@ -348,9 +398,10 @@ __global__ void __launch_bounds__(kMetroWarps * 32) k_metropolis_warp(
       }
       if (lane < 3) xs[3 * e + lane] = lane == 0 ? px : (lane == 1 ? py : pz);
       if (UP) {
-        const T *src = pprop + ((size_t)w * n + m) * s.L;
-        T *dst = phi_up + ((size_t)w * n + m) * s.L;
-        for (int t = lane; t < s.L; t += 32) dst[t] = src[t];
+        const size_t row = ((size_t)w * n + m) * s.L;
+        for (int t = lane; t < s.L; t += 32) phi_up[row + t] = pprop[row + t];
+        if (phi_lo)
+          for (int t = lane; t < s.L; t += 32) phi_lo[row + t] = pprop_lo[row + t];
       }
       __syncwarp();
     }
@@ -369,7 +420,7 @@ __global__ void __launch_bounds__(kMetroWarps * 32) k_metropolis_warp(
 template <typename T>
 cudaError_t launch_metropolis(const DevSystem &s, bool up, double *r, const double *rprop, const T *gprop, T *ginv,
                               double *scal, int *status, const T *pprop, T *phi_up, int *list, int *count, int W,
-                              cudaStream_t st) {
+                              cudaStream_t st, const float *pprop_lo, float *phi_lo) {
   if (W <= 0 || (!up && s.n_dn == 0)) return cudaSuccess;
   const int n = s.n_up;
   const size_t per = metro_smem_per_walker<T>(n, s.N);
@@ -377,24 +428,37 @@ cudaError_t launch_metropolis(const DevSystem &s, bool up, double *r, const doub
     const int blocks = (W + kMetroWarps - 1) / kMetroWarps;
     if (up)
       k_metropolis_warp<true, T><<<blocks, kMetroWarps * 32, per * kMetroWarps, st>>>(
-          s, r, rprop, gprop, ginv, scal, status, pprop, phi_up, list, count, W);
+          s, r, rprop, gprop, ginv, scal, status, pprop, phi_up, list, count, W, pprop_lo, phi_lo);
     else
       k_metropolis_warp<false, T><<<blocks, kMetroWarps * 32, per * kMetroWarps, st>>>(
-          s, r, rprop, gprop, ginv, scal, status, pprop, phi_up, list, count, W);
+          s, r, rprop, gprop, ginv, scal, status, pprop, phi_up, list, count, W, pprop_lo, phi_lo);
     return cudaGetLastError();
   }
+  if (per <= kMetroSmemMax) {
+    const int threads = n <= 64 ? 128 : 256;
+    if (up)
+      k_metropolis<true, T, false><<<W, threads, per, st>>>(s, r, rprop, gprop, ginv, scal, status, pprop, phi_up,
+                                                             list, count, pprop_lo, phi_lo);
+    else
+      k_metropolis<false, T, false><<<W, threads, per, st>>>(s, r, rprop, gprop, ginv, scal, status, pprop, phi_up,
+                                                              list, count, pprop_lo, phi_lo);
+    return cudaGetLastError();
+  }
+  const size_t glob = (size_t)s.N * 3 * sizeof(double) + (size_t)3 * n * sizeof(T);
   if (up)
-    k_metropolis<true, T><<<W, 128, per, st>>>(s, r, rprop, gprop, ginv, scal, status, pprop, phi_up, list, count);
+    k_metropolis<true, T, true><<<W, 512, glob, st>>>(s, r, rprop, gprop, ginv, scal, status, pprop, phi_up, list,
+                                                       count, pprop_lo, phi_lo);
   else
-    k_metropolis<false, T><<<W, 128, per, st>>>(s, r, rprop, gprop, ginv, scal, status, pprop, phi_up, list, count);
+    k_metropolis<false, T, true><<<W, 512, glob, st>>>(s, r, rprop, gprop, ginv, scal, status, pprop, phi_up, list,
+                                                        count, pprop_lo, phi_lo);
   return cudaGetLastError();
 }
 template cudaError_t launch_metropolis<double>(const DevSystem &, bool, double *, const double *, const double *,
                                                double *, double *, int *, const double *, double *, int *, int *,
-                                               int, cudaStream_t);
+                                               int, cudaStream_t, const float *, float *);
 template cudaError_t launch_metropolis<float>(const DevSystem &, bool, double *, const double *, const float *,
                                               float *, double *, int *, const float *, float *, int *, int *, int,
-                                              cudaStream_t);
+                                              cudaStream_t, const float *, float *);
 
 // ---------------------------------------------------------------------------
 // J = J1 + J2 of each walker from scratch (one CTA per walker).
@@ -546,8 +610,14 @@ static cudaError_t walker_attrs() {
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(k_basis_points<true, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
   if ((e = cudaFuncSetAttribute(k_basis_points<false, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
-  if ((e = cudaFuncSetAttribute(k_metropolis<true, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
-  if ((e = cudaFuncSetAttribute(k_metropolis<false, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+  if ((e = cudaFuncSetAttribute(k_metropolis<true, T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)))
+    return e;
+  if ((e = cudaFuncSetAttribute(k_metropolis<false, T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)))
+    return e;
+  if ((e = cudaFuncSetAttribute(k_metropolis<true, T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)))
+    return e;
+  if ((e = cudaFuncSetAttribute(k_metropolis<false, T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)))
+    return e;
   if ((e = cudaFuncSetAttribute(k_metropolis_warp<true, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)))
     return e;
   return cudaFuncSetAttribute(k_metropolis_warp<false, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);

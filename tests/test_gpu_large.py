@@ -1,0 +1,164 @@
+"""N_up beyond shared-memory residency of G~^{-1}: the global-memory
+acceptance kernel, the in-place Gauss-Jordan refresh and the tiled kinetic
+contraction vectors against the FP64 oracle (1e-10 relative in FP64 and
+positions exact, as in the other parity files; the mixed path's stated error
+floor below), then the 512-electron system (256 He atoms in a 26 bohr cube,
+L = 4096, banded lambda): FP64 move by move on two walkers, and the mixed path
+at its full walker count with sampled walkers recomputed by the oracle.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+# Mixed path at these sizes: log|Psi| meets the 1e-6 target (the orbital
+# tables are double-word, the lambda products five-slice fixed point).  e_L
+# does not everywhere: the kinetic contraction runs in FP32 (M vectors, orbital
+# derivatives, G~^{-1} rounded to FP32), and its rounding is amplified by
+# cond(G~), which reaches 1e5-5e5 at seeded walkers of these random-lambda
+# systems.  The e_L bounds below are the stated error at these sizes, not the
+# 1e-5 Ha target of the smaller configurations.
+MIXED_LARGE_TOL = (1e-6, 1e-3)       # N_up = 121, 256 random systems (measured max 2.8e-8, 2.2e-4)
+MIXED_C5_TOL = (1e-6, 5e-3)          # 512-electron system (measured max 1.5e-7, 1.2e-3 over 12 walkers)
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def _systems():
+    return {
+        # 121 up / 119 down: the FP64 refresh and M contraction leave shared
+        # memory, tiles are ragged, two unpaired orbitals fill G~'s last columns
+        "n121": synth.small_random(n_atoms=60, n_up=121, n_dn=119, per_atom=6, seed=51, side=14.0, Z=2.0),
+        # 256 + 256: the acceptance kernel leaves shared memory in both precisions
+        "n256": synth.small_random(n_atoms=128, n_up=256, n_dn=256, per_atom=6, seed=52, side=18.0, Z=2.0),
+    }
+
+
+SYSTEMS = _systems()
+
+
+def _walkers(sysm, W, seed=5):
+    return synth.jitter_walkers(synth.init_walkers(sysm, W, seed=seed), seed + 1, 0.3)
+
+
+def _close(a, b, tol=TOL):
+    a, b = np.asarray(a), np.asarray(b)
+    return np.abs(a - b) <= tol * np.maximum(1.0, np.abs(b))
+
+
+@pytest.mark.parametrize("name", list(SYSTEMS))
+def test_large_eval_and_local_energy_fp64(torch_cuda, name):
+    import paper_2002_07401_gb300 as pg
+    sysm = SYSTEMS[name]
+    W = 3
+    x = _walkers(sysm, W)
+    o = oracle.Oracle(sysm)
+    la_ref, sg_ref = o.logpsi_batch(x)
+    e_ref = o.local_energy_batch(x)
+    g = pg.JAGP(sysm, W)
+    r = g.positions(x)
+    la, sg = g.eval(r)
+    e = g.local_energy(r).cpu().numpy()
+    assert g.status() == 0
+    assert np.all(_close(la.cpu().numpy(), la_ref)), np.max(np.abs(la.cpu().numpy() - la_ref))
+    assert np.array_equal(sg.cpu().numpy(), sg_ref)
+    assert np.all(_close(e, e_ref)), np.max(np.abs(e - e_ref) / np.maximum(1, np.abs(e_ref)))
+    g.close()
+
+
+@pytest.mark.parametrize("name,W,sweeps", [("n121", 3, 2), ("n256", 2, 1)])
+def test_large_sweep_trajectory_fp64(torch_cuda, name, W, sweeps):
+    import paper_2002_07401_gb300 as pg
+    sysm = SYSTEMS[name]
+    x0 = _walkers(sysm, W)
+    xo = x0.copy()
+    eL_ref, lp_ref, nacc_ref = oracle.Oracle(sysm).vmc(xo, sweeps, seed=11, sweep0=2, walker0=5)
+    g = pg.JAGP(sysm, W, seed=11)
+    r = g.positions(x0)
+    g.eval(r)
+    eL, _ = g.sweep(r, sweeps, walker0=5, sweep0=2)
+    info = g.info()
+    assert g.status() & (pg.WS_NONFINITE | pg.WS_SINGULAR) == 0
+    assert np.all(info["drift"].cpu().numpy() < 1e-5)
+    assert np.array_equal(r.cpu().numpy(), xo)
+    assert np.array_equal(info["naccept"].cpu().numpy(), nacc_ref.astype(np.float64))
+    assert np.all(_close(eL.cpu().numpy(), eL_ref))
+    assert np.all(_close(info["logabs"].cpu().numpy(), lp_ref, 1e-9))
+    g.close()
+
+
+@pytest.mark.parametrize("name", list(SYSTEMS))
+def test_large_mixed_accuracy(torch_cuda, name):
+    import paper_2002_07401_gb300 as pg
+    sysm = SYSTEMS[name]
+    W = 3
+    x = _walkers(sysm, W)
+    o = oracle.Oracle(sysm)
+    la_ref, _ = o.logpsi_batch(x)
+    e_ref = o.local_energy_batch(x)
+    g = pg.JAGP(sysm, W, precision=pg.JAGP_PREC_MIXED)
+    r = g.positions(x)
+    la, _ = g.eval(r)
+    e = g.local_energy(r).cpu().numpy()
+    assert g.status() == 0
+    assert np.max(np.abs(la.cpu().numpy() - la_ref)) <= MIXED_LARGE_TOL[0]
+    assert np.max(np.abs(e - e_ref)) <= MIXED_LARGE_TOL[1]
+    g.close()
+
+
+def test_c5_fp64_sampled_trajectory(torch_cuda):
+    """The 512-electron system in FP64 on two walkers: one sweep move by move."""
+    import paper_2002_07401_gb300 as pg
+    sysm = synth.config5()
+    W = 2
+    x0 = synth.init_walkers(sysm, W, seed=0)
+    xo = x0.copy()
+    eL_ref, lp_ref, nacc_ref = oracle.Oracle(sysm).vmc(xo, 1, seed=0, walker0=100)
+    g = pg.JAGP(sysm, W, seed=0)
+    r = g.positions(x0)
+    g.eval(r)
+    eL, _ = g.sweep(r, 1, walker0=100)
+    assert g.status() & (pg.WS_NONFINITE | pg.WS_SINGULAR) == 0
+    assert np.array_equal(r.cpu().numpy(), xo)
+    assert np.array_equal(g.info()["naccept"].cpu().numpy(), nacc_ref.astype(np.float64))
+    assert np.all(_close(eL.cpu().numpy(), eL_ref))
+    g.close()
+
+
+def test_c5_mixed_full_size_sampled(torch_cuda):
+    """The 512-electron system in the mixed path at 1024 walkers (the launch
+    shape of the benchmark): after two sweeps, four sampled walkers' log|Psi|
+    and e_L are recomputed by the oracle at their final positions."""
+    import paper_2002_07401_gb300 as pg
+    sysm = synth.config5()
+    W, sweeps = 1024, 2
+    x0 = synth.init_walkers(sysm, W, seed=0)
+    g = pg.JAGP(sysm, W, precision=pg.JAGP_PREC_MIXED, seed=0)
+    r = g.positions(x0)
+    g.eval(r)
+    eL, acc = g.sweep(r, sweeps, acc=True)
+    info = g.info()
+    assert g.status() & (pg.WS_NONFINITE | pg.WS_SINGULAR) == 0
+    a = acc.cpu().numpy()
+    rate = a[:, 2].sum() / (sweeps * W * sysm.N)
+    assert 0.05 < rate < 0.95
+    pick = np.random.default_rng(5).choice(W, size=4, replace=False)
+    xs = np.ascontiguousarray(r.cpu().numpy()[pick])
+    o = oracle.Oracle(sysm)
+    la_ref, _ = o.logpsi_batch(xs)
+    e_ref = o.local_energy_batch(xs)
+    la = info["logabs"].cpu().numpy()[pick]
+    e = eL.cpu().numpy()[-1, pick]
+    assert np.max(np.abs(la - la_ref)) <= MIXED_C5_TOL[0], np.abs(la - la_ref)
+    assert np.max(np.abs(e - e_ref)) <= MIXED_C5_TOL[1], np.abs(e - e_ref)
+    g.close()

@@ -1,6 +1,6 @@
-"""Mixed-precision path (FP32 orbitals and tables, BF16 tensor-core lambda
-products with a three-term split, FP64 refresh / log-det / energies) against
-the FP64 oracle.
+"""Mixed-precision path (double-word FP32 orbital tables, BF16 tensor-core
+lambda products on five-slice fixed-point operands, FP64 refresh / log-det /
+energies, FP32 kinetic contraction) against the FP64 oracle.
 
 Stated tolerances per configuration: |log|Psi| error| <= 1e-6 and
 |e_L error| <= 1e-5 Ha.  Sampling: the mixed path's accept decisions are taken
@@ -20,9 +20,10 @@ pytestmark = pytest.mark.gpu
 LOGPSI_TOL = 1e-6
 EL_TOL = 1e-5
 # The N_up = 40 random system is an ill-conditioned stress case outside the
-# workload configurations; its measured errors (about 2e-6 on log|Psi| and
-# 4e-5 Ha on e_L) are stated rather than held to the workload targets.
-STRESS_TOL = {"mid-n40": (5e-6, 1e-4)}
+# workload configurations; its measured e_L error (about 3e-5 Ha, from the FP32
+# kinetic contraction amplified by cond(G~)) is stated rather than held to the
+# workload target.
+STRESS_TOL = {"mid-n40": (1e-6, 1e-4)}
 
 
 @pytest.fixture(scope="module")
@@ -39,7 +40,17 @@ SYSTEMS = {
     "small-unpaired-slater": lambda: synth.small_random(n_atoms=3, n_up=4, n_dn=2, per_atom=20, seed=31,
                                                         slater_fraction=0.3),
     "mid-n40": lambda: synth.small_random(n_atoms=20, n_up=40, n_dn=37, per_atom=6, seed=33, side=7.0, Z=2.0),
+    # the batched workload's systems: smallest, median and largest electron count
+    "C3-min": lambda: _c3("min"),
+    "C3-median": lambda: _c3("median"),
+    "C3-max": lambda: _c3("max"),
 }
+
+
+def _c3(which):
+    systems = synth.config3_systems()
+    order = np.argsort([s.N for s in systems], kind="stable")
+    return systems[int({"min": order[0], "median": order[len(order) // 2], "max": order[-1]}[which])]
 
 
 def _equilibrated(sysm, W, sweeps=20, seed=5):
@@ -100,3 +111,24 @@ def test_mixed_hydrogen_zero_variance(torch_cuda):
     g.eval(r)
     eL, _ = g.sweep(r, 4)
     assert np.max(np.abs(eL.cpu().numpy() + 0.5)) < EL_TOL
+
+
+def test_fp32_orbital_value_is_rounded_once(torch_cuda):
+    """One electron in one Gaussian orbital: log|Psi| = -alpha r^2 exactly, so
+    the mixed path's log|Psi| exposes the FP32 orbital value's own error: at
+    most half an FP32 ulp from the rounding plus a few 1e-9 from the
+    exponential, for alpha r^2 up to 85 (above the FP32 denormal range)."""
+    import paper_2002_07401_gb300 as pg
+    alpha = 1.3
+    sysm = synth.one_electron_gauss(alpha)
+    W = 4096
+    rng = np.random.default_rng(3)
+    rad = np.sqrt(rng.uniform(0.0, 85.0 / alpha, W))
+    d = rng.normal(size=(W, 3))
+    x = np.ascontiguousarray((d / np.linalg.norm(d, axis=1, keepdims=True) * rad[:, None])[:, None, :])
+    g = pg.JAGP(sysm, W, precision=pg.JAGP_PREC_MIXED)
+    la, _ = g.eval(g.positions(x))
+    exact = -alpha * (x[:, 0, :] ** 2).sum(1)
+    err = np.abs(la.cpu().numpy() - exact)
+    assert err.max() <= 2.0 ** -24 + 5e-9, err.max()
+    g.close()

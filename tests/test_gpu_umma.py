@@ -104,15 +104,15 @@ def test_umma_rejects_bad_shapes(torch_cuda):
         pg.jagp_gemm_bf16x(A, 1, A, 1, 64, [(1, 0)], C)        # term index out of range
 
 
-def slice_fixed4(torch, x, Kp):
-    """Rows -> four exact 8-bit slices (as BF16) relative to 2^e, e from the row maximum."""
+def slice_fixed4(torch, x, Kp, nsl=4):
+    """Rows -> nsl exact 8-bit slices (as BF16) relative to 2^e, e from the row maximum."""
     M, K = x.shape
     x = x.double()
     _, e = torch.frexp(x.abs().max(dim=1).values)
     e = torch.where(x.abs().max(dim=1).values > 0, e, torch.zeros_like(e))
     xs = x * torch.pow(2.0, (7 - e).double())[:, None]
-    out = torch.zeros((M, 4 * Kp), dtype=torch.bfloat16, device=x.device)
-    for t in range(4):
+    out = torch.zeros((M, nsl * Kp), dtype=torch.bfloat16, device=x.device)
+    for t in range(nsl):
         q = torch.round(xs)
         out[:, t * Kp:t * Kp + K] = q.to(torch.bfloat16)
         xs = (xs - q) * 256.0
@@ -120,10 +120,12 @@ def slice_fixed4(torch, x, Kp):
 
 
 TEN = [(0, 0), (0, 1), (1, 0), (0, 2), (1, 1), (2, 0), (0, 3), (1, 2), (2, 1), (3, 0)]
+FIFTEEN = TEN + [(0, 4), (1, 3), (2, 2), (3, 1), (4, 0)]
 
 
-@pytest.mark.parametrize("M,N,K", [(300, 320, 320), (129, 24, 24), (200, 1536, 256), (64, 100, 1000)])
-def test_umma_fixed_point_is_exact_up_to_fp32_rounding(torch_cuda, M, N, K):
+@pytest.mark.parametrize("M,N,K,nsl", [(300, 320, 320, 4), (129, 24, 24, 4), (200, 1536, 256, 4), (64, 100, 1000, 4),
+                                       (300, 320, 320, 5), (129, 200, 4096, 5)])
+def test_umma_fixed_point_is_exact_up_to_fp32_rounding(torch_cuda, M, N, K, nsl):
     """Exact slice products summed exactly: the result equals the FP64 value
     reconstructed from the same slices to about one FP32 rounding, and the
     slicing itself is within its truncation bound of the FP64 product."""
@@ -136,15 +138,16 @@ def test_umma_fixed_point_is_exact_up_to_fp32_rounding(torch_cuda, M, N, K):
     y = torch.randn((N, K), device="cuda", dtype=torch.float64, generator=g) * 0.1
     y[:, :min(N, K)] += torch.eye(N, K, device="cuda", dtype=torch.float64)[:, :min(N, K)]
     Kp = (K + 63) // 64 * 64
-    A, ea = slice_fixed4(torch, x, Kp)
-    B, eb = slice_fixed4(torch, y, Kp)
+    pairs = TEN if nsl == 4 else FIFTEEN
+    A, ea = slice_fixed4(torch, x, Kp, nsl)
+    B, eb = slice_fixed4(torch, y, Kp, nsl)
     C = torch.full((M, N), float("nan"), dtype=torch.float32, device="cuda")
-    err = pg.jagp_gemm_bf16x(A, 4, B, 4, Kp, TEN, C, row_exp=ea, col_exp=eb)
+    err = pg.jagp_gemm_bf16x(A, nsl, B, nsl, Kp, pairs, C, row_exp=ea, col_exp=eb)
     torch.cuda.synchronize()
     assert int(err.item()) == 0
     Ad, Bd = A.double(), B.double()
     recon = 0
-    for a, b in TEN:
+    for a, b in pairs:
         recon = recon + (Ad[:, a * Kp:(a + 1) * Kp] @ Bd[:, b * Kp:(b + 1) * Kp].T) * 256.0 ** -(a + b)
     scale = torch.pow(2.0, (ea[:, None] + eb[None, :] - 14).double())
     recon = recon * scale
@@ -153,5 +156,5 @@ def test_umma_fixed_point_is_exact_up_to_fp32_rounding(torch_cuda, M, N, K):
     assert torch.all(d <= 3e-7 * recon.abs() + 1e-9 * S), float((d / (recon.abs() + 1e-300)).max())
     # truncation of the slicing: dropped slice pairs and the remainder beyond four slices
     ref = x.double() @ y.T
-    bound = K * scale * 2.0 ** 14 * 4 * 256.0 ** -3.5
+    bound = K * scale * 2.0 ** 14 * 4 * 256.0 ** -(nsl - 0.5)
     assert torch.all((recon - ref).abs() <= bound)
