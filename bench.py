@@ -39,6 +39,7 @@ WORKLOAD = ("plain FP64 VMC: 16 He atoms in a 10 bohr cube (min separation 1.5),
 FP64_PEAK_TFLOPS = 1.25
 # BF16 dense tensor-core peak, sustained (the machine's fallback figure; no measured file)
 BF16_SUSTAINED_TFLOPS = 1700.0
+FIXED_PAIRS = 15  # BF16 slice-pair products per element of the mixed path's lambda products
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "k_lambda_rows_C2_traffic.txt")
 
 
@@ -368,6 +369,40 @@ def batch_bench(pg, torch, dist, args, dev, rank, ws):
             "dtype": "f32+bf16 (f64 refresh)", "workload": BATCH_WORKLOAD}
 
 
+LARGE_WORKLOAD = ("large system, mixed precision: 256 He atoms in a 26 bohr cube (min separation 1.5), N=512 "
+                  "(256 up, 256 down), 16 s/p/d Gaussians/atom (L=4096), banded lambda (|i-j| <= 204) stored dense, "
+                  "J1 + J2, 1024 walkers/GPU; FP64 refresh of G^-1 every N_up moves, e_L every sweep")
+
+
+def large_bench(pg, torch, dist, args, dev, rank, ws, local):
+    """Walker-electron moves/s of the mixed path on the 512-electron system
+    (G^-1 in global memory, in-place Gauss-Jordan refresh, tiled kernels)."""
+    import numpy as np
+    import synth
+    sysm = synth.config5()
+    W = args.large_walkers
+    x0 = np.ascontiguousarray(synth.init_walkers(sysm, W * ws, seed=0)[rank * W:(rank + 1) * W])
+    rr = timed_sweeps(pg, torch, dist, sysm, W, rank * W, x0, pg.JAGP_PREC_MIXED, args.large_steps, 3, ws, dev,
+                      local, pg.KERNEL_LAMBDA_ROWS)
+    rr["g"].close()
+    N, L = sysm.N, sysm.L
+    kp = (L + 63) // 64 * 64
+    secs = rr["prof_ms"] / 1e3
+    issued = FIXED_PAIRS * 2.0 * kp * L * rr["accepted"]
+    tc = issued / secs / 1e12 if secs > 0 else None
+    return {"metric": "walker-electron moves/s", "value": W * N * args.large_steps * ws / (rr["ms_max"] / 1e3),
+            "unit": "walker-electron moves/s", "ms_per_sweep": rr["ms_max"] / args.large_steps,
+            "sweeps": args.large_steps, "warmup": 3, "walkers_per_gpu": W,
+            "acceptance": rr["accepted"] / (W * N * args.large_steps), "status_bits": rr["bits"],
+            "gpu_launches": rr["launches"], "dtype": "f32+bf16 (f64 refresh)", "workload": LARGE_WORKLOAD,
+            "clocks": rr["clocks"],
+            "roofline": {"kernel": "k_umma_gemm (tcgen05, BF16 fixed-point slices)", "bound": "tensor",
+                         "achieved": tc, "peak": BF16_SUSTAINED_TFLOPS, "unit": "TFLOP/s",
+                         "frac": tc / BF16_SUSTAINED_TFLOPS if tc else None, "traffic": None,
+                         "peak_source": "fallback BF16 sustained (no MEASURED_PEAKS file)",
+                         "launches": rr["prof_n"], "share_of_step": rr["prof_ms"] / rr["ms"] if rr["ms"] > 0 else None}}
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -384,6 +419,16 @@ def run_gpu(args):
     dev = torch.device("cuda", local)
     if ws > 1:
         dist.init_process_group("nccl", device_id=dev)
+
+    if args.large_only:
+        # the 512-electron measurement alone (for profiling its launches)
+        large = large_bench(pg, torch, dist, args, dev, rank, ws, local)
+        if rank == 0:
+            emit(dict(large, n_gpus=ws, higher_is_better=True, scaling="weak", data="synthetic"))
+        if ws > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return 0
 
     sysm = synth.config2()
     W = args.walkers
@@ -431,6 +476,7 @@ def run_gpu(args):
 
     forces = None if args.no_forces else forces_bench(pg, torch, dist, args, dev, rank, ws, local)
     batched = None if args.no_batch else batch_bench(pg, torch, dist, args, dev, rank, ws)
+    large = None if args.no_large else large_bench(pg, torch, dist, args, dev, rank, ws, local)
 
     if rank != 0:
         if ws > 1:
@@ -450,7 +496,7 @@ def run_gpu(args):
              "gpu_launches": rr["launches"], "clocks": rr["clocks"]}
         if mixed:
             kp = (L + 63) // 64 * 64
-            issued = 10 * 2.0 * kp * L * rr["accepted"]  # ten BF16 slice-pair products per row
+            issued = FIXED_PAIRS * 2.0 * kp * L * rr["accepted"]  # BF16 slice-pair products per row
             tc = issued / secs / 1e12 if secs > 0 else None
             d["roofline"] = {"kernel": "k_umma_gemm (tcgen05, BF16 fixed-point slices)", "bound": "tensor",
                              "achieved": tc, "peak": BF16_SUSTAINED_TFLOPS, "unit": "TFLOP/s",
@@ -495,6 +541,8 @@ def run_gpu(args):
         out["forces"] = forces
     if batched is not None:
         out["batched"] = batched
+    if large is not None:
+        out["large"] = large
     if ws == 1 and not args.no_cpu_baseline:
         mv, els, cores, sample, secs = oracle_rate(sysm, target_s=args.cpu_seconds)
         out["cpu_baseline"] = {"value": mv, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -524,6 +572,10 @@ def main():
     ap.add_argument("--batch-walkers", type=int, default=512)
     ap.add_argument("--batch-sweeps", type=int, default=20)
     ap.add_argument("--batch-streams", type=int, default=16)
+    ap.add_argument("--no-large", action="store_true", help="skip the 512-electron mixed-precision measurement")
+    ap.add_argument("--large-walkers", type=int, default=1024)
+    ap.add_argument("--large-steps", type=int, default=3)
+    ap.add_argument("--large-only", action="store_true", help="run only the 512-electron measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     args = ap.parse_args()
