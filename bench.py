@@ -39,7 +39,15 @@ WORKLOAD = ("plain FP64 VMC: 16 He atoms in a 10 bohr cube (min separation 1.5),
 FP64_PEAK_TFLOPS = 1.25
 # BF16 dense tensor-core peak, sustained (the machine's fallback figure; no measured file)
 BF16_SUSTAINED_TFLOPS = 1700.0
-FIXED_PAIRS = 15  # BF16 slice-pair products per element of the mixed path's lambda products
+# BF16 slice-pair products per element of the mixed path's lambda products: the
+# up-spin rows (phi^T lambda, FP32 result) take 10, the down-spin rows (lambda
+# phi, two-float result) 15; accepted moves are split between the spins in
+# proportion to their electron counts when the issued work is counted
+PAIRS_UP, PAIRS_DN = 10, 15
+
+
+def fixed_pairs(sysm):
+    return (PAIRS_UP * sysm.n_up + PAIRS_DN * sysm.n_dn) / sysm.N
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "k_lambda_rows_C2_traffic.txt")
 
 
@@ -388,7 +396,7 @@ def large_bench(pg, torch, dist, args, dev, rank, ws, local):
     N, L = sysm.N, sysm.L
     kp = (L + 63) // 64 * 64
     secs = rr["prof_ms"] / 1e3
-    issued = FIXED_PAIRS * 2.0 * kp * L * rr["accepted"]
+    issued = fixed_pairs(sysm) * 2.0 * kp * L * rr["accepted"]
     tc = issued / secs / 1e12 if secs > 0 else None
     return {"metric": "walker-electron moves/s", "value": W * N * args.large_steps * ws / (rr["ms_max"] / 1e3),
             "unit": "walker-electron moves/s", "ms_per_sweep": rr["ms_max"] / args.large_steps,
@@ -496,7 +504,7 @@ def run_gpu(args):
              "gpu_launches": rr["launches"], "clocks": rr["clocks"]}
         if mixed:
             kp = (L + 63) // 64 * 64
-            issued = FIXED_PAIRS * 2.0 * kp * L * rr["accepted"]  # BF16 slice-pair products per row
+            issued = fixed_pairs(sysm) * 2.0 * kp * L * rr["accepted"]  # BF16 slice-pair products per row
             tc = issued / secs / 1e12 if secs > 0 else None
             d["roofline"] = {"kernel": "k_umma_gemm (tcgen05, BF16 fixed-point slices)", "bound": "tensor",
                              "achieved": tc, "peak": BF16_SUSTAINED_TFLOPS, "unit": "TFLOP/s",

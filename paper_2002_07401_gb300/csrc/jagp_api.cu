@@ -68,7 +68,11 @@ Layout layout_of(const jagp_ctx *h, int W) {
 }
 
 // the fifteen slice pairs (a, b) with a + b <= 4 of the five-slice fixed-point
-// operands (each row kept to 2^-39 of its largest magnitude)
+// operands (each row kept to 2^-39 of its largest magnitude).  The rows
+// phi^T lambda (A_up) only feed FP32 work (proposed columns, M vectors), so
+// they take the first ten pairs (a + b <= 3: 2^-31, beyond FP32 rounding);
+// the rows lambda phi (Bt) enter G~ as two-float numbers and take all fifteen.
+constexpr int kFixedPairsF32 = 10;
 const int kPairA[kFixedPairs] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3, 0, 1, 2, 3, 4};
 const int kPairB[kFixedPairs] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0, 4, 3, 2, 1, 0};
 
@@ -134,8 +138,8 @@ jagp_status_t lambda_products(jagp_ctx *h, const float *P, const float *P_lo, fl
   float *out_lo = left ? nullptr : at<float>(state, L.bt_lo);
   LAUNCH(JAGP_KERNEL_LAMBDA_ROWS, 1,
          launch_umma_gemm(pack, max_rows, count, kFixedSlices, left ? h->split_lamT : h->split_lam, h->ds.L,
-                          kFixedSlices, h->kp, kFixedPairs, kPairA, kPairB, out, h->ds.L, rows, h->d_err, st, exps,
-                          left ? h->exp_lamT : h->exp_lam, out_lo));
+                          kFixedSlices, h->kp, left ? kFixedPairsF32 : kFixedPairs, kPairA, kPairB, out, h->ds.L,
+                          rows, h->d_err, st, exps, left ? h->exp_lamT : h->exp_lam, out_lo));
   return JAGP_OK;
 }
 

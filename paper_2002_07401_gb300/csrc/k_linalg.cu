@@ -93,10 +93,126 @@ __global__ void __launch_bounds__(256) k_gemm_rows_dot2(const float *__restrict_
     Out[(size_t)w * ow + (size_t)(a0 + ty) * ldo + b0 + tx] = static_cast<double>(s) + static_cast<double>(c);
 }
 
+// ---------------------------------------------------------------------------
+// Register-blocked variant of the two kernels above for N_up >= 32: a TM x TM
+// output tile per CTA of 256 threads, R x R outputs per thread (R = TM / 16),
+// operands staged through shared memory in k-chunks of 32, transposed so that
+// each thread reads R consecutive entries of a column.  With DOT2 every output
+// keeps the compensated pair (s, c) of the kernel above; the order of the
+// k-sum is the same as there.
+// ---------------------------------------------------------------------------
+template <typename T, int TM, bool DOT2, typename OutT>
+__global__ void __launch_bounds__(256) k_gemm_rows_blk(const T *__restrict__ X, const float *__restrict__ Xlo,
+                                                       size_t xw, const T *__restrict__ Y,
+                                                       const float *__restrict__ Ylo, size_t yw, int ma, int nb,
+                                                       int K, OutT *__restrict__ Out, size_t ow, int ldo) {
+  constexpr int KC = 32, R = TM / 16, PAD = TM + 1;
+  __shared__ T Xs[KC][PAD];
+  __shared__ T Ys[KC][PAD];
+  __shared__ float Xl[DOT2 ? KC : 1][DOT2 ? PAD : 1];
+  __shared__ float Yl[DOT2 ? KC : 1][DOT2 ? PAD : 1];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int w = blockIdx.z, a0 = blockIdx.y * TM, b0 = blockIdx.x * TM;
+  const T *Xw = X + (size_t)w * xw;
+  const T *Yw = Y + (size_t)w * yw;
+  T acc[R][R];
+  float cmp[DOT2 ? R : 1][DOT2 ? R : 1];
+#pragma unroll
+  for (int i = 0; i < R; ++i)
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      acc[i][j] = T(0);
+      if constexpr (DOT2) cmp[i][j] = 0.0f;
+    }
+  for (int k0 = 0; k0 < K; k0 += KC) {
+    // TM rows x KC columns of each operand; consecutive threads take consecutive k
+#pragma unroll
+    for (int q = 0; q < TM * KC / 256; ++q) {
+      const int idx = tid + q * 256, row = idx / KC, kk = idx % KC;
+      const int k = k0 + kk, a = a0 + row, b = b0 + row;
+      const bool xa = a < ma && k < K, yb = b < nb && k < K;
+      const size_t xi = (size_t)a * K + k, yi = (size_t)b * K + k;
+      Xs[kk][row] = xa ? Xw[xi] : T(0);
+      Ys[kk][row] = yb ? Yw[yi] : T(0);
+      if constexpr (DOT2) {
+        Xl[kk][row] = (Xlo && xa) ? Xlo[(size_t)w * xw + xi] : 0.0f;
+        Yl[kk][row] = (Ylo && yb) ? Ylo[(size_t)w * yw + yi] : 0.0f;
+      }
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < KC; ++kk) {
+      T xa[R], yb[R];
+#pragma unroll
+      for (int i = 0; i < R; ++i) xa[i] = Xs[kk][ty * R + i];
+#pragma unroll
+      for (int j = 0; j < R; ++j) yb[j] = Ys[kk][tx * R + j];
+      if constexpr (DOT2) {
+        float xl[R], yl[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) xl[i] = Xl[kk][ty * R + i];
+#pragma unroll
+        for (int j = 0; j < R; ++j) yl[j] = Yl[kk][tx * R + j];
+#pragma unroll
+        for (int i = 0; i < R; ++i)
+#pragma unroll
+          for (int j = 0; j < R; ++j) {
+            const float x = xa[i], y = yb[j], s = acc[i][j];
+            const float p = __fmul_rn(x, y);
+            const float pe = __fmaf_rn(x, y, -p);
+            const float t = __fadd_rn(s, p);
+            const float z = __fsub_rn(t, s);
+            const float se = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
+            acc[i][j] = t;
+            const float cross = __fmaf_rn(xl[i], y, __fmul_rn(x, yl[j]));
+            cmp[i][j] = __fadd_rn(cmp[i][j], __fadd_rn(__fadd_rn(cross, pe), se));
+          }
+      } else {
+#pragma unroll
+        for (int i = 0; i < R; ++i)
+#pragma unroll
+          for (int j = 0; j < R; ++j) acc[i][j] = fma(xa[i], yb[j], acc[i][j]);
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    const int a = a0 + ty * R + i;
+    if (a >= ma) continue;
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      const int b = b0 + tx * R + j;
+      if (b >= nb) continue;
+      OutT v;
+      if constexpr (DOT2)
+        v = static_cast<double>(acc[i][j]) + static_cast<double>(cmp[i][j]);
+      else
+        v = acc[i][j];
+      Out[(size_t)w * ow + (size_t)a * ldo + b] = v;
+    }
+  }
+}
+
+// tile of the blocked variant for an ma x nb output (0: the one-output-per-thread kernel)
+inline int gemm_rows_tile(int ma, int nb) {
+  const int m = ma < nb ? ma : nb;
+  return m >= 64 ? 64 : (m >= 32 ? 32 : 0);
+}
+
 cudaError_t launch_gemm_rows_dot2(const float *X, const float *Xlo, size_t xw, const float *Y, const float *Ylo,
                                   size_t yw, int ma, int nb, int K, double *Out, size_t ow, int ldo, int W,
                                   cudaStream_t st) {
   if (W <= 0 || ma <= 0 || nb <= 0) return cudaSuccess;
+  const int tm = gemm_rows_tile(ma, nb);
+  if (tm) {
+    dim3 grid((nb + tm - 1) / tm, (ma + tm - 1) / tm, W);
+    if (tm == 64)
+      k_gemm_rows_blk<float, 64, true, double><<<grid, 256, 0, st>>>(X, Xlo, xw, Y, Ylo, yw, ma, nb, K, Out, ow, ldo);
+    else
+      k_gemm_rows_blk<float, 32, true, double><<<grid, 256, 0, st>>>(X, Xlo, xw, Y, Ylo, yw, ma, nb, K, Out, ow, ldo);
+    return cudaGetLastError();
+  }
   dim3 grid((nb + 15) / 16, (ma + 15) / 16, W);
   k_gemm_rows_dot2<<<grid, 256, 0, st>>>(X, Xlo, xw, Y, Ylo, yw, ma, nb, K, Out, ow, ldo);
   return cudaGetLastError();
@@ -106,6 +222,15 @@ template <typename T>
 cudaError_t launch_gemm_rows(const T *X, size_t xw, const T *Y, size_t yw, int ma, int nb, int K, T *Out, size_t ow,
                              int ldo, int W, cudaStream_t st) {
   if (W <= 0 || ma <= 0 || nb <= 0) return cudaSuccess;
+  const int tm = gemm_rows_tile(ma, nb);
+  if (tm) {
+    dim3 grid((nb + tm - 1) / tm, (ma + tm - 1) / tm, W);
+    if (tm == 64)
+      k_gemm_rows_blk<T, 64, false, T><<<grid, 256, 0, st>>>(X, nullptr, xw, Y, nullptr, yw, ma, nb, K, Out, ow, ldo);
+    else
+      k_gemm_rows_blk<T, 32, false, T><<<grid, 256, 0, st>>>(X, nullptr, xw, Y, nullptr, yw, ma, nb, K, Out, ow, ldo);
+    return cudaGetLastError();
+  }
   dim3 grid((nb + 15) / 16, (ma + 15) / 16, W);
   k_gemm_rows<T><<<grid, 256, 0, st>>>(X, xw, Y, yw, ma, nb, K, Out, ow, ldo);
   return cudaGetLastError();
@@ -164,6 +289,21 @@ cudaError_t launch_fill_unpaired_lo(const DevSystem &s, float *lo, int W, cudaSt
 }
 template cudaError_t launch_fill_unpaired<float>(const DevSystem &, float *, int, cudaStream_t);
 
+// log|prod of pivots| without a logarithm per pivot: the product is kept as a
+// mantissa in [1/2, 1) and a binary exponent (frexp after every factor), and
+// one log at the end gives log|m| + E ln 2.
+struct PivotProduct {
+  double m = 1.0;
+  int e = 0;
+  __device__ __forceinline__ void mul(double pv) {
+    int e1, e2;
+    const double a = frexp(fabs(pv), &e1);
+    m = frexp(m * a, &e2);
+    e += e1 + e2;
+  }
+  __device__ __forceinline__ double log_abs() const { return log(m) + e * 0.6931471805599453; }
+};
+
 // ---------------------------------------------------------------------------
 // FP64 refresh: Gauss-Jordan elimination with partial pivoting on [G~ | I]
 // (one CTA per walker, the n x 2n block in shared memory).  log|det G~| is the
@@ -195,7 +335,8 @@ __global__ void __launch_bounds__(256) k_refresh_inverse(const double *__restric
     }
     A[i * ld + j] = v;
   }
-  double logdet = 0.0, sgn = 1.0;
+  PivotProduct pp;
+  double sgn = 1.0;
   bool ok = true;
   __syncthreads();
   for (int k = 0; k < n; ++k) {
@@ -238,7 +379,7 @@ __global__ void __launch_bounds__(256) k_refresh_inverse(const double *__restric
       }
       sgn = -sgn;
     }
-    logdet += log(fabs(pv));
+    pp.mul(pv);
     if (pv < 0.0) sgn = -sgn;
     __syncthreads();
     const double ip = 1.0 / pv;
@@ -284,7 +425,7 @@ __global__ void __launch_bounds__(256) k_refresh_inverse(const double *__restric
       d = fmax(d, red[q]);
       g = fmax(g, red[16 + q]);
     }
-    scal[(size_t)w * S_STRIDE + S_LOGDET] = logdet;
+    scal[(size_t)w * S_STRIDE + S_LOGDET] = pp.log_abs();
     scal[(size_t)w * S_STRIDE + S_SIGN] = sgn;
     if (check_drift) {
       const double drift = d * g;
@@ -325,7 +466,8 @@ __global__ void __launch_bounds__(kRefreshWarps * 32) k_refresh_inverse_warp(
     A[i * ld + j] = v;
   }
   __syncwarp();
-  double logdet = 0.0, sgn = 1.0;
+  PivotProduct pp;
+  double sgn = 1.0;
   bool ok = true;
   for (int k = 0; k < n; ++k) {
     double best = -1.0;
@@ -360,7 +502,7 @@ __global__ void __launch_bounds__(kRefreshWarps * 32) k_refresh_inverse_warp(
       }
       sgn = -sgn;
     }
-    logdet += log(fabs(pv));
+    pp.mul(pv);
     if (pv < 0.0) sgn = -sgn;
     __syncwarp();
     const double ip = 1.0 / pv;
@@ -398,7 +540,7 @@ __global__ void __launch_bounds__(kRefreshWarps * 32) k_refresh_inverse_warp(
     gmax = fmax(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
   }
   if (lane == 0) {
-    sw[S_LOGDET] = logdet;
+    sw[S_LOGDET] = pp.log_abs();
     sw[S_SIGN] = sgn;
     if (check_drift) {
       const double drift = dmax * gmax;
@@ -428,7 +570,8 @@ __global__ void __launch_bounds__(512) k_refresh_inverse_global(double *__restri
   double *A = gm + (size_t)w * n * n;
   double gmax = 0.0;
   for (int idx = tid; idx < n * n; idx += bs) gmax = fmax(gmax, fabs(A[idx]));
-  double logdet = 0.0, sgn = 1.0;
+  PivotProduct pp;
+  double sgn = 1.0;
   bool ok = true;
   __syncthreads();
   for (int k = 0; k < n; ++k) {
@@ -471,7 +614,7 @@ __global__ void __launch_bounds__(512) k_refresh_inverse_global(double *__restri
       }
       sgn = -sgn;
     }
-    logdet += log(fabs(pv));
+    pp.mul(pv);
     if (pv < 0.0) sgn = -sgn;
     if (tid == 0) perm[k] = p;
     __syncthreads();
@@ -530,7 +673,7 @@ __global__ void __launch_bounds__(512) k_refresh_inverse_global(double *__restri
       d = fmax(d, red[q]);
       g = fmax(g, red[16 + q]);
     }
-    scal[(size_t)w * S_STRIDE + S_LOGDET] = logdet;
+    scal[(size_t)w * S_STRIDE + S_LOGDET] = pp.log_abs();
     scal[(size_t)w * S_STRIDE + S_SIGN] = sgn;
     if (check_drift) {
       const double drift = d * g;
