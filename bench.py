@@ -223,6 +223,7 @@ def timed_sweeps(pg, torch, dist, sysm, W, walker0, x0, prec, steps, warmup, ws,
     launching stream; the profiled kernel class is bracketed by event pairs."""
     g = pg.JAGP(sysm, W, seed=0, precision=prec)
     h = g.h
+    tuning = g.autotune()  # tile choices for this system and walker count (overwrites the state)
     r = g.positions(x0)
     stream = torch.cuda.current_stream()
     eL = torch.empty((1, W), dtype=torch.float64, device=dev)
@@ -259,7 +260,7 @@ def timed_sweeps(pg, torch, dist, sysm, W, walker0, x0, prec, steps, warmup, ws,
     bits |= g.status()
     return {"g": g, "r": r, "eL": eL, "ms": ms, "ms_max": float(t.item()), "launches": launches,
             "prof_ms": prof_ms, "prof_n": prof_n, "accepted": float(acc[:, 2].sum()), "bits": bits,
-            "clocks": clk.summary()}
+            "clocks": clk.summary(), "tuning": tuning}
 
 
 FORCES_WORKLOAD = ("adjoint gradients: 64 He atoms in a 16 bohr cube, N=128 (64 up, 64 down), 24 s/p/d Gaussians/"
@@ -403,7 +404,7 @@ def large_bench(pg, torch, dist, args, dev, rank, ws, local):
             "sweeps": args.large_steps, "warmup": 3, "walkers_per_gpu": W,
             "acceptance": rr["accepted"] / (W * N * args.large_steps), "status_bits": rr["bits"],
             "gpu_launches": rr["launches"], "dtype": "f32+bf16 (f64 refresh)", "workload": LARGE_WORKLOAD,
-            "clocks": rr["clocks"],
+            "clocks": rr["clocks"], "tuning": rr["tuning"],
             "roofline": {"kernel": "k_umma_gemm (tcgen05, BF16 fixed-point slices)", "bound": "tensor",
                          "achieved": tc, "peak": BF16_SUSTAINED_TFLOPS, "unit": "TFLOP/s",
                          "frac": tc / BF16_SUSTAINED_TFLOPS if tc else None, "traffic": None,
@@ -501,7 +502,7 @@ def run_gpu(args):
         d = {"value": value, "ms_per_step": rr["ms_max"] / args.steps,
              "el_per_s": W * args.steps * ws / (rr["ms_max"] / 1e3),
              "acceptance": rr["accepted"] / (W * N * args.steps), "status_bits": rr["bits"],
-             "gpu_launches": rr["launches"], "clocks": rr["clocks"]}
+             "gpu_launches": rr["launches"], "clocks": rr["clocks"], "tuning": rr["tuning"]}
         if mixed:
             kp = (L + 63) // 64 * 64
             issued = fixed_pairs(sysm) * 2.0 * kp * L * rr["accepted"]  # BF16 slice-pair products per row
@@ -535,7 +536,7 @@ def run_gpu(args):
                    "precision": args.precision, "l2": "inputs larger than L2 (walker state ~1 GB per GPU)",
                    "parallelism": f"walker shards x{ws}"},
         "el_per_s": prim["el_per_s"], "acceptance": prim["acceptance"], "status_bits": prim["status_bits"],
-        "roofline": prim["roofline"], "gpu_launches": prim["gpu_launches"],
+        "roofline": prim["roofline"], "gpu_launches": prim["gpu_launches"], "tuning": prim["tuning"],
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(hx.numel() * 8),
                 "d2h_bytes_per_step": int(he.numel() * 8 + hr.numel() * 8), "steps": e2e_steps},
         "clocks": prim["clocks"],

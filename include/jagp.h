@@ -181,6 +181,26 @@ jagp_status_t jagp_walker_info(jagp_handle_t h, const void *d_state, int W, doub
 jagp_status_t jagp_walker_status(jagp_handle_t h, const void *d_state, int W, int *h_bits,
                                  void *stream);
 
+/* Tile autotuner (no counterpart in the paper: a property of this GPU code).
+ * Times the candidate tilings of the per-walker products (proposed rows and
+ * columns: one output per thread, 32x32 or 64x64 register-blocked tiles; the
+ * refresh product G~ = Phi_up Bt^T likewise) and, in the mixed path, the
+ * output-tile width of the tensor-core lambda products (32..128 columns), on
+ * this handle's operands and the caller's state buffer of W walkers; keeps the
+ * fastest in the handle for every later call.  The choices change only the
+ * tiling of outputs, never the order of a sum: results are identical with or
+ * without tuning.  The state's tables are overwritten: call jagp_eval before
+ * the next sweep.  Synchronises `stream`.  out (host) receives the choices and
+ * the best times (ms per call: proposals, refresh, A_up rows, Bt rows). */
+typedef struct {
+  int tile_proposals;  /* 0: one output per thread; 32 / 64: blocked tiles */
+  int tile_refresh;
+  int umma_bn_left;    /* mixed path: tensor-core tile width, A_up = phi^T lambda (0 in FP64) */
+  int umma_bn_right;   /* mixed path: tensor-core tile width, Bt = lambda phi */
+  float ms[4];
+} jagp_tuning_t;
+jagp_status_t jagp_autotune(jagp_handle_t h, void *d_state, int W, jagp_tuning_t *out, void *stream);
+
 /* The tensor-core contraction behind the lambda products of the mixed
  * precision path (Sec. AGP, Eq. agp_expansion: rows phi^T lambda and
  * lambda phi), exposed for direct use and testing.  tcgen05.mma (BF16 in,

@@ -44,6 +44,11 @@ class _Options(C.Structure):
     ]
 
 
+class _Tuning(C.Structure):
+    _fields_ = [("tile_proposals", C.c_int), ("tile_refresh", C.c_int), ("umma_bn_left", C.c_int),
+                ("umma_bn_right", C.c_int), ("ms", C.c_float * 4)]
+
+
 _lib = None
 
 
@@ -83,6 +88,8 @@ def lib():
         L.jagp_batch_sweep.restype = i
         L.jagp_batch_destroy.argtypes = [vp]
         L.jagp_batch_destroy.restype = i
+        L.jagp_autotune.argtypes = [vp, vp, i, C.POINTER(_Tuning), vp]
+        L.jagp_autotune.restype = i
         L.jagp_eval_noalloc.argtypes = [vp, vp, i, vp, vp, vp]
         L.jagp_eval_noalloc.restype = i
         L.jagp_last_cuda_error.argtypes = []
@@ -256,6 +263,14 @@ def jagp_launch_count(h) -> int:
 # convenience owner of a handle plus the walker state (device memory from torch)
 # --------------------------------------------------------------------------
 
+def jagp_autotune(h, state, W, stream=None) -> dict:
+    """Tile autotuner (see include/jagp.h); returns the choices and best times."""
+    t = _Tuning()
+    _check(lib().jagp_autotune(h, _ptr(state), int(W), C.byref(t), _stream(stream)), "jagp_autotune")
+    return {"tile_proposals": t.tile_proposals, "tile_refresh": t.tile_refresh, "umma_bn_left": t.umma_bn_left,
+            "umma_bn_right": t.umma_bn_right, "ms": [float(v) for v in t.ms]}
+
+
 class JAGP:
     """One system on the current CUDA device with state for up to W walkers."""
 
@@ -287,6 +302,14 @@ class JAGP:
     def positions(self, x):
         import torch
         return torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float64, device=self.device).contiguous()
+
+    def autotune(self, r=None):
+        """Tune the tile choices on this handle's state; re-evaluates r afterwards
+        (the tuner overwrites the state's tables)."""
+        out = jagp_autotune(self.h, self.state, self.W)
+        if r is not None:
+            self.eval(r)
+        return out
 
     def eval(self, r):
         import torch

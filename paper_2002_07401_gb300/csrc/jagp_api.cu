@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <cmath>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "jagp_launch.h"
@@ -139,18 +140,19 @@ jagp_status_t lambda_products(jagp_ctx *h, const float *P, const float *P_lo, fl
   LAUNCH(JAGP_KERNEL_LAMBDA_ROWS, 1,
          launch_umma_gemm(pack, max_rows, count, kFixedSlices, left ? h->split_lamT : h->split_lam, h->ds.L,
                           kFixedSlices, h->kp, left ? kFixedPairsF32 : kFixedPairs, kPairA, kPairB, out, h->ds.L,
-                          rows, h->d_err, st, exps, left ? h->exp_lamT : h->exp_lam, out_lo));
+                          rows, h->d_err, st, exps, left ? h->exp_lamT : h->exp_lam, out_lo,
+                          left ? h->tune_bn_left : h->tune_bn_right));
   return JAGP_OK;
 }
 
 // G~ = Phi_up Bt^T at a refresh: plain FP64 products, or the compensated FP32 sum
 cudaError_t refresh_geminal(const double *phi, const float *, size_t pw, const double *bt, const float *, size_t bw,
-                            int n, int Lb, double *g, int W, cudaStream_t st) {
-  return launch_gemm_rows<double>(phi, pw, bt, bw, n, n, Lb, g, (size_t)n * n, n, W, st);
+                            int n, int Lb, double *g, int W, cudaStream_t st, int tile) {
+  return launch_gemm_rows<double>(phi, pw, bt, bw, n, n, Lb, g, (size_t)n * n, n, W, st, tile);
 }
 cudaError_t refresh_geminal(const float *phi, const float *phi_lo, size_t pw, const float *bt, const float *bt_lo,
-                            size_t bw, int n, int Lb, double *g, int W, cudaStream_t st) {
-  return launch_gemm_rows_dot2(phi, phi_lo, pw, bt, bt_lo, bw, n, n, Lb, g, (size_t)n * n, n, W, st);
+                            size_t bw, int n, int Lb, double *g, int W, cudaStream_t st, int tile) {
+  return launch_gemm_rows_dot2(phi, phi_lo, pw, bt, bt_lo, bw, n, n, Lb, g, (size_t)n * n, n, W, st, tile);
 }
 // low parts of the two-float tables of the mixed path (none in the FP64 path)
 float *lo_table(const jagp_ctx *h, void *state, size_t off) {
@@ -184,7 +186,7 @@ jagp_status_t run_refresh(jagp_ctx *h, const double *r, void *state, int W, int 
   double *gm = refresh_g(static_cast<T *>(nullptr), L, state);
   LAUNCH(JAGP_KERNEL_GEMM_ROWS, 1,
          refresh_geminal(at<T>(state, L.phi_up), lo_table(h, state, L.phi_lo), (size_t)n * Lb, at<T>(state, L.bt),
-                         lo_table(h, state, L.bt_lo), (size_t)n * Lb, n, Lb, gm, W, st));
+                         lo_table(h, state, L.bt_lo), (size_t)n * Lb, n, Lb, gm, W, st, h->tune_tile_refresh));
   LAUNCH(0, 1,
          launch_refresh_inverse<T>(gm, at<T>(state, L.ginv), at<double>(state, L.scal), at<int>(state, L.status), n,
                                    W, check_drift, h->drift_tol, st));
@@ -247,7 +249,8 @@ jagp_status_t run_sweeps(jagp_ctx *h, double *d_r, void *d_state, int W, int nsw
            launch_basis_points<T>(d, true, d_r, W, 0, n, pprop, pprop_lo, rprop, (uint32_t)walker0, sw, st,
                                   sweep_dev));
     LAUNCH(JAGP_KERNEL_GEMM_ROWS, 1,
-           launch_gemm_rows<T>(pprop, (size_t)n * Lb, bt, (size_t)n * Lb, n, n, Lb, gprop, (size_t)n * n, n, W, st));
+           launch_gemm_rows<T>(pprop, (size_t)n * Lb, bt, (size_t)n * Lb, n, n, Lb, gprop, (size_t)n * n, n, W, st,
+                               h->tune_tile_prop));
     LAUNCH(JAGP_KERNEL_METROPOLIS, 1,
            launch_metropolis<T>(d, true, d_r, rprop, gprop, ginv, scal, status, pprop, phi_up, list, count, W, st,
                                 pprop_lo, phi_lo));
@@ -264,7 +267,7 @@ jagp_status_t run_sweeps(jagp_ctx *h, double *d_r, void *d_state, int W, int nsw
                                     sweep_dev));
       LAUNCH(JAGP_KERNEL_GEMM_ROWS, 1,
              launch_gemm_rows<T>(pprop, (size_t)n * Lb, a_up, (size_t)n * Lb, d.n_dn, n, Lb, gprop, (size_t)n * n, n,
-                                 W, st));
+                                 W, st, h->tune_tile_prop));
       LAUNCH(JAGP_KERNEL_METROPOLIS, 1,
              launch_metropolis<T>(d, false, d_r, rprop, gprop, ginv, scal, status, pprop, phi_up, list, count + 1, W,
                                   st));
@@ -591,6 +594,130 @@ jagp_status_t jagp_eval(jagp_handle_t h, const double *d_r, int W, void *d_state
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (h->precision == JAGP_PREC_MIXED) return run_eval<float>(h, d_r, W, d_state, d_logabs, d_sign, st);
   return run_eval<double>(h, d_r, W, d_state, d_logabs, d_sign, st);
+}
+
+// ---------------------------------------------------------------------------
+// Tile autotuner: every candidate is launched on the handle's own operands in
+// the walker state (its tables are overwritten: jagp_eval must follow), timed
+// with CUDA events on the caller's stream (two untimed and five timed calls),
+// and the fastest is kept in the handle.  The candidates change only how the
+// outputs are tiled, never the order of any sum, so results do not depend on
+// the choice.
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+namespace {
+
+template <typename F>
+cudaError_t time_calls(F &&f, cudaStream_t st, float *ms) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaError_t e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = f();
+  if (e == cudaSuccess) e = cudaEventRecord(a, st);
+  for (int i = 0; i < 5 && e == cudaSuccess; ++i) e = f();
+  if (e == cudaSuccess) e = cudaEventRecord(b, st);
+  if (e == cudaSuccess) e = cudaEventSynchronize(b);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(ms, a, b);
+  if (e == cudaSuccess) *ms /= 5.0f;
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  return e;
+}
+
+template <typename T>
+jagp_status_t tune_products(jagp_ctx *h, void *state, int W, cudaStream_t st, jagp_tuning_t *out) {
+  const Layout L = layout_of(h, W);
+  const DevSystem &d = h->ds;
+  const int n = d.n_up, Lb = d.L;
+  JAGP_CU(cudaMemsetAsync(state, 0, L.total, st));
+  T *pprop = at<T>(state, L.pprop), *bt = at<T>(state, L.bt), *gprop = at<T>(state, L.gprop);
+  T *phi = at<T>(state, L.phi_up);
+  const int tiles[3] = {0, 32, 64};
+  float best = 0.0f;
+  for (int c = 0; c < 3; ++c) {
+    float ms = 0.0f;
+    JAGP_CU(time_calls([&] { return launch_gemm_rows<T>(pprop, (size_t)n * Lb, bt, (size_t)n * Lb, n, n, Lb, gprop,
+                                                        (size_t)n * n, n, W, st, tiles[c]); },
+                       st, &ms));
+    if (c == 0 || ms < best) {
+      best = ms;
+      h->tune_tile_prop = tiles[c];
+    }
+  }
+  out->tile_proposals = h->tune_tile_prop;
+  out->ms[0] = best;
+  double *gm = std::is_same<T, float>::value ? at<double>(state, L.g64) : at<double>(state, L.gprop);
+  for (int c = 0; c < 3; ++c) {
+    float ms = 0.0f;
+    JAGP_CU(time_calls([&] { return refresh_geminal(phi, lo_table(h, state, L.phi_lo), (size_t)n * Lb, bt,
+                                                    lo_table(h, state, L.bt_lo), (size_t)n * Lb, n, Lb, gm, W, st,
+                                                    tiles[c]); },
+                       st, &ms));
+    if (c == 0 || ms < best) {
+      best = ms;
+      h->tune_tile_refresh = tiles[c];
+    }
+  }
+  out->tile_refresh = h->tune_tile_refresh;
+  out->ms[1] = best;
+  if (!std::is_same<T, float>::value) return JAGP_OK;
+  // tensor-core lambda products of half the orbital rows (the accepted rows of
+  // a half-sweep at ~50% acceptance), A_up (ten pairs) and Bt (fifteen)
+  uint16_t *pack = at<uint16_t>(state, L.pack);
+  int *exps = at<int>(state, L.exps);
+  const int rows = (W * n + 1) / 2;
+  for (int side = 0; side < 2; ++side) {
+    const bool left = side == 0;
+    const int cands[6] = {32, 48, 64, 80, 96, 128};
+    const int limit = left ? 128 : 96;
+    float bs = 0.0f;
+    int bbn = 0;
+    for (int c = 0; c < 6; ++c) {
+      if (cands[c] > limit) continue;
+      float ms = 0.0f;
+      JAGP_CU(time_calls(
+          [&] {
+            return launch_umma_gemm(pack, rows, nullptr, kFixedSlices, left ? h->split_lamT : h->split_lam, Lb,
+                                    kFixedSlices, h->kp, left ? kFixedPairsF32 : kFixedPairs, kPairA, kPairB,
+                                    reinterpret_cast<float *>(left ? at<T>(state, L.a_up) : bt), Lb, nullptr,
+                                    h->d_err, st, exps, left ? h->exp_lamT : h->exp_lam,
+                                    left ? nullptr : at<float>(state, L.bt_lo), cands[c]);
+          },
+          st, &ms));
+      if (bbn == 0 || ms < bs) {
+        bs = ms;
+        bbn = cands[c];
+      }
+    }
+    if (left) {
+      h->tune_bn_left = bbn;
+      out->umma_bn_left = bbn;
+      out->ms[2] = bs;
+    } else {
+      h->tune_bn_right = bbn;
+      out->umma_bn_right = bbn;
+      out->ms[3] = bs;
+    }
+  }
+  return JAGP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+jagp_status_t jagp_autotune(jagp_handle_t h, void *d_state, int W, jagp_tuning_t *out, void *stream) {
+  jagp_status_t s = check_walkers(h, W, d_state);
+  if (s != JAGP_OK) return s;
+  if (!out) return JAGP_ERR_INVALID_ARG;
+  memset(out, 0, sizeof(*out));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  s = h->precision == JAGP_PREC_MIXED ? tune_products<float>(h, d_state, W, st, out)
+                                      : tune_products<double>(h, d_state, W, st, out);
+  if (s != JAGP_OK) return s;
+  JAGP_CU(cudaStreamSynchronize(st));
+  return JAGP_OK;
 }
 
 jagp_status_t vmc_sweep(jagp_handle_t h, double *d_r, void *d_state, int W, int nsweeps, uint64_t walker0,

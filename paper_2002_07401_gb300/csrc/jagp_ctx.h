@@ -16,12 +16,16 @@ struct jagp_ctx {
   long long launches = 0;
   int prof_kernel = 0;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events;
-  // mixed path: lambda as fixed-point slices (four exact 8-bit integer terms per
-  // element, BF16) with one exponent per output column, for the tensor cores
+  // mixed path: lambda as fixed-point slices (kFixedSlices exact 8-bit integer
+  // terms per element, BF16) with one exponent per output column, for the tensor cores
   int kp = 0;                            // L padded to a multiple of 64
-  const uint16_t *split_lamT = nullptr;  // [L][4 kp]: row n slices lambda[:, n]  (A_up = phi^T lambda)
-  const uint16_t *split_lam = nullptr;   // [L][4 kp]: row n slices lambda[n, :]  (Bt = lambda phi)
+  const uint16_t *split_lamT = nullptr;  // [L][5 kp]: row n slices lambda[:, n]  (A_up = phi^T lambda)
+  const uint16_t *split_lam = nullptr;   // [L][5 kp]: row n slices lambda[n, :]  (Bt = lambda phi)
   const int *exp_lamT = nullptr;         // [L] exponents of those rows
   const int *exp_lam = nullptr;          // [L]
   int *d_err = nullptr;                  // tensor-core pipeline timeout flag
+  // tile choices of jagp_autotune (0 / -1: the shape heuristics)
+  int tune_bn_left = 0, tune_bn_right = 0;  // tensor-core tile width of the lambda products
+  int tune_tile_prop = -1;                  // per-walker proposal products (gemm_rows tile)
+  int tune_tile_refresh = -1;               // per-walker refresh product G~ = Phi_up Bt^T
 };

@@ -27,15 +27,17 @@ cudaError_t launch_metropolis(const DevSystem &s, bool up, double *r, const doub
                               float *phi_lo = nullptr);
 
 // Out[w][a][b] = sum_k X[w][a][k] Y[w][b][k]  (a < ma, b < nb, k < K); row stride K.
+// tile: -1 picks by shape, 0 one output per thread (16 x 16 tiles), 32 or 64
+// register-blocked tiles (the autotuner's choice)
 template <typename T>
 cudaError_t launch_gemm_rows(const T *X, size_t xw, const T *Y, size_t yw, int ma, int nb, int K, T *Out,
-                             size_t ow, int ldo, int W, cudaStream_t st);
+                             size_t ow, int ldo, int W, cudaStream_t st, int tile = -1);
 
 // FP32 variant with a compensated (error-free transformation) dot product; X and
 // Y may carry low parts Xlo, Ylo (same layouts) so that they are two-float operands
 cudaError_t launch_gemm_rows_dot2(const float *X, const float *Xlo, size_t xw, const float *Y, const float *Ylo,
                                   size_t yw, int ma, int nb, int K, double *Out, size_t ow, int ldo, int W,
-                                  cudaStream_t st);
+                                  cudaStream_t st, int tile = -1);
 // low parts of the unpaired-orbital rows of Bt (two-float table of the FP32 path)
 cudaError_t launch_fill_unpaired_lo(const DevSystem &s, float *bt_lo, int W, cudaStream_t st);
 
@@ -90,7 +92,8 @@ int umma_pick_bn(int n, int max_bn);
 cudaError_t launch_umma_gemm(const uint16_t *A, int m_max, const int *m_dev, int a_terms, const uint16_t *B, int n,
                              int b_terms, int kp, int npairs, const int *pair_a, const int *pair_b, float *out,
                              long long ldo, const int *out_rows, int *err, cudaStream_t st,
-                             const int *a_exp = nullptr, const int *b_exp = nullptr, float *out_lo = nullptr);
+                             const int *a_exp = nullptr, const int *b_exp = nullptr, float *out_lo = nullptr,
+                             int bn_max = 0);
 // FP32 rows (two-float rows P + P_lo when P_lo is given) -> kFixedSlices exact
 // 8-bit slices per element (BF16) plus a row exponent
 cudaError_t launch_pack_fixed(const float *P, const float *P_lo, const int *list, const int *count, int nrows,

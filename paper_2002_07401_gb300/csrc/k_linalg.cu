@@ -202,9 +202,10 @@ inline int gemm_rows_tile(int ma, int nb) {
 
 cudaError_t launch_gemm_rows_dot2(const float *X, const float *Xlo, size_t xw, const float *Y, const float *Ylo,
                                   size_t yw, int ma, int nb, int K, double *Out, size_t ow, int ldo, int W,
-                                  cudaStream_t st) {
+                                  cudaStream_t st, int tile) {
   if (W <= 0 || ma <= 0 || nb <= 0) return cudaSuccess;
-  const int tm = gemm_rows_tile(ma, nb);
+  if (tile != -1 && tile != 0 && tile != 32 && tile != 64) return cudaErrorInvalidValue;
+  const int tm = tile >= 0 ? tile : gemm_rows_tile(ma, nb);
   if (tm) {
     dim3 grid((nb + tm - 1) / tm, (ma + tm - 1) / tm, W);
     if (tm == 64)
@@ -220,9 +221,10 @@ cudaError_t launch_gemm_rows_dot2(const float *X, const float *Xlo, size_t xw, c
 
 template <typename T>
 cudaError_t launch_gemm_rows(const T *X, size_t xw, const T *Y, size_t yw, int ma, int nb, int K, T *Out, size_t ow,
-                             int ldo, int W, cudaStream_t st) {
+                             int ldo, int W, cudaStream_t st, int tile) {
   if (W <= 0 || ma <= 0 || nb <= 0) return cudaSuccess;
-  const int tm = gemm_rows_tile(ma, nb);
+  if (tile != -1 && tile != 0 && tile != 32 && tile != 64) return cudaErrorInvalidValue;
+  const int tm = tile >= 0 ? tile : gemm_rows_tile(ma, nb);
   if (tm) {
     dim3 grid((nb + tm - 1) / tm, (ma + tm - 1) / tm, W);
     if (tm == 64)
@@ -236,9 +238,9 @@ cudaError_t launch_gemm_rows(const T *X, size_t xw, const T *Y, size_t yw, int m
   return cudaGetLastError();
 }
 template cudaError_t launch_gemm_rows<double>(const double *, size_t, const double *, size_t, int, int, int, double *,
-                                              size_t, int, int, cudaStream_t);
+                                              size_t, int, int, cudaStream_t, int);
 template cudaError_t launch_gemm_rows<float>(const float *, size_t, const float *, size_t, int, int, int, float *,
-                                             size_t, int, int, cudaStream_t);
+                                             size_t, int, int, cudaStream_t, int);
 
 template <typename T>
 __global__ void k_fill_unpaired(const double *__restrict__ unp, T *__restrict__ bt, int W, int nu, int nd,

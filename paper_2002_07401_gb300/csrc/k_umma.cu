@@ -332,7 +332,7 @@ int umma_pick_bn(int n, int max_bn) {
 cudaError_t launch_umma_gemm(const uint16_t *A, int m_max, const int *m_dev, int a_terms, const uint16_t *B, int n,
                              int b_terms, int kp, int npairs, const int *pair_a, const int *pair_b, float *out,
                              long long ldo, const int *out_rows, int *err, cudaStream_t st, const int *a_exp,
-                             const int *b_exp, float *out_lo) {
+                             const int *b_exp, float *out_lo, int bn_max) {
   if (m_max <= 0 || n <= 0) return cudaSuccess;
   if (kp <= 0 || kp % 64 != 0 || npairs < 1 || npairs > 16 || a_terms < 1 || b_terms < 1) return cudaErrorInvalidValue;
   if ((reinterpret_cast<uintptr_t>(A) & 15u) || (reinterpret_cast<uintptr_t>(B) & 15u)) return cudaErrorInvalidValue;
@@ -353,8 +353,14 @@ cudaError_t launch_umma_gemm(const uint16_t *A, int m_max, const int *m_dev, int
   g.m_dev = m_dev;
   g.n = n;
   g.kp = kp;
-  // the ngroups accumulators of bn columns share the 512 tensor-memory columns
-  g.bn = umma_pick_bn(n, g.ngroups <= 2 ? 256 : (g.ngroups <= 4 ? 128 : 96));
+  // the ngroups accumulators of bn columns share the 512 tensor-memory columns;
+  // bn_max (a multiple of 16, from the autotuner) may lower the limit
+  int limit = g.ngroups <= 2 ? 256 : (g.ngroups <= 4 ? 128 : 96);
+  if (bn_max > 0) {
+    if (bn_max % 16) return cudaErrorInvalidValue;
+    limit = bn_max < limit ? bn_max : limit;
+  }
+  g.bn = umma_pick_bn(n, limit);
   const uint32_t stage_bytes = 128u * 128u + static_cast<uint32_t>(g.bn) * 128u;
   g.stages = static_cast<int>((200u * 1024u) / stage_bytes);
   if (g.stages > 6) g.stages = 6;
