@@ -329,7 +329,8 @@ def forces_bench(pg, torch, dist, args, dev, rank, ws, local):
 
 BATCH_WORKLOAD = ("batched uneven systems, mixed precision: 64 independent neutral He systems, N uniform in "
                   "{8,...,128} (N/2 up, N/2 down, N/2 atoms), 16 Gaussians/atom, 512 walkers per system, every sweep "
-                  "one replay of a captured CUDA graph over all systems; FP64 refresh of G^-1 every N_up moves")
+                  "one replay of a captured CUDA graph over all systems; FP64 refresh of G^-1 every 16 moves of a "
+                  "spin half-sweep and at its end")
 
 
 def batch_bench(pg, torch, dist, args, dev, rank, ws):
@@ -339,7 +340,7 @@ def batch_bench(pg, torch, dist, args, dev, rank, ws):
     W = args.batch_walkers
     members, pos = [], []
     for s in systems:
-        m = pg.JAGP(s, W, seed=0, precision=pg.JAGP_PREC_MIXED)
+        m = pg.JAGP(s, W, seed=0, precision=pg.JAGP_PREC_MIXED, refresh_moves=16)
         p = m.positions(synth.init_walkers(s, W * ws, seed=0)[rank * W:(rank + 1) * W])
         m.eval(p)
         members.append(m)

@@ -86,6 +86,9 @@ typedef struct jagp_options {
   uint64_t seed;              /* Philox4x32-10 key */
   double drift_tol;           /* Sherman-Morrison drift tolerance checked at each refresh
                                  (<= 0: 1e-8 for FP64, 1e-3 for MIXED) */
+  int refresh_moves;          /* 0: refresh G~^{-1} from the tables once per sweep (FP64) or
+                                 after each spin half-sweep (MIXED); k > 0: also after every
+                                 k moves within a spin half-sweep (e.g. 16); < 0: INVALID_ARG */
 } jagp_options_t;
 
 typedef struct jagp_ctx *jagp_handle_t;

@@ -158,9 +158,9 @@ cudaError_t refresh_geminal(const float *phi, const float *phi_lo, size_t pw, co
 float *lo_table(const jagp_ctx *h, void *state, size_t off) {
   return h->precision == JAGP_PREC_MIXED ? at<float>(state, off) : nullptr;
 }
-// where the refresh keeps G~: the FP64 table, or the FP64 side array of the FP32 path
-double *refresh_g(double *, const Layout &L, void *state) { return at<double>(state, L.gprop); }
-double *refresh_g(float *, const Layout &L, void *state) { return at<double>(state, L.g64); }
+// where the refresh keeps G~ (its own array: the proposed rows in gprop stay
+// valid across refreshes within a half-sweep)
+double *refresh_g(const Layout &L, void *state) { return at<double>(state, L.g64); }
 
 // the local-energy sequence on a current state
 template <typename T>
@@ -183,7 +183,7 @@ jagp_status_t run_refresh(jagp_ctx *h, const double *r, void *state, int W, int 
                           cudaStream_t st) {
   const Layout L = layout_of(h, W);
   const int n = h->ds.n_up, Lb = h->ds.L;
-  double *gm = refresh_g(static_cast<T *>(nullptr), L, state);
+  double *gm = refresh_g(L, state);
   LAUNCH(JAGP_KERNEL_GEMM_ROWS, 1,
          refresh_geminal(at<T>(state, L.phi_up), lo_table(h, state, L.phi_lo), (size_t)n * Lb, at<T>(state, L.bt),
                          lo_table(h, state, L.bt_lo), (size_t)n * Lb, n, Lb, gm, W, st, h->tune_tile_refresh));
@@ -241,39 +241,55 @@ jagp_status_t run_sweeps(jagp_ctx *h, double *d_r, void *d_state, int W, int nsw
   int *status = at<int>(d_state, L.status), *list = at<int>(d_state, L.list), *count = at<int>(d_state, L.count);
   float *phi_lo = lo_table(h, d_state, L.phi_lo), *pprop_lo = lo_table(h, d_state, L.pprop_lo);
   jagp_status_t s;
+  // one spin half-sweep: all proposals and their rows (up) or columns (down) of
+  // G~ at once, then the acceptance in chunks of refresh_moves moves, each
+  // followed by the lambda products of its accepted rows and, but for the
+  // last chunk, a refresh of G~^{-1} from the tables
+  auto half_sweep = [&](bool up, uint32_t sw) -> jagp_status_t {
+    const int moves = up ? n : d.n_dn;
+    if (moves == 0) return JAGP_OK;
+    int *total = count + (up ? 0 : 1), *chunk = count + 2;
+    LAUNCH(JAGP_KERNEL_BASIS, 1,
+           launch_basis_points<T>(d, true, d_r, W, up ? 0 : n, moves, pprop, pprop_lo, rprop, (uint32_t)walker0, sw,
+                                  st, sweep_dev));
+    if (up)
+      LAUNCH(JAGP_KERNEL_GEMM_ROWS, 1,
+             launch_gemm_rows<T>(pprop, (size_t)n * Lb, bt, (size_t)n * Lb, n, n, Lb, gprop, (size_t)n * n, n, W, st,
+                                 h->tune_tile_prop));
+    else
+      LAUNCH(JAGP_KERNEL_GEMM_ROWS, 1,
+             launch_gemm_rows<T>(pprop, (size_t)n * Lb, a_up, (size_t)n * Lb, d.n_dn, n, Lb, gprop, (size_t)n * n, n,
+                                 W, st, h->tune_tile_prop));
+    const int step = h->refresh_moves > 0 ? h->refresh_moves : moves;
+    for (int m0 = 0; m0 < moves; m0 += step) {
+      const int m1 = m0 + step < moves ? m0 + step : moves;
+      JAGP_CU(cudaMemsetAsync(chunk, 0, sizeof(int), st));
+      LAUNCH(JAGP_KERNEL_METROPOLIS, 1,
+             launch_metropolis<T>(d, up, d_r, rprop, gprop, ginv, scal, status, pprop, phi_up, list, chunk, W, st,
+                                  pprop_lo, phi_lo, m0, m1, total));
+      jagp_status_t q =
+          lambda_products(h, pprop, pprop_lo, up ? a_up : bt, up, list, chunk, 0, 1, 0, W * n, d_state, W, st);
+      if (q != JAGP_OK) return q;
+      if (m1 < moves) {
+        q = run_refresh<T>(h, d_r, d_state, W, 1, false, st);
+        if (q != JAGP_OK) return q;
+      }
+    }
+    return JAGP_OK;
+  };
   for (int t = 0; t < nsweeps; ++t) {
     const uint32_t sw = (uint32_t)(sweep0 + (uint64_t)t);
     JAGP_CU(cudaMemsetAsync(count, 0, 2 * sizeof(int), st));
     // up electrons: rows of G~ against the frozen down-spin table Bt
-    LAUNCH(JAGP_KERNEL_BASIS, 1,
-           launch_basis_points<T>(d, true, d_r, W, 0, n, pprop, pprop_lo, rprop, (uint32_t)walker0, sw, st,
-                                  sweep_dev));
-    LAUNCH(JAGP_KERNEL_GEMM_ROWS, 1,
-           launch_gemm_rows<T>(pprop, (size_t)n * Lb, bt, (size_t)n * Lb, n, n, Lb, gprop, (size_t)n * n, n, W, st,
-                               h->tune_tile_prop));
-    LAUNCH(JAGP_KERNEL_METROPOLIS, 1,
-           launch_metropolis<T>(d, true, d_r, rprop, gprop, ginv, scal, status, pprop, phi_up, list, count, W, st,
-                                pprop_lo, phi_lo));
-    s = lambda_products(h, pprop, pprop_lo, a_up, true, list, count, 0, 1, 0, W * n, d_state, W, st);
+    s = half_sweep(true, sw);
     if (s != JAGP_OK) return s;
     if (half_refresh && d.n_dn > 0) {
       s = run_refresh<T>(h, d_r, d_state, W, 1, false, st);
       if (s != JAGP_OK) return s;
     }
-    if (d.n_dn > 0) {
-      // down electrons: columns of G~ against the updated up-spin table A_up
-      LAUNCH(JAGP_KERNEL_BASIS, 1,
-             launch_basis_points<T>(d, true, d_r, W, n, d.n_dn, pprop, pprop_lo, rprop, (uint32_t)walker0, sw, st,
-                                    sweep_dev));
-      LAUNCH(JAGP_KERNEL_GEMM_ROWS, 1,
-             launch_gemm_rows<T>(pprop, (size_t)n * Lb, a_up, (size_t)n * Lb, d.n_dn, n, Lb, gprop, (size_t)n * n, n,
-                                 W, st, h->tune_tile_prop));
-      LAUNCH(JAGP_KERNEL_METROPOLIS, 1,
-             launch_metropolis<T>(d, false, d_r, rprop, gprop, ginv, scal, status, pprop, phi_up, list, count + 1, W,
-                                  st));
-      s = lambda_products(h, pprop, pprop_lo, bt, false, list, count + 1, 0, 1, 0, W * d.n_dn, d_state, W, st);
-      if (s != JAGP_OK) return s;
-    }
+    // down electrons: columns of G~ against the updated up-spin table A_up
+    s = half_sweep(false, sw);
+    if (s != JAGP_OK) return s;
     double *eL = d_eL ? d_eL + (accumulate ? 0 : (size_t)t * W) : nullptr;
     // the local-energy pass also forms J, so the refresh skips its Jastrow pass then
     s = run_refresh<T>(h, d_r, d_state, W, 1, eL == nullptr, st);
@@ -415,6 +431,7 @@ jagp_status_t jagp_create(jagp_handle_t *out, const jagp_system_t *sys, const ja
   if (sys->n_up > sys->n_dn && !sys->unpaired) return JAGP_ERR_INVALID_ARG;
   if (opt->precision != JAGP_PREC_FP64 && opt->precision != JAGP_PREC_MIXED) return JAGP_ERR_UNSUPPORTED;
   if (opt->max_walkers <= 0 || !(opt->delta > 0.0) || !isfinite(opt->delta)) return JAGP_ERR_INVALID_ARG;
+  if (opt->refresh_moves < 0) return JAGP_ERR_INVALID_ARG;
   // Shell table in evaluation order: grouped by (radial type, l) so that the 32
   // lanes of a warp, which take consecutive shells, run the same branch; each
   // record keeps the offset of its first function in the caller's order.
@@ -566,6 +583,7 @@ jagp_status_t jagp_create(jagp_handle_t *out, const jagp_system_t *sys, const ja
   h->d_err = reinterpret_cast<int *>(b + oE);
   h->max_walkers = opt->max_walkers;
   h->drift_tol = opt->drift_tol > 0.0 ? opt->drift_tol : (mixed ? 1e-3 : 1e-8);
+  h->refresh_moves = opt->refresh_moves;
   *out = h;
   return JAGP_OK;
 }
@@ -647,7 +665,7 @@ jagp_status_t tune_products(jagp_ctx *h, void *state, int W, cudaStream_t st, ja
   }
   out->tile_proposals = h->tune_tile_prop;
   out->ms[0] = best;
-  double *gm = std::is_same<T, float>::value ? at<double>(state, L.g64) : at<double>(state, L.gprop);
+  double *gm = refresh_g(L, state);
   for (int c = 0; c < 3; ++c) {
     float ms = 0.0f;
     JAGP_CU(time_calls([&] { return refresh_geminal(phi, lo_table(h, state, L.phi_lo), (size_t)n * Lb, bt,

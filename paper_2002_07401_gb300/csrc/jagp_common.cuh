@@ -60,7 +60,7 @@ struct Layout {
   size_t pack;     // BF16   [W n_up][5 kp]  mixed path: fixed-point slices of the lambda-product rows
   size_t rows;     // int    [W n_up]        mixed path: destination rows of the packed operand
   size_t exps;     // int    [W n_up]        mixed path: row exponents of the packed operand
-  size_t g64;      // double [W][n_up][n_up] mixed path: G~ at a refresh (FP64 result of the compensated sum)
+  size_t g64;      // double [W][n_up][n_up] G~ at a refresh (overwritten by the in-place inverse when large)
   size_t bt_lo;    // float  [W][n_up][L]    mixed path: low parts of Bt (Bt + bt_lo is a two-float table)
   size_t phi_lo;   // float  [W][n_up][L]    mixed path: low parts of phi_up
   size_t pprop_lo; // float  [W][n_up][L]    mixed path: low parts of pprop
@@ -92,7 +92,7 @@ inline Layout make_layout(size_t W, size_t nu, size_t N, size_t L, size_t esz = 
   l.pack = take(W * nu * kFixedSlices * kp * 2);
   l.rows = take(kp ? W * nu * 4 : 0);
   l.exps = take(kp ? W * nu * 4 : 0);
-  l.g64 = take(esz == 4 ? W * nu * nu * 8 : 0);
+  l.g64 = take(W * nu * nu * 8);
   l.bt_lo = take(esz == 4 ? W * nu * L * 4 : 0);
   l.phi_lo = take(esz == 4 ? W * nu * L * 4 : 0);
   l.pprop_lo = take(esz == 4 ? W * nu * L * 4 : 0);

@@ -12,6 +12,7 @@ struct jagp_ctx {
   int precision = JAGP_PREC_FP64;
   int max_walkers = 0;
   double drift_tol = 1e-8;
+  int refresh_moves = 0;  // see jagp_options_t
   void *d_mem = nullptr;
   long long launches = 0;
   int prof_kernel = 0;

@@ -17,14 +17,16 @@ cudaError_t launch_basis_points(const DevSystem &s, bool propose, const double *
                                 int npts, T *out, float *out_lo, double *rprop, uint32_t walker0,
                                 uint32_t sweep, cudaStream_t st, const uint32_t *sweep_dev = nullptr);
 
-// Sequential Metropolis over one spin species with Sherman-Morrison updates.
-// Accepted up moves copy their proposal row of pprop (and pprop_lo, when given)
-// into phi_up (phi_lo).
+// Sequential Metropolis over one spin species with Sherman-Morrison updates,
+// moves m_begin .. m_end - 1 of the half-sweep (m_end < 0: to the last).
+// Accepted moves are appended to list (*count) and counted in *total (when
+// given); accepted up moves copy their proposal row of pprop (and pprop_lo,
+// when given) into phi_up (phi_lo).
 template <typename T>
 cudaError_t launch_metropolis(const DevSystem &s, bool up, double *r, const double *rprop, const T *gprop,
                               T *ginv, double *scal, int *status, const T *pprop, T *phi_up, int *list,
                               int *count, int W, cudaStream_t st, const float *pprop_lo = nullptr,
-                              float *phi_lo = nullptr);
+                              float *phi_lo = nullptr, int m_begin = 0, int m_end = -1, int *total = nullptr);
 
 // Out[w][a][b] = sum_k X[w][a][k] Y[w][b][k]  (a < ma, b < nb, k < K); row stride K.
 // tile: -1 picks by shape, 0 one output per thread (16 x 16 tiles), 32 or 64

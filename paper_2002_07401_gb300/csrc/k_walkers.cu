@@ -186,7 +186,8 @@ __global__ void __launch_bounds__(512) k_metropolis(DevSystem s, double *__restr
                                                     T *__restrict__ phi_up, int *__restrict__ list,
                                                     int *__restrict__ count,
                                                     const float *__restrict__ pprop_lo,
-                                                    float *__restrict__ phi_lo) {
+                                                    float *__restrict__ phi_lo, int m_begin, int m_end,
+                                                    int *__restrict__ total) {
   extern __shared__ double sm[];
   const int n = s.n_up, N = s.N, tid = threadIdx.x, bs = blockDim.x;
   const int w = blockIdx.x;
@@ -213,10 +214,10 @@ __global__ void __launch_bounds__(512) k_metropolis(DevSystem s, double *__restr
     nacc = scal[(size_t)w * S_STRIDE + S_NACC];
     st_bits = status[w];
   }
-  const int nmoves = UP ? s.n_up : s.n_dn;
+  const int nmoves = m_end < (UP ? s.n_up : s.n_dn) ? m_end : (UP ? s.n_up : s.n_dn);
   const int e0 = UP ? 0 : s.n_up;
   __syncthreads();
-  for (int m = 0; m < nmoves; ++m) {
+  for (int m = m_begin; m < nmoves; ++m) {
     const int e = e0 + m;
     const double *rp4 = rprop + ((size_t)w * n + m) * kPropStride;
     const double px = rp4[0], py = rp4[1], pz = rp4[2];
@@ -243,6 +244,7 @@ __global__ void __launch_bounds__(512) k_metropolis(DevSystem s, double *__restr
         J += pj;
         nacc += 1.0;
         list[atomicAdd(count, 1)] = w * n + m;
+        if (total) atomicAdd(total, 1);
       }
       s_acc = acc;
       s_R = pr;
@@ -325,7 +327,8 @@ __global__ void __launch_bounds__(kMetroWarps * 32) k_metropolis_warp(
     DevSystem s, double *__restrict__ r, const double *__restrict__ rprop, const T *__restrict__ gprop,
     T *__restrict__ ginv, double *__restrict__ scal, int *__restrict__ status,
     const T *__restrict__ pprop, T *__restrict__ phi_up, int *__restrict__ list,
-    int *__restrict__ count, int W, const float *__restrict__ pprop_lo, float *__restrict__ phi_lo) {
+    int *__restrict__ count, int W, const float *__restrict__ pprop_lo, float *__restrict__ phi_lo, int m_begin,
+    int m_end, int *__restrict__ total) {
   extern __shared__ double sm[];
   const int n = s.n_up, N = s.N, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int w = blockIdx.x * kMetroWarps + warp;
@@ -341,10 +344,10 @@ __global__ void __launch_bounds__(kMetroWarps * 32) k_metropolis_warp(
   double *sw = scal + (size_t)w * S_STRIDE;
   double logdet = sw[S_LOGDET], sgn = sw[S_SIGN], J = sw[S_J], nacc = sw[S_NACC];
   int st_bits = status[w];
-  const int nmoves = UP ? s.n_up : s.n_dn;
+  const int nmoves = m_end < (UP ? s.n_up : s.n_dn) ? m_end : (UP ? s.n_up : s.n_dn);
   const int e0 = UP ? 0 : s.n_up;
   __syncwarp();
-  for (int m = 0; m < nmoves; ++m) {
+  for (int m = m_begin; m < nmoves; ++m) {
     const int e = e0 + m;
     const double *rec = rprop + ((size_t)w * n + m) * kPropStride;
     const double px = rec[0], py = rec[1], pz = rec[2];
@@ -375,7 +378,10 @@ __global__ void __launch_bounds__(kMetroWarps * 32) k_metropolis_warp(
       if (pr < 0.0) sgn = -sgn;
       J += pj;
       nacc += 1.0;
-      if (lane == 0) list[atomicAdd(count, 1)] = w * n + m;
+      if (lane == 0) {
+        list[atomicAdd(count, 1)] = w * n + m;
+        if (total) atomicAdd(total, 1);
+      }
       for (int t = lane; t < n; t += 32) {
         T a = T(0);
         if (UP) {
@@ -420,45 +426,48 @@ __global__ void __launch_bounds__(kMetroWarps * 32) k_metropolis_warp(
 template <typename T>
 cudaError_t launch_metropolis(const DevSystem &s, bool up, double *r, const double *rprop, const T *gprop, T *ginv,
                               double *scal, int *status, const T *pprop, T *phi_up, int *list, int *count, int W,
-                              cudaStream_t st, const float *pprop_lo, float *phi_lo) {
+                              cudaStream_t st, const float *pprop_lo, float *phi_lo, int m_begin, int m_end,
+                              int *total) {
   if (W <= 0 || (!up && s.n_dn == 0)) return cudaSuccess;
+  if (m_end < 0) m_end = up ? s.n_up : s.n_dn;
+  if (m_begin >= m_end) return cudaSuccess;
   const int n = s.n_up;
   const size_t per = metro_smem_per_walker<T>(n, s.N);
   if (n <= 32) {
     const int blocks = (W + kMetroWarps - 1) / kMetroWarps;
     if (up)
       k_metropolis_warp<true, T><<<blocks, kMetroWarps * 32, per * kMetroWarps, st>>>(
-          s, r, rprop, gprop, ginv, scal, status, pprop, phi_up, list, count, W, pprop_lo, phi_lo);
+          s, r, rprop, gprop, ginv, scal, status, pprop, phi_up, list, count, W, pprop_lo, phi_lo, m_begin, m_end, total);
     else
       k_metropolis_warp<false, T><<<blocks, kMetroWarps * 32, per * kMetroWarps, st>>>(
-          s, r, rprop, gprop, ginv, scal, status, pprop, phi_up, list, count, W, pprop_lo, phi_lo);
+          s, r, rprop, gprop, ginv, scal, status, pprop, phi_up, list, count, W, pprop_lo, phi_lo, m_begin, m_end, total);
     return cudaGetLastError();
   }
   if (per <= kMetroSmemMax) {
     const int threads = n <= 64 ? 128 : 256;
     if (up)
       k_metropolis<true, T, false><<<W, threads, per, st>>>(s, r, rprop, gprop, ginv, scal, status, pprop, phi_up,
-                                                             list, count, pprop_lo, phi_lo);
+                                                             list, count, pprop_lo, phi_lo, m_begin, m_end, total);
     else
       k_metropolis<false, T, false><<<W, threads, per, st>>>(s, r, rprop, gprop, ginv, scal, status, pprop, phi_up,
-                                                              list, count, pprop_lo, phi_lo);
+                                                              list, count, pprop_lo, phi_lo, m_begin, m_end, total);
     return cudaGetLastError();
   }
   const size_t glob = (size_t)s.N * 3 * sizeof(double) + (size_t)3 * n * sizeof(T);
   if (up)
     k_metropolis<true, T, true><<<W, 512, glob, st>>>(s, r, rprop, gprop, ginv, scal, status, pprop, phi_up, list,
-                                                       count, pprop_lo, phi_lo);
+                                                       count, pprop_lo, phi_lo, m_begin, m_end, total);
   else
     k_metropolis<false, T, true><<<W, 512, glob, st>>>(s, r, rprop, gprop, ginv, scal, status, pprop, phi_up, list,
-                                                        count, pprop_lo, phi_lo);
+                                                        count, pprop_lo, phi_lo, m_begin, m_end, total);
   return cudaGetLastError();
 }
 template cudaError_t launch_metropolis<double>(const DevSystem &, bool, double *, const double *, const double *,
                                                double *, double *, int *, const double *, double *, int *, int *,
-                                               int, cudaStream_t, const float *, float *);
+                                               int, cudaStream_t, const float *, float *, int, int, int *);
 template cudaError_t launch_metropolis<float>(const DevSystem &, bool, double *, const double *, const float *,
                                               float *, double *, int *, const float *, float *, int *, int *, int,
-                                              cudaStream_t, const float *, float *);
+                                              cudaStream_t, const float *, float *, int, int, int *);
 
 // ---------------------------------------------------------------------------
 // J = J1 + J2 of each walker from scratch (one CTA per walker).

@@ -84,6 +84,28 @@ def test_mixed_per_configuration_errors(torch_cuda, name):
     assert de <= et, de
 
 
+def test_mixed_refresh_every_16_moves_keeps_the_tables_consistent(torch_cuda):
+    """The batched workload's setting (refresh every 16 moves) on its largest
+    system: after sweeps, log|Psi| of the state and e_L agree with the oracle
+    at the final positions to the mixed-path targets."""
+    import paper_2002_07401_gb300 as pg
+    sysm = _c3("max")
+    W = 8
+    x = _equilibrated(sysm, W, sweeps=4)
+    g = pg.JAGP(sysm, W, precision=pg.JAGP_PREC_MIXED, seed=2, refresh_moves=16)
+    r = g.positions(x)
+    g.eval(r)
+    eL, _ = g.sweep(r, 2)
+    assert g.status() & (pg.WS_NONFINITE | pg.WS_SINGULAR) == 0
+    xf = r.cpu().numpy()
+    o = oracle.Oracle(sysm)
+    la_ref, _ = o.logpsi_batch(xf)
+    e_ref = o.local_energy_batch(xf)
+    assert np.max(np.abs(g.info()["logabs"].cpu().numpy() - la_ref)) <= LOGPSI_TOL
+    assert np.max(np.abs(eL.cpu().numpy()[-1] - e_ref)) <= EL_TOL
+    g.close()
+
+
 def test_mixed_vmc_mean_matches_oracle(torch_cuda):
     import paper_2002_07401_gb300 as pg
     sysm = synth.config1()

@@ -193,3 +193,27 @@ def test_nonfinite_position_sets_status(torch_cuda):
     assert st[2] & pg.WS_SINGULAR and st[0] == st[1] == st[3] == 0
     ref, _ = oracle.Oracle(sysm).logpsi_batch(x[[0, 1, 3]])
     assert np.all(_close(la.cpu().numpy()[[0, 1, 3]], ref))
+
+
+@pytest.mark.parametrize("name,W,sweeps,k", [("small-unpaired-slater", 9, 3, 1), ("C2", 4, 2, 5),
+                                             ("mid-n40", 3, 2, 16)])
+def test_sweep_trajectory_parity_with_refresh_every_k_moves(torch_cuda, name, W, sweeps, k):
+    """Refreshing G~^-1 from the tables every k moves of a spin half-sweep
+    (the option the batched workload uses with k = 16) keeps the trajectory
+    move-by-move identical to the oracle's."""
+    import paper_2002_07401_gb300 as pg
+    sysm = SYSTEMS[name]
+    x0 = _walkers(sysm, W, seed=9)
+    xo = x0.copy()
+    eL_ref, lp_ref, nacc_ref = oracle.Oracle(sysm).vmc(xo, sweeps, seed=5, sweep0=1, walker0=2)
+    g = pg.JAGP(sysm, W, seed=5, refresh_moves=k)
+    r = g.positions(x0)
+    g.eval(r)
+    eL, acc = g.sweep(r, sweeps, walker0=2, sweep0=1, acc=True)
+    info = g.info()
+    assert g.status() & (pg.WS_NONFINITE | pg.WS_SINGULAR) == 0
+    assert np.array_equal(r.cpu().numpy(), xo)
+    assert np.array_equal(info["naccept"].cpu().numpy(), nacc_ref.astype(np.float64))
+    assert acc.cpu().numpy()[:, 2].sum() == nacc_ref.sum()
+    assert np.all(_close(eL.cpu().numpy(), eL_ref))
+    g.close()
