@@ -307,138 +307,13 @@ struct PivotProduct {
 };
 
 // ---------------------------------------------------------------------------
-// FP64 refresh: Gauss-Jordan elimination with partial pivoting on [G~ | I]
-// (one CTA per walker, the n x 2n block in shared memory).  log|det G~| is the
-// sum of log|pivot|, the sign the product of pivot signs and row swaps.  The
+// FP64 refresh: Gauss-Jordan elimination with partial pivoting.  log|det G~| is
+// log|prod of pivots|, the sign the product of pivot signs and row swaps.  The
 // fresh inverse replaces the Sherman-Morrison one; their largest difference
 // times max|G~| is the walker's drift.
 // ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(256) k_refresh_inverse(const double *__restrict__ gm, T *__restrict__ ginv,
-                                                         double *__restrict__ scal, int *__restrict__ status,
-                                                         int n, int check_drift, double drift_tol) {
-  extern __shared__ double sm[];
-  const int ld = 2 * n + 1, tid = threadIdx.x, bs = blockDim.x, w = blockIdx.x;
-  double *A = sm;              // n x ld
-  double *f = A + n * ld;      // n
-  __shared__ int s_piv;
-  __shared__ double s_pv;
-  __shared__ double red[32];
-  const double *G = gm + (size_t)w * n * n;
-  double gmax = 0.0;
-  for (int idx = tid; idx < n * 2 * n; idx += bs) {
-    const int i = idx / (2 * n), j = idx - i * 2 * n;
-    double v;
-    if (j < n) {
-      v = G[i * n + j];
-      gmax = fmax(gmax, fabs(v));
-    } else {
-      v = (j - n == i) ? 1.0 : 0.0;
-    }
-    A[i * ld + j] = v;
-  }
-  PivotProduct pp;
-  double sgn = 1.0;
-  bool ok = true;
-  __syncthreads();
-  for (int k = 0; k < n; ++k) {
-    if (tid < 32) {
-      double best = -1.0;
-      int bi = k;  // stays a valid row even if every candidate is NaN (then pv is NaN: singular)
-      for (int i = k + tid; i < n; i += 32) {
-        const double v = fabs(A[i * ld + k]);
-        if (v > best) {
-          best = v;
-          bi = i;
-        }
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (ob > best || (ob == best && oi < bi)) {
-          best = ob;
-          bi = oi;
-        }
-      }
-      if (tid == 0) {
-        s_piv = bi;
-        s_pv = A[bi * ld + k];
-      }
-    }
-    __syncthreads();
-    const int p = s_piv;
-    const double pv = s_pv;
-    if (!(pv != 0.0) || !isfinite(pv)) {
-      ok = false;
-      break;
-    }
-    if (p != k) {
-      for (int j = tid; j < 2 * n; j += bs) {
-        const double t = A[k * ld + j];
-        A[k * ld + j] = A[p * ld + j];
-        A[p * ld + j] = t;
-      }
-      sgn = -sgn;
-    }
-    pp.mul(pv);
-    if (pv < 0.0) sgn = -sgn;
-    __syncthreads();
-    const double ip = 1.0 / pv;
-    for (int j = tid; j < 2 * n; j += bs) A[k * ld + j] *= ip;
-    __syncthreads();
-    for (int i = tid; i < n; i += bs) f[i] = A[i * ld + k];
-    __syncthreads();
-    for (int idx = tid; idx < n * 2 * n; idx += bs) {
-      const int i = idx / (2 * n), j = idx - i * 2 * n;
-      if (i != k && j >= k) A[i * ld + j] -= f[i] * A[k * ld + j];
-    }
-    __syncthreads();
-  }
-  T *gi = ginv + (size_t)w * n * n;
-  if (!ok) {
-    if (tid == 0) {
-      status[w] |= JAGP_WS_SINGULAR;
-      scal[(size_t)w * S_STRIDE + S_LOGDET] = -INFINITY;
-      scal[(size_t)w * S_STRIDE + S_SIGN] = 0.0;
-    }
-    return;
-  }
-  double dmax = 0.0;
-  for (int idx = tid; idx < n * n; idx += bs) {
-    const int i = idx / n, j = idx - i * n;
-    const double v = A[i * ld + n + j];
-    if (check_drift) dmax = fmax(dmax, fabs(v - static_cast<double>(gi[idx])));
-    gi[idx] = static_cast<T>(v);
-  }
-  // block max of dmax and gmax
-  for (int o = 16; o > 0; o >>= 1) {
-    dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
-    gmax = fmax(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
-  }
-  if ((tid & 31) == 0) {
-    red[tid >> 5] = dmax;
-    red[16 + (tid >> 5)] = gmax;
-  }
-  __syncthreads();
-  if (tid == 0) {
-    double d = 0.0, g = 0.0;
-    for (int q = 0; q < (bs >> 5); ++q) {
-      d = fmax(d, red[q]);
-      g = fmax(g, red[16 + q]);
-    }
-    scal[(size_t)w * S_STRIDE + S_LOGDET] = pp.log_abs();
-    scal[(size_t)w * S_STRIDE + S_SIGN] = sgn;
-    if (check_drift) {
-      const double drift = d * g;
-      scal[(size_t)w * S_STRIDE + S_DRIFT] = drift;
-      if (!(drift <= drift_tol)) status[w] |= JAGP_WS_DRIFT;
-    }
-  }
-}
-
-// The same elimination with one warp per walker (N_up <= 32): lane j owns the
-// columns j and j + 32 of [G~ | I]; pivot search by shuffles, no block barriers.
+// N_up <= 32: one warp per walker on [G~ | I]; lane j owns the columns j and
+// j + 32; pivot search by shuffles, no block barriers.
 constexpr int kRefreshWarps = 4;
 constexpr size_t kMmatSmemMax = 200 * 1024;  // k_mmat stages G~^{-1} whole up to this footprint
 constexpr size_t kRefreshSmemMax = 200 * 1024;  // [G~ | I] kept in shared memory up to this footprint
@@ -552,17 +427,19 @@ __global__ void __launch_bounds__(kRefreshWarps * 32) k_refresh_inverse_warp(
   }
 }
 
-// In-place Gauss-Jordan for N_up too large for shared memory: the FP64 G~ of
-// the walker is overwritten by its inverse in global memory (L2-resident while
-// the CTA works on it).  Step k scales the pivot row, stores -f_i / p in column
-// k and updates the rest; the row swaps of the partial pivoting become column
-// swaps of the result, undone in reverse order at the end.
-template <typename T>
-__global__ void __launch_bounds__(512) k_refresh_inverse_global(double *__restrict__ gm, T *__restrict__ ginv,
-                                                                double *__restrict__ scal, int *__restrict__ status,
-                                                                int n, int check_drift, double drift_tol) {
+// In-place Gauss-Jordan (N_up > 32): step k scales the pivot row, stores
+// -f_i / p in column k and updates the rest, so the inverse takes the place of
+// G~ (half the work of eliminating [G~ | I]); the row swaps of the partial
+// pivoting become column swaps of the result, undone in reverse order at the
+// end.  SMEM: the matrix is copied to shared memory (row pitch n + 1); else it
+// is overwritten in global memory (L2-resident while the CTA works on it).
+template <typename T, bool SMEM>
+__global__ void __launch_bounds__(512) k_refresh_inverse_inplace(double *__restrict__ gm, T *__restrict__ ginv,
+                                                                 double *__restrict__ scal, int *__restrict__ status,
+                                                                 int n, int check_drift, double drift_tol) {
   extern __shared__ double sm[];
-  double *prow = sm;                                // n: the scaled pivot row
+  const int ld = SMEM ? n + 1 : n;
+  double *prow = sm + (SMEM ? (size_t)n * ld : 0);  // n: the scaled pivot row
   double *f = prow + n;                             // n: column k before the step
   int *perm = reinterpret_cast<int *>(f + n);       // n: pivot row of each step
   __shared__ int s_piv;
@@ -571,7 +448,17 @@ __global__ void __launch_bounds__(512) k_refresh_inverse_global(double *__restri
   const int tid = threadIdx.x, bs = blockDim.x, w = blockIdx.x, lane = tid & 31, warp = tid >> 5, nw = bs >> 5;
   double *A = gm + (size_t)w * n * n;
   double gmax = 0.0;
-  for (int idx = tid; idx < n * n; idx += bs) gmax = fmax(gmax, fabs(A[idx]));
+  if (SMEM) {
+    for (int idx = tid; idx < n * n; idx += bs) {
+      const int i = idx / n, j = idx - i * n;
+      const double v = A[idx];
+      gmax = fmax(gmax, fabs(v));
+      sm[(size_t)i * ld + j] = v;
+    }
+    A = sm;
+  } else {
+    for (int idx = tid; idx < n * n; idx += bs) gmax = fmax(gmax, fabs(A[idx]));
+  }
   PivotProduct pp;
   double sgn = 1.0;
   bool ok = true;
@@ -581,7 +468,7 @@ __global__ void __launch_bounds__(512) k_refresh_inverse_global(double *__restri
       double best = -1.0;
       int bi = k;
       for (int i = k + lane; i < n; i += 32) {
-        const double v = fabs(A[(size_t)i * n + k]);
+        const double v = fabs(A[(size_t)i * ld + k]);
         if (v > best) {
           best = v;
           bi = i;
@@ -598,7 +485,7 @@ __global__ void __launch_bounds__(512) k_refresh_inverse_global(double *__restri
       }
       if (lane == 0) {
         s_piv = bi;
-        s_pv = A[(size_t)bi * n + k];
+        s_pv = A[(size_t)bi * ld + k];
       }
     }
     __syncthreads();
@@ -610,9 +497,9 @@ __global__ void __launch_bounds__(512) k_refresh_inverse_global(double *__restri
     }
     if (p != k) {
       for (int j = tid; j < n; j += bs) {
-        const double t = A[(size_t)k * n + j];
-        A[(size_t)k * n + j] = A[(size_t)p * n + j];
-        A[(size_t)p * n + j] = t;
+        const double t = A[(size_t)k * ld + j];
+        A[(size_t)k * ld + j] = A[(size_t)p * ld + j];
+        A[(size_t)p * ld + j] = t;
       }
       sgn = -sgn;
     }
@@ -621,11 +508,11 @@ __global__ void __launch_bounds__(512) k_refresh_inverse_global(double *__restri
     if (tid == 0) perm[k] = p;
     __syncthreads();
     const double ip = 1.0 / pv;
-    for (int j = tid; j < n; j += bs) prow[j] = j == k ? ip : A[(size_t)k * n + j] * ip;
-    for (int i = tid; i < n; i += bs) f[i] = i == k ? 0.0 : A[(size_t)i * n + k];
+    for (int j = tid; j < n; j += bs) prow[j] = j == k ? ip : A[(size_t)k * ld + j] * ip;
+    for (int i = tid; i < n; i += bs) f[i] = i == k ? 0.0 : A[(size_t)i * ld + k];
     __syncthreads();
     for (int i = warp; i < n; i += nw) {
-      double *Ai = A + (size_t)i * n;
+      double *Ai = A + (size_t)i * ld;
       if (i == k) {
         for (int j = lane; j < n; j += 32) Ai[j] = prow[j];
       } else {
@@ -648,15 +535,15 @@ __global__ void __launch_bounds__(512) k_refresh_inverse_global(double *__restri
     const int p = perm[k];
     if (p != k)
       for (int i = tid; i < n; i += bs) {
-        const double t = A[(size_t)i * n + k];
-        A[(size_t)i * n + k] = A[(size_t)i * n + p];
-        A[(size_t)i * n + p] = t;
+        const double t = A[(size_t)i * ld + k];
+        A[(size_t)i * ld + k] = A[(size_t)i * ld + p];
+        A[(size_t)i * ld + p] = t;
       }
     __syncthreads();
   }
   double dmax = 0.0;
   for (int idx = tid; idx < n * n; idx += bs) {
-    const double v = A[idx];
+    const double v = A[(size_t)(idx / n) * ld + idx % n];
     if (check_drift) dmax = fmax(dmax, fabs(v - static_cast<double>(gi[idx])));
     gi[idx] = static_cast<T>(v);
   }
@@ -689,10 +576,15 @@ template <typename T>
 cudaError_t launch_refresh_inverse(double *gm, T *ginv, double *scal, int *status, int n, int W,
                                    int check_drift, double drift_tol, cudaStream_t st) {
   if (W <= 0) return cudaSuccess;
-  const size_t block_smem = (size_t)(n * (2 * n + 1) + n) * sizeof(double);
-  if (n > 32 && block_smem > kRefreshSmemMax) {
-    const size_t smem = (size_t)n * (2 * sizeof(double) + sizeof(int));
-    k_refresh_inverse_global<T><<<W, 512, smem, st>>>(gm, ginv, scal, status, n, check_drift, drift_tol);
+  const size_t aux = (size_t)n * (2 * sizeof(double) + sizeof(int));
+  const size_t inplace_smem = (size_t)n * (n + 1) * sizeof(double) + aux;
+  if (n > 32 && inplace_smem <= kRefreshSmemMax) {
+    k_refresh_inverse_inplace<T, true><<<W, 256, inplace_smem, st>>>(gm, ginv, scal, status, n, check_drift,
+                                                                      drift_tol);
+    return cudaGetLastError();
+  }
+  if (n > 32) {
+    k_refresh_inverse_inplace<T, false><<<W, 512, aux, st>>>(gm, ginv, scal, status, n, check_drift, drift_tol);
     return cudaGetLastError();
   }
   if (n <= 32) {
@@ -701,8 +593,7 @@ cudaError_t launch_refresh_inverse(double *gm, T *ginv, double *scal, int *statu
         gm, ginv, scal, status, n, W, check_drift, drift_tol);
     return cudaGetLastError();
   }
-  k_refresh_inverse<T><<<W, 256, block_smem, st>>>(gm, ginv, scal, status, n, check_drift, drift_tol);
-  return cudaGetLastError();
+  return cudaErrorInvalidValue;
 }
 template cudaError_t launch_refresh_inverse<double>(double *, double *, double *, int *, int, int, int, double,
                                                     cudaStream_t);
@@ -842,10 +733,13 @@ template <typename T>
 static cudaError_t linalg_attrs() {
   const int big = 200 * 1024;
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(k_refresh_inverse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
   if ((e = cudaFuncSetAttribute(k_refresh_inverse_warp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)))
     return e;
-  if ((e = cudaFuncSetAttribute(k_refresh_inverse_global<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)))
+  if ((e = cudaFuncSetAttribute(k_refresh_inverse_inplace<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                big)))
+    return e;
+  if ((e = cudaFuncSetAttribute(k_refresh_inverse_inplace<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                big)))
     return e;
   return cudaFuncSetAttribute(k_mmat<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
 }
