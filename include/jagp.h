@@ -52,11 +52,12 @@ typedef int jagp_status_t;
 #define JAGP_WS_DRIFT 4          /* Sherman-Morrison drift above tolerance at a refresh */
 
 #define JAGP_PREC_FP64 0         /* every step in float64 */
-#define JAGP_PREC_MIXED 1        /* orbitals, lambda products, proposed rows and Sherman-Morrison in
-                                    FP32 (lambda products on the BF16 tensor cores with FP32
-                                    accumulation, operands cut into exact 8-bit fixed-point slices);
-                                    G~^{-1} refreshed by an FP64 elimination after every half-sweep;
-                                    log|det|, Jastrow, energies and their sums in FP64 */
+#define JAGP_PREC_MIXED 1        /* orbitals as double-word FP32 tables, proposed rows, Sherman-Morrison
+                                    and the kinetic contraction in FP32, lambda products on the BF16
+                                    tensor cores (operands cut into exact 8-bit fixed-point slices,
+                                    FP32 accumulation); G~^{-1} refreshed by an FP64 elimination after
+                                    every half-sweep (or every refresh_moves moves); log|det|, Jastrow,
+                                    energies and their sums in FP64 */
 
 /* The system: atoms, basis, pairing matrix lambda, unpaired orbitals, Jastrow.
  * All pointers are host pointers, read during jagp_create only. */
@@ -97,7 +98,7 @@ typedef struct jagp_ctx *jagp_handle_t;
  * table and the unpaired orbitals to the current device (the handle owns
  * those copies; jagp_destroy frees them).  Synchronous.
  * Errors: INVALID_ARG (bad sizes/pointers), UNSUPPORTED (l > 2, N_dn > N_up,
- * N_up > 64 in this release), OOM, CUDA. */
+ * N_up > 1024), OOM, CUDA. */
 jagp_status_t jagp_create(jagp_handle_t *out, const jagp_system_t *sys, const jagp_options_t *opt);
 jagp_status_t jagp_destroy(jagp_handle_t h);
 
@@ -122,7 +123,8 @@ jagp_status_t jagp_eval(jagp_handle_t h, const double *d_r, int W, void *d_state
  * key = (seed lo, seed hi): x0..x2 give the proposal, x3 the acceptance draw
  * u = x3 2^-32; accept iff u < |Psi(x')/Psi(x)|^2.  The ratio uses
  * Sherman-Morrison updates of G~^{-1}; G~^{-1}, log|det| and J are refreshed
- * in FP64 after every sweep.  d_r is updated in place.
+ * in FP64 after every sweep (and as jagp_options_t.refresh_moves and the
+ * precision ask within it).  d_r is updated in place.
  * d_eL: [nsweeps][W] local energy after each sweep, or NULL (no energies).
  * d_acc: [nsweeps][4] (sum e_L, sum e_L^2, accepted moves, max drift) or NULL. */
 jagp_status_t vmc_sweep(jagp_handle_t h, double *d_r, void *d_state, int W, int nsweeps,

@@ -354,7 +354,7 @@ jagp_status_t jagp_grad(jagp_handle_t h, const double *d_r, void *d_state, int W
   jagp_status_t s = check_walkers(h, W, d_state);
   if (s != JAGP_OK) return s;
   if (!d_r || !d_work || (reinterpret_cast<uintptr_t>(d_work) & 255u)) return JAGP_ERR_INVALID_ARG;
-  if (h->precision != JAGP_PREC_FP64 || h->ds.n_up > kMaxUpGrad) return JAGP_ERR_UNSUPPORTED;
+  if (h->precision != JAGP_PREC_FP64) return JAGP_ERR_UNSUPPORTED;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const DevSystem &d = h->ds;
   const int n = d.n_up, nd = d.n_dn, N = d.N, Lb = d.L;
@@ -375,11 +375,18 @@ jagp_status_t jagp_grad(jagp_handle_t h, const double *d_r, void *d_state, int W
     LAUNCH(JAGP_KERNEL_GEMM_ROWS, 1,
            launch_gemm_rows<double>(at<double>(d_state, L.a_up), (size_t)n * Lb, kbar + (size_t)n * Lb,
                                     (size_t)N * Lb, n, nd, Lb, wp(G.h2), (size_t)n * n, n, W, st));
-  LAUNCH(0, 1, launch_adj_gbar(at<double>(d_state, L.ginv), wp(G.h1), wp(G.h2), d_seed_logpsi, n, nd, wp(G.gbar), W,
-                               st));
-  LAUNCH(0, 1,
-         launch_adj_rows(d, at<double>(d_state, L.ginv), wp(G.gbar), at<double>(d_state, L.phi_up),
-                         at<double>(d_state, L.bt), kbar, wp(G.btbar), wp(G.abar), wp(G.phibar_a), W, st));
+  if (n <= kMaxUpGrad) {
+    LAUNCH(0, 1, launch_adj_gbar(at<double>(d_state, L.ginv), wp(G.h1), wp(G.h2), d_seed_logpsi, n, nd, wp(G.gbar),
+                                 W, st));
+    LAUNCH(0, 1,
+           launch_adj_rows(d, at<double>(d_state, L.ginv), wp(G.gbar), at<double>(d_state, L.phi_up),
+                           at<double>(d_state, L.bt), kbar, wp(G.btbar), wp(G.abar), wp(G.phibar_a), W, st));
+  } else {
+    LAUNCH(0, 8,
+           launch_adj_rows_gemm(d, at<double>(d_state, L.ginv), wp(G.h1), wp(G.h2), d_seed_logpsi,
+                                at<double>(d_state, L.phi_up), at<double>(d_state, L.bt), kbar, wp(G.gbar),
+                                wp(G.btbar), wp(G.abar), wp(G.phibar_a), W, st));
+  }
   if (nd > 0)
     LAUNCH(JAGP_KERNEL_LAMBDA_ROWS, 1,
            launch_lambda_rows(wp(G.btbar), d.lam, wp(G.phibar_dn), nullptr, nullptr, W * nd, nd, n, Lb, W * nd, st));

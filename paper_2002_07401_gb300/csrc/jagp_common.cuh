@@ -12,7 +12,7 @@
 namespace jagp {
 
 constexpr int kMaxUp = 1024;        // largest N_up accepted (G~^{-1} leaves shared memory above ~160)
-constexpr int kMaxUpGrad = 64;     // largest N_up of the adjoint (its G~-sized tables stay in shared memory)
+constexpr int kMaxUpGrad = 64;     // above this N_up the adjoint's G~-sized steps run as per-walker GEMMs
 constexpr int kWarp = 32;
 constexpr int kPropStride = 8;     // doubles per proposal record
 constexpr int kFixedSlices = 5;    // 8-bit slices per element of the fixed-point lambda products (mixed path)

@@ -114,6 +114,11 @@ cudaError_t launch_adj_gbar(const double *ginv, const double *h1, const double *
 cudaError_t launch_adj_rows(const DevSystem &s, const double *ginv, const double *gbar, const double *phi_up,
                             const double *bt, const double *kbar, double *btbar, double *abar, double *phibar, int W,
                             cudaStream_t st);
+// steps 2 and 3 as per-walker GEMMs for N_up too large for shared-memory staging
+// (h1, h2 are overwritten; gbarT receives Gbar transposed)
+cudaError_t launch_adj_rows_gemm(const DevSystem &s, const double *ginv, double *h1, double *h2, const double *sL,
+                                 const double *phi_up, const double *bt, const double *kbar, double *gbarT,
+                                 double *btbar, double *abar, double *phibar, int W, cudaStream_t st);
 int adj_position_parts(const DevSystem &s);
 cudaError_t launch_adj_positions(const DevSystem &s, const double *r, const double *sE, const double *jg,
                                  const double *mbuf, const double *phibar_a, const double *phibar_b,

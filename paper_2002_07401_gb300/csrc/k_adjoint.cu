@@ -583,6 +583,125 @@ cudaError_t launch_adj_rows(const DevSystem &s, const double *ginv, const double
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// N_up beyond shared-memory staging: the same adjoints of steps 2 and 3 as
+// per-walker GEMMs (k_bgemm below) with Gbar kept transposed,
+//   GbarT = sL Ginv - (Ginv H) Ginv,
+//   Btbar = GbarT Phi_up + Ginv Mbar_up,   Abar = Ginv^T Mbar_dn,
+//   phibar = GbarT^T Bt.
+// ---------------------------------------------------------------------------
+// C[w] = alpha op(A[w]) B[w] (+ C[w] when accumulate), op(A) = A or A^T, all
+// row-major: op(A) M x K, B K x N, C M x N.  64 x 64 output tiles, 4 x 4 per
+// thread, k in chunks of 16 (the k order of every output is 0, 1, ..., K-1).
+template <bool TA>
+__global__ void __launch_bounds__(256) k_bgemm(const double *__restrict__ A, size_t sa, int lda,
+                                               const double *__restrict__ B, size_t sb, int ldb,
+                                               double *__restrict__ C, size_t sc, int ldc, int M, int N, int K,
+                                               double alpha, int accumulate) {
+  __shared__ double As[16][65];  // As[k][i] = op(A)[i0 + i][k0 + k]
+  __shared__ double Bs[16][65];  // Bs[k][c] = B[k0 + k][c0 + c]
+  const int w = blockIdx.z, i0 = blockIdx.y * 64, c0 = blockIdx.x * 64, tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const double *Aw = A + (size_t)w * sa, *Bw = B + (size_t)w * sb;
+  double acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+  for (int k0 = 0; k0 < K; k0 += 16) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int idx = tid + q * 256;
+      double av = 0.0, bv = 0.0;
+      if (TA) {  // op(A)[i][k] = A[k][i]: consecutive threads take consecutive i
+        const int kk = idx >> 6, i = idx & 63;
+        if (k0 + kk < K && i0 + i < M) av = Aw[(size_t)(k0 + kk) * lda + i0 + i];
+        As[kk][i] = av;
+      } else {   // op(A)[i][k] = A[i][k]: consecutive threads take consecutive k
+        const int i = idx >> 4, kk = idx & 15;
+        if (k0 + kk < K && i0 + i < M) av = Aw[(size_t)(i0 + i) * lda + k0 + kk];
+        As[kk][i] = av;
+      }
+      const int kk = idx >> 6, c = idx & 63;
+      if (k0 + kk < K && c0 + c < N) bv = Bw[(size_t)(k0 + kk) * ldb + c0 + c];
+      Bs[kk][c] = bv;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      double xa[4], yb[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) xa[a] = As[kk][ty * 4 + a];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) yb[b] = Bs[kk][tx * 4 + b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = fma(xa[a], yb[b], acc[a][b]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int i = i0 + ty * 4 + a;
+    if (i >= M) continue;
+    double *Cr = C + (size_t)w * sc + (size_t)i * ldc;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int c = c0 + tx * 4 + b;
+      if (c >= N) continue;
+      Cr[c] = accumulate ? fma(alpha, acc[a][b], Cr[c]) : alpha * acc[a][b];
+    }
+  }
+}
+
+static cudaError_t bgemm(bool ta, const double *A, size_t sa, int lda, const double *B, size_t sb, int ldb, double *C,
+                         size_t sc, int ldc, int M, int N, int K, double alpha, int accumulate, int W,
+                         cudaStream_t st) {
+  if (W <= 0 || M <= 0 || N <= 0) return cudaSuccess;
+  dim3 grid((N + 63) / 64, (M + 63) / 64, W);
+  if (ta)
+    k_bgemm<true><<<grid, 256, 0, st>>>(A, sa, lda, B, sb, ldb, C, sc, ldc, M, N, K, alpha, accumulate);
+  else
+    k_bgemm<false><<<grid, 256, 0, st>>>(A, sa, lda, B, sb, ldb, C, sc, ldc, M, N, K, alpha, accumulate);
+  return cudaGetLastError();
+}
+
+// H = H1 + H2 (H2 only in the first n_dn columns), in place in h1; GbarT = sL Ginv
+__global__ void k_adj_gbar_init(const double *__restrict__ ginv, double *__restrict__ h1,
+                                const double *__restrict__ h2, const double *__restrict__ sL, int n, int nd, int W,
+                                double *__restrict__ gbarT) {
+  const long nn = (long)n * n, total = (long)W * nn;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+    const int w = (int)(t / nn), j = (int)(t % n);
+    if (j < nd) h1[t] += h2[t];
+    gbarT[t] = (sL ? sL[w] : 0.0) * ginv[t];
+  }
+}
+
+cudaError_t launch_adj_rows_gemm(const DevSystem &s, const double *ginv, double *h1, double *h2, const double *sL,
+                                 const double *phi_up, const double *bt, const double *kbar, double *gbarT,
+                                 double *btbar, double *abar, double *phibar, int W, cudaStream_t st) {
+  const int n = s.n_up, nd = s.n_dn, N = s.N, L = s.L;
+  const size_t nn = (size_t)n * n, nL = (size_t)n * L, NL = (size_t)N * L;
+  long blocks = ((long)W * nn + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  k_adj_gbar_init<<<(int)blocks, 256, 0, st>>>(ginv, h1, h2, sL, n, nd, W, gbarT);
+  cudaError_t e = cudaGetLastError();
+  // T = Ginv H (into h2), GbarT -= T Ginv
+  if (!e) e = bgemm(false, ginv, nn, n, h1, nn, n, h2, nn, n, n, n, n, 1.0, 0, W, st);
+  if (!e) e = bgemm(false, h2, nn, n, ginv, nn, n, gbarT, nn, n, n, n, n, -1.0, 1, W, st);
+  // Btbar (rows j < n_dn) = GbarT Phi_up + Ginv Mbar_up
+  if (!e && nd > 0) e = bgemm(false, gbarT, nn, n, phi_up, nL, L, btbar, nL, L, nd, L, n, 1.0, 0, W, st);
+  if (!e && nd > 0) e = bgemm(false, ginv, nn, n, kbar, NL, L, btbar, nL, L, nd, L, n, 1.0, 1, W, st);
+  // Abar = Ginv^T Mbar_dn (zero without down electrons)
+  if (!e && nd > 0) e = bgemm(true, ginv, nn, n, kbar + nL, NL, L, abar, nL, L, n, L, nd, 1.0, 0, W, st);
+  if (!e && nd == 0) e = cudaMemsetAsync(abar, 0, (size_t)W * nL * sizeof(double), st);
+  // phibar = GbarT^T Bt
+  if (!e) e = bgemm(true, gbarT, nn, n, bt, nL, L, phibar, nL, L, n, L, n, 1.0, 0, W, st);
+  return e;
+}
+
 int adj_position_parts(const DevSystem &s) { return (s.N + kAdjWarps - 1) / kAdjWarps; }
 
 cudaError_t launch_adj_positions(const DevSystem &s, const double *r, const double *sE, const double *jg,
