@@ -218,10 +218,11 @@ def profiled_traffic(src_hash):
     return d.get("dram_bytes_per_accepted_row"), d
 
 
-def timed_sweeps(pg, torch, dist, sysm, W, walker0, x0, prec, steps, warmup, ws, dev, local, profile_kernel):
+def timed_sweeps(pg, torch, dist, sysm, W, walker0, x0, prec, steps, warmup, ws, dev, local, profile_kernel,
+                 fp64_tc=False):
     """Warm up, then time `steps` sweeps (+ local energies) with CUDA events on the
     launching stream; the profiled kernel class is bracketed by event pairs."""
-    g = pg.JAGP(sysm, W, seed=0, precision=prec)
+    g = pg.JAGP(sysm, W, seed=0, precision=prec, fp64_tc=fp64_tc)
     h = g.h
     tuning = g.autotune()  # tile choices for this system and walker count (overwrites the state)
     r = g.positions(x0)
@@ -394,7 +395,9 @@ def large_bench(pg, torch, dist, args, dev, rank, ws, local):
     x0 = np.ascontiguousarray(synth.init_walkers(sysm, W * ws, seed=0)[rank * W:(rank + 1) * W])
     rr = timed_sweeps(pg, torch, dist, sysm, W, rank * W, x0, pg.JAGP_PREC_MIXED, args.large_steps, 3, ws, dev,
                       local, pg.KERNEL_LAMBDA_ROWS)
+    xs = rr["r"][:args.large_force_walkers].clone()
     rr["g"].close()
+    forces = large_forces(pg, torch, dist, sysm, xs, ws, dev) if args.large_force_walkers > 0 else None
     N, L = sysm.N, sysm.L
     kp = (L + 63) // 64 * 64
     secs = rr["prof_ms"] / 1e3
@@ -410,7 +413,40 @@ def large_bench(pg, torch, dist, args, dev, rank, ws, local):
                          "achieved": tc, "peak": BF16_SUSTAINED_TFLOPS, "unit": "TFLOP/s",
                          "frac": tc / BF16_SUSTAINED_TFLOPS if tc else None, "traffic": None,
                          "peak_source": "fallback BF16 sustained (no MEASURED_PEAKS file)",
-                         "launches": rr["prof_n"], "share_of_step": rr["prof_ms"] / rr["ms"] if rr["ms"] > 0 else None}}
+                         "launches": rr["prof_n"], "share_of_step": rr["prof_ms"] / rr["ms"] if rr["ms"] > 0 else None},
+            "forces": forces}
+
+
+def large_forces(pg, torch, dist, sysm, xs, ws, dev):
+    """E_L + forces per second on the 512-electron system (FP64 adjoint): the
+    sampled walkers' configurations, one jagp_eval + jagp_grad per step."""
+    W = xs.shape[0]
+    g = pg.JAGP(sysm, W, seed=0)
+    r = xs.contiguous()
+
+    def step():
+        g.eval(r)
+        eL = g.local_energy(r)
+        sL = 2.0 * (eL - eL.mean()) / W
+        sE = torch.full((W,), 1.0 / W, dtype=torch.float64, device=dev)
+        return g.grad(r, seed_logpsi=sL, seed_eL=sE)
+    step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if ws > 1:
+        dist.barrier()
+    e0.record()
+    step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    g.close()
+    return {"metric": "E_L+forces/s", "value": W * ws / (float(t.item()) / 1e3), "unit": "configurations/s",
+            "ms_per_step": float(t.item()), "walkers_per_gpu": W, "dtype": "f64",
+            "note": "one jagp_eval + local_energy + jagp_grad (FP64) on configurations of the mixed sweeps"}
 
 
 def run_gpu(args):
@@ -484,6 +520,12 @@ def run_gpu(args):
                              pg.KERNEL_LAMBDA_ROWS)
         other["g"].close()
 
+    # FP64-equivalent lambda products on the tensor cores (fp64_tensor_cores=1)
+    tc64 = None
+    if not args.no_fp64tc:
+        tc64 = timed_sweeps(pg, torch, dist, sysm, W, walker0, x0, pg.JAGP_PREC_FP64, args.steps, args.warmup, ws, dev,
+                            local, pg.KERNEL_LAMBDA_ROWS, fp64_tc=True)
+        tc64["g"].close()
     forces = None if args.no_forces else forces_bench(pg, torch, dist, args, dev, rank, ws, local)
     batched = None if args.no_batch else batch_bench(pg, torch, dist, args, dev, rank, ws)
     large = None if args.no_large else large_bench(pg, torch, dist, args, dev, rank, ws, local)
@@ -547,6 +589,22 @@ def run_gpu(args):
         o["precision"] = "fp64" if mixed_primary else "mixed"
         o["speedup_vs_primary"] = o["value"] / prim["value"]
         out["mixed" if not mixed_primary else "fp64"] = o
+    if tc64 is not None:
+        o = summary(tc64, False)
+        kp = (L + 63) // 64 * 64
+        nsl = 7 if L <= 512 else 8
+        secs = tc64["prof_ms"] / 1e3
+        issued = nsl * (nsl + 1) / 2 * 2.0 * kp * L * tc64["accepted"]
+        tc = issued / secs / 1e12 if secs > 0 else None
+        o["roofline"] = {"kernel": "k_umma_gemm (tcgen05, FP64-equivalent: %d BF16 slices, FP64 epilogue)" % nsl,
+                         "bound": "tensor", "achieved": tc, "peak": BF16_SUSTAINED_TFLOPS, "unit": "TFLOP/s",
+                         "frac": tc / BF16_SUSTAINED_TFLOPS if tc else None, "traffic": None,
+                         "algorithmic_fp64_tflops": 2.0 * L * L * tc64["accepted"] / secs / 1e12 if secs > 0 else None,
+                         "peak_source": "fallback BF16 sustained (no MEASURED_PEAKS file)",
+                         "launches": tc64["prof_n"], "share_of_step": tc64["prof_ms"] / tc64["ms"] if tc64["ms"] else None}
+        o["precision"] = "fp64 (lambda products FP64-equivalent on tensor cores)"
+        o["speedup_vs_primary"] = o["value"] / prim["value"]
+        out["fp64_tc"] = o
     if forces is not None:
         out["forces"] = forces
     if batched is not None:
@@ -574,6 +632,7 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--no-other", action="store_true", help="skip timing the other precision")
     ap.add_argument("--no-forces", action="store_true", help="skip the E_L + forces measurement")
+    ap.add_argument("--no-fp64tc", action="store_true", help="skip the FP64-equivalent tensor-core measurement")
     ap.add_argument("--force-walkers", type=int, default=2048)
     ap.add_argument("--force-steps", type=int, default=2)
     ap.add_argument("--force-warmup", type=int, default=1)
@@ -586,6 +645,8 @@ def main():
     ap.add_argument("--large-walkers", type=int, default=1024)
     ap.add_argument("--large-steps", type=int, default=3)
     ap.add_argument("--large-only", action="store_true", help="run only the 512-electron measurement")
+    ap.add_argument("--large-force-walkers", type=int, default=16,
+                    help="walkers of the 512-electron FP64 forces measurement (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     args = ap.parse_args()

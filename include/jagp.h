@@ -90,6 +90,11 @@ typedef struct jagp_options {
   int refresh_moves;          /* 0: refresh G~^{-1} from the tables once per sweep (FP64) or
                                  after each spin half-sweep (MIXED); k > 0: also after every
                                  k moves within a spin half-sweep (e.g. 16); < 0: INVALID_ARG */
+  int fp64_tensor_cores;      /* FP64 only.  0: lambda products with FP64 instructions.  1: the
+                                 same products FP64-equivalent on the BF16 tensor cores: FP64
+                                 rows cut into 7 exact 8-bit slices (8 slices of 7 bits when
+                                 L > 512), every slice pair of weight >= 2^-56 summed exactly in
+                                 its own accumulator, combined in FP64 (Ozaki-style splitting) */
 } jagp_options_t;
 
 typedef struct jagp_ctx *jagp_handle_t;

@@ -41,6 +41,7 @@ class _Options(C.Structure):
     _fields_ = [
         ("precision", C.c_int), ("max_walkers", C.c_int), ("delta", C.c_double),
         ("seed", C.c_uint64), ("drift_tol", C.c_double), ("refresh_moves", C.c_int),
+        ("fp64_tensor_cores", C.c_int),
     ]
 
 
@@ -133,7 +134,7 @@ def _stream(stream) -> Optional[int]:
 # --------------------------------------------------------------------------
 
 def jagp_create(sysm, precision: int = JAGP_PREC_FP64, max_walkers: int = 1, delta: Optional[float] = None,
-                seed: int = 0, drift_tol: float = 0.0, refresh_moves: int = 0) -> int:
+                seed: int = 0, drift_tol: float = 0.0, refresh_moves: int = 0, fp64_tc: bool = False) -> int:
     """sysm: a ``synth.System``-like object (numpy arrays).  Returns the handle."""
     keep = []
 
@@ -161,6 +162,7 @@ def jagp_create(sysm, precision: int = JAGP_PREC_FP64, max_walkers: int = 1, del
     o.delta = float(sysm.delta if delta is None else delta)
     o.seed, o.drift_tol = int(seed), float(drift_tol)
     o.refresh_moves = int(refresh_moves)
+    o.fp64_tensor_cores = int(bool(fp64_tc))
     h = C.c_void_p()
     _check(lib().jagp_create(C.byref(h), C.byref(s), C.byref(o)), "jagp_create")
     return h.value
@@ -277,13 +279,13 @@ class JAGP:
 
     def __init__(self, sysm, W: int, precision: int = JAGP_PREC_FP64, seed: int = 0,
                  delta: Optional[float] = None, drift_tol: float = 0.0, device: str = "cuda",
-                 refresh_moves: int = 0):
+                 refresh_moves: int = 0, fp64_tc: bool = False):
         import torch
         if not torch.cuda.is_available():
             raise JagpError("libjagp needs a CUDA device; there is no CPU fallback")
         self.sys, self.W, self.device = sysm, int(W), torch.device(device)
         with torch.cuda.device(self.device):
-            self.h = jagp_create(sysm, precision, W, delta, seed, drift_tol, refresh_moves)
+            self.h = jagp_create(sysm, precision, W, delta, seed, drift_tol, refresh_moves, fp64_tc)
             nbytes = jagp_state_bytes(self.h, W)
             # 256-byte aligned: the caching allocator hands out 512-byte aligned blocks
             self.state = torch.empty(nbytes, dtype=torch.uint8, device=self.device)

@@ -65,7 +65,7 @@ struct LaunchScope {
 Layout layout_of(const jagp_ctx *h, int W) {
   const bool mixed = h->precision == JAGP_PREC_MIXED;
   return make_layout((size_t)W, (size_t)h->ds.n_up, (size_t)h->ds.N, (size_t)h->ds.L, mixed ? 4 : 8,
-                     mixed ? (size_t)h->kp : 0);
+                     h->tc_lambda ? (size_t)h->kp : 0, (size_t)h->tc_slices);
 }
 
 // the fifteen slice pairs (a, b) with a + b <= 4 of the five-slice fixed-point
@@ -76,6 +76,18 @@ Layout layout_of(const jagp_ctx *h, int W) {
 constexpr int kFixedPairsF32 = 10;
 const int kPairA[kFixedPairs] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3, 0, 1, 2, 3, 4};
 const int kPairB[kFixedPairs] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0, 4, 3, 2, 1, 0};
+
+// all slice pairs (a, b) with a + b < nsl, ordered by a + b, then a
+int slice_pairs(int nsl, int *pa, int *pb) {
+  int np = 0;
+  for (int d = 0; d < nsl; ++d)
+    for (int a = 0; a <= d; ++a) {
+      pa[np] = a;
+      pb[np] = d - a;
+      ++np;
+    }
+  return np;
+}
 
 template <typename T>
 T *at(void *base, size_t off) {
@@ -91,17 +103,17 @@ uint16_t bf16_of_small_int(double q) {
   memcpy(&u, &f, 4);
   return static_cast<uint16_t>(u >> 16);
 }
-int slice_row_fixed(const double *v, size_t vstride, int L, uint16_t *dst, size_t kp) {
+int slice_row_fixed(const double *v, size_t vstride, int L, uint16_t *dst, size_t kp, int nsl, int bits) {
   double mx = 0.0;
   for (int k = 0; k < L; ++k) mx = std::max(mx, std::fabs(v[k * vstride]));
   int e = 0;
   if (mx > 0.0) std::frexp(mx, &e);  // mx = f 2^e, f in [0.5, 1)
   for (int k = 0; k < L; ++k) {
-    double x = std::ldexp(v[k * vstride], 7 - e);
-    for (int t = 0; t < kFixedSlices; ++t) {
+    double x = std::ldexp(v[k * vstride], bits - 1 - e);
+    for (int t = 0; t < nsl; ++t) {
       const double q = std::nearbyint(x);
       dst[t * kp + k] = bf16_of_small_int(q);
-      x = (x - q) * 256.0;
+      x = (x - q) * std::ldexp(1.0, bits);
     }
   }
   return e;
@@ -117,8 +129,26 @@ jagp_status_t check_walkers(const jagp_ctx *h, int W, const void *state) {
 // lambda products of orbital rows: out[row] = P[row]^T lambda (left) or lambda P[row] (!left)
 // for the listed rows (list/count) or the (nsub, stride) rows r < nrows.
 jagp_status_t lambda_products(jagp_ctx *h, const double *P, const float *, double *out, bool left, const int *list,
-                              const int *count, int nrows, int nsub, int stride, int max_rows, void *, int,
+                              const int *count, int nrows, int nsub, int stride, int max_rows, void *state, int W,
                               cudaStream_t st) {
+  if (h->tc_lambda) {
+    // FP64-equivalent products on the tensor cores: FP64 rows cut into exact
+    // slices, every pair of weight >= 2^-(slices x bits) summed exactly, FP64 epilogue
+    const Layout L = layout_of(h, W);
+    uint16_t *pack = at<uint16_t>(state, L.pack);
+    int *rows = at<int>(state, L.rows), *exps = at<int>(state, L.exps);
+    int pa[kMaxPairs], pb[kMaxPairs];
+    const int np = slice_pairs(h->tc_slices, pa, pb);
+    LAUNCH(0, 1,
+           launch_pack_fixed64(P, list, count, nrows, nsub, stride, h->ds.L, h->kp, h->tc_slices, h->tc_bits, pack,
+                               rows, exps, max_rows, st));
+    LAUNCH(JAGP_KERNEL_LAMBDA_ROWS, 1,
+           launch_umma_gemm(pack, max_rows, count, h->tc_slices, left ? h->split_lamT : h->split_lam, h->ds.L,
+                            h->tc_slices, h->kp, np, pa, pb, nullptr, h->ds.L, rows, h->d_err, st, exps,
+                            left ? h->exp_lamT : h->exp_lam, nullptr, left ? h->tune_bn_left : h->tune_bn_right, out,
+                            h->tc_bits));
+    return JAGP_OK;
+  }
   LAUNCH(JAGP_KERNEL_LAMBDA_ROWS, 1,
          launch_lambda_rows(P, left ? h->ds.lam : h->ds.lamT, out, list, count, nrows, nsub, stride, h->ds.L, max_rows,
                             st));
@@ -513,18 +543,24 @@ jagp_status_t jagp_create(jagp_handle_t *out, const jagp_system_t *sys, const ja
   const size_t oU = take((size_t)(k_unp > 0 ? k_unp : 1) * L * 8);
   // mixed path: lambda^T and lambda as fixed-point slices, rows padded to kp
   const bool mixed = opt->precision == JAGP_PREC_MIXED;
+  const bool tc64 = !mixed && opt->fp64_tensor_cores != 0;
+  const bool tc = mixed || tc64;
   const int kp = (L + 63) / 64 * 64;
-  const size_t split_bytes = mixed ? (size_t)L * kFixedSlices * kp * 2 : 0;
-  const size_t exp_bytes = mixed ? (size_t)L * 4 : 0;
+  // slices per element: mixed 5 x 8 bits; FP64-equivalent 7 x 8 bits, or 8 x 7
+  // bits when L > 512 so that the leading accumulators stay exact
+  const int nsl = mixed ? kFixedSlices : (tc64 ? (L <= 512 ? 7 : 8) : 0);
+  const int bits = tc64 && L > 512 ? 7 : 8;
+  const size_t split_bytes = tc ? (size_t)L * nsl * kp * 2 : 0;
+  const size_t exp_bytes = tc ? (size_t)L * 4 : 0;
   const size_t oSA = take(split_bytes), oSB = take(split_bytes), oXA = take(exp_bytes), oXB = take(exp_bytes);
   const size_t oE = take(16);
   std::vector<uint16_t> sA(split_bytes / 2, 0), sB(split_bytes / 2, 0);
-  std::vector<int> xA(mixed ? L : 0), xB(mixed ? L : 0);
-  if (mixed) {
+  std::vector<int> xA(tc ? L : 0), xB(tc ? L : 0);
+  if (tc) {
     for (int nn = 0; nn < L; ++nn) {
       // column nn, then row nn
-      xA[nn] = slice_row_fixed(sys->lambda + nn, (size_t)L, L, &sA[(size_t)nn * kFixedSlices * kp], (size_t)kp);
-      xB[nn] = slice_row_fixed(sys->lambda + (size_t)nn * L, 1, L, &sB[(size_t)nn * kFixedSlices * kp], (size_t)kp);
+      xA[nn] = slice_row_fixed(sys->lambda + nn, (size_t)L, L, &sA[(size_t)nn * nsl * kp], (size_t)kp, nsl, bits);
+      xB[nn] = slice_row_fixed(sys->lambda + (size_t)nn * L, 1, L, &sB[(size_t)nn * nsl * kp], (size_t)kp, nsl, bits);
     }
   }
   if (cudaMalloc(&h->d_mem, off) != cudaSuccess) {
@@ -544,7 +580,7 @@ jagp_status_t jagp_create(jagp_handle_t *out, const jagp_system_t *sys, const ja
             cudaMemcpy(b + oT, lamT.data(), (size_t)L * L * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
             (k_unp == 0 ||
              cudaMemcpy(b + oU, sys->unpaired, (size_t)k_unp * L * 8, cudaMemcpyHostToDevice) == cudaSuccess) &&
-            (!mixed || (cudaMemcpy(b + oSA, sA.data(), split_bytes, cudaMemcpyHostToDevice) == cudaSuccess &&
+            (!tc || (cudaMemcpy(b + oSA, sA.data(), split_bytes, cudaMemcpyHostToDevice) == cudaSuccess &&
                         cudaMemcpy(b + oSB, sB.data(), split_bytes, cudaMemcpyHostToDevice) == cudaSuccess &&
                         cudaMemcpy(b + oXA, xA.data(), exp_bytes, cudaMemcpyHostToDevice) == cudaSuccess &&
                         cudaMemcpy(b + oXB, xB.data(), exp_bytes, cudaMemcpyHostToDevice) == cudaSuccess)) &&
@@ -583,10 +619,13 @@ jagp_status_t jagp_create(jagp_handle_t *out, const jagp_system_t *sys, const ja
   d.key1 = (uint32_t)(opt->seed >> 32);
   h->precision = opt->precision;
   h->kp = kp;
-  h->split_lamT = mixed ? reinterpret_cast<const uint16_t *>(b + oSA) : nullptr;
-  h->split_lam = mixed ? reinterpret_cast<const uint16_t *>(b + oSB) : nullptr;
-  h->exp_lamT = mixed ? reinterpret_cast<const int *>(b + oXA) : nullptr;
-  h->exp_lam = mixed ? reinterpret_cast<const int *>(b + oXB) : nullptr;
+  h->split_lamT = tc ? reinterpret_cast<const uint16_t *>(b + oSA) : nullptr;
+  h->split_lam = tc ? reinterpret_cast<const uint16_t *>(b + oSB) : nullptr;
+  h->exp_lamT = tc ? reinterpret_cast<const int *>(b + oXA) : nullptr;
+  h->exp_lam = tc ? reinterpret_cast<const int *>(b + oXB) : nullptr;
+  h->tc_lambda = tc;
+  h->tc_slices = nsl;
+  h->tc_bits = bits;
   h->d_err = reinterpret_cast<int *>(b + oE);
   h->max_walkers = opt->max_walkers;
   h->drift_tol = opt->drift_tol > 0.0 ? opt->drift_tol : (mixed ? 1e-3 : 1e-8);

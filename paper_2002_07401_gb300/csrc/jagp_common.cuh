@@ -17,6 +17,7 @@ constexpr int kWarp = 32;
 constexpr int kPropStride = 8;     // doubles per proposal record
 constexpr int kFixedSlices = 5;    // 8-bit slices per element of the fixed-point lambda products (mixed path)
 constexpr int kFixedPairs = 15;    // slice pairs (a, b) with a + b < kFixedSlices
+constexpr int kMaxPairs = 36;      // slice pairs of the FP64-equivalent products (eight slices)
 
 // Shell record packed for one 32-byte load: centre (x, y, z) and exponent.
 // info = l | radial << 2 | first-function-offset << 8.
@@ -57,7 +58,7 @@ struct Layout {
   size_t status;   // int    [W]
   size_t list;     // int    [W][n_up]       accepted moves of a half-sweep
   size_t count;    // int    [4]
-  size_t pack;     // BF16   [W n_up][5 kp]  mixed path: fixed-point slices of the lambda-product rows
+  size_t pack;     // BF16   [W n_up][nsl kp] fixed-point slices of the lambda-product rows (tensor-core paths)
   size_t rows;     // int    [W n_up]        mixed path: destination rows of the packed operand
   size_t exps;     // int    [W n_up]        mixed path: row exponents of the packed operand
   size_t g64;      // double [W][n_up][n_up] G~ at a refresh (overwritten by the in-place inverse when large)
@@ -72,7 +73,8 @@ enum { S_LOGDET = 0, S_SIGN = 1, S_J = 2, S_NACC = 3, S_DRIFT = 4, S_STRIDE = 8 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // esz: bytes per table element (8 or 4); kp: padded K of the packed operand (0 = none)
-inline Layout make_layout(size_t W, size_t nu, size_t N, size_t L, size_t esz = 8, size_t kp = 0) {
+inline Layout make_layout(size_t W, size_t nu, size_t N, size_t L, size_t esz = 8, size_t kp = 0,
+                          size_t nsl = kFixedSlices) {
   Layout l;
   size_t o = 0;
   auto take = [&](size_t bytes) { size_t r = o; o = align256(o + bytes); return r; };
@@ -89,7 +91,7 @@ inline Layout make_layout(size_t W, size_t nu, size_t N, size_t L, size_t esz = 
   l.status = take(W * 4);
   l.list = take(W * nu * 4);
   l.count = take(16);
-  l.pack = take(W * nu * kFixedSlices * kp * 2);
+  l.pack = take(W * nu * nsl * kp * 2);
   l.rows = take(kp ? W * nu * 4 : 0);
   l.exps = take(kp ? W * nu * 4 : 0);
   l.g64 = take(W * nu * nu * 8);

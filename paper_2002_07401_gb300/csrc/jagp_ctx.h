@@ -13,6 +13,10 @@ struct jagp_ctx {
   int max_walkers = 0;
   double drift_tol = 1e-8;
   int refresh_moves = 0;  // see jagp_options_t
+  // lambda products on the tensor cores: the mixed path, or FP64 with
+  // fp64_tensor_cores (slices per element and bits per slice)
+  bool tc_lambda = false;
+  int tc_slices = 0, tc_bits = 8;
   void *d_mem = nullptr;
   long long launches = 0;
   int prof_kernel = 0;

@@ -95,7 +95,11 @@ cudaError_t launch_umma_gemm(const uint16_t *A, int m_max, const int *m_dev, int
                              int b_terms, int kp, int npairs, const int *pair_a, const int *pair_b, float *out,
                              long long ldo, const int *out_rows, int *err, cudaStream_t st,
                              const int *a_exp = nullptr, const int *b_exp = nullptr, float *out_lo = nullptr,
-                             int bn_max = 0);
+                             int bn_max = 0, double *out64 = nullptr, int slice_bits = 8);
+// FP64 rows -> nsl exact slices of `bits` bits per element plus a row exponent
+cudaError_t launch_pack_fixed64(const double *P, const int *list, const int *count, int nrows, int nsub, int stride,
+                                int L, int kp, int nsl, int bits, uint16_t *A, int *rows_out, int *exps,
+                                int max_rows, cudaStream_t st);
 // FP32 rows (two-float rows P + P_lo when P_lo is given) -> kFixedSlices exact
 // 8-bit slices per element (BF16) plus a row exponent
 cudaError_t launch_pack_fixed(const float *P, const float *P_lo, const int *list, const int *count, int nrows,

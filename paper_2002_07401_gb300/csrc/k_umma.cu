@@ -131,8 +131,10 @@ struct UmmaArgs {
   int bn;                // output columns per CTA (multiple of 16, <= 256)
   int stages;
   int npairs;
-  int pair_a[16], pair_b[16], pair_group[16];
+  int pair_a[kMaxPairs], pair_b[kMaxPairs], pair_group[kMaxPairs];
   int ngroups;           // accumulators (1 in plain mode)
+  int slice_bits;        // fixed-point mode: bits per slice (8, or 7 for long K)
+  double *out64;         // fixed-point mode: FP64 result instead of out / out_lo, or null
   const int *a_exp;      // fixed-point mode: row exponents [m_max], else null
   const int *b_exp;      // fixed-point mode: column exponents [n]
   uint32_t idesc;
@@ -232,6 +234,29 @@ __global__ void __launch_bounds__(128, 1) k_umma_gemm(const __grid_constant__ CU
     const uint32_t t_row = tmem + (static_cast<uint32_t>(warp * 32) << 16);
     const int ea = (g.a_exp && live) ? g.a_exp[row] : 0;
     for (int c = 0; c < g.bn; c += 16) {
+      if (g.out64) {
+        // FP64 result: v = S_0 + 2^-b (S_1 + 2^-b (S_2 + ...)) by Horner in FP64
+        // from the exact integer sums, then the power-of-two scale
+        double acc[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) acc[j] = 0.0;
+        const double wq = ldexp(1.0, -g.slice_bits);
+        for (int q = g.ngroups - 1; q >= 0; --q) {
+          float u[16];
+          tmem_ld16(t_row + static_cast<uint32_t>(q * g.bn + c), u);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) acc[j] = fma(acc[j], wq, static_cast<double>(u[j]));
+        }
+        if (live) {
+          double *o = g.out64 + dst * g.ldo + n0 + c;
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int col = n0 + c + j;
+            if (col < g.n) o[j] = ldexp(acc[j], ea + g.b_exp[col] - 2 * (g.slice_bits - 1));
+          }
+        }
+        continue;
+      }
       float v[16];
       tmem_ld16(t_row + static_cast<uint32_t>(c), v);
       if (g.a_exp) {
@@ -332,9 +357,11 @@ int umma_pick_bn(int n, int max_bn) {
 cudaError_t launch_umma_gemm(const uint16_t *A, int m_max, const int *m_dev, int a_terms, const uint16_t *B, int n,
                              int b_terms, int kp, int npairs, const int *pair_a, const int *pair_b, float *out,
                              long long ldo, const int *out_rows, int *err, cudaStream_t st, const int *a_exp,
-                             const int *b_exp, float *out_lo, int bn_max) {
+                             const int *b_exp, float *out_lo, int bn_max, double *out64, int slice_bits) {
   if (m_max <= 0 || n <= 0) return cudaSuccess;
-  if (kp <= 0 || kp % 64 != 0 || npairs < 1 || npairs > 16 || a_terms < 1 || b_terms < 1) return cudaErrorInvalidValue;
+  if (kp <= 0 || kp % 64 != 0 || npairs < 1 || npairs > kMaxPairs || a_terms < 1 || b_terms < 1)
+    return cudaErrorInvalidValue;
+  if (out64 && (!a_exp || (slice_bits != 7 && slice_bits != 8))) return cudaErrorInvalidValue;
   if ((reinterpret_cast<uintptr_t>(A) & 15u) || (reinterpret_cast<uintptr_t>(B) & 15u)) return cudaErrorInvalidValue;
   if ((a_exp == nullptr) != (b_exp == nullptr)) return cudaErrorInvalidValue;
   UmmaArgs g{};
@@ -346,7 +373,9 @@ cudaError_t launch_umma_gemm(const uint16_t *A, int m_max, const int *m_dev, int
     g.pair_group[p] = a_exp ? pair_a[p] + pair_b[p] : 0;
     if (g.pair_group[p] + 1 > g.ngroups) g.ngroups = g.pair_group[p] + 1;
   }
-  if (g.ngroups > 5) return cudaErrorInvalidValue;
+  if (g.ngroups > 8) return cudaErrorInvalidValue;
+  g.slice_bits = slice_bits;
+  g.out64 = out64;
   g.a_exp = a_exp;
   g.b_exp = b_exp;
   g.m_max = m_max;
@@ -355,7 +384,7 @@ cudaError_t launch_umma_gemm(const uint16_t *A, int m_max, const int *m_dev, int
   g.kp = kp;
   // the ngroups accumulators of bn columns share the 512 tensor-memory columns;
   // bn_max (a multiple of 16, from the autotuner) may lower the limit
-  int limit = g.ngroups <= 2 ? 256 : (g.ngroups <= 4 ? 128 : 96);
+  int limit = g.ngroups <= 2 ? 256 : (g.ngroups <= 4 ? 128 : (g.ngroups <= 5 ? 96 : 64));
   if (bn_max > 0) {
     if (bn_max % 16) return cudaErrorInvalidValue;
     limit = bn_max < limit ? bn_max : limit;
@@ -485,6 +514,53 @@ cudaError_t launch_pack_fixed(const float *P, const float *P_lo, const int *list
   if (blocks > 152 * 16) blocks = 152 * 16;
   k_pack_fixed<<<(int)blocks, 256, 0, st>>>(P, P_lo, list, count, nrows, nsub > 0 ? nsub : 1, stride, L, kp,
                                               reinterpret_cast<__nv_bfloat16 *>(A), rows_out, exps);
+  return cudaGetLastError();
+}
+
+// FP64 rows -> nsl exact slices of `bits` bits (|t| <= 2^(bits-1), BF16) per
+// element relative to 2^e, e = 1 + the binary exponent of the row's largest
+// magnitude, for the FP64-equivalent products (every step exact in FP64).
+__global__ void __launch_bounds__(256) k_pack_fixed64(const double *__restrict__ P, const int *__restrict__ list,
+                                                      const int *__restrict__ count, int nrows, int nsub, int stride,
+                                                      int L, int kp, int nsl, int bits,
+                                                      __nv_bfloat16 *__restrict__ A, int *__restrict__ rows_out,
+                                                      int *__restrict__ exps) {
+  const int rows = count ? *count : nrows;
+  const int lane = threadIdx.x & 31;
+  const long nw = (long)gridDim.x * (blockDim.x >> 5);
+  const double step = ldexp(1.0, bits);
+  for (long m = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); m < rows; m += nw) {
+    const long phys = list ? (long)list[m] : (m / nsub) * stride + (m % nsub);
+    const double *src = P + phys * L;
+    double mx = 0.0;
+    for (int k = lane; k < L; k += 32) mx = fmax(mx, fabs(src[k]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    const int e = (mx > 0.0) ? ilogb(mx) + 1 : 0;
+    if (lane == 0) {
+      rows_out[m] = (int)phys;
+      exps[m] = e;
+    }
+    __nv_bfloat16 *dst = A + m * nsl * (long)kp;
+    for (int k = lane; k < kp; k += 32) {
+      double x = k < L ? ldexp(src[k], bits - 1 - e) : 0.0;  // |x| < 2^(bits-1)
+      for (int t = 0; t < nsl; ++t) {
+        const double q = rint(x);
+        dst[t * kp + k] = __float2bfloat16_rn(static_cast<float>(q));
+        x = (x - q) * step;
+      }
+    }
+  }
+}
+
+cudaError_t launch_pack_fixed64(const double *P, const int *list, const int *count, int nrows, int nsub, int stride,
+                                int L, int kp, int nsl, int bits, uint16_t *A, int *rows_out, int *exps,
+                                int max_rows, cudaStream_t st) {
+  if (max_rows <= 0) return cudaSuccess;
+  long blocks = (max_rows + 7) / 8;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  k_pack_fixed64<<<(int)blocks, 256, 0, st>>>(P, list, count, nrows, nsub > 0 ? nsub : 1, stride, L, kp, nsl, bits,
+                                               reinterpret_cast<__nv_bfloat16 *>(A), rows_out, exps);
   return cudaGetLastError();
 }
 
