@@ -44,6 +44,7 @@ BF16_SUSTAINED_TFLOPS = 1700.0
 # phi, two-float result) 15; accepted moves are split between the spins in
 # proportion to their electron counts when the issued work is counted
 PAIRS_UP, PAIRS_DN = 10, 15
+NO_AUTOTUNE = False  # --no-autotune: time the shape heuristics' tiles
 
 
 def fixed_pairs(sysm):
@@ -224,7 +225,7 @@ def timed_sweeps(pg, torch, dist, sysm, W, walker0, x0, prec, steps, warmup, ws,
     launching stream; the profiled kernel class is bracketed by event pairs."""
     g = pg.JAGP(sysm, W, seed=0, precision=prec, fp64_tc=fp64_tc)
     h = g.h
-    tuning = g.autotune()  # tile choices for this system and walker count (overwrites the state)
+    tuning = None if NO_AUTOTUNE else g.autotune()  # tile choices for this system and walker count
     r = g.positions(x0)
     stream = torch.cuda.current_stream()
     eL = torch.empty((1, W), dtype=torch.float64, device=dev)
@@ -269,7 +270,7 @@ FORCES_WORKLOAD = ("adjoint gradients: 64 He atoms in a 16 bohr cube, N=128 (64 
                    "+ Pulay, Eq. forces:aad without space warp), d log|Psi|/d lambda and d log|Psi|/d b")
 
 
-def forces_bench(pg, torch, dist, args, dev, rank, ws, local):
+def forces_bench(pg, torch, dist, args, dev, rank, ws, local, fp64_tc=False):
     """E_L + forces per second: one step = jagp_grad over all walkers with the
     force-estimator seeds (sE = 1/M, sL = 2 (e_L - <e_L>)/M from the walkers'
     local energies), producing e_L, dE/dR, d log|Psi|/d lambda and d/d b."""
@@ -278,7 +279,7 @@ def forces_bench(pg, torch, dist, args, dev, rank, ws, local):
     sysm = synth.config4()
     W = args.force_walkers
     x0 = np.ascontiguousarray(synth.init_walkers(sysm, W * ws, seed=0)[rank * W:(rank + 1) * W])
-    g = pg.JAGP(sysm, W, seed=0)
+    g = pg.JAGP(sysm, W, seed=0, fp64_tc=fp64_tc)
     r = g.positions(x0)
     g.eval(r)
     eL, _ = g.sweep(r, 1, walker0=rank * W, sweep0=0)
@@ -527,6 +528,11 @@ def run_gpu(args):
                             local, pg.KERNEL_LAMBDA_ROWS, fp64_tc=True)
         tc64["g"].close()
     forces = None if args.no_forces else forces_bench(pg, torch, dist, args, dev, rank, ws, local)
+    forces_tc = None
+    if not args.no_forces and not args.no_fp64tc:
+        forces_tc = forces_bench(pg, torch, dist, args, dev, rank, ws, local, fp64_tc=True)
+        forces_tc["dtype"] = "f64 (lambda products FP64-equivalent on tensor cores)"
+        forces_tc["roofline"] = None
     batched = None if args.no_batch else batch_bench(pg, torch, dist, args, dev, rank, ws)
     large = None if args.no_large else large_bench(pg, torch, dist, args, dev, rank, ws, local)
 
@@ -607,6 +613,8 @@ def run_gpu(args):
         out["fp64_tc"] = o
     if forces is not None:
         out["forces"] = forces
+    if forces_tc is not None:
+        out["forces_fp64tc"] = forces_tc
     if batched is not None:
         out["batched"] = batched
     if large is not None:
@@ -649,7 +657,10 @@ def main():
                     help="walkers of the 512-electron FP64 forces measurement (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-autotune", action="store_true", help="skip the tile autotuner (heuristic tiles)")
     args = ap.parse_args()
+    global NO_AUTOTUNE
+    NO_AUTOTUNE = args.no_autotune
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

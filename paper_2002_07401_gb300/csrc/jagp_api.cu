@@ -62,10 +62,12 @@ struct LaunchScope {
     JAGP_CU(call);                              \
   } while (0)
 
+bool tc_refresh(const jagp_ctx *h) { return h->precision == JAGP_PREC_MIXED && h->ds.n_up >= kTcRefreshMinUp; }
+
 Layout layout_of(const jagp_ctx *h, int W) {
   const bool mixed = h->precision == JAGP_PREC_MIXED;
   return make_layout((size_t)W, (size_t)h->ds.n_up, (size_t)h->ds.N, (size_t)h->ds.L, mixed ? 4 : 8,
-                     h->tc_lambda ? (size_t)h->kp : 0, (size_t)h->tc_slices);
+                     h->tc_lambda ? (size_t)h->kp : 0, (size_t)h->tc_slices, tc_refresh(h));
 }
 
 // the fifteen slice pairs (a, b) with a + b <= 4 of the five-slice fixed-point
@@ -214,9 +216,26 @@ jagp_status_t run_refresh(jagp_ctx *h, const double *r, void *state, int W, int 
   const Layout L = layout_of(h, W);
   const int n = h->ds.n_up, Lb = h->ds.L;
   double *gm = refresh_g(L, state);
-  LAUNCH(JAGP_KERNEL_GEMM_ROWS, 1,
-         refresh_geminal(at<T>(state, L.phi_up), lo_table(h, state, L.phi_lo), (size_t)n * Lb, at<T>(state, L.bt),
-                         lo_table(h, state, L.bt_lo), (size_t)n * Lb, n, Lb, gm, W, st, h->tune_tile_refresh));
+  if (tc_refresh(h)) {
+    // G~ = (Phi_up + lo)(Bt + lo)^T per walker on the tensor cores: both tables
+    // cut into five fixed-point slices, fifteen pairs, FP64 epilogue
+    int *rows = at<int>(state, L.grows);
+    uint16_t *pa = at<uint16_t>(state, L.gpack_a), *pb = at<uint16_t>(state, L.gpack_b);
+    int *ea = at<int>(state, L.gexp_a), *eb = at<int>(state, L.gexp_b);
+    LAUNCH(0, 1,
+           launch_pack_fixed(at<float>(state, L.phi_up), lo_table(h, state, L.phi_lo), nullptr, nullptr, W * n, 1, 1,
+                             Lb, h->kp, pa, rows, ea, W * n, st));
+    LAUNCH(0, 1,
+           launch_pack_fixed(at<float>(state, L.bt), lo_table(h, state, L.bt_lo), nullptr, nullptr, W * n, 1, 1, Lb,
+                             h->kp, pb, rows, eb, W * n, st));
+    LAUNCH(JAGP_KERNEL_GEMM_ROWS, 1,
+           launch_umma_gemm(pa, W * n, nullptr, kFixedSlices, pb, n, kFixedSlices, h->kp, kFixedPairs, kPairA, kPairB,
+                            nullptr, n, nullptr, h->d_err, st, ea, eb, nullptr, 0, gm, 8, n, W));
+  } else {
+    LAUNCH(JAGP_KERNEL_GEMM_ROWS, 1,
+           refresh_geminal(at<T>(state, L.phi_up), lo_table(h, state, L.phi_lo), (size_t)n * Lb, at<T>(state, L.bt),
+                           lo_table(h, state, L.bt_lo), (size_t)n * Lb, n, Lb, gm, W, st, h->tune_tile_refresh));
+  }
   LAUNCH(0, 1,
          launch_refresh_inverse<T>(gm, at<T>(state, L.ginv), at<double>(state, L.scal), at<int>(state, L.status), n,
                                    W, check_drift, h->drift_tol, st));
@@ -417,11 +436,16 @@ jagp_status_t jagp_grad(jagp_handle_t h, const double *d_r, void *d_state, int W
                                 at<double>(d_state, L.phi_up), at<double>(d_state, L.bt), kbar, wp(G.gbar),
                                 wp(G.btbar), wp(G.abar), wp(G.phibar_a), W, st));
   }
-  if (nd > 0)
-    LAUNCH(JAGP_KERNEL_LAMBDA_ROWS, 1,
-           launch_lambda_rows(wp(G.btbar), d.lam, wp(G.phibar_dn), nullptr, nullptr, W * nd, nd, n, Lb, W * nd, st));
-  LAUNCH(JAGP_KERNEL_LAMBDA_ROWS, 1,
-         launch_lambda_rows(wp(G.abar), d.lamT, wp(G.phibar_b), nullptr, nullptr, W * n, n, n, Lb, W * n, st));
+  // phibar_dn = Btbar^T lambda rows, phibar_b = lambda Abar rows (on the tensor
+  // cores when the handle has FP64-equivalent products)
+  if (nd > 0) {
+    s = lambda_products(h, wp(G.btbar), nullptr, wp(G.phibar_dn), true, nullptr, nullptr, W * nd, nd, n, W * nd,
+                        d_state, W, st);
+    if (s != JAGP_OK) return s;
+  }
+  s = lambda_products(h, wp(G.abar), nullptr, wp(G.phibar_b), false, nullptr, nullptr, W * n, n, n, W * n, d_state,
+                      W, st);
+  if (s != JAGP_OK) return s;
   LAUNCH(0, 1,
          launch_adj_positions(d, d_r, d_seed_eL, wp(G.jg), at<double>(d_state, L.mbuf), wp(G.phibar_a),
                               wp(G.phibar_b), wp(G.phibar_dn), d.shell_atom, wp(G.rbar), wp(G.part), W, st));

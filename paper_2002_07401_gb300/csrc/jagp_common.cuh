@@ -18,6 +18,7 @@ constexpr int kPropStride = 8;     // doubles per proposal record
 constexpr int kFixedSlices = 5;    // 8-bit slices per element of the fixed-point lambda products (mixed path)
 constexpr int kFixedPairs = 15;    // slice pairs (a, b) with a + b < kFixedSlices
 constexpr int kMaxPairs = 36;      // slice pairs of the FP64-equivalent products (eight slices)
+constexpr int kTcRefreshMinUp = 96;  // mixed path: G~ of a refresh on the tensor cores from this N_up on
 
 // Shell record packed for one 32-byte load: centre (x, y, z) and exponent.
 // info = l | radial << 2 | first-function-offset << 8.
@@ -65,6 +66,11 @@ struct Layout {
   size_t bt_lo;    // float  [W][n_up][L]    mixed path: low parts of Bt (Bt + bt_lo is a two-float table)
   size_t phi_lo;   // float  [W][n_up][L]    mixed path: low parts of phi_up
   size_t pprop_lo; // float  [W][n_up][L]    mixed path: low parts of pprop
+  size_t gpack_a;  // BF16   [W n_up][5 kp]  mixed path, large N_up: slices of Phi_up + lo for G~ on the tensor cores
+  size_t gpack_b;  // BF16   [W n_up][5 kp]  ... and of Bt + lo
+  size_t gexp_a;   // int    [W n_up]        their row exponents
+  size_t gexp_b;   // int    [W n_up]
+  size_t grows;    // int    [W n_up]        scratch row map of the packing
   size_t total;
 };
 
@@ -74,7 +80,7 @@ inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // esz: bytes per table element (8 or 4); kp: padded K of the packed operand (0 = none)
 inline Layout make_layout(size_t W, size_t nu, size_t N, size_t L, size_t esz = 8, size_t kp = 0,
-                          size_t nsl = kFixedSlices) {
+                          size_t nsl = kFixedSlices, bool tc_refresh = false) {
   Layout l;
   size_t o = 0;
   auto take = [&](size_t bytes) { size_t r = o; o = align256(o + bytes); return r; };
@@ -98,6 +104,12 @@ inline Layout make_layout(size_t W, size_t nu, size_t N, size_t L, size_t esz = 
   l.bt_lo = take(esz == 4 ? W * nu * L * 4 : 0);
   l.phi_lo = take(esz == 4 ? W * nu * L * 4 : 0);
   l.pprop_lo = take(esz == 4 ? W * nu * L * 4 : 0);
+  const size_t gp = tc_refresh ? W * nu * kFixedSlices * kp * 2 : 0, gi = tc_refresh ? W * nu * 4 : 0;
+  l.gpack_a = take(gp);
+  l.gpack_b = take(gp);
+  l.gexp_a = take(gi);
+  l.gexp_b = take(gi);
+  l.grows = take(gi);
   l.total = o;
   return l;
 }

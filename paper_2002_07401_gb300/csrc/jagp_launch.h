@@ -86,6 +86,8 @@ cudaError_t launch_increment(uint32_t *c, uint32_t by, cudaStream_t st);
 
 // Tensor-core contraction (k_umma.cu):
 //   out[out_rows[m]][c] = sum_p sum_k A[m][pair_a[p] kp + k] B[c][pair_b[p] kp + k]
+// (batched: A and B are `batches` stacked blocks of batch_rows rows, block b of
+// A against block b of B, c < n <= batch_rows; out rows as A's)
 // A: BF16 [m_max][a_terms kp], B: BF16 [n][b_terms kp] (kp % 64 == 0, 16-byte
 // aligned bases); rows m < *m_dev (or m_max) are written; out FP32, pitch ldo.
 // With a_exp/b_exp (row / column exponents) the terms are fixed-point slices and
@@ -95,7 +97,8 @@ cudaError_t launch_umma_gemm(const uint16_t *A, int m_max, const int *m_dev, int
                              int b_terms, int kp, int npairs, const int *pair_a, const int *pair_b, float *out,
                              long long ldo, const int *out_rows, int *err, cudaStream_t st,
                              const int *a_exp = nullptr, const int *b_exp = nullptr, float *out_lo = nullptr,
-                             int bn_max = 0, double *out64 = nullptr, int slice_bits = 8);
+                             int bn_max = 0, double *out64 = nullptr, int slice_bits = 8, int batch_rows = 0,
+                             int batches = 0);
 // FP64 rows -> nsl exact slices of `bits` bits per element plus a row exponent
 cudaError_t launch_pack_fixed64(const double *P, const int *list, const int *count, int nrows, int nsub, int stride,
                                 int L, int kp, int nsl, int bits, uint16_t *A, int *rows_out, int *exps,

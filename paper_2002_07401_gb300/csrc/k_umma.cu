@@ -135,6 +135,9 @@ struct UmmaArgs {
   int ngroups;           // accumulators (1 in plain mode)
   int slice_bits;        // fixed-point mode: bits per slice (8, or 7 for long K)
   double *out64;         // fixed-point mode: FP64 result instead of out / out_lo, or null
+  int batch_rows;        // batched mode (> 0): A and B are stacked per-batch blocks of batch_rows
+                         // rows; batch b's rows of A meet only batch b's rows of B
+  int tiles_per_batch;   // batched mode: 128-row tiles per batch
   const int *a_exp;      // fixed-point mode: row exponents [m_max], else null
   const int *b_exp;      // fixed-point mode: column exponents [n]
   uint32_t idesc;
@@ -151,7 +154,12 @@ __global__ void __launch_bounds__(128, 1) k_umma_gemm(const __grid_constant__ CU
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int M = g.m_dev ? *g.m_dev : g.m_max;
-  const int m0 = blockIdx.y * 128;
+  // batched mode: tile t of batch b starts at row b * batch_rows + 128 t; rows
+  // past the batch's end (read from the next batch) are computed but not written
+  const int bb = g.batch_rows ? (int)blockIdx.y / g.tiles_per_batch : 0;
+  const int bt0 = g.batch_rows ? ((int)blockIdx.y - bb * g.tiles_per_batch) * 128 : 0;
+  const int m0 = g.batch_rows ? bb * g.batch_rows + bt0 : (int)blockIdx.y * 128;
+  const int bbase = bb * g.batch_rows;  // first B row (and column exponent) of this batch
   if (m0 >= M) return;  // whole CTA, before any barrier or tensor-memory use
   const int n0 = blockIdx.x * g.bn;
   const uint32_t a_bytes = 128u * 128u;
@@ -196,7 +204,7 @@ __global__ void __launch_bounds__(128, 1) k_umma_gemm(const __grid_constant__ CU
       mbar_expect_tx(full, stage_bytes);
       const int p = it / kchunks, c = it - p * kchunks;
       tma_load_2d(tiles + s * stage_bytes, &tmA, g.pair_a[p] * g.kp + c * 64, m0, full);
-      tma_load_2d(tiles + s * stage_bytes + a_bytes, &tmB, g.pair_b[p] * g.kp + c * 64, n0, full);
+      tma_load_2d(tiles + s * stage_bytes + a_bytes, &tmB, g.pair_b[p] * g.kp + c * 64, bbase + n0, full);
     }
   } else if (warp == 1 && lane == 0) {
     // MMA issuer: four K = 16 slices per 64-wide chunk, accumulating in TMEM
@@ -229,7 +237,7 @@ __global__ void __launch_bounds__(128, 1) k_umma_gemm(const __grid_constant__ CU
   tc_fence_after();
   if (ready) {
     const int row = m0 + warp * 32 + lane;
-    const bool live = row < M;
+    const bool live = row < M && (!g.batch_rows || bt0 + warp * 32 + lane < g.batch_rows);
     const long long dst = live ? (g.out_rows ? g.out_rows[row] : row) : 0;
     const uint32_t t_row = tmem + (static_cast<uint32_t>(warp * 32) << 16);
     const int ea = (g.a_exp && live) ? g.a_exp[row] : 0;
@@ -252,7 +260,7 @@ __global__ void __launch_bounds__(128, 1) k_umma_gemm(const __grid_constant__ CU
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
             const int col = n0 + c + j;
-            if (col < g.n) o[j] = ldexp(acc[j], ea + g.b_exp[col] - 2 * (g.slice_bits - 1));
+            if (col < g.n) o[j] = ldexp(acc[j], ea + g.b_exp[bbase + col] - 2 * (g.slice_bits - 1));
           }
         }
         continue;
@@ -286,7 +294,7 @@ __global__ void __launch_bounds__(128, 1) k_umma_gemm(const __grid_constant__ CU
           const float hi = __fadd_rn(v[j], lo[j]);
           const float l2 = __fsub_rn(lo[j], __fsub_rn(hi, v[j]));
           const int col = n0 + c + j;
-          const int sh = ea + (col < g.n ? g.b_exp[col] : 0) - 14;
+          const int sh = ea + (col < g.n ? g.b_exp[bbase + col] : 0) - 14;
           v[j] = ldexpf(hi, sh);
           lo[j] = ldexpf(l2, sh);
         }
@@ -357,7 +365,8 @@ int umma_pick_bn(int n, int max_bn) {
 cudaError_t launch_umma_gemm(const uint16_t *A, int m_max, const int *m_dev, int a_terms, const uint16_t *B, int n,
                              int b_terms, int kp, int npairs, const int *pair_a, const int *pair_b, float *out,
                              long long ldo, const int *out_rows, int *err, cudaStream_t st, const int *a_exp,
-                             const int *b_exp, float *out_lo, int bn_max, double *out64, int slice_bits) {
+                             const int *b_exp, float *out_lo, int bn_max, double *out64, int slice_bits,
+                             int batch_rows, int batches) {
   if (m_max <= 0 || n <= 0) return cudaSuccess;
   if (kp <= 0 || kp % 64 != 0 || npairs < 1 || npairs > kMaxPairs || a_terms < 1 || b_terms < 1)
     return cudaErrorInvalidValue;
@@ -376,6 +385,9 @@ cudaError_t launch_umma_gemm(const uint16_t *A, int m_max, const int *m_dev, int
   if (g.ngroups > 8) return cudaErrorInvalidValue;
   g.slice_bits = slice_bits;
   g.out64 = out64;
+  if (batch_rows < 0 || (batch_rows > 0 && (batches <= 0 || n > batch_rows))) return cudaErrorInvalidValue;
+  g.batch_rows = batch_rows;
+  g.tiles_per_batch = batch_rows > 0 ? (batch_rows + 127) / 128 : 0;
   g.a_exp = a_exp;
   g.b_exp = b_exp;
   g.m_max = m_max;
@@ -408,11 +420,12 @@ cudaError_t launch_umma_gemm(const uint16_t *A, int m_max, const int *m_dev, int
   g.out_rows = out_rows;
   g.err = err;
   CUtensorMap ta, tb;
+  const uint64_t b_rows = batch_rows > 0 ? static_cast<uint64_t>(batch_rows) * batches : static_cast<uint64_t>(n);
   if (!make_map(&ta, A, static_cast<uint64_t>(a_terms) * kp, static_cast<uint64_t>(m_max), 128) ||
-      !make_map(&tb, B, static_cast<uint64_t>(b_terms) * kp, static_cast<uint64_t>(n), static_cast<uint32_t>(g.bn)))
+      !make_map(&tb, B, static_cast<uint64_t>(b_terms) * kp, b_rows, static_cast<uint32_t>(g.bn)))
     return cudaErrorInvalidValue;
   const size_t smem = 1024 + static_cast<size_t>(g.stages) * stage_bytes + 8 * (2 * g.stages + 1) + 16;
-  dim3 grid((n + g.bn - 1) / g.bn, (m_max + 127) / 128);
+  dim3 grid((n + g.bn - 1) / g.bn, batch_rows > 0 ? batches * g.tiles_per_batch : (m_max + 127) / 128);
   k_umma_gemm<<<grid, 128, smem, st>>>(ta, tb, g);
   return cudaGetLastError();
 }
