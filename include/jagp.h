@@ -195,7 +195,8 @@ jagp_status_t jagp_walker_status(jagp_handle_t h, const void *d_state, int W, in
  * Times the candidate tilings of the per-walker products (proposed rows and
  * columns: one output per thread, 32x32 or 64x64 register-blocked tiles; the
  * refresh product G~ = Phi_up Bt^T likewise) and, in the mixed path, the
- * output-tile width of the tensor-core lambda products (32..128 columns), on
+ * output-tile width (32..128 columns) and pipeline depth of the tensor-core
+ * lambda products, on
  * this handle's operands and the caller's state buffer of W walkers; keeps the
  * fastest in the handle for every later call.  The choices change only the
  * tiling of outputs, never the order of a sum: results are identical with or
@@ -208,6 +209,8 @@ typedef struct {
   int umma_bn_left;    /* mixed path: tensor-core tile width, A_up = phi^T lambda (0 in FP64) */
   int umma_bn_right;   /* mixed path: tensor-core tile width, Bt = lambda phi */
   float ms[4];
+  int umma_stages_left;   /* pipeline stages of those products (0: as many as fit in 200 KB) */
+  int umma_stages_right;
 } jagp_tuning_t;
 jagp_status_t jagp_autotune(jagp_handle_t h, void *d_state, int W, jagp_tuning_t *out, void *stream);
 

@@ -47,7 +47,8 @@ class _Options(C.Structure):
 
 class _Tuning(C.Structure):
     _fields_ = [("tile_proposals", C.c_int), ("tile_refresh", C.c_int), ("umma_bn_left", C.c_int),
-                ("umma_bn_right", C.c_int), ("ms", C.c_float * 4)]
+                ("umma_bn_right", C.c_int), ("ms", C.c_float * 4), ("umma_stages_left", C.c_int),
+                ("umma_stages_right", C.c_int)]
 
 
 _lib = None
@@ -271,7 +272,8 @@ def jagp_autotune(h, state, W, stream=None) -> dict:
     t = _Tuning()
     _check(lib().jagp_autotune(h, _ptr(state), int(W), C.byref(t), _stream(stream)), "jagp_autotune")
     return {"tile_proposals": t.tile_proposals, "tile_refresh": t.tile_refresh, "umma_bn_left": t.umma_bn_left,
-            "umma_bn_right": t.umma_bn_right, "ms": [float(v) for v in t.ms]}
+            "umma_bn_right": t.umma_bn_right, "umma_stages_left": t.umma_stages_left,
+            "umma_stages_right": t.umma_stages_right, "ms": [float(v) for v in t.ms]}
 
 
 class JAGP:

@@ -148,7 +148,7 @@ jagp_status_t lambda_products(jagp_ctx *h, const double *P, const float *, doubl
            launch_umma_gemm(pack, max_rows, count, h->tc_slices, left ? h->split_lamT : h->split_lam, h->ds.L,
                             h->tc_slices, h->kp, np, pa, pb, nullptr, h->ds.L, rows, h->d_err, st, exps,
                             left ? h->exp_lamT : h->exp_lam, nullptr, left ? h->tune_bn_left : h->tune_bn_right, out,
-                            h->tc_bits));
+                            h->tc_bits, 0, 0, left ? h->tune_st_left : h->tune_st_right));
     return JAGP_OK;
   }
   LAUNCH(JAGP_KERNEL_LAMBDA_ROWS, 1,
@@ -173,7 +173,8 @@ jagp_status_t lambda_products(jagp_ctx *h, const float *P, const float *P_lo, fl
          launch_umma_gemm(pack, max_rows, count, kFixedSlices, left ? h->split_lamT : h->split_lam, h->ds.L,
                           kFixedSlices, h->kp, left ? kFixedPairsF32 : kFixedPairs, kPairA, kPairB, out, h->ds.L,
                           rows, h->d_err, st, exps, left ? h->exp_lamT : h->exp_lam, out_lo,
-                          left ? h->tune_bn_left : h->tune_bn_right));
+                          left ? h->tune_bn_left : h->tune_bn_right, nullptr, 8, 0, 0,
+                          left ? h->tune_st_left : h->tune_st_right));
   return JAGP_OK;
 }
 
@@ -203,9 +204,11 @@ jagp_status_t run_local_energy(jagp_ctx *h, const double *r, void *state, int W,
          launch_mmat<T>(h->ds, at<T>(state, L.ginv), at<T>(state, L.bt), at<T>(state, L.a_up), at<T>(state, L.mbuf), W,
                         st));
   LAUNCH(JAGP_KERNEL_ENERGY, 1, launch_kinetic<T>(h->ds, r, at<T>(state, L.mbuf), at<double>(state, L.kin), W, st));
-  LAUNCH(JAGP_KERNEL_ENERGY, 1,
-         launch_elocal(h->ds, r, at<double>(state, L.kin), eL, parts, W, st,
-                       write_jastrow ? at<double>(state, L.scal) : nullptr));
+  double *sc = write_jastrow ? at<double>(state, L.scal) : nullptr;
+  if (std::is_same<T, float>::value)
+    LAUNCH(JAGP_KERNEL_ENERGY, 1, launch_elocal_dw(h->ds, r, at<double>(state, L.kin), eL, parts, W, st, sc));
+  else
+    LAUNCH(JAGP_KERNEL_ENERGY, 1, launch_elocal(h->ds, r, at<double>(state, L.kin), eL, parts, W, st, sc));
   return JAGP_OK;
 }
 
@@ -749,42 +752,59 @@ jagp_status_t tune_products(jagp_ctx *h, void *state, int W, cudaStream_t st, ja
   }
   out->tile_refresh = h->tune_tile_refresh;
   out->ms[1] = best;
-  if (!std::is_same<T, float>::value) return JAGP_OK;
+  if (!h->tc_lambda) return JAGP_OK;
   // tensor-core lambda products of half the orbital rows (the accepted rows of
-  // a half-sweep at ~50% acceptance), A_up (ten pairs) and Bt (fifteen)
+  // a half-sweep at ~50% acceptance): mixed A_up (ten pairs) and Bt (fifteen),
+  // or the FP64-equivalent products (all pairs of 7 or 8 slices, FP64 result)
+  const bool f64 = !std::is_same<T, float>::value;
   uint16_t *pack = at<uint16_t>(state, L.pack);
   int *exps = at<int>(state, L.exps);
   const int rows = (W * n + 1) / 2;
+  int pa64[kMaxPairs], pb64[kMaxPairs];
+  const int np64 = slice_pairs(h->tc_slices, pa64, pb64);
   for (int side = 0; side < 2; ++side) {
     const bool left = side == 0;
     const int cands[6] = {32, 48, 64, 80, 96, 128};
-    const int limit = left ? 128 : 96;
+    const int stages[2] = {0, 3};  // as many as fit (one CTA per SM), or three (several CTAs per SM)
+    const int limit = f64 ? 64 : (left ? 128 : 96);
     float bs = 0.0f;
-    int bbn = 0;
-    for (int c = 0; c < 6; ++c) {
-      if (cands[c] > limit) continue;
-      float ms = 0.0f;
-      JAGP_CU(time_calls(
-          [&] {
-            return launch_umma_gemm(pack, rows, nullptr, kFixedSlices, left ? h->split_lamT : h->split_lam, Lb,
-                                    kFixedSlices, h->kp, left ? kFixedPairsF32 : kFixedPairs, kPairA, kPairB,
-                                    reinterpret_cast<float *>(left ? at<T>(state, L.a_up) : bt), Lb, nullptr,
-                                    h->d_err, st, exps, left ? h->exp_lamT : h->exp_lam,
-                                    left ? nullptr : at<float>(state, L.bt_lo), cands[c]);
-          },
-          st, &ms));
-      if (bbn == 0 || ms < bs) {
-        bs = ms;
-        bbn = cands[c];
+    int bbn = 0, bst = 0;
+    for (int c = 0; c < 6; ++c)
+      for (int q = 0; q < 2; ++q) {
+        if (cands[c] > limit) continue;
+        float ms = 0.0f;
+        JAGP_CU(time_calls(
+            [&] {
+              T *dst = left ? at<T>(state, L.a_up) : bt;
+              if (f64)
+                return launch_umma_gemm(pack, rows, nullptr, h->tc_slices, left ? h->split_lamT : h->split_lam, Lb,
+                                        h->tc_slices, h->kp, np64, pa64, pb64, nullptr, Lb, nullptr, h->d_err, st,
+                                        exps, left ? h->exp_lamT : h->exp_lam, nullptr, cands[c],
+                                        reinterpret_cast<double *>(dst), h->tc_bits, 0, 0, stages[q]);
+              return launch_umma_gemm(pack, rows, nullptr, kFixedSlices, left ? h->split_lamT : h->split_lam, Lb,
+                                      kFixedSlices, h->kp, left ? kFixedPairsF32 : kFixedPairs, kPairA, kPairB,
+                                      reinterpret_cast<float *>(dst), Lb, nullptr, h->d_err, st, exps,
+                                      left ? h->exp_lamT : h->exp_lam, left ? nullptr : at<float>(state, L.bt_lo),
+                                      cands[c], nullptr, 8, 0, 0, stages[q]);
+            },
+            st, &ms));
+        if (bbn == 0 || ms < bs) {
+          bs = ms;
+          bbn = cands[c];
+          bst = stages[q];
+        }
       }
-    }
     if (left) {
       h->tune_bn_left = bbn;
+      h->tune_st_left = bst;
       out->umma_bn_left = bbn;
+      out->umma_stages_left = bst;
       out->ms[2] = bs;
     } else {
       h->tune_bn_right = bbn;
+      h->tune_st_right = bst;
       out->umma_bn_right = bbn;
+      out->umma_stages_right = bst;
       out->ms[3] = bs;
     }
   }

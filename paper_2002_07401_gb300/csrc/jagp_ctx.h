@@ -31,6 +31,7 @@ struct jagp_ctx {
   int *d_err = nullptr;                  // tensor-core pipeline timeout flag
   // tile choices of jagp_autotune (0 / -1: the shape heuristics)
   int tune_bn_left = 0, tune_bn_right = 0;  // tensor-core tile width of the lambda products
+  int tune_st_left = 0, tune_st_right = 0;  // and pipeline depth (0: as many stages as fit)
   int tune_tile_prop = -1;                  // per-walker proposal products (gemm_rows tile)
   int tune_tile_refresh = -1;               // per-walker refresh product G~ = Phi_up Bt^T
 };

@@ -72,6 +72,9 @@ cudaError_t launch_kinetic(const DevSystem &s, const double *r, const T *mbuf, d
                            cudaStream_t st);
 cudaError_t launch_elocal(const DevSystem &s, const double *r, const double *kin, double *eL,
                           double *parts, int W, cudaStream_t st, double *scal = nullptr);
+// the FP32 path's version (double-word distances, Coulomb sums and Jastrow values)
+cudaError_t launch_elocal_dw(const DevSystem &s, const double *r, const double *kin, double *eL,
+                             double *parts, int W, cudaStream_t st, double *scal = nullptr);
 
 cudaError_t launch_walker_init(double *scal, int *status, int W, cudaStream_t st);
 cudaError_t launch_logpsi_out(const double *scal, int W, double *logabs, double *sign,
@@ -98,7 +101,7 @@ cudaError_t launch_umma_gemm(const uint16_t *A, int m_max, const int *m_dev, int
                              long long ldo, const int *out_rows, int *err, cudaStream_t st,
                              const int *a_exp = nullptr, const int *b_exp = nullptr, float *out_lo = nullptr,
                              int bn_max = 0, double *out64 = nullptr, int slice_bits = 8, int batch_rows = 0,
-                             int batches = 0);
+                             int batches = 0, int stages_max = 0);
 // FP64 rows -> nsl exact slices of `bits` bits per element plus a row exponent
 cudaError_t launch_pack_fixed64(const double *P, const int *list, const int *count, int nrows, int nsub, int stride,
                                 int L, int kp, int nsl, int bits, uint16_t *A, int *rows_out, int *exps,

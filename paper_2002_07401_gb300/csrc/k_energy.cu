@@ -246,6 +246,137 @@ __global__ void __launch_bounds__(128) k_elocal(DevSystem s, const double *__res
   }
 }
 
+// ---------------------------------------------------------------------------
+// The same local-energy assembly for the FP32 path with FP32 instructions:
+// distances, 1/r, the Coulomb sums and the Jastrow values in double-word
+// arithmetic (dword.cuh; ~1e-14 relative, so V, J and the Jastrow gradients
+// and Laplacians keep FP64-level accuracy without the FP64 pipe; the Jastrow
+// gradient multiplies grad D / D in the kinetic term, so FP32 there was not
+// enough).  One CTA per walker; the per-thread sums are double-words,
+// combined in FP64 at the end.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ fdw dw_recip(fdw x) {
+  const float y = __frcp_rn(x.hi);
+  // e = 1 - x y (exactly as a double-word via fma), y' = y + y e
+  const float e = __fadd_rn(__fmaf_rn(-x.hi, y, 1.0f), -__fmul_rn(x.lo, y));
+  return fast_two_sum(y, __fmul_rn(y, e));
+}
+
+__global__ void __launch_bounds__(128) k_elocal_dw(DevSystem s, const double *__restrict__ r,
+                                                   const double *__restrict__ kin, double *__restrict__ eL,
+                                                   double *__restrict__ parts, double *__restrict__ scal) {
+  const int w = blockIdx.x, N = s.N, tid = threadIdx.x, na = s.n_atoms;
+  extern __shared__ float sf[];
+  float *xh = sf, *xl = xh + 3 * N;      // electron coordinates as double-words
+  float *ah = xl + 3 * N, *al = ah + 3 * na;  // atom coordinates
+  for (int t = tid; t < N * 3; t += blockDim.x) {
+    const fdw v = dw_of(r[(size_t)w * N * 3 + t]);
+    xh[t] = v.hi;
+    xl[t] = v.lo;
+  }
+  for (int t = tid; t < na * 3; t += blockDim.x) {
+    const fdw v = dw_of(s.R[t]);
+    ah[t] = v.hi;
+    al[t] = v.lo;
+  }
+  __syncthreads();
+  fdw tkin{0.0f, 0.0f}, vee{0.0f, 0.0f}, vei{0.0f, 0.0f}, jv{0.0f, 0.0f};
+  for (int e = tid; e < N; e += blockDim.x) {
+    const fdw pe[3] = {{xh[3 * e], xl[3 * e]}, {xh[3 * e + 1], xl[3 * e + 1]}, {xh[3 * e + 2], xl[3 * e + 2]}};
+    fdw gJx{0.0f, 0.0f}, gJy{0.0f, 0.0f}, gJz{0.0f, 0.0f}, lJ{0.0f, 0.0f};
+    for (int a = 0; a < na; ++a) {
+      const fdw dx = dw_add(pe[0], fdw{-ah[3 * a], -al[3 * a]});
+      const fdw dy = dw_add(pe[1], fdw{-ah[3 * a + 1], -al[3 * a + 1]});
+      const fdw dz = dw_add(pe[2], fdw{-ah[3 * a + 2], -al[3 * a + 2]});
+      const fdw r2 = dw_add(dw_add(dw_mul(dx, dx), dw_mul(dy, dy)), dw_mul(dz, dz));
+      const fdw rr = dw_sqrt(r2), rinv = dw_recip(rr);
+      vei = dw_add(vei, dw_mul(rinv, dw_neg(dw_of(s.Z[a]))));
+      if (s.use_j1) {
+        // f = -c^3 u(c r), u = (1 - e^{-b c r}) / (2b); f' = -c^4 e / 2, f'' = c^5 b e / 2
+        const double c = s.c1[a], b = s.b_ea;
+        fdw ex{1.0f, 0.0f};
+        if (b == 0.0) {
+          jv = dw_add(jv, dw_mul(rr, dw_of(-0.5 * c * c * c * c)));
+        } else {
+          ex = dw_exp_neg(dw_mul(rr, dw_of(-b * c)));
+          // -c^3 (1 - e) / (2b) = c^3 / (2b) (e - 1)
+          jv = dw_add(jv, dw_mul(dw_add_f(ex, -1.0f), dw_of(c * c * c / (2.0 * b))));
+        }
+        const fdw fp = dw_mul(ex, dw_of(-0.5 * c * c * c * c));   // f'
+        const fdw fpp = dw_mul(fp, dw_of(-c * b));                 // f'' = -b c f'
+        const fdw q = dw_mul(fp, rinv);
+        gJx = dw_add(gJx, dw_mul(q, dx));
+        gJy = dw_add(gJy, dw_mul(q, dy));
+        gJz = dw_add(gJz, dw_mul(q, dz));
+        lJ = dw_add(lJ, dw_add(fpp, dw_add(q, q)));
+      }
+    }
+    for (int k = 0; k < N; ++k) {
+      if (k == e) continue;
+      const fdw dx = dw_add(pe[0], fdw{-xh[3 * k], -xl[3 * k]});
+      const fdw dy = dw_add(pe[1], fdw{-xh[3 * k + 1], -xl[3 * k + 1]});
+      const fdw dz = dw_add(pe[2], fdw{-xh[3 * k + 2], -xl[3 * k + 2]});
+      const fdw r2 = dw_add(dw_add(dw_mul(dx, dx), dw_mul(dy, dy)), dw_mul(dz, dz));
+      const fdw rr = dw_sqrt(r2), rinv = dw_recip(rr);
+      if (k > e) vee = dw_add(vee, rinv);
+      if (s.use_j2) {
+        double kk, bb;
+        j2_params(s, (e < s.n_up) == (k < s.n_up), &kk, &bb);
+        const fdw den = dw_add_f(dw_mul(rr, dw_of(bb * kk)), static_cast<float>(kk));  // k (1 + b r), k exact
+        const fdw iq = dw_recip(den);                                                 // 1 / (k (1 + b r))
+        if (k > e) jv = dw_add(jv, dw_mul(rr, iq));
+        const fdw qi = dw_mul_f(iq, static_cast<float>(kk));                          // 1/q (k exact)
+        const fdw vp = dw_mul(iq, qi);                                               // 1 / (k q^2)
+        const fdw vpp = dw_mul(dw_mul(vp, qi), dw_of(-2.0 * bb));                     // -2b / (k q^3)
+        const fdw q = dw_mul(vp, rinv);
+        gJx = dw_add(gJx, dw_mul(q, dx));
+        gJy = dw_add(gJy, dw_mul(q, dy));
+        gJz = dw_add(gJz, dw_mul(q, dz));
+        lJ = dw_add(lJ, dw_add(vpp, dw_add(q, q)));
+      }
+    }
+    const double *kd = kin + ((size_t)w * N + e) * 4;
+    const double gx = static_cast<double>(gJx.hi) + gJx.lo, gy = static_cast<double>(gJy.hi) + gJy.lo,
+                 gz = static_cast<double>(gJz.hi) + gJz.lo, lj = static_cast<double>(lJ.hi) + lJ.lo;
+    const double t = kd[3] + lj + 2.0 * (kd[0] * gx + kd[1] * gy + kd[2] * gz) + (gx * gx + gy * gy + gz * gz);
+    tkin = dw_add(tkin, dw_of(-0.5 * t));
+  }
+  __shared__ double red[4][4];
+  double a4[4] = {static_cast<double>(tkin.hi) + tkin.lo, static_cast<double>(vee.hi) + vee.lo,
+                  static_cast<double>(vei.hi) + vei.lo, static_cast<double>(jv.hi) + jv.lo};
+#pragma unroll
+  for (int q = 0; q < 4; ++q) a4[q] = warp_sum(a4[q]);
+  if ((tid & 31) == 0)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) red[q][tid >> 5] = a4[q];
+  __syncthreads();
+  if (tid == 0) {
+    double a = 0.0, b = 0.0, c = 0.0, j = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
+      a += red[0][q];
+      b += red[1][q];
+      c += red[2][q];
+      j += red[3][q];
+    }
+    eL[w] = a + b + c + s.v_ii;
+    if (parts) {
+      parts[(size_t)w * 4 + 0] = a;
+      parts[(size_t)w * 4 + 1] = b;
+      parts[(size_t)w * 4 + 2] = c;
+      parts[(size_t)w * 4 + 3] = s.v_ii;
+    }
+    if (scal) scal[(size_t)w * S_STRIDE + S_J] = j;
+  }
+}
+
+cudaError_t launch_elocal_dw(const DevSystem &s, const double *r, const double *kin, double *eL, double *parts, int W,
+                             cudaStream_t st, double *scal) {
+  if (W <= 0) return cudaSuccess;
+  const size_t smem = (size_t)(s.N + s.n_atoms) * 6 * sizeof(float);
+  k_elocal_dw<<<W, 128, smem, st>>>(s, r, kin, eL, parts, scal);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_elocal(const DevSystem &s, const double *r, const double *kin, double *eL, double *parts, int W,
                           cudaStream_t st, double *scal) {
   if (W <= 0) return cudaSuccess;

@@ -149,7 +149,7 @@ struct UmmaArgs {
   int *err;
 };
 
-__global__ void __launch_bounds__(128, 1) k_umma_gemm(const __grid_constant__ CUtensorMap tmA,
+__global__ void __launch_bounds__(128) k_umma_gemm(const __grid_constant__ CUtensorMap tmA,
                                                       const __grid_constant__ CUtensorMap tmB, UmmaArgs g) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -366,7 +366,7 @@ cudaError_t launch_umma_gemm(const uint16_t *A, int m_max, const int *m_dev, int
                              int b_terms, int kp, int npairs, const int *pair_a, const int *pair_b, float *out,
                              long long ldo, const int *out_rows, int *err, cudaStream_t st, const int *a_exp,
                              const int *b_exp, float *out_lo, int bn_max, double *out64, int slice_bits,
-                             int batch_rows, int batches) {
+                             int batch_rows, int batches, int stages_max) {
   if (m_max <= 0 || n <= 0) return cudaSuccess;
   if (kp <= 0 || kp % 64 != 0 || npairs < 1 || npairs > kMaxPairs || a_terms < 1 || b_terms < 1)
     return cudaErrorInvalidValue;
@@ -403,8 +403,11 @@ cudaError_t launch_umma_gemm(const uint16_t *A, int m_max, const int *m_dev, int
   }
   g.bn = umma_pick_bn(n, limit);
   const uint32_t stage_bytes = 128u * 128u + static_cast<uint32_t>(g.bn) * 128u;
+  // pipeline depth: as many stages as fit in 200 KB, at most 6, or fewer
+  // (stages_max, from the autotuner) so that several CTAs share an SM
   g.stages = static_cast<int>((200u * 1024u) / stage_bytes);
   if (g.stages > 6) g.stages = 6;
+  if (stages_max > 0 && stages_max < g.stages) g.stages = stages_max < 2 ? 2 : stages_max;
   g.npairs = npairs;
   g.idesc = (1u << 4)                                   // D: FP32
             | (1u << 7) | (1u << 10)                    // A, B: BF16

@@ -25,17 +25,18 @@ SYSTEMS = {
 }
 
 
-@pytest.mark.parametrize("mixed", [False, True])
+@pytest.mark.parametrize("mode", ["fp64", "fp64tc", "mixed"])
 @pytest.mark.parametrize("name", list(SYSTEMS))
-def test_autotune_changes_no_result(torch_cuda, name, mixed):
+def test_autotune_changes_no_result(torch_cuda, name, mode):
     import paper_2002_07401_gb300 as pg
     sysm = SYSTEMS[name]()
+    mixed = mode == "mixed"
     prec = pg.JAGP_PREC_MIXED if mixed else pg.JAGP_PREC_FP64
     W = 96
     x0 = synth.jitter_walkers(synth.init_walkers(sysm, W, seed=4), 5, 0.2)
     runs = []
     for tune in (False, True):
-        g = pg.JAGP(sysm, W, precision=prec, seed=3)
+        g = pg.JAGP(sysm, W, precision=prec, seed=3, fp64_tc=mode == "fp64tc")
         r = g.positions(x0)
         if tune:
             t = g.autotune()
@@ -43,6 +44,10 @@ def test_autotune_changes_no_result(torch_cuda, name, mixed):
             if mixed:
                 assert t["umma_bn_left"] in (32, 48, 64, 80, 96, 128)
                 assert t["umma_bn_right"] in (32, 48, 64, 80, 96)
+                assert t["umma_stages_left"] in (0, 3) and t["umma_stages_right"] in (0, 3)
+                assert all(m > 0 for m in t["ms"])
+            elif mode == "fp64tc":
+                assert t["umma_bn_left"] in (32, 48, 64) and t["umma_bn_right"] in (32, 48, 64)
                 assert all(m > 0 for m in t["ms"])
             else:
                 assert t["umma_bn_left"] == t["umma_bn_right"] == 0

@@ -99,3 +99,27 @@ def test_fp64tc_full_size_c2_matches_native_fp64(torch_cuda):
         g.close()
     assert np.array_equal(out[0][0], out[1][0])
     assert np.all(_close(out[1][1], out[0][1]))
+
+
+def test_fp64tc_adjoint_matches_native(torch_cuda):
+    """jagp_grad with the tensor-core FP64-equivalent lambda products equals the
+    native FP64 adjoint to 1e-9 (relative to the largest component)."""
+    torch = torch_cuda
+    import paper_2002_07401_gb300 as pg
+    sysm = SYSTEMS["mid-n40"]()
+    W = 4
+    x = _walkers(sysm, W, seed=12)
+    sL = torch.tensor([0.3, -1.1, 0.7, 0.2], dtype=torch.float64, device="cuda")
+    sE = torch.tensor([0.25, 0.25, -0.5, 1.0], dtype=torch.float64, device="cuda")
+    outs = []
+    for tc in (False, True):
+        g = pg.JAGP(sysm, W, fp64_tc=tc)
+        r = g.positions(x)
+        g.eval(r)
+        o = g.grad(r, seed_logpsi=sL, seed_eL=sE)
+        outs.append({k: v.cpu().numpy() for k, v in o.items() if v is not None})
+        g.close()
+    for k in ("eL", "lam", "jas", "R", "r"):
+        a, b = outs[1][k], outs[0][k]
+        scale = max(1.0, float(np.abs(b).max()))
+        assert float(np.abs(a - b).max()) <= 1e-9 * scale, (k, float(np.abs(a - b).max()) / scale)
