@@ -18,7 +18,7 @@ constexpr int kPropStride = 8;     // doubles per proposal record
 constexpr int kFixedSlices = 5;    // 8-bit slices per element of the fixed-point lambda products (mixed path)
 constexpr int kFixedPairs = 15;    // slice pairs (a, b) with a + b < kFixedSlices
 constexpr int kMaxPairs = 36;      // slice pairs of the FP64-equivalent products (eight slices)
-constexpr int kTcRefreshMinUp = 96;  // mixed path: G~ of a refresh on the tensor cores from this N_up on
+constexpr int kTcRefreshMinUp = 32;  // mixed path: G~ of a refresh on the tensor cores from this N_up on
 
 // Shell record packed for one 32-byte load: centre (x, y, z) and exponent.
 // info = l | radial << 2 | first-function-offset << 8.

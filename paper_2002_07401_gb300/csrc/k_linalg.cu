@@ -572,12 +572,144 @@ __global__ void __launch_bounds__(512) k_refresh_inverse_inplace(double *__restr
   }
 }
 
+// 32 < N_up <= 64: the in-place elimination (as above) with one warp per
+// walker; lane j owns columns j and j + 32 of G~; pivot search by shuffles and
+// no block barriers, which matters when refreshes come every few moves.
+template <typename T>
+__global__ void __launch_bounds__(kRefreshWarps * 32) k_refresh_inverse_warp64(
+    const double *__restrict__ gm, T *__restrict__ ginv, double *__restrict__ scal, int *__restrict__ status,
+    int n, int W, int check_drift, double drift_tol) {
+  extern __shared__ double sm[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int w = blockIdx.x * kRefreshWarps + warp;
+  if (w >= W) return;  // warp-uniform; no block-wide barrier below
+  const int ld = n + 1;
+  double *A = sm + (size_t)warp * (n * ld + n + n / 2 + 1);
+  double *f = A + n * ld;
+  int *perm = reinterpret_cast<int *>(f + n);
+  const double *G = gm + (size_t)w * n * n;
+  double gmax = 0.0;
+  for (int idx = lane; idx < n * n; idx += 32) {
+    const int i = idx / n, j = idx - i * n;
+    const double v = G[idx];
+    gmax = fmax(gmax, fabs(v));
+    A[i * ld + j] = v;
+  }
+  __syncwarp();
+  PivotProduct pp;
+  double sgn = 1.0;
+  bool ok = true;
+  const int j0 = lane, j1 = lane + 32;
+  for (int k = 0; k < n; ++k) {
+    double best = -1.0;
+    int bi = k;
+    for (int i = k + lane; i < n; i += 32) {
+      const double v = fabs(A[i * ld + k]);
+      if (v > best) {
+        best = v;
+        bi = i;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) {
+        best = ob;
+        bi = oi;
+      }
+    }
+    bi = __shfl_sync(0xffffffffu, bi, 0);
+    const double pv = A[bi * ld + k];
+    if (!(pv != 0.0) || !isfinite(pv)) {
+      ok = false;
+      break;
+    }
+    if (bi != k) {
+      for (int j = lane; j < n; j += 32) {
+        const double t = A[k * ld + j];
+        A[k * ld + j] = A[bi * ld + j];
+        A[bi * ld + j] = t;
+      }
+      sgn = -sgn;
+    }
+    if (lane == 0) perm[k] = bi;
+    pp.mul(pv);
+    if (pv < 0.0) sgn = -sgn;
+    __syncwarp();
+    const double ip = 1.0 / pv;
+    const double p0 = j0 < n ? (j0 == k ? ip : A[k * ld + j0] * ip) : 0.0;
+    const double p1 = j1 < n ? (j1 == k ? ip : A[k * ld + j1] * ip) : 0.0;
+    for (int i = lane; i < n; i += 32) f[i] = i == k ? 0.0 : A[i * ld + k];
+    __syncwarp();
+    for (int i = 0; i < n; ++i) {
+      double *Ai = A + i * ld;
+      if (i == k) {
+        if (j0 < n) Ai[j0] = p0;
+        if (j1 < n) Ai[j1] = p1;
+      } else {
+        const double fi = f[i];
+        if (j0 < n) Ai[j0] = j0 == k ? -fi * ip : fma(-fi, p0, Ai[j0]);
+        if (j1 < n) Ai[j1] = j1 == k ? -fi * ip : fma(-fi, p1, Ai[j1]);
+      }
+    }
+    __syncwarp();
+  }
+  T *gi = ginv + (size_t)w * n * n;
+  double *sw = scal + (size_t)w * S_STRIDE;
+  if (!ok) {
+    if (lane == 0) {
+      status[w] |= JAGP_WS_SINGULAR;
+      sw[S_LOGDET] = -INFINITY;
+      sw[S_SIGN] = 0.0;
+    }
+    return;
+  }
+  for (int k = n - 1; k >= 0; --k) {
+    const int p = perm[k];
+    if (p != k)
+      for (int i = lane; i < n; i += 32) {
+        const double t = A[i * ld + k];
+        A[i * ld + k] = A[i * ld + p];
+        A[i * ld + p] = t;
+      }
+    __syncwarp();
+  }
+  double dmax = 0.0;
+  for (int idx = lane; idx < n * n; idx += 32) {
+    const int i = idx / n, j = idx - i * n;
+    const double v = A[i * ld + j];
+    if (check_drift) dmax = fmax(dmax, fabs(v - static_cast<double>(gi[idx])));
+    gi[idx] = static_cast<T>(v);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+    gmax = fmax(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
+  }
+  if (lane == 0) {
+    sw[S_LOGDET] = pp.log_abs();
+    sw[S_SIGN] = sgn;
+    if (check_drift) {
+      const double drift = dmax * gmax;
+      sw[S_DRIFT] = drift;
+      if (!(drift <= drift_tol)) status[w] |= JAGP_WS_DRIFT;
+    }
+  }
+}
+
 template <typename T>
 cudaError_t launch_refresh_inverse(double *gm, T *ginv, double *scal, int *status, int n, int W,
                                    int check_drift, double drift_tol, cudaStream_t st) {
   if (W <= 0) return cudaSuccess;
   const size_t aux = (size_t)n * (2 * sizeof(double) + sizeof(int));
   const size_t inplace_smem = (size_t)n * (n + 1) * sizeof(double) + aux;
+  if (n > 32 && n <= 64) {
+    const size_t per = (size_t)(n * (n + 1) + n + n / 2 + 1) * sizeof(double);
+    k_refresh_inverse_warp64<T><<<(W + kRefreshWarps - 1) / kRefreshWarps, kRefreshWarps * 32, per * kRefreshWarps,
+                                  st>>>(gm, ginv, scal, status, n, W, check_drift, drift_tol);
+    return cudaGetLastError();
+  }
   if (n > 32 && inplace_smem <= kRefreshSmemMax) {
     k_refresh_inverse_inplace<T, true><<<W, 256, inplace_smem, st>>>(gm, ginv, scal, status, n, check_drift,
                                                                       drift_tol);
@@ -734,6 +866,8 @@ static cudaError_t linalg_attrs() {
   const int big = 200 * 1024;
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(k_refresh_inverse_warp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)))
+    return e;
+  if ((e = cudaFuncSetAttribute(k_refresh_inverse_warp64<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)))
     return e;
   if ((e = cudaFuncSetAttribute(k_refresh_inverse_inplace<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 big)))
