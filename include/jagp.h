@@ -204,7 +204,8 @@ jagp_status_t jagp_walker_status(jagp_handle_t h, const void *d_state, int W, in
  * the next sweep.  Synchronises `stream`.  out (host) receives the choices and
  * the best times (ms per call: proposals, refresh, A_up rows, Bt rows). */
 typedef struct {
-  int tile_proposals;  /* 0: one output per thread; 32 / 64: blocked tiles */
+  int tile_proposals;  /* 0: one output per thread; 32 / 64: blocked tiles; 16 (refresh, mixed,
+                          N_up <= 16): four walkers per CTA, 2x2 outputs per thread */
   int tile_refresh;
   int umma_bn_left;    /* mixed path: tensor-core tile width, A_up = phi^T lambda (0 in FP64) */
   int umma_bn_right;   /* mixed path: tensor-core tile width, Bt = lambda phi */

@@ -739,15 +739,17 @@ jagp_status_t tune_products(jagp_ctx *h, void *state, int W, cudaStream_t st, ja
   out->tile_proposals = h->tune_tile_prop;
   out->ms[0] = best;
   double *gm = refresh_g(L, state);
-  for (int c = 0; c < 3; ++c) {
+  const int rtiles[4] = {0, 32, 64, 16};  // 16: the four-walkers-per-CTA compensated kernel (FP32, N_up <= 16)
+  const int nref = (std::is_same<T, float>::value && n <= 16) ? 4 : 3;
+  for (int c = 0; c < nref; ++c) {
     float ms = 0.0f;
     JAGP_CU(time_calls([&] { return refresh_geminal(phi, lo_table(h, state, L.phi_lo), (size_t)n * Lb, bt,
                                                     lo_table(h, state, L.bt_lo), (size_t)n * Lb, n, Lb, gm, W, st,
-                                                    tiles[c]); },
+                                                    rtiles[c]); },
                        st, &ms));
     if (c == 0 || ms < best) {
       best = ms;
-      h->tune_tile_refresh = tiles[c];
+      h->tune_tile_refresh = rtiles[c];
     }
   }
   out->tile_refresh = h->tune_tile_refresh;

@@ -200,12 +200,79 @@ inline int gemm_rows_tile(int ma, int nb) {
   return m >= 64 ? 64 : (m >= 32 ? 32 : 0);
 }
 
+// The compensated product for small blocks (ma, nb <= 16): four walkers per
+// CTA, 64 threads each with a 2 x 2 output block, so that every shared-memory
+// operand read serves two outputs instead of one; k order as above.
+__global__ void __launch_bounds__(256) k_gemm_rows_dot2_small(const float *__restrict__ X,
+                                                              const float *__restrict__ Xlo, size_t xw,
+                                                              const float *__restrict__ Y,
+                                                              const float *__restrict__ Ylo, size_t yw, int ma,
+                                                              int nb, int K, double *__restrict__ Out, size_t ow,
+                                                              int ldo, int W) {
+  constexpr int KC = 32;
+  __shared__ float Xs[4][KC][17], Xl[4][KC][17], Ys[4][KC][17], Yl[4][KC][17];
+  const int sub = threadIdx.x >> 6, t = threadIdx.x & 63;
+  const int w = blockIdx.x * 4 + sub;
+  const bool active = w < W;  // inactive groups still take part in the barriers
+  const int tx = t & 7, ty = t >> 3;  // outputs (2 ty + i, 2 tx + j)
+  float s[2][2] = {{0.0f, 0.0f}, {0.0f, 0.0f}}, c[2][2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
+  for (int k0 = 0; k0 < K; k0 += KC) {
+    for (int idx = t; idx < 16 * KC; idx += 64) {
+      const int row = idx / KC, kk = idx % KC, k = k0 + kk;
+      const bool xa = active && row < ma && k < K, yb = active && row < nb && k < K;
+      const size_t xi = (size_t)w * xw + (size_t)row * K + k, yi = (size_t)w * yw + (size_t)row * K + k;
+      Xs[sub][kk][row] = xa ? X[xi] : 0.0f;
+      Xl[sub][kk][row] = (Xlo && xa) ? Xlo[xi] : 0.0f;
+      Ys[sub][kk][row] = yb ? Y[yi] : 0.0f;
+      Yl[sub][kk][row] = (Ylo && yb) ? Ylo[yi] : 0.0f;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < KC; ++kk) {
+      const float x0 = Xs[sub][kk][2 * ty], x1 = Xs[sub][kk][2 * ty + 1];
+      const float l0 = Xl[sub][kk][2 * ty], l1 = Xl[sub][kk][2 * ty + 1];
+      const float y0 = Ys[sub][kk][2 * tx], y1 = Ys[sub][kk][2 * tx + 1];
+      const float m0 = Yl[sub][kk][2 * tx], m1 = Yl[sub][kk][2 * tx + 1];
+      const float xv[2] = {x0, x1}, xl[2] = {l0, l1}, yv[2] = {y0, y1}, yl[2] = {m0, m1};
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          const float x = xv[i], y = yv[j], sv = s[i][j];
+          const float p = __fmul_rn(x, y);
+          const float pe = __fmaf_rn(x, y, -p);
+          const float tt = __fadd_rn(sv, p);
+          const float z = __fsub_rn(tt, sv);
+          const float se = __fadd_rn(__fsub_rn(sv, __fsub_rn(tt, z)), __fsub_rn(p, z));
+          s[i][j] = tt;
+          const float cross = __fmaf_rn(xl[i], y, __fmul_rn(x, yl[j]));
+          c[i][j] = __fadd_rn(c[i][j], __fadd_rn(__fadd_rn(cross, pe), se));
+        }
+    }
+    __syncthreads();
+  }
+  if (!active) return;
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int a = 2 * ty + i, b = 2 * tx + j;
+      if (a < ma && b < nb)
+        Out[(size_t)w * ow + (size_t)a * ldo + b] = static_cast<double>(s[i][j]) + static_cast<double>(c[i][j]);
+    }
+}
+
 cudaError_t launch_gemm_rows_dot2(const float *X, const float *Xlo, size_t xw, const float *Y, const float *Ylo,
                                   size_t yw, int ma, int nb, int K, double *Out, size_t ow, int ldo, int W,
                                   cudaStream_t st, int tile) {
   if (W <= 0 || ma <= 0 || nb <= 0) return cudaSuccess;
-  if (tile != -1 && tile != 0 && tile != 32 && tile != 64) return cudaErrorInvalidValue;
-  const int tm = tile >= 0 ? tile : gemm_rows_tile(ma, nb);
+  if (tile != -1 && tile != 0 && tile != 16 && tile != 32 && tile != 64) return cudaErrorInvalidValue;
+  const int tm = tile >= 0 ? tile : (ma <= 16 && nb <= 16 ? 16 : gemm_rows_tile(ma, nb));
+  if (tm == 16) {
+    if (ma > 16 || nb > 16) return cudaErrorInvalidValue;
+    k_gemm_rows_dot2_small<<<(W + 3) / 4, 256, 0, st>>>(X, Xlo, xw, Y, Ylo, yw, ma, nb, K, Out, ow, ldo, W);
+    return cudaGetLastError();
+  }
   if (tm) {
     dim3 grid((nb + tm - 1) / tm, (ma + tm - 1) / tm, W);
     if (tm == 64)
@@ -290,6 +357,18 @@ cudaError_t launch_fill_unpaired_lo(const DevSystem &s, float *lo, int W, cudaSt
   return cudaGetLastError();
 }
 template cudaError_t launch_fill_unpaired<float>(const DevSystem &, float *, int, cudaStream_t);
+
+// 1/p in FP64 from an FP32 seed and two Newton steps y <- y (2 - p y) (error
+// squares each step: 2^-23 -> 2^-46 -> below FP64 rounding); p must be a
+// normal number within FP32 range, else the FP64 division is used.
+__device__ __forceinline__ double recip_newton(double p) {
+  const double a = fabs(p);
+  if (!(a > 1e-37 && a < 1e37)) return 1.0 / p;
+  double y = static_cast<double>(__frcp_rn(static_cast<float>(p)));
+  y = y * fma(-p, y, 2.0);
+  y = y * fma(-p, y, 2.0);
+  return y;
+}
 
 // log|prod of pivots| without a logarithm per pivot: the product is kept as a
 // mantissa in [1/2, 1) and a binary exponent (frexp after every factor), and
@@ -382,7 +461,7 @@ __global__ void __launch_bounds__(kRefreshWarps * 32) k_refresh_inverse_warp(
     pp.mul(pv);
     if (pv < 0.0) sgn = -sgn;
     __syncwarp();
-    const double ip = 1.0 / pv;
+    const double ip = recip_newton(pv);
     for (int j = lane; j < n2; j += 32) A[k * ld + j] *= ip;
     for (int i = lane; i < n; i += 32) f[i] = A[i * ld + k];
     __syncwarp();
@@ -507,7 +586,7 @@ __global__ void __launch_bounds__(512) k_refresh_inverse_inplace(double *__restr
     if (pv < 0.0) sgn = -sgn;
     if (tid == 0) perm[k] = p;
     __syncthreads();
-    const double ip = 1.0 / pv;
+    const double ip = recip_newton(pv);
     for (int j = tid; j < n; j += bs) prow[j] = j == k ? ip : A[(size_t)k * ld + j] * ip;
     for (int i = tid; i < n; i += bs) f[i] = i == k ? 0.0 : A[(size_t)i * ld + k];
     __syncthreads();
@@ -637,7 +716,7 @@ __global__ void __launch_bounds__(kRefreshWarps * 32) k_refresh_inverse_warp64(
     pp.mul(pv);
     if (pv < 0.0) sgn = -sgn;
     __syncwarp();
-    const double ip = 1.0 / pv;
+    const double ip = recip_newton(pv);
     const double p0 = j0 < n ? (j0 == k ? ip : A[k * ld + j0] * ip) : 0.0;
     const double p1 = j1 < n ? (j1 == k ? ip : A[k * ld + j1] * ip) : 0.0;
     for (int i = lane; i < n; i += 32) f[i] = i == k ? 0.0 : A[i * ld + k];

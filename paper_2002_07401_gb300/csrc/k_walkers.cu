@@ -175,6 +175,8 @@ __device__ __forceinline__ void block_sum2(double &a, double &b, double *red) {
 // a down electron replaces column m, with the transposed formulas.  The
 // Jastrow factor contributes exp(2 dJ), dJ summed over the atoms (J1) and the
 // other electrons at their current positions (J2).  Accept iff u < R^2 e^{2 dJ}.
+// log|det| is not tracked move by move: the refresh that ends every
+// half-sweep or sweep recomputes it from the tables.
 // ---------------------------------------------------------------------------
 template <bool UP, typename T, bool GLOB>
 __global__ void __launch_bounds__(512) k_metropolis(DevSystem s, double *__restrict__ r,
@@ -205,10 +207,9 @@ __global__ void __launch_bounds__(512) k_metropolis(DevSystem s, double *__restr
   if (!GLOB)
     for (int t = tid; t < n * n; t += bs) Gi[t] = gw[t];
   for (int t = tid; t < N * 3; t += bs) xs[t] = r[(size_t)w * N * 3 + t];
-  double logdet = 0.0, sgn = 1.0, J = 0.0, nacc = 0.0;
+  double sgn = 1.0, J = 0.0, nacc = 0.0;
   int st_bits = 0;
   if (tid == 0) {
-    logdet = scal[(size_t)w * S_STRIDE + S_LOGDET];
     sgn = scal[(size_t)w * S_STRIDE + S_SIGN];
     J = scal[(size_t)w * S_STRIDE + S_J];
     nacc = scal[(size_t)w * S_STRIDE + S_NACC];
@@ -239,7 +240,6 @@ __global__ void __launch_bounds__(512) k_metropolis(DevSystem s, double *__restr
         st_bits |= JAGP_WS_NONFINITE;
       } else if (pr != 0.0 && u < p) {
         acc = 1;
-        logdet += log(fabs(pr));
         if (pr < 0.0) sgn = -sgn;
         J += pj;
         nacc += 1.0;
@@ -301,7 +301,6 @@ __global__ void __launch_bounds__(512) k_metropolis(DevSystem s, double *__restr
     for (int t = tid; t < n * n; t += bs) gw[t] = Gi[t];
   for (int t = tid; t < N * 3; t += bs) r[(size_t)w * N * 3 + t] = xs[t];
   if (tid == 0) {
-    scal[(size_t)w * S_STRIDE + S_LOGDET] = logdet;
     scal[(size_t)w * S_STRIDE + S_SIGN] = sgn;
     scal[(size_t)w * S_STRIDE + S_J] = J;
     scal[(size_t)w * S_STRIDE + S_NACC] = nacc;
@@ -342,7 +341,7 @@ __global__ void __launch_bounds__(kMetroWarps * 32) k_metropolis_warp(
   for (int t = lane; t < n * n; t += 32) Gi[t] = gw[t];
   for (int t = lane; t < N * 3; t += 32) xs[t] = r[(size_t)w * N * 3 + t];
   double *sw = scal + (size_t)w * S_STRIDE;
-  double logdet = sw[S_LOGDET], sgn = sw[S_SIGN], J = sw[S_J], nacc = sw[S_NACC];
+  double sgn = sw[S_SIGN], J = sw[S_J], nacc = sw[S_NACC];
   int st_bits = status[w];
   const int nmoves = m_end < (UP ? s.n_up : s.n_dn) ? m_end : (UP ? s.n_up : s.n_dn);
   const int e0 = UP ? 0 : s.n_up;
@@ -374,7 +373,6 @@ __global__ void __launch_bounds__(kMetroWarps * 32) k_metropolis_warp(
     }
     __syncwarp();
     if (acc) {
-      logdet += log(fabs(pr));
       if (pr < 0.0) sgn = -sgn;
       J += pj;
       nacc += 1.0;
@@ -415,7 +413,6 @@ __global__ void __launch_bounds__(kMetroWarps * 32) k_metropolis_warp(
   for (int t = lane; t < n * n; t += 32) gw[t] = Gi[t];
   for (int t = lane; t < N * 3; t += 32) r[(size_t)w * N * 3 + t] = xs[t];
   if (lane == 0) {
-    sw[S_LOGDET] = logdet;
     sw[S_SIGN] = sgn;
     sw[S_J] = J;
     sw[S_NACC] = nacc;
