@@ -25,6 +25,7 @@ import math
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -74,7 +75,9 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        # raw samples go to $JAGP_CLOCK_LOG_DIR (default: the temporary directory)
+        log_dir = os.environ.get("JAGP_CLOCK_LOG_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(log_dir, f"jagp_clocks_rank{gpu_index}.csv")
 
     def __enter__(self):
         try:
