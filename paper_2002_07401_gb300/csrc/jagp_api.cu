@@ -766,13 +766,15 @@ jagp_status_t tune_products(jagp_ctx *h, void *state, int W, cudaStream_t st, ja
   const int np64 = slice_pairs(h->tc_slices, pa64, pb64);
   for (int side = 0; side < 2; ++side) {
     const bool left = side == 0;
-    const int cands[6] = {32, 48, 64, 80, 96, 128};
-    const int stages[2] = {0, 3};  // as many as fit (one CTA per SM), or three (several CTAs per SM)
+    // tile widths; 16 lets four CTAs share an SM's tensor memory (5 x 16 columns each)
+    const int cands[7] = {16, 32, 48, 64, 80, 96, 128};
+    // stages: as many as fit (one CTA per SM), three or two (several CTAs per SM)
+    const int stages[3] = {0, 3, 2};
     const int limit = f64 ? 64 : (left ? 128 : 96);
     float bs = 0.0f;
     int bbn = 0, bst = 0;
-    for (int c = 0; c < 6; ++c)
-      for (int q = 0; q < 2; ++q) {
+    for (int c = 0; c < 7; ++c)
+      for (int q = 0; q < 3; ++q) {
         if (cands[c] > limit) continue;
         float ms = 0.0f;
         JAGP_CU(time_calls(

@@ -42,12 +42,12 @@ def test_autotune_changes_no_result(torch_cuda, name, mode):
             t = g.autotune()
             assert t["tile_proposals"] in (0, 32, 64) and t["tile_refresh"] in (0, 16, 32, 64)
             if mixed:
-                assert t["umma_bn_left"] in (32, 48, 64, 80, 96, 128)
-                assert t["umma_bn_right"] in (32, 48, 64, 80, 96)
-                assert t["umma_stages_left"] in (0, 3) and t["umma_stages_right"] in (0, 3)
+                assert t["umma_bn_left"] in (16, 32, 48, 64, 80, 96, 128)
+                assert t["umma_bn_right"] in (16, 32, 48, 64, 80, 96)
+                assert t["umma_stages_left"] in (0, 2, 3) and t["umma_stages_right"] in (0, 2, 3)
                 assert all(m > 0 for m in t["ms"])
             elif mode == "fp64tc":
-                assert t["umma_bn_left"] in (32, 48, 64) and t["umma_bn_right"] in (32, 48, 64)
+                assert t["umma_bn_left"] in (16, 32, 48, 64) and t["umma_bn_right"] in (16, 32, 48, 64)
                 assert all(m > 0 for m in t["ms"])
             else:
                 assert t["umma_bn_left"] == t["umma_bn_right"] == 0
