@@ -34,6 +34,7 @@ namespace jagp {
 namespace {
 
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s per wait
+constexpr int kGroupM = 8;                         // row tiles per group of the tile order
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -156,12 +157,26 @@ __global__ void __launch_bounds__(128) k_umma_gemm(const __grid_constant__ CUten
   const int M = g.m_dev ? *g.m_dev : g.m_max;
   // batched mode: tile t of batch b starts at row b * batch_rows + 128 t; rows
   // past the batch's end (read from the next batch) are computed but not written
-  const int bb = g.batch_rows ? (int)blockIdx.y / g.tiles_per_batch : 0;
-  const int bt0 = g.batch_rows ? ((int)blockIdx.y - bb * g.tiles_per_batch) * 128 : 0;
-  const int m0 = g.batch_rows ? bb * g.batch_rows + bt0 : (int)blockIdx.y * 128;
+  // grouped tile order: CTAs in launch order walk kGroupM row tiles of one
+  // column tile before the next column tile, so that a wave reuses both A and
+  // B tiles from L2 (with large K the operands exceed L2)
+  int tile_y, tile_x;
+  {
+    const int tiles_n = gridDim.x, tiles_m = gridDim.y;
+    const int pid = blockIdx.x + blockIdx.y * tiles_n;
+    const int span = kGroupM * tiles_n;
+    const int first = (pid / span) * kGroupM;
+    const int gsize = tiles_m - first < kGroupM ? tiles_m - first : kGroupM;
+    const int r = pid - (pid / span) * span;
+    tile_y = first + r % gsize;
+    tile_x = r / gsize;
+  }
+  const int bb = g.batch_rows ? tile_y / g.tiles_per_batch : 0;
+  const int bt0 = g.batch_rows ? (tile_y - bb * g.tiles_per_batch) * 128 : 0;
+  const int m0 = g.batch_rows ? bb * g.batch_rows + bt0 : tile_y * 128;
   const int bbase = bb * g.batch_rows;  // first B row (and column exponent) of this batch
   if (m0 >= M) return;  // whole CTA, before any barrier or tensor-memory use
-  const int n0 = blockIdx.x * g.bn;
+  const int n0 = tile_x * g.bn;
   const uint32_t a_bytes = 128u * 128u;
   const uint32_t b_bytes = static_cast<uint32_t>(g.bn) * 128u;
   const uint32_t stage_bytes = a_bytes + b_bytes;
