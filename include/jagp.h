@@ -210,10 +210,23 @@ typedef struct {
   int umma_bn_left;    /* mixed path: tensor-core tile width, A_up = phi^T lambda (0 in FP64) */
   int umma_bn_right;   /* mixed path: tensor-core tile width, Bt = lambda phi */
   float ms[4];
-  int umma_stages_left;   /* pipeline stages of those products (0: as many as fit in 200 KB) */
+  int umma_stages_left;   /* pipeline stages of those products (0: as many as fit in 200 KB;
+                             -1: chunk-major, two stages each holding every slice of one
+                             64-wide K chunk, so that a slice is read once for all its pairs) */
   int umma_stages_right;
 } jagp_tuning_t;
 jagp_status_t jagp_autotune(jagp_handle_t h, void *d_state, int W, jagp_tuning_t *out, void *stream);
+/* Pin the tile choices of a handle without timing (e.g. those an earlier
+ * jagp_autotune returned for the same system and walker count).  Host-only, no
+ * CUDA call; ms is ignored.  tile_proposals / tile_refresh: -1 (the shape
+ * heuristics), 0, 32 or 64, and 16 for tile_refresh in the mixed path with
+ * N_up <= 16.  umma_*: 0 without tensor-core lambda products (FP64 without
+ * fp64_tensor_cores); else bn 0 (heuristic) or a multiple of 16 up to 128 (A_up
+ * rows) / 96 (Bt rows) in the mixed path, 64 in the FP64 one, and stages -1
+ * (chunk-major, only where two such stages fit in shared memory), 0 or 2..6.
+ * Every choice changes the tiling only, so results stay as without tuning.
+ * Returns JAGP_ERR_INVALID_ARG (and keeps the earlier choices) on any other value. */
+jagp_status_t jagp_set_tuning(jagp_handle_t h, const jagp_tuning_t *t);
 
 /* The tensor-core contraction behind the lambda products of the mixed
  * precision path (Sec. AGP, Eq. agp_expansion: rows phi^T lambda and

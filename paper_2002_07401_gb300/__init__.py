@@ -92,6 +92,8 @@ def lib():
         L.jagp_batch_destroy.restype = i
         L.jagp_autotune.argtypes = [vp, vp, i, C.POINTER(_Tuning), vp]
         L.jagp_autotune.restype = i
+        L.jagp_set_tuning.argtypes = [vp, C.POINTER(_Tuning)]
+        L.jagp_set_tuning.restype = i
         L.jagp_eval_noalloc.argtypes = [vp, vp, i, vp, vp, vp]
         L.jagp_eval_noalloc.restype = i
         L.jagp_last_cuda_error.argtypes = []
@@ -276,6 +278,16 @@ def jagp_autotune(h, state, W, stream=None) -> dict:
             "umma_stages_right": t.umma_stages_right, "ms": [float(v) for v in t.ms]}
 
 
+def jagp_set_tuning(h, tuning: dict) -> None:
+    """Pin tile choices (keys as jagp_autotune returns; see include/jagp.h)."""
+    t = _Tuning()
+    t.tile_proposals = int(tuning.get("tile_proposals", -1))
+    t.tile_refresh = int(tuning.get("tile_refresh", -1))
+    for k in ("umma_bn_left", "umma_bn_right", "umma_stages_left", "umma_stages_right"):
+        setattr(t, k, int(tuning.get(k, 0)))
+    _check(lib().jagp_set_tuning(h, C.byref(t)), "jagp_set_tuning")
+
+
 class JAGP:
     """One system on the current CUDA device with state for up to W walkers."""
 
@@ -316,6 +328,9 @@ class JAGP:
         if r is not None:
             self.eval(r)
         return out
+
+    def set_tuning(self, tuning):
+        jagp_set_tuning(self.h, tuning)
 
     def eval(self, r):
         import torch

@@ -768,14 +768,19 @@ jagp_status_t tune_products(jagp_ctx *h, void *state, int W, cudaStream_t st, ja
     const bool left = side == 0;
     // tile widths; 16 lets four CTAs share an SM's tensor memory (5 x 16 columns each)
     const int cands[7] = {16, 32, 48, 64, 80, 96, 128};
-    // stages: as many as fit (one CTA per SM), three or two (several CTAs per SM)
-    const int stages[3] = {0, 3, 2};
+    // stages: as many as fit (one CTA per SM), three or two (several CTAs per SM),
+    // or chunk-major (-1: every slice of a K chunk per stage, each loaded once
+    // for all pairs; two stages, where they fit)
+    const int stages[4] = {0, 3, 2, -1};
+    const int npairs = f64 ? np64 : (left ? kFixedPairsF32 : kFixedPairs);
+    const int *tpa = f64 ? pa64 : kPairA, *tpb = f64 ? pb64 : kPairB;
     const int limit = f64 ? 64 : (left ? 128 : 96);
     float bs = 0.0f;
     int bbn = 0, bst = 0;
     for (int c = 0; c < 7; ++c)
-      for (int q = 0; q < 3; ++q) {
+      for (int q = 0; q < 4; ++q) {
         if (cands[c] > limit) continue;
+        if (stages[q] < 0 && !umma_chunk_fits(npairs, tpa, tpb, cands[c])) continue;
         float ms = 0.0f;
         JAGP_CU(time_calls(
             [&] {
@@ -829,6 +834,38 @@ jagp_status_t jagp_autotune(jagp_handle_t h, void *d_state, int W, jagp_tuning_t
                                       : tune_products<double>(h, d_state, W, st, out);
   if (s != JAGP_OK) return s;
   JAGP_CU(cudaStreamSynchronize(st));
+  return JAGP_OK;
+}
+
+jagp_status_t jagp_set_tuning(jagp_handle_t h, const jagp_tuning_t *t) {
+  if (!h || !t) return JAGP_ERR_INVALID_ARG;
+  const bool mixed = h->precision == JAGP_PREC_MIXED;
+  auto tile_ok = [](int v, bool allow16) { return v == -1 || v == 0 || v == 32 || v == 64 || (allow16 && v == 16); };
+  if (!tile_ok(t->tile_proposals, false) || !tile_ok(t->tile_refresh, mixed && h->ds.n_up <= 16))
+    return JAGP_ERR_INVALID_ARG;
+  const int bn[2] = {t->umma_bn_left, t->umma_bn_right}, stg[2] = {t->umma_stages_left, t->umma_stages_right};
+  if (!h->tc_lambda) {
+    if (bn[0] || bn[1] || stg[0] || stg[1]) return JAGP_ERR_INVALID_ARG;
+  } else {
+    int pa64[kMaxPairs], pb64[kMaxPairs];
+    const int np64 = slice_pairs(h->tc_slices, pa64, pb64);
+    for (int side = 0; side < 2; ++side) {
+      const bool left = side == 0;
+      const int limit = mixed ? (left ? 128 : 96) : 64;
+      if (bn[side] < 0 || bn[side] % 16 || bn[side] > limit) return JAGP_ERR_INVALID_ARG;
+      if (stg[side] < -1 || stg[side] == 1 || stg[side] > 6) return JAGP_ERR_INVALID_ARG;
+      const int npairs = mixed ? (left ? kFixedPairsF32 : kFixedPairs) : np64;
+      const int actual = umma_pick_bn(h->ds.L, bn[side] ? bn[side] : limit);
+      if (stg[side] == -1 && !umma_chunk_fits(npairs, mixed ? kPairA : pa64, mixed ? kPairB : pb64, actual))
+        return JAGP_ERR_INVALID_ARG;
+    }
+  }
+  h->tune_tile_prop = t->tile_proposals;
+  h->tune_tile_refresh = t->tile_refresh;
+  h->tune_bn_left = bn[0];
+  h->tune_bn_right = bn[1];
+  h->tune_st_left = stg[0];
+  h->tune_st_right = stg[1];
   return JAGP_OK;
 }
 

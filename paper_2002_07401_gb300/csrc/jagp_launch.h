@@ -95,6 +95,7 @@ cudaError_t launch_increment(uint32_t *c, uint32_t by, cudaStream_t st);
 // aligned bases); rows m < *m_dev (or m_max) are written; out FP32, pitch ldo.
 // With a_exp/b_exp (row / column exponents) the terms are fixed-point slices and
 // pairs of equal a + b share an exact accumulator (see k_umma.cu).
+// stages_max: pipeline depth (0: as many as fit); -1: chunk-major stages.
 int umma_pick_bn(int n, int max_bn);
 cudaError_t launch_umma_gemm(const uint16_t *A, int m_max, const int *m_dev, int a_terms, const uint16_t *B, int n,
                              int b_terms, int kp, int npairs, const int *pair_a, const int *pair_b, float *out,
@@ -102,6 +103,8 @@ cudaError_t launch_umma_gemm(const uint16_t *A, int m_max, const int *m_dev, int
                              const int *a_exp = nullptr, const int *b_exp = nullptr, float *out_lo = nullptr,
                              int bn_max = 0, double *out64 = nullptr, int slice_bits = 8, int batch_rows = 0,
                              int batches = 0, int stages_max = 0);
+// whether two chunk-major stages (stages_max = -1) of these pairs fit at tile width bn
+bool umma_chunk_fits(int npairs, const int *pair_a, const int *pair_b, int bn);
 // FP64 rows -> nsl exact slices of `bits` bits per element plus a row exponent
 cudaError_t launch_pack_fixed64(const double *P, const int *list, const int *count, int nrows, int nsub, int stride,
                                 int L, int kp, int nsl, int bits, uint16_t *A, int *rows_out, int *exps,

@@ -139,6 +139,8 @@ struct UmmaArgs {
   int batch_rows;        // batched mode (> 0): A and B are stacked per-batch blocks of batch_rows
                          // rows; batch b's rows of A meet only batch b's rows of B
   int tiles_per_batch;   // batched mode: 128-row tiles per batch
+  int chunk_major;       // 1: one stage holds every slice of one 64-wide K chunk of A (na) and B (nb),
+  int na, nb;            //    and the MMA thread issues all pairs from it (slices loaded once per chunk)
   const int *a_exp;      // fixed-point mode: row exponents [m_max], else null
   const int *b_exp;      // fixed-point mode: column exponents [n]
   uint32_t idesc;
@@ -179,7 +181,8 @@ __global__ void __launch_bounds__(128) k_umma_gemm(const __grid_constant__ CUten
   const int n0 = tile_x * g.bn;
   const uint32_t a_bytes = 128u * 128u;
   const uint32_t b_bytes = static_cast<uint32_t>(g.bn) * 128u;
-  const uint32_t stage_bytes = a_bytes + b_bytes;
+  const uint32_t stage_bytes =
+      g.chunk_major ? static_cast<uint32_t>(g.na) * a_bytes + static_cast<uint32_t>(g.nb) * b_bytes : a_bytes + b_bytes;
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + g.stages * stage_bytes);
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * g.stages + 1);
   const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8u * g.stages, done = full0 + 16u * g.stages;
@@ -203,10 +206,51 @@ __global__ void __launch_bounds__(128) k_umma_gemm(const __grid_constant__ CUten
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   const int kchunks = g.kp / 64;
-  const int iters = g.npairs * kchunks;
+  const int iters = g.chunk_major ? kchunks : g.npairs * kchunks;
   const uint32_t tiles = smem_u32(smem);
 
-  if (warp == 0 && lane == 0) {
+  if (warp == 0 && lane == 0 && g.chunk_major) {
+    // producer, chunk-major: every slice of A and B for one K chunk per stage
+    for (int it = 0; it < iters; ++it) {
+      const int s = it % g.stages;
+      const uint32_t use = static_cast<uint32_t>(it / g.stages);
+      if (it >= g.stages && !mbar_wait(empty0 + 8u * s, (use & 1u) ^ 1u)) {
+        atomicExch(g.err, 1);
+        break;
+      }
+      const uint32_t full = full0 + 8u * s, base = tiles + s * stage_bytes;
+      mbar_expect_tx(full, stage_bytes);
+      for (int a = 0; a < g.na; ++a) tma_load_2d(base + a * a_bytes, &tmA, a * g.kp + it * 64, m0, full);
+      for (int b = 0; b < g.nb; ++b)
+        tma_load_2d(base + g.na * a_bytes + b * b_bytes, &tmB, b * g.kp + it * 64, bbase + n0, full);
+    }
+  } else if (warp == 1 && lane == 0 && g.chunk_major) {
+    // MMA issuer, chunk-major: all pairs of the chunk from the one stage
+    uint32_t started = 0;
+    for (int it = 0; it < iters; ++it) {
+      const int s = it % g.stages;
+      const uint32_t use = static_cast<uint32_t>(it / g.stages);
+      if (!mbar_wait(full0 + 8u * s, use & 1u)) {
+        atomicExch(g.err, 2);
+        break;
+      }
+      tc_fence_after();
+      const uint32_t base = tiles + s * stage_bytes;
+      for (int p = 0; p < g.npairs; ++p) {
+        const int grp = g.pair_group[p];
+        const uint32_t a0 = base + g.pair_a[p] * a_bytes, b0 = base + g.na * a_bytes + g.pair_b[p] * b_bytes;
+        const uint32_t d_tmem = tmem + static_cast<uint32_t>(grp * g.bn);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          umma_bf16(d_tmem, desc_sw128_kmajor(a0 + kk * 32), desc_sw128_kmajor(b0 + kk * 32), g.idesc,
+                    (started >> grp) & 1u);
+          started |= 1u << grp;
+        }
+      }
+      umma_commit(empty0 + 8u * s);
+    }
+    umma_commit(done);
+  } else if (warp == 0 && lane == 0) {
     // producer: one A tile (128 x 64) and one B tile (bn x 64) per stage
     for (int it = 0; it < iters; ++it) {
       const int s = it % g.stages;
@@ -377,6 +421,25 @@ int umma_pick_bn(int n, int max_bn) {
   return (((n + tiles - 1) / tiles) + 15) / 16 * 16;
 }
 
+namespace {
+int g_smem_optin = 220 * 1024;  // the kernel's dynamic shared-memory limit, set once per process
+
+uint32_t chunk_stage_bytes(int na, int nb, int bn) {
+  return static_cast<uint32_t>(na) * 128u * 128u + static_cast<uint32_t>(nb * bn) * 128u;
+}
+// room for the stages: the limit less the 1 KB alignment slack and the barriers
+uint32_t chunk_budget() { return static_cast<uint32_t>(g_smem_optin - 1024 - 64); }
+}  // namespace
+
+bool umma_chunk_fits(int npairs, const int *pair_a, const int *pair_b, int bn) {
+  int na = 0, nb = 0;
+  for (int p = 0; p < npairs; ++p) {
+    na = pair_a[p] + 1 > na ? pair_a[p] + 1 : na;
+    nb = pair_b[p] + 1 > nb ? pair_b[p] + 1 : nb;
+  }
+  return 2u * chunk_stage_bytes(na, nb, bn) <= chunk_budget();
+}
+
 cudaError_t launch_umma_gemm(const uint16_t *A, int m_max, const int *m_dev, int a_terms, const uint16_t *B, int n,
                              int b_terms, int kp, int npairs, const int *pair_a, const int *pair_b, float *out,
                              long long ldo, const int *out_rows, int *err, cudaStream_t st, const int *a_exp,
@@ -417,12 +480,26 @@ cudaError_t launch_umma_gemm(const uint16_t *A, int m_max, const int *m_dev, int
     limit = bn_max < limit ? bn_max : limit;
   }
   g.bn = umma_pick_bn(n, limit);
-  const uint32_t stage_bytes = 128u * 128u + static_cast<uint32_t>(g.bn) * 128u;
-  // pipeline depth: as many stages as fit in 200 KB, at most 6, or fewer
-  // (stages_max, from the autotuner) so that several CTAs share an SM
-  g.stages = static_cast<int>((200u * 1024u) / stage_bytes);
-  if (g.stages > 6) g.stages = 6;
-  if (stages_max > 0 && stages_max < g.stages) g.stages = stages_max < 2 ? 2 : stages_max;
+  g.na = g.nb = 0;
+  for (int p = 0; p < npairs; ++p) {
+    g.na = pair_a[p] + 1 > g.na ? pair_a[p] + 1 : g.na;
+    g.nb = pair_b[p] + 1 > g.nb ? pair_b[p] + 1 : g.nb;
+  }
+  uint32_t stage_bytes = 128u * 128u + static_cast<uint32_t>(g.bn) * 128u;
+  if (stages_max < -1) return cudaErrorInvalidValue;
+  // stages_max = -1: chunk-major, two stages of every slice of a 64-wide K chunk
+  g.chunk_major = stages_max == -1 ? 1 : 0;
+  if (g.chunk_major) {
+    stage_bytes = chunk_stage_bytes(g.na, g.nb, g.bn);
+    if (2u * stage_bytes > chunk_budget()) return cudaErrorInvalidValue;
+    g.stages = 2;
+  } else {
+    // pipeline depth: as many stages as fit in 200 KB, at most 6, or fewer
+    // (stages_max, from the autotuner) so that several CTAs share an SM
+    g.stages = static_cast<int>((200u * 1024u) / stage_bytes);
+    if (g.stages > 6) g.stages = 6;
+    if (stages_max > 0 && stages_max < g.stages) g.stages = stages_max < 2 ? 2 : stages_max;
+  }
   g.npairs = npairs;
   g.idesc = (1u << 4)                                   // D: FP32
             | (1u << 7) | (1u << 10)                    // A, B: BF16
@@ -596,7 +673,14 @@ cudaError_t launch_pack_fixed64(const double *P, const int *list, const int *cou
 }
 
 cudaError_t setup_umma_attributes() {
-  return cudaFuncSetAttribute(k_umma_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  // the largest opt-in shared memory per block (227 KB on this part), so that
+  // two chunk-major stages of five slices fit
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  g_smem_optin = optin < 220 * 1024 ? 220 * 1024 : optin;
+  return cudaFuncSetAttribute(k_umma_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, g_smem_optin);
 }
 
 }  // namespace jagp

@@ -162,3 +162,27 @@ def test_c5_mixed_full_size_sampled(torch_cuda):
     assert np.max(np.abs(la - la_ref)) <= MIXED_C5_TOL[0], np.abs(la - la_ref)
     assert np.max(np.abs(e - e_ref)) <= MIXED_C5_TOL[1], np.abs(e - e_ref)
     g.close()
+
+
+def test_c5_mixed_chunk_major_matches_default(torch_cuda):
+    """The 512-electron system (K = 4096): the chunk-major tensor-core stages
+    (every slice of a K chunk loaded once for all pairs) give the same log|Psi|,
+    trajectory and e_L as the default slice-by-slice stages."""
+    import paper_2002_07401_gb300 as pg
+    sysm = synth.config5()
+    W = 48
+    x0 = synth.init_walkers(sysm, W, seed=2)
+    runs = []
+    for tuning in (None, {"umma_bn_left": 96, "umma_bn_right": 48, "umma_stages_left": -1,
+                          "umma_stages_right": -1}):
+        g = pg.JAGP(sysm, W, precision=pg.JAGP_PREC_MIXED, seed=4)
+        if tuning:
+            g.set_tuning(tuning)
+        r = g.positions(x0)
+        la, _ = g.eval(r)
+        eL, _ = g.sweep(r, 1)
+        assert g.status() & (pg.WS_NONFINITE | pg.WS_SINGULAR) == 0
+        runs.append([la.cpu().numpy(), r.cpu().numpy(), eL.cpu().numpy(), g.info()["logabs"].cpu().numpy()])
+        g.close()
+    for a, b in zip(*runs):
+        assert np.array_equal(a, b)
