@@ -510,33 +510,31 @@ __global__ void __launch_bounds__(kRefreshWarps * 32) k_refresh_inverse_warp(
 // -f_i / p in column k and updates the rest, so the inverse takes the place of
 // G~ (half the work of eliminating [G~ | I]); the row swaps of the partial
 // pivoting become column swaps of the result, undone in reverse order at the
-// end.  SMEM: the matrix is copied to shared memory (row pitch n + 1); else it
-// is overwritten in global memory (L2-resident while the CTA works on it).
-template <typename T, bool SMEM>
+// end.  Rows i < rs are copied to shared memory (row pitch n + 1); the others
+// are overwritten in global memory, where they stay L2-resident while the CTA
+// works on them (the launch keeps one CTA per SM, so the resident rows of all
+// CTAs together fit in L2).
+template <typename T>
 __global__ void __launch_bounds__(512) k_refresh_inverse_inplace(double *__restrict__ gm, T *__restrict__ ginv,
                                                                  double *__restrict__ scal, int *__restrict__ status,
-                                                                 int n, int check_drift, double drift_tol) {
+                                                                 int n, int rs, int check_drift, double drift_tol) {
   extern __shared__ double sm[];
-  const int ld = SMEM ? n + 1 : n;
-  double *prow = sm + (SMEM ? (size_t)n * ld : 0);  // n: the scaled pivot row
-  double *f = prow + n;                             // n: column k before the step
-  int *perm = reinterpret_cast<int *>(f + n);       // n: pivot row of each step
+  const int ld = n + 1;
+  double *prow = sm + (size_t)rs * ld;          // n: the scaled pivot row
+  double *f = prow + n;                         // n: column k before the step
+  int *perm = reinterpret_cast<int *>(f + n);   // n: pivot row of each step
   __shared__ int s_piv;
   __shared__ double s_pv;
   __shared__ double red[32];
   const int tid = threadIdx.x, bs = blockDim.x, w = blockIdx.x, lane = tid & 31, warp = tid >> 5, nw = bs >> 5;
-  double *A = gm + (size_t)w * n * n;
+  double *const G = gm + (size_t)w * n * n;
+  auto R = [&](int i) -> double * { return i < rs ? sm + (size_t)i * ld : G + (size_t)i * n; };
   double gmax = 0.0;
-  if (SMEM) {
-    for (int idx = tid; idx < n * n; idx += bs) {
-      const int i = idx / n, j = idx - i * n;
-      const double v = A[idx];
-      gmax = fmax(gmax, fabs(v));
-      sm[(size_t)i * ld + j] = v;
-    }
-    A = sm;
-  } else {
-    for (int idx = tid; idx < n * n; idx += bs) gmax = fmax(gmax, fabs(A[idx]));
+  for (int idx = tid; idx < n * n; idx += bs) {
+    const int i = idx / n, j = idx - i * n;
+    const double v = G[idx];
+    gmax = fmax(gmax, fabs(v));
+    if (i < rs) sm[(size_t)i * ld + j] = v;
   }
   PivotProduct pp;
   double sgn = 1.0;
@@ -547,7 +545,7 @@ __global__ void __launch_bounds__(512) k_refresh_inverse_inplace(double *__restr
       double best = -1.0;
       int bi = k;
       for (int i = k + lane; i < n; i += 32) {
-        const double v = fabs(A[(size_t)i * ld + k]);
+        const double v = fabs(R(i)[k]);
         if (v > best) {
           best = v;
           bi = i;
@@ -564,7 +562,7 @@ __global__ void __launch_bounds__(512) k_refresh_inverse_inplace(double *__restr
       }
       if (lane == 0) {
         s_piv = bi;
-        s_pv = A[(size_t)bi * ld + k];
+        s_pv = R(bi)[k];
       }
     }
     __syncthreads();
@@ -575,10 +573,11 @@ __global__ void __launch_bounds__(512) k_refresh_inverse_inplace(double *__restr
       break;
     }
     if (p != k) {
+      double *Rk = R(k), *Rp = R(p);
       for (int j = tid; j < n; j += bs) {
-        const double t = A[(size_t)k * ld + j];
-        A[(size_t)k * ld + j] = A[(size_t)p * ld + j];
-        A[(size_t)p * ld + j] = t;
+        const double t = Rk[j];
+        Rk[j] = Rp[j];
+        Rp[j] = t;
       }
       sgn = -sgn;
     }
@@ -587,11 +586,14 @@ __global__ void __launch_bounds__(512) k_refresh_inverse_inplace(double *__restr
     if (tid == 0) perm[k] = p;
     __syncthreads();
     const double ip = recip_newton(pv);
-    for (int j = tid; j < n; j += bs) prow[j] = j == k ? ip : A[(size_t)k * ld + j] * ip;
-    for (int i = tid; i < n; i += bs) f[i] = i == k ? 0.0 : A[(size_t)i * ld + k];
+    {
+      const double *Rk = R(k);
+      for (int j = tid; j < n; j += bs) prow[j] = j == k ? ip : Rk[j] * ip;
+    }
+    for (int i = tid; i < n; i += bs) f[i] = i == k ? 0.0 : R(i)[k];
     __syncthreads();
     for (int i = warp; i < n; i += nw) {
-      double *Ai = A + (size_t)i * ld;
+      double *Ai = R(i);
       if (i == k) {
         for (int j = lane; j < n; j += 32) Ai[j] = prow[j];
       } else {
@@ -614,15 +616,16 @@ __global__ void __launch_bounds__(512) k_refresh_inverse_inplace(double *__restr
     const int p = perm[k];
     if (p != k)
       for (int i = tid; i < n; i += bs) {
-        const double t = A[(size_t)i * ld + k];
-        A[(size_t)i * ld + k] = A[(size_t)i * ld + p];
-        A[(size_t)i * ld + p] = t;
+        double *Ai = R(i);
+        const double t = Ai[k];
+        Ai[k] = Ai[p];
+        Ai[p] = t;
       }
     __syncthreads();
   }
   double dmax = 0.0;
   for (int idx = tid; idx < n * n; idx += bs) {
-    const double v = A[(size_t)(idx / n) * ld + idx % n];
+    const double v = R(idx / n)[idx % n];
     if (check_drift) dmax = fmax(dmax, fabs(v - static_cast<double>(gi[idx])));
     gi[idx] = static_cast<T>(v);
   }
@@ -721,15 +724,29 @@ __global__ void __launch_bounds__(kRefreshWarps * 32) k_refresh_inverse_warp64(
     const double p1 = j1 < n ? (j1 == k ? ip : A[k * ld + j1] * ip) : 0.0;
     for (int i = lane; i < n; i += 32) f[i] = i == k ? 0.0 : A[i * ld + k];
     __syncwarp();
-    for (int i = 0; i < n; ++i) {
-      double *Ai = A + i * ld;
-      if (i == k) {
-        if (j0 < n) Ai[j0] = p0;
-        if (j1 < n) Ai[j1] = p1;
-      } else {
-        const double fi = f[i];
-        if (j0 < n) Ai[j0] = j0 == k ? -fi * ip : fma(-fi, p0, Ai[j0]);
-        if (j1 < n) Ai[j1] = j1 == k ? -fi * ip : fma(-fi, p1, Ai[j1]);
+    // rows in groups of four: every load of a group before its eight
+    // multiply-adds, so that they overlap (the rows are independent)
+    for (int i0 = 0; i0 < n; i0 += 4) {
+      double fi[4], a0[4], a1[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i = i0 + u < n ? i0 + u : n - 1;
+        fi[u] = f[i];
+        a0[u] = j0 < n ? A[i * ld + j0] : 0.0;
+        a1[u] = j1 < n ? A[i * ld + j1] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i = i0 + u;
+        if (i >= n) break;
+        double *Ai = A + i * ld;
+        if (i == k) {
+          if (j0 < n) Ai[j0] = p0;
+          if (j1 < n) Ai[j1] = p1;
+        } else {
+          if (j0 < n) Ai[j0] = j0 == k ? -fi[u] * ip : fma(-fi[u], p0, a0[u]);
+          if (j1 < n) Ai[j1] = j1 == k ? -fi[u] * ip : fma(-fi[u], p1, a1[u]);
+        }
       }
     }
     __syncwarp();
@@ -790,12 +807,15 @@ cudaError_t launch_refresh_inverse(double *gm, T *ginv, double *scal, int *statu
     return cudaGetLastError();
   }
   if (n > 32 && inplace_smem <= kRefreshSmemMax) {
-    k_refresh_inverse_inplace<T, true><<<W, 256, inplace_smem, st>>>(gm, ginv, scal, status, n, check_drift,
-                                                                      drift_tol);
+    k_refresh_inverse_inplace<T><<<W, 256, inplace_smem, st>>>(gm, ginv, scal, status, n, n, check_drift, drift_tol);
     return cudaGetLastError();
   }
   if (n > 32) {
-    k_refresh_inverse_inplace<T, false><<<W, 512, aux, st>>>(gm, ginv, scal, status, n, check_drift, drift_tol);
+    // as many leading rows in shared memory as fit in kRefreshSmemMax (which
+    // also keeps one CTA per SM), the rest in global memory
+    const int rs = static_cast<int>((kRefreshSmemMax - aux) / ((size_t)(n + 1) * sizeof(double)));
+    const size_t smem = (size_t)rs * (n + 1) * sizeof(double) + aux;
+    k_refresh_inverse_inplace<T><<<W, 512, smem, st>>>(gm, ginv, scal, status, n, rs, check_drift, drift_tol);
     return cudaGetLastError();
   }
   if (n <= 32) {
@@ -948,11 +968,7 @@ static cudaError_t linalg_attrs() {
     return e;
   if ((e = cudaFuncSetAttribute(k_refresh_inverse_warp64<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)))
     return e;
-  if ((e = cudaFuncSetAttribute(k_refresh_inverse_inplace<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                big)))
-    return e;
-  if ((e = cudaFuncSetAttribute(k_refresh_inverse_inplace<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                big)))
+  if ((e = cudaFuncSetAttribute(k_refresh_inverse_inplace<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)))
     return e;
   return cudaFuncSetAttribute(k_mmat<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
 }
