@@ -387,122 +387,125 @@ struct PivotProduct {
 
 // ---------------------------------------------------------------------------
 // FP64 refresh: Gauss-Jordan elimination with partial pivoting.  log|det G~| is
-// log|prod of pivots|, the sign the product of pivot signs and row swaps.  The
+// log|prod of pivots|, the sign the product of pivot signs and the parity of
+// the row order.  The
 // fresh inverse replaces the Sherman-Morrison one; their largest difference
 // times max|G~| is the walker's drift.
 // ---------------------------------------------------------------------------
-// N_up <= 32: one warp per walker on [G~ | I]; lane j owns the columns j and
-// j + 32; pivot search by shuffles, no block barriers.
 constexpr int kRefreshWarps = 4;
 constexpr size_t kMmatSmemMax = 200 * 1024;  // k_mmat stages G~^{-1} whole up to this footprint
-constexpr size_t kRefreshSmemMax = 200 * 1024;  // [G~ | I] kept in shared memory up to this footprint
+constexpr size_t kRefreshSmemMax = 200 * 1024;  // shared-memory rows of the in-place refresh up to this footprint
 
-template <typename T>
-__global__ void __launch_bounds__(kRefreshWarps * 32) k_refresh_inverse_warp(
-    const double *__restrict__ gm, T *__restrict__ ginv, double *__restrict__ scal, int *__restrict__ status,
-    int n, int W, int check_drift, double drift_tol) {
-  extern __shared__ double sm[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int w = blockIdx.x * kRefreshWarps + warp;
-  if (w >= W) return;  // warp-uniform; no block-wide barrier below
-  const int ld = 2 * n + 1, n2 = 2 * n;
-  double *A = sm + (size_t)warp * (n * ld + n);
-  double *f = A + n * ld;
-  const double *G = gm + (size_t)w * n * n;
+// N_up <= 32: register-resident in-place Gauss-Jordan.  A group of NM lanes
+// (NM = 8, 16 or 32, the smallest >= N_up) holds one walker's matrix, lane c
+// its column c in NM registers (rows and columns past N_up are the identity);
+// a warp holds 32 / NM walkers.  No rows are swapped: step k pivots on the
+// largest |entry| of column k among the rows not yet pivoted (the lowest row
+// on ties), with the in-place update of the exchange form (pivot row scaled by
+// 1/p, -f_i / p into column k, f_i = A[i][k]).  After the last step row p_k
+// holds x_k, so inverse[k][p_k'] is entry (p_k, k') of the result, and the
+// determinant's sign is that of the pivot product times (-1)^(inversions of
+// the pivot order).  Pivot keys compare as the integer bits of |value|.
+template <typename T, int NM>
+__global__ void __launch_bounds__(128) k_refresh_inverse_reg(const double *__restrict__ gm, T *__restrict__ ginv,
+                                                             double *__restrict__ scal, int *__restrict__ status,
+                                                             int n, int W, int check_drift, double drift_tol) {
+  constexpr int kGroups = 32 / NM;
+  constexpr unsigned kFull = 0xffffffffu;
+  const int lane = threadIdx.x & 31, c = lane & (NM - 1), g0 = lane - c;
+  const int w = (blockIdx.x * 4 + (threadIdx.x >> 5)) * kGroups + lane / NM;
+  const bool live = w < W;  // lanes of walkers past W run on the identity and write nothing
+  const double *Gw = gm + (size_t)(live ? w : 0) * n * n;
+  double a[NM];
   double gmax = 0.0;
-  for (int idx = lane; idx < n * n2; idx += 32) {
-    const int i = idx / n2, j = idx - i * n2;
-    double v;
-    if (j < n) {
-      v = G[i * n + j];
-      gmax = fmax(gmax, fabs(v));
-    } else {
-      v = (j - n == i) ? 1.0 : 0.0;
-    }
-    A[i * ld + j] = v;
-  }
-  __syncwarp();
-  PivotProduct pp;
-  double sgn = 1.0;
-  bool ok = true;
-  for (int k = 0; k < n; ++k) {
-    double best = -1.0;
-    int bi = k;
-    for (int i = k + lane; i < n; i += 32) {
-      const double v = fabs(A[i * ld + k]);
-      if (v > best) {
-        best = v;
-        bi = i;
-      }
-    }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
-      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-      if (ob > best || (ob == best && oi < bi)) {
-        best = ob;
-        bi = oi;
-      }
+  for (int i = 0; i < NM; ++i) {
+    double v = i == c ? 1.0 : 0.0;
+    if (live && i < n && c < n) {
+      v = Gw[i * n + c];
+      gmax = fmax(gmax, fabs(v));
     }
-    bi = __shfl_sync(0xffffffffu, bi, 0);
-    const double pv = A[bi * ld + k];
-    if (!(pv != 0.0) || !isfinite(pv)) {
-      ok = false;
-      break;
-    }
-    if (bi != k) {
-      for (int j = lane; j < n2; j += 32) {
-        const double t = A[k * ld + j];
-        A[k * ld + j] = A[bi * ld + j];
-        A[bi * ld + j] = t;
-      }
-      sgn = -sgn;
-    }
-    pp.mul(pv);
-    if (pv < 0.0) sgn = -sgn;
-    __syncwarp();
-    const double ip = recip_newton(pv);
-    for (int j = lane; j < n2; j += 32) A[k * ld + j] *= ip;
-    for (int i = lane; i < n; i += 32) f[i] = A[i * ld + k];
-    __syncwarp();
-    for (int i = 0; i < n; ++i) {
-      if (i == k) continue;
-      const double fi = f[i];
-      for (int j = lane; j < n2; j += 32)
-        if (j >= k) A[i * ld + j] = fma(-fi, A[k * ld + j], A[i * ld + j]);
-    }
-    __syncwarp();
+    a[i] = v;
   }
-  T *gi = ginv + (size_t)w * n * n;
+  const unsigned rows_n = n >= 32 ? kFull : ((1u << n) - 1u);
+  unsigned used = 0;  // rows pivoted so far (the same in every lane of a group)
+  int inversions = 0, myp = 0, myq = 0;  // lane c: pivot row of step c; step at which row c was pivoted
+  PivotProduct pp;
+  bool neg = false, ok = true;
+  for (int k = 0; k < n; ++k) {
+    // lane i of the group picks up f_i = A[i][k] from lane k
+    double fme = 0.0;
+#pragma unroll
+    for (int i = 0; i < NM; ++i) {
+      const double t = __shfl_sync(kFull, a[i], g0 + k);
+      if (c == i) fme = t;
+    }
+    unsigned long long key = (c < n && !((used >> c) & 1u))
+                                 ? static_cast<unsigned long long>(__double_as_longlong(fme)) & 0x7fffffffffffffffull
+                                 : 0ull;
+    int pi = c;
+#pragma unroll
+    for (int o = NM / 2; o > 0; o >>= 1) {
+      const unsigned long long ok2 = __shfl_xor_sync(kFull, key, o);
+      const int oi = __shfl_xor_sync(kFull, pi, o);
+      if (ok2 > key || (ok2 == key && oi < pi)) {
+        key = ok2;
+        pi = oi;
+      }
+    }
+    const int p = pi;
+    const double pv = __shfl_sync(kFull, fme, g0 + p);
+    ok = ok && !((used >> p) & 1u) && pv != 0.0 && isfinite(pv);
+    inversions += __popc(~used & rows_n & ((1u << p) - 1u));
+    used |= 1u << p;
+    if (c == k) myp = p;
+    if (c == p) myq = k;
+    pp.mul(pv);
+    neg ^= pv < 0.0;
+    const double ip = recip_newton(pv);
+    double prow = 0.0;
+#pragma unroll
+    for (int i = 0; i < NM; ++i)
+      if (i == p) prow = a[i];
+    prow = c == k ? ip : prow * ip;
+    const bool colk = c == k;
+#pragma unroll
+    for (int i = 0; i < NM; ++i) {
+      const double fi = __shfl_sync(kFull, a[i], g0 + k);
+      a[i] = i == p ? prow : fma(-fi, prow, colk ? 0.0 : a[i]);
+    }
+  }
+  // inverse[k][p_c] = result[p_k][c]: row i of the result goes to row q_i
+  T *gi = ginv + (size_t)(live ? w : 0) * n * n;
+  double dmax = 0.0;
+#pragma unroll
+  for (int i = 0; i < NM; ++i) {
+    const int qi = __shfl_sync(kFull, myq, g0 + i);
+    if (live && ok && i < n && c < n) {
+      const size_t idx = (size_t)qi * n + myp;
+      if (check_drift) dmax = fmax(dmax, fabs(a[i] - static_cast<double>(gi[idx])));
+      gi[idx] = static_cast<T>(a[i]);
+    }
+  }
+#pragma unroll
+  for (int o = NM / 2; o > 0; o >>= 1) {
+    dmax = fmax(dmax, __shfl_xor_sync(kFull, dmax, o));
+    gmax = fmax(gmax, __shfl_xor_sync(kFull, gmax, o));
+  }
+  if (!live || c != 0) return;
   double *sw = scal + (size_t)w * S_STRIDE;
   if (!ok) {
-    if (lane == 0) {
-      status[w] |= JAGP_WS_SINGULAR;
-      sw[S_LOGDET] = -INFINITY;
-      sw[S_SIGN] = 0.0;
-    }
+    status[w] |= JAGP_WS_SINGULAR;
+    sw[S_LOGDET] = -INFINITY;
+    sw[S_SIGN] = 0.0;
     return;
   }
-  double dmax = 0.0;
-  for (int idx = lane; idx < n * n; idx += 32) {
-    const int i = idx / n, j = idx - i * n;
-    const double v = A[i * ld + n + j];
-    if (check_drift) dmax = fmax(dmax, fabs(v - static_cast<double>(gi[idx])));
-    gi[idx] = static_cast<T>(v);
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
-    gmax = fmax(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
-  }
-  if (lane == 0) {
-    sw[S_LOGDET] = pp.log_abs();
-    sw[S_SIGN] = sgn;
-    if (check_drift) {
-      const double drift = dmax * gmax;
-      sw[S_DRIFT] = drift;
-      if (!(drift <= drift_tol)) status[w] |= JAGP_WS_DRIFT;
-    }
+  sw[S_LOGDET] = pp.log_abs();
+  sw[S_SIGN] = (neg != (inversions & 1)) ? -1.0 : 1.0;
+  if (check_drift) {
+    const double drift = dmax * gmax;
+    sw[S_DRIFT] = drift;
+    if (!(drift <= drift_tol)) status[w] |= JAGP_WS_DRIFT;
   }
 }
 
@@ -597,10 +600,28 @@ __global__ void __launch_bounds__(512) k_refresh_inverse_inplace(double *__restr
       if (i == k) {
         for (int j = lane; j < n; j += 32) Ai[j] = prow[j];
       } else {
+        // eight columns per lane at a time, all loads before the stores, so
+        // that they are in flight together (Ai may be global memory)
         const double fi = f[i];
-        for (int j = lane; j < n; j += 32) Ai[j] = j == k ? -fi * ip : fma(-fi, prow[j], Ai[j]);
+        for (int jb = 0; jb < n; jb += 256) {
+          double v[8];
+#pragma unroll
+          for (int t = 0; t < 8; ++t) {
+            const int j = jb + lane + 32 * t;
+            v[t] = j < n ? Ai[j] : 0.0;
+          }
+#pragma unroll
+          for (int t = 0; t < 8; ++t) {
+            const int j = jb + lane + 32 * t;
+            if (j < n) Ai[j] = fma(-fi, prow[j], v[t]);
+          }
+        }
       }
     }
+    __syncthreads();
+    // column k of the other rows: -f_i / p (replacing what the update left there)
+    for (int i = tid; i < n; i += bs)
+      if (i != k) R(i)[k] = -f[i] * ip;
     __syncthreads();
   }
   T *gi = ginv + (size_t)w * n * n;
@@ -740,15 +761,14 @@ __global__ void __launch_bounds__(kRefreshWarps * 32) k_refresh_inverse_warp64(
         const int i = i0 + u;
         if (i >= n) break;
         double *Ai = A + i * ld;
-        if (i == k) {
-          if (j0 < n) Ai[j0] = p0;
-          if (j1 < n) Ai[j1] = p1;
-        } else {
-          if (j0 < n) Ai[j0] = j0 == k ? -fi[u] * ip : fma(-fi[u], p0, a0[u]);
-          if (j1 < n) Ai[j1] = j1 == k ? -fi[u] * ip : fma(-fi[u], p1, a1[u]);
-        }
+        if (j0 < n) Ai[j0] = i == k ? p0 : fma(-fi[u], p0, a0[u]);
+        if (j1 < n) Ai[j1] = i == k ? p1 : fma(-fi[u], p1, a1[u]);
       }
     }
+    __syncwarp();
+    // column k of the other rows: -f_i / p (replacing what the update left there)
+    for (int i = lane; i < n; i += 32)
+      if (i != k) A[i * ld + k] = -f[i] * ip;
     __syncwarp();
   }
   T *gi = ginv + (size_t)w * n * n;
@@ -819,9 +839,13 @@ cudaError_t launch_refresh_inverse(double *gm, T *ginv, double *scal, int *statu
     return cudaGetLastError();
   }
   if (n <= 32) {
-    const size_t smem = (size_t)kRefreshWarps * (n * (2 * n + 1) + n) * sizeof(double);
-    k_refresh_inverse_warp<T><<<(W + kRefreshWarps - 1) / kRefreshWarps, kRefreshWarps * 32, smem, st>>>(
-        gm, ginv, scal, status, n, W, check_drift, drift_tol);
+    // 4 warps per CTA, 32 / NM walkers per warp
+    if (n <= 8)
+      k_refresh_inverse_reg<T, 8><<<(W + 15) / 16, 128, 0, st>>>(gm, ginv, scal, status, n, W, check_drift, drift_tol);
+    else if (n <= 16)
+      k_refresh_inverse_reg<T, 16><<<(W + 7) / 8, 128, 0, st>>>(gm, ginv, scal, status, n, W, check_drift, drift_tol);
+    else
+      k_refresh_inverse_reg<T, 32><<<(W + 3) / 4, 128, 0, st>>>(gm, ginv, scal, status, n, W, check_drift, drift_tol);
     return cudaGetLastError();
   }
   return cudaErrorInvalidValue;
@@ -964,8 +988,6 @@ template <typename T>
 static cudaError_t linalg_attrs() {
   const int big = 200 * 1024;
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(k_refresh_inverse_warp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)))
-    return e;
   if ((e = cudaFuncSetAttribute(k_refresh_inverse_warp64<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)))
     return e;
   if ((e = cudaFuncSetAttribute(k_refresh_inverse_inplace<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)))
