@@ -14,7 +14,9 @@ The walker state (~1 GB) is larger than L2, so no flush is needed between
 steps.  Under torchrun each rank runs its own 4096 walkers (weak scaling, no
 data-path collective; a barrier and a max-reduction of the timings only).
 
-Prints one JSON line (rank 0).
+Prints one JSON line (rank 0).  Each timed region is an NVTX push/pop range
+(fp64, mixed, fp64tc, batched, forces, large, large_forces), so that a profiler
+can keep to it (ncu --nvtx --nvtx-include "batched/").
 """
 from __future__ import annotations
 
@@ -238,9 +240,12 @@ def profiled_traffic(src_hash):
 
 
 def timed_sweeps(pg, torch, dist, sysm, W, walker0, x0, prec, steps, warmup, ws, dev, local, profile_kernel,
-                 fp64_tc=False):
+                 fp64_tc=False, label=None):
     """Warm up, then time `steps` sweeps (+ local energies) with CUDA events on the
-    launching stream; the profiled kernel class is bracketed by event pairs."""
+    launching stream; the profiled kernel class is bracketed by event pairs.  The
+    timed sweeps form the NVTX range `label` (default: fp64, mixed or fp64tc)."""
+    if label is None:
+        label = "fp64tc" if fp64_tc else ("mixed" if prec == pg.JAGP_PREC_MIXED else "fp64")
     g = pg.JAGP(sysm, W, seed=0, precision=prec, fp64_tc=fp64_tc)
     h = g.h
     tuning = None if NO_AUTOTUNE else g.autotune()  # tile choices for this system and walker count
@@ -262,10 +267,12 @@ def timed_sweeps(pg, torch, dist, sysm, W, walker0, x0, prec, steps, warmup, ws,
         if ws > 1:
             dist.barrier()
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push(label)
         e_start.record(stream)
         for k in range(steps):
             pg.vmc_sweep(h, r, g.state, W, 1, walker0, warmup + k, eL, acc_steps[k:k + 1])
         e_stop.record(stream)
+        torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         if ws > 1:
             dist.barrier()
@@ -320,10 +327,12 @@ def forces_bench(pg, torch, dist, args, dev, rank, ws, local, fp64_tc=False):
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("forces")
     e0.record()
     for _ in range(args.force_steps):
         call()
     e1.record()
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
@@ -373,9 +382,11 @@ def batch_bench(pg, torch, dist, args, dev, rank, ws):
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("batched")
     e0.record()
     b.sweep(args.batch_sweeps, sweep0=args.warmup)
     e1.record()
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
@@ -413,7 +424,7 @@ def large_bench(pg, torch, dist, args, dev, rank, ws, local):
     W = args.large_walkers
     x0 = np.ascontiguousarray(synth.init_walkers(sysm, W * ws, seed=0)[rank * W:(rank + 1) * W])
     rr = timed_sweeps(pg, torch, dist, sysm, W, rank * W, x0, pg.JAGP_PREC_MIXED, args.large_steps, 3, ws, dev,
-                      local, pg.KERNEL_LAMBDA_ROWS)
+                      local, pg.KERNEL_LAMBDA_ROWS, label="large")
     xs = rr["r"][:args.large_force_walkers].clone()
     rr["g"].close()
     forces = large_forces(pg, torch, dist, sysm, xs, ws, dev) if args.large_force_walkers > 0 else None
@@ -454,9 +465,11 @@ def large_forces(pg, torch, dist, sysm, xs, ws, dev):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if ws > 1:
         dist.barrier()
+    torch.cuda.nvtx.range_push("large_forces")
     e0.record()
     step()
     e1.record()
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     t = torch.tensor([ms], dtype=torch.float64, device=dev)
