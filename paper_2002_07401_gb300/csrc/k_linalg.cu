@@ -388,11 +388,9 @@ struct PivotProduct {
 // ---------------------------------------------------------------------------
 // FP64 refresh: Gauss-Jordan elimination with partial pivoting.  log|det G~| is
 // log|prod of pivots|, the sign the product of pivot signs and the parity of
-// the row order.  The
-// fresh inverse replaces the Sherman-Morrison one; their largest difference
-// times max|G~| is the walker's drift.
+// the row order.  The fresh inverse replaces the Sherman-Morrison one; their
+// largest difference times max|G~| is the walker's drift.
 // ---------------------------------------------------------------------------
-constexpr int kRefreshWarps = 4;
 constexpr size_t kMmatSmemMax = 200 * 1024;  // k_mmat stages G~^{-1} whole up to this footprint
 constexpr size_t kRefreshSmemMax = 200 * 1024;  // shared-memory rows of the in-place refresh up to this footprint
 
@@ -493,6 +491,187 @@ __global__ void __launch_bounds__(128) k_refresh_inverse_reg(const double *__res
     gmax = fmax(gmax, __shfl_xor_sync(kFull, gmax, o));
   }
   if (!live || c != 0) return;
+  double *sw = scal + (size_t)w * S_STRIDE;
+  if (!ok) {
+    status[w] |= JAGP_WS_SINGULAR;
+    sw[S_LOGDET] = -INFINITY;
+    sw[S_SIGN] = 0.0;
+    return;
+  }
+  sw[S_LOGDET] = pp.log_abs();
+  sw[S_SIGN] = (neg != (inversions & 1)) ? -1.0 : 1.0;
+  if (check_drift) {
+    const double drift = dmax * gmax;
+    sw[S_DRIFT] = drift;
+    if (!(drift <= drift_tol)) status[w] |= JAGP_WS_DRIFT;
+  }
+}
+
+// 32 < N_up <= 64: the same register-resident scheme on two warps per walker.
+// Warp h of a walker holds rows 32 h .. 32 h + 31, lane c the columns c and
+// c + 32 (identity past N_up); the pivot of each step is found per warp by
+// shuffles and between the two warps through shared memory, and the warp
+// holding the pivot row publishes it, scaled, for both.  Each step passes two
+// 64-thread named barriers; the exchange slots are double-buffered by step
+// parity, so no third barrier is needed.  Two walkers per CTA of 128 threads.
+template <typename T>
+__global__ void __launch_bounds__(128) k_refresh_inverse_reg64(const double *__restrict__ gm, T *__restrict__ ginv,
+                                                               double *__restrict__ scal, int *__restrict__ status,
+                                                               int n, int W, int check_drift, double drift_tol) {
+  constexpr unsigned kFull = 0xffffffffu;
+  __shared__ double s_prow[2][2][64];                 // [walker slot][parity][column]
+  __shared__ unsigned long long s_key[2][2][2];       // [slot][parity][half]
+  __shared__ int s_idx[2][2][2];
+  __shared__ double s_val[2][2][2];
+  __shared__ int s_q[2][64];                          // step at which each row was pivoted
+  __shared__ double s_red[2][2][2];                   // [slot][half][gmax, dmax]
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5, slot = wi >> 1, h = wi & 1;
+  const int w = blockIdx.x * 2 + slot;
+  if (w >= W) return;  // both warps of the walker leave; its barriers involve no one else
+  const int bar_id = 1 + slot;
+  const int c0 = lane, c1 = lane + 32, r0 = 32 * h;
+  const double *Gw = gm + (size_t)w * n * n;
+  double a0[32], a1[32];
+  double gmax = 0.0;
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    const int r = r0 + i;
+    double v0 = r == c0 ? 1.0 : 0.0, v1 = r == c1 ? 1.0 : 0.0;
+    if (r < n) {
+      if (c0 < n) v0 = Gw[(size_t)r * n + c0];
+      if (c1 < n) v1 = Gw[(size_t)r * n + c1];
+      gmax = fmax(gmax, fmax(c0 < n ? fabs(v0) : 0.0, c1 < n ? fabs(v1) : 0.0));
+    }
+    a0[i] = v0;
+    a1[i] = v1;
+  }
+  unsigned long long used = 0;
+  int inversions = 0, myp0 = 0, myp1 = 0;
+  PivotProduct pp;
+  bool neg = false, ok = true;
+  const unsigned long long rows_n = n >= 64 ? ~0ull : ((1ull << n) - 1ull);
+  for (int k = 0; k < n; ++k) {
+    const int par = k & 1, kl = k & 31;
+    const bool hi = k >= 32;
+    // this warp's rows of column k: lane i keeps f of row r0 + i
+    double fme = 0.0;
+    if (hi) {
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        const double t = __shfl_sync(kFull, a1[i], kl);
+        if (lane == i) fme = t;
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        const double t = __shfl_sync(kFull, a0[i], kl);
+        if (lane == i) fme = t;
+      }
+    }
+    const int myrow = r0 + lane;
+    unsigned long long key = (myrow < n && !((used >> myrow) & 1ull))
+                                 ? static_cast<unsigned long long>(__double_as_longlong(fme)) & 0x7fffffffffffffffull
+                                 : 0ull;
+    int pi = myrow;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long k2 = __shfl_xor_sync(kFull, key, o);
+      const int i2 = __shfl_xor_sync(kFull, pi, o);
+      if (k2 > key || (k2 == key && i2 < pi)) {
+        key = k2;
+        pi = i2;
+      }
+    }
+    const double pval = __shfl_sync(kFull, fme, pi - r0);
+    if (lane == 0) {
+      s_key[slot][par][h] = key;
+      s_idx[slot][par][h] = pi;
+      s_val[slot][par][h] = pval;
+    }
+    asm volatile("bar.sync %0, 64;" ::"r"(bar_id) : "memory");
+    // the better of the two halves (the lower rows on ties)
+    const unsigned long long ka = s_key[slot][par][0], kb = s_key[slot][par][1];
+    const int hp = kb > ka ? 1 : 0;
+    const int p = s_idx[slot][par][hp];
+    const double pv = s_val[slot][par][hp];
+    ok = ok && !((used >> p) & 1ull) && pv != 0.0 && isfinite(pv);
+    inversions += __popcll(~used & rows_n & ((1ull << p) - 1ull));
+    used |= 1ull << p;
+    if (k == c0) myp0 = p;
+    if (k == c1) myp1 = p;
+    if (h == 0 && lane == 0) s_q[slot][p] = k;
+    pp.mul(pv);
+    neg ^= pv < 0.0;
+    const double ip = recip_newton(pv);
+    if ((p >> 5) == h) {
+      // this warp holds the pivot row: publish it scaled (column k: 1/p)
+      const int pl = p & 31;
+      double x0 = 0.0, x1 = 0.0;
+#pragma unroll
+      for (int i = 0; i < 32; ++i)
+        if (i == pl) {
+          x0 = a0[i];
+          x1 = a1[i];
+        }
+      s_prow[slot][par][c0] = c0 == k ? ip : x0 * ip;
+      s_prow[slot][par][c1] = c1 == k ? ip : x1 * ip;
+    }
+    asm volatile("bar.sync %0, 64;" ::"r"(bar_id) : "memory");
+    const double v0 = s_prow[slot][par][c0], v1 = s_prow[slot][par][c1];
+    const bool k0 = c0 == k, k1 = c1 == k;
+    if (hi) {
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        const int r = r0 + i;
+        if (r >= n) break;  // warp-uniform
+        const double fi = __shfl_sync(kFull, a1[i], kl);
+        a0[i] = r == p ? v0 : fma(-fi, v0, a0[i]);
+        a1[i] = r == p ? v1 : fma(-fi, v1, k1 ? 0.0 : a1[i]);
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        const int r = r0 + i;
+        if (r >= n) break;  // warp-uniform
+        const double fi = __shfl_sync(kFull, a0[i], kl);
+        a0[i] = r == p ? v0 : fma(-fi, v0, k0 ? 0.0 : a0[i]);
+        a1[i] = r == p ? v1 : fma(-fi, v1, a1[i]);
+      }
+    }
+  }
+  asm volatile("bar.sync %0, 64;" ::"r"(bar_id) : "memory");  // s_q complete
+  // inverse[k][p_c] = result[p_k][c]: row r of the result goes to row q_r
+  T *gi = ginv + (size_t)w * n * n;
+  double dmax = 0.0;
+  if (ok) {
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      const int r = r0 + i;
+      if (r >= n) break;
+      const size_t row = (size_t)s_q[slot][r] * n;
+      if (c0 < n) {
+        if (check_drift) dmax = fmax(dmax, fabs(a0[i] - static_cast<double>(gi[row + myp0])));
+        gi[row + myp0] = static_cast<T>(a0[i]);
+      }
+      if (c1 < n) {
+        if (check_drift) dmax = fmax(dmax, fabs(a1[i] - static_cast<double>(gi[row + myp1])));
+        gi[row + myp1] = static_cast<T>(a1[i]);
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    dmax = fmax(dmax, __shfl_xor_sync(kFull, dmax, o));
+    gmax = fmax(gmax, __shfl_xor_sync(kFull, gmax, o));
+  }
+  if (lane == 0) {
+    s_red[slot][h][0] = gmax;
+    s_red[slot][h][1] = dmax;
+  }
+  asm volatile("bar.sync %0, 64;" ::"r"(bar_id) : "memory");
+  if (h != 0 || lane != 0) return;
+  gmax = fmax(s_red[slot][0][0], s_red[slot][1][0]);
+  dmax = fmax(s_red[slot][0][1], s_red[slot][1][1]);
   double *sw = scal + (size_t)w * S_STRIDE;
   if (!ok) {
     status[w] |= JAGP_WS_SINGULAR;
@@ -675,144 +854,6 @@ __global__ void __launch_bounds__(512) k_refresh_inverse_inplace(double *__restr
   }
 }
 
-// 32 < N_up <= 64: the in-place elimination (as above) with one warp per
-// walker; lane j owns columns j and j + 32 of G~; pivot search by shuffles and
-// no block barriers, which matters when refreshes come every few moves.
-template <typename T>
-__global__ void __launch_bounds__(kRefreshWarps * 32) k_refresh_inverse_warp64(
-    const double *__restrict__ gm, T *__restrict__ ginv, double *__restrict__ scal, int *__restrict__ status,
-    int n, int W, int check_drift, double drift_tol) {
-  extern __shared__ double sm[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int w = blockIdx.x * kRefreshWarps + warp;
-  if (w >= W) return;  // warp-uniform; no block-wide barrier below
-  const int ld = n + 1;
-  double *A = sm + (size_t)warp * (n * ld + n + n / 2 + 1);
-  double *f = A + n * ld;
-  int *perm = reinterpret_cast<int *>(f + n);
-  const double *G = gm + (size_t)w * n * n;
-  double gmax = 0.0;
-  for (int idx = lane; idx < n * n; idx += 32) {
-    const int i = idx / n, j = idx - i * n;
-    const double v = G[idx];
-    gmax = fmax(gmax, fabs(v));
-    A[i * ld + j] = v;
-  }
-  __syncwarp();
-  PivotProduct pp;
-  double sgn = 1.0;
-  bool ok = true;
-  const int j0 = lane, j1 = lane + 32;
-  for (int k = 0; k < n; ++k) {
-    double best = -1.0;
-    int bi = k;
-    for (int i = k + lane; i < n; i += 32) {
-      const double v = fabs(A[i * ld + k]);
-      if (v > best) {
-        best = v;
-        bi = i;
-      }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
-      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-      if (ob > best || (ob == best && oi < bi)) {
-        best = ob;
-        bi = oi;
-      }
-    }
-    bi = __shfl_sync(0xffffffffu, bi, 0);
-    const double pv = A[bi * ld + k];
-    if (!(pv != 0.0) || !isfinite(pv)) {
-      ok = false;
-      break;
-    }
-    if (bi != k) {
-      for (int j = lane; j < n; j += 32) {
-        const double t = A[k * ld + j];
-        A[k * ld + j] = A[bi * ld + j];
-        A[bi * ld + j] = t;
-      }
-      sgn = -sgn;
-    }
-    if (lane == 0) perm[k] = bi;
-    pp.mul(pv);
-    if (pv < 0.0) sgn = -sgn;
-    __syncwarp();
-    const double ip = recip_newton(pv);
-    const double p0 = j0 < n ? (j0 == k ? ip : A[k * ld + j0] * ip) : 0.0;
-    const double p1 = j1 < n ? (j1 == k ? ip : A[k * ld + j1] * ip) : 0.0;
-    for (int i = lane; i < n; i += 32) f[i] = i == k ? 0.0 : A[i * ld + k];
-    __syncwarp();
-    // rows in groups of four: every load of a group before its eight
-    // multiply-adds, so that they overlap (the rows are independent)
-    for (int i0 = 0; i0 < n; i0 += 4) {
-      double fi[4], a0[4], a1[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int i = i0 + u < n ? i0 + u : n - 1;
-        fi[u] = f[i];
-        a0[u] = j0 < n ? A[i * ld + j0] : 0.0;
-        a1[u] = j1 < n ? A[i * ld + j1] : 0.0;
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int i = i0 + u;
-        if (i >= n) break;
-        double *Ai = A + i * ld;
-        if (j0 < n) Ai[j0] = i == k ? p0 : fma(-fi[u], p0, a0[u]);
-        if (j1 < n) Ai[j1] = i == k ? p1 : fma(-fi[u], p1, a1[u]);
-      }
-    }
-    __syncwarp();
-    // column k of the other rows: -f_i / p (replacing what the update left there)
-    for (int i = lane; i < n; i += 32)
-      if (i != k) A[i * ld + k] = -f[i] * ip;
-    __syncwarp();
-  }
-  T *gi = ginv + (size_t)w * n * n;
-  double *sw = scal + (size_t)w * S_STRIDE;
-  if (!ok) {
-    if (lane == 0) {
-      status[w] |= JAGP_WS_SINGULAR;
-      sw[S_LOGDET] = -INFINITY;
-      sw[S_SIGN] = 0.0;
-    }
-    return;
-  }
-  for (int k = n - 1; k >= 0; --k) {
-    const int p = perm[k];
-    if (p != k)
-      for (int i = lane; i < n; i += 32) {
-        const double t = A[i * ld + k];
-        A[i * ld + k] = A[i * ld + p];
-        A[i * ld + p] = t;
-      }
-    __syncwarp();
-  }
-  double dmax = 0.0;
-  for (int idx = lane; idx < n * n; idx += 32) {
-    const int i = idx / n, j = idx - i * n;
-    const double v = A[i * ld + j];
-    if (check_drift) dmax = fmax(dmax, fabs(v - static_cast<double>(gi[idx])));
-    gi[idx] = static_cast<T>(v);
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
-    gmax = fmax(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
-  }
-  if (lane == 0) {
-    sw[S_LOGDET] = pp.log_abs();
-    sw[S_SIGN] = sgn;
-    if (check_drift) {
-      const double drift = dmax * gmax;
-      sw[S_DRIFT] = drift;
-      if (!(drift <= drift_tol)) status[w] |= JAGP_WS_DRIFT;
-    }
-  }
-}
 
 template <typename T>
 cudaError_t launch_refresh_inverse(double *gm, T *ginv, double *scal, int *status, int n, int W,
@@ -821,9 +862,7 @@ cudaError_t launch_refresh_inverse(double *gm, T *ginv, double *scal, int *statu
   const size_t aux = (size_t)n * (2 * sizeof(double) + sizeof(int));
   const size_t inplace_smem = (size_t)n * (n + 1) * sizeof(double) + aux;
   if (n > 32 && n <= 64) {
-    const size_t per = (size_t)(n * (n + 1) + n + n / 2 + 1) * sizeof(double);
-    k_refresh_inverse_warp64<T><<<(W + kRefreshWarps - 1) / kRefreshWarps, kRefreshWarps * 32, per * kRefreshWarps,
-                                  st>>>(gm, ginv, scal, status, n, W, check_drift, drift_tol);
+    k_refresh_inverse_reg64<T><<<(W + 1) / 2, 128, 0, st>>>(gm, ginv, scal, status, n, W, check_drift, drift_tol);
     return cudaGetLastError();
   }
   if (n > 32 && inplace_smem <= kRefreshSmemMax) {
@@ -988,8 +1027,6 @@ template <typename T>
 static cudaError_t linalg_attrs() {
   const int big = 200 * 1024;
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(k_refresh_inverse_warp64<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)))
-    return e;
   if ((e = cudaFuncSetAttribute(k_refresh_inverse_inplace<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)))
     return e;
   return cudaFuncSetAttribute(k_mmat<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
