@@ -990,6 +990,7 @@ struct jagp_batch {
   std::vector<int> W;
   std::vector<uint64_t> walker0;
   std::vector<int> order;  // systems by decreasing cost
+  std::vector<int> lane;   // stream of order[q]: least-loaded stream at its turn
   double *acc = nullptr;
   uint32_t *counter = nullptr;
   std::vector<cudaStream_t> streams;
@@ -1017,7 +1018,7 @@ jagp_status_t batch_capture(jagp_batch *b) {
     jagp_ctx *h = b->h[sidx];
     const int prof = h->prof_kernel;
     h->prof_kernel = 0;  // no event pairs inside a graph
-    cudaStream_t ss = b->streams[q % K];
+    cudaStream_t ss = b->streams[b->lane[q]];
     double *acc = b->acc ? b->acc + 4 * (size_t)sidx : nullptr;
     if (h->precision == JAGP_PREC_MIXED)
       rc = run_sweeps<float>(h, b->r[sidx], b->state[sidx], b->W[sidx], 1, b->walker0[sidx], 0, b->eL[sidx], acc, ss,
@@ -1077,6 +1078,19 @@ jagp_status_t jagp_batch_create(jagp_batch_t *out, int S, const jagp_handle_t *h
   std::stable_sort(b->order.begin(), b->order.end(), [&](int a, int c) { return cost(a) > cost(c); });
   b->acc = d_acc;
   const int K = std::max(1, std::min(n_streams > 0 ? n_streams : 8, S));
+  // longest first onto the least-loaded stream, so that the streams of the
+  // graph end at about the same time (round robin leaves the stream with the
+  // largest systems about half again above the mean)
+  {
+    std::vector<double> load(K, 0.0);
+    for (int q = 0; q < S; ++q) {
+      int best = 0;
+      for (int k = 1; k < K; ++k)
+        if (load[k] < load[best]) best = k;
+      b->lane.push_back(best);
+      load[best] += cost(b->order[q]);
+    }
+  }
   bool ok = cudaMalloc(&b->counter, sizeof(uint32_t)) == cudaSuccess &&
             cudaMemset(b->counter, 0, sizeof(uint32_t)) == cudaSuccess &&
             cudaEventCreateWithFlags(&b->ev0, cudaEventDisableTiming) == cudaSuccess &&
