@@ -240,15 +240,20 @@ def profiled_traffic(src_hash):
 
 
 def timed_sweeps(pg, torch, dist, sysm, W, walker0, x0, prec, steps, warmup, ws, dev, local, profile_kernel,
-                 fp64_tc=False, label=None):
+                 fp64_tc=False, label=None, pin=None):
     """Warm up, then time `steps` sweeps (+ local energies) with CUDA events on the
     launching stream; the profiled kernel class is bracketed by event pairs.  The
-    timed sweeps form the NVTX range `label` (default: fp64, mixed or fp64tc)."""
+    timed sweeps form the NVTX range `label` (default: fp64, mixed or fp64tc).
+    `pin` (a tuning dict) replaces the autotuner's choices."""
     if label is None:
         label = "fp64tc" if fp64_tc else ("mixed" if prec == pg.JAGP_PREC_MIXED else "fp64")
     g = pg.JAGP(sysm, W, seed=0, precision=prec, fp64_tc=fp64_tc)
     h = g.h
-    tuning = None if NO_AUTOTUNE else g.autotune()  # tile choices for this system and walker count
+    if pin is not None:
+        g.set_tuning(pin)
+        tuning = dict(pin, pinned=True)
+    else:
+        tuning = None if NO_AUTOTUNE else g.autotune()  # tile choices for this system and walker count
     r = g.positions(x0)
     stream = torch.cuda.current_stream()
     eL = torch.empty((1, W), dtype=torch.float64, device=dev)
@@ -367,11 +372,13 @@ def batch_bench(pg, torch, dist, args, dev, rank, ws):
     import synth
     systems = synth.config3_systems(seed=0, n_systems=args.batch_systems)
     W = args.batch_walkers
-    members, pos = [], []
+    members, pos, tunings = [], [], []
     for s in systems:
         m = pg.JAGP(s, W, seed=0, precision=pg.JAGP_PREC_MIXED, refresh_moves=16)
         p = m.positions(synth.init_walkers(s, W * ws, seed=0)[rank * W:(rank + 1) * W])
         m.eval(p)
+        if not NO_AUTOTUNE:
+            tunings.append(m.autotune(p))  # per system, before the graph is captured
         members.append(m)
         pos.append(p)
     b = pg.Batch(members, pos, walker0=[rank * W] * len(members), n_streams=args.batch_streams)
@@ -407,7 +414,23 @@ def batch_bench(pg, torch, dist, args, dev, rank, ws):
             "ms_per_sweep": ms_max / args.batch_sweeps, "sweeps": args.batch_sweeps, "warmup": args.warmup,
             "systems": len(systems), "walkers_per_system": W, "moves_per_sweep": moves // args.batch_sweeps // ws,
             "acceptance": float(acc[:, 2].sum()) / (moves / ws), "status_bits": bits,
-            "dtype": "f32+bf16 (f64 refresh)", "workload": BATCH_WORKLOAD}
+            "dtype": "f32+bf16 (f64 refresh)", "workload": BATCH_WORKLOAD,
+            "tuning": tuning_summary(tunings)}
+
+
+def tuning_summary(tunings):
+    """How often each tile choice won among the autotuned handles (None without tuning)."""
+    if not tunings:
+        return None
+    keys = ("tile_proposals", "tile_refresh", "umma_bn_left", "umma_bn_right", "umma_stages_left",
+            "umma_stages_right")
+    out = {"handles": len(tunings)}
+    for k in keys:
+        counts = {}
+        for t in tunings:
+            counts[str(t[k])] = counts.get(str(t[k]), 0) + 1
+        out[k] = counts
+    return out
 
 
 LARGE_WORKLOAD = ("large system, mixed precision: 256 He atoms in a 26 bohr cube (min separation 1.5), N=512 "
@@ -424,7 +447,8 @@ def large_bench(pg, torch, dist, args, dev, rank, ws, local):
     W = args.large_walkers
     x0 = np.ascontiguousarray(synth.init_walkers(sysm, W * ws, seed=0)[rank * W:(rank + 1) * W])
     rr = timed_sweeps(pg, torch, dist, sysm, W, rank * W, x0, pg.JAGP_PREC_MIXED, args.large_steps, 3, ws, dev,
-                      local, pg.KERNEL_LAMBDA_ROWS, label="large")
+                      local, pg.KERNEL_LAMBDA_ROWS, label="large",
+                      pin=json.loads(args.large_tuning) if args.large_tuning else None)
     xs = rr["r"][:args.large_force_walkers].clone()
     rr["g"].close()
     forces = large_forces(pg, torch, dist, sysm, xs, ws, dev) if args.large_force_walkers > 0 else None
@@ -684,6 +708,8 @@ def main():
     ap.add_argument("--large-walkers", type=int, default=1024)
     ap.add_argument("--large-steps", type=int, default=3)
     ap.add_argument("--large-only", action="store_true", help="run only the 512-electron measurement")
+    ap.add_argument("--large-tuning", default=None,
+                    help="JSON tile choices for the 512-electron line (jagp_set_tuning) instead of autotuning")
     ap.add_argument("--large-force-walkers", type=int, default=16,
                     help="walkers of the 512-electron FP64 forces measurement (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
