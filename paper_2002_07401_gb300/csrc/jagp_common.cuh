@@ -135,17 +135,17 @@ __device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32
   }
 }
 
-// The move of `electron` in `sweep` of `walker`: proposal r' and acceptance draw.
-__device__ __forceinline__ void move_draw(const DevSystem &s, uint32_t walker, uint32_t sweep,
-                                          uint32_t electron, const double r[3], double rp[3],
-                                          double *u) {
+// The move of `electron` in `sweep` of `walker`: coordinate k (0, 1, 2) of the
+// proposal r' = r + delta (2 t - 1) from Philox output word k, and the
+// acceptance draw u from word 3.  A warp's lanes each take one coordinate, so
+// the FP64 arithmetic of a proposal is issued once rather than three times.
+__device__ __forceinline__ void move_draw_coord(const DevSystem &s, uint32_t walker, uint32_t sweep,
+                                                uint32_t electron, double rk, int k, double *rpk, double *u) {
   uint32_t c[4] = {walker, sweep, electron, 1u};
   philox4x32_10(c, s.key0, s.key1);
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    const double t = __dsub_rn(__dmul_rn(__dadd_rn((double)c[k], 0.5), 0x1p-31), 1.0);
-    rp[k] = fma(s.delta, t, r[k]);
-  }
+  const uint32_t ck = k == 0 ? c[0] : (k == 1 ? c[1] : c[2]);
+  const double t = __dsub_rn(__dmul_rn(__dadd_rn((double)ck, 0.5), 0x1p-31), 1.0);
+  *rpk = fma(s.delta, t, rk);
   *u = (double)c[3] * 0x1p-32;
 }
 

@@ -116,11 +116,29 @@ __global__ void __launch_bounds__(256) k_kinetic(DevSystem s, const double *__re
       tz = fma(g, fma(f, dz, Sz), tz);
       tl = fma(g * S0, lapfac, tl);
     }
-    // lane partials are summed in FP64
-    const double gx = warp_sum(static_cast<double>(tx));
-    const double gy = warp_sum(static_cast<double>(ty));
-    const double gz = warp_sum(static_cast<double>(tz));
-    const double lp = warp_sum(static_cast<double>(tl));
+    // lane partials summed in FP64, or (FP32 partials) as double-words with
+    // FP32 instructions only
+    double gx, gy, gz, lp;
+    if constexpr (kDw) {
+      fdw sx{static_cast<float>(tx), 0.0f}, sy{static_cast<float>(ty), 0.0f}, sz{static_cast<float>(tz), 0.0f},
+          sl{static_cast<float>(tl), 0.0f};
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        sx = dw_add(sx, fdw{__shfl_xor_sync(0xffffffffu, sx.hi, o), __shfl_xor_sync(0xffffffffu, sx.lo, o)});
+        sy = dw_add(sy, fdw{__shfl_xor_sync(0xffffffffu, sy.hi, o), __shfl_xor_sync(0xffffffffu, sy.lo, o)});
+        sz = dw_add(sz, fdw{__shfl_xor_sync(0xffffffffu, sz.hi, o), __shfl_xor_sync(0xffffffffu, sz.lo, o)});
+        sl = dw_add(sl, fdw{__shfl_xor_sync(0xffffffffu, sl.hi, o), __shfl_xor_sync(0xffffffffu, sl.lo, o)});
+      }
+      gx = static_cast<double>(sx.hi) + sx.lo;
+      gy = static_cast<double>(sy.hi) + sy.lo;
+      gz = static_cast<double>(sz.hi) + sz.lo;
+      lp = static_cast<double>(sl.hi) + sl.lo;
+    } else {
+      gx = warp_sum(static_cast<double>(tx));
+      gy = warp_sum(static_cast<double>(ty));
+      gz = warp_sum(static_cast<double>(tz));
+      lp = warp_sum(static_cast<double>(tl));
+    }
     if (lane == 0) {
       double *o = kin + pt * 4;
       o[0] = gx;
@@ -266,9 +284,14 @@ __global__ void __launch_bounds__(128) k_elocal_dw(DevSystem s, const double *__
                                                    const double *__restrict__ kin, double *__restrict__ eL,
                                                    double *__restrict__ parts, double *__restrict__ scal) {
   const int w = blockIdx.x, N = s.N, tid = threadIdx.x, na = s.n_atoms;
+  const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   extern __shared__ float sf[];
-  float *xh = sf, *xl = xh + 3 * N;      // electron coordinates as double-words
+  float *xh = sf, *xl = xh + 3 * N;           // electron coordinates as double-words
   float *ah = xl + 3 * N, *al = ah + 3 * na;  // atom coordinates
+  // per atom, as double-words: -Z, and for J1 -c^4/2, c^3/(2b), -b c
+  float *ac = al + 3 * na;
+  // two-body Jastrow constants [same spin, opposite spin]: b k (dw), k, -2 b (dw)
+  __shared__ float j2c[2][5];
   for (int t = tid; t < N * 3; t += blockDim.x) {
     const fdw v = dw_of(r[(size_t)w * N * 3 + t]);
     xh[t] = v.hi;
@@ -279,39 +302,71 @@ __global__ void __launch_bounds__(128) k_elocal_dw(DevSystem s, const double *__
     ah[t] = v.hi;
     al[t] = v.lo;
   }
+  for (int a = tid; a < na; a += blockDim.x) {
+    const double c = s.c1[a], b = s.b_ea;
+    const fdw z = dw_of(-s.Z[a]), c4 = dw_of(-0.5 * c * c * c * c);
+    const fdw c3 = dw_of(b == 0.0 ? 0.0 : c * c * c / (2.0 * b)), bc = dw_of(-b * c);
+    float *q = ac + 8 * a;
+    q[0] = z.hi;
+    q[1] = z.lo;
+    q[2] = c4.hi;
+    q[3] = c4.lo;
+    q[4] = c3.hi;
+    q[5] = c3.lo;
+    q[6] = bc.hi;
+    q[7] = bc.lo;
+  }
+  if (tid < 2) {
+    double kk, bb;
+    j2_params(s, tid == 0, &kk, &bb);
+    const fdw bk = dw_of(bb * kk), m2b = dw_of(-2.0 * bb);
+    j2c[tid][0] = bk.hi;
+    j2c[tid][1] = bk.lo;
+    j2c[tid][2] = static_cast<float>(kk);  // 2 or 4, exact
+    j2c[tid][3] = m2b.hi;
+    j2c[tid][4] = m2b.lo;
+  }
   __syncthreads();
+  // a warp per electron, its lanes over the partners (atoms, then electrons);
+  // every constant comes from shared memory, so the loops are FP32 only
   fdw tkin{0.0f, 0.0f}, vee{0.0f, 0.0f}, vei{0.0f, 0.0f}, jv{0.0f, 0.0f};
-  for (int e = tid; e < N; e += blockDim.x) {
+  const int P = na + N;
+  for (int e = warp; e < N; e += nw) {
     const fdw pe[3] = {{xh[3 * e], xl[3 * e]}, {xh[3 * e + 1], xl[3 * e + 1]}, {xh[3 * e + 2], xl[3 * e + 2]}};
+    const bool eup = e < s.n_up;
     fdw gJx{0.0f, 0.0f}, gJy{0.0f, 0.0f}, gJz{0.0f, 0.0f}, lJ{0.0f, 0.0f};
-    for (int a = 0; a < na; ++a) {
-      const fdw dx = dw_add(pe[0], fdw{-ah[3 * a], -al[3 * a]});
-      const fdw dy = dw_add(pe[1], fdw{-ah[3 * a + 1], -al[3 * a + 1]});
-      const fdw dz = dw_add(pe[2], fdw{-ah[3 * a + 2], -al[3 * a + 2]});
-      const fdw r2 = dw_add(dw_add(dw_mul(dx, dx), dw_mul(dy, dy)), dw_mul(dz, dz));
-      const fdw rr = dw_sqrt(r2), rinv = dw_recip(rr);
-      vei = dw_add(vei, dw_mul(rinv, dw_neg(dw_of(s.Z[a]))));
-      if (s.use_j1) {
-        // f = -c^3 u(c r), u = (1 - e^{-b c r}) / (2b); f' = -c^4 e / 2, f'' = c^5 b e / 2
-        const double c = s.c1[a], b = s.b_ea;
-        fdw ex{1.0f, 0.0f};
-        if (b == 0.0) {
-          jv = dw_add(jv, dw_mul(rr, dw_of(-0.5 * c * c * c * c)));
-        } else {
-          ex = dw_exp_neg(dw_mul(rr, dw_of(-b * c)));
-          // -c^3 (1 - e) / (2b) = c^3 / (2b) (e - 1)
-          jv = dw_add(jv, dw_mul(dw_add_f(ex, -1.0f), dw_of(c * c * c / (2.0 * b))));
+    for (int p = lane; p < P; p += 32) {
+      if (p < na) {
+        const int a = p;
+        const float *q = ac + 8 * a;
+        const fdw dx = dw_add(pe[0], fdw{-ah[3 * a], -al[3 * a]});
+        const fdw dy = dw_add(pe[1], fdw{-ah[3 * a + 1], -al[3 * a + 1]});
+        const fdw dz = dw_add(pe[2], fdw{-ah[3 * a + 2], -al[3 * a + 2]});
+        const fdw r2 = dw_add(dw_add(dw_mul(dx, dx), dw_mul(dy, dy)), dw_mul(dz, dz));
+        const fdw rr = dw_sqrt(r2), rinv = dw_recip(rr);
+        vei = dw_add(vei, dw_mul(rinv, fdw{q[0], q[1]}));
+        if (s.use_j1) {
+          // f = -c^3 u(c r), u = (1 - e^{-b c r}) / (2b); f' = -c^4 e / 2, f'' = c^5 b e / 2
+          const fdw c4{q[2], q[3]}, bc{q[6], q[7]};
+          fdw ex{1.0f, 0.0f};
+          if (s.b_ea == 0.0) {
+            jv = dw_add(jv, dw_mul(rr, c4));
+          } else {
+            ex = dw_exp_neg(dw_mul(rr, bc));
+            // -c^3 (1 - e) / (2b) = c^3 / (2b) (e - 1)
+            jv = dw_add(jv, dw_mul(dw_add_f(ex, -1.0f), fdw{q[4], q[5]}));
+          }
+          const fdw fp = dw_mul(ex, c4);   // f'
+          const fdw fpp = dw_mul(fp, bc);  // f'' = -b c f'
+          const fdw qq = dw_mul(fp, rinv);
+          gJx = dw_add(gJx, dw_mul(qq, dx));
+          gJy = dw_add(gJy, dw_mul(qq, dy));
+          gJz = dw_add(gJz, dw_mul(qq, dz));
+          lJ = dw_add(lJ, dw_add(fpp, dw_add(qq, qq)));
         }
-        const fdw fp = dw_mul(ex, dw_of(-0.5 * c * c * c * c));   // f'
-        const fdw fpp = dw_mul(fp, dw_of(-c * b));                 // f'' = -b c f'
-        const fdw q = dw_mul(fp, rinv);
-        gJx = dw_add(gJx, dw_mul(q, dx));
-        gJy = dw_add(gJy, dw_mul(q, dy));
-        gJz = dw_add(gJz, dw_mul(q, dz));
-        lJ = dw_add(lJ, dw_add(fpp, dw_add(q, q)));
+        continue;
       }
-    }
-    for (int k = 0; k < N; ++k) {
+      const int k = p - na;
       if (k == e) continue;
       const fdw dx = dw_add(pe[0], fdw{-xh[3 * k], -xl[3 * k]});
       const fdw dy = dw_add(pe[1], fdw{-xh[3 * k + 1], -xl[3 * k + 1]});
@@ -320,26 +375,37 @@ __global__ void __launch_bounds__(128) k_elocal_dw(DevSystem s, const double *__
       const fdw rr = dw_sqrt(r2), rinv = dw_recip(rr);
       if (k > e) vee = dw_add(vee, rinv);
       if (s.use_j2) {
-        double kk, bb;
-        j2_params(s, (e < s.n_up) == (k < s.n_up), &kk, &bb);
-        const fdw den = dw_add_f(dw_mul(rr, dw_of(bb * kk)), static_cast<float>(kk));  // k (1 + b r), k exact
-        const fdw iq = dw_recip(den);                                                 // 1 / (k (1 + b r))
+        const float *jc = j2c[eup == (k < s.n_up) ? 0 : 1];
+        const float kk = jc[2];
+        const fdw den = dw_add_f(dw_mul(rr, fdw{jc[0], jc[1]}), kk);  // k (1 + b r), k exact
+        const fdw iq = dw_recip(den);                                  // 1 / (k (1 + b r))
         if (k > e) jv = dw_add(jv, dw_mul(rr, iq));
-        const fdw qi = dw_mul_f(iq, static_cast<float>(kk));                          // 1/q (k exact)
-        const fdw vp = dw_mul(iq, qi);                                               // 1 / (k q^2)
-        const fdw vpp = dw_mul(dw_mul(vp, qi), dw_of(-2.0 * bb));                     // -2b / (k q^3)
-        const fdw q = dw_mul(vp, rinv);
-        gJx = dw_add(gJx, dw_mul(q, dx));
-        gJy = dw_add(gJy, dw_mul(q, dy));
-        gJz = dw_add(gJz, dw_mul(q, dz));
-        lJ = dw_add(lJ, dw_add(vpp, dw_add(q, q)));
+        const fdw qi = dw_mul_f(iq, kk);                               // 1/q (k exact)
+        const fdw vp = dw_mul(iq, qi);                                 // 1 / (k q^2)
+        const fdw vpp = dw_mul(dw_mul(vp, qi), fdw{jc[3], jc[4]});      // -2b / (k q^3)
+        const fdw qq = dw_mul(vp, rinv);
+        gJx = dw_add(gJx, dw_mul(qq, dx));
+        gJy = dw_add(gJy, dw_mul(qq, dy));
+        gJz = dw_add(gJz, dw_mul(qq, dz));
+        lJ = dw_add(lJ, dw_add(vpp, dw_add(qq, qq)));
       }
     }
-    const double *kd = kin + ((size_t)w * N + e) * 4;
-    const double gx = static_cast<double>(gJx.hi) + gJx.lo, gy = static_cast<double>(gJy.hi) + gJy.lo,
-                 gz = static_cast<double>(gJz.hi) + gJz.lo, lj = static_cast<double>(lJ.hi) + lJ.lo;
-    const double t = kd[3] + lj + 2.0 * (kd[0] * gx + kd[1] * gy + kd[2] * gz) + (gx * gx + gy * gy + gz * gz);
-    tkin = dw_add(tkin, dw_of(-0.5 * t));
+    // the electron's Jastrow gradient and Laplacian over the warp
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      gJx = dw_add(gJx, fdw{__shfl_xor_sync(0xffffffffu, gJx.hi, o), __shfl_xor_sync(0xffffffffu, gJx.lo, o)});
+      gJy = dw_add(gJy, fdw{__shfl_xor_sync(0xffffffffu, gJy.hi, o), __shfl_xor_sync(0xffffffffu, gJy.lo, o)});
+      gJz = dw_add(gJz, fdw{__shfl_xor_sync(0xffffffffu, gJz.hi, o), __shfl_xor_sync(0xffffffffu, gJz.lo, o)});
+      lJ = dw_add(lJ, fdw{__shfl_xor_sync(0xffffffffu, lJ.hi, o), __shfl_xor_sync(0xffffffffu, lJ.lo, o)});
+    }
+    if (lane == 0) {
+      const double *kd = kin + ((size_t)w * N + e) * 4;
+      const double gx = static_cast<double>(gJx.hi) + gJx.lo, gy = static_cast<double>(gJy.hi) + gJy.lo,
+                   gz = static_cast<double>(gJz.hi) + gJz.lo, lj = static_cast<double>(lJ.hi) + lJ.lo;
+      const double t =
+          kd[3] + lj + 2.0 * (kd[0] * gx + kd[1] * gy + kd[2] * gz) + (gx * gx + gy * gy + gz * gz);
+      tkin = dw_add(tkin, dw_of(-0.5 * t));
+    }
   }
   __shared__ double red[4][4];
   double a4[4] = {static_cast<double>(tkin.hi) + tkin.lo, static_cast<double>(vee.hi) + vee.lo,
@@ -372,7 +438,7 @@ __global__ void __launch_bounds__(128) k_elocal_dw(DevSystem s, const double *__
 cudaError_t launch_elocal_dw(const DevSystem &s, const double *r, const double *kin, double *eL, double *parts, int W,
                              cudaStream_t st, double *scal) {
   if (W <= 0) return cudaSuccess;
-  const size_t smem = (size_t)(s.N + s.n_atoms) * 6 * sizeof(float);
+  const size_t smem = ((size_t)(s.N + s.n_atoms) * 6 + (size_t)s.n_atoms * 8) * sizeof(float);
   k_elocal_dw<<<W, 128, smem, st>>>(s, r, kin, eL, parts, scal);
   return cudaGetLastError();
 }
@@ -386,6 +452,8 @@ cudaError_t launch_elocal(const DevSystem &s, const double *r, const double *kin
 
 cudaError_t setup_energy_attributes() {
   cudaError_t e = cudaFuncSetAttribute(k_kinetic<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_elocal_dw, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_kinetic<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }

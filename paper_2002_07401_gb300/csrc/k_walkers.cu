@@ -73,9 +73,12 @@ __global__ void __launch_bounds__(256) k_basis_points(DevSystem s, const double 
     const int w = (int)(pt / npts), i = (int)(pt % npts);
     const double *rr = r + ((size_t)w * s.N + e0 + i) * 3;
     double p[3] = {rr[0], rr[1], rr[2]};
+    const int kc = lane < 3 ? lane : 2;  // the coordinate this lane converts
     if (PROPOSE) {
-      double rp[3], u;
-      move_draw(s, walker0 + (uint32_t)w, sweep, (uint32_t)(e0 + i), p, rp, &u);
+      double rp[3], u, rpk;
+      move_draw_coord(s, walker0 + (uint32_t)w, sweep, (uint32_t)(e0 + i), p[kc], kc, &rpk, &u);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) rp[k] = __shfl_sync(0xffffffffu, rpk, k);
       p[0] = rp[0];
       p[1] = rp[1];
       p[2] = rp[2];
@@ -88,7 +91,11 @@ __global__ void __launch_bounds__(256) k_basis_points(DevSystem s, const double 
     }
     T *o = out + ((size_t)w * s.n_up + i) * s.L;
     if constexpr (kDw) {
-      const fdw pd[3] = {dw_of(p[0]), dw_of(p[1]), dw_of(p[2])};
+      const fdw mine = dw_of(p[kc]);  // one conversion per lane, shared by shuffles
+      fdw pd[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        pd[k] = fdw{__shfl_sync(0xffffffffu, mine.hi, k), __shfl_sync(0xffffffffu, mine.lo, k)};
       float *ol = out_lo ? out_lo + ((size_t)w * s.n_up + i) * s.L : nullptr;
       for (int k = lane; k < s.n_shells; k += 32) {
         const float4 gh = sh_dw[2 * k], gl = sh_dw[2 * k + 1];
@@ -178,6 +185,18 @@ __device__ __forceinline__ void block_sum2(double &a, double &b, double *red) {
 // log|det| is not tracked move by move: the refresh that ends every
 // half-sweep or sweep recomputes it from the tables.
 // ---------------------------------------------------------------------------
+// Acceptance probability R^2 e^{2 dJ}.  The mixed path (T = float) takes the
+// exponential in FP32, like the rest of its acceptance test; FP64 where
+// |2 dJ| >= 80 (FP32's range) and in the FP64 path.
+template <typename T>
+__device__ __forceinline__ double accept_prob(double pr, double pj) {
+  if constexpr (std::is_same<T, float>::value) {
+    const float x = static_cast<float>(2.0 * pj);
+    if (fabsf(x) < 80.0f) return pr * pr * static_cast<double>(expf(x));
+  }
+  return pr * pr * exp(2.0 * pj);
+}
+
 template <bool UP, typename T, bool GLOB>
 __global__ void __launch_bounds__(512) k_metropolis(DevSystem s, double *__restrict__ r,
                                                     const double *__restrict__ rprop,
@@ -234,7 +253,7 @@ __global__ void __launch_bounds__(512) k_metropolis(DevSystem s, double *__restr
     block_sum2(pr, pj, red);
     if (tid == 0) {
       const double u = rp4[3];
-      const double p = pr * pr * exp(2.0 * pj);
+      const double p = accept_prob<T>(pr, pj);
       int acc = 0;
       if (!isfinite(p) || !isfinite(pr)) {
         st_bits |= JAGP_WS_NONFINITE;
@@ -364,7 +383,7 @@ __global__ void __launch_bounds__(kMetroWarps * 32) k_metropolis_warp(
       pj += j2_move_change<T, UP>(s, xs, e, px, py, pz, xs[3 * e], xs[3 * e + 1], xs[3 * e + 2], lane, 32);
     pr = __shfl_sync(0xffffffffu, warp_sum(pr), 0);
     pj = __shfl_sync(0xffffffffu, warp_sum(pj), 0);
-    const double p = pr * pr * exp(2.0 * pj);
+    const double p = accept_prob<T>(pr, pj);
     int acc = 0;
     if (!isfinite(p) || !isfinite(pr)) {
       st_bits |= JAGP_WS_NONFINITE;
