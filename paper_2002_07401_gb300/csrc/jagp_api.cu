@@ -566,6 +566,7 @@ jagp_status_t jagp_create(jagp_handle_t *out, const jagp_system_t *sys, const ja
   const size_t oG = take(sys->n_shells * sizeof(double4)), oI = take(sys->n_shells * sizeof(int));
   const size_t oGd = take(sys->n_shells * 2 * sizeof(float4));
   const size_t oSa = take(sys->n_shells * sizeof(int));
+  const size_t oAf = take(na * sizeof(float4));
   const size_t oL = take((size_t)L * L * 8), oT = take((size_t)L * L * 8);
   const size_t oU = take((size_t)(k_unp > 0 ? k_unp : 1) * L * 8);
   // mixed path: lambda^T and lambda as fixed-point slices, rows padded to kp
@@ -590,6 +591,10 @@ jagp_status_t jagp_create(jagp_handle_t *out, const jagp_system_t *sys, const ja
       xB[nn] = slice_row_fixed(sys->lambda + (size_t)nn * L, 1, L, &sB[(size_t)nn * nsl * kp], (size_t)kp, nsl, bits);
     }
   }
+  std::vector<float4> atom_f(na);
+  for (int a = 0; a < na; ++a)
+    atom_f[a] = make_float4(static_cast<float>(sys->R[3 * a]), static_cast<float>(sys->R[3 * a + 1]),
+                            static_cast<float>(sys->R[3 * a + 2]), static_cast<float>(c1[a]));
   if (cudaMalloc(&h->d_mem, off) != cudaSuccess) {
     delete h;
     return JAGP_ERR_OOM;
@@ -603,6 +608,7 @@ jagp_status_t jagp_create(jagp_handle_t *out, const jagp_system_t *sys, const ja
                 cudaSuccess &&
             cudaMemcpy(b + oI, info.data(), sys->n_shells * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess &&
             cudaMemcpy(b + oSa, satom.data(), sys->n_shells * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy(b + oAf, atom_f.data(), na * sizeof(float4), cudaMemcpyHostToDevice) == cudaSuccess &&
             cudaMemcpy(b + oL, sys->lambda, (size_t)L * L * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
             cudaMemcpy(b + oT, lamT.data(), (size_t)L * L * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
             (k_unp == 0 ||
@@ -637,6 +643,10 @@ jagp_status_t jagp_create(jagp_handle_t *out, const jagp_system_t *sys, const ja
   d.b_ea = sys->b_ea;
   d.b_para = sys->b_para;
   d.b_anti = sys->b_anti;
+  d.atom_f = reinterpret_cast<const float4 *>(b + oAf);
+  d.b_ea_f = static_cast<float>(sys->b_ea);
+  d.b_para_f = static_cast<float>(sys->b_para);
+  d.b_anti_f = static_cast<float>(sys->b_anti);
   d.use_j1 = sys->use_j1 ? 1 : 0;
   d.use_j2 = sys->use_j2 ? 1 : 0;
   d.j2_si = sys->j2_spin_independent ? 1 : 0;

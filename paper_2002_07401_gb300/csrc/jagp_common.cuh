@@ -35,6 +35,9 @@ struct DevSystem {
   const double *lamT;       // [L][L] = lambda^T
   const double *unpaired;   // [n_up - n_dn][L]
   double b_ea, b_para, b_anti;
+  // FP32 copies for the mixed path's acceptance test (Jastrow changes only)
+  const float4 *atom_f;     // [n_atoms]: (x, y, z, c1) rounded to FP32
+  float b_ea_f, b_para_f, b_anti_f;
   int use_j1, use_j2, j2_si;
   double v_ii;              // ion-ion repulsion (a constant of the system)
   double delta;
@@ -354,6 +357,27 @@ __device__ __forceinline__ double j2_move_change(const DevSystem &s, const doubl
       const float ik = static_cast<float>(1.0 / kk), b = static_cast<float>(bb);
       pj += static_cast<double>(ik * (__fdividef(dn, 1.0f + b * dn) - __fdividef(d0, 1.0f + b * d0)));
     }
+  }
+  return pj;
+}
+
+// The mixed path's two-body change with FP32 instructions only: positions from
+// an FP32 mirror xf of the walker's coordinates, proposal p and old position o
+// rounded to FP32 (the value only enters the acceptance test).
+template <bool UP>
+__device__ __forceinline__ float j2_move_change_f(const DevSystem &s, const float *xf, int e, const float p[3],
+                                                  const float o[3], int k0, int dk) {
+  float pj = 0.0f;
+  for (int k = k0; k < s.N; k += dk) {
+    if (k == e) continue;
+    const bool same = (k < s.n_up) == UP;
+    const bool para = same && !s.j2_si;  // k = 4, b_para; else k = 2, b_anti
+    const float ik = para ? 0.25f : 0.5f, b = para ? s.b_para_f : s.b_anti_f;
+    const float qx = xf[3 * k], qy = xf[3 * k + 1], qz = xf[3 * k + 2];
+    const float ax = p[0] - qx, ay = p[1] - qy, az = p[2] - qz;
+    const float bx = o[0] - qx, by = o[1] - qy, bz = o[2] - qz;
+    const float dn = sqrtf(ax * ax + ay * ay + az * az), d0 = sqrtf(bx * bx + by * by + bz * bz);
+    pj += ik * (__fdividef(dn, 1.0f + b * dn) - __fdividef(d0, 1.0f + b * d0));
   }
   return pj;
 }

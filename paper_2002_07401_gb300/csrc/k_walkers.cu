@@ -21,28 +21,36 @@ namespace jagp {
 // one-body Jastrow change of the move is taken here as well (FP32 distances in
 // the FP32 path: it only enters the acceptance test).
 // ---------------------------------------------------------------------------
-template <typename T>
+// FP64 path: the change from FP64 distances.
 __device__ __forceinline__ double j1_move_change(const DevSystem &s, const double *rp, const double *rr, int lane) {
   double dj1 = 0.0;
   // lane pairs: even lanes take the new position, odd lanes the old one
   for (int q = lane; q < 2 * s.n_atoms; q += 32) {
     const int a = q >> 1;
     const double *pos = (q & 1) ? rr : rp;
-    if constexpr (std::is_same<T, double>::value) {
-      const double ax = pos[0] - s.R[3 * a], ay = pos[1] - s.R[3 * a + 1], az = pos[2] - s.R[3 * a + 2];
-      const double v = j1_val(s.c1[a], s.b_ea, sqrt(ax * ax + ay * ay + az * az));
-      dj1 += (q & 1) ? -v : v;
-    } else {
-      const float ax = static_cast<float>(pos[0] - s.R[3 * a]), ay = static_cast<float>(pos[1] - s.R[3 * a + 1]),
-                  az = static_cast<float>(pos[2] - s.R[3 * a + 2]);
-      const float c = static_cast<float>(s.c1[a]), b = static_cast<float>(s.b_ea);
-      const float sc = c * sqrtf(ax * ax + ay * ay + az * az);
-      const float u = (b == 0.0f) ? 0.5f * sc : -expm1f(-b * sc) / (2.0f * b);
-      const float v = -c * c * c * u;
-      dj1 += (q & 1) ? -static_cast<double>(v) : static_cast<double>(v);
-    }
+    const double ax = pos[0] - s.R[3 * a], ay = pos[1] - s.R[3 * a + 1], az = pos[2] - s.R[3 * a + 2];
+    const double v = j1_val(s.c1[a], s.b_ea, sqrt(ax * ax + ay * ay + az * az));
+    dj1 += (q & 1) ? -v : v;
   }
   return warp_sum(dj1);
+}
+
+// Mixed path: FP32 instructions only, from the positions and atoms rounded to
+// FP32 (the change only enters the acceptance test); every lane gets the sum.
+__device__ __forceinline__ double j1_move_change_f(const DevSystem &s, const float *rp, const float *rr, int lane) {
+  float dj1 = 0.0f;
+  const float b = s.b_ea_f;
+  for (int q = lane; q < 2 * s.n_atoms; q += 32) {
+    const float4 A = s.atom_f[q >> 1];
+    const float *pos = (q & 1) ? rr : rp;
+    const float ax = pos[0] - A.x, ay = pos[1] - A.y, az = pos[2] - A.z;
+    const float c = A.w;
+    const float sc = c * sqrtf(ax * ax + ay * ay + az * az);
+    const float u = (b == 0.0f) ? 0.5f * sc : -expm1f(-b * sc) / (2.0f * b);
+    const float v = -c * c * c * u;
+    dj1 += (q & 1) ? -v : v;
+  }
+  return static_cast<double>(warp_sum(dj1));
 }
 
 template <bool PROPOSE, typename T>
@@ -84,7 +92,22 @@ __global__ void __launch_bounds__(256) k_basis_points(DevSystem s, const double 
       p[2] = rp[2];
       // change of the one-body Jastrow for this move: it depends only on the
       // electron's own old and new positions, so it is taken here, in parallel
-      const double dj1 = s.use_j1 ? j1_move_change<T>(s, rp, rr, lane) : 0.0;
+      double dj1 = 0.0;
+      if (s.use_j1) {
+        if constexpr (kDw) {
+          // new and old position in FP32, one coordinate converted per lane
+          const float pk = static_cast<float>(rpk), ok = static_cast<float>(rr[kc]);
+          float pf[3], of[3];
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            pf[k] = __shfl_sync(0xffffffffu, pk, k);
+            of[k] = __shfl_sync(0xffffffffu, ok, k);
+          }
+          dj1 = j1_move_change_f(s, pf, of, lane);
+        } else {
+          dj1 = j1_move_change(s, rp, rr, lane);
+        }
+      }
       double *rec = rprop + ((size_t)w * s.n_up + i) * kPropStride;
       if (lane < 4) rec[lane] = lane < 3 ? rp[lane] : u;
       if (lane == 0) rec[4] = dj1;
@@ -220,12 +243,17 @@ __global__ void __launch_bounds__(512) k_metropolis(DevSystem s, double *__restr
   T *gp = GLOB ? reinterpret_cast<T *>(xs + N * 3) : Gi + n * n;  // n
   T *vv = gp + n;                                   // n
   T *cc = vv + n;                                   // n
+  float *xf = reinterpret_cast<float *>(cc + n);    // mixed path: N * 3 positions rounded to FP32
+  constexpr bool kF32 = std::is_same<T, float>::value;
   __shared__ double red[64];
   __shared__ int s_acc;
   __shared__ double s_R;
   if (!GLOB)
     for (int t = tid; t < n * n; t += bs) Gi[t] = gw[t];
-  for (int t = tid; t < N * 3; t += bs) xs[t] = r[(size_t)w * N * 3 + t];
+  for (int t = tid; t < N * 3; t += bs) {
+    xs[t] = r[(size_t)w * N * 3 + t];
+    if constexpr (kF32) xf[t] = static_cast<float>(xs[t]);
+  }
   double sgn = 1.0, J = 0.0, nacc = 0.0;
   int st_bits = 0;
   if (tid == 0) {
@@ -249,7 +277,15 @@ __global__ void __launch_bounds__(512) k_metropolis(DevSystem s, double *__restr
     double pr = static_cast<double>(prt);
     const double ox = xs[3 * e], oy = xs[3 * e + 1], oz = xs[3 * e + 2];
     if (tid == 0) pj = rp4[4];   // one-body Jastrow change, from the proposal kernel
-    if (s.use_j2) pj += j2_move_change<T, UP>(s, xs, e, px, py, pz, ox, oy, oz, tid, bs);
+    if (s.use_j2) {
+      if constexpr (kF32) {
+        const float pf[3] = {static_cast<float>(px), static_cast<float>(py), static_cast<float>(pz)};
+        const float of[3] = {xf[3 * e], xf[3 * e + 1], xf[3 * e + 2]};
+        pj += static_cast<double>(j2_move_change_f<UP>(s, xf, e, pf, of, tid, bs));
+      } else {
+        pj += j2_move_change<T, UP>(s, xs, e, px, py, pz, ox, oy, oz, tid, bs);
+      }
+    }
     block_sum2(pr, pj, red);
     if (tid == 0) {
       const double u = rp4[3];
@@ -306,6 +342,11 @@ __global__ void __launch_bounds__(512) k_metropolis(DevSystem s, double *__restr
         xs[3 * e] = px;
         xs[3 * e + 1] = py;
         xs[3 * e + 2] = pz;
+        if constexpr (kF32) {
+          xf[3 * e] = static_cast<float>(px);
+          xf[3 * e + 1] = static_cast<float>(py);
+          xf[3 * e + 2] = static_cast<float>(pz);
+        }
       }
       if (UP) {
         const size_t row = ((size_t)w * n + m) * s.L;
@@ -337,7 +378,10 @@ constexpr size_t kMetroSmemMax = 200 * 1024;  // G~^{-1} kept in shared memory u
 
 template <typename T>
 __host__ __device__ inline size_t metro_smem_per_walker(int n, int N) {
-  return ((size_t)N * 3 * sizeof(double) + (size_t)(n * n + 3 * n) * sizeof(T) + 15) & ~size_t(15);
+  // positions (FP64), G~^{-1}, three n-vectors, and in the mixed path the FP32
+  // mirror of the positions
+  const size_t mirror = std::is_same<T, float>::value ? (size_t)N * 3 * sizeof(float) : 0;
+  return ((size_t)N * 3 * sizeof(double) + (size_t)(n * n + 3 * n) * sizeof(T) + mirror + 15) & ~size_t(15);
 }
 
 template <bool UP, typename T>
@@ -356,9 +400,14 @@ __global__ void __launch_bounds__(kMetroWarps * 32) k_metropolis_warp(
   T *gp = Gi + n * n;
   T *vv = gp + n;
   T *cc = vv + n;
+  float *xf = reinterpret_cast<float *>(cc + n);  // mixed path: N * 3 positions rounded to FP32
+  constexpr bool kF32 = std::is_same<T, float>::value;
   T *gw = ginv + (size_t)w * n * n;
   for (int t = lane; t < n * n; t += 32) Gi[t] = gw[t];
-  for (int t = lane; t < N * 3; t += 32) xs[t] = r[(size_t)w * N * 3 + t];
+  for (int t = lane; t < N * 3; t += 32) {
+    xs[t] = r[(size_t)w * N * 3 + t];
+    if constexpr (kF32) xf[t] = static_cast<float>(xs[t]);
+  }
   double *sw = scal + (size_t)w * S_STRIDE;
   double sgn = sw[S_SIGN], J = sw[S_J], nacc = sw[S_NACC];
   int st_bits = status[w];
@@ -377,12 +426,25 @@ __global__ void __launch_bounds__(kMetroWarps * 32) k_metropolis_warp(
       gp[t] = g;
       prt += UP ? g * Gi[t * n + m] : Gi[m * n + t] * g;
     }
-    double pr = static_cast<double>(prt);
-    if (lane == 0) pj = rec[4];
-    if (s.use_j2)
-      pj += j2_move_change<T, UP>(s, xs, e, px, py, pz, xs[3 * e], xs[3 * e + 1], xs[3 * e + 2], lane, 32);
-    pr = __shfl_sync(0xffffffffu, warp_sum(pr), 0);
-    pj = __shfl_sync(0xffffffffu, warp_sum(pj), 0);
+    double pr;
+    if constexpr (kF32) {
+      // ratio and two-body change summed in FP32 (the acceptance test's precision)
+      float pjf = 0.0f;
+      if (s.use_j2) {
+        const float pf[3] = {static_cast<float>(px), static_cast<float>(py), static_cast<float>(pz)};
+        const float of[3] = {xf[3 * e], xf[3 * e + 1], xf[3 * e + 2]};
+        pjf = j2_move_change_f<UP>(s, xf, e, pf, of, lane, 32);
+      }
+      pr = static_cast<double>(__shfl_sync(0xffffffffu, warp_sum(prt), 0));
+      pj = rec[4] + static_cast<double>(__shfl_sync(0xffffffffu, warp_sum(pjf), 0));
+    } else {
+      pr = static_cast<double>(prt);
+      if (lane == 0) pj = rec[4];
+      if (s.use_j2)
+        pj += j2_move_change<T, UP>(s, xs, e, px, py, pz, xs[3 * e], xs[3 * e + 1], xs[3 * e + 2], lane, 32);
+      pr = __shfl_sync(0xffffffffu, warp_sum(pr), 0);
+      pj = __shfl_sync(0xffffffffu, warp_sum(pj), 0);
+    }
     const double p = accept_prob<T>(pr, pj);
     int acc = 0;
     if (!isfinite(p) || !isfinite(pr)) {
@@ -419,7 +481,11 @@ __global__ void __launch_bounds__(kMetroWarps * 32) k_metropolis_warp(
         else
           Gi[idx] -= (vv[j] - (j == m ? T(1) : T(0))) * cc[k] * invR;
       }
-      if (lane < 3) xs[3 * e + lane] = lane == 0 ? px : (lane == 1 ? py : pz);
+      if (lane < 3) {
+        const double v = lane == 0 ? px : (lane == 1 ? py : pz);
+        xs[3 * e + lane] = v;
+        if constexpr (kF32) xf[3 * e + lane] = static_cast<float>(v);
+      }
       if (UP) {
         const size_t row = ((size_t)w * n + m) * s.L;
         for (int t = lane; t < s.L; t += 32) phi_up[row + t] = pprop[row + t];
@@ -469,7 +535,8 @@ cudaError_t launch_metropolis(const DevSystem &s, bool up, double *r, const doub
                                                               list, count, pprop_lo, phi_lo, m_begin, m_end, total);
     return cudaGetLastError();
   }
-  const size_t glob = (size_t)s.N * 3 * sizeof(double) + (size_t)3 * n * sizeof(T);
+  const size_t glob = (size_t)s.N * 3 * sizeof(double) + (size_t)3 * n * sizeof(T) +
+                      (std::is_same<T, float>::value ? (size_t)s.N * 3 * sizeof(float) : 0);
   if (up)
     k_metropolis<true, T, true><<<W, 512, glob, st>>>(s, r, rprop, gprop, ginv, scal, status, pprop, phi_up, list,
                                                        count, pprop_lo, phi_lo, m_begin, m_end, total);
