@@ -54,9 +54,12 @@ __global__ void __launch_bounds__(256) k_kinetic(DevSystem s, const double *__re
     const double px = rr[0], py = rr[1], pz = rr[2];
     fdw pd[3];
     if constexpr (kDw) {
-      pd[0] = dw_of(px);
-      pd[1] = dw_of(py);
-      pd[2] = dw_of(pz);
+      // one FP64 -> double-word conversion per lane, shared by shuffles
+      const int kc = lane < 3 ? lane : 2;
+      const fdw mine = dw_of(kc == 0 ? px : (kc == 1 ? py : pz));
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        pd[k] = fdw{__shfl_sync(0xffffffffu, mine.hi, k), __shfl_sync(0xffffffffu, mine.lo, k)};
     }
     const T *M = mbuf + pt * s.L;
     T tx = T(0), ty = T(0), tz = T(0), tl = T(0);
@@ -331,6 +334,11 @@ __global__ void __launch_bounds__(128) k_elocal_dw(DevSystem s, const double *__
   // every constant comes from shared memory, so the loops are FP32 only
   fdw tkin{0.0f, 0.0f}, vee{0.0f, 0.0f}, vei{0.0f, 0.0f}, jv{0.0f, 0.0f};
   const int P = na + N;
+  // lane j keeps the Jastrow gradient and Laplacian of the warp's j-th electron
+  // of the current group of 32, so that the FP64 assembly of the kinetic term
+  // is issued once per group instead of once per electron
+  fdw kx{0.0f, 0.0f}, ky{0.0f, 0.0f}, kz{0.0f, 0.0f}, kl{0.0f, 0.0f};
+  int mine = -1, slot = 0;
   for (int e = warp; e < N; e += nw) {
     const fdw pe[3] = {{xh[3 * e], xl[3 * e]}, {xh[3 * e + 1], xl[3 * e + 1]}, {xh[3 * e + 2], xl[3 * e + 2]}};
     const bool eup = e < s.n_up;
@@ -398,32 +406,49 @@ __global__ void __launch_bounds__(128) k_elocal_dw(DevSystem s, const double *__
       gJz = dw_add(gJz, fdw{__shfl_xor_sync(0xffffffffu, gJz.hi, o), __shfl_xor_sync(0xffffffffu, gJz.lo, o)});
       lJ = dw_add(lJ, fdw{__shfl_xor_sync(0xffffffffu, lJ.hi, o), __shfl_xor_sync(0xffffffffu, lJ.lo, o)});
     }
-    if (lane == 0) {
-      const double *kd = kin + ((size_t)w * N + e) * 4;
-      const double gx = static_cast<double>(gJx.hi) + gJx.lo, gy = static_cast<double>(gJy.hi) + gJy.lo,
-                   gz = static_cast<double>(gJz.hi) + gJz.lo, lj = static_cast<double>(lJ.hi) + lJ.lo;
-      const double t =
-          kd[3] + lj + 2.0 * (kd[0] * gx + kd[1] * gy + kd[2] * gz) + (gx * gx + gy * gy + gz * gz);
-      tkin = dw_add(tkin, dw_of(-0.5 * t));
+    if (lane == slot) {
+      kx = gJx;
+      ky = gJy;
+      kz = gJz;
+      kl = lJ;
+      mine = e;
+    }
+    if (++slot == 32 || e + nw >= N) {  // warp-uniform
+      if (mine >= 0) {
+        const double *kd = kin + ((size_t)w * N + mine) * 4;
+        const double gx = static_cast<double>(kx.hi) + kx.lo, gy = static_cast<double>(ky.hi) + ky.lo,
+                     gz = static_cast<double>(kz.hi) + kz.lo, lj = static_cast<double>(kl.hi) + kl.lo;
+        const double t =
+            kd[3] + lj + 2.0 * (kd[0] * gx + kd[1] * gy + kd[2] * gz) + (gx * gx + gy * gy + gz * gz);
+        tkin = dw_add(tkin, dw_of(-0.5 * t));
+      }
+      mine = -1;
+      slot = 0;
     }
   }
-  __shared__ double red[4][4];
-  double a4[4] = {static_cast<double>(tkin.hi) + tkin.lo, static_cast<double>(vee.hi) + vee.lo,
-                  static_cast<double>(vei.hi) + vei.lo, static_cast<double>(jv.hi) + jv.lo};
+  // the four sums over the block as double-words (FP32 instructions), FP64 at the end
+  __shared__ float red[4][4][2];
+  fdw a4[4] = {tkin, vee, vei, jv};
 #pragma unroll
-  for (int q = 0; q < 4; ++q) a4[q] = warp_sum(a4[q]);
-  if ((tid & 31) == 0)
+  for (int q = 0; q < 4; ++q)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) red[q][tid >> 5] = a4[q];
+    for (int o = 16; o > 0; o >>= 1)
+      a4[q] = dw_add(a4[q], fdw{__shfl_xor_sync(0xffffffffu, a4[q].hi, o), __shfl_xor_sync(0xffffffffu, a4[q].lo, o)});
+  if (lane == 0)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      red[q][warp][0] = a4[q].hi;
+      red[q][warp][1] = a4[q].lo;
+    }
   __syncthreads();
   if (tid == 0) {
-    double a = 0.0, b = 0.0, c = 0.0, j = 0.0;
-    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
-      a += red[0][q];
-      b += red[1][q];
-      c += red[2][q];
-      j += red[3][q];
+    fdw sum[4];
+    for (int q = 0; q < 4; ++q) {
+      sum[q] = fdw{red[q][0][0], red[q][0][1]};
+      for (int k = 1; k < nw; ++k) sum[q] = dw_add(sum[q], fdw{red[q][k][0], red[q][k][1]});
     }
+    const double a = static_cast<double>(sum[0].hi) + sum[0].lo, b = static_cast<double>(sum[1].hi) + sum[1].lo,
+                 c = static_cast<double>(sum[2].hi) + sum[2].lo, j = static_cast<double>(sum[3].hi) + sum[3].lo;
     eL[w] = a + b + c + s.v_ii;
     if (parts) {
       parts[(size_t)w * 4 + 0] = a;
