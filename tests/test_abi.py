@@ -49,6 +49,10 @@ def test_status_strings_and_bad_args_without_gpu():
     assert L.local_energy(None, None, None, 1, None, None, None) == 1
     h = ctypes.c_void_p()
     assert L.jagp_create(ctypes.byref(h), None, None) == 1
+    # tuning calls reject a null handle or tuning before touching CUDA
+    t = pg._Tuning()
+    assert L.jagp_set_tuning(None, ctypes.byref(t)) == 1
+    assert L.jagp_autotune(None, None, 1, ctypes.byref(t), None) == 1
 
 
 def test_oracle_and_product_share_no_code():
