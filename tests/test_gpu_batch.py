@@ -59,3 +59,43 @@ def test_batch_equals_individual_sweeps(torch_cuda, precision):
         assert abs(acc[k, 0] - ref_acc[k][:, 0].sum()) <= 1e-9 * abs(ref_acc[k][:, 0]).sum()
         assert members[k].status() & (pg.WS_NONFINITE | pg.WS_SINGULAR) == 0
     b.close()
+
+
+def test_batched_full_size_sampled(torch_cuda):
+    """The batched workload at full size (64 systems, N = 8..128, 512 walkers
+    each, refresh every 16 moves, every system autotuned, one graph over 16
+    streams): after one sweep, one sampled walker of each of five systems (the
+    smallest, the largest and three others) is recomputed by the oracle."""
+    torch = torch_cuda
+    import oracle
+    import paper_2002_07401_gb300 as pg
+    systems = synth.config3_systems(seed=0, n_systems=64)
+    W = 512
+    members, pos = [], []
+    for s in systems:
+        m = pg.JAGP(s, W, seed=0, precision=pg.JAGP_PREC_MIXED, refresh_moves=16)
+        p = m.positions(synth.init_walkers(s, W, seed=0))
+        m.eval(p)
+        m.autotune(p)
+        members.append(m)
+        pos.append(p)
+    b = pg.Batch(members, pos, n_streams=16)
+    b.sweep(1, sweep0=0)
+    torch.cuda.synchronize()
+    Ns = [s.N for s in systems]
+    picks = sorted({int(np.argmin(Ns)), int(np.argmax(Ns)), 5, 23, 41})
+    rng = np.random.default_rng(11)
+    for k in picks:
+        assert members[k].status() & (pg.WS_NONFINITE | pg.WS_SINGULAR) == 0, k
+        w = int(rng.integers(W))
+        x = np.ascontiguousarray(pos[k].cpu().numpy()[w:w + 1])
+        o = oracle.Oracle(systems[k])
+        la_ref, _ = o.logpsi_batch(x)
+        e_ref = o.local_energy_batch(x)
+        la = members[k].info()["logabs"].cpu().numpy()[w]
+        e = b.eL[k].cpu().numpy()[w]
+        assert abs(la - la_ref[0]) <= 1e-6, (k, la, la_ref[0])
+        assert abs(e - e_ref[0]) <= 1e-5, (k, e, e_ref[0])
+    b.close()
+    for m in members:
+        m.close()

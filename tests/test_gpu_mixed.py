@@ -154,3 +154,26 @@ def test_fp32_orbital_value_is_rounded_once(torch_cuda):
     err = np.abs(la.cpu().numpy() - exact)
     assert err.max() <= 2.0 ** -24 + 5e-9, err.max()
     g.close()
+
+
+def test_full_size_c2_mixed_sampled(torch_cuda):
+    """C2 at its full walker count (4096) in the mixed path, in the launch shape
+    the bench times (autotuned tiles): after two sweeps, four sampled walkers'
+    log|Psi| and e_L are recomputed by the oracle at their final positions."""
+    import paper_2002_07401_gb300 as pg
+    sysm = synth.config2()
+    W, sweeps = 4096, 2
+    g = pg.JAGP(sysm, W, precision=pg.JAGP_PREC_MIXED, seed=0)
+    r = g.positions(synth.init_walkers(sysm, W, seed=0))
+    g.autotune(r)
+    eL, _ = g.sweep(r, sweeps)
+    info = g.info()
+    assert g.status() & (pg.WS_NONFINITE | pg.WS_SINGULAR) == 0
+    pick = np.random.default_rng(7).choice(W, size=4, replace=False)
+    xs = np.ascontiguousarray(r.cpu().numpy()[pick])
+    o = oracle.Oracle(sysm)
+    la_ref, _ = o.logpsi_batch(xs)
+    e_ref = o.local_energy_batch(xs)
+    assert np.max(np.abs(info["logabs"].cpu().numpy()[pick] - la_ref)) <= LOGPSI_TOL
+    assert np.max(np.abs(eL.cpu().numpy()[-1, pick] - e_ref)) <= EL_TOL
+    g.close()
