@@ -193,3 +193,36 @@ def test_large_nup_gradients_match_oracle(torch_cuda):
         scale = max(1.0, np.abs(Rw[w]).max(), np.abs(rr[w]).max())
         assert np.abs(tot).max() <= 1e-9 * scale, (w, tot)
     g.close()
+
+
+def test_full_size_c4_logpsi_gradients_sampled(torch_cuda):
+    """The adjoint workload at full size (64 He, N = 128, L = 1536, 2048
+    walkers, after one sweep as the bench runs it): the per-walker nuclear and
+    electron gradients of sum_w s_w log|Psi_w| for two sampled walkers against
+    the oracle's analytic gradients, and their local energies."""
+    torch = torch_cuda
+    import paper_2002_07401_gb300 as pg
+    sysm = synth.config4()
+    W = 2048
+    g = pg.JAGP(sysm, W, seed=0)
+    r = g.positions(synth.init_walkers(sysm, W, seed=0))
+    g.eval(r)
+    eL, _ = g.sweep(r, 1)
+    assert g.status() & (pg.WS_NONFINITE | pg.WS_SINGULAR) == 0
+    seeds = np.random.default_rng(3).normal(size=W)
+    g.eval(r)
+    out = g.grad(r, seed_logpsi=torch.tensor(seeds, device="cuda"), want_lambda=False)
+    Rw = out["R_walker"].cpu().numpy()
+    rr = out["r"].cpu().numpy()
+    x_all = r.cpu().numpy()
+    o = oracle.Oracle(sysm)
+    for w in np.random.default_rng(4).choice(W, size=2, replace=False):
+        x = np.ascontiguousarray(x_all[w])
+        ref = o.grad_logpsi(x, want_lam=False)
+        ok, err = _close(Rw[w], seeds[w] * ref["R"], 1e-9)
+        assert ok, ("R", w, err)
+        ok, err = _close(rr[w], seeds[w] * ref["r"], 1e-9)
+        assert ok, ("r", w, err)
+        e_ref = o.local_energy(x)
+        assert abs(eL.cpu().numpy()[0, w] - e_ref) <= 1e-10 * max(1.0, abs(e_ref)), (w, e_ref)
+    g.close()
