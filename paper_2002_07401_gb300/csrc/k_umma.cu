@@ -21,7 +21,11 @@
 // One CTA computes a 128 x BN tile: warp 0 lane 0 issues the TMA loads, warp 1
 // lane 0 issues the MMAs (one per 16-wide K slice), all four warps drain the
 // accumulator from tensor memory (warp w owns TMEM lanes 32w..32w+31 = rows).
-// Every wait is bounded by the global timer; a timeout sets *err.
+// Stages hold one A and one B slice of a 64-wide K chunk, pair after pair; in
+// chunk-major mode (stages_max = -1, for long K) a stage holds every slice of
+// the chunk and the MMA thread issues all pairs from it.  CTAs walk kGroupM row
+// tiles of one column tile before the next, so that a wave shares operand
+// tiles in L2.  Every wait is bounded by the global timer; a timeout sets *err.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
