@@ -115,9 +115,6 @@ cudaError_t launch_pack_fixed(const float *P, const float *P_lo, const int *list
                                int nsub, int stride, int L, int kp, uint16_t *A, int *rows_out, int *exps,
                                int max_rows, cudaStream_t st);
 cudaError_t setup_umma_attributes();
-// FP32 rows -> compact three-term BF16 operand rows (see k_umma.cu)
-cudaError_t launch_pack_split3(const float *P, const int *list, const int *count, int nrows, int nsub, int stride,
-                               int L, int kp, uint16_t *A, int *rows_out, int max_rows, cudaStream_t st);
 
 // Reverse-mode derivatives (k_adjoint.cu); see that file for the formulas.
 cudaError_t launch_adj_kvec(const DevSystem &s, const double *r, const double *sE, double *jg, double *kbar,

@@ -530,49 +530,11 @@ cudaError_t launch_umma_gemm(const uint16_t *A, int m_max, const int *m_dev, int
 }
 
 // ---------------------------------------------------------------------------
-// Operand packing: FP32 orbital rows -> three BF16 terms (hi, mid, lo) side by
-// side, zero-padded to kp each, compacted in list order.  Row m of the output
-// comes from table row list[m] (m < *count) or, without a list, from
-// (m / nsub) * stride + m % nsub (m < nrows); rows_out[m] records it so the
-// contraction can write its result row back in place.  One warp per row.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_pack_split3(const float *__restrict__ P, const int *__restrict__ list,
-                                                     const int *__restrict__ count, int nrows, int nsub, int stride,
-                                                     int L, int kp, __nv_bfloat16 *__restrict__ A,
-                                                     int *__restrict__ rows_out) {
-  const int rows = count ? *count : nrows;
-  const int lane = threadIdx.x & 31;
-  const long nw = (long)gridDim.x * (blockDim.x >> 5);
-  for (long m = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); m < rows; m += nw) {
-    const long phys = list ? (long)list[m] : (m / nsub) * stride + (m % nsub);
-    if (lane == 0) rows_out[m] = (int)phys;
-    const float *src = P + phys * L;
-    __nv_bfloat16 *dst = A + m * 3 * (long)kp;
-    for (int k = lane; k < kp; k += 32) {
-      const float v = k < L ? src[k] : 0.0f;
-      const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-      const float r1 = v - __bfloat162float(hi);
-      const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
-      const float r2 = r1 - __bfloat162float(mid);
-      dst[k] = hi;
-      dst[kp + k] = mid;
-      dst[2 * kp + k] = __float2bfloat16_rn(r2);
-    }
-  }
-}
-
-cudaError_t launch_pack_split3(const float *P, const int *list, const int *count, int nrows, int nsub, int stride,
-                               int L, int kp, uint16_t *A, int *rows_out, int max_rows, cudaStream_t st) {
-  if (max_rows <= 0) return cudaSuccess;
-  long blocks = (max_rows + 7) / 8;
-  if (blocks > 152 * 16) blocks = 152 * 16;
-  k_pack_split3<<<(int)blocks, 256, 0, st>>>(P, list, count, nrows, nsub > 0 ? nsub : 1, stride, L, kp,
-                                              reinterpret_cast<__nv_bfloat16 *>(A), rows_out);
-  return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------------------
-// Fixed-point operand packing: each FP32 row (compacted as above) is scaled by
+// Fixed-point operand packing.  Operand rows are compacted in list order: row
+// m comes from table row list[m] (m < *count) or, without a list, from
+// (m / nsub) * stride + m % nsub (m < nrows); rows_out[m] records it so that
+// the contraction can write its result row back in place.  One warp per row.
+// Each FP32 row is scaled by
 // 2^-e (e = 1 + the binary exponent of its largest magnitude) and cut into
 // kFixedSlices exact 8-bit integer slices t0, t1, ... (|t| <= 128), stored as
 // BF16 side by side, with e in exps[m].  Every step of the cut is exact in
