@@ -27,8 +27,11 @@
  * paper's definition.
  *
  * Parity status: pinned (see tests/test_oracle_pins.py) for the basis, the
- * determinant, the Jastrow, the local energy, the sampler and log|Psi|
- * gradients.
+ * determinant (symmetric and non-symmetric lambda), the Jastrow, the local
+ * energy, the sampler, log|Psi| gradients and the finite-difference references
+ * for d e_L / d R_a, d e_L / d r_i (closed forms of the He product and of an
+ * off-centre Slater orbital between two nuclei; the translation sum rule) and
+ * d e_L / d lambda (closed form of a two-orbital geminal; Euler's identity).
  */
 #include <math.h>
 #include <stdint.h>

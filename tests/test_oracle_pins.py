@@ -399,3 +399,142 @@ def test_cusp_conditions():
     x1 = np.array([s.R[0] + [1e-7, 0, 0], [far, far, far], [-far, far, -far]])
     x2 = np.array([s.R[0] + [2e-7, 0, 0], [far, far, far], [-far, far, -far]])
     assert abs((o.jastrow(x2) - o.jastrow(x1)) / 1e-7 - (-2.0)) < 1e-5
+
+
+# ----------------------------------------------------------------------------
+# the finite-difference references for d e_L / d R_a, d e_L / d r_i and
+# d e_L / d lambda (Sec. "Atomic forces", Eq. forces:aad; Sec. "Derivatives
+# with respect to variational parameters"), pinned to closed forms
+# ----------------------------------------------------------------------------
+
+def test_elocal_grad_fd_helium_closed_form():
+    """He with psi = exp(-beta (r1 + r2)) around a nucleus at R:
+    e_L = -beta^2 + (beta - Z)(1/|r1-R| + 1/|r2-R|) + 1/r12, so
+    d e_L/d r1 = -(beta - Z)(r1-R)/|r1-R|^3 - (r1-r2)/r12^3 and
+    d e_L/d R = (beta - Z) sum_i (r_i-R)/|r_i-R|^3."""
+    beta, Z = 1.45, 2.0
+    s = synth.helium_slater(beta)
+    s.R = np.ascontiguousarray(np.array([[0.3, -0.2, 0.5]]))
+    o = oracle.Oracle(s)
+    rng = np.random.default_rng(40)
+    for _ in range(6):
+        x = s.R + rng.normal(0, 1.0, size=(2, 3))
+        d = x - s.R
+        r = np.linalg.norm(d, axis=1)
+        r12v = x[0] - x[1]
+        r12 = np.linalg.norm(r12v)
+        ref_r = -(beta - Z) * d / r[:, None] ** 3
+        ref_r[0] -= r12v / r12 ** 3
+        ref_r[1] += r12v / r12 ** 3
+        ref_R = (beta - Z) * (d / r[:, None] ** 3).sum(0)
+        dR, dr = o.elocal_grad(x, h=1e-3)
+        scale = 1.0 + np.abs(ref_r).max()
+        assert np.allclose(dr, ref_r, rtol=0, atol=1e-8 * scale), (dr, ref_r)
+        assert np.allclose(dR[0], ref_R, rtol=0, atol=1e-8 * scale), (dR, ref_R)
+
+
+def test_elocal_grad_fd_off_centre_slater_two_nuclei():
+    """One electron in exp(-beta |r - R0|) with nuclei Z0 at R0 and Z1 at R1:
+    e_L = -beta^2/2 + (beta - Z0)/d0 - Z1/d1 + Z0 Z1/|R0 - R1|; the nuclear
+    derivatives carry the orbital's centre, the second nucleus and V_ii."""
+    beta, Z0, Z1 = 1.3, 1.0, 2.0
+    R = np.array([[0.1, 0.2, -0.3], [1.4, -0.6, 0.9]])
+    s = synth.System("slater-off-centre", R, np.array([Z0, Z1]), np.array([0], np.int32),
+                     np.array([0], np.int32), np.array([1], np.int32), np.array([beta]),
+                     np.zeros((1, 1)), 1, 0, unpaired=np.ones((1, 1)), use_j1=False,
+                     use_j2=False, delta=1.0).check()
+    o = oracle.Oracle(s)
+    rng = np.random.default_rng(41)
+    for _ in range(6):
+        x = (R[0] + rng.normal(0, 0.8, size=3))[None]
+        d0, d1 = x[0] - R[0], x[0] - R[1]
+        n0, n1 = np.linalg.norm(d0), np.linalg.norm(d1)
+        R01 = R[0] - R[1]
+        n01 = np.linalg.norm(R01)
+        e = -beta ** 2 / 2 + (beta - Z0) / n0 - Z1 / n1 + Z0 * Z1 / n01
+        assert abs(o.local_energy(x) - e) < 1e-12 * (1 + abs(e))
+        ref_r = -(beta - Z0) * d0 / n0 ** 3 + Z1 * d1 / n1 ** 3
+        ref_R0 = (beta - Z0) * d0 / n0 ** 3 - Z0 * Z1 * R01 / n01 ** 3
+        ref_R1 = -Z1 * d1 / n1 ** 3 + Z0 * Z1 * R01 / n01 ** 3
+        dR, dr = o.elocal_grad(x, h=1e-3)
+        scale = 1.0 + np.abs(ref_r).max()
+        assert np.allclose(dr[0], ref_r, rtol=0, atol=1e-8 * scale)
+        assert np.allclose(dR[0], ref_R0, rtol=0, atol=1e-8 * scale)
+        assert np.allclose(dR[1], ref_R1, rtol=0, atol=1e-8 * scale)
+
+
+def test_elocal_dlambda_fd_two_orbital_geminal_closed_form():
+    """Two electrons (one up, one down) in the geminal psi = sum lambda_{mu,nu}
+    phi_mu(r1) phi_nu(r2) of two Slater s orbitals (Eq. agp_expansion with
+    L = 2, non-symmetric lambda).  With t_{mu,nu} the kinetic energy of the
+    product phi_mu(r1) phi_nu(r2) over itself and p_{mu,nu} the product,
+    d e_L / d lambda_{mu,nu} = p_{mu,nu} (t_{mu,nu} - T) / psi, T = (H - V) psi / psi.
+    Summed against lambda this is Euler's identity for e_L(c lambda) = e_L(lambda)."""
+    zeta = np.array([1.7, 0.6])
+    lam = np.array([[1.0, 0.35], [-0.2, 0.8]])
+    s = synth.System("2-orbital geminal", np.zeros((1, 3)), np.array([2.0]), np.array([0, 0], np.int32),
+                     np.array([0, 0], np.int32), np.array([1, 1], np.int32), zeta, lam, 1, 1,
+                     use_j1=False, use_j2=False, delta=0.6).check()
+    o = oracle.Oracle(s)
+    rng = np.random.default_rng(42)
+    for _ in range(4):
+        x = rng.normal(0, 0.9, size=(2, 3))
+        r1, r2 = np.linalg.norm(x[0]), np.linalg.norm(x[1])
+        phi1, phi2 = np.exp(-zeta * r1), np.exp(-zeta * r2)
+        p = np.outer(phi1, phi2)
+        k1 = -0.5 * (zeta ** 2 - 2 * zeta / r1)      # -1/2 lap phi / phi at r1
+        k2 = -0.5 * (zeta ** 2 - 2 * zeta / r2)
+        t = k1[:, None] + k2[None, :]
+        psi = (lam * p).sum()
+        T = (lam * t * p).sum() / psi
+        V = -2.0 / r1 - 2.0 / r2 + 1.0 / np.linalg.norm(x[0] - x[1])
+        assert abs(o.local_energy(x) - (T + V)) < 1e-11 * (1 + abs(T + V))
+        ref = p * (t - T) / psi
+        got = np.array([[o.elocal_dlambda(x, mu, nu, h=1e-4) for nu in range(2)] for mu in range(2)])
+        assert np.allclose(got, ref, rtol=1e-8, atol=1e-9), (got, ref)
+        assert abs((lam * got).sum()) < 1e-8 * (1 + np.abs(got).max())
+
+
+def test_elocal_dlambda_fd_euler_identity_random_system():
+    """e_L is invariant under lambda -> c lambda (N_up = N_dn), so
+    sum lambda_{mu,nu} d e_L / d lambda_{mu,nu} = 0 for every configuration
+    (non-symmetric lambda, Jastrow on, s/p/d shells)."""
+    s = synth.small_random(n_atoms=2, n_up=2, n_dn=2, per_atom=6, seed=43, symmetric=False,
+                           slater_fraction=0.3)
+    o = oracle.Oracle(s)
+    x = _rand_cfg(s, 44)
+    g = np.array([[o.elocal_dlambda(x, mu, nu, h=1e-4) for nu in range(s.L)] for mu in range(s.L)])
+    assert np.abs(g).max() > 1e-3
+    assert abs((s.lam * g).sum()) < 1e-8 * np.abs(s.lam * g).sum()
+
+
+def test_elocal_grad_fd_translation_sum():
+    """Rigid translation leaves e_L unchanged: sum_a d e_L/d R_a + sum_i d e_L/d r_i = 0
+    (J1, J2 and d shells on; pins the nuclear and electronic loops jointly)."""
+    s = synth.small_random(n_atoms=3, n_up=3, n_dn=2, per_atom=20, seed=45, slater_fraction=0.2)
+    o = oracle.Oracle(s)
+    x = _rand_cfg(s, 46)
+    dR, dr = o.elocal_grad(x, h=1e-3)
+    scale = np.abs(dR).max() + np.abs(dr).max()
+    assert scale > 1e-2
+    assert np.allclose(dR.sum(0) + dr.sum(0), 0.0, atol=1e-8 * scale)
+
+
+def test_agp_nonsymmetric_rank_n_lambda():
+    """lambda = C D^T (non-symmetric, rank n): G~ = (Phi_up C)(Phi_dn D)^T, so
+    det G~ = det(Phi_up C) det(Phi_dn D); a transposed lambda would give
+    det(Phi_up D) det(Phi_dn C) instead (Eq. agp_expansion, Sec. SD)."""
+    s = synth.small_random(n_atoms=3, n_up=3, n_dn=3, per_atom=6, seed=47, use_j1=False, use_j2=False)
+    rng = np.random.default_rng(47)
+    Cm, Dm = rng.normal(size=(s.L, 3)), rng.normal(size=(s.L, 3))
+    s.lam = np.ascontiguousarray(Cm @ Dm.T)
+    o = oracle.Oracle(s)
+    x = _rand_cfg(s, 48)
+    phi = np.stack([o.ao(x[i])[0] for i in range(s.N)])
+    ref = np.linalg.det(phi[:3] @ Cm) * np.linalg.det(phi[3:] @ Dm)
+    wrong = np.linalg.det(phi[:3] @ Dm) * np.linalg.det(phi[3:] @ Cm)
+    assert abs(ref - wrong) > 1e-3 * abs(ref)
+    G = o.geminal(x)
+    assert abs(np.linalg.det(G) - ref) < 1e-10 * abs(ref)
+    la, sg, ld, J = o.logpsi(x)
+    assert abs(ld - math.log(abs(ref))) < 1e-10 and sg == np.sign(ref)
