@@ -187,7 +187,9 @@ jagp_status_t jagp_walker_info(jagp_handle_t h, const void *d_state, int W, doub
                                double *d_sign, double *d_naccept, double *d_drift, int *d_status,
                                void *stream);
 
-/* OR of the status bits of all W walkers.  Synchronises `stream`. */
+/* OR of the status bits of all W walkers.  Synchronises `stream`.  Returns
+ * JAGP_ERR_TIMEOUT if a bounded wait of the handle's tensor-core pipeline
+ * expired in an earlier call (the bits are still written). */
 jagp_status_t jagp_walker_status(jagp_handle_t h, const void *d_state, int W, int *h_bits,
                                  void *stream);
 
@@ -272,10 +274,13 @@ long long jagp_launch_count(jagp_handle_t h);
  * callers that cannot allocate device memory when they need log|Psi| (code
  * running under an allocator or memory pool that forbids new reservations, a
  * host framework that owns every allocation, a loop that must not touch the
- * allocator).  It computes the same d_logabs and d_sign [W] as jagp_eval for
- * the configurations d_r [W][N][3], keeping its scratch in one file-scope
- * device array of JAGP_NOALLOC_SCRATCH_BYTES that every GPU loading the
- * library holds until the process exits.
+ * allocator).  It computes d_logabs and d_sign [W] for the configurations
+ * d_r [W][N][3] always in FP64, whatever the handle's precision: on an FP64
+ * handle the same values as jagp_eval, on a mixed-precision handle the FP64
+ * values (jagp_eval's mixed-precision log|Psi| differs from them by at most its
+ * stated 1e-6).  Its scratch is one file-scope device array of
+ * JAGP_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until the
+ * process exits.  Its kernels count towards jagp_launch_count.
  *   - Allocates nothing: no cudaMalloc, cudaFree or allocating library call
  *     (jagp_create still allocates the handle's tables once, at set-up).
  *   - W whose scratch (about 4 N_up L + 2 N_up^2 doubles per walker) exceeds
@@ -293,6 +298,20 @@ jagp_status_t jagp_eval_noalloc(jagp_handle_t h, const double *d_r, int W, doubl
 const char *jagp_status_string(jagp_status_t s);
 /* The text of the last CUDA runtime error behind a JAGP_ERR_CUDA of this thread. */
 const char *jagp_last_cuda_error(void);
+
+/* The last failure recorded on handle h (Sec. "Implementation and operations"
+ * has no counterpart: a diagnostic of this library).  Every entry point that
+ * takes h records a non-OK return as one line "<entry point>: <status text>"
+ * followed by the CUDA error text behind a JAGP_ERR_CUDA and, where the failing
+ * check gives one, the offending value (e.g. "W = 5 outside 1..4").
+ * jagp_walker_status also records which walkers carry status bits (the device
+ * status words) without failing, and returns JAGP_ERR_TIMEOUT when a bounded
+ * tensor-core pipeline wait of this handle expired.  buf (host, may be NULL)
+ * receives the text, truncated to len - 1 characters and NUL-terminated.
+ * Returns the status of the last failure (JAGP_OK if none), or
+ * JAGP_ERR_INVALID_ARG for a NULL handle.  Host-only; not thread-safe against
+ * concurrent calls on the same handle. */
+jagp_status_t jagp_last_error(jagp_handle_t h, char *buf, size_t len);
 
 #ifdef __cplusplus
 }

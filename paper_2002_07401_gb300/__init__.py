@@ -98,6 +98,8 @@ def lib():
         L.jagp_eval_noalloc.restype = i
         L.jagp_last_cuda_error.argtypes = []
         L.jagp_last_cuda_error.restype = C.c_char_p
+        L.jagp_last_error.argtypes = [vp, C.c_char_p, C.c_size_t]
+        L.jagp_last_error.restype = i
         L.jagp_status_string.argtypes = [i]
         L.jagp_status_string.restype = C.c_char_p
         for f in ("jagp_create", "jagp_destroy", "jagp_eval", "vmc_sweep", "local_energy",
@@ -111,12 +113,21 @@ def library_path() -> str:
     return _build.LIB
 
 
-def _check(status: int, what: str):
+def _check(status: int, what: str, h=None):
     if status != JAGP_OK:
         msg = lib().jagp_status_string(status).decode()
-        if status == 7:
+        if h:
+            msg = jagp_last_error(h)[1]
+        elif status == 7:
             msg += ": " + lib().jagp_last_cuda_error().decode()
         raise JagpError(f"{what} failed: {msg} (status {status})")
+
+
+def jagp_last_error(h):
+    """(status, text) of the last failure recorded on handle h."""
+    buf = C.create_string_buffer(512)
+    st = lib().jagp_last_error(h, buf, len(buf))
+    return int(st), buf.value.decode()
 
 
 def _ptr(t) -> Optional[int]:
@@ -181,7 +192,7 @@ def jagp_state_bytes(h: int, W: int) -> int:
 
 def jagp_eval(h, r, W, state, logabs=None, sign=None, stream=None):
     _check(lib().jagp_eval(h, _ptr(r), int(W), _ptr(state), _ptr(logabs), _ptr(sign), _stream(stream)),
-           "jagp_eval")
+           "jagp_eval", h)
 
 
 NOALLOC_SCRATCH_BYTES = 32 << 20
@@ -193,17 +204,17 @@ def jagp_eval_noalloc(h, r, W, logabs=None, sign=None, stream=None):
     by all calls (serialise calls; the first call on a device must precede any
     stream capture).  Raises for W whose scratch does not fit."""
     _check(lib().jagp_eval_noalloc(h, _ptr(r), int(W), _ptr(logabs), _ptr(sign), _stream(stream)),
-           "jagp_eval_noalloc")
+           "jagp_eval_noalloc", h)
 
 
 def vmc_sweep(h, r, state, W, nsweeps, walker0=0, sweep0=0, eL=None, acc=None, stream=None):
     _check(lib().vmc_sweep(h, _ptr(r), _ptr(state), int(W), int(nsweeps), int(walker0), int(sweep0),
-                           _ptr(eL), _ptr(acc), _stream(stream)), "vmc_sweep")
+                           _ptr(eL), _ptr(acc), _stream(stream)), "vmc_sweep", h)
 
 
 def local_energy(h, r, state, W, eL, parts=None, stream=None):
     _check(lib().local_energy(h, _ptr(r), _ptr(state), int(W), _ptr(eL), _ptr(parts), _stream(stream)),
-           "local_energy")
+           "local_energy", h)
 
 
 def jagp_grad_workspace_bytes(h, W) -> int:
@@ -214,18 +225,18 @@ def jagp_grad(h, r, state, W, work, seed_logpsi=None, seed_eL=None, eL=None, dla
               dR_walker=None, dr=None, stream=None):
     _check(lib().jagp_grad(h, _ptr(r), _ptr(state), int(W), _ptr(seed_logpsi), _ptr(seed_eL), _ptr(work), _ptr(eL),
                            _ptr(dlambda), _ptr(djas), _ptr(dR), _ptr(dR_walker), _ptr(dr), _stream(stream)),
-           "jagp_grad")
+           "jagp_grad", h)
 
 
 def jagp_walker_info(h, state, W, logabs=None, sign=None, naccept=None, drift=None, status=None, stream=None):
     _check(lib().jagp_walker_info(h, _ptr(state), int(W), _ptr(logabs), _ptr(sign), _ptr(naccept), _ptr(drift),
-                                  _ptr(status), _stream(stream)), "jagp_walker_info")
+                                  _ptr(status), _stream(stream)), "jagp_walker_info", h)
 
 
 def jagp_walker_status(h, state, W, stream=None) -> int:
     bits = C.c_int(0)
     _check(lib().jagp_walker_status(h, _ptr(state), int(W), C.byref(bits), _stream(stream)),
-           "jagp_walker_status")
+           "jagp_walker_status", h)
     return bits.value
 
 
@@ -251,13 +262,13 @@ KERNEL_LAMBDA_ROWS, KERNEL_GEMM_ROWS, KERNEL_METROPOLIS, KERNEL_BASIS, KERNEL_EN
 
 
 def jagp_profile(h, kernel: int, enable: bool = True):
-    _check(lib().jagp_profile(h, int(kernel), int(bool(enable))), "jagp_profile")
+    _check(lib().jagp_profile(h, int(kernel), int(bool(enable))), "jagp_profile", h)
 
 
 def jagp_profile_read(h):
     """(summed device milliseconds, launches) of the profiled kernel; synchronises its events."""
     ms, n = C.c_double(0.0), C.c_longlong(0)
-    _check(lib().jagp_profile_read(h, C.byref(ms), C.byref(n)), "jagp_profile_read")
+    _check(lib().jagp_profile_read(h, C.byref(ms), C.byref(n)), "jagp_profile_read", h)
     return ms.value, n.value
 
 
@@ -272,7 +283,7 @@ def jagp_launch_count(h) -> int:
 def jagp_autotune(h, state, W, stream=None) -> dict:
     """Tile autotuner (see include/jagp.h); returns the choices and best times."""
     t = _Tuning()
-    _check(lib().jagp_autotune(h, _ptr(state), int(W), C.byref(t), _stream(stream)), "jagp_autotune")
+    _check(lib().jagp_autotune(h, _ptr(state), int(W), C.byref(t), _stream(stream)), "jagp_autotune", h)
     return {"tile_proposals": t.tile_proposals, "tile_refresh": t.tile_refresh, "umma_bn_left": t.umma_bn_left,
             "umma_bn_right": t.umma_bn_right, "umma_stages_left": t.umma_stages_left,
             "umma_stages_right": t.umma_stages_right, "ms": [float(v) for v in t.ms]}
@@ -285,7 +296,7 @@ def jagp_set_tuning(h, tuning: dict) -> None:
     t.tile_refresh = int(tuning.get("tile_refresh", -1))
     for k in ("umma_bn_left", "umma_bn_right", "umma_stages_left", "umma_stages_right"):
         setattr(t, k, int(tuning.get(k, 0)))
-    _check(lib().jagp_set_tuning(h, C.byref(t)), "jagp_set_tuning")
+    _check(lib().jagp_set_tuning(h, C.byref(t)), "jagp_set_tuning", h)
 
 
 class JAGP:
@@ -432,8 +443,10 @@ def _autograd_function():
     class LogPsiLocalEnergy(torch.autograd.Function):
         """(log|Psi|, e_L) of W configurations as a differentiable function of
         (lambda, Jastrow parameters, R, r); the backward pass is the library's
-        adjoint (jagp_grad).  The Jastrow-parameter gradient is that of log|Psi|
-        only (d e_L / d b is not formed).  The tensors lam, jas, R must hold the
+        adjoint (jagp_grad).  The library forms the Jastrow-parameter gradient
+        of log|Psi| only (not d e_L / d b): a backward pass in which a non-zero
+        e_L gradient would reach the Jastrow parameters raises instead of
+        returning an incomplete gradient.  The tensors lam, jas, R must hold the
         values the JAGP object was created with."""
 
         @staticmethod
@@ -449,6 +462,9 @@ def _autograd_function():
         def backward(ctx, g_log, g_el):
             (r,) = ctx.saved_tensors
             g = ctx.g
+            if ctx.needs_input_grad[2] and g_el is not None and bool((g_el != 0).any()):
+                raise JagpError("d e_L / d (Jastrow parameters) is not formed by jagp_grad: detach the "
+                                "Jastrow parameters or keep e_L out of the loss")
             g.eval(r)
             out = g.grad(r, seed_logpsi=g_log, seed_eL=g_el, want_lambda=ctx.needs_input_grad[1])
             return None, out["lam"], out["jas"], out["R"], out["r"]

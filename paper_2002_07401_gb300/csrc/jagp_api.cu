@@ -17,12 +17,16 @@ using namespace jagp;
 
 #include "jagp_ctx.h"
 
+#include <stdarg.h>
+#include <stdio.h>
+
 namespace {
 
 std::once_flag g_attr_once;
 cudaError_t g_attr_err = cudaSuccess;
 
 thread_local const char *g_last_cuda_error = "no error";
+thread_local char g_detail[256] = "";
 
 #define JAGP_CU(call)                                  \
   do {                                                 \
@@ -123,8 +127,14 @@ int slice_row_fixed(const double *v, size_t vstride, int L, uint16_t *dst, size_
 
 jagp_status_t check_walkers(const jagp_ctx *h, int W, const void *state) {
   if (!h) return JAGP_ERR_INVALID_ARG;
-  if (W <= 0 || W > h->max_walkers) return JAGP_ERR_INVALID_ARG;
-  if (!state || (reinterpret_cast<uintptr_t>(state) & 255u)) return JAGP_ERR_INVALID_ARG;
+  if (W <= 0 || W > h->max_walkers) {
+    jagp_set_detail("W = %d outside 1..%d (max_walkers)", W, h->max_walkers);
+    return JAGP_ERR_INVALID_ARG;
+  }
+  if (!state || (reinterpret_cast<uintptr_t>(state) & 255u)) {
+    jagp_set_detail("walker state is null or not 256-byte aligned");
+    return JAGP_ERR_INVALID_ARG;
+  }
   return JAGP_OK;
 }
 
@@ -254,7 +264,7 @@ jagp_status_t run_eval(jagp_ctx *h, const double *d_r, int W, void *d_state, dou
   const int n = d.n_up;
   T *phi_up = at<T>(d_state, L.phi_up), *pprop = at<T>(d_state, L.pprop);
   float *phi_lo = lo_table(h, d_state, L.phi_lo), *pprop_lo = lo_table(h, d_state, L.pprop_lo);
-  LAUNCH(0, 1, launch_walker_init(at<double>(d_state, L.scal), at<int>(d_state, L.status), W, st));
+  LAUNCH(0, 1, launch_walker_init(at<double>(d_state, L.scal), at<int>(d_state, L.status), W, st, d_r, d.N));
   LAUNCH(JAGP_KERNEL_BASIS, 1, launch_basis_points<T>(d, false, d_r, W, 0, n, phi_up, phi_lo, nullptr, 0, 0, st));
   LAUNCH(JAGP_KERNEL_BASIS, d.n_dn > 0,
          launch_basis_points<T>(d, false, d_r, W, n, d.n_dn, pprop, pprop_lo, nullptr, 0, 0, st));
@@ -393,6 +403,26 @@ GradLayout grad_layout(const jagp_ctx *h, int W) {
 
 }  // namespace
 
+void jagp_set_cuda_error(cudaError_t e) { g_last_cuda_error = cudaGetErrorString(e); }
+
+void jagp_set_detail(const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_detail, sizeof(g_detail), fmt, ap);
+  va_end(ap);
+}
+
+jagp_status_t jagp_note(jagp_ctx *h, const char *fn, jagp_status_t s) {
+  if (s != JAGP_OK && h) {
+    h->last_status = s;
+    snprintf(h->last_error, sizeof(h->last_error), "%s: %s%s%s%s%s", fn, jagp_status_string(s),
+             s == JAGP_ERR_CUDA ? ": " : "", s == JAGP_ERR_CUDA ? g_last_cuda_error : "", g_detail[0] ? ": " : "",
+             g_detail);
+  }
+  g_detail[0] = 0;
+  return s;
+}
+
 extern "C" {
 
 size_t jagp_grad_workspace_bytes(jagp_handle_t h, int W) {
@@ -400,7 +430,7 @@ size_t jagp_grad_workspace_bytes(jagp_handle_t h, int W) {
   return grad_layout(h, W).total;
 }
 
-jagp_status_t jagp_grad(jagp_handle_t h, const double *d_r, void *d_state, int W, const double *d_seed_logpsi,
+static jagp_status_t jagp_grad_impl(jagp_handle_t h, const double *d_r, void *d_state, int W, const double *d_seed_logpsi,
                         const double *d_seed_eL, void *d_work, double *d_eL, double *d_dlambda, double *d_djas,
                         double *d_dR, double *d_dR_walker, double *d_dr, void *stream) {
   jagp_status_t s = check_walkers(h, W, d_state);
@@ -687,7 +717,7 @@ size_t jagp_state_bytes(jagp_handle_t h, int W) {
   return layout_of(h, W).total;
 }
 
-jagp_status_t jagp_eval(jagp_handle_t h, const double *d_r, int W, void *d_state, double *d_logabs,
+static jagp_status_t jagp_eval_impl(jagp_handle_t h, const double *d_r, int W, void *d_state, double *d_logabs,
                         double *d_sign, void *stream) {
   jagp_status_t s = check_walkers(h, W, d_state);
   if (s != JAGP_OK) return s;
@@ -834,7 +864,7 @@ jagp_status_t tune_products(jagp_ctx *h, void *state, int W, cudaStream_t st, ja
 
 extern "C" {
 
-jagp_status_t jagp_autotune(jagp_handle_t h, void *d_state, int W, jagp_tuning_t *out, void *stream) {
+static jagp_status_t jagp_autotune_impl(jagp_handle_t h, void *d_state, int W, jagp_tuning_t *out, void *stream) {
   jagp_status_t s = check_walkers(h, W, d_state);
   if (s != JAGP_OK) return s;
   if (!out) return JAGP_ERR_INVALID_ARG;
@@ -847,7 +877,7 @@ jagp_status_t jagp_autotune(jagp_handle_t h, void *d_state, int W, jagp_tuning_t
   return JAGP_OK;
 }
 
-jagp_status_t jagp_set_tuning(jagp_handle_t h, const jagp_tuning_t *t) {
+static jagp_status_t jagp_set_tuning_impl(jagp_handle_t h, const jagp_tuning_t *t) {
   if (!h || !t) return JAGP_ERR_INVALID_ARG;
   const bool mixed = h->precision == JAGP_PREC_MIXED;
   auto tile_ok = [](int v, bool allow16) { return v == -1 || v == 0 || v == 32 || v == 64 || (allow16 && v == 16); };
@@ -879,7 +909,7 @@ jagp_status_t jagp_set_tuning(jagp_handle_t h, const jagp_tuning_t *t) {
   return JAGP_OK;
 }
 
-jagp_status_t vmc_sweep(jagp_handle_t h, double *d_r, void *d_state, int W, int nsweeps, uint64_t walker0,
+static jagp_status_t vmc_sweep_impl(jagp_handle_t h, double *d_r, void *d_state, int W, int nsweeps, uint64_t walker0,
                         uint64_t sweep0, double *d_eL, double *d_acc, void *stream) {
   jagp_status_t s = check_walkers(h, W, d_state);
   if (s != JAGP_OK) return s;
@@ -892,7 +922,7 @@ jagp_status_t vmc_sweep(jagp_handle_t h, double *d_r, void *d_state, int W, int 
   return run_sweeps<double>(h, d_r, d_state, W, nsweeps, walker0, sweep0, d_eL, d_acc, st);
 }
 
-jagp_status_t local_energy(jagp_handle_t h, const double *d_r, void *d_state, int W, double *d_eL,
+static jagp_status_t local_energy_impl(jagp_handle_t h, const double *d_r, void *d_state, int W, double *d_eL,
                            double *d_parts, void *stream) {
   jagp_status_t s = check_walkers(h, W, d_state);
   if (s != JAGP_OK) return s;
@@ -928,13 +958,13 @@ jagp_status_t jagp_gemm_bf16x(const uint16_t *d_A, int M, int a_terms, const uin
   return e == cudaSuccess ? JAGP_OK : JAGP_ERR_CUDA;
 }
 
-jagp_status_t jagp_profile(jagp_handle_t h, int kernel, int enable) {
+static jagp_status_t jagp_profile_impl(jagp_handle_t h, int kernel, int enable) {
   if (!h || kernel < 1 || kernel > JAGP_KERNEL_ENERGY) return JAGP_ERR_INVALID_ARG;
   h->prof_kernel = enable ? kernel : 0;
   return JAGP_OK;
 }
 
-jagp_status_t jagp_profile_read(jagp_handle_t h, double *h_total_ms, long long *h_launches) {
+static jagp_status_t jagp_profile_read_impl(jagp_handle_t h, double *h_total_ms, long long *h_launches) {
   if (!h || !h_total_ms || !h_launches) return JAGP_ERR_INVALID_ARG;
   double tot = 0.0;
   jagp_status_t rc = JAGP_OK;
@@ -955,7 +985,7 @@ jagp_status_t jagp_profile_read(jagp_handle_t h, double *h_total_ms, long long *
 long long jagp_launch_count(jagp_handle_t h) { return h ? h->launches : -1;
 }
 
-jagp_status_t jagp_walker_info(jagp_handle_t h, const void *d_state, int W, double *d_logabs, double *d_sign,
+static jagp_status_t jagp_walker_info_impl(jagp_handle_t h, const void *d_state, int W, double *d_logabs, double *d_sign,
                                double *d_naccept, double *d_drift, int *d_status, void *stream) {
   jagp_status_t s = check_walkers(h, W, d_state);
   if (s != JAGP_OK) return s;
@@ -967,7 +997,7 @@ jagp_status_t jagp_walker_info(jagp_handle_t h, const void *d_state, int W, doub
   return JAGP_OK;
 }
 
-jagp_status_t jagp_walker_status(jagp_handle_t h, const void *d_state, int W, int *h_bits, void *stream) {
+static jagp_status_t jagp_walker_status_impl(jagp_handle_t h, const void *d_state, int W, int *h_bits, void *stream) {
   jagp_status_t s = check_walkers(h, W, d_state);
   if (s != JAGP_OK) return s;
   if (!h_bits) return JAGP_ERR_INVALID_ARG;
@@ -977,9 +1007,26 @@ jagp_status_t jagp_walker_status(jagp_handle_t h, const void *d_state, int W, in
   JAGP_CU(cudaMemcpyAsync(bits.data(), static_cast<const char *>(d_state) + L.status, (size_t)W * sizeof(int),
                           cudaMemcpyDeviceToHost, st));
   JAGP_CU(cudaStreamSynchronize(st));
-  int o = 0;
-  for (int w = 0; w < W; ++w) o |= bits[w];
+  int o = 0, nbad = 0;
+  for (int w = 0; w < W; ++w) {
+    o |= bits[w];
+    nbad += bits[w] != 0;
+  }
   *h_bits = o;
+  // a tensor-core pipeline wait that ran out of time leaves its flag set
+  int err = 0;
+  JAGP_CU(cudaMemcpy(&err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (err) {
+    jagp_set_detail("a tensor-core pipeline wait expired (flag %d)", err);
+    return JAGP_ERR_TIMEOUT;
+  }
+  if (nbad) {
+    // not a failure of the call: the text records which walkers carry bits
+    h->last_status = JAGP_OK;
+    snprintf(h->last_error, sizeof(h->last_error),
+             "jagp_walker_status: %d of %d walkers with status bits 0x%x (1 NONFINITE, 2 SINGULAR, 4 DRIFT)", nbad, W,
+             o);
+  }
   return JAGP_OK;
 }
 
@@ -1147,6 +1194,64 @@ jagp_status_t jagp_batch_destroy(jagp_batch_t b) {
   if (b->counter) cudaFree(b->counter);
   delete b;
   return JAGP_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Entry points: each records a failure in the handle for jagp_last_error.
+// ---------------------------------------------------------------------------
+extern "C" {
+jagp_status_t jagp_eval(jagp_handle_t h, const double *d_r, int W, void *d_state, double *d_logabs,
+                        double *d_sign, void *stream) {
+  return jagp_note(h, "jagp_eval", jagp_eval_impl(h, d_r, W, d_state, d_logabs, d_sign, stream));
+}
+
+jagp_status_t vmc_sweep(jagp_handle_t h, double *d_r, void *d_state, int W, int nsweeps, uint64_t walker0,
+                        uint64_t sweep0, double *d_eL, double *d_acc, void *stream) {
+  return jagp_note(h, "vmc_sweep", vmc_sweep_impl(h, d_r, d_state, W, nsweeps, walker0, sweep0, d_eL, d_acc, stream));
+}
+
+jagp_status_t local_energy(jagp_handle_t h, const double *d_r, void *d_state, int W, double *d_eL,
+                           double *d_parts, void *stream) {
+  return jagp_note(h, "local_energy", local_energy_impl(h, d_r, d_state, W, d_eL, d_parts, stream));
+}
+
+jagp_status_t jagp_grad(jagp_handle_t h, const double *d_r, void *d_state, int W, const double *d_seed_logpsi,
+                        const double *d_seed_eL, void *d_work, double *d_eL, double *d_dlambda, double *d_djas,
+                        double *d_dR, double *d_dR_walker, double *d_dr, void *stream) {
+  return jagp_note(h, "jagp_grad", jagp_grad_impl(h, d_r, d_state, W, d_seed_logpsi, d_seed_eL, d_work, d_eL, d_dlambda, d_djas, d_dR, d_dR_walker, d_dr, stream));
+}
+
+jagp_status_t jagp_walker_info(jagp_handle_t h, const void *d_state, int W, double *d_logabs, double *d_sign,
+                               double *d_naccept, double *d_drift, int *d_status, void *stream) {
+  return jagp_note(h, "jagp_walker_info", jagp_walker_info_impl(h, d_state, W, d_logabs, d_sign, d_naccept, d_drift, d_status, stream));
+}
+
+jagp_status_t jagp_walker_status(jagp_handle_t h, const void *d_state, int W, int *h_bits, void *stream) {
+  return jagp_note(h, "jagp_walker_status", jagp_walker_status_impl(h, d_state, W, h_bits, stream));
+}
+
+jagp_status_t jagp_autotune(jagp_handle_t h, void *d_state, int W, jagp_tuning_t *out, void *stream) {
+  return jagp_note(h, "jagp_autotune", jagp_autotune_impl(h, d_state, W, out, stream));
+}
+
+jagp_status_t jagp_set_tuning(jagp_handle_t h, const jagp_tuning_t *t) {
+  return jagp_note(h, "jagp_set_tuning", jagp_set_tuning_impl(h, t));
+}
+
+jagp_status_t jagp_profile(jagp_handle_t h, int kernel, int enable) {
+  return jagp_note(h, "jagp_profile", jagp_profile_impl(h, kernel, enable));
+}
+
+jagp_status_t jagp_profile_read(jagp_handle_t h, double *h_total_ms, long long *h_launches) {
+  return jagp_note(h, "jagp_profile_read", jagp_profile_read_impl(h, h_total_ms, h_launches));
+}
+
+jagp_status_t jagp_last_error(jagp_handle_t h, char *buf, size_t len) {
+  if (!h) return JAGP_ERR_INVALID_ARG;
+  if (buf && len > 0) snprintf(buf, len, "%s", h->last_error);
+  return h->last_status;
 }
 
 }  // extern "C"

@@ -34,4 +34,17 @@ struct jagp_ctx {
   int tune_st_left = 0, tune_st_right = 0;  // and pipeline depth (0: as many stages as fit)
   int tune_tile_prop = -1;                  // per-walker proposal products (gemm_rows tile)
   int tune_tile_refresh = -1;               // per-walker refresh product G~ = Phi_up Bt^T
+  // text of the last failed call on this handle (jagp_last_error)
+  jagp_status_t last_status = JAGP_OK;
+  char last_error[512] = "no error";
 };
+
+// Error reporting shared by the translation units of libjagp (jagp_api.cu):
+// jagp_note records a failed entry point's status, its name, the CUDA error
+// text behind a JAGP_ERR_CUDA and the detail set by the failing check, in the
+// handle (jagp_last_error) and returns the status unchanged.
+jagp_status_t jagp_note(jagp_ctx *h, const char *fn, jagp_status_t s);
+// the CUDA error text behind the next JAGP_ERR_CUDA of this thread
+void jagp_set_cuda_error(cudaError_t e);
+// a one-line detail of the next failure of this thread (e.g. which argument)
+void jagp_set_detail(const char *fmt, ...);

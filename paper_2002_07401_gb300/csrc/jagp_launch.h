@@ -76,7 +76,10 @@ cudaError_t launch_elocal(const DevSystem &s, const double *r, const double *kin
 cudaError_t launch_elocal_dw(const DevSystem &s, const double *r, const double *kin, double *eL,
                              double *parts, int W, cudaStream_t st, double *scal = nullptr);
 
-cudaError_t launch_walker_init(double *scal, int *status, int W, cudaStream_t st);
+// zero the per-walker counters; status = JAGP_WS_NONFINITE for a walker with a
+// non-finite coordinate in r [W][N][3] (when r is given), else 0
+cudaError_t launch_walker_init(double *scal, int *status, int W, cudaStream_t st, const double *r = nullptr,
+                               int N = 0);
 cudaError_t launch_logpsi_out(const double *scal, int W, double *logabs, double *sign,
                               cudaStream_t st);
 cudaError_t launch_walker_info(const double *scal, const int *status, int W, double *logabs,

@@ -24,6 +24,12 @@
 //   * jagp_create (which copies the system to the device) still allocates
 //     once, at set-up; this entry point itself calls no cudaMalloc, cudaFree or
 //     allocating library routine.
+//   * It always evaluates in FP64 (FP64 orbitals, lambda products, G~ and its
+//     elimination), whatever the handle's precision: on a mixed-precision
+//     handle its log|Psi| is the FP64 value, which differs from jagp_eval's
+//     mixed-precision one by that path's stated error (<= 1e-6).
+//   * Its kernels count towards jagp_launch_count; a failure is recorded for
+//     jagp_last_error like that of any other entry point.
 #include <mutex>
 
 #include "jagp_ctx.h"
@@ -70,30 +76,44 @@ jagp_status_t scratch_address(int device, void **out) {
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
   if (!g_noalloc_ptr[device]) {
     void *p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return JAGP_ERR_CUDA;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      jagp_set_cuda_error(e);
+      return JAGP_ERR_CUDA;
+    }
     g_noalloc_ptr[device] = p;
   }
   *out = g_noalloc_ptr[device];
   return JAGP_OK;
 }
 
-#define NA_CU(call)                              \
-  do {                                           \
-    if ((call) != cudaSuccess) return JAGP_ERR_CUDA; \
+#define NA_CU(call)                      \
+  do {                                   \
+    const cudaError_t e_ = (call);       \
+    ++h->launches;                       \
+    if (e_ != cudaSuccess) {             \
+      jagp_set_cuda_error(e_);           \
+      return JAGP_ERR_CUDA;              \
+    }                                    \
   } while (0)
 
-}  // namespace
-
-extern "C" jagp_status_t jagp_eval_noalloc(jagp_handle_t h, const double *d_r, int W, double *d_logabs,
-                                          double *d_sign, void *stream) {
+jagp_status_t eval_noalloc(jagp_handle_t h, const double *d_r, int W, double *d_logabs, double *d_sign,
+                           void *stream) {
   if (!h || !d_r || W <= 0 || W > h->max_walkers) return JAGP_ERR_INVALID_ARG;
   const DevSystem &d = h->ds;
   const int n = d.n_up, Lb = d.L;
   const EvalScratch S = eval_scratch_layout((size_t)W, (size_t)n, (size_t)Lb);
-  if (S.total > kNoAllocScratchBytes) return JAGP_ERR_UNSUPPORTED;
+  if (S.total > kNoAllocScratchBytes) {
+    jagp_set_detail("W = %d needs %zu bytes of scratch, more than the %zu of the fixed array", W, S.total,
+                    kNoAllocScratchBytes);
+    return JAGP_ERR_UNSUPPORTED;
+  }
   int device = -1;
-  NA_CU(cudaGetDevice(&device));
-  if (device != h->device) return JAGP_ERR_INVALID_ARG;
+  if (cudaGetDevice(&device) != cudaSuccess) return JAGP_ERR_CUDA;
+  if (device != h->device) {
+    jagp_set_detail("current device %d is not the handle's device %d", device, h->device);
+    return JAGP_ERR_INVALID_ARG;
+  }
   void *base = nullptr;
   jagp_status_t rc = scratch_address(device, &base);
   if (rc != JAGP_OK) return rc;
@@ -105,7 +125,7 @@ extern "C" jagp_status_t jagp_eval_noalloc(jagp_handle_t h, const double *d_r, i
   int *status = reinterpret_cast<int *>(b + S.status);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   // the same sequence as jagp_eval, on the static scratch
-  NA_CU(launch_walker_init(scal, status, W, st));
+  NA_CU(launch_walker_init(scal, status, W, st, d_r, d.N));
   NA_CU(launch_basis_points(d, false, d_r, W, 0, n, phi_up, nullptr, nullptr, 0, 0, st));
   NA_CU(launch_basis_points(d, false, d_r, W, n, d.n_dn, pprop, nullptr, nullptr, 0, 0, st));
   NA_CU(launch_lambda_rows(phi_up, d.lam, a_up, nullptr, nullptr, W * n, n, n, Lb, W * n, st));
@@ -117,4 +137,11 @@ extern "C" jagp_status_t jagp_eval_noalloc(jagp_handle_t h, const double *d_r, i
   NA_CU(launch_jastrow_full(d, d_r, scal, W, st));
   NA_CU(launch_logpsi_out(scal, W, d_logabs, d_sign, st));
   return JAGP_OK;
+}
+
+}  // namespace
+
+extern "C" jagp_status_t jagp_eval_noalloc(jagp_handle_t h, const double *d_r, int W, double *d_logabs,
+                                          double *d_sign, void *stream) {
+  return jagp_note(h, "jagp_eval_noalloc", eval_noalloc(h, d_r, W, d_logabs, d_sign, stream));
 }

@@ -589,17 +589,22 @@ cudaError_t launch_jastrow_full(const DevSystem &s, const double *r, double *sca
 // ---------------------------------------------------------------------------
 // bookkeeping
 // ---------------------------------------------------------------------------
-__global__ void k_walker_init(double *scal, int *status, int W) {
+// clears the counters and flags a walker with a non-finite coordinate
+__global__ void k_walker_init(double *scal, int *status, int W, const double *r, int N) {
   const int w = blockIdx.x * blockDim.x + threadIdx.x;
   if (w >= W) return;
   scal[(size_t)w * S_STRIDE + S_NACC] = 0.0;
   scal[(size_t)w * S_STRIDE + S_DRIFT] = 0.0;
-  status[w] = 0;
+  int bits = 0;
+  if (r)
+    for (int q = 0; q < 3 * N; ++q)
+      if (!isfinite(r[(size_t)w * 3 * N + q])) bits = JAGP_WS_NONFINITE;
+  status[w] = bits;
 }
 
-cudaError_t launch_walker_init(double *scal, int *status, int W, cudaStream_t st) {
+cudaError_t launch_walker_init(double *scal, int *status, int W, cudaStream_t st, const double *r, int N) {
   if (W <= 0) return cudaSuccess;
-  k_walker_init<<<(W + 255) / 256, 256, 0, st>>>(scal, status, W);
+  k_walker_init<<<(W + 255) / 256, 256, 0, st>>>(scal, status, W, r, N);
   return cudaGetLastError();
 }
 

@@ -53,6 +53,8 @@ def test_status_strings_and_bad_args_without_gpu():
     t = pg._Tuning()
     assert L.jagp_set_tuning(None, ctypes.byref(t)) == 1
     assert L.jagp_autotune(None, None, 1, ctypes.byref(t), None) == 1
+    # the per-handle error text needs a handle
+    assert L.jagp_last_error(None, None, 0) == 1
 
 
 def test_oracle_and_product_share_no_code():

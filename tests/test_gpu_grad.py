@@ -146,13 +146,22 @@ def test_autograd_function_force(torch_cuda):
     x = _cfgs(sysm, W, seed=13)
     g = pg.JAGP(sysm, W)
     lam = torch.tensor(sysm.lam, device="cuda", requires_grad=True)
-    jas = torch.tensor([sysm.b_ea, sysm.b_para, sysm.b_anti], dtype=torch.float64, device="cuda", requires_grad=True)
+    # d e_L / d b is not formed: the Jastrow parameters stay out of this graph
+    jas = torch.tensor([sysm.b_ea, sysm.b_para, sysm.b_anti], dtype=torch.float64, device="cuda")
     R = torch.tensor(sysm.R, device="cuda", requires_grad=True)
     r = g.positions(x).requires_grad_(True)
     logpsi, eL = pg.logpsi_and_local_energy(g, lam, jas, R, r)
     E = eL.mean()
     surrogate = E + 2.0 * ((eL - E).detach() * logpsi).mean()
     surrogate.backward()
+    # with the Jastrow parameters in the graph, an e_L gradient reaching them raises
+    jas_g = jas.clone().requires_grad_(True)
+    lp2, el2 = pg.logpsi_and_local_energy(g, lam, jas_g, R, r)
+    with pytest.raises(pg.JagpError, match="not formed"):
+        el2.sum().backward()
+    lp3, _ = pg.logpsi_and_local_energy(g, lam, jas_g, R, r)
+    lp3.sum().backward()            # the log|Psi| part alone is formed
+    assert jas_g.grad is not None
     o = oracle.Oracle(sysm)
     el = np.array([o.local_energy(x[w]) for w in range(W)])
     want = np.zeros_like(sysm.R)

@@ -180,7 +180,8 @@ def test_determinism_and_edge_cases(torch_cuda):
 
 
 def test_nonfinite_position_sets_status(torch_cuda):
-    """A walker poisoned on the host with NaN is flagged, the others are untouched."""
+    """A walker poisoned on the host with NaN is flagged NONFINITE, the others
+    are untouched; jagp_walker_status records which walkers carry bits."""
     import paper_2002_07401_gb300 as pg
     sysm = SYSTEMS["C1"]
     x = _walkers(sysm, 4)
@@ -190,9 +191,30 @@ def test_nonfinite_position_sets_status(torch_cuda):
     la, _ = g.eval(r)
     info = g.info()
     st = info["status"].cpu().numpy()
-    assert st[2] & pg.WS_SINGULAR and st[0] == st[1] == st[3] == 0
+    assert st[2] & pg.WS_NONFINITE and st[0] == st[1] == st[3] == 0
     ref, _ = oracle.Oracle(sysm).logpsi_batch(x[[0, 1, 3]])
     assert np.all(_close(la.cpu().numpy()[[0, 1, 3]], ref))
+    assert g.status() & pg.WS_NONFINITE
+    code, text = pg.jagp_last_error(g.h)
+    assert code == 0 and "1 of 4 walkers" in text
+    g.close()
+
+
+def test_last_error_records_the_failing_call(torch_cuda):
+    """jagp_last_error gives the failing entry point and the offending value."""
+    import paper_2002_07401_gb300 as pg
+    sysm = SYSTEMS["C1"]
+    g = pg.JAGP(sysm, 4)
+    assert pg.jagp_last_error(g.h) == (0, "no error")
+    r = g.positions(_walkers(sysm, 8))
+    with pytest.raises(pg.JagpError, match="W = 8 outside 1..4"):
+        pg.jagp_eval(g.h, r, 8, g.state)
+    code, text = pg.jagp_last_error(g.h)
+    assert code == 1 and text.startswith("jagp_eval: invalid argument")
+    with pytest.raises(pg.JagpError, match="vmc_sweep"):
+        pg.vmc_sweep(g.h, r, g.state, 0, 1)
+    assert pg.jagp_last_error(g.h)[1].startswith("vmc_sweep: invalid argument")
+    g.close()
 
 
 @pytest.mark.parametrize("name,W,sweeps,k", [("small-unpaired-slater", 9, 3, 1), ("C2", 4, 2, 5),
