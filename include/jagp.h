@@ -141,6 +141,26 @@ jagp_status_t vmc_sweep(jagp_handle_t h, double *d_r, void *d_state, int W, int 
 jagp_status_t local_energy(jagp_handle_t h, const double *d_r, void *d_state, int W, double *d_eL,
                            double *d_parts, void *stream);
 
+/* Statistics of the sampled local energies (Sec. VMC: the VMC energy is the
+ * mean of e_L over the Markov chain, its error bar from the correlated samples
+ * by reblocking).  d_eL: [T][W] local energies of W walkers over T sweeps (as
+ * vmc_sweep writes them).  The series is the walker mean per sweep,
+ * m_t = (1/W) sum_w d_eL[t][w] (kept in d_work [T], caller-owned).  Level k
+ * (k < jagp_reblock_levels(T), the levels with at least two blocks) cuts it
+ * into n_k = floor(T / 2^k) consecutive blocks of B = 2^k sweeps (a ragged
+ * tail is dropped) with block means b_j and writes d_levels[k] = (B, n_k,
+ * sigma_k, err_k), sigma_k = sqrt(sum_j (b_j - bbar)^2 / (n_k (n_k - 1))),
+ * err_k = sigma_k / sqrt(2 (n_k - 1)).  d_stats [4] = (mean of all T W values,
+ * chosen sigma, chosen level, 1 if a plateau was found): the chosen level is
+ * the smallest k whose next level still has >= 8 blocks and lies within err_k
+ * of sigma_k, else the last level with >= 8 blocks (plateau 0).  FP64, fixed
+ * summation order.  Device pointers; asynchronous on stream.  Errors:
+ * INVALID_ARG for T or W < 1 or a NULL pointer (d_levels may be NULL when
+ * T = 1). */
+int jagp_reblock_levels(int T);
+jagp_status_t jagp_reblock(const double *d_eL, int T, int W, double *d_work, double *d_levels, double *d_stats,
+                           void *stream);
+
 /* Batches of independent systems (uneven electron counts, each with its own
  * handle and walker state): jagp_batch_sweep runs nsweeps sweeps of every
  * system, exactly as vmc_sweep would (same Philox counters, walker indices

@@ -86,6 +86,10 @@ def lib():
         L.orc_elocal_grad_fd.restype = i
         L.orc_elocal_dlambda_fd.argtypes = [vp, vp, i, i, d]
         L.orc_elocal_dlambda_fd.restype = d
+        L.orc_reblock_levels.argtypes = [i]
+        L.orc_reblock_levels.restype = i
+        L.orc_reblock.argtypes = [vp, i, i, vp, vp]
+        L.orc_reblock.restype = i
         _lib = L
     return _lib
 
@@ -130,6 +134,21 @@ def move_draws(seed, walker, sweep, electron, delta, r):
     u = np.zeros(1)
     lib().orc_move_draws(C.c_uint64(seed), walker, sweep, electron, float(delta), _p(r), _p(rp), _p(u))
     return rp, float(u[0])
+
+
+def reblock(eL):
+    """Reblocking of eL [T][W] (see orc_reblock): (levels [nlev][4] = block
+    size, blocks, sigma, error of sigma; stats = mean, chosen sigma, chosen
+    level, plateau flag)."""
+    eL = np.ascontiguousarray(eL, dtype=np.float64)
+    if eL.ndim == 1:
+        eL = eL[:, None]
+    T, W = eL.shape
+    nlev = lib().orc_reblock_levels(T)
+    lev = np.zeros((max(nlev, 1), 4))
+    st = np.zeros(4)
+    lib().orc_reblock(_p(eL), T, W, _p(lev), _p(st))
+    return lev[:nlev], st
 
 
 def max_threads() -> int:

@@ -898,3 +898,79 @@ double orc_elocal_dlambda_fd(const orc_system *s, const double *x, int mu, int n
   free(lam);
   return (4.0 * D[1] - D[0]) / 3.0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Error bar of the VMC mean from correlated samples by reblocking (Sec.    */
+/* VMC: blocks of growing size until the estimate of the error plateaus).   */
+/* eL: [T][W] local energies of W walkers over T sweeps.  The series is the  */
+/* walker mean per sweep, m_t = (1/W) sum_w eL[t][w].  Level k groups it in  */
+/* n_k = floor(T / 2^k) consecutive blocks of B = 2^k sweeps (a ragged tail  */
+/* is dropped) with block means b_j; for n_k >= 2:                          */
+/*   sigma_k = sqrt( sum_j (b_j - bbar)^2 / (n_k (n_k - 1)) ),              */
+/*   err_k   = sigma_k / sqrt(2 (n_k - 1))    (error of sigma_k for          */
+/*                                             independent Gaussian blocks). */
+/* levels: [nlev][4] = (B, n_k, sigma_k, err_k), nlev = levels with n_k >= 2. */
+/* stats[4] = (mean of all T W values, chosen sigma, chosen level, plateau): */
+/* the chosen level is the smallest k whose next level has n_{k+1} >= 8     */
+/* blocks and |sigma_{k+1} - sigma_k| <= err_k (plateau = 1); without such a */
+/* k, the last level with n_k >= 8 (plateau = 0).  Returns nlev.            */
+/* ------------------------------------------------------------------------ */
+int orc_reblock_levels(int T) {
+  int n = 0;
+  for (long B = 1; T / B >= 2; B *= 2) n++;
+  return n;
+}
+
+int orc_reblock(const double *eL, int T, int W, double *levels, double *stats) {
+  double *m = (double *)malloc(sizeof(double) * (T > 0 ? T : 1));
+  double tot = 0.0;
+  for (int t = 0; t < T; ++t) {
+    double s = 0.0;
+    for (int w = 0; w < W; ++w) s += eL[(size_t)t * W + w];
+    m[t] = s / W;
+    tot += s;
+  }
+  int nlev = orc_reblock_levels(T);
+  for (int k = 0; k < nlev; ++k) {
+    long B = 1L << k;
+    long nb = T / B;
+    double bbar = 0.0;
+    for (long j = 0; j < nb; ++j) {
+      double b = 0.0;
+      for (long t = 0; t < B; ++t) b += m[j * B + t];
+      bbar += b / B;
+    }
+    bbar /= nb;
+    double ss = 0.0;
+    for (long j = 0; j < nb; ++j) {
+      double b = 0.0;
+      for (long t = 0; t < B; ++t) b += m[j * B + t];
+      double d = b / B - bbar;
+      ss += d * d;
+    }
+    double sig = sqrt(ss / ((double)nb * (double)(nb - 1)));
+    levels[4 * k + 0] = (double)B;
+    levels[4 * k + 1] = (double)nb;
+    levels[4 * k + 2] = sig;
+    levels[4 * k + 3] = sig / sqrt(2.0 * (double)(nb - 1));
+  }
+  int chosen = -1, plateau = 0;
+  for (int k = 0; k + 1 < nlev; ++k) {
+    if (levels[4 * (k + 1) + 1] < 8.0) break;
+    if (fabs(levels[4 * (k + 1) + 2] - levels[4 * k + 2]) <= levels[4 * k + 3]) {
+      chosen = k;
+      plateau = 1;
+      break;
+    }
+  }
+  if (chosen < 0)
+    for (int k = 0; k < nlev; ++k)
+      if (levels[4 * k + 1] >= 8.0) chosen = k;
+  if (chosen < 0) chosen = 0;
+  stats[0] = T > 0 && W > 0 ? tot / ((double)T * W) : 0.0;
+  stats[1] = nlev > 0 ? levels[4 * chosen + 2] : 0.0;
+  stats[2] = (double)chosen;
+  stats[3] = (double)plateau;
+  free(m);
+  return nlev;
+}

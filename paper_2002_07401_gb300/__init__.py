@@ -98,6 +98,10 @@ def lib():
         L.jagp_eval_noalloc.restype = i
         L.jagp_last_cuda_error.argtypes = []
         L.jagp_last_cuda_error.restype = C.c_char_p
+        L.jagp_reblock_levels.argtypes = [i]
+        L.jagp_reblock_levels.restype = i
+        L.jagp_reblock.argtypes = [vp, i, i, vp, vp, vp, vp]
+        L.jagp_reblock.restype = i
         L.jagp_last_error.argtypes = [vp, C.c_char_p, C.c_size_t]
         L.jagp_last_error.restype = i
         L.jagp_status_string.argtypes = [i]
@@ -226,6 +230,26 @@ def jagp_grad(h, r, state, W, work, seed_logpsi=None, seed_eL=None, eL=None, dla
     _check(lib().jagp_grad(h, _ptr(r), _ptr(state), int(W), _ptr(seed_logpsi), _ptr(seed_eL), _ptr(work), _ptr(eL),
                            _ptr(dlambda), _ptr(djas), _ptr(dR), _ptr(dR_walker), _ptr(dr), _stream(stream)),
            "jagp_grad", h)
+
+
+def jagp_reblock_levels(T) -> int:
+    return int(lib().jagp_reblock_levels(int(T)))
+
+
+def jagp_reblock(eL, work=None, levels=None, stats=None, stream=None):
+    """Reblocked error bar of the mean of eL [T][W] (device FP64; see
+    include/jagp.h).  Returns (levels [nlev][4], stats [4]) device tensors."""
+    import torch
+    eL = eL.reshape(eL.shape[0], -1) if eL.dim() > 1 else eL.reshape(-1, 1)
+    T, W = eL.shape
+    f64 = dict(dtype=torch.float64, device=eL.device)
+    nlev = jagp_reblock_levels(T)
+    work = torch.empty(T, **f64) if work is None else work
+    levels = torch.empty((max(nlev, 1), 4), **f64) if levels is None else levels
+    stats = torch.empty(4, **f64) if stats is None else stats
+    _check(lib().jagp_reblock(_ptr(eL.contiguous()), int(T), int(W), _ptr(work), _ptr(levels), _ptr(stats),
+                              _stream(stream)), "jagp_reblock")
+    return levels[:nlev], stats
 
 
 def jagp_walker_info(h, state, W, logabs=None, sign=None, naccept=None, drift=None, status=None, stream=None):

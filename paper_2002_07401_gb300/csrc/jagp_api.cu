@@ -1248,6 +1248,16 @@ jagp_status_t jagp_profile_read(jagp_handle_t h, double *h_total_ms, long long *
   return jagp_note(h, "jagp_profile_read", jagp_profile_read_impl(h, h_total_ms, h_launches));
 }
 
+int jagp_reblock_levels(int T) { return T >= 1 ? reblock_levels(T) : 0; }
+
+jagp_status_t jagp_reblock(const double *d_eL, int T, int W, double *d_work, double *d_levels, double *d_stats,
+                           void *stream) {
+  if (!d_eL || !d_work || !d_stats || T <= 0 || W <= 0) return JAGP_ERR_INVALID_ARG;
+  if (reblock_levels(T) > 0 && !d_levels) return JAGP_ERR_INVALID_ARG;
+  JAGP_CU(launch_reblock(d_eL, T, W, d_work, d_levels, d_stats, static_cast<cudaStream_t>(stream)));
+  return JAGP_OK;
+}
+
 jagp_status_t jagp_last_error(jagp_handle_t h, char *buf, size_t len) {
   if (!h) return JAGP_ERR_INVALID_ARG;
   if (buf && len > 0) snprintf(buf, len, "%s", h->last_error);

@@ -146,6 +146,13 @@ cudaError_t launch_adj_lambda(const double *btbar, const double *dnphi, const do
                               int W, int n, int nd, int L, double *part, int nz, double *dlam, cudaStream_t st);
 cudaError_t setup_adjoint_attributes();
 
+// Reblocking (k_stats.cu): walker means per sweep of eL [T][W] into work [T],
+// then every level's (block size, blocks, sigma, error of sigma) into levels
+// [reblock_levels(T)][4] and (mean, chosen sigma, chosen level, plateau) into stats [4]
+int reblock_levels(int T);
+cudaError_t launch_reblock(const double *eL, int T, int W, double *work, double *levels, double *stats,
+                           cudaStream_t st);
+
 // one-time kernel attribute set-up (dynamic shared memory limits), per file
 cudaError_t setup_kernel_attributes();
 cudaError_t setup_walker_attributes();

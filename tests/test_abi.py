@@ -55,6 +55,9 @@ def test_status_strings_and_bad_args_without_gpu():
     assert L.jagp_autotune(None, None, 1, ctypes.byref(t), None) == 1
     # the per-handle error text needs a handle
     assert L.jagp_last_error(None, None, 0) == 1
+    # reblocking checks its sizes on the host
+    assert L.jagp_reblock_levels(257) == 8 and L.jagp_reblock_levels(1) == 0
+    assert L.jagp_reblock(None, 10, 1, None, None, None, None) == 1
 
 
 def test_oracle_and_product_share_no_code():

@@ -538,3 +538,55 @@ def test_agp_nonsymmetric_rank_n_lambda():
     assert abs(np.linalg.det(G) - ref) < 1e-10 * abs(ref)
     la, sg, ld, J = o.logpsi(x)
     assert abs(ld - math.log(abs(ref))) < 1e-10 and sg == np.sign(ref)
+
+
+# ----------------------------------------------------------------------------
+# reblocking of correlated samples (Sec. VMC): textbook and closed-form pins
+# ----------------------------------------------------------------------------
+
+def test_reblock_level0_is_the_textbook_standard_error():
+    rng = np.random.default_rng(60)
+    eL = rng.normal(-1.0, 0.3, size=(257, 5))     # odd T: the ragged tail is dropped above level 0
+    lev, st = oracle.reblock(eL)
+    m = eL.mean(axis=1)
+    assert len(lev) == 8                            # 257 // 2^k >= 2 for k = 0..7
+    assert lev[0][0] == 1 and lev[0][1] == 257
+    assert abs(lev[0][2] - m.std(ddof=1) / math.sqrt(257)) < 1e-14
+    assert abs(lev[0][3] - lev[0][2] / math.sqrt(2 * 256)) < 1e-16
+    assert abs(st[0] - eL.mean()) < 1e-14
+    for k, (B, nb, sig, err) in enumerate(lev):
+        B, nb = int(B), int(nb)
+        b = m[: nb * B].reshape(nb, B).mean(axis=1)
+        assert B == 2 ** k and nb == 257 // B
+        assert abs(sig - b.std(ddof=1) / math.sqrt(nb)) < 1e-13 * max(sig, 1e-300)
+
+
+def test_reblock_piecewise_constant_series():
+    """A series constant over blocks of four sweeps: at level 2 the block means
+    are the distinct values themselves."""
+    rng = np.random.default_rng(61)
+    v = rng.normal(size=64)
+    eL = np.repeat(v, 4)[:, None]
+    lev, _ = oracle.reblock(eL)
+    assert abs(lev[2][2] - v.std(ddof=1) / 8.0) < 1e-14
+    nb = 64
+    assert abs(lev[2][2] / lev[0][2] - math.sqrt((4 * nb - 1) / (nb - 1))) < 1e-12
+
+
+def test_reblock_ar1_plateau_matches_closed_form():
+    """x_t = phi x_{t-1} + e_t with Var e = s^2: the variance of the mean of T
+    samples tends to s^2 / ((1 - phi)^2 T); level 0 underestimates it by the
+    integrated autocorrelation time (1 + phi) / (1 - phi)."""
+    phi, s, T = 0.8, 0.5, 1 << 17
+    rng = np.random.default_rng(62)
+    e = rng.normal(0, s, size=T)
+    x = np.empty(T)
+    x[0] = e[0] / math.sqrt(1 - phi * phi)
+    for t in range(1, T):
+        x[t] = phi * x[t - 1] + e[t]
+    lev, st = oracle.reblock(x)
+    want = s / ((1 - phi) * math.sqrt(T))
+    assert st[3] == 1.0, lev
+    assert abs(st[1] - want) < 0.1 * want, (st, want)
+    naive = s / math.sqrt(1 - phi * phi) / math.sqrt(T)
+    assert abs(lev[0][2] - naive) < 0.05 * naive
