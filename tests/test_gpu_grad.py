@@ -154,6 +154,7 @@ def test_autograd_function_force(torch_cuda):
     E = eL.mean()
     surrogate = E + 2.0 * ((eL - E).detach() * logpsi).mean()
     surrogate.backward()
+    grad_R = R.grad.clone()
     # with the Jastrow parameters in the graph, an e_L gradient reaching them raises
     jas_g = jas.clone().requires_grad_(True)
     lp2, el2 = pg.logpsi_and_local_energy(g, lam, jas_g, R, r)
@@ -168,7 +169,7 @@ def test_autograd_function_force(torch_cuda):
     for w in range(W):
         dR, _ = o.elocal_grad(x[w], h=5e-4)
         want += dR / W + 2.0 * (el[w] - el.mean()) / W * o.grad_logpsi(x[w], want_lam=False)["R"]
-    ok, err = _close(R.grad.cpu().numpy(), want, 1e-7)
+    ok, err = _close(grad_R.cpu().numpy(), want, 1e-7)
     assert ok, err
 
 
