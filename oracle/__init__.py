@@ -90,6 +90,8 @@ def lib():
         L.orc_reblock_levels.restype = i
         L.orc_reblock.argtypes = [vp, i, i, vp, vp]
         L.orc_reblock.restype = i
+        L.orc_sr.argtypes = [vp, vp, i, i, d, d, vp, vp, vp, vp]
+        L.orc_sr.restype = i
         _lib = L
     return _lib
 
@@ -149,6 +151,20 @@ def reblock(eL):
     st = np.zeros(4)
     lib().orc_reblock(_p(eL), T, W, _p(lev), _p(st))
     return lev[:nlev], st
+
+
+def sr(O, e, eps=1e-3, delta=1.0, want_S=True):
+    """Stochastic reconfiguration from samples (see orc_sr): O [M][P]
+    log-derivatives, e [M] local energies.  Returns dict(Obar, S, f, dalpha)."""
+    O = np.ascontiguousarray(O, dtype=np.float64)
+    e = np.ascontiguousarray(e, dtype=np.float64)
+    M, P = O.shape
+    Ob, f, da = np.zeros(P), np.zeros(P), np.zeros(P)
+    S = np.zeros((P, P)) if want_S else None
+    ok = lib().orc_sr(_p(O), _p(e), M, P, float(eps), float(delta), _p(Ob), _p(S), _p(f), _p(da))
+    if not ok:
+        raise ValueError("singular regularised S matrix")
+    return {"Obar": Ob, "S": S, "f": f, "dalpha": da}
 
 
 def max_threads() -> int:
@@ -224,6 +240,19 @@ class Oracle:
         if not ok:
             raise ValueError("singular geminal matrix")
         return (tuple(float(v) for v in out) + (gD, lD)) if parts else float(out[0])
+
+    def logpsi_derivs(self, x):
+        """Per-configuration log-derivatives O_k = d ln|Psi| / d alpha_k for the
+        parameters (every entry of lambda, row-major, then b_ea, b_para,
+        b_anti): x [W][N][3] -> O [W][L*L + 3]."""
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        W = x.shape[0]
+        O = np.zeros((W, self.L * self.L + 3))
+        for w in range(W):
+            g = self.grad_logpsi(x[w])
+            O[w, :self.L * self.L] = g["lam"].ravel()
+            O[w, self.L * self.L:] = g["jas"]
+        return O
 
     def grad_logpsi(self, x, want_lam=True):
         x = np.ascontiguousarray(x, dtype=np.float64)

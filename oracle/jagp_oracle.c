@@ -974,3 +974,61 @@ int orc_reblock(const double *eL, int T, int W, double *levels, double *stats) {
   free(m);
   return nlev;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Stochastic reconfiguration (Sec. "Stochastic reconfiguration", Eqs.      */
+/* SRupdate, sr and the diagonal shift of the regularised matrix): from M   */
+/* samples with log-derivatives O [M][P] (O_k(x_i) = d ln|Psi(x_i)| / d     */
+/* alpha_k, Sec. "Derivatives with respect to variational parameters") and  */
+/* local energies e [M]:                                                    */
+/*   Obar_k = (1/M) sum_i O_ik                                              */
+/*   S_kl   = (1/M) sum_i (O_ik - Obar_k)(O_il - Obar_l)                    */
+/*   f_k    = -2 (1/M) sum_i e_i (O_ik - Obar_k)     (Eq. eq_general_force)  */
+/*   S'_kk  = S_kk (1 + eps), S'_kl = S_kl for k != l                       */
+/*   dalpha = Delta S'^{-1} f   (solved by LU with partial pivoting)        */
+/* Outputs (each may be NULL except f): Obar [P], S [P][P], f [P],          */
+/* dalpha [P].  Returns 0 if S' is singular.                                */
+/* ------------------------------------------------------------------------ */
+int orc_sr(const double *O, const double *e, int M, int P, double eps, double delta, double *Obar_out,
+           double *S_out, double *f, double *dalpha) {
+  double *Ob = (double *)malloc(sizeof(double) * P);
+  double *S = (double *)malloc(sizeof(double) * (size_t)P * P);
+  for (int k = 0; k < P; ++k) {
+    double s = 0.0;
+    for (int i = 0; i < M; ++i) s += O[(size_t)i * P + k];
+    Ob[k] = s / M;
+  }
+  for (int k = 0; k < P; ++k)
+    for (int l = 0; l < P; ++l) {
+      double s = 0.0;
+      for (int i = 0; i < M; ++i) s += (O[(size_t)i * P + k] - Ob[k]) * (O[(size_t)i * P + l] - Ob[l]);
+      S[(size_t)k * P + l] = s / M;
+    }
+  for (int k = 0; k < P; ++k) {
+    double s = 0.0;
+    for (int i = 0; i < M; ++i) s += e[i] * (O[(size_t)i * P + k] - Ob[k]);
+    f[k] = -2.0 * s / M;
+  }
+  if (Obar_out) memcpy(Obar_out, Ob, sizeof(double) * P);
+  if (S_out) memcpy(S_out, S, sizeof(double) * (size_t)P * P);
+  int ok = 1;
+  if (dalpha) {
+    double *Sp = (double *)malloc(sizeof(double) * (size_t)P * P);
+    double *inv = (double *)malloc(sizeof(double) * (size_t)P * P);
+    memcpy(Sp, S, sizeof(double) * (size_t)P * P);
+    for (int k = 0; k < P; ++k) Sp[(size_t)k * P + k] *= 1.0 + eps;
+    double la, sg;
+    ok = orc_det_inverse(P, Sp, &la, &sg, inv);
+    if (ok)
+      for (int k = 0; k < P; ++k) {
+        double s = 0.0;
+        for (int l = 0; l < P; ++l) s += inv[(size_t)k * P + l] * f[l];
+        dalpha[k] = delta * s;
+      }
+    free(Sp);
+    free(inv);
+  }
+  free(Ob);
+  free(S);
+  return ok;
+}

@@ -590,3 +590,100 @@ def test_reblock_ar1_plateau_matches_closed_form():
     assert abs(st[1] - want) < 0.1 * want, (st, want)
     naive = s / math.sqrt(1 - phi * phi) / math.sqrt(T)
     assert abs(lev[0][2] - naive) < 0.05 * naive
+
+
+# ----------------------------------------------------------------------------
+# stochastic reconfiguration (Sec. "Stochastic reconfiguration", Eqs. SRupdate,
+# sr, the diagonal shift; Sec. "Derivatives with respect to variational
+# parameters", Eq. eq_general_force)
+# ----------------------------------------------------------------------------
+
+def test_sr_against_library_statistics():
+    """S is the (biased) covariance of the log-derivatives, f = -2 cov(e_L, O),
+    dalpha = Delta (S + eps diag S)^{-1} f: against NumPy's covariance and solver."""
+    rng = np.random.default_rng(71)
+    M, P = 300, 7
+    O = rng.normal(size=(M, P)) @ rng.normal(size=(P, P)) + rng.normal(size=P)
+    e = -1.0 + 0.3 * rng.normal(size=M) + 0.1 * O[:, 2]
+    eps, delta = 0.05, 0.2
+    r = oracle.sr(O, e, eps=eps, delta=delta)
+    S_np = np.cov(O.T, bias=True)
+    f_np = -2.0 * np.cov(np.vstack([e, O.T]), bias=True)[0, 1:]
+    assert np.allclose(r["Obar"], O.mean(axis=0), rtol=0, atol=1e-13)
+    assert np.allclose(r["S"], S_np, rtol=1e-12, atol=1e-13)
+    assert np.allclose(r["f"], f_np, rtol=1e-12, atol=1e-13)
+    Sp = S_np + eps * np.diag(np.diag(S_np))
+    assert np.allclose(r["dalpha"], delta * np.linalg.solve(Sp, f_np), rtol=1e-10, atol=1e-13)
+    w = np.linalg.eigvalsh(r["S"])
+    assert w.min() > -1e-12 * w.max()          # positive semi-definite
+
+
+def test_sr_force_vanishes_at_an_exact_eigenstate():
+    """exp(J1) with b_ea -> 0 is exp(-Z r), an exact eigenstate: e_L is constant,
+    so the generalized force vanishes sample by sample, without statistical error."""
+    s = synth.hydrogenic_gauss_j1(2.0)
+    o = oracle.Oracle(s)
+    x = synth.init_walkers(s, 256, seed=72)
+    eL, _, _ = o.vmc(x, 30, seed=72)
+    O = o.logpsi_derivs(x)[:, [s.L * s.L]]
+    assert O.std() > 1e-2
+    r = oracle.sr(O, eL[-1], eps=1e-3)
+    assert abs(r["f"][0]) < 1e-13 * np.abs(O).max()
+
+
+def _quad_slater_j1(beta, b, Z=1.0):
+    """psi = exp(-beta r) exp(J1(r)) with J1 = -c^3 u(c r), u = (1 - e^{-b s}) / (2b),
+    c = (2Z)^{1/4} (Eqs. onebody_J_hom, onebody_u), by radial quadrature:
+    E, <O_b>, Var(O_b) with O_b = d ln psi / d b."""
+    from scipy.integrate import quad
+    c = (2 * Z) ** 0.25
+
+    def parts(r):
+        ex = math.exp(-b * c * r)
+        F = -beta * r - c ** 3 * (1 - ex) / (2 * b)
+        Fp = -beta - c ** 4 * ex / 2
+        Fpp = c ** 5 * b * ex / 2
+        eL = -0.5 * (Fpp + 2 * Fp / r + Fp ** 2) - Z / r
+        sarg = c * r
+        Ob = -c ** 3 * (b * sarg * math.exp(-b * sarg) - 1 + math.exp(-b * sarg)) / (2 * b * b)
+        return F, eL, Ob
+
+    w = lambda r: math.exp(2 * parts(r)[0]) * r * r          # noqa: E731
+    nrm = quad(w, 0, np.inf, limit=200)[0]
+    E = quad(lambda r: w(r) * parts(r)[1], 0, np.inf, limit=200)[0] / nrm
+    o1 = quad(lambda r: w(r) * parts(r)[2], 0, np.inf, limit=200)[0] / nrm
+    o2 = quad(lambda r: w(r) * parts(r)[2] ** 2, 0, np.inf, limit=200)[0] / nrm
+    return E, o1, o2 - o1 * o1, parts
+
+
+def test_sr_step_against_radial_quadrature():
+    """One electron, exp(-0.3 r) exp(J1) with b_ea = 0.8: the sampled force
+    f = -2 cov(e_L, O_b) and metric S = Var(O_b) agree with -dE/db and Var(O_b)
+    by quadrature within their statistical errors, and the SR step moves b_ea
+    downhill in the quadrature energy."""
+    pytest.importorskip("scipy")
+    beta, b = 0.3, 0.8
+    s = synth.one_electron_slater(beta)
+    s.use_j1, s.b_ea = True, b
+    o = oracle.Oracle(s)
+    W = 4096
+    x = synth.init_walkers(s, W, seed=73, spread=3.0)
+    eL, _, _ = o.vmc(x, 80, seed=73, delta=2.5)
+    e = eL[-1]
+    O = o.logpsi_derivs(x)[:, [s.L * s.L]]
+    E0, _, varO, parts = _quad_slater_j1(beta, b)
+    for w in range(5):                         # the oracle's O_b against the closed form
+        rr = float(np.linalg.norm(x[w, 0]))
+        assert abs(O[w, 0] - parts(rr)[2]) < 1e-12 * (1 + abs(O[w, 0]))
+    h = 1e-4
+    f_exact = -(_quad_slater_j1(beta, b + h)[0] - _quad_slater_j1(beta, b - h)[0]) / (2 * h)
+    r = oracle.sr(O, e, eps=1e-3, delta=0.05)
+    Oc = O[:, 0] - O[:, 0].mean()
+    sig_f = 2 * np.std((e - e.mean()) * Oc) / math.sqrt(W)
+    sig_S = np.std(Oc ** 2) / math.sqrt(W)
+    assert abs(f_exact) > 10 * sig_f
+    assert abs(r["f"][0] - f_exact) < 4.5 * sig_f, (r["f"], f_exact, sig_f)
+    assert abs(r["S"][0, 0] - varO) < 4.5 * sig_S, (r["S"], varO, sig_S)
+    db = r["dalpha"][0]
+    assert db * f_exact > 0
+    assert _quad_slater_j1(beta, b + db)[0] < E0
