@@ -90,6 +90,9 @@ def lib():
         L.orc_reblock_levels.restype = i
         L.orc_reblock.argtypes = [vp, i, i, vp, vp]
         L.orc_reblock.restype = i
+        L.orc_swct_omega.argtypes = [vp, vp, vp, vp]
+        L.orc_swct_derivs.argtypes = [vp, vp, d, vp, vp]
+        L.orc_swct_derivs.restype = i
         L.orc_sr.argtypes = [vp, vp, i, i, d, d, vp, vp, vp, vp]
         L.orc_sr.restype = i
         _lib = L
@@ -273,6 +276,23 @@ class Oracle:
         dr = np.zeros((self.N, 3)) if want_r else None
         lib().orc_elocal_grad_fd(self._ps, _p(x), float(h), _p(dR), _p(dr))
         return dR, dr
+
+    def swct_omega(self, r):
+        """Space-warp weights omega_a(r) [n_atoms] and their gradients [n_atoms][3]."""
+        r = np.ascontiguousarray(r, dtype=np.float64)
+        na = self.sys.n_atoms
+        om, dom = np.zeros(na), np.zeros((na, 3))
+        lib().orc_swct_omega(self._ps, _p(r), _p(om), _p(dom))
+        return om, dom
+
+    def swct_derivs(self, x, h=1e-3):
+        """(d e_L / d R_a, d ln(J^1/2 Psi) / d R_a) with the space warp, [n_atoms][3] each."""
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        na = self.sys.n_atoms
+        dE, dL = np.zeros((na, 3)), np.zeros((na, 3))
+        if not lib().orc_swct_derivs(self._ps, _p(x), float(h), _p(dE), _p(dL)):
+            raise ValueError("singular geminal matrix")
+        return dE, dL
 
     def elocal_dlambda(self, x, mu, nu, h=1e-4):
         x = np.ascontiguousarray(x, dtype=np.float64)

@@ -1032,3 +1032,64 @@ int orc_sr(const double *O, const double *e, int M, int P, double eps, double de
   free(S);
   return ok;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Space-warp coordinate transformation for forces (Sec. "Atomic forces"):  */
+/* an electron at r moves with nucleus a by Delta R_a omega_a(r),           */
+/*   omega_a(r) = kappa(|r - R_a|) / sum_b kappa(|r - R_b|), kappa(d) = 1/d^4 */
+/* omega: [n_atoms], domega: [n_atoms][3] (the gradient of omega_a at r).   */
+/* ------------------------------------------------------------------------ */
+void orc_swct_omega(const orc_system *s, const double r[3], double *omega, double *domega) {
+  int na = s->n_atoms;
+  double *k = (double *)malloc(sizeof(double) * na), *gk = (double *)malloc(sizeof(double) * 3 * na);
+  double sk = 0.0, sg[3] = {0.0, 0.0, 0.0};
+  for (int a = 0; a < na; ++a) {
+    double d[3], d2 = 0.0;
+    for (int q = 0; q < 3; ++q) {
+      d[q] = r[q] - s->R[3 * a + q];
+      d2 += d[q] * d[q];
+    }
+    k[a] = 1.0 / (d2 * d2);                                       /* |d|^-4 */
+    for (int q = 0; q < 3; ++q) gk[3 * a + q] = -4.0 * d[q] / (d2 * d2 * d2);  /* grad |d|^-4 */
+    sk += k[a];
+    for (int q = 0; q < 3; ++q) sg[q] += gk[3 * a + q];
+  }
+  for (int a = 0; a < na; ++a) {
+    omega[a] = k[a] / sk;
+    if (domega)
+      for (int q = 0; q < 3; ++q) domega[3 * a + q] = (gk[3 * a + q] * sk - k[a] * sg[q]) / (sk * sk);
+  }
+  free(k);
+  free(gk);
+}
+
+/* The total derivatives of Eq. forces:aad with the space warp, for one      */
+/* configuration x:                                                         */
+/*   dEL[a] = d e_L / d R_a = de_L/dR_a + sum_i omega_a(r_i) de_L/dr_i      */
+/*   dLJ[a] = d ln(J^{1/2} Psi) / d R_a                                     */
+/*          = d ln|Psi|/dR_a + sum_i [omega_a(r_i) d ln|Psi|/dr_i + grad omega_a(r_i) / 2] */
+/* with the partial derivatives of e_L from orc_elocal_grad_fd (step h) and  */
+/* those of ln|Psi| from orc_grad_logpsi.  dEL, dLJ: [n_atoms][3].          */
+int orc_swct_derivs(const orc_system *s, const double *x, double h, double *dEL, double *dLJ) {
+  int N = s->n_up + s->n_dn, na = s->n_atoms;
+  double *eR = (double *)malloc(sizeof(double) * 3 * na), *er = (double *)malloc(sizeof(double) * 3 * N);
+  double *lR = (double *)malloc(sizeof(double) * 3 * na), *lr = (double *)malloc(sizeof(double) * 3 * N);
+  double *om = (double *)malloc(sizeof(double) * na), *dom = (double *)malloc(sizeof(double) * 3 * na);
+  double djas[3];
+  orc_elocal_grad_fd(s, x, h, eR, er);
+  int ok = orc_grad_logpsi(s, x, NULL, djas, lR, lr);
+  if (ok) {
+    memcpy(dEL, eR, sizeof(double) * 3 * na);
+    memcpy(dLJ, lR, sizeof(double) * 3 * na);
+    for (int i = 0; i < N; ++i) {
+      orc_swct_omega(s, x + 3 * i, om, dom);
+      for (int a = 0; a < na; ++a)
+        for (int q = 0; q < 3; ++q) {
+          dEL[3 * a + q] += om[a] * er[3 * i + q];
+          dLJ[3 * a + q] += om[a] * lr[3 * i + q] + 0.5 * dom[3 * a + q];
+        }
+    }
+  }
+  free(eR); free(er); free(lR); free(lr); free(om); free(dom);
+  return ok;
+}

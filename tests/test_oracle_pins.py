@@ -687,3 +687,70 @@ def test_sr_step_against_radial_quadrature():
     db = r["dalpha"][0]
     assert db * f_exact > 0
     assert _quad_slater_j1(beta, b + db)[0] < E0
+
+
+# ----------------------------------------------------------------------------
+# space-warp coordinate transformation for forces (Sec. "Atomic forces")
+# ----------------------------------------------------------------------------
+
+def _omega_ref(R, r):
+    """omega_a(r) = kappa_a / sum_b kappa_b, kappa = |r - R_a|^-4, written out here."""
+    k = 1.0 / np.sum((r[None, :] - R) ** 2, axis=1) ** 2
+    return k / k.sum()
+
+
+def test_swct_weights_partition_unity_and_gradient():
+    s = synth.small_random(n_atoms=4, n_up=2, n_dn=2, per_atom=6, seed=90)
+    o = oracle.Oracle(s)
+    rng = np.random.default_rng(90)
+    for _ in range(5):
+        r = s.R.mean(axis=0) + rng.normal(0, 1.0, size=3)
+        om, dom = o.swct_omega(r)
+        assert abs(om.sum() - 1.0) < 1e-14 and np.abs(dom.sum(axis=0)).max() < 1e-12 * np.abs(dom).max()
+        assert np.allclose(om, _omega_ref(s.R, r), rtol=1e-13, atol=0)
+        h = 1e-5
+        for q in range(3):
+            rp, rm = r.copy(), r.copy()
+            rp[q] += h
+            rm[q] -= h
+            fd = (_omega_ref(s.R, rp) - _omega_ref(s.R, rm)) / (2 * h)
+            assert np.allclose(dom[:, q], fd, rtol=1e-7, atol=1e-9)
+
+
+def test_swct_derivatives_are_derivatives_along_the_warp():
+    """d e_L / d R_a (warped) is the derivative of e_L when nucleus a moves by h
+    and every electron by h omega_a(r_i); d ln(J^1/2 Psi) / d R_a likewise with
+    ln|Psi| + 1/2 sum_i ln(1 + h d omega_a / d r_q) (the Jacobian of the warp)."""
+    s = synth.small_random(n_atoms=3, n_up=2, n_dn=2, per_atom=6, seed=91, slater_fraction=0.3)
+    o = oracle.Oracle(s)
+    x = _rand_cfg(s, 92)
+    dE, dL = o.swct_derivs(x, h=1e-3)
+    R0 = s.R.copy()
+    h = 1e-4
+
+    def warped(a, q, t):
+        R = R0.copy()
+        R[a, q] += t
+        y = x.copy()
+        logJ = 0.0
+        for i in range(s.N):
+            om = _omega_ref(R0, x[i])
+            y[i, q] += t * om[a]
+            # d omega_a / d r_q by central differences of the written-out definition
+            e = np.zeros(3)
+            e[q] = 1e-6
+            dq = (_omega_ref(R0, x[i] + e)[a] - _omega_ref(R0, x[i] - e)[a]) / 2e-6
+            logJ += math.log(1.0 + t * dq)
+        s2 = synth.small_random(n_atoms=3, n_up=2, n_dn=2, per_atom=6, seed=91, slater_fraction=0.3)
+        s2.R = np.ascontiguousarray(R)
+        o2 = oracle.Oracle(s2)
+        return o2.local_energy(y), o2.logpsi(y)[0] + 0.5 * logJ
+
+    for a in range(3):
+        for q in range(3):
+            ep, lp = warped(a, q, h)
+            em, lm = warped(a, q, -h)
+            assert abs((ep - em) / (2 * h) - dE[a, q]) < 1e-6 * (1 + abs(dE[a, q])), (a, q)
+            assert abs((lp - lm) / (2 * h) - dL[a, q]) < 1e-6 * (1 + abs(dL[a, q])), (a, q)
+    # the warp moves charge with the nuclei: the total still vanishes (translation)
+    assert np.abs(dE.sum(axis=0)).max() < 1e-7 * (1 + np.abs(dE).max())
