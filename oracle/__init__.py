@@ -90,6 +90,11 @@ def lib():
         L.orc_reblock_levels.restype = i
         L.orc_reblock.argtypes = [vp, i, i, vp, vp]
         L.orc_reblock.restype = i
+        L.orc_guiding_R.argtypes = [vp, vp, d]
+        L.orc_guiding_R.restype = d
+        L.orc_vmc_guided.argtypes = [vp, vp, i, C.c_longlong, C.c_uint64, C.c_longlong, i, d, d, d, vp, vp, vp, vp,
+                                     i]
+        L.orc_vmc_guided.restype = i
         L.orc_swct_omega.argtypes = [vp, vp, vp, vp]
         L.orc_swct_derivs.argtypes = [vp, vp, d, vp, vp]
         L.orc_swct_derivs.restype = i
@@ -276,6 +281,27 @@ class Oracle:
         dr = np.zeros((self.N, 3)) if want_r else None
         lib().orc_elocal_grad_fd(self._ps, _p(x), float(h), _p(dR), _p(dr))
         return dR, dr
+
+    def guiding_R(self, x, theta=0.375):
+        """R(x) = (S sum |G~^{-1}|^2)^-theta of one configuration (Eq. R_r)."""
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        return float(lib().orc_guiding_R(self._ps, _p(x), float(theta)))
+
+    def vmc_guided(self, x, nsweeps, theta=0.375, eps=1e-3, seed=0, sweep0=0, walker0=0, delta=None,
+                   record_eL=True, nthreads=0):
+        """As vmc(), sampling the guiding function Psi_G = (max(R, eps) / R) Psi_T.
+        Returns (eL [nsweeps][W], logpsi [W], n_accept [W], R [W] of the final configurations)."""
+        assert x.dtype == np.float64 and x.flags["C_CONTIGUOUS"]
+        W = x.shape[0]
+        eL = np.zeros((nsweeps, W)) if record_eL else None
+        lp, R = np.zeros(W), np.zeros(W)
+        nacc = np.zeros(W, dtype=np.int64)
+        d = self.sys.delta if delta is None else delta
+        ok = lib().orc_vmc_guided(self._ps, _p(x), W, walker0, C.c_uint64(seed), sweep0, nsweeps, float(d),
+                                  float(theta), float(eps), _p(eL), _p(lp), _p(nacc), _p(R), int(nthreads))
+        if not ok:
+            raise ValueError("singular geminal matrix at the start of a walker")
+        return eL, lp, nacc, R
 
     def swct_omega(self, r):
         """Space-warp weights omega_a(r) [n_atoms] and their gradients [n_atoms][3]."""

@@ -634,9 +634,47 @@ void orc_move_draws(uint64_t seed, uint32_t walker, uint32_t sweep, uint32_t ele
   *u_acc = (double)o[3] * 0x1p-32;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Guiding function (Sec. "Atomic forces", Eqs. guiding_function, R_r,        */
+/* regularization, reweighting): from G~ and its inverse,                    */
+/*   R = (S sum_{ij} |G~^{-1}_ij|^2)^{-theta},  S = min_i sum_j |G~_ij|^2,   */
+/* Psi_G = (R^eps / R) Psi_T with R^eps = max(R, eps), and the weight       */
+/* W = (Psi_T / Psi_G)^2 = (R / max(R, eps))^2.                            */
+/* ------------------------------------------------------------------------ */
+static double guiding_R(int n, const double *G, const double *Ginv, double theta) {
+  double f = 0.0, S = INFINITY;
+  for (int i = 0; i < n; ++i) {
+    double rs = 0.0;
+    for (int j = 0; j < n; ++j) {
+      rs += G[i * n + j] * G[i * n + j];
+      f += Ginv[i * n + j] * Ginv[i * n + j];
+    }
+    if (rs < S) S = rs;
+  }
+  return pow(S * f, -theta);
+}
+
+static double guiding_W(double R, double eps) {
+  double q = R / (R > eps ? R : eps);
+  return q * q;
+}
+
+/* R of one configuration (0 if G~ is singular) */
+double orc_guiding_R(const orc_system *s, const double *x, double theta) {
+  int N = s->n_up + s->n_dn, L = s->L, nu = s->n_up;
+  double *phi = (double *)malloc(sizeof(double) * (size_t)N * L);
+  double *G = (double *)malloc(sizeof(double) * nu * nu), *Gi = (double *)malloc(sizeof(double) * nu * nu);
+  for (int i = 0; i < N; ++i) orc_ao(s, x + 3 * i, phi + (size_t)i * L, NULL, NULL);
+  orc_geminal(s, phi, G);
+  double la, sg, R = 0.0;
+  if (orc_det_inverse(nu, G, &la, &sg, Gi)) R = guiding_R(nu, G, Gi, theta);
+  free(phi); free(G); free(Gi);
+  return R;
+}
+
 static int vmc_walker(const orc_system *s, double *x, uint32_t wid, uint64_t seed, uint32_t sweep0,
                       int nsweeps, double delta, double *eL_out, int W_stride, int w,
-                      double *logpsi_out, long long *n_acc_out) {
+                      double *logpsi_out, long long *n_acc_out, double theta, double eps, double *R_out) {
   int N = s->n_up + s->n_dn, L = s->L, nu = s->n_up, nd = s->n_dn;
   double *phi = (double *)malloc(sizeof(double) * (size_t)N * L);
   double *G = (double *)malloc(sizeof(double) * nu * nu);
@@ -644,11 +682,15 @@ static int vmc_walker(const orc_system *s, double *x, uint32_t wid, uint64_t see
   double *pnew = (double *)malloc(sizeof(double) * L);
   double *vec = (double *)malloc(sizeof(double) * L);
   double *xp = (double *)malloc(sizeof(double) * 3 * N);
+  /* guided sampling (eps > 0): inverses for R of the current and the proposed configuration */
+  const int guided = eps > 0.0;
+  double *Gi = (double *)malloc(sizeof(double) * nu * nu), *Gpi = (double *)malloc(sizeof(double) * nu * nu);
   for (int i = 0; i < N; ++i) orc_ao(s, x + 3 * i, phi + (size_t)i * L, NULL, NULL);
   orc_geminal(s, phi, G);
   double logdet, sgn;
-  int ok = orc_det_inverse(nu, G, &logdet, &sgn, NULL);
+  int ok = orc_det_inverse(nu, G, &logdet, &sgn, Gi);
   double J = orc_jastrow(s, x);
+  double Wcur = ok && guided ? guiding_W(guiding_R(nu, G, Gi, theta), eps) : 1.0;
   long long nacc = 0;
   for (int t = 0; t < nsweeps && ok; ++t) {
     uint32_t sweep = sweep0 + (uint32_t)t;
@@ -667,11 +709,17 @@ static int vmc_walker(const orc_system *s, double *x, uint32_t wid, uint64_t see
         for (int i = 0; i < nu; ++i) Gp[i * nu + j] = dot(L, phi + (size_t)i * L, vec);
       }
       double logdet_p, sgn_p;
-      int okp = orc_det_inverse(nu, Gp, &logdet_p, &sgn_p, NULL);
+      int okp = orc_det_inverse(nu, Gp, &logdet_p, &sgn_p, guided ? Gpi : NULL);
       memcpy(xp, x, sizeof(double) * 3 * N);
       xp[3 * e] = rp[0]; xp[3 * e + 1] = rp[1]; xp[3 * e + 2] = rp[2];
       double Jp = orc_jastrow(s, xp);
       double p = okp ? exp(2.0 * (logdet_p - logdet) + 2.0 * (Jp - J)) : 0.0;
+      /* |Psi_G(x')/Psi_G(x)|^2 = |Psi_T(x')/Psi_T(x)|^2 W(x) / W(x') */
+      double Wp = 1.0;
+      if (guided && okp) {
+        Wp = guiding_W(guiding_R(nu, Gp, Gpi, theta), eps);
+        p *= Wcur / Wp;
+      }
       if (uacc < p) {
         memcpy(x + 3 * e, rp, sizeof(double) * 3);
         memcpy(phi + (size_t)e * L, pnew, sizeof(double) * L);
@@ -679,6 +727,7 @@ static int vmc_walker(const orc_system *s, double *x, uint32_t wid, uint64_t see
         logdet = logdet_p;
         sgn = sgn_p;
         J = Jp;
+        Wcur = Wp;
         nacc++;
       }
     }
@@ -690,8 +739,9 @@ static int vmc_walker(const orc_system *s, double *x, uint32_t wid, uint64_t see
   }
   if (logpsi_out) logpsi_out[w] = logdet + J;
   if (n_acc_out) n_acc_out[w] = nacc;
+  if (R_out) R_out[w] = ok ? orc_guiding_R(s, x, theta > 0.0 ? theta : 0.375) : 0.0;
   (void)sgn;
-  free(phi); free(G); free(Gp); free(pnew); free(vec); free(xp);
+  free(phi); free(G); free(Gp); free(pnew); free(vec); free(xp); free(Gi); free(Gpi);
   return ok;
 }
 
@@ -709,7 +759,28 @@ int orc_vmc(const orc_system *s, double *x, int W, long long walker0, uint64_t s
 #pragma omp parallel for schedule(dynamic) reduction(+ : bad)
   for (int w = 0; w < W; ++w)
     if (!vmc_walker(s, x + (size_t)w * N * 3, (uint32_t)(walker0 + w), seed, (uint32_t)sweep0, nsweeps,
-                    delta, eL_out, W, w, logpsi_out, n_acc))
+                    delta, eL_out, W, w, logpsi_out, n_acc, 0.0, 0.0, NULL))
+      bad++;
+  return bad == 0;
+}
+
+/* orc_vmc sampling the guiding function Psi_G = (max(R, eps) / R) Psi_T
+ * (Eq. guiding_function) instead of Psi_T: the acceptance probability is
+ * |Psi_T(x')/Psi_T(x)|^2 W(x) / W(x').  R_out [W] (may be NULL) receives R of
+ * each walker's final configuration. */
+int orc_vmc_guided(const orc_system *s, double *x, int W, long long walker0, uint64_t seed, long long sweep0,
+                   int nsweeps, double delta, double theta, double eps, double *eL_out, double *logpsi_out,
+                   long long *n_acc, double *R_out, int nthreads) {
+  int N = s->n_up + s->n_dn, bad = 0;
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+  (void)nthreads;
+#endif
+#pragma omp parallel for schedule(dynamic) reduction(+ : bad)
+  for (int w = 0; w < W; ++w)
+    if (!vmc_walker(s, x + (size_t)w * N * 3, (uint32_t)(walker0 + w), seed, (uint32_t)sweep0, nsweeps,
+                    delta, eL_out, W, w, logpsi_out, n_acc, theta, eps, R_out))
       bad++;
   return bad == 0;
 }

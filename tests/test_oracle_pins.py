@@ -754,3 +754,103 @@ def test_swct_derivatives_are_derivatives_along_the_warp():
             assert abs((lp - lm) / (2 * h) - dL[a, q]) < 1e-6 * (1 + abs(dL[a, q])), (a, q)
     # the warp moves charge with the nuclei: the total still vanishes (translation)
     assert np.abs(dE.sum(axis=0)).max() < 1e-7 * (1 + np.abs(dE).max())
+
+
+# ----------------------------------------------------------------------------
+# guiding function and reweighting (Sec. "Atomic forces", Eqs.
+# guiding_function, R_r, regularization, reweighting)
+# ----------------------------------------------------------------------------
+
+def test_guiding_R_is_scale_invariant():
+    """R is unchanged when G~ is scaled by a constant (lambda -> c lambda, N_up = N_dn)."""
+    s = synth.small_random(n_atoms=3, n_up=3, n_dn=3, per_atom=6, seed=93)
+    x = _rand_cfg(s, 94)
+    R1 = oracle.Oracle(s).guiding_R(x)
+    s.lam = np.ascontiguousarray(-7.5 * s.lam)
+    R2 = oracle.Oracle(s).guiding_R(x)
+    assert R1 > 0 and abs(R2 - R1) < 1e-12 * R1
+
+
+def test_guiding_R_vanishes_as_the_antisymmetric_part_to_the_power_2theta():
+    """Two up electrons approaching each other (a node of det G~ linear in their
+    separation d): sum |G~^{-1}|^2 grows as 1/d^2, so R ~ d^(2 theta)."""
+    s = synth.small_random(n_atoms=2, n_up=2, n_dn=2, per_atom=6, seed=95, use_j1=False, use_j2=False)
+    o = oracle.Oracle(s)
+    x = _rand_cfg(s, 96)
+    theta = 0.375
+    direction = np.array([0.3, -0.5, 0.8]) / np.linalg.norm([0.3, -0.5, 0.8])
+
+    def R(d):
+        y = x.copy()
+        y[1] = y[0] + d * direction
+        return o.guiding_R(y, theta)
+    for d in (1e-3, 1e-4):
+        assert abs(math.log2(R(d) / R(d / 2)) - 2 * theta) < 2e-3
+
+
+def test_guiding_R_stays_finite_for_an_electron_far_away():
+    """S = min_i sum_j |G~_ij|^2 vanishes with the row of an electron at infinity
+    and compensates the growth of G~^{-1}: R tends to a finite, non-zero value."""
+    s = synth.small_random(n_atoms=2, n_up=2, n_dn=2, per_atom=6, seed=97, use_j1=False, use_j2=False)
+    o = oracle.Oracle(s)
+    x = _rand_cfg(s, 98)
+    vals = []
+    for far in (3.0, 4.0, 5.0, 6.0):
+        y = x.copy()
+        y[0] = s.R[0] + far * np.array([1.0, 0.2, -0.1])
+        vals.append(o.guiding_R(y))
+    assert all(v > 0 for v in vals)
+    assert abs(vals[-1] / vals[-2] - 1.0) < abs(vals[1] / vals[0] - 1.0)
+
+
+def _eps_for_mean_weight(R, target=0.8):
+    lo, hi = 1e-12 * R.max(), R.max()
+    for _ in range(200):
+        eps = math.sqrt(lo * hi)
+        m = np.mean(np.minimum(1.0, R / eps) ** 2)
+        lo, hi = (eps, hi) if m > target else (lo, eps)
+    return math.sqrt(lo * hi)
+
+
+def test_guided_sampling_reweights_to_the_trial_distribution():
+    """Sampling Psi_G and weighting by W = (R / max(R, eps))^2 gives the same
+    energy as sampling Psi_T: <W e_L>_G / <W>_G = <e_L>_T within the error bars
+    (eps chosen so that <W> over Psi_T samples is 0.8)."""
+    s = synth.small_random(n_atoms=2, n_up=2, n_dn=2, per_atom=6, seed=99, Z=1.0)
+    o = oracle.Oracle(s)
+    W, sweeps, equil = 2048, 60, 20
+    x = np.ascontiguousarray(synth.init_walkers(s, W, seed=99))
+    eT, _, _ = o.vmc(x, sweeps, seed=99)
+    Rs = np.array([o.guiding_R(x[w]) for w in range(W)])
+    eps = _eps_for_mean_weight(Rs)
+    xg = np.ascontiguousarray(synth.init_walkers(s, W, seed=99))
+    eG, _, _, _ = o.vmc_guided(xg, sweeps, eps=eps, seed=101)
+    # the weights along the guided chains: recompute R per recorded sweep from the final walkers only
+    # (the estimator below uses per-walker means over the last sweeps, weighted at the final configuration)
+    Rg = np.array([o.guiding_R(xg[w]) for w in range(W)])
+    wg = np.minimum(1.0, Rg / eps) ** 2
+    assert 0.2 < wg.mean() < 0.97      # lower than under Psi_T: Psi_G samples the nodes more often
+    mT = eT[equil:].mean(axis=0)
+    errT = mT.std(ddof=1) / math.sqrt(W)
+    e_last = eG[-1]
+    est = np.sum(wg * e_last) / np.sum(wg)
+    errG = np.sqrt(np.sum((wg * (e_last - est)) ** 2)) / np.sum(wg)
+    assert abs(est - mT.mean()) < 4.5 * math.hypot(errT, errG), (est, mT.mean(), errT, errG)
+    # the stationary density of the guided chain is Psi_T^2 / W: for the observable
+    # 1/W the reweighting identity gives <W>_G = 1 / <1/W>_T (an inverted weight
+    # ratio in the acceptance would give <W^2>_T / <W>_T instead)
+    wt = np.minimum(1.0, Rs / eps) ** 2
+    inv = 1.0 / wt
+    ref = 1.0 / inv.mean()
+    err_ref = ref * ref * inv.std(ddof=1) / math.sqrt(W)
+    err_g = wg.std(ddof=1) / math.sqrt(W)
+    assert abs(wg.mean() - ref) < 4.5 * math.hypot(err_ref, err_g), (wg.mean(), ref, err_ref, err_g)
+    wrong = (wt ** 2).mean() / wt.mean()
+    assert abs(wrong - ref) > 10 * math.hypot(err_ref, err_g)
+    # without the weights the guided chain is a different (biased) distribution in general;
+    # an eps of zero reproduces the unguided chain exactly
+    xz = np.ascontiguousarray(synth.init_walkers(s, 16, seed=99))
+    xz2 = xz.copy()
+    e1, _, _ = o.vmc(xz, 5, seed=7)
+    e2, _, _, _ = o.vmc_guided(xz2, 5, eps=0.0, seed=7)
+    assert np.array_equal(xz, xz2) and np.array_equal(e1, e2)
