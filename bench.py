@@ -42,6 +42,21 @@ WORKLOAD = ("plain FP64 VMC: 16 He atoms in a 10 bohr cube (min separation 1.5),
 FP64_PEAK_TFLOPS = 1.25
 
 
+def _hbm_peak():
+    """Measured HBM copy bandwidth (MEASURED_PEAKS.json), else the fallback 6.8 TB/s."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            v = float(json.load(fh)["hbm_gbs"])
+        if v > 0:
+            return v, "measured HBM copy (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, KeyError, ValueError, TypeError):
+        pass
+    return 6800.0, "fallback HBM 6.8 TB/s (no MEASURED_PEAKS file)"
+
+
+HBM_GBS, HBM_SOURCE = _hbm_peak()
+
+
 def _bf16_sustained_peak():
     """BF16 dense tensor-core peak for kernels timed inside a long step: the
     sustained cuBLAS figure of MEASURED_PEAKS.json when that file is present,
@@ -57,12 +72,23 @@ def _bf16_sustained_peak():
 
 
 BF16_SUSTAINED_TFLOPS, BF16_PEAK_SOURCE = _bf16_sustained_peak()
-# BF16 slice-pair products per element of the mixed path's lambda products: the
-# up-spin rows (phi^T lambda, FP32 result) take 10, the down-spin rows (lambda
-# phi, two-float result) 15; accepted moves are split between the spins in
-# proportion to their electron counts when the issued work is counted
-PAIRS_UP, PAIRS_DN = 10, 15
+# BF16 slice-pair products per element of the mixed path's lambda products:
+# both the up-spin rows (phi^T lambda) and the down-spin rows (lambda phi) take
+# all 15 pairs of the five-slice operands (two-float results)
+PAIRS_UP, PAIRS_DN = 15, 15
 NO_AUTOTUNE = False  # --no-autotune: time the shape heuristics' tiles
+
+
+def tensor_roofline(kernel, achieved, issued, launches, prof_ms, ms, work):
+    """Roofline of a tensor-core kernel: `achieved` is the method's work
+    (algorithmic flops) per second of kernel time, against the measured BF16
+    peak; the issued BF16 slice-pair rate is reported beside it."""
+    return {"kernel": kernel, "bound": "tensor", "achieved": achieved, "peak": BF16_SUSTAINED_TFLOPS,
+            "unit": "TFLOP/s", "frac": achieved / BF16_SUSTAINED_TFLOPS if achieved else None, "traffic": None,
+            "work": work, "issued_tflops": issued,
+            "issued_frac": issued / BF16_SUSTAINED_TFLOPS if issued else None, "peak_source": BF16_PEAK_SOURCE,
+            "launches": launches, "avg_launch_ms": prof_ms / max(launches, 1),
+            "share_of_step": prof_ms / ms if ms > 0 else None}
 
 
 def fixed_pairs(sysm):
@@ -145,15 +171,16 @@ class ClockSampler:
 # ----------------------------------------------------------------------------
 # CPU oracle (test infrastructure) timed on the host cores
 # ----------------------------------------------------------------------------
-def oracle_rate(sysm, target_s: float = 15.0, max_walkers: int = 4096):
+def oracle_rate(sysm, target_s: float = 15.0, max_walkers: int = 4096, threads: int = 0):
     """Oracle VMC sweeps + local energies on a bounded sample of the same
     workload (up to all of its walkers, then more sweeps) sized to roughly
-    target_s seconds; returns (moves/s, e_L/s, cores, sample description, seconds)."""
+    target_s seconds, on all host cores (threads = 0) or the given number;
+    returns (moves/s, e_L/s, cores, sample description, seconds)."""
     import oracle
     import synth
     o = oracle.Oracle(sysm)
-    cores = oracle.max_threads()
-    Ws, sweeps = max(cores, 8), 1
+    cores = threads if threads > 0 else oracle.max_threads()
+    Ws, sweeps = max(cores, 8) if threads == 0 else 2, 1
     while True:
         x = synth.init_walkers(sysm, Ws, seed=0)
         t0 = time.perf_counter()
@@ -171,13 +198,35 @@ def oracle_rate(sysm, target_s: float = 15.0, max_walkers: int = 4096):
             f"{Ws} walkers x {sweeps} sweep(s) (+ e_L per walker and sweep) of the same system", dt)
 
 
+# Arm CPU part numbers (/proc/cpuinfo "CPU part") of the cores these boxes may carry
+ARM_PARTS = {"0xd4f": "Arm Neoverse V2", "0xd40": "Arm Neoverse V1", "0xd0c": "Arm Neoverse N1",
+             "0xd49": "Arm Neoverse N2", "0xd84": "Arm Neoverse V3", "0xd8e": "Arm Neoverse N3"}
+
+
 def cpu_model():
+    """The host CPU's model name: lscpu's, else /proc/cpuinfo's model name, else
+    the Arm core named from its part number."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                name = line.split(":", 1)[1].strip()
+                if name and name != "-":
+                    return name
+    except Exception:
+        pass
+    part = None
     try:
         for line in open("/proc/cpuinfo"):
-            if line.lower().startswith(("model name", "cpu part")):
+            low = line.lower()
+            if low.startswith("model name"):
                 return line.split(":", 1)[1].strip()
+            if low.startswith("cpu part"):
+                part = line.split(":", 1)[1].strip()
     except OSError:
         pass
+    if part:
+        return ARM_PARTS.get(part, f"Arm core part {part}")
     return os.uname().machine
 
 
@@ -257,6 +306,7 @@ def timed_sweeps(pg, torch, dist, sysm, W, walker0, x0, prec, steps, warmup, ws,
     r = g.positions(x0)
     stream = torch.cuda.current_stream()
     eL = torch.empty((1, W), dtype=torch.float64, device=dev)
+    eL_steps = torch.empty((steps, W), dtype=torch.float64, device=dev)
     acc_steps = torch.empty((steps, 4), dtype=torch.float64, device=dev)
     acc_tmp = torch.empty((1, 4), dtype=torch.float64, device=dev)
     pg.jagp_eval(h, r, W, g.state)
@@ -275,7 +325,7 @@ def timed_sweeps(pg, torch, dist, sysm, W, walker0, x0, prec, steps, warmup, ws,
         torch.cuda.nvtx.range_push(label)
         e_start.record(stream)
         for k in range(steps):
-            pg.vmc_sweep(h, r, g.state, W, 1, walker0, warmup + k, eL, acc_steps[k:k + 1])
+            pg.vmc_sweep(h, r, g.state, W, 1, walker0, warmup + k, eL_steps[k:k + 1], acc_steps[k:k + 1])
         e_stop.record(stream)
         torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
@@ -290,14 +340,17 @@ def timed_sweeps(pg, torch, dist, sysm, W, walker0, x0, prec, steps, warmup, ws,
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     acc = acc_steps.cpu().numpy()
     bits |= g.status()
-    return {"g": g, "r": r, "eL": eL, "ms": ms, "ms_max": float(t.item()), "launches": launches,
+    eL.copy_(eL_steps[-1:])
+    return {"g": g, "r": r, "eL": eL, "eL_steps": eL_steps, "acc_steps": acc_steps, "ms": ms,
+            "ms_max": float(t.item()), "launches": launches,
             "prof_ms": prof_ms, "prof_n": prof_n, "accepted": float(acc[:, 2].sum()), "bits": bits,
             "clocks": clk.summary(), "tuning": tuning}
 
 
 FORCES_WORKLOAD = ("adjoint gradients: 64 He atoms in a 16 bohr cube, N=128 (64 up, 64 down), 24 s/p/d Gaussians/"
                    "atom (L=1536), 2048 walkers/GPU; per configuration e_L, the ionic force vector (Hellmann-Feynman "
-                   "+ Pulay, Eq. forces:aad without space warp), d log|Psi|/d lambda and d log|Psi|/d b")
+                   "+ Pulay, Eq. forces:aad with the space-warp transformation), d log|Psi|/d lambda and "
+                   "d log|Psi|/d b")
 
 
 def forces_bench(pg, torch, dist, args, dev, rank, ws, local, fp64_tc=False):
@@ -320,8 +373,13 @@ def forces_bench(pg, torch, dist, args, dev, rank, ws, local, fp64_tc=False):
     f64 = dict(dtype=torch.float64, device=dev)
     L, na = sysm.L, sysm.n_atoms
     out = dict(eL=torch.empty(W, **f64), lam=torch.empty((L, L), **f64), jas=torch.empty(3, **f64),
-               R=torch.empty((na, 3), **f64))
-    call = lambda: pg.jagp_grad(g.h, r, g.state, W, work, sL, sE, out["eL"], out["lam"], out["jas"], out["R"])  # noqa
+               R=torch.empty((na, 3), **f64), Rw=torch.empty((W, na, 3), **f64),
+               r=torch.empty((W, sysm.N, 3), **f64))
+
+    def call():
+        # adjoint with the force seeds, then the space warp (Eq. forces:aad with the warp's total derivatives)
+        pg.jagp_grad(g.h, r, g.state, W, work, sL, sE, out["eL"], out["lam"], out["jas"], None, out["Rw"], out["r"])
+        pg.jagp_space_warp(g.h, r, W, out["r"], out["Rw"], seed_logpsi=sL, dR=out["R"])
     for _ in range(args.force_warmup):
         call()
     torch.cuda.synchronize()
@@ -343,22 +401,48 @@ def forces_bench(pg, torch, dist, args, dev, rank, ws, local, fp64_tc=False):
         dist.barrier()
     launches = pg.jagp_launch_count(g.h) - n0
     lam_ms, lam_n = pg.jagp_profile_read(g.h)
+    pg.jagp_profile(g.h, pg.KERNEL_LAMBDA_ROWS, False)
     ms = e0.elapsed_time(e1)
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    # the energy alone on the same configurations (log|Psi| and e_L: what a VMC
+    # energy evaluation costs), for the cost ratio of forces to energy
+    ecall = lambda: (pg.jagp_eval(g.h, r, W, g.state), pg.local_energy(g.h, r, g.state, W, out["eL"]))  # noqa
+    ecall()
+    torch.cuda.synchronize()
+    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2.record()
+    for _ in range(args.force_steps):
+        ecall()
+    e3.record()
+    torch.cuda.synchronize()
+    ems = e2.elapsed_time(e3)
+    t = torch.tensor([ms, ems], dtype=torch.float64, device=dev)
     if ws > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max, ems_max = float(t[0].item()), float(t[1].item())
     g.close()
     n, nd = sysm.n_up, sysm.n_dn
     flops = 2.0 * L * L * W * (n + nd)  # the two lambda-product launches: 2 L^2 per orbital row
     achieved = flops * args.force_steps / (lam_ms / 1e3) / 1e12 if lam_ms > 0 else None
+    if fp64_tc:
+        kp = (L + 63) // 64 * 64
+        nsl = 7 if L <= 512 else 8
+        issued = achieved * (nsl * (nsl + 1) // 2) * kp / L if achieved else None
+        roof = tensor_roofline("k_umma_gemm (tcgen05, FP64-equivalent adjoint lambda products, %d slices)" % nsl,
+                               achieved, issued, lam_n, lam_ms, ms,
+                               "2 L^2 FP64-equivalent flop per orbital row of the two adjoint lambda products")
+    else:
+        roof = {"kernel": "k_lambda_rows (adjoint orbital rows)", "bound": "alu", "achieved": achieved,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS if achieved else None,
+                "traffic": None, "work": "2 L^2 flop per orbital row of the two adjoint lambda products",
+                "launches": lam_n, "share_of_step": lam_ms / ms if ms > 0 else None}
     return {"metric": "E_L+forces/s", "value": W * ws * args.force_steps / (ms_max / 1e3), "unit": "configurations/s",
             "ms_per_step": ms_max / args.force_steps, "steps": args.force_steps, "warmup": args.force_warmup,
             "dtype": "f64", "workload": FORCES_WORKLOAD, "walkers_per_gpu": W, "gpu_launches": launches,
-            "roofline": {"kernel": "k_lambda_rows (adjoint orbital rows)", "bound": "alu", "achieved": achieved,
-                         "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / FP64_PEAK_TFLOPS if achieved else None, "traffic": None,
-                         "launches": lam_n, "share_of_step": lam_ms / ms if ms > 0 else None}}
+            "energy_only": {"metric": "E_L/s", "value": W * ws * args.force_steps / (ems_max / 1e3),
+                            "unit": "configurations/s", "ms_per_step": ems_max / args.force_steps,
+                            "note": "jagp_eval + local_energy on the same configurations"},
+            "forces_to_energy_cost": ms_max / ems_max if ems_max > 0 else None,
+            "roofline": roof}
 
 
 BATCH_WORKLOAD = ("batched uneven systems, mixed precision: 64 independent neutral He systems, N uniform in "
@@ -367,14 +451,20 @@ BATCH_WORKLOAD = ("batched uneven systems, mixed precision: 64 independent neutr
                   "spin half-sweep and at its end")
 
 
-def batch_bench(pg, torch, dist, args, dev, rank, ws):
-    """Walker-electron moves/s of the batched mixed-precision path."""
+def batch_bench(pg, torch, dist, args, dev, rank, ws, precision=None, sweeps=None):
+    """Walker-electron moves/s of the batched path (mixed precision unless
+    given), then the roofline of its lambda products from one profiled sweep
+    of every member outside the graph (CUDA events cannot sit inside it)."""
     import synth
+    if precision is None:
+        precision = pg.JAGP_PREC_MIXED
+    mixed = precision == pg.JAGP_PREC_MIXED
+    nsw = args.batch_sweeps if sweeps is None else sweeps
     systems = synth.config3_systems(seed=0, n_systems=args.batch_systems)
     W = args.batch_walkers
     members, pos, tunings = [], [], []
     for s in systems:
-        m = pg.JAGP(s, W, seed=0, precision=pg.JAGP_PREC_MIXED, refresh_moves=16)
+        m = pg.JAGP(s, W, seed=0, precision=precision, refresh_moves=16)
         p = m.positions(synth.init_walkers(s, W * ws, seed=0)[rank * W:(rank + 1) * W])
         m.eval(p)
         if not NO_AUTOTUNE:
@@ -389,9 +479,9 @@ def batch_bench(pg, torch, dist, args, dev, rank, ws):
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    torch.cuda.nvtx.range_push("batched")
+    torch.cuda.nvtx.range_push("batched" if mixed else "batched_fp64")
     e0.record()
-    b.sweep(args.batch_sweeps, sweep0=args.warmup)
+    b.sweep(nsw, sweep0=args.warmup)
     e1.record()
     torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
@@ -406,16 +496,42 @@ def batch_bench(pg, torch, dist, args, dev, rank, ws):
     for m in members:
         bits |= m.status()
     acc = b.acc.cpu().numpy()
+    launches_per_sweep = b.launches_per_sweep()
     b.close()
+    # roofline: every member's lambda products of one sweep, timed per launch
+    lam_ms, lam_n, flops = 0.0, 0, 0.0
+    acc1 = torch.empty((1, 4), dtype=torch.float64, device=dev)
+    for s, m, p in zip(systems, members, pos):
+        pg.jagp_profile(m.h, pg.KERNEL_LAMBDA_ROWS, True)
+        pg.jagp_profile_read(m.h)
+        pg.vmc_sweep(m.h, p, m.state, W, 1, rank * W, 100000, None, acc1)
+        ms_k, n_k = pg.jagp_profile_read(m.h)
+        pg.jagp_profile(m.h, pg.KERNEL_LAMBDA_ROWS, False)
+        lam_ms += ms_k
+        lam_n += n_k
+        flops += 2.0 * s.L * s.L * float(acc1[0, 2].item())
     for m in members:
         m.close()
-    moves = W * sum(s.N for s in systems) * args.batch_sweeps * ws
+    achieved = flops / (lam_ms / 1e3) / 1e12 if lam_ms > 0 else None
+    if mixed:
+        roof = tensor_roofline("k_umma_gemm (tcgen05, BF16 fixed-point slices), all member systems", achieved,
+                               achieved * 15 if achieved else None, lam_n, lam_ms, 0.0,
+                               "2 L^2 flop per accepted orbital row, summed over the systems of one sweep; issued: "
+                               "15 BF16 slice-pair products per flop (before padding K to 64)")
+    else:
+        roof = {"kernel": "k_lambda_rows, all member systems", "bound": "alu", "achieved": achieved,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS if achieved else None,
+                "traffic": None, "work": "2 L^2 flop per accepted orbital row, summed over the systems of one sweep",
+                "launches": lam_n, "avg_launch_ms": lam_ms / max(lam_n, 1)}
+    roof["note"] = "kernel time from one profiled sweep of each member outside the graph"
+    moves = W * sum(s.N for s in systems) * nsw * ws
     return {"metric": "walker-electron moves/s", "value": moves / (ms_max / 1e3), "unit": "walker-electron moves/s",
-            "ms_per_sweep": ms_max / args.batch_sweeps, "sweeps": args.batch_sweeps, "warmup": args.warmup,
-            "systems": len(systems), "walkers_per_system": W, "moves_per_sweep": moves // args.batch_sweeps // ws,
+            "ms_per_sweep": ms_max / nsw, "sweeps": nsw, "warmup": args.warmup,
+            "systems": len(systems), "walkers_per_system": W, "moves_per_sweep": moves // nsw // ws,
             "acceptance": float(acc[:, 2].sum()) / (moves / ws), "status_bits": bits,
-            "dtype": "f32+bf16 (f64 refresh)", "workload": BATCH_WORKLOAD,
-            "tuning": tuning_summary(tunings)}
+            "dtype": "f32+bf16 (f64 refresh)" if mixed else "f64", "workload": BATCH_WORKLOAD if mixed else
+            BATCH_WORKLOAD.replace("mixed precision", "plain FP64"), "graph_launches_per_sweep": launches_per_sweep,
+            "tuning": tuning_summary(tunings), "roofline": roof}
 
 
 def tuning_summary(tunings):
@@ -463,12 +579,211 @@ def large_bench(pg, torch, dist, args, dev, rank, ws, local):
             "acceptance": rr["accepted"] / (W * N * args.large_steps), "status_bits": rr["bits"],
             "gpu_launches": rr["launches"], "dtype": "f32+bf16 (f64 refresh)", "workload": LARGE_WORKLOAD,
             "clocks": rr["clocks"], "tuning": rr["tuning"],
-            "roofline": {"kernel": "k_umma_gemm (tcgen05, BF16 fixed-point slices)", "bound": "tensor",
-                         "achieved": tc, "peak": BF16_SUSTAINED_TFLOPS, "unit": "TFLOP/s",
-                         "frac": tc / BF16_SUSTAINED_TFLOPS if tc else None, "traffic": None,
-                         "peak_source": BF16_PEAK_SOURCE,
-                         "launches": rr["prof_n"], "share_of_step": rr["prof_ms"] / rr["ms"] if rr["ms"] > 0 else None},
+            "roofline": tensor_roofline("k_umma_gemm (tcgen05, BF16 fixed-point slices)",
+                                        2.0 * L * L * rr["accepted"] / secs / 1e12 if secs > 0 else None, tc,
+                                        rr["prof_n"], rr["prof_ms"], rr["ms"],
+                                        "2 L^2 flop per accepted orbital row (the lambda product); issued: 15 BF16 "
+                                        "slice-pair products per flop"),
             "forces": forces}
+
+
+PIPELINE_WORKLOAD = ("large system, full pipeline: the 512-electron system's 1024 walkers swept in mixed precision "
+                     "(autotuned tiles), and every 10 sweeps the FP64 adjoint forces (lambda products FP64-equivalent "
+                     "on the tensor cores) of a fixed subset of the walkers' current configurations: e_L, the ionic "
+                     "force vector (Hellmann-Feynman + Pulay, Eq. forces:aad with the space warp), d log|Psi|/d lambda "
+                     "and d/d b")
+
+
+def pipeline_bench(pg, torch, dist, args, dev, rank, ws, local):
+    """Config 5 as one timed pipeline: args.pipeline_sweeps mixed sweeps of all
+    walkers; after every args.pipeline_every sweeps the first
+    args.pipeline_force_walkers walkers' configurations go (device to device)
+    to an FP64 handle, which evaluates log|Psi|, e_L and the adjoint with the
+    force-estimator seeds.  Moves/s counts every walker's moves over the whole
+    region; E_L+forces/s counts the force configurations over the time of the
+    force phases (CUDA events around them on the same stream)."""
+    import numpy as np
+    import synth
+    sysm = synth.config5()
+    W, K = args.large_walkers, args.pipeline_force_walkers
+    S, every = args.pipeline_sweeps, args.pipeline_every
+    x0 = np.ascontiguousarray(synth.init_walkers(sysm, W * ws, seed=0)[rank * W:(rank + 1) * W])
+    gm = pg.JAGP(sysm, W, seed=0, precision=pg.JAGP_PREC_MIXED)
+    tuning = None if NO_AUTOTUNE else gm.autotune()
+    r = gm.positions(x0)
+    gf = pg.JAGP(sysm, K, seed=0, fp64_tc=True)
+    rf = torch.empty((K, sysm.N, 3), dtype=torch.float64, device=dev)
+    work = torch.empty(pg.jagp_grad_workspace_bytes(gf.h, K), dtype=torch.uint8, device=dev)
+    f64 = dict(dtype=torch.float64, device=dev)
+    L, na = sysm.L, sysm.n_atoms
+    eLf, lam = torch.empty(K, **f64), torch.empty((L, L), **f64)
+    jas, dR = torch.empty(3, **f64), torch.empty((na, 3), **f64)
+    eL = torch.empty((1, W), **f64)
+    stream = torch.cuda.current_stream()
+
+    Rw = torch.empty((K, na, 3), **f64)
+    rb = torch.empty((K, sysm.N, 3), **f64)
+
+    def forces():
+        rf.copy_(r[:K])
+        pg.jagp_eval(gf.h, rf, K, gf.state)
+        pg.local_energy(gf.h, rf, gf.state, K, eLf)
+        sL, sE, _ = pg.jagp_force_seeds(eLf)
+        pg.jagp_grad(gf.h, rf, gf.state, K, work, sL, sE, eLf, lam, jas, None, Rw, rb)
+        pg.jagp_space_warp(gf.h, rf, K, rb, Rw, seed_logpsi=sL, dR=dR)
+
+    pg.jagp_eval(gm.h, r, W, gm.state)
+    for k in range(3):
+        pg.vmc_sweep(gm.h, r, gm.state, W, 1, rank * W, k, eL, None)
+    forces()
+    torch.cuda.synchronize()
+    nforce = S // every
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nforce)]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n0 = pg.jagp_launch_count(gm.h) + pg.jagp_launch_count(gf.h)
+    with ClockSampler(local) as clk:
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("pipeline")
+        e0.record(stream)
+        q = 0
+        for t in range(S):
+            pg.vmc_sweep(gm.h, r, gm.state, W, 1, rank * W, 3 + t, eL, None)
+            if (t + 1) % every == 0:
+                ev[q][0].record(stream)
+                forces()
+                ev[q][1].record(stream)
+                q += 1
+        e1.record(stream)
+        torch.cuda.nvtx.range_pop()
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+    launches = pg.jagp_launch_count(gm.h) + pg.jagp_launch_count(gf.h) - n0
+    ms = e0.elapsed_time(e1)
+    fms = sum(a.elapsed_time(b) for a, b in ev)
+    t = torch.tensor([ms, fms], dtype=torch.float64, device=dev)
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms, fms = float(t[0].item()), float(t[1].item())
+    bits = gm.status() | gf.status()
+    force_norm = float(dR.norm().item())
+    gm.close()
+    gf.close()
+    return {"metric": "walker-electron moves/s", "value": W * sysm.N * S * ws / (ms / 1e3),
+            "unit": "walker-electron moves/s", "ms_total": ms, "sweeps": S, "force_every": every,
+            "force_evaluations": nforce, "force_walkers": K,
+            "forces": {"metric": "E_L+forces/s", "value": K * nforce * ws / (fms / 1e3), "unit": "configurations/s",
+                       "ms_per_evaluation": fms / max(nforce, 1)},
+            "sweep_share": (ms - fms) / ms if ms > 0 else None, "status_bits": bits, "gpu_launches": launches,
+            "dtype": "f32+bf16 sweeps (f64 refresh), f64 adjoint", "workload": PIPELINE_WORKLOAD,
+            "walkers_per_gpu": W, "clocks": clk.summary(), "tuning": tuning, "last_force_norm": force_norm}
+
+
+SR_WORKLOAD = ("stochastic reconfiguration on the C2 workload (16 He, N=32, L=320, 4096 walkers/GPU, after sweeps): "
+               "per-walker log-derivatives of every lambda entry and the three Jastrow parameters (P = L^2 + 3 = "
+               "102403), then the regularised step (eps = 1e-3) by matrix-free preconditioned CG")
+
+
+def sr_bench(pg, torch, dist, args, dev, rank, ws, local):
+    """SR steps per second: one step = jagp_logpsi_derivs (the M x P samples,
+    FP64 per-walker products) + jagp_sr_step with a fixed number of CG
+    iterations (each two passes over the samples, bound by HBM)."""
+    import numpy as np
+    import synth
+    sysm = synth.config2()
+    W = args.walkers
+    P = sysm.L * sysm.L + 3
+    x0 = np.ascontiguousarray(synth.init_walkers(sysm, W * ws, seed=0)[rank * W:(rank + 1) * W])
+    g = pg.JAGP(sysm, W, seed=0)
+    r = g.positions(x0)
+    g.eval(r)
+    g.sweep(r, 2, walker0=rank * W)
+    eL = g.local_energy(r)
+    O = torch.empty((W, P), dtype=torch.float64, device=dev)
+    work = torch.empty(pg.jagp_sr_workspace_bytes(W, P), dtype=torch.uint8, device=dev)
+    it = args.sr_iters
+    g.logpsi_derivs(r, O)
+    pg.jagp_sr_step(O, eL, eps=1e-3, delta=0.05, max_iter=it, tol=0.0, work=work)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    steps = args.sr_steps
+    d_ms = cg_ms = 0.0
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.nvtx.range_push("sr")
+    for _ in range(steps):
+        ev[0].record()
+        g.logpsi_derivs(r, O)
+        ev[1].record()
+        f, da, iters, res = pg.jagp_sr_step(O, eL, eps=1e-3, delta=0.05, max_iter=it, tol=0.0, work=work)
+        ev[2].record()
+        torch.cuda.synchronize()
+        d_ms += ev[0].elapsed_time(ev[1])
+        cg_ms += ev[1].elapsed_time(ev[2])
+    torch.cuda.nvtx.range_pop()
+    t = torch.tensor([d_ms, cg_ms], dtype=torch.float64, device=dev)
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    d_ms, cg_ms = float(t[0].item()), float(t[1].item())
+    g.close()
+    # the CG: two passes over the FP64 samples per iteration, plus the three of the set-up (Obar, diag S, f)
+    cg_bytes = (2.0 * iters + 3.0) * W * P * 8
+    gbs = cg_bytes / (cg_ms / steps / 1e3) / 1e9
+    n, nd, L = sysm.n_up, sysm.n_dn, sysm.L
+    dflops = 2.0 * W * (n * nd * L + n * L * L)
+    return {"metric": "SR steps/s", "value": steps * ws / ((d_ms + cg_ms) / 1e3), "unit": "steps/s",
+            "ms_per_step": (d_ms + cg_ms) / steps, "ms_log_derivs": d_ms / steps, "ms_solve": cg_ms / steps,
+            "cg_iterations": iters, "relative_residual": res, "parameters": P, "samples_per_gpu": W, "dtype": "f64",
+            "workload": SR_WORKLOAD,
+            "roofline": {"kernel": "SR solve (k_sr_rowdot + k_sr_colsum passes over the samples)", "bound": "hbm",
+                         "achieved": gbs, "peak": HBM_GBS, "unit": "GB/s", "frac": gbs / HBM_GBS, "traffic": None,
+                         "work": "(2 iterations + 3) x M x P x 8 bytes of samples read", "peak_source": HBM_SOURCE},
+            "log_derivs_roofline": {"kernel": "k_bgemm_tn (per-walker FP64 products)", "bound": "alu",
+                                    "achieved": dflops / (d_ms / steps / 1e3) / 1e12, "peak": FP64_PEAK_TFLOPS,
+                                    "unit": "TFLOP/s",
+                                    "frac": dflops / (d_ms / steps / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
+                                    "work": "2 (N_up N_dn L + N_up L^2) flop per walker"}}
+
+
+C1_WORKLOAD = ("plain FP64 VMC, 4 H atoms in a 3 bohr cube, N=4 (2 up, 2 down), 6 s+p Gaussians/atom (L=24), "
+               "spin-independent J2, no J1, 256 walkers/GPU")
+
+
+def c1_bench(pg, torch, dist, args, dev, rank, ws, local):
+    """The smallest configuration: launch- and latency-bound (a few microseconds
+    of work per kernel), reported as moves/s only."""
+    import numpy as np
+    import synth
+    sysm = synth.config1()
+    W = 256
+    x0 = np.ascontiguousarray(synth.init_walkers(sysm, W * ws, seed=0)[rank * W:(rank + 1) * W])
+    rr = timed_sweeps(pg, torch, dist, sysm, W, rank * W, x0, pg.JAGP_PREC_FP64, args.c1_sweeps, args.warmup, ws,
+                      dev, local, pg.KERNEL_LAMBDA_ROWS, label="c1")
+    rr["g"].close()
+    ms = rr["ms_max"]
+    return {"metric": "walker-electron moves/s", "value": W * sysm.N * args.c1_sweeps * ws / (ms / 1e3),
+            "unit": "walker-electron moves/s", "ms_per_sweep": ms / args.c1_sweeps, "sweeps": args.c1_sweeps,
+            "gpu_launches": rr["launches"], "launches_per_sweep": rr["launches"] / args.c1_sweeps,
+            "us_per_launch": ms * 1e3 / max(rr["launches"], 1), "dtype": "f64", "workload": C1_WORKLOAD,
+            "roofline": {"bound": "latency", "note": "each launch carries microseconds of work: the sweep is bound "
+                         "by launch latency and the sequential acceptance, not by a roofline", "frac": None}}
+
+
+def reblocked_energy(pg, eL_steps, acc_steps, ws, dev):
+    """VMC energy of the timed sweeps: the reblocked mean and error bar of this
+    rank's samples (jagp_reblock), and the sums over all ranks' accumulators
+    (the only collective of the data path: one all-reduce per statistics block)."""
+    from paper_2002_07401_gb300 import shard
+    levels, stats = pg.jagp_reblock(eL_steps)
+    st = stats.cpu().numpy()
+    tot = shard.sum_over_ranks(acc_steps[:, :3].sum(dim=0), device=dev).cpu().numpy()
+    T, W = eL_steps.shape
+    return {"mean": float(st[0]), "error": float(st[1]), "block_level": int(st[2]), "plateau": bool(st[3]),
+            "levels": int(levels.shape[0]), "samples": T * W,
+            "all_ranks_mean": float(tot[0] / (T * W * ws)),
+            "all_ranks_sum_eL2": float(tot[1]), "all_ranks_accepted": float(tot[2])}
 
 
 def large_forces(pg, torch, dist, sysm, xs, ws, dev):
@@ -545,13 +860,14 @@ def run_gpu(args):
                        pg.KERNEL_LAMBDA_ROWS)
     g, r, eL = run["g"], run["r"], run["eL"]
     h = g.h
+    energy = reblocked_energy(pg, run["eL_steps"], run["acc_steps"], ws, dev)
 
     # end to end through the public API with host buffers: pinned host positions
     # in, e_L and positions out, every step (state rebuilt by jagp_eval)
     hx = torch.from_numpy(x0.copy()).pin_memory()
     he = torch.empty(W, dtype=torch.float64).pin_memory()
     hr = torch.empty_like(hx).pin_memory()
-    e2e_steps = max(2, min(args.steps, 5))
+    e2e_steps = max(2, args.steps)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for k in range(e2e_steps):
@@ -587,9 +903,15 @@ def run_gpu(args):
     if not args.no_forces and not args.no_fp64tc:
         forces_tc = forces_bench(pg, torch, dist, args, dev, rank, ws, local, fp64_tc=True)
         forces_tc["dtype"] = "f64 (lambda products FP64-equivalent on tensor cores)"
-        forces_tc["roofline"] = None
     batched = None if args.no_batch else batch_bench(pg, torch, dist, args, dev, rank, ws)
+    batched64 = None
+    if not args.no_batch and not args.no_other:
+        batched64 = batch_bench(pg, torch, dist, args, dev, rank, ws, precision=pg.JAGP_PREC_FP64,
+                                sweeps=args.batch_fp64_sweeps)
     large = None if args.no_large else large_bench(pg, torch, dist, args, dev, rank, ws, local)
+    pipeline = None if args.no_large else pipeline_bench(pg, torch, dist, args, dev, rank, ws, local)
+    sr = None if args.no_sr else sr_bench(pg, torch, dist, args, dev, rank, ws, local)
+    c1 = None if args.no_c1 else c1_bench(pg, torch, dist, args, dev, rank, ws, local)
 
     if rank != 0:
         if ws > 1:
@@ -611,13 +933,10 @@ def run_gpu(args):
             kp = (L + 63) // 64 * 64
             issued = fixed_pairs(sysm) * 2.0 * kp * L * rr["accepted"]  # BF16 slice-pair products per row
             tc = issued / secs / 1e12 if secs > 0 else None
-            d["roofline"] = {"kernel": "k_umma_gemm (tcgen05, BF16 fixed-point slices)", "bound": "tensor",
-                             "achieved": tc, "peak": BF16_SUSTAINED_TFLOPS, "unit": "TFLOP/s",
-                             "frac": tc / BF16_SUSTAINED_TFLOPS if tc else None, "traffic": None,
-                             "algorithmic_tflops": achieved, "peak_source": BF16_PEAK_SOURCE,
-                             "launches": rr["prof_n"],
-                             "avg_launch_ms": rr["prof_ms"] / max(rr["prof_n"], 1),
-                             "share_of_step": rr["prof_ms"] / rr["ms"] if rr["ms"] > 0 else None}
+            d["roofline"] = tensor_roofline("k_umma_gemm (tcgen05, BF16 fixed-point slices)", achieved, tc,
+                                            rr["prof_n"], rr["prof_ms"], rr["ms"],
+                                            "2 L^2 flop per accepted orbital row (the lambda product); issued: "
+                                            "15 BF16 slice-pair products per flop on K padded to 64")
         else:
             traffic_per_row, _ = profiled_traffic(kernel_source_hash())
             rows_per_launch = rr["accepted"] / max(rr["prof_n"], 1)
@@ -657,12 +976,11 @@ def run_gpu(args):
         secs = tc64["prof_ms"] / 1e3
         issued = nsl * (nsl + 1) / 2 * 2.0 * kp * L * tc64["accepted"]
         tc = issued / secs / 1e12 if secs > 0 else None
-        o["roofline"] = {"kernel": "k_umma_gemm (tcgen05, FP64-equivalent: %d BF16 slices, FP64 epilogue)" % nsl,
-                         "bound": "tensor", "achieved": tc, "peak": BF16_SUSTAINED_TFLOPS, "unit": "TFLOP/s",
-                         "frac": tc / BF16_SUSTAINED_TFLOPS if tc else None, "traffic": None,
-                         "algorithmic_fp64_tflops": 2.0 * L * L * tc64["accepted"] / secs / 1e12 if secs > 0 else None,
-                         "peak_source": BF16_PEAK_SOURCE,
-                         "launches": tc64["prof_n"], "share_of_step": tc64["prof_ms"] / tc64["ms"] if tc64["ms"] else None}
+        o["roofline"] = tensor_roofline(
+            "k_umma_gemm (tcgen05, FP64-equivalent: %d BF16 slices, FP64 epilogue)" % nsl,
+            2.0 * L * L * tc64["accepted"] / secs / 1e12 if secs > 0 else None, tc, tc64["prof_n"], tc64["prof_ms"],
+            tc64["ms"], "2 L^2 FP64-equivalent flop per accepted orbital row; issued: %d BF16 slice-pair products "
+            "per flop on K padded to 64" % (nsl * (nsl + 1) // 2))
         o["precision"] = "fp64 (lambda products FP64-equivalent on tensor cores)"
         o["speedup_vs_primary"] = o["value"] / prim["value"]
         out["fp64_tc"] = o
@@ -672,12 +990,24 @@ def run_gpu(args):
         out["forces_fp64tc"] = forces_tc
     if batched is not None:
         out["batched"] = batched
+    if batched64 is not None:
+        out["batched_fp64"] = batched64
     if large is not None:
         out["large"] = large
+    if pipeline is not None:
+        out["pipeline"] = pipeline
+    if sr is not None:
+        out["sr"] = sr
+    if c1 is not None:
+        out["c1"] = c1
+    out["energy"] = energy
     if ws == 1 and not args.no_cpu_baseline:
         mv, els, cores, sample, secs = oracle_rate(sysm, target_s=args.cpu_seconds)
+        mv1, _, _, sample1, secs1 = oracle_rate(sysm, target_s=args.cpu_seconds / 3, threads=1)
         out["cpu_baseline"] = {"value": mv, "unit": UNIT, "cores": cores, "kind": "oracle",
-                               "sample": f"{sample}; {secs:.1f} s; {cpu_model()}"}
+                               "sample": f"{sample}; {secs:.1f} s; {cpu_model()}", "cpu_model": cpu_model(),
+                               "single_thread": {"value": mv1, "unit": UNIT, "cores": 1,
+                                                 "sample": f"{sample1}; {secs1:.1f} s"}}
     emit(out)
     if ws > 1:
         dist.barrier()
@@ -697,16 +1027,25 @@ def main():
     ap.add_argument("--no-forces", action="store_true", help="skip the E_L + forces measurement")
     ap.add_argument("--no-fp64tc", action="store_true", help="skip the FP64-equivalent tensor-core measurement")
     ap.add_argument("--force-walkers", type=int, default=2048)
-    ap.add_argument("--force-steps", type=int, default=2)
+    ap.add_argument("--force-steps", type=int, default=20)
     ap.add_argument("--force-warmup", type=int, default=1)
     ap.add_argument("--no-batch", action="store_true", help="skip the batched uneven-systems measurement")
     ap.add_argument("--batch-systems", type=int, default=64)
     ap.add_argument("--batch-walkers", type=int, default=512)
-    ap.add_argument("--batch-sweeps", type=int, default=20)
+    ap.add_argument("--batch-sweeps", type=int, default=50)
+    ap.add_argument("--batch-fp64-sweeps", type=int, default=20)
     ap.add_argument("--batch-streams", type=int, default=16)
     ap.add_argument("--no-large", action="store_true", help="skip the 512-electron mixed-precision measurement")
     ap.add_argument("--large-walkers", type=int, default=1024)
-    ap.add_argument("--large-steps", type=int, default=3)
+    ap.add_argument("--large-steps", type=int, default=20)
+    ap.add_argument("--pipeline-sweeps", type=int, default=20)
+    ap.add_argument("--pipeline-every", type=int, default=10)
+    ap.add_argument("--pipeline-force-walkers", type=int, default=64)
+    ap.add_argument("--no-sr", action="store_true", help="skip the stochastic-reconfiguration measurement")
+    ap.add_argument("--sr-steps", type=int, default=3)
+    ap.add_argument("--sr-iters", type=int, default=50)
+    ap.add_argument("--no-c1", action="store_true", help="skip the 4-electron latency-bound line")
+    ap.add_argument("--c1-sweeps", type=int, default=200)
     ap.add_argument("--large-only", action="store_true", help="run only the 512-electron measurement")
     ap.add_argument("--large-tuning", default=None,
                     help="JSON tile choices for the 512-electron line (jagp_set_tuning) instead of autotuning")

@@ -141,6 +141,42 @@ jagp_status_t vmc_sweep(jagp_handle_t h, double *d_r, void *d_state, int W, int 
 jagp_status_t local_energy(jagp_handle_t h, const double *d_r, void *d_state, int W, double *d_eL,
                            double *d_parts, void *stream);
 
+/* Per-walker log-derivatives for stochastic reconfiguration (Sec.
+ * "Derivatives with respect to variational parameters": O_k(x) =
+ * d ln|Psi(x)| / d alpha_k) of W walkers whose state is current (jagp_eval /
+ * vmc_sweep on d_r), for the P = L*L + 3 parameters: every entry of lambda
+ * taken as independent (row-major, O[mu L + nu] = sum_{i, j < N_dn}
+ * G~^{-1}[j][i] phi_mu(r_i^up) phi_nu(r_j^dn)), then b_ea, b_para, b_anti.
+ * d_O: [W][ldo] FP64, ldo >= P (device, caller-owned); d_work: device
+ * workspace of jagp_logpsi_derivs_workspace_bytes(h, W) bytes, 256-byte
+ * aligned.  FP64 handles only (UNSUPPORTED otherwise); INVALID_ARG for
+ * ldo < P.  Leaves d_state unchanged. */
+size_t jagp_logpsi_derivs_workspace_bytes(jagp_handle_t h, int W);
+jagp_status_t jagp_logpsi_derivs(jagp_handle_t h, const double *d_r, void *d_state, int W, void *d_work, double *d_O,
+                                 long long ldo, void *stream);
+
+/* One regularised stochastic-reconfiguration step (Sec. "Stochastic
+ * reconfiguration", Eqs. SRupdate and sr with the diagonal shift
+ * s'_kk = s_kk (1 + eps)) from M samples: d_O [M][ldo] log-derivatives (the
+ * first P columns are used) and d_eL [M] local energies, all device FP64.
+ *   Obar_k = (1/M) sum_i O_ik,  S_kl = (1/M) sum_i (O_ik - Obar_k)(O_il - Obar_l),
+ *   d_f[k] = f_k = -2 (1/M) sum_i (e_i - ebar)(O_ik - Obar_k)     (Eq. eq_general_force),
+ *   d_dalpha = delta (S')^{-1} f,
+ * solved by conjugate gradients preconditioned with diag(S') without forming
+ * S: each iteration multiplies by S' through two passes over the samples,
+ * (1/M) O_c^T (O_c v) + eps diag(S) v, O_c = O - Obar.  A parameter whose
+ * samples do not vary (S_kk = 0) keeps dalpha_k = 0.  Iterates until the
+ * residual norm is at most tol times that of f, or max_iter iterations;
+ * *h_iters and *h_resid (host, may be NULL) receive the iterations and the
+ * final relative residual.  d_work: device workspace of
+ * jagp_sr_workspace_bytes(M, P) bytes, 256-byte aligned.  Synchronises
+ * stream (the iteration is steered from the host).  Errors: INVALID_ARG for
+ * M < 2, P < 1, ldo < P, eps < 0, tol < 0 or a NULL pointer. */
+size_t jagp_sr_workspace_bytes(int M, int P);
+jagp_status_t jagp_sr_step(const double *d_O, long long ldo, const double *d_eL, int M, int P, double eps,
+                           double delta, int max_iter, double tol, void *d_work, double *d_f, double *d_dalpha,
+                           int *h_iters, double *h_resid, void *stream);
+
 /* Statistics of the sampled local energies (Sec. VMC: the VMC energy is the
  * mean of e_L over the Markov chain, its error bar from the correlated samples
  * by reblocking).  d_eL: [T][W] local energies of W walkers over T sweeps (as
@@ -179,6 +215,10 @@ jagp_status_t jagp_batch_create(jagp_batch_t *out, int S, const jagp_handle_t *h
                                 double *d_acc, int n_streams);
 jagp_status_t jagp_batch_sweep(jagp_batch_t b, int nsweeps, uint64_t sweep0, void *stream);
 jagp_status_t jagp_batch_destroy(jagp_batch_t b);
+/* Kernel launches (*h_kernels) and all nodes (*h_nodes, may be NULL) of the
+ * CUDA graph that one batched sweep replays (0 before the first
+ * jagp_batch_sweep captures it).  Host-only. */
+jagp_status_t jagp_batch_launches(jagp_batch_t b, long long *h_kernels, long long *h_nodes);
 
 /* Reverse-mode (adjoint) derivatives, Sec. "Derivatives of energy" (AAD) and
  * Eqs. eq_general_force, forces:aad (without the space warp):  for W walkers
@@ -200,6 +240,53 @@ size_t jagp_grad_workspace_bytes(jagp_handle_t h, int W);
 jagp_status_t jagp_grad(jagp_handle_t h, const double *d_r, void *d_state, int W, const double *d_seed_logpsi,
                         const double *d_seed_eL, void *d_work, double *d_eL, double *d_dlambda, double *d_djas,
                         double *d_dR, double *d_dR_walker, double *d_dr, void *stream);
+
+/* Space-warp coordinate transformation for the forces (Sec. "Atomic forces",
+ * Eq. forces:aad and the two total derivatives that follow it): electrons
+ * move with nucleus a by Delta R_a omega_a(r), omega_a(r) = kappa(|r - R_a|) /
+ * sum_b kappa(|r - R_b|), kappa(d) = 1/d^4.  Takes jagp_grad's per-walker
+ * outputs for the same d_r and seeds, d_rbar = d_dr [W][N][3] (sL d ln|Psi|/dr
+ * + sE d e_L/dr) and d_dR_walker [W][n_atoms][3] (the same w.r.t. R_a), and
+ * adds in place, per walker,
+ *   sum_i omega_a(r_i) d_rbar[w][i] + (sL_w / 2) sum_i grad omega_a(r_i)
+ * (d_seed_logpsi = sL, NULL = 0), so that d_dR_walker[w][a] becomes
+ * sE d e_L/dR_a + sL d ln(J^{1/2} Psi)/dR_a with the warp's total derivatives;
+ * d_dR [n_atoms][3] (may be NULL) receives their sum over walkers.  With the
+ * force seeds (jagp_force_seeds) the sum is minus the force.  Device pointers,
+ * asynchronous.  Errors: INVALID_ARG. */
+jagp_status_t jagp_space_warp(jagp_handle_t h, const double *d_r, int W, const double *d_rbar,
+                              const double *d_seed_logpsi, double *d_dR_walker, double *d_dR, void *stream);
+
+/* The guiding function's regularisation (Sec. "Atomic forces", Eqs. R_r,
+ * regularization, reweighting) for W walkers whose state is current:
+ *   R(x) = (S sum_{i,j} |G~^{-1}_{ij}|^2)^{-theta},  S = min_i sum_j |G~_ij|^2,
+ *   d_W[w] = (R / max(R, eps))^2   (the reweighting factor of Psi_G samples),
+ * d_R [W], d_W [W] device (either may be NULL, not both).  G~ is recomputed from
+ * the state's tables into the state's refresh scratch.  theta > 0 (the paper
+ * uses 3/8), eps >= 0.  Errors: INVALID_ARG. */
+jagp_status_t jagp_guiding_weights(jagp_handle_t h, void *d_state, int W, double theta, double eps, double *d_R,
+                                   double *d_W, void *stream);
+
+/* Sample the guiding function instead of the trial wave function (Sec.
+ * "Atomic forces", Eq. guiding_function): with eps > 0 every later vmc_sweep
+ * (and batched sweep) of h accepts a move with probability
+ * |Psi_T(x')/Psi_T(x)|^2 W(x) / W(x'), W = (R / max(R, eps))^2 and R as in
+ * jagp_guiding_weights, i.e. samples |Psi_G|^2 = |Psi_T|^2 / W; estimates then
+ * take the weights W (<W A>_G / <W>_G = <A>_T, Eq. reweighting).  eps = 0
+ * restores plain sampling.  Host-only.  Errors: INVALID_ARG (theta <= 0,
+ * eps < 0), UNSUPPORTED (eps > 0 on a mixed-precision handle or N_up > 64:
+ * the guided acceptance keeps G~ and G~^{-1} in shared memory). */
+jagp_status_t jagp_set_guiding(jagp_handle_t h, double theta, double eps);
+
+/* Seeds of the (reweighted) force estimator for jagp_grad (Sec. "Atomic
+ * forces", Eq. reweighting; Eq. eq_general_force): from local energies d_eL [M]
+ * and weights u = d_weight [M] (NULL: all 1), with U = sum u and
+ * E = sum u e / U,
+ *   d_seed_eL[i] = u_i / U,   d_seed_logpsi[i] = 2 u_i (e_i - E) / U,
+ * so that jagp_grad (plus jagp_space_warp) returns minus the force
+ * <W F>/<W>.  d_mean [2] (may be NULL) = (E, U / M).  Device pointers. */
+jagp_status_t jagp_force_seeds(const double *d_eL, const double *d_weight, int M, double *d_seed_logpsi,
+                               double *d_seed_eL, double *d_mean, void *stream);
 
 /* Copy per-walker bookkeeping to device arrays (each may be NULL):
  * log|Psi|, sign, accepted moves since jagp_eval, last drift, status bits. */

@@ -88,6 +88,8 @@ def lib():
         L.jagp_batch_create.restype = i
         L.jagp_batch_sweep.argtypes = [vp, i, u64, vp]
         L.jagp_batch_sweep.restype = i
+        L.jagp_batch_launches.argtypes = [vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]
+        L.jagp_batch_launches.restype = i
         L.jagp_batch_destroy.argtypes = [vp]
         L.jagp_batch_destroy.restype = i
         L.jagp_autotune.argtypes = [vp, vp, i, C.POINTER(_Tuning), vp]
@@ -98,6 +100,23 @@ def lib():
         L.jagp_eval_noalloc.restype = i
         L.jagp_last_cuda_error.argtypes = []
         L.jagp_last_cuda_error.restype = C.c_char_p
+        L.jagp_logpsi_derivs_workspace_bytes.argtypes = [vp, i]
+        L.jagp_logpsi_derivs_workspace_bytes.restype = C.c_size_t
+        L.jagp_logpsi_derivs.argtypes = [vp, vp, vp, i, vp, vp, C.c_longlong, vp]
+        L.jagp_logpsi_derivs.restype = i
+        L.jagp_sr_workspace_bytes.argtypes = [i, i]
+        L.jagp_sr_workspace_bytes.restype = C.c_size_t
+        L.jagp_sr_step.argtypes = [vp, C.c_longlong, vp, i, i, d, d, i, d, vp, vp, vp, C.POINTER(i), C.POINTER(d),
+                                   vp]
+        L.jagp_sr_step.restype = i
+        L.jagp_set_guiding.argtypes = [vp, d, d]
+        L.jagp_set_guiding.restype = i
+        L.jagp_space_warp.argtypes = [vp, vp, i, vp, vp, vp, vp, vp]
+        L.jagp_space_warp.restype = i
+        L.jagp_guiding_weights.argtypes = [vp, vp, i, d, d, vp, vp, vp]
+        L.jagp_guiding_weights.restype = i
+        L.jagp_force_seeds.argtypes = [vp, vp, i, vp, vp, vp, vp]
+        L.jagp_force_seeds.restype = i
         L.jagp_reblock_levels.argtypes = [i]
         L.jagp_reblock_levels.restype = i
         L.jagp_reblock.argtypes = [vp, i, i, vp, vp, vp, vp]
@@ -230,6 +249,88 @@ def jagp_grad(h, r, state, W, work, seed_logpsi=None, seed_eL=None, eL=None, dla
     _check(lib().jagp_grad(h, _ptr(r), _ptr(state), int(W), _ptr(seed_logpsi), _ptr(seed_eL), _ptr(work), _ptr(eL),
                            _ptr(dlambda), _ptr(djas), _ptr(dR), _ptr(dR_walker), _ptr(dr), _stream(stream)),
            "jagp_grad", h)
+
+
+def jagp_logpsi_derivs_workspace_bytes(h, W) -> int:
+    return int(lib().jagp_logpsi_derivs_workspace_bytes(h, int(W)))
+
+
+def jagp_logpsi_derivs(h, r, state, W, work, O, stream=None):
+    _check(lib().jagp_logpsi_derivs(h, _ptr(r), _ptr(state), int(W), _ptr(work), _ptr(O), int(O.stride(0)),
+                                    _stream(stream)), "jagp_logpsi_derivs", h)
+
+
+def jagp_sr_workspace_bytes(M, P) -> int:
+    return int(lib().jagp_sr_workspace_bytes(int(M), int(P)))
+
+
+def jagp_sr_step(O, eL, eps=1e-3, delta=1.0, max_iter=500, tol=1e-12, P=None, work=None, stream=None):
+    """One regularised SR step from samples O [M][>= P] and eL [M] (device FP64;
+    see include/jagp.h).  Returns (f, dalpha, iterations, relative residual)."""
+    import torch
+    M = int(O.shape[0])
+    P = int(O.shape[1]) if P is None else int(P)
+    f64 = dict(dtype=torch.float64, device=O.device)
+    if work is None:
+        work = torch.empty(jagp_sr_workspace_bytes(M, P), dtype=torch.uint8, device=O.device)
+    f, da = torch.empty(P, **f64), torch.empty(P, **f64)
+    it, res = C.c_int(0), C.c_double(0.0)
+    _check(lib().jagp_sr_step(_ptr(O), int(O.stride(0)), _ptr(eL.contiguous()), M, P, float(eps), float(delta),
+                              int(max_iter), float(tol), _ptr(work), _ptr(f), _ptr(da), C.byref(it), C.byref(res),
+                              _stream(stream)), "jagp_sr_step")
+    return f, da, it.value, res.value
+
+
+def jagp_set_guiding(h, theta=0.375, eps=0.0):
+    _check(lib().jagp_set_guiding(h, float(theta), float(eps)), "jagp_set_guiding", h)
+
+
+def tune_guiding_eps(g, r, target=0.8, theta=0.375, sweeps=4, rounds=8, walker0=0, sweep0=0):
+    """Choose eps so that the mean reweighting factor <W> of the guided chain is
+    near `target` (the paper takes 0.8): bisection in log eps over short guided
+    runs of the JAGP object g on positions r (its state must be current).
+    Leaves g sampling the guiding function with the chosen eps."""
+    import torch
+    W = r.shape[0]
+    R = torch.empty(W, dtype=torch.float64, device=r.device)
+    jagp_guiding_weights(g.h, g.state, W, theta, 0.0, R=R)
+    Rs = R.sort().values
+    lo, hi = float(Rs[0]) * 1e-3, float(Rs[-1])
+    eps = float(torch.quantile(Rs, 1.0 - target))
+    wt = torch.empty(W, dtype=torch.float64, device=r.device)
+    for k in range(rounds):
+        jagp_set_guiding(g.h, theta, eps)
+        g.sweep(r, sweeps, walker0=walker0, sweep0=sweep0 + k * sweeps, energies=False)
+        jagp_guiding_weights(g.h, g.state, W, theta, eps, weights=wt)
+        m = float(wt.mean())
+        if m > target:
+            lo = eps
+        else:
+            hi = eps
+        eps = (lo * hi) ** 0.5
+    jagp_set_guiding(g.h, theta, eps)
+    return eps
+
+
+def jagp_space_warp(h, r, W, rbar, dR_walker, seed_logpsi=None, dR=None, stream=None):
+    _check(lib().jagp_space_warp(h, _ptr(r), int(W), _ptr(rbar), _ptr(seed_logpsi), _ptr(dR_walker), _ptr(dR),
+                                 _stream(stream)), "jagp_space_warp", h)
+
+
+def jagp_guiding_weights(h, state, W, theta=0.375, eps=0.0, R=None, weights=None, stream=None):
+    _check(lib().jagp_guiding_weights(h, _ptr(state), int(W), float(theta), float(eps), _ptr(R), _ptr(weights),
+                                      _stream(stream)), "jagp_guiding_weights", h)
+
+
+def jagp_force_seeds(eL, weights=None, stream=None):
+    """(seed_logpsi, seed_eL, (E, mean weight)) of the (reweighted) force estimator."""
+    import torch
+    M = int(eL.shape[0])
+    f64 = dict(dtype=torch.float64, device=eL.device)
+    sL, sE, mean = torch.empty(M, **f64), torch.empty(M, **f64), torch.empty(2, **f64)
+    _check(lib().jagp_force_seeds(_ptr(eL.contiguous()), _ptr(None if weights is None else weights.contiguous()), M,
+                                  _ptr(sL), _ptr(sE), _ptr(mean), _stream(stream)), "jagp_force_seeds")
+    return sL, sE, mean
 
 
 def jagp_reblock_levels(T) -> int:
@@ -403,6 +504,18 @@ class JAGP:
     def status(self, W=None) -> int:
         return jagp_walker_status(self.h, self.state, self.W if W is None else W)
 
+    def logpsi_derivs(self, r, O=None):
+        """Per-walker log-derivatives O [W][L*L + 3] (lambda entries, then
+        b_ea, b_para, b_anti) at the current state (jagp_logpsi_derivs)."""
+        import torch
+        W = r.shape[0]
+        P = self.sys.L * self.sys.L + 3
+        if O is None:
+            O = torch.empty((W, P), dtype=torch.float64, device=self.device)
+        work = torch.empty(jagp_logpsi_derivs_workspace_bytes(self.h, W), dtype=torch.uint8, device=self.device)
+        jagp_logpsi_derivs(self.h, r, self.state, W, work, O)
+        return O
+
     def grad(self, r, seed_logpsi=None, seed_eL=None, want_lambda=True):
         """Vector-Jacobian products of (log|Psi|, e_L) at the current state (see
         jagp_grad in include/jagp.h).  Returns a dict of device tensors."""
@@ -448,6 +561,12 @@ class Batch:
 
     def sweep(self, nsweeps, sweep0=0, stream=None):
         _check(lib().jagp_batch_sweep(self.b, int(nsweeps), int(sweep0), _stream(stream)), "jagp_batch_sweep")
+
+    def launches_per_sweep(self) -> int:
+        """Kernel launches in the graph one sweep replays (jagp_batch_launches)."""
+        k, n = C.c_longlong(0), C.c_longlong(0)
+        _check(lib().jagp_batch_launches(self.b, C.byref(k), C.byref(n)), "jagp_batch_launches")
+        return int(k.value)
 
     def close(self):
         if getattr(self, "b", None):

@@ -77,6 +77,14 @@ __device__ __forceinline__ fdw dw_sqrt(fdw x) {
   return fast_two_sum(s, __fdiv_rn(res, __fmul_rn(2.0f, s)));
 }
 
+// 1 / x as a double-word: the FP32 reciprocal y refined by one Newton step,
+// y' = y + y e with the residual e = 1 - x y formed exactly by an fma
+__device__ __forceinline__ fdw dw_recip(fdw x) {
+  const float y = __frcp_rn(x.hi);
+  const float e = __fadd_rn(__fmaf_rn(-x.hi, y, 1.0f), -__fmul_rn(x.lo, y));
+  return fast_two_sum(y, __fmul_rn(y, e));
+}
+
 // e^x for x <= 0 as a double-word, relative error ~1e-9:
 // Cody-Waite reduction x = k ln2 + r, |r| <= ln2/2, with ln2 split into three
 // FP32 parts (the first with 16 significant bits, so that k * part1 and the

@@ -75,11 +75,10 @@ Layout layout_of(const jagp_ctx *h, int W) {
 }
 
 // the fifteen slice pairs (a, b) with a + b <= 4 of the five-slice fixed-point
-// operands (each row kept to 2^-39 of its largest magnitude).  The rows
-// phi^T lambda (A_up) only feed FP32 work (proposed columns, M vectors), so
-// they take the first ten pairs (a + b <= 3: 2^-31, beyond FP32 rounding);
-// the rows lambda phi (Bt) enter G~ as two-float numbers and take all fifteen.
-constexpr int kFixedPairsF32 = 10;
+// operands (each row kept to 2^-39 of its largest magnitude).  Both lambda
+// products take all fifteen: the rows lambda phi (Bt) enter G~ and the up
+// electrons' M vectors, the rows phi^T lambda (A_up) the down electrons' M
+// vectors, all as two-float numbers.
 const int kPairA[kFixedPairs] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3, 0, 1, 2, 3, 4};
 const int kPairB[kFixedPairs] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0, 4, 3, 2, 1, 0};
 
@@ -177,11 +176,11 @@ jagp_status_t lambda_products(jagp_ctx *h, const float *P, const float *P_lo, fl
   LAUNCH(0, 1,
          launch_pack_fixed(P, P_lo, list, count, nrows, nsub, stride, h->ds.L, h->kp, pack, rows, exps, max_rows,
                             st));
-  // Bt rows (lambda phi) also keep their low parts for the refresh of G~
-  float *out_lo = left ? nullptr : at<float>(state, L.bt_lo);
+  // the rows keep their low parts (two-float Bt and A_up tables)
+  float *out_lo = at<float>(state, left ? L.a_up_lo : L.bt_lo);
   LAUNCH(JAGP_KERNEL_LAMBDA_ROWS, 1,
          launch_umma_gemm(pack, max_rows, count, kFixedSlices, left ? h->split_lamT : h->split_lam, h->ds.L,
-                          kFixedSlices, h->kp, left ? kFixedPairsF32 : kFixedPairs, kPairA, kPairB, out, h->ds.L,
+                          kFixedSlices, h->kp, kFixedPairs, kPairA, kPairB, out, h->ds.L,
                           rows, h->d_err, st, exps, left ? h->exp_lamT : h->exp_lam, out_lo,
                           left ? h->tune_bn_left : h->tune_bn_right, nullptr, 8, 0, 0,
                           left ? h->tune_st_left : h->tune_st_right));
@@ -206,14 +205,72 @@ float *lo_table(const jagp_ctx *h, void *state, size_t off) {
 double *refresh_g(const Layout &L, void *state) { return at<double>(state, L.g64); }
 
 // the local-energy sequence on a current state
+// Mixed path: the M vectors of the kinetic energy as exact fixed-point
+// tensor-core products of the FP64 inverse of the last refresh with the
+// two-float tables (five 8-bit slices per element, fifteen slice pairs, a
+// two-float result M + M_lo; every accumulator sum exact for N_up <= 256 but
+// the last, whose rounding lies below 2^-55 of the leading term):
+//   up:   M[i][mu]        = sum_j Bt[j][mu] Ginv[j][i]    (columns of Bt against columns of G~^{-1})
+//   down: M[n_up + j][mu] = sum_i A_up[i][mu] Ginv[j][i]  (columns of A_up against rows of G~^{-1})
+// as transposed products (the L basis functions of a walker are the rows of a
+// tile, its electrons the columns), written back transposed; for N_up up to
+// kMmatDwMaxUp the same sums as compensated dot products on the CUDA cores.
+// Then the per-shell contraction in double-word arithmetic.
+jagp_status_t run_kinetic_mixed(jagp_ctx *h, const double *r, void *state, int W, cudaStream_t st) {
+  const Layout L = layout_of(h, W);
+  const DevSystem &d = h->ds;
+  const int n = d.n_up, nd = d.n_dn, Lb = d.L, kpn = (n + 63) / 64 * 64;
+  const long long NL = (long long)d.N * Lb;
+  const double *gi64 = at<double>(state, L.ginv64);
+  uint16_t *pa = at<uint16_t>(state, L.mpack_a), *pb = at<uint16_t>(state, L.mpack_b);
+  int *ea = at<int>(state, L.mexp_a), *eb = at<int>(state, L.mexp_b), *mr = at<int>(state, L.mrows);
+  float *mb = at<float>(state, L.mbuf), *ml = at<float>(state, L.mbuf_lo);
+  if (n <= kMmatDwMaxUp) {
+    // small N_up: compensated sums on the CUDA cores (a tensor-core tile would be mostly padding)
+    LAUNCH(JAGP_KERNEL_ENERGY, 1,
+           launch_mmat_dw(d, gi64, at<float>(state, L.bt), at<float>(state, L.bt_lo), at<float>(state, L.a_up),
+                          at<float>(state, L.a_up_lo), mb, ml, W, st));
+    LAUNCH(JAGP_KERNEL_ENERGY, 1, launch_kinetic_m2(d, r, mb, ml, at<double>(state, L.kin), W, st));
+    return JAGP_OK;
+  }
+  // up electrons: A = columns of Bt (L rows per walker), B = columns of G~^{-1} (N_up rows)
+  LAUNCH(0, 1, launch_pack_cols(gi64, nullptr, nullptr, (size_t)n * n, n, n, kpn, W, pa, ea, nullptr, 0, 0, st));
+  LAUNCH(0, 1,
+         launch_pack_cols(nullptr, at<float>(state, L.bt), at<float>(state, L.bt_lo), (size_t)n * Lb, n, Lb, kpn, W,
+                          pb, eb, nullptr, 0, 0, st));
+  LAUNCH(JAGP_KERNEL_ENERGY, 1,
+         launch_umma_gemm(pb, W * Lb, nullptr, kFixedSlices, pa, n, kFixedSlices, kpn, kFixedPairs, kPairA, kPairB, mb,
+                          0, nullptr, h->d_err, st, eb, ea, ml, 0, nullptr, 8, Lb, W, 0, n, NL, 1, Lb));
+  if (nd > 0) {
+    // down electrons: A = columns of A_up, B = rows j < N_dn of G~^{-1}
+    LAUNCH(0, 1,
+           launch_pack_fixed64(gi64, nullptr, nullptr, W * nd, nd, n, n, kpn, kFixedSlices, 8, pa, mr, ea, W * nd, st));
+    LAUNCH(0, 1,
+           launch_pack_cols(nullptr, at<float>(state, L.a_up), at<float>(state, L.a_up_lo), (size_t)n * Lb, n, Lb,
+                            kpn, W, pb, eb, nullptr, 0, 0, st));
+    LAUNCH(JAGP_KERNEL_ENERGY, 1,
+           launch_umma_gemm(pb, W * Lb, nullptr, kFixedSlices, pa, nd, kFixedSlices, kpn, kFixedPairs, kPairA, kPairB,
+                            mb + (size_t)n * Lb, 0, nullptr, h->d_err, st, eb, ea, ml + (size_t)n * Lb, 0, nullptr, 8,
+                            Lb, W, 0, nd, NL, 1, Lb));
+  }
+  LAUNCH(JAGP_KERNEL_ENERGY, 1, launch_kinetic_m2(d, r, mb, ml, at<double>(state, L.kin), W, st));
+  return JAGP_OK;
+}
+
 template <typename T>
 jagp_status_t run_local_energy(jagp_ctx *h, const double *r, void *state, int W, double *eL, double *parts,
                                cudaStream_t st, bool write_jastrow = false) {
   const Layout L = layout_of(h, W);
-  LAUNCH(JAGP_KERNEL_ENERGY, 1,
-         launch_mmat<T>(h->ds, at<T>(state, L.ginv), at<T>(state, L.bt), at<T>(state, L.a_up), at<T>(state, L.mbuf), W,
-                        st));
-  LAUNCH(JAGP_KERNEL_ENERGY, 1, launch_kinetic<T>(h->ds, r, at<T>(state, L.mbuf), at<double>(state, L.kin), W, st));
+  if (std::is_same<T, float>::value) {
+    const jagp_status_t s = run_kinetic_mixed(h, r, state, W, st);
+    if (s != JAGP_OK) return s;
+  } else {
+    LAUNCH(JAGP_KERNEL_ENERGY, 1,
+           launch_mmat<T>(h->ds, at<T>(state, L.ginv), at<T>(state, L.bt), at<T>(state, L.a_up), at<T>(state, L.mbuf),
+                          W, st));
+    LAUNCH(JAGP_KERNEL_ENERGY, 1,
+           launch_kinetic<T>(h->ds, r, at<T>(state, L.mbuf), at<double>(state, L.kin), W, st));
+  }
   double *sc = write_jastrow ? at<double>(state, L.scal) : nullptr;
   if (std::is_same<T, float>::value)
     LAUNCH(JAGP_KERNEL_ENERGY, 1, launch_elocal_dw(h->ds, r, at<double>(state, L.kin), eL, parts, W, st, sc));
@@ -249,9 +306,11 @@ jagp_status_t run_refresh(jagp_ctx *h, const double *r, void *state, int W, int 
            refresh_geminal(at<T>(state, L.phi_up), lo_table(h, state, L.phi_lo), (size_t)n * Lb, at<T>(state, L.bt),
                            lo_table(h, state, L.bt_lo), (size_t)n * Lb, n, Lb, gm, W, st, h->tune_tile_refresh));
   }
+  // the mixed path keeps an FP64 copy of the inverse for the local energy
+  double *gi64 = h->precision == JAGP_PREC_MIXED ? at<double>(state, L.ginv64) : nullptr;
   LAUNCH(0, 1,
          launch_refresh_inverse<T>(gm, at<T>(state, L.ginv), at<double>(state, L.scal), at<int>(state, L.status), n,
-                                   W, check_drift, h->drift_tol, st));
+                                   W, check_drift, h->drift_tol, st, gi64));
   if (jastrow) LAUNCH(0, 1, launch_jastrow_full(h->ds, r, at<double>(state, L.scal), W, st));
   return JAGP_OK;
 }
@@ -326,9 +385,20 @@ jagp_status_t run_sweeps(jagp_ctx *h, double *d_r, void *d_state, int W, int nsw
     for (int m0 = 0; m0 < moves; m0 += step) {
       const int m1 = m0 + step < moves ? m0 + step : moves;
       JAGP_CU(cudaMemsetAsync(chunk, 0, sizeof(int), st));
-      LAUNCH(JAGP_KERNEL_METROPOLIS, 1,
-             launch_metropolis<T>(d, up, d_r, rprop, gprop, ginv, scal, status, pprop, phi_up, list, chunk, W, st,
-                                  pprop_lo, phi_lo, m0, m1, total));
+      bool guided = false;
+      if constexpr (std::is_same<T, double>::value) {
+        if (h->guide_eps > 0.0) {
+          guided = true;
+          LAUNCH(JAGP_KERNEL_METROPOLIS, 1,
+                 launch_metropolis_guided(d, up, d_r, rprop, gprop, ginv, scal, status, pprop, phi_up, list, chunk,
+                                          refresh_g(L, d_state), h->guide_theta, h->guide_eps, W, st, m0, m1,
+                                          total));
+        }
+      }
+      if (!guided)
+        LAUNCH(JAGP_KERNEL_METROPOLIS, 1,
+               launch_metropolis<T>(d, up, d_r, rprop, gprop, ginv, scal, status, pprop, phi_up, list, chunk, W, st,
+                                    pprop_lo, phi_lo, m0, m1, total));
       jagp_status_t q =
           lambda_products(h, pprop, pprop_lo, up ? a_up : bt, up, list, chunk, 0, 1, 0, W * n, d_state, W, st);
       if (q != JAGP_OK) return q;
@@ -584,6 +654,7 @@ jagp_status_t jagp_create(jagp_handle_t *out, const jagp_system_t *sys, const ja
     if (g_attr_err == cudaSuccess) g_attr_err = setup_energy_attributes();
     if (g_attr_err == cudaSuccess) g_attr_err = setup_umma_attributes();
     if (g_attr_err == cudaSuccess) g_attr_err = setup_adjoint_attributes();
+    if (g_attr_err == cudaSuccess) g_attr_err = setup_forces_attributes();
   });
   if (g_attr_err != cudaSuccess) {
     delete h;
@@ -812,9 +883,9 @@ jagp_status_t tune_products(jagp_ctx *h, void *state, int W, cudaStream_t st, ja
     // or chunk-major (-1: every slice of a K chunk per stage, each loaded once
     // for all pairs; two stages, where they fit)
     const int stages[4] = {0, 3, 2, -1};
-    const int npairs = f64 ? np64 : (left ? kFixedPairsF32 : kFixedPairs);
+    const int npairs = f64 ? np64 : kFixedPairs;
     const int *tpa = f64 ? pa64 : kPairA, *tpb = f64 ? pb64 : kPairB;
-    const int limit = f64 ? 64 : (left ? 128 : 96);
+    const int limit = f64 ? 64 : 96;
     float bs = 0.0f;
     int bbn = 0, bst = 0;
     for (int c = 0; c < 7; ++c)
@@ -831,9 +902,9 @@ jagp_status_t tune_products(jagp_ctx *h, void *state, int W, cudaStream_t st, ja
                                         exps, left ? h->exp_lamT : h->exp_lam, nullptr, cands[c],
                                         reinterpret_cast<double *>(dst), h->tc_bits, 0, 0, stages[q]);
               return launch_umma_gemm(pack, rows, nullptr, kFixedSlices, left ? h->split_lamT : h->split_lam, Lb,
-                                      kFixedSlices, h->kp, left ? kFixedPairsF32 : kFixedPairs, kPairA, kPairB,
+                                      kFixedSlices, h->kp, kFixedPairs, kPairA, kPairB,
                                       reinterpret_cast<float *>(dst), Lb, nullptr, h->d_err, st, exps,
-                                      left ? h->exp_lamT : h->exp_lam, left ? nullptr : at<float>(state, L.bt_lo),
+                                      left ? h->exp_lamT : h->exp_lam, at<float>(state, left ? L.a_up_lo : L.bt_lo),
                                       cands[c], nullptr, 8, 0, 0, stages[q]);
             },
             st, &ms));
@@ -891,10 +962,10 @@ static jagp_status_t jagp_set_tuning_impl(jagp_handle_t h, const jagp_tuning_t *
     const int np64 = slice_pairs(h->tc_slices, pa64, pb64);
     for (int side = 0; side < 2; ++side) {
       const bool left = side == 0;
-      const int limit = mixed ? (left ? 128 : 96) : 64;
+      const int limit = mixed ? 96 : 64;
       if (bn[side] < 0 || bn[side] % 16 || bn[side] > limit) return JAGP_ERR_INVALID_ARG;
       if (stg[side] < -1 || stg[side] == 1 || stg[side] > 6) return JAGP_ERR_INVALID_ARG;
-      const int npairs = mixed ? (left ? kFixedPairsF32 : kFixedPairs) : np64;
+      const int npairs = mixed ? kFixedPairs : np64;
       const int actual = umma_pick_bn(h->ds.L, bn[side] ? bn[side] : limit);
       if (stg[side] == -1 && !umma_chunk_fits(npairs, mixed ? kPairA : pa64, mixed ? kPairB : pb64, actual))
         return JAGP_ERR_INVALID_ARG;
@@ -949,6 +1020,7 @@ jagp_status_t jagp_gemm_bf16x(const uint16_t *d_A, int M, int a_terms, const uin
     if (g_attr_err == cudaSuccess) g_attr_err = setup_energy_attributes();
     if (g_attr_err == cudaSuccess) g_attr_err = setup_umma_attributes();
     if (g_attr_err == cudaSuccess) g_attr_err = setup_adjoint_attributes();
+    if (g_attr_err == cudaSuccess) g_attr_err = setup_forces_attributes();
   });
   if (g_attr_err != cudaSuccess) return JAGP_ERR_CUDA;
   const cudaError_t e = launch_umma_gemm(d_A, M, d_count, a_terms, d_B, N, b_terms, Kp, npairs, h_pair_a, h_pair_b,
@@ -1183,6 +1255,26 @@ jagp_status_t jagp_batch_sweep(jagp_batch_t b, int nsweeps, uint64_t sweep0, voi
   return JAGP_OK;
 }
 
+jagp_status_t jagp_batch_launches(jagp_batch_t b, long long *h_kernels, long long *h_nodes) {
+  if (!b || !h_kernels) return JAGP_ERR_INVALID_ARG;
+  *h_kernels = 0;
+  if (h_nodes) *h_nodes = 0;
+  if (!b->graph) return JAGP_OK;
+  size_t n = 0;
+  JAGP_CU(cudaGraphGetNodes(b->graph, nullptr, &n));
+  std::vector<cudaGraphNode_t> nodes(n);
+  JAGP_CU(cudaGraphGetNodes(b->graph, nodes.data(), &n));
+  long long k = 0;
+  for (size_t i = 0; i < n; ++i) {
+    cudaGraphNodeType t;
+    JAGP_CU(cudaGraphNodeGetType(nodes[i], &t));
+    k += t == cudaGraphNodeTypeKernel;
+  }
+  *h_kernels = k;
+  if (h_nodes) *h_nodes = (long long)n;
+  return JAGP_OK;
+}
+
 jagp_status_t jagp_batch_destroy(jagp_batch_t b) {
   if (!b) return JAGP_ERR_INVALID_ARG;
   if (b->exec) cudaGraphExecDestroy(b->exec);
@@ -1248,6 +1340,76 @@ jagp_status_t jagp_profile_read(jagp_handle_t h, double *h_total_ms, long long *
   return jagp_note(h, "jagp_profile_read", jagp_profile_read_impl(h, h_total_ms, h_launches));
 }
 
+size_t jagp_logpsi_derivs_workspace_bytes(jagp_handle_t h, int W) {
+  if (!h || W <= 0 || W > h->max_walkers) return 0;
+  const size_t blk = align256((size_t)W * h->ds.n_up * h->ds.L * 8);
+  return 2 * blk;
+}
+
+static jagp_status_t jagp_logpsi_derivs_impl(jagp_handle_t h, const double *d_r, void *d_state, int W, void *d_work,
+                                             double *d_O, long long ldo, void *stream) {
+  jagp_status_t s = check_walkers(h, W, d_state);
+  if (s != JAGP_OK) return s;
+  if (!d_r || !d_work || !d_O || (reinterpret_cast<uintptr_t>(d_work) & 255u)) return JAGP_ERR_INVALID_ARG;
+  const DevSystem &d = h->ds;
+  const int n = d.n_up, nd = d.n_dn, Lb = d.L;
+  const long long P = (long long)Lb * Lb + 3;
+  if (ldo < P) {
+    jagp_set_detail("ldo = %lld below the %lld parameters", ldo, P);
+    return JAGP_ERR_INVALID_ARG;
+  }
+  if (h->precision != JAGP_PREC_FP64) return JAGP_ERR_UNSUPPORTED;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const Layout L = layout_of(h, W);
+  const size_t blk = align256((size_t)W * n * Lb * 8);
+  double *phidn = reinterpret_cast<double *>(d_work);
+  double *ybuf = reinterpret_cast<double *>(static_cast<char *>(d_work) + blk);
+  // orbitals of the down electrons (rows j < N_dn of each walker's block)
+  LAUNCH(JAGP_KERNEL_BASIS, nd > 0, launch_basis_points<double>(d, false, d_r, W, n, nd, phidn, nullptr, nullptr, 0, 0, st));
+  // Y[i][nu] = sum_{j < N_dn} Ginv[j][i] phi_nu(r_j^dn); O_lambda[mu][nu] = sum_i phi_mu(r_i^up) Y[i][nu]
+  LAUNCH(0, 1,
+         launch_bgemm_tn(at<double>(d_state, L.ginv), (size_t)n * n, n, phidn, (size_t)n * Lb, Lb, nd, n, Lb, ybuf,
+                         (size_t)n * Lb, Lb, W, st));
+  LAUNCH(0, 1,
+         launch_bgemm_tn(at<double>(d_state, L.phi_up), (size_t)n * Lb, Lb, ybuf, (size_t)n * Lb, Lb, n, Lb, Lb, d_O,
+                         (size_t)ldo, Lb, W, st));
+  LAUNCH(0, 1, launch_sr_jastrow(d, d_r, d_O, ldo, (long long)Lb * Lb, W, st));
+  return JAGP_OK;
+}
+
+size_t jagp_sr_workspace_bytes(int M, int P) {
+  if (M <= 0 || P <= 0) return 0;
+  return sr_layout(M, P).total * sizeof(double);
+}
+
+jagp_status_t jagp_sr_step(const double *d_O, long long ldo, const double *d_eL, int M, int P, double eps,
+                           double delta, int max_iter, double tol, void *d_work, double *d_f, double *d_dalpha,
+                           int *h_iters, double *h_resid, void *stream) {
+  if (!d_O || !d_eL || !d_work || !d_f || !d_dalpha || M < 2 || P < 1 || ldo < P || max_iter < 0 || !(eps >= 0.0) ||
+      !(tol >= 0.0) || (reinterpret_cast<uintptr_t>(d_work) & 255u))
+    return JAGP_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const SrLayout L = sr_layout(M, P);
+  double *w = static_cast<double *>(d_work);
+  JAGP_CU(sr_prepare(d_O, ldo, d_eL, M, P, w, L, d_f, st));
+  JAGP_CU(sr_cg_init(d_f, eps, P, w, L, st));
+  double rr0 = 0.0, rr = 0.0;
+  JAGP_CU(cudaMemcpyAsync(&rr0, w + L.sc + 3, sizeof(double), cudaMemcpyDeviceToHost, st));
+  JAGP_CU(cudaStreamSynchronize(st));
+  rr = rr0;
+  int it = 0;
+  while (it < max_iter && rr > tol * tol * rr0 && rr > 0.0) {
+    JAGP_CU(sr_cg_iter(d_O, ldo, M, P, eps, w, L, st));
+    JAGP_CU(cudaMemcpyAsync(&rr, w + L.sc + 3, sizeof(double), cudaMemcpyDeviceToHost, st));
+    JAGP_CU(cudaStreamSynchronize(st));
+    ++it;
+  }
+  JAGP_CU(sr_finish(delta, P, w, L, d_dalpha, st));
+  if (h_iters) *h_iters = it;
+  if (h_resid) *h_resid = rr0 > 0.0 ? sqrt(rr / rr0) : 0.0;
+  return JAGP_OK;
+}
+
 int jagp_reblock_levels(int T) { return T >= 1 ? reblock_levels(T) : 0; }
 
 jagp_status_t jagp_reblock(const double *d_eL, int T, int W, double *d_work, double *d_levels, double *d_stats,
@@ -1256,6 +1418,78 @@ jagp_status_t jagp_reblock(const double *d_eL, int T, int W, double *d_work, dou
   if (reblock_levels(T) > 0 && !d_levels) return JAGP_ERR_INVALID_ARG;
   JAGP_CU(launch_reblock(d_eL, T, W, d_work, d_levels, d_stats, static_cast<cudaStream_t>(stream)));
   return JAGP_OK;
+}
+
+static jagp_status_t jagp_space_warp_impl(jagp_handle_t h, const double *d_r, int W, const double *d_rbar,
+                                          const double *d_seed_logpsi, double *d_dR_walker, double *d_dR,
+                                          void *stream) {
+  if (!h || W <= 0 || W > h->max_walkers || !d_r || !d_rbar || !d_dR_walker) return JAGP_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  LAUNCH(0, 1 + (d_dR != nullptr), launch_space_warp(h->ds, d_r, d_rbar, d_seed_logpsi, d_dR_walker, d_dR, W, st));
+  return JAGP_OK;
+}
+
+static jagp_status_t jagp_guiding_weights_impl(jagp_handle_t h, void *d_state, int W, double theta, double eps,
+                                               double *d_R, double *d_W, void *stream) {
+  jagp_status_t s = check_walkers(h, W, d_state);
+  if (s != JAGP_OK) return s;
+  if (!(theta > 0.0) || !(eps >= 0.0) || (!d_R && !d_W)) return JAGP_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const Layout L = layout_of(h, W);
+  const int n = h->ds.n_up, Lb = h->ds.L;
+  double *gm = refresh_g(L, d_state);
+  // G~ = Phi_up Bt^T from the current tables (FP64, or compensated from the two-float tables)
+  if (h->precision == JAGP_PREC_MIXED) {
+    LAUNCH(0, 1,
+           refresh_geminal(at<float>(d_state, L.phi_up), lo_table(h, d_state, L.phi_lo), (size_t)n * Lb,
+                           at<float>(d_state, L.bt), lo_table(h, d_state, L.bt_lo), (size_t)n * Lb, n, Lb, gm, W, st,
+                           -1));
+    LAUNCH(0, 1, launch_guiding<float>(gm, at<float>(d_state, L.ginv), n, W, theta, eps, d_R, d_W, st));
+  } else {
+    LAUNCH(0, 1,
+           refresh_geminal(at<double>(d_state, L.phi_up), nullptr, (size_t)n * Lb, at<double>(d_state, L.bt), nullptr,
+                           (size_t)n * Lb, n, Lb, gm, W, st, -1));
+    LAUNCH(0, 1, launch_guiding<double>(gm, at<double>(d_state, L.ginv), n, W, theta, eps, d_R, d_W, st));
+  }
+  return JAGP_OK;
+}
+
+jagp_status_t jagp_set_guiding(jagp_handle_t h, double theta, double eps) {
+  if (!h) return JAGP_ERR_INVALID_ARG;
+  if (!(theta > 0.0) || !(eps >= 0.0) || !std::isfinite(eps)) {
+    jagp_set_detail("theta = %g, eps = %g (theta > 0, eps >= 0)", theta, eps);
+    return jagp_note(h, "jagp_set_guiding", JAGP_ERR_INVALID_ARG);
+  }
+  if (eps > 0.0 && (h->precision != JAGP_PREC_FP64 || h->ds.n_up > kGuidedMaxUp)) {
+    jagp_set_detail("guided sampling needs an FP64 handle with N_up <= %d", kGuidedMaxUp);
+    return jagp_note(h, "jagp_set_guiding", JAGP_ERR_UNSUPPORTED);
+  }
+  h->guide_theta = theta;
+  h->guide_eps = eps;
+  return JAGP_OK;
+}
+
+jagp_status_t jagp_space_warp(jagp_handle_t h, const double *d_r, int W, const double *d_rbar,
+                              const double *d_seed_logpsi, double *d_dR_walker, double *d_dR, void *stream) {
+  return jagp_note(h, "jagp_space_warp",
+                   jagp_space_warp_impl(h, d_r, W, d_rbar, d_seed_logpsi, d_dR_walker, d_dR, stream));
+}
+
+jagp_status_t jagp_guiding_weights(jagp_handle_t h, void *d_state, int W, double theta, double eps, double *d_R,
+                                   double *d_W, void *stream) {
+  return jagp_note(h, "jagp_guiding_weights", jagp_guiding_weights_impl(h, d_state, W, theta, eps, d_R, d_W, stream));
+}
+
+jagp_status_t jagp_force_seeds(const double *d_eL, const double *d_weight, int M, double *d_seed_logpsi,
+                               double *d_seed_eL, double *d_mean, void *stream) {
+  if (!d_eL || M <= 0 || !d_seed_logpsi || !d_seed_eL) return JAGP_ERR_INVALID_ARG;
+  JAGP_CU(launch_force_seeds(d_eL, d_weight, M, d_seed_logpsi, d_seed_eL, d_mean, static_cast<cudaStream_t>(stream)));
+  return JAGP_OK;
+}
+
+jagp_status_t jagp_logpsi_derivs(jagp_handle_t h, const double *d_r, void *d_state, int W, void *d_work, double *d_O,
+                                 long long ldo, void *stream) {
+  return jagp_note(h, "jagp_logpsi_derivs", jagp_logpsi_derivs_impl(h, d_r, d_state, W, d_work, d_O, ldo, stream));
 }
 
 jagp_status_t jagp_last_error(jagp_handle_t h, char *buf, size_t len) {

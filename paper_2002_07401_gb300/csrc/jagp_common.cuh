@@ -19,6 +19,8 @@ constexpr int kFixedSlices = 5;    // 8-bit slices per element of the fixed-poin
 constexpr int kFixedPairs = 15;    // slice pairs (a, b) with a + b < kFixedSlices
 constexpr int kMaxPairs = 36;      // slice pairs of the FP64-equivalent products (eight slices)
 constexpr int kTcRefreshMinUp = 32;  // mixed path: G~ of a refresh on the tensor cores from this N_up on
+constexpr int kGuidedMaxUp = 64;     // guided sampling: G~ and G~^{-1} in shared memory up to this N_up
+constexpr int kMmatDwMaxUp = 32;     // mixed path: exact M vectors on the CUDA cores up to this N_up (tensor cores above)
 
 // Shell record packed for one 32-byte load: centre (x, y, z) and exponent.
 // info = l | radial << 2 | first-function-offset << 8.
@@ -74,6 +76,16 @@ struct Layout {
   size_t gexp_a;   // int    [W n_up]        their row exponents
   size_t gexp_b;   // int    [W n_up]
   size_t grows;    // int    [W n_up]        scratch row map of the packing
+  // mixed path, local energy: the M vectors as exact fixed-point tensor-core
+  // products of the FP64 inverse with the two-float tables (kpn = N_up padded to 64)
+  size_t ginv64;   // double [W][n_up][n_up] G~^{-1} of the last refresh in FP64
+  size_t a_up_lo;  // float  [W][n_up][L]    low parts of A_up (A_up + a_up_lo is a two-float table)
+  size_t mbuf_lo;  // float  [W][N][L]       low parts of the M vectors
+  size_t mpack_a;  // BF16   [W n_up][5 kpn] slices of G~^{-1} columns (up) or rows (down)
+  size_t mpack_b;  // BF16   [W L][5 kpn]    slices of Bt columns (up) or A_up columns (down)
+  size_t mexp_a;   // int    [W n_up]        their exponents
+  size_t mexp_b;   // int    [W L]
+  size_t mrows;    // int    [W n_up]        destination rows of the M product
   size_t total;
 };
 
@@ -113,6 +125,16 @@ inline Layout make_layout(size_t W, size_t nu, size_t N, size_t L, size_t esz = 
   l.gexp_a = take(gi);
   l.gexp_b = take(gi);
   l.grows = take(gi);
+  const bool mx = esz == 4;
+  const size_t kpn = (nu + 63) / 64 * 64;
+  l.ginv64 = take(mx ? W * nu * nu * 8 : 0);
+  l.a_up_lo = take(mx ? W * nu * L * 4 : 0);
+  l.mbuf_lo = take(mx ? W * N * L * 4 : 0);
+  l.mpack_a = take(mx ? W * nu * kFixedSlices * kpn * 2 : 0);
+  l.mpack_b = take(mx ? W * L * kFixedSlices * kpn * 2 : 0);
+  l.mexp_a = take(mx ? W * nu * 4 : 0);
+  l.mexp_b = take(mx ? W * L * 4 : 0);
+  l.mrows = take(mx ? W * nu * 4 : 0);
   l.total = o;
   return l;
 }
@@ -320,6 +342,14 @@ __device__ __forceinline__ void j1_d(double c, double b, double r, double *fp, d
     *fp = -0.5 * c4 * e;
     *fpp = 0.5 * c4 * c * b * e;
   }
+}
+// d/d b of an atom's J1 term F = -c^3 u(c r), u = (1 - e^{-b s}) / (2b) (the
+// b -> 0 limit at b = 0)
+__device__ __forceinline__ double j1_db(double c, double b, double r) {
+  const double s = c * r;
+  if (b == 0.0) return -c * c * c * (-s * s / 4.0);
+  const double e = exp(-b * s);
+  return -c * c * c * (s * e / (2.0 * b) - (1.0 - e) / (2.0 * b * b));
 }
 // pair term v(r) = r / (k (1 + b r)); parameters chosen by spins
 __device__ __forceinline__ void j2_params(const DevSystem &s, bool same, double *k, double *b) {

@@ -34,6 +34,8 @@ struct jagp_ctx {
   int tune_st_left = 0, tune_st_right = 0;  // and pipeline depth (0: as many stages as fit)
   int tune_tile_prop = -1;                  // per-walker proposal products (gemm_rows tile)
   int tune_tile_refresh = -1;               // per-walker refresh product G~ = Phi_up Bt^T
+  // guided sampling (jagp_set_guiding): eps > 0 samples Psi_G instead of Psi_T
+  double guide_theta = 0.375, guide_eps = 0.0;
   // text of the last failed call on this handle (jagp_last_error)
   jagp_status_t last_status = JAGP_OK;
   char last_error[512] = "no error";

@@ -28,6 +28,15 @@ cudaError_t launch_metropolis(const DevSystem &s, bool up, double *r, const doub
                               int *count, int W, cudaStream_t st, const float *pprop_lo = nullptr,
                               float *phi_lo = nullptr, int m_begin = 0, int m_end = -1, int *total = nullptr);
 
+// The Metropolis half-sweep (FP64, N_up <= kGuidedMaxUp) sampling the guiding
+// function: acceptance |Psi_T'/Psi_T|^2 W / W', W = (R / max(R, eps))^2; gmat
+// ([W][n][n], in/out) holds G~ of the current configurations.
+cudaError_t launch_metropolis_guided(const DevSystem &s, bool up, double *r, const double *rprop,
+                                     const double *gprop, double *ginv, double *scal, int *status,
+                                     const double *pprop, double *phi_up, int *list, int *count, double *gmat,
+                                     double theta, double eps, int W, cudaStream_t st, int m_begin, int m_end,
+                                     int *total);
+
 // Out[w][a][b] = sum_k X[w][a][k] Y[w][b][k]  (a < ma, b < nb, k < K); row stride K.
 // tile: -1 picks by shape, 0 one output per thread (16 x 16 tiles), 32 or 64
 // register-blocked tiles (the autotuner's choice)
@@ -54,10 +63,11 @@ template <typename T>
 cudaError_t launch_fill_unpaired(const DevSystem &s, T *bt, int W, cudaStream_t st);
 
 // Gauss-Jordan inverse with partial pivoting of G~ (in gm), log|det|, sign and
-// the Sherman-Morrison drift against the inverse held in ginv.
+// the Sherman-Morrison drift against the inverse held in ginv; ginv64 (or
+// null) also receives the inverse in FP64 (the mixed path's local energy)
 template <typename T>
 cudaError_t launch_refresh_inverse(double *gm, T *ginv, double *scal, int *status, int n, int W,
-                                   int check_drift, double drift_tol, cudaStream_t st);
+                                   int check_drift, double drift_tol, cudaStream_t st, double *ginv64 = nullptr);
 
 cudaError_t launch_jastrow_full(const DevSystem &s, const double *r, double *scal, int W,
                                 cudaStream_t st);
@@ -70,6 +80,13 @@ cudaError_t launch_mmat(const DevSystem &s, const T *ginv, const T *bt, const T 
 template <typename T>
 cudaError_t launch_kinetic(const DevSystem &s, const double *r, const T *mbuf, double *kin, int W,
                            cudaStream_t st);
+// the mixed path's two-float M vectors on the CUDA cores (small N_up): compensated
+// sums of the FP64 inverse against the two-float Bt / A_up tables
+cudaError_t launch_mmat_dw(const DevSystem &s, const double *ginv64, const float *bt, const float *bt_lo,
+                           const float *a_up, const float *a_lo, float *mbuf, float *mlo, int W, cudaStream_t st);
+// the mixed path's contraction with two-float M vectors, in double-word arithmetic
+cudaError_t launch_kinetic_m2(const DevSystem &s, const double *r, const float *mbuf, const float *mlo, double *kin,
+                              int W, cudaStream_t st);
 cudaError_t launch_elocal(const DevSystem &s, const double *r, const double *kin, double *eL,
                           double *parts, int W, cudaStream_t st, double *scal = nullptr);
 // the FP32 path's version (double-word distances, Coulomb sums and Jastrow values)
@@ -92,8 +109,10 @@ cudaError_t launch_increment(uint32_t *c, uint32_t by, cudaStream_t st);
 
 // Tensor-core contraction (k_umma.cu):
 //   out[out_rows[m]][c] = sum_p sum_k A[m][pair_a[p] kp + k] B[c][pair_b[p] kp + k]
-// (batched: A and B are `batches` stacked blocks of batch_rows rows, block b of
-// A against block b of B, c < n <= batch_rows; out rows as A's)
+// (batched: A is `batches` stacked blocks of batch_rows rows, B of b_batch_rows
+// rows (default batch_rows), block b of A against block b of B, c < n <=
+// b_batch_rows; out rows as A's, or with o_cstride != 0 the element of local row
+// r and column c of block b at out[b o_bstride + r o_rstride + c o_cstride])
 // A: BF16 [m_max][a_terms kp], B: BF16 [n][b_terms kp] (kp % 64 == 0, 16-byte
 // aligned bases); rows m < *m_dev (or m_max) are written; out FP32, pitch ldo.
 // With a_exp/b_exp (row / column exponents) the terms are fixed-point slices and
@@ -105,13 +124,22 @@ cudaError_t launch_umma_gemm(const uint16_t *A, int m_max, const int *m_dev, int
                              long long ldo, const int *out_rows, int *err, cudaStream_t st,
                              const int *a_exp = nullptr, const int *b_exp = nullptr, float *out_lo = nullptr,
                              int bn_max = 0, double *out64 = nullptr, int slice_bits = 8, int batch_rows = 0,
-                             int batches = 0, int stages_max = 0);
+                             int batches = 0, int stages_max = 0, int b_batch_rows = 0, long long o_bstride = 0,
+                             long long o_rstride = 0, long long o_cstride = 0);
 // whether two chunk-major stages (stages_max = -1) of these pairs fit at tile width bn
 bool umma_chunk_fits(int npairs, const int *pair_a, const int *pair_b, int bn);
-// FP64 rows -> nsl exact slices of `bits` bits per element plus a row exponent
+// FP64 rows -> nsl exact slices of `bits` bits per element plus a row exponent;
+// rows_out[m] = the source row, or (dst_stride > 0) (m / nsub) dst_stride + dst_off + m % nsub
 cudaError_t launch_pack_fixed64(const double *P, const int *list, const int *count, int nrows, int nsub, int stride,
                                 int L, int kp, int nsl, int bits, uint16_t *A, int *rows_out, int *exps,
-                                int max_rows, cudaStream_t st);
+                                int max_rows, cudaStream_t st, long dst_stride = 0, long dst_off = 0);
+// columns c < C of the per-walker matrices X_w ([R][C], X_w = X + w xw; FP64 X64,
+// or two-float X32 + Xlo) -> operand rows w C + c of kFixedSlices exact 8-bit
+// slices over the R rows (K padded to kp), exponents exps[w C + c], and
+// rows_out[w C + c] = w dst_stride + dst_off + c (when given)
+cudaError_t launch_pack_cols(const double *X64, const float *X32, const float *Xlo, size_t xw, int R, int C, int kp,
+                             int W, uint16_t *A, int *exps, int *rows_out, long dst_stride, long dst_off,
+                             cudaStream_t st);
 // FP32 rows (two-float rows P + P_lo when P_lo is given) -> kFixedSlices exact
 // 8-bit slices per element (BF16) plus a row exponent
 cudaError_t launch_pack_fixed(const float *P, const float *P_lo, const int *list, const int *count, int nrows,
@@ -152,6 +180,43 @@ cudaError_t setup_adjoint_attributes();
 int reblock_levels(int T);
 cudaError_t launch_reblock(const double *eL, int T, int W, double *work, double *levels, double *stats,
                            cudaStream_t st);
+
+// Stochastic reconfiguration (k_sr.cu).
+// Out[w][a][b] = sum_{k < K} X[w][k][a] Y[w][k][b] (per-walker FP64 products
+// with a shared leading index; row pitches ldx, ldy, ldo; walker strides xw, yw, ow)
+cudaError_t launch_bgemm_tn(const double *X, size_t xw, int ldx, const double *Y, size_t yw, int ldy, int K, int Ma,
+                            int Nb, double *Out, size_t ow, long long ldo, int W, cudaStream_t st);
+// d ln|Psi| / d (b_ea, b_para, b_anti) per walker into O[w][off + 0..2]
+cudaError_t launch_sr_jastrow(const DevSystem &s, const double *r, double *O, long long ldo, long long off, int W,
+                              cudaStream_t st);
+// workspace of the SR solve (offsets in doubles)
+struct SrLayout {
+  size_t obar, diag, dinv, x, r, z, p, q, u, part, ec, t, sc, total;
+};
+SrLayout sr_layout(int M, int P);
+// Obar, diag S and f = -(2/M) sum_i (e_i - ebar)(O_i - Obar) from the samples
+cudaError_t sr_prepare(const double *O, long long ldo, const double *e, int M, int P, double *w, const SrLayout &L,
+                       double *f, cudaStream_t st);
+// preconditioned CG on (S + eps diag S) x = f: start (x = 0), one iteration
+// (device scalars at w + L.sc: [0] r.z, [3] r.r), and dalpha = delta x
+cudaError_t sr_cg_init(const double *f, double eps, int P, double *w, const SrLayout &L, cudaStream_t st);
+cudaError_t sr_cg_iter(const double *O, long long ldo, int M, int P, double eps, double *w, const SrLayout &L,
+                       cudaStream_t st);
+cudaError_t sr_finish(double delta, int P, const double *w, const SrLayout &L, double *dalpha, cudaStream_t st);
+
+// Finite-variance forces (k_forces.cu).
+// rbar_at[w][a] += sum_i omega_a(r_i) rbar[w][i] + sL_w / 2 sum_i grad omega_a(r_i) (the space
+// warp); dR (or null) = sum_w rbar_at[w]
+cudaError_t launch_space_warp(const DevSystem &s, const double *r, const double *rbar, const double *sL,
+                              double *rbar_at, double *dR, int W, cudaStream_t st);
+// R = (min_i sum_j G_ij^2 sum_jk Ginv_jk^2)^-theta and W = (R / max(R, eps))^2 per walker
+template <typename T>
+cudaError_t launch_guiding(const double *g, const T *ginv, int n, int W, double theta, double eps, double *R,
+                           double *Wt, cudaStream_t st);
+// sE = u / sum u, sL = 2 u (e - E) / sum u, E = sum u e / sum u; mean_out = (E, mean u)
+cudaError_t launch_force_seeds(const double *e, const double *u, int M, double *sL, double *sE, double *mean_out,
+                               cudaStream_t st);
+cudaError_t setup_forces_attributes();
 
 // one-time kernel attribute set-up (dynamic shared memory limits), per file
 cudaError_t setup_kernel_attributes();

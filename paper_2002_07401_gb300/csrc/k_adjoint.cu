@@ -106,12 +106,6 @@ __device__ __forceinline__ void j1_d3(double c, double b, double r, double *f1, 
   *f2 = 0.5 * c4 * c * b * e;
   *f3 = -0.5 * c4 * c * c * b * b * e;
 }
-__device__ __forceinline__ double j1_db(double c, double b, double r) {
-  const double s = c * r;
-  if (b == 0.0) return -c * c * c * (-s * s / 4.0);
-  const double e = exp(-b * s);
-  return -c * c * c * (s * e / (2.0 * b) - (1.0 - e) / (2.0 * b * b));
-}
 __device__ __forceinline__ void j2_d3(double k, double b, double r, double *v1, double *v2, double *v3) {
   const double q = 1.0 + b * r;
   *v1 = 1.0 / (k * q * q);

@@ -168,6 +168,121 @@ template cudaError_t launch_kinetic<float>(const DevSystem &, const double *, co
                                            cudaStream_t);
 
 // ---------------------------------------------------------------------------
+// The mixed path's contraction with two-float M vectors (M + M_lo: exact
+// fixed-point tensor-core products of the FP64 inverse with the two-float
+// tables): the same per-shell formulas as k_kinetic with every step in
+// double-word arithmetic (FP32 instructions only), so that the result keeps
+// the M vectors' accuracy.  Rounding the shells' terms to FP32 would not: the
+// shells' contributions cancel to a sum that is smaller by about cond(G~),
+// which makes their FP32 rounding the dominant error of e_L at large N_up.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_kinetic_m2(DevSystem s, const double *__restrict__ r,
+                                                    const float *__restrict__ mbuf, const float *__restrict__ mlo,
+                                                    double *__restrict__ kin, int W) {
+  extern __shared__ double4 sh_geo[];
+  int *sh_info = reinterpret_cast<int *>(sh_geo + s.n_shells);
+  float4 *sh_dw = reinterpret_cast<float4 *>(sh_geo);
+  for (int k = threadIdx.x; k < s.n_shells; k += blockDim.x) {
+    sh_dw[2 * k] = s.shell_dw[2 * k];
+    sh_dw[2 * k + 1] = s.shell_dw[2 * k + 1];
+    sh_info[k] = s.shell_info[k];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const long nwarps = (long)gridDim.x * (blockDim.x >> 5);
+  const long total = (long)W * s.N;
+  const fdw zero{0.0f, 0.0f};
+  for (long pt = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); pt < total; pt += nwarps) {
+    const double *rr = r + pt * 3;
+    fdw pd[3];
+    {
+      const int kc = lane < 3 ? lane : 2;
+      const fdw mine = dw_of(rr[kc]);
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        pd[k] = fdw{__shfl_sync(0xffffffffu, mine.hi, k), __shfl_sync(0xffffffffu, mine.lo, k)};
+    }
+    const float *M = mbuf + pt * s.L, *Ml = mlo + pt * s.L;
+    fdw tx = zero, ty = zero, tz = zero, tl = zero;
+    for (int k = lane; k < s.n_shells; k += 32) {
+      const int info = sh_info[k];
+      const int l = shell_l(info), off = shell_off(info), rad = shell_rad(info);
+      const float4 gh = sh_dw[2 * k], gl = sh_dw[2 * k + 1];
+      const DwDisp d = dw_displacement(pd, gh, gl);
+      const fdw zw{gh.w, gl.w};
+      fdw g, rinv = zero;
+      if (rad) {
+        const fdw rw = dw_sqrt(d.r2);
+        g = dw_exp_neg(dw_neg(dw_mul(zw, rw)));
+        rinv = dw_recip(rw);
+      } else {
+        g = dw_exp_neg(dw_neg(dw_mul(zw, d.r2)));
+      }
+      fdw S0, Sx = zero, Sy = zero, Sz = zero;
+      const fdw m0{M[off], Ml[off]};
+      if (l == 0) {
+        S0 = m0;
+      } else if (l == 1) {
+        const fdw m1{M[off + 1], Ml[off + 1]}, m2{M[off + 2], Ml[off + 2]};
+        S0 = dw_add(dw_add(dw_mul(m0, d.x), dw_mul(m1, d.y)), dw_mul(m2, d.z));
+        Sx = m0;
+        Sy = m1;
+        Sz = m2;
+      } else {
+        const fdw m1{M[off + 1], Ml[off + 1]}, m2{M[off + 2], Ml[off + 2]}, m3{M[off + 3], Ml[off + 3]},
+            m4{M[off + 4], Ml[off + 4]};
+        const fdw xx = dw_mul(d.x, d.x), yy = dw_mul(d.y, d.y), zz = dw_mul(d.z, d.z);
+        S0 = dw_add(dw_add(dw_mul(m0, dw_mul(d.x, d.y)), dw_mul(m1, dw_mul(d.y, d.z))),
+                    dw_add(dw_mul(m2, dw_mul(d.z, d.x)), dw_mul(m3, dw_add(xx, dw_neg(yy)))));
+        S0 = dw_add(S0, dw_mul(m4, dw_add(dw_mul_f(zz, 3.0f), dw_neg(d.r2))));
+        const fdw d34 = dw_add(m3, dw_neg(m4)), s34 = dw_add(m3, m4);
+        Sx = dw_add(dw_add(dw_mul(m0, d.y), dw_mul(m2, d.z)), dw_mul_f(dw_mul(d34, d.x), 2.0f));
+        Sy = dw_add(dw_add(dw_mul(m0, d.x), dw_mul(m1, d.z)), dw_neg(dw_mul_f(dw_mul(s34, d.y), 2.0f)));
+        Sz = dw_add(dw_add(dw_mul(m1, d.y), dw_mul(m2, d.x)), dw_mul_f(dw_mul(m4, d.z), 4.0f));
+      }
+      fdw f, lapfac;
+      const fdw zz2 = dw_mul(zw, zw);
+      if (rad) {
+        f = dw_neg(dw_mul(dw_mul(zw, S0), rinv));
+        lapfac = dw_add(zz2, dw_neg(dw_mul_f(dw_mul(zw, rinv), static_cast<float>(2 * (l + 1)))));
+      } else {
+        f = dw_neg(dw_mul_f(dw_mul(zw, S0), 2.0f));
+        lapfac = dw_add(dw_mul_f(dw_mul(zz2, d.r2), 4.0f), dw_neg(dw_mul_f(zw, static_cast<float>(4 * l + 6))));
+      }
+      tx = dw_add(tx, dw_mul(g, dw_add(Sx, dw_mul(f, d.x))));
+      ty = dw_add(ty, dw_mul(g, dw_add(Sy, dw_mul(f, d.y))));
+      tz = dw_add(tz, dw_mul(g, dw_add(Sz, dw_mul(f, d.z))));
+      tl = dw_add(tl, dw_mul(dw_mul(g, S0), lapfac));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      tx = dw_add(tx, fdw{__shfl_xor_sync(0xffffffffu, tx.hi, o), __shfl_xor_sync(0xffffffffu, tx.lo, o)});
+      ty = dw_add(ty, fdw{__shfl_xor_sync(0xffffffffu, ty.hi, o), __shfl_xor_sync(0xffffffffu, ty.lo, o)});
+      tz = dw_add(tz, fdw{__shfl_xor_sync(0xffffffffu, tz.hi, o), __shfl_xor_sync(0xffffffffu, tz.lo, o)});
+      tl = dw_add(tl, fdw{__shfl_xor_sync(0xffffffffu, tl.hi, o), __shfl_xor_sync(0xffffffffu, tl.lo, o)});
+    }
+    if (lane == 0) {
+      double *o = kin + pt * 4;
+      o[0] = static_cast<double>(tx.hi) + tx.lo;
+      o[1] = static_cast<double>(ty.hi) + ty.lo;
+      o[2] = static_cast<double>(tz.hi) + tz.lo;
+      o[3] = static_cast<double>(tl.hi) + tl.lo;
+    }
+  }
+}
+
+cudaError_t launch_kinetic_m2(const DevSystem &s, const double *r, const float *mbuf, const float *mlo, double *kin,
+                              int W, cudaStream_t st) {
+  if (W <= 0) return cudaSuccess;
+  const long total = (long)W * s.N;
+  long blocks = (total + 7) / 8;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  const size_t smem = (size_t)s.n_shells * (sizeof(double4) + sizeof(int));
+  k_kinetic_m2<<<(int)blocks, 256, smem, st>>>(s, r, mbuf, mlo, kin, W);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // Jastrow value and derivatives, kinetic assembly and the Coulomb terms: one
 // CTA per walker.  With scal given, J = J1 + J2 is written too (the sweep then
 // needs no separate Jastrow pass).
@@ -276,13 +391,6 @@ __global__ void __launch_bounds__(128) k_elocal(DevSystem s, const double *__res
 // enough).  One CTA per walker; the per-thread sums are double-words,
 // combined in FP64 at the end.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ fdw dw_recip(fdw x) {
-  const float y = __frcp_rn(x.hi);
-  // e = 1 - x y (exactly as a double-word via fma), y' = y + y e
-  const float e = __fadd_rn(__fmaf_rn(-x.hi, y, 1.0f), -__fmul_rn(x.lo, y));
-  return fast_two_sum(y, __fmul_rn(y, e));
-}
-
 __global__ void __launch_bounds__(128) k_elocal_dw(DevSystem s, const double *__restrict__ r,
                                                    const double *__restrict__ kin, double *__restrict__ eL,
                                                    double *__restrict__ parts, double *__restrict__ scal) {
@@ -479,6 +587,8 @@ cudaError_t setup_energy_attributes() {
   cudaError_t e = cudaFuncSetAttribute(k_kinetic<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_elocal_dw, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_kinetic_m2, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_kinetic<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }

@@ -407,7 +407,8 @@ constexpr size_t kRefreshSmemMax = 200 * 1024;  // shared-memory rows of the in-
 template <typename T, int NM>
 __global__ void __launch_bounds__(128) k_refresh_inverse_reg(const double *__restrict__ gm, T *__restrict__ ginv,
                                                              double *__restrict__ scal, int *__restrict__ status,
-                                                             int n, int W, int check_drift, double drift_tol) {
+                                                             int n, int W, int check_drift, double drift_tol,
+                                                             double *__restrict__ ginv64) {
   constexpr int kGroups = 32 / NM;
   constexpr unsigned kFull = 0xffffffffu;
   const int lane = threadIdx.x & 31, c = lane & (NM - 1), g0 = lane - c;
@@ -483,6 +484,7 @@ __global__ void __launch_bounds__(128) k_refresh_inverse_reg(const double *__res
       const size_t idx = (size_t)qi * n + myp;
       if (check_drift) dmax = fmax(dmax, fabs(a[i] - static_cast<double>(gi[idx])));
       gi[idx] = static_cast<T>(a[i]);
+      if (ginv64) ginv64[(size_t)w * n * n + idx] = a[i];
     }
   }
 #pragma unroll
@@ -517,7 +519,8 @@ __global__ void __launch_bounds__(128) k_refresh_inverse_reg(const double *__res
 template <typename T>
 __global__ void __launch_bounds__(128) k_refresh_inverse_reg64(const double *__restrict__ gm, T *__restrict__ ginv,
                                                                double *__restrict__ scal, int *__restrict__ status,
-                                                               int n, int W, int check_drift, double drift_tol) {
+                                                               int n, int W, int check_drift, double drift_tol,
+                                                               double *__restrict__ ginv64) {
   constexpr unsigned kFull = 0xffffffffu;
   __shared__ double s_prow[2][2][64];                 // [walker slot][parity][column]
   __shared__ unsigned long long s_key[2][2][2];       // [slot][parity][half]
@@ -652,10 +655,12 @@ __global__ void __launch_bounds__(128) k_refresh_inverse_reg64(const double *__r
       if (c0 < n) {
         if (check_drift) dmax = fmax(dmax, fabs(a0[i] - static_cast<double>(gi[row + myp0])));
         gi[row + myp0] = static_cast<T>(a0[i]);
+        if (ginv64) ginv64[(size_t)w * n * n + row + myp0] = a0[i];
       }
       if (c1 < n) {
         if (check_drift) dmax = fmax(dmax, fabs(a1[i] - static_cast<double>(gi[row + myp1])));
         gi[row + myp1] = static_cast<T>(a1[i]);
+        if (ginv64) ginv64[(size_t)w * n * n + row + myp1] = a1[i];
       }
     }
   }
@@ -699,7 +704,8 @@ __global__ void __launch_bounds__(128) k_refresh_inverse_reg64(const double *__r
 template <typename T>
 __global__ void __launch_bounds__(512) k_refresh_inverse_inplace(double *__restrict__ gm, T *__restrict__ ginv,
                                                                  double *__restrict__ scal, int *__restrict__ status,
-                                                                 int n, int rs, int check_drift, double drift_tol) {
+                                                                 int n, int rs, int check_drift, double drift_tol,
+                                                                 double *__restrict__ ginv64) {
   extern __shared__ double sm[];
   const int ld = n + 1;
   double *prow = sm + (size_t)rs * ld;          // n: the scaled pivot row
@@ -828,6 +834,7 @@ __global__ void __launch_bounds__(512) k_refresh_inverse_inplace(double *__restr
     const double v = R(idx / n)[idx % n];
     if (check_drift) dmax = fmax(dmax, fabs(v - static_cast<double>(gi[idx])));
     gi[idx] = static_cast<T>(v);
+    if (ginv64) ginv64[(size_t)w * n * n + idx] = v;
   }
   for (int o = 16; o > 0; o >>= 1) {
     dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
@@ -857,16 +864,16 @@ __global__ void __launch_bounds__(512) k_refresh_inverse_inplace(double *__restr
 
 template <typename T>
 cudaError_t launch_refresh_inverse(double *gm, T *ginv, double *scal, int *status, int n, int W,
-                                   int check_drift, double drift_tol, cudaStream_t st) {
+                                   int check_drift, double drift_tol, cudaStream_t st, double *ginv64) {
   if (W <= 0) return cudaSuccess;
   const size_t aux = (size_t)n * (2 * sizeof(double) + sizeof(int));
   const size_t inplace_smem = (size_t)n * (n + 1) * sizeof(double) + aux;
   if (n > 32 && n <= 64) {
-    k_refresh_inverse_reg64<T><<<(W + 1) / 2, 128, 0, st>>>(gm, ginv, scal, status, n, W, check_drift, drift_tol);
+    k_refresh_inverse_reg64<T><<<(W + 1) / 2, 128, 0, st>>>(gm, ginv, scal, status, n, W, check_drift, drift_tol, ginv64);
     return cudaGetLastError();
   }
   if (n > 32 && inplace_smem <= kRefreshSmemMax) {
-    k_refresh_inverse_inplace<T><<<W, 256, inplace_smem, st>>>(gm, ginv, scal, status, n, n, check_drift, drift_tol);
+    k_refresh_inverse_inplace<T><<<W, 256, inplace_smem, st>>>(gm, ginv, scal, status, n, n, check_drift, drift_tol, ginv64);
     return cudaGetLastError();
   }
   if (n > 32) {
@@ -874,25 +881,25 @@ cudaError_t launch_refresh_inverse(double *gm, T *ginv, double *scal, int *statu
     // also keeps one CTA per SM), the rest in global memory
     const int rs = static_cast<int>((kRefreshSmemMax - aux) / ((size_t)(n + 1) * sizeof(double)));
     const size_t smem = (size_t)rs * (n + 1) * sizeof(double) + aux;
-    k_refresh_inverse_inplace<T><<<W, 512, smem, st>>>(gm, ginv, scal, status, n, rs, check_drift, drift_tol);
+    k_refresh_inverse_inplace<T><<<W, 512, smem, st>>>(gm, ginv, scal, status, n, rs, check_drift, drift_tol, ginv64);
     return cudaGetLastError();
   }
   if (n <= 32) {
     // 4 warps per CTA, 32 / NM walkers per warp
     if (n <= 8)
-      k_refresh_inverse_reg<T, 8><<<(W + 15) / 16, 128, 0, st>>>(gm, ginv, scal, status, n, W, check_drift, drift_tol);
+      k_refresh_inverse_reg<T, 8><<<(W + 15) / 16, 128, 0, st>>>(gm, ginv, scal, status, n, W, check_drift, drift_tol, ginv64);
     else if (n <= 16)
-      k_refresh_inverse_reg<T, 16><<<(W + 7) / 8, 128, 0, st>>>(gm, ginv, scal, status, n, W, check_drift, drift_tol);
+      k_refresh_inverse_reg<T, 16><<<(W + 7) / 8, 128, 0, st>>>(gm, ginv, scal, status, n, W, check_drift, drift_tol, ginv64);
     else
-      k_refresh_inverse_reg<T, 32><<<(W + 3) / 4, 128, 0, st>>>(gm, ginv, scal, status, n, W, check_drift, drift_tol);
+      k_refresh_inverse_reg<T, 32><<<(W + 3) / 4, 128, 0, st>>>(gm, ginv, scal, status, n, W, check_drift, drift_tol, ginv64);
     return cudaGetLastError();
   }
   return cudaErrorInvalidValue;
 }
 template cudaError_t launch_refresh_inverse<double>(double *, double *, double *, int *, int, int, int, double,
-                                                    cudaStream_t);
+                                                    cudaStream_t, double *);
 template cudaError_t launch_refresh_inverse<float>(double *, float *, double *, int *, int, int, int, double,
-                                                   cudaStream_t);
+                                                   cudaStream_t, double *);
 
 // ---------------------------------------------------------------------------
 // Kinetic-energy contraction vectors.  D = det G~ is linear in row i (up
@@ -1003,6 +1010,71 @@ __global__ void __launch_bounds__(256) k_mmat_tiled(DevSystem s, const T *__rest
   }
 }
 
+// The mixed path's M vectors for small N_up on the CUDA cores: the sums of
+// k_mmat with the FP64 inverse of the last refresh (split into two floats)
+// against the two-float tables, as compensated dot products (error-free
+// products and sums, the errors summed apart; Ogita, Rump and Oishi 2005) with
+// the cross terms of the low parts, so that M + M_lo keeps about twice the
+// FP32 precision.  One CTA per (walker, 64 columns).
+__global__ void __launch_bounds__(256) k_mmat_dw(DevSystem s, const double *__restrict__ ginv64,
+                                                 const float *__restrict__ bt, const float *__restrict__ bt_lo,
+                                                 const float *__restrict__ a_up, const float *__restrict__ a_lo,
+                                                 float *__restrict__ mbuf, float *__restrict__ mlo) {
+  extern __shared__ float smf[];
+  const int n = s.n_up, N = s.N, L = s.L;
+  const int w = blockIdx.y, c0 = blockIdx.x * 64, tid = threadIdx.x;
+  float *Gh = smf, *Gl = Gh + n * n;              // n*n each
+  float *Bh = Gl + n * n, *Bl = Bh + n * 64;       // n*64 each
+  float *Ah = Bl + n * 64, *Al = Ah + n * 64;      // n*64 each
+  for (int t = tid; t < n * n; t += 256) {
+    const fdw v = dw_of(ginv64[(size_t)w * n * n + t]);
+    Gh[t] = v.hi;
+    Gl[t] = v.lo;
+  }
+  for (int t = tid; t < n * 64; t += 256) {
+    const int j = t >> 6, c = t & 63;
+    const bool in = c0 + c < L;
+    const size_t src = ((size_t)w * n + j) * L + c0 + c;
+    Bh[t] = in ? bt[src] : 0.0f;
+    Bl[t] = in ? bt_lo[src] : 0.0f;
+    Ah[t] = in ? a_up[src] : 0.0f;
+    Al[t] = in ? a_lo[src] : 0.0f;
+  }
+  __syncthreads();
+  for (int idx = tid; idx < N * 64; idx += 256) {
+    const int e = idx >> 6, c = idx & 63;
+    if (c0 + c >= L) continue;
+    float sh = 0.0f, err = 0.0f;
+    const bool upe = e < n;
+    const int jj = e - n;
+    for (int j = 0; j < n; ++j) {
+      // up: Ginv[j][e] Bt[j][c]; down: Ginv[jj][j] A_up[j][c]
+      const int gi = upe ? j * n + e : jj * n + j;
+      const float gh = Gh[gi], gl = Gl[gi];
+      const float bh = upe ? Bh[j * 64 + c] : Ah[j * 64 + c], bl = upe ? Bl[j * 64 + c] : Al[j * 64 + c];
+      const fdw p = two_prod(gh, bh);
+      const fdw q = two_sum(sh, p.hi);
+      sh = q.hi;
+      err = __fadd_rn(err, __fadd_rn(q.lo, __fadd_rn(p.lo, __fmaf_rn(gh, bl, __fmul_rn(gl, bh)))));
+    }
+    const fdw r = fast_two_sum(sh, err);
+    const size_t o = ((size_t)w * N + e) * L + c0 + c;
+    mbuf[o] = r.hi;
+    mlo[o] = r.lo;
+  }
+}
+
+cudaError_t launch_mmat_dw(const DevSystem &s, const double *ginv64, const float *bt, const float *bt_lo,
+                           const float *a_up, const float *a_lo, float *mbuf, float *mlo, int W, cudaStream_t st) {
+  if (W <= 0) return cudaSuccess;
+  const int n = s.n_up;
+  const size_t smem = (size_t)(2 * n * n + 4 * n * 64) * sizeof(float);
+  if (smem > kMmatSmemMax) return cudaErrorInvalidValue;
+  dim3 grid((s.L + 63) / 64, W);
+  k_mmat_dw<<<grid, 256, smem, st>>>(s, ginv64, bt, bt_lo, a_up, a_lo, mbuf, mlo);
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_mmat(const DevSystem &s, const T *ginv, const T *bt, const T *a_up, T *mbuf, int W,
                         cudaStream_t st) {
@@ -1029,6 +1101,7 @@ static cudaError_t linalg_attrs() {
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(k_refresh_inverse_inplace<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)))
     return e;
+  if ((e = cudaFuncSetAttribute(k_mmat_dw, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
   return cudaFuncSetAttribute(k_mmat<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
 }
 

@@ -143,6 +143,7 @@ struct UmmaArgs {
   int batch_rows;        // batched mode (> 0): A and B are stacked per-batch blocks of batch_rows
                          // rows; batch b's rows of A meet only batch b's rows of B
   int tiles_per_batch;   // batched mode: 128-row tiles per batch
+  int b_batch_rows;      // batched mode: rows of B per batch (= batch_rows unless given)
   int chunk_major;       // 1: one stage holds every slice of one 64-wide K chunk of A (na) and B (nb),
   int na, nb;            //    and the MMA thread issues all pairs from it (slices loaded once per chunk)
   const int *a_exp;      // fixed-point mode: row exponents [m_max], else null
@@ -153,6 +154,9 @@ struct UmmaArgs {
   float *out_lo;         // fixed-point mode: low part of a two-float result, or null
   long long ldo;         // output row pitch (elements)
   const int *out_rows;   // destination row of row m, or null (= m)
+  // batched mode, affine output (o_cstride != 0): the element of local row r
+  // (within its batch b) and column c goes to out[b o_bstride + r o_rstride + c o_cstride]
+  long long o_bstride, o_rstride, o_cstride;
   int *err;
 };
 
@@ -180,7 +184,7 @@ __global__ void __launch_bounds__(128) k_umma_gemm(const __grid_constant__ CUten
   const int bb = g.batch_rows ? tile_y / g.tiles_per_batch : 0;
   const int bt0 = g.batch_rows ? (tile_y - bb * g.tiles_per_batch) * 128 : 0;
   const int m0 = g.batch_rows ? bb * g.batch_rows + bt0 : tile_y * 128;
-  const int bbase = bb * g.batch_rows;  // first B row (and column exponent) of this batch
+  const int bbase = bb * g.b_batch_rows;  // first B row (and column exponent) of this batch
   if (m0 >= M) return;  // whole CTA, before any barrier or tensor-memory use
   const int n0 = tile_x * g.bn;
   const uint32_t a_bytes = 128u * 128u;
@@ -302,6 +306,10 @@ __global__ void __launch_bounds__(128) k_umma_gemm(const __grid_constant__ CUten
     const int row = m0 + warp * 32 + lane;
     const bool live = row < M && (!g.batch_rows || bt0 + warp * 32 + lane < g.batch_rows);
     const long long dst = live ? (g.out_rows ? g.out_rows[row] : row) : 0;
+    // element offset of this row's column 0 and the stride between columns
+    const long long obase = g.o_cstride ? (long long)bb * g.o_bstride + (long long)(bt0 + warp * 32 + lane) * g.o_rstride
+                                        : dst * g.ldo;
+    const long long ocs = g.o_cstride ? g.o_cstride : 1;
     const uint32_t t_row = tmem + (static_cast<uint32_t>(warp * 32) << 16);
     const int ea = (g.a_exp && live) ? g.a_exp[row] : 0;
     for (int c = 0; c < g.bn; c += 16) {
@@ -319,11 +327,11 @@ __global__ void __launch_bounds__(128) k_umma_gemm(const __grid_constant__ CUten
           for (int j = 0; j < 16; ++j) acc[j] = fma(acc[j], wq, static_cast<double>(u[j]));
         }
         if (live) {
-          double *o = g.out64 + dst * g.ldo + n0 + c;
+          double *o = g.out64 + obase;
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
             const int col = n0 + c + j;
-            if (col < g.n) o[j] = ldexp(acc[j], ea + g.b_exp[bbase + col] - 2 * (g.slice_bits - 1));
+            if (col < g.n) o[col * ocs] = ldexp(acc[j], ea + g.b_exp[bbase + col] - 2 * (g.slice_bits - 1));
           }
         }
         continue;
@@ -362,17 +370,17 @@ __global__ void __launch_bounds__(128) k_umma_gemm(const __grid_constant__ CUten
           lo[j] = ldexpf(l2, sh);
         }
         if (live && g.out_lo) {
-          float *ol = g.out_lo + dst * g.ldo + n0 + c;
+          float *ol = g.out_lo + obase;
 #pragma unroll
           for (int j = 0; j < 16; ++j)
-            if (n0 + c + j < g.n) ol[j] = lo[j];
+            if (n0 + c + j < g.n) ol[(n0 + c + j) * ocs] = lo[j];
         }
       }
       if (live) {
-        float *o = g.out + dst * g.ldo + n0 + c;
+        float *o = g.out + obase;
 #pragma unroll
         for (int j = 0; j < 16; ++j)
-          if (n0 + c + j < g.n) o[j] = v[j];
+          if (n0 + c + j < g.n) o[(n0 + c + j) * ocs] = v[j];
       }
     }
   } else if (lane == 0) {
@@ -448,7 +456,8 @@ cudaError_t launch_umma_gemm(const uint16_t *A, int m_max, const int *m_dev, int
                              int b_terms, int kp, int npairs, const int *pair_a, const int *pair_b, float *out,
                              long long ldo, const int *out_rows, int *err, cudaStream_t st, const int *a_exp,
                              const int *b_exp, float *out_lo, int bn_max, double *out64, int slice_bits,
-                             int batch_rows, int batches, int stages_max) {
+                             int batch_rows, int batches, int stages_max, int b_batch_rows, long long o_bstride,
+                             long long o_rstride, long long o_cstride) {
   if (m_max <= 0 || n <= 0) return cudaSuccess;
   if (kp <= 0 || kp % 64 != 0 || npairs < 1 || npairs > kMaxPairs || a_terms < 1 || b_terms < 1)
     return cudaErrorInvalidValue;
@@ -467,8 +476,10 @@ cudaError_t launch_umma_gemm(const uint16_t *A, int m_max, const int *m_dev, int
   if (g.ngroups > 8) return cudaErrorInvalidValue;
   g.slice_bits = slice_bits;
   g.out64 = out64;
-  if (batch_rows < 0 || (batch_rows > 0 && (batches <= 0 || n > batch_rows))) return cudaErrorInvalidValue;
+  if (b_batch_rows <= 0) b_batch_rows = batch_rows;
+  if (batch_rows < 0 || (batch_rows > 0 && (batches <= 0 || n > b_batch_rows))) return cudaErrorInvalidValue;
   g.batch_rows = batch_rows;
+  g.b_batch_rows = b_batch_rows;
   g.tiles_per_batch = batch_rows > 0 ? (batch_rows + 127) / 128 : 0;
   g.a_exp = a_exp;
   g.b_exp = b_exp;
@@ -517,9 +528,13 @@ cudaError_t launch_umma_gemm(const uint16_t *A, int m_max, const int *m_dev, int
   g.out_lo = a_exp ? out_lo : nullptr;
   g.ldo = ldo;
   g.out_rows = out_rows;
+  if (o_cstride != 0 && (batch_rows <= 0 || out_rows)) return cudaErrorInvalidValue;
+  g.o_bstride = o_bstride;
+  g.o_rstride = o_rstride;
+  g.o_cstride = o_cstride;
   g.err = err;
   CUtensorMap ta, tb;
-  const uint64_t b_rows = batch_rows > 0 ? static_cast<uint64_t>(batch_rows) * batches : static_cast<uint64_t>(n);
+  const uint64_t b_rows = batch_rows > 0 ? static_cast<uint64_t>(b_batch_rows) * batches : static_cast<uint64_t>(n);
   if (!make_map(&ta, A, static_cast<uint64_t>(a_terms) * kp, static_cast<uint64_t>(m_max), 128) ||
       !make_map(&tb, B, static_cast<uint64_t>(b_terms) * kp, b_rows, static_cast<uint32_t>(g.bn)))
     return cudaErrorInvalidValue;
@@ -598,7 +613,7 @@ __global__ void __launch_bounds__(256) k_pack_fixed64(const double *__restrict__
                                                       const int *__restrict__ count, int nrows, int nsub, int stride,
                                                       int L, int kp, int nsl, int bits,
                                                       __nv_bfloat16 *__restrict__ A, int *__restrict__ rows_out,
-                                                      int *__restrict__ exps) {
+                                                      int *__restrict__ exps, long dst_stride, long dst_off) {
   const int rows = count ? *count : nrows;
   const int lane = threadIdx.x & 31;
   const long nw = (long)gridDim.x * (blockDim.x >> 5);
@@ -612,7 +627,8 @@ __global__ void __launch_bounds__(256) k_pack_fixed64(const double *__restrict__
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     const int e = (mx > 0.0) ? ilogb(mx) + 1 : 0;
     if (lane == 0) {
-      rows_out[m] = (int)phys;
+      // the row of the result: the source row, or (m / nsub) * dst_stride + dst_off + m % nsub
+      rows_out[m] = dst_stride > 0 ? (int)((m / nsub) * dst_stride + dst_off + m % nsub) : (int)phys;
       exps[m] = e;
     }
     __nv_bfloat16 *dst = A + m * nsl * (long)kp;
@@ -629,12 +645,153 @@ __global__ void __launch_bounds__(256) k_pack_fixed64(const double *__restrict__
 
 cudaError_t launch_pack_fixed64(const double *P, const int *list, const int *count, int nrows, int nsub, int stride,
                                 int L, int kp, int nsl, int bits, uint16_t *A, int *rows_out, int *exps,
-                                int max_rows, cudaStream_t st) {
+                                int max_rows, cudaStream_t st, long dst_stride, long dst_off) {
   if (max_rows <= 0) return cudaSuccess;
   long blocks = (max_rows + 7) / 8;
   if (blocks > 152 * 16) blocks = 152 * 16;
   k_pack_fixed64<<<(int)blocks, 256, 0, st>>>(P, list, count, nrows, nsub > 0 ? nsub : 1, stride, L, kp, nsl, bits,
-                                               reinterpret_cast<__nv_bfloat16 *>(A), rows_out, exps);
+                                               reinterpret_cast<__nv_bfloat16 *>(A), rows_out, exps, dst_stride,
+                                               dst_off);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Columns of per-walker matrices as fixed-point operand rows (the operands of
+// the kinetic M products, whose contraction runs over the rows of G~^{-1},
+// Bt and A_up): for walker w < W and column c < C of X_w = X + w xw
+// ([R][C] row-major), operand row m = w C + c holds X_w[0..R)[c] (zero from R
+// to kp) relative to 2^e, e = 1 + the binary exponent of the column's largest
+// magnitude, cut into kFixedSlices exact 8-bit slices as k_pack_fixed cuts a
+// row (an FP64 X, or a two-float X + Xlo with the remainder carried exactly).
+// exps[m] = e; rows_out[m] = w dst_stride + dst_off + c when rows_out is given.
+// One CTA per (walker, 32 columns): the column maxima first, then tiles of 64
+// rows through shared memory, so that the reads (32 consecutive columns of a
+// row) and the writes (64 consecutive entries of one slice of an operand row)
+// are both coalesced.
+// ---------------------------------------------------------------------------
+template <bool kF64>
+__global__ void __launch_bounds__(256) k_pack_cols(const double *__restrict__ X64, const float *__restrict__ X32,
+                                                   const float *__restrict__ Xlo, size_t xw, int R, int C, int kp,
+                                                   __nv_bfloat16 *__restrict__ A, int *__restrict__ exps,
+                                                   int *__restrict__ rows_out, long dst_stride, long dst_off) {
+  __shared__ double t64[kF64 ? 64 : 1][33];
+  __shared__ float th[kF64 ? 1 : 64][33], tl[kF64 ? 1 : 64][33];
+  __shared__ float cmax[8][32];
+  __shared__ int cexp[32];
+  const int tid = threadIdx.x, cl = tid & 31, jr = tid >> 5;
+  const int w = blockIdx.y, c0 = blockIdx.x * 32;
+  const int c = c0 + cl;
+  const size_t base = (size_t)w * xw;
+  float mx = 0.0f;
+  double mx64 = 0.0;
+  if (c < C)
+    for (int j = jr; j < R; j += 8) {
+      if constexpr (kF64)
+        mx64 = fmax(mx64, fabs(X64[base + (size_t)j * C + c]));
+      else
+        mx = fmaxf(mx, fabsf(X32[base + (size_t)j * C + c]));
+    }
+  if constexpr (kF64) {
+    // exponents from the FP64 maxima: compare through the exponent only
+    cmax[jr][cl] = 0.0f;
+    __shared__ double cmax64[8][32];
+    cmax64[jr][cl] = mx64;
+    __syncthreads();
+    if (jr == 0) {
+      double m = cmax64[0][cl];
+      for (int q = 1; q < 8; ++q) m = fmax(m, cmax64[q][cl]);
+      const int e = m > 0.0 ? ilogb(m) + 1 : 0;
+      cexp[cl] = e;
+      if (c < C) {
+        exps[(size_t)w * C + c] = e;
+        if (rows_out) rows_out[(size_t)w * C + c] = (int)(w * dst_stride + dst_off + c);
+      }
+    }
+  } else {
+    cmax[jr][cl] = mx;
+    __syncthreads();
+    if (jr == 0) {
+      float m = cmax[0][cl];
+      for (int q = 1; q < 8; ++q) m = fmaxf(m, cmax[q][cl]);
+      const int e = m > 0.0f ? ilogbf(m) + 1 : 0;
+      cexp[cl] = e;
+      if (c < C) {
+        exps[(size_t)w * C + c] = e;
+        if (rows_out) rows_out[(size_t)w * C + c] = (int)(w * dst_stride + dst_off + c);
+      }
+    }
+  }
+  __syncthreads();
+  for (int j0 = 0; j0 < kp; j0 += 64) {
+    // tile [64 rows][32 columns], zero past R or C
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int jj = jr + 8 * q, j = j0 + jj;
+      const bool in = j < R && c < C;
+      if constexpr (kF64) {
+        t64[jj][cl] = in ? X64[base + (size_t)j * C + c] : 0.0;
+      } else {
+        th[jj][cl] = in ? X32[base + (size_t)j * C + c] : 0.0f;
+        tl[jj][cl] = (in && Xlo) ? Xlo[base + (size_t)j * C + c] : 0.0f;
+      }
+    }
+    __syncthreads();
+    // warp jr writes columns jr, jr + 8, jr + 16, jr + 24; lane: rows 2 lane, 2 lane + 1
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) {
+      const int col = jr + 8 * cc, cg = c0 + col;
+      if (cg >= C) continue;
+      const int e = cexp[col];
+      __nv_bfloat16 sl[2][kFixedSlices];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int jj = 2 * (tid & 31) + h;
+        if constexpr (kF64) {
+          double x = ldexp(t64[jj][col], 7 - e);  // |x| < 128
+#pragma unroll
+          for (int t = 0; t < kFixedSlices; ++t) {
+            const double q = rint(x);
+            sl[h][t] = __float2bfloat16_rn(static_cast<float>(q));
+            x = (x - q) * 256.0;
+          }
+        } else {
+          float x = ldexpf(th[jj][col], 7 - e), xl = ldexpf(tl[jj][col], 7 - e);
+#pragma unroll
+          for (int t = 0; t < kFixedSlices; ++t) {
+            const float q = rintf(x);
+            sl[h][t] = __float2bfloat16_rn(q);
+            const fdw r = two_sum(__fsub_rn(x, q), xl);
+            x = __fmul_rn(r.hi, 256.0f);
+            xl = __fmul_rn(r.lo, 256.0f);
+          }
+        }
+      }
+      __nv_bfloat16 *dst = A + ((size_t)w * C + cg) * kFixedSlices * (size_t)kp + j0 + 2 * (tid & 31);
+#pragma unroll
+      for (int t = 0; t < kFixedSlices; ++t) {
+        __nv_bfloat162 v;
+        v.x = sl[0][t];
+        v.y = sl[1][t];
+        *reinterpret_cast<__nv_bfloat162 *>(dst + (size_t)t * kp) = v;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_pack_cols(const double *X64, const float *X32, const float *Xlo, size_t xw, int R, int C, int kp,
+                             int W, uint16_t *A, int *exps, int *rows_out, long dst_stride, long dst_off,
+                             cudaStream_t st) {
+  if (W <= 0 || C <= 0) return cudaSuccess;
+  if (kp % 64 != 0 || kp < R || (X64 == nullptr) == (X32 == nullptr)) return cudaErrorInvalidValue;
+  dim3 grid((C + 31) / 32, W);
+  if (X64)
+    k_pack_cols<true><<<grid, 256, 0, st>>>(X64, nullptr, nullptr, xw, R, C, kp,
+                                            reinterpret_cast<__nv_bfloat16 *>(A), exps, rows_out, dst_stride, dst_off);
+  else
+    k_pack_cols<false><<<grid, 256, 0, st>>>(nullptr, X32, Xlo, xw, R, C, kp,
+                                             reinterpret_cast<__nv_bfloat16 *>(A), exps, rows_out, dst_stride,
+                                             dst_off);
   return cudaGetLastError();
 }
 

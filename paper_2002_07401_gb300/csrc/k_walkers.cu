@@ -373,6 +373,254 @@ __global__ void __launch_bounds__(512) k_metropolis(DevSystem s, double *__restr
 // the warp's slice of shared memory, reductions by shuffles, no block barriers.
 // Every lane takes the accept decision from lane 0's sums so that it is uniform.
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// Metropolis sampling of the guiding function Psi_G = (max(R, eps) / R) Psi_T
+// (Sec. "Atomic forces", Eqs. guiding_function, R_r, regularization) for the
+// FP64 path with N_up <= 64: R = (S F)^-theta, F = sum |G~^{-1}|^2,
+// S = min_i sum_j |G~_ij|^2, and a move is accepted with probability
+// |Psi_T(x')/Psi_T(x)|^2 W(x) / W(x'), W = (R / max(R, eps))^2.  One CTA per
+// walker with G~^{-1} and G~ in shared memory.  For the proposed replacement
+// of row (up) or column (down) m by g' with ratio R_d, the Sherman-Morrison
+// form A' = A - c (v - e_m)^T / R_d (up; the transpose for down) gives
+//   |A'|^2 = |A|^2 - 2 (w . (v - e_m)) / R_d + |c|^2 |v - e_m|^2 / R_d^2,
+// with w = c^T A (up) or A c (down), so F' costs O(N_up^2) per proposal; the
+// row sums of squares of G~ follow the replaced row or column.  F and the row
+// sums are recomputed at every launch; G~ is kept current in gmat.
+// ---------------------------------------------------------------------------
+template <bool UP>
+__global__ void __launch_bounds__(128) k_metropolis_guided(DevSystem s, double *__restrict__ r,
+                                                           const double *__restrict__ rprop,
+                                                           const double *__restrict__ gprop,
+                                                           double *__restrict__ ginv, double *__restrict__ scal,
+                                                           int *__restrict__ status, const double *__restrict__ pprop,
+                                                           double *__restrict__ phi_up, int *__restrict__ list,
+                                                           int *__restrict__ count, double *__restrict__ gmat,
+                                                           double theta, double eps, int m_begin, int m_end,
+                                                           int *__restrict__ total) {
+  extern __shared__ double sm[];
+  const int n = s.n_up, N = s.N, tid = threadIdx.x, bs = blockDim.x;
+  const int w = blockIdx.x;
+  double *gw = ginv + (size_t)w * n * n, *gg = gmat + (size_t)w * n * n;
+  double *xs = sm;              // N * 3
+  double *Gi = xs + N * 3;      // n * n  G~^{-1}
+  double *Gm = Gi + n * n;      // n * n  G~
+  double *gp = Gm + n * n;      // n      proposed row / column of G~
+  double *vv = gp + n;          // n
+  double *cc = vv + n;          // n
+  double *ww = cc + n;          // n
+  double *rn = ww + n;          // n      row sums of squares of G~
+  __shared__ double red[8][4];
+  __shared__ int s_acc;
+  __shared__ double s_R, s_F, s_W;
+  for (int t = tid; t < n * n; t += bs) {
+    Gi[t] = gw[t];
+    Gm[t] = gg[t];
+  }
+  for (int t = tid; t < N * 3; t += bs) xs[t] = r[(size_t)w * N * 3 + t];
+  __syncthreads();
+  // F and the row sums of the current configuration
+  double f = 0.0;
+  for (int t = tid; t < n * n; t += bs) f = fma(Gi[t], Gi[t], f);
+  for (int i = tid; i < n; i += bs) {
+    double q = 0.0;
+    for (int j = 0; j < n; ++j) q = fma(Gm[i * n + j], Gm[i * n + j], q);
+    rn[i] = q;
+  }
+  f = warp_sum(f);
+  if ((tid & 31) == 0) red[tid >> 5][0] = f;
+  __syncthreads();
+  if (tid == 0) {
+    double F = 0.0, S = INFINITY;
+    for (int q = 0; q < (bs >> 5); ++q) F += red[q][0];
+    for (int i = 0; i < n; ++i) S = fmin(S, rn[i]);
+    const double R = pow(S * F, -theta), qw = R / fmax(R, eps);
+    s_F = F;
+    s_W = qw * qw;
+  }
+  double sgn = 1.0, J = 0.0, nacc = 0.0;
+  int st_bits = 0;
+  if (tid == 0) {
+    sgn = scal[(size_t)w * S_STRIDE + S_SIGN];
+    J = scal[(size_t)w * S_STRIDE + S_J];
+    nacc = scal[(size_t)w * S_STRIDE + S_NACC];
+    st_bits = status[w];
+  }
+  const int nmoves = m_end < (UP ? s.n_up : s.n_dn) ? m_end : (UP ? s.n_up : s.n_dn);
+  const int e0 = UP ? 0 : s.n_up;
+  __syncthreads();
+  for (int m = m_begin; m < nmoves; ++m) {
+    const int e = e0 + m;
+    const double *rp4 = rprop + ((size_t)w * n + m) * kPropStride;
+    const double px = rp4[0], py = rp4[1], pz = rp4[2];
+    for (int t = tid; t < n; t += bs) gp[t] = gprop[((size_t)w * n + m) * n + t];
+    __syncthreads();
+    double pr = 0.0, pj = 0.0;
+    for (int t = tid; t < n; t += bs) pr += UP ? gp[t] * Gi[t * n + m] : Gi[m * n + t] * gp[t];
+    const double ox = xs[3 * e], oy = xs[3 * e + 1], oz = xs[3 * e + 2];
+    if (tid == 0) pj = rp4[4];
+    if (s.use_j2) pj += j2_move_change<double, UP>(s, xs, e, px, py, pz, ox, oy, oz, tid, bs);
+    // v, c and w of the Sherman-Morrison form, for the proposal whether or not it is taken
+    for (int t = tid; t < n; t += bs) {
+      double a = 0.0;
+      if (UP) {
+        for (int j = 0; j < n; ++j) a = fma(gp[j], Gi[j * n + t], a);
+        cc[t] = Gi[t * n + m];
+      } else {
+        for (int i = 0; i < n; ++i) a = fma(Gi[t * n + i], gp[i], a);
+        cc[t] = Gi[m * n + t];
+      }
+      vv[t] = a;
+    }
+    __syncthreads();
+    for (int t = tid; t < n; t += bs) {
+      double a = 0.0;
+      if (UP)
+        for (int j = 0; j < n; ++j) a = fma(cc[j], Gi[j * n + t], a);
+      else
+        for (int k = 0; k < n; ++k) a = fma(Gi[t * n + k], cc[k], a);
+      ww[t] = a;
+    }
+    __syncthreads();
+    double d1 = 0.0, cn = 0.0, un = 0.0, smin = INFINITY;
+    for (int t = tid; t < n; t += bs) {
+      const double u = vv[t] - (t == m ? 1.0 : 0.0);
+      d1 = fma(ww[t], u, d1);
+      cn = fma(cc[t], cc[t], cn);
+      un = fma(u, u, un);
+      // row sums of G~ after the replacement
+      double rt;
+      if (!UP) {
+        rt = rn[t] - Gm[t * n + m] * Gm[t * n + m] + gp[t] * gp[t];
+      } else if (t != m) {
+        rt = rn[t];
+      } else {
+        rt = 0.0;
+        for (int j = 0; j < n; ++j) rt = fma(gp[j], gp[j], rt);
+      }
+      smin = fmin(smin, rt);
+    }
+    pr = warp_sum(pr);
+    pj = warp_sum(pj);
+    d1 = warp_sum(d1);
+    cn = warp_sum(cn);
+    un = warp_sum(un);
+    for (int o = 16; o > 0; o >>= 1) smin = fmin(smin, __shfl_xor_sync(0xffffffffu, smin, o));
+    const int warp = tid >> 5, lane = tid & 31, nw = bs >> 5;
+    __syncthreads();
+    if (lane == 0) {
+      red[warp][0] = pr;
+      red[warp][1] = pj;
+      red[warp][2] = d1;
+      red[warp][3] = smin;
+    }
+    __shared__ double red2[8][2];
+    if (lane == 0) {
+      red2[warp][0] = cn;
+      red2[warp][1] = un;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double P = 0.0, PJ = 0.0, D = 0.0, C = 0.0, U = 0.0, Sm = INFINITY;
+      for (int q = 0; q < nw; ++q) {
+        P += red[q][0];
+        PJ += red[q][1];
+        D += red[q][2];
+        Sm = fmin(Sm, red[q][3]);
+        C += red2[q][0];
+        U += red2[q][1];
+      }
+      const double Fp = s_F - 2.0 * D / P + C * U / (P * P);
+      const double Rp = pow(Sm * Fp, -theta), qw = Rp / fmax(Rp, eps), Wp = qw * qw;
+      const double u = rp4[3];
+      const double p = P * P * exp(2.0 * PJ) * (s_W / Wp);
+      int acc = 0;
+      if (!isfinite(p) || !isfinite(P)) {
+        st_bits |= JAGP_WS_NONFINITE;
+      } else if (P != 0.0 && u < p) {
+        acc = 1;
+        if (P < 0.0) sgn = -sgn;
+        J += PJ;
+        nacc += 1.0;
+        list[atomicAdd(count, 1)] = w * n + m;
+        if (total) atomicAdd(total, 1);
+        s_F = Fp;
+        s_W = Wp;
+      }
+      s_acc = acc;
+      s_R = P;
+    }
+    __syncthreads();
+    if (s_acc) {
+      const double invR = 1.0 / s_R;
+      for (int idx = tid; idx < n * n; idx += bs) {
+        const int j = idx / n, k = idx - j * n;
+        if (UP)
+          Gi[idx] -= cc[j] * (vv[k] - (k == m ? 1.0 : 0.0)) * invR;
+        else
+          Gi[idx] -= (vv[j] - (j == m ? 1.0 : 0.0)) * cc[k] * invR;
+      }
+      // G~ and its row sums follow the replaced row / column
+      for (int t = tid; t < n; t += bs) {
+        if (UP) {
+          Gm[m * n + t] = gp[t];
+        } else {
+          rn[t] = rn[t] - Gm[t * n + m] * Gm[t * n + m] + gp[t] * gp[t];
+          Gm[t * n + m] = gp[t];
+        }
+      }
+      if (tid == 0) {
+        xs[3 * e] = px;
+        xs[3 * e + 1] = py;
+        xs[3 * e + 2] = pz;
+      }
+      if (UP) {
+        const size_t row = ((size_t)w * n + m) * s.L;
+        for (int t = tid; t < s.L; t += bs) phi_up[row + t] = pprop[row + t];
+      }
+      __syncthreads();
+      if (UP && tid == 0) {
+        double q = 0.0;
+        for (int j = 0; j < n; ++j) q = fma(gp[j], gp[j], q);
+        rn[m] = q;
+      }
+    }
+    __syncthreads();
+  }
+  for (int t = tid; t < n * n; t += bs) {
+    gw[t] = Gi[t];
+    gg[t] = Gm[t];
+  }
+  for (int t = tid; t < N * 3; t += bs) r[(size_t)w * N * 3 + t] = xs[t];
+  if (tid == 0) {
+    scal[(size_t)w * S_STRIDE + S_SIGN] = sgn;
+    scal[(size_t)w * S_STRIDE + S_J] = J;
+    scal[(size_t)w * S_STRIDE + S_NACC] = nacc;
+    status[w] = st_bits;
+  }
+}
+
+cudaError_t launch_metropolis_guided(const DevSystem &s, bool up, double *r, const double *rprop,
+                                     const double *gprop, double *ginv, double *scal, int *status,
+                                     const double *pprop, double *phi_up, int *list, int *count, double *gmat,
+                                     double theta, double eps, int W, cudaStream_t st, int m_begin, int m_end,
+                                     int *total) {
+  if (W <= 0 || (!up && s.n_dn == 0)) return cudaSuccess;
+  if (s.n_up > kGuidedMaxUp) return cudaErrorInvalidValue;
+  if (m_end < 0) m_end = up ? s.n_up : s.n_dn;
+  if (m_begin >= m_end) return cudaSuccess;
+  const int n = s.n_up;
+  // positions (3N), G~^{-1} and G~ (n^2 each), five n-vectors
+  const size_t smem = ((size_t)s.N * 3 + 2 * (size_t)n * n + 5 * (size_t)n + 1) * sizeof(double);
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  if (up)
+    k_metropolis_guided<true><<<W, 128, smem, st>>>(s, r, rprop, gprop, ginv, scal, status, pprop, phi_up, list,
+                                                    count, gmat, theta, eps, m_begin, m_end, total);
+  else
+    k_metropolis_guided<false><<<W, 128, smem, st>>>(s, r, rprop, gprop, ginv, scal, status, pprop, phi_up, list,
+                                                     count, gmat, theta, eps, m_begin, m_end, total);
+  return cudaGetLastError();
+}
+
 constexpr int kMetroWarps = 4;
 constexpr size_t kMetroSmemMax = 200 * 1024;  // G~^{-1} kept in shared memory up to this footprint
 
@@ -722,6 +970,11 @@ static cudaError_t walker_attrs() {
 
 cudaError_t setup_walker_attributes() {
   cudaError_t e = walker_attrs<double>();
-  return e != cudaSuccess ? e : walker_attrs<float>();
+  if (e == cudaSuccess) e = walker_attrs<float>();
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_metropolis_guided<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_metropolis_guided<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  return e;
 }
 }  // namespace jagp

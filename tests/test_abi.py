@@ -58,6 +58,10 @@ def test_status_strings_and_bad_args_without_gpu():
     # reblocking checks its sizes on the host
     assert L.jagp_reblock_levels(257) == 8 and L.jagp_reblock_levels(1) == 0
     assert L.jagp_reblock(None, 10, 1, None, None, None, None) == 1
+    # the SR step checks its arguments on the host
+    assert L.jagp_sr_workspace_bytes(0, 5) == 0 and L.jagp_sr_workspace_bytes(10, 5) > 0
+    assert L.jagp_sr_step(None, 5, None, 10, 5, 1e-3, 1.0, 10, 1e-10, None, None, None, None, None, None) == 1
+    assert L.jagp_logpsi_derivs(None, None, None, 1, None, None, 1, None) == 1
 
 
 def test_oracle_and_product_share_no_code():

@@ -1,6 +1,7 @@
 """Mixed-precision path (double-word FP32 orbital tables, BF16 tensor-core
 lambda products on five-slice fixed-point operands, FP64 refresh / log-det /
-energies, FP32 kinetic contraction) against the FP64 oracle.
+energies, kinetic contraction from exact fixed-point M vectors in double-word
+arithmetic) against the FP64 oracle.
 
 Stated tolerances per configuration: |log|Psi| error| <= 1e-6 and
 |e_L error| <= 1e-5 Ha.  Sampling: the mixed path's accept decisions are taken
@@ -20,10 +21,8 @@ pytestmark = pytest.mark.gpu
 LOGPSI_TOL = 1e-6
 EL_TOL = 1e-5
 # The N_up = 40 random system is an ill-conditioned stress case outside the
-# workload configurations; its measured e_L error (about 3e-5 Ha, from the FP32
-# kinetic contraction amplified by cond(G~)) is stated rather than held to the
-# workload target.
-STRESS_TOL = {"mid-n40": (1e-6, 1e-4)}
+# workload configurations; it is held to the same targets.
+STRESS_TOL = {}
 
 
 @pytest.fixture(scope="module")
