@@ -33,6 +33,9 @@ class _OrcSystem(C.Structure):
         ("unpaired", C.c_void_p), ("b_ea", C.c_double), ("b_para", C.c_double),
         ("b_anti", C.c_double), ("use_j1", C.c_int), ("use_j2", C.c_int),
         ("j2_spin_independent", C.c_int),
+        ("n_jshells", C.c_int), ("jshell_atom", C.c_void_p), ("jshell_l", C.c_void_p),
+        ("jshell_radial", C.c_void_p), ("jshell_zeta", C.c_void_p), ("LJ", C.c_int),
+        ("j3_para", C.c_void_p), ("j3_anti", C.c_void_p), ("use_j3", C.c_int),
     ]
 
 
@@ -199,6 +202,15 @@ class Oracle:
         s.b_ea, s.b_para, s.b_anti = sys.b_ea, sys.b_para, sys.b_anti
         s.use_j1, s.use_j2 = int(sys.use_j1), int(sys.use_j2)
         s.j2_spin_independent = int(sys.j2_spin_independent)
+        j3 = getattr(sys, "j3", None)
+        if j3 is not None:
+            self._keep += [j3[k] for k in ("shell_atom", "shell_l", "shell_radial", "shell_zeta", "para", "anti")]
+            s.n_jshells = int(len(j3["shell_l"]))
+            s.jshell_atom, s.jshell_l = _p(j3["shell_atom"]), _p(j3["shell_l"])
+            s.jshell_radial, s.jshell_zeta = _p(j3["shell_radial"]), _p(j3["shell_zeta"])
+            s.LJ = int(j3["para"].shape[0])
+            s.j3_para, s.j3_anti = _p(j3["para"]), _p(j3["anti"])
+            s.use_j3 = 1
         self._s = s
         self._ps = C.addressof(s)
         self.N, self.L, self.nu = sys.N, sys.L, sys.n_up

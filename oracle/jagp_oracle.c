@@ -56,6 +56,15 @@ typedef struct {
   const double *unpaired;   /* [n_up-n_dn][L] unpaired orbital coefficients */
   double b_ea, b_para, b_anti;
   int use_j1, use_j2, j2_spin_independent;
+  /* three/four-body Jastrow (Eq. threebody_jastrow): its own atomic basis chi
+   * (shells as above, LJ functions) and the coupling matrices for parallel and
+   * antiparallel pairs, [LJ][LJ] each, symmetric */
+  int n_jshells;
+  const int *jshell_atom, *jshell_l, *jshell_radial;
+  const double *jshell_zeta;
+  int LJ;
+  const double *j3_para, *j3_anti;
+  int use_j3;
 } orc_system;
 
 /* ------------------------------------------------------------------------ */
@@ -362,6 +371,37 @@ static void j2_term(const orc_system *s, int same_spin, double r, double *v, dou
 
 static int is_up(const orc_system *s, int i) { return i < s->n_up; }
 
+/* the Jastrow basis chi at r (values, gradients [LJ][3], Laplacians; the last
+ * two may be NULL), evaluated by orc_ao on the Jastrow shells */
+static void jastrow_basis(const orc_system *s, const double r[3], double *val, double *grad, double *lap) {
+  orc_system t = *s;
+  t.n_shells = s->n_jshells;
+  t.shell_atom = s->jshell_atom;
+  t.shell_l = s->jshell_l;
+  t.shell_radial = s->jshell_radial;
+  t.shell_zeta = s->jshell_zeta;
+  t.L = s->LJ;
+  orc_ao(&t, r, val, grad, lap);
+}
+
+/* J3 = sum_{i<j} sum_{mu,nu} M^{s_i s_j}_{mu,nu} chi_mu(r_i) chi_nu(r_j), M = j3_para for
+ * equal spins and j3_anti otherwise (Eq. threebody_jastrow), as the pair sum itself */
+static double jastrow3(const orc_system *s, const double *x) {
+  int N = s->n_up + s->n_dn, LJ = s->LJ;
+  double *chi = (double *)malloc(sizeof(double) * (size_t)N * LJ);
+  for (int i = 0; i < N; ++i) jastrow_basis(s, x + 3 * i, chi + (size_t)i * LJ, NULL, NULL);
+  double J = 0.0;
+  for (int i = 0; i < N; ++i)
+    for (int j = i + 1; j < N; ++j) {
+      const double *M = is_up(s, i) == is_up(s, j) ? s->j3_para : s->j3_anti;
+      for (int mu = 0; mu < LJ; ++mu)
+        for (int nu = 0; nu < LJ; ++nu)
+          J += M[mu * LJ + nu] * chi[(size_t)i * LJ + mu] * chi[(size_t)j * LJ + nu];
+    }
+  free(chi);
+  return J;
+}
+
 double orc_jastrow(const orc_system *s, const double *x) {
   int N = s->n_up + s->n_dn;
   double J = 0.0, f, fp, fpp, vdb;
@@ -379,6 +419,7 @@ double orc_jastrow(const orc_system *s, const double *x) {
         j2_term(s, is_up(s, i) == is_up(s, j), sqrt(d0 * d0 + d1 * d1 + d2 * d2), &f, &fp, &fpp, &vdb);
         J += f;
       }
+  if (s->use_j3) J += jastrow3(s, x);
   return J;
 }
 
@@ -409,6 +450,29 @@ void orc_jastrow_derivs(const orc_system *s, const double *x, double *gJ, double
         for (int q = 0; q < 3; ++q) gJ[3 * i + q] += fp * d[q] / r;
         lJ[i] += fpp + 2.0 * fp / r;
       }
+  if (s->use_j3) {
+    /* d/dr_i of sum_{j != i} chi(r_i)^T M^{s_i s_j} chi(r_j) (M symmetric) */
+    int LJ = s->LJ;
+    double *chi = (double *)malloc(sizeof(double) * (size_t)N * LJ);
+    double *gch = (double *)malloc(sizeof(double) * (size_t)N * LJ * 3);
+    double *lch = (double *)malloc(sizeof(double) * (size_t)N * LJ);
+    for (int i = 0; i < N; ++i)
+      jastrow_basis(s, x + 3 * i, chi + (size_t)i * LJ, gch + (size_t)i * LJ * 3, lch + (size_t)i * LJ);
+    for (int i = 0; i < N; ++i)
+      for (int j = 0; j < N; ++j) {
+        if (j == i) continue;
+        const double *M = is_up(s, i) == is_up(s, j) ? s->j3_para : s->j3_anti;
+        for (int mu = 0; mu < LJ; ++mu)
+          for (int nu = 0; nu < LJ; ++nu) {
+            double m = M[mu * LJ + nu] * chi[(size_t)j * LJ + nu];
+            for (int q = 0; q < 3; ++q) gJ[3 * i + q] += m * gch[((size_t)i * LJ + mu) * 3 + q];
+            lJ[i] += m * lch[(size_t)i * LJ + mu];
+          }
+      }
+    free(chi);
+    free(gch);
+    free(lch);
+  }
 }
 
 /* ------------------------------------------------------------------------ */
@@ -881,6 +945,29 @@ int orc_grad_logpsi(const orc_system *s, const double *x, double *dlam, double *
           j1_term(s->Z[at], s->b_ea, r, &f, &fp, &fpp);
           for (int q = 0; q < 3; ++q) dR[3 * at + q] -= fp * d[q] / r;
         }
+    if (s->use_j3) {
+      /* chi_mu on atom a depends on r - R_a: d/dR_a = -d/dr on its functions */
+      int LJ = s->LJ;
+      int *jowner = (int *)malloc(sizeof(int) * LJ);
+      for (int k = 0, mu = 0; k < s->n_jshells; ++k)
+        for (int c = 0; c < ncomp(s->jshell_l[k]); ++c) jowner[mu++] = s->jshell_atom[k];
+      double *chi = (double *)malloc(sizeof(double) * (size_t)N * LJ);
+      double *gch = (double *)malloc(sizeof(double) * (size_t)N * LJ * 3);
+      for (int i = 0; i < N; ++i) jastrow_basis(s, x + 3 * i, chi + (size_t)i * LJ, gch + (size_t)i * LJ * 3, NULL);
+      for (int i = 0; i < N; ++i)
+        for (int j = 0; j < N; ++j) {
+          if (j == i) continue;
+          const double *M = is_up(s, i) == is_up(s, j) ? s->j3_para : s->j3_anti;
+          for (int mu = 0; mu < LJ; ++mu)
+            for (int nu = 0; nu < LJ; ++nu) {
+              double m = M[mu * LJ + nu] * chi[(size_t)j * LJ + nu];
+              for (int q = 0; q < 3; ++q) dR[3 * jowner[mu] + q] -= m * gch[((size_t)i * LJ + mu) * 3 + q];
+            }
+        }
+      free(jowner);
+      free(chi);
+      free(gch);
+    }
   }
   if (dr) {
     double *gD = (double *)malloc(sizeof(double) * 3 * N), *lD = (double *)malloc(sizeof(double) * N);

@@ -18,6 +18,7 @@ from .systems import (  # noqa: F401
     one_electron_gauss,
     helium_slater,
     small_random,
+    with_j3,
     init_walkers,
     jitter_walkers,
     CONFIGS,

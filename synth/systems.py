@@ -64,6 +64,10 @@ class System:
     delta: float = 0.5       # proposal half-width (bohr)
     seed: int = 0
     meta: dict = field(default_factory=dict)
+    # three/four-body Jastrow (Eq. threebody_jastrow), or None: its own shells
+    # (keys shell_atom, shell_l, shell_radial, shell_zeta) and the symmetric
+    # coupling matrices "para" and "anti" ([LJ][LJ])
+    j3: Optional[dict] = None
 
     @property
     def n_atoms(self) -> int:
@@ -98,6 +102,15 @@ class System:
             setattr(self, a, np.ascontiguousarray(getattr(self, a), dtype=np.int32))
         if self.unpaired is not None:
             self.unpaired = np.ascontiguousarray(self.unpaired, dtype=np.float64)
+        if self.j3 is not None:
+            j = self.j3
+            for a in ("shell_atom", "shell_l", "shell_radial"):
+                j[a] = np.ascontiguousarray(j[a], dtype=np.int32)
+            for a in ("shell_zeta", "para", "anti"):
+                j[a] = np.ascontiguousarray(j[a], dtype=np.float64)
+            LJ = _n_funcs(j["shell_l"])
+            assert j["para"].shape == (LJ, LJ) and j["anti"].shape == (LJ, LJ)
+            assert np.array_equal(j["para"], j["para"].T) and np.array_equal(j["anti"], j["anti"].T)
         return self
 
 
@@ -288,6 +301,29 @@ def small_random(n_atoms: int = 3, n_up: int = 3, n_dn: int = 2, per_atom: int =
                   lam, n_up, n_dn, unpaired=unp, b_ea=0.8, b_para=1.3, b_anti=0.7,
                   use_j1=use_j1, use_j2=use_j2, j2_spin_independent=spin_independent,
                   delta=0.5, seed=seed).check()
+
+
+def with_j3(sys: System, seed: int = 0, per_atom=(1, 1), sd: float = 0.05) -> System:
+    """Attach a three/four-body Jastrow to sys: per atom per_atom = (s, p)
+    Gaussian shells with exponents log-uniform in [0.3, 3], and random symmetric
+    coupling matrices with N(0, sd^2) entries for parallel and antiparallel pairs."""
+    g = _rng(seed, STREAM_GEN, 7000 + sys.n_atoms)
+    atom, ls, zeta = [], [], []
+    for a in range(sys.n_atoms):
+        for l, cnt in ((0, per_atom[0]), (1, per_atom[1])):
+            for z in sorted(np.exp(g.uniform(np.log(0.3), np.log(3.0), size=cnt)), reverse=True):
+                atom.append(a)
+                ls.append(l)
+                zeta.append(z)
+    LJ = _n_funcs(ls)
+
+    def sym():
+        m = g.normal(0.0, sd, size=(LJ, LJ))
+        return np.triu(m) + np.triu(m, 1).T
+    sys.j3 = {"shell_atom": np.array(atom, np.int32), "shell_l": np.array(ls, np.int32),
+              "shell_radial": np.zeros(len(ls), np.int32), "shell_zeta": np.array(zeta),
+              "para": sym(), "anti": sym()}
+    return sys.check()
 
 
 # ----------------------------------------------------------------------------

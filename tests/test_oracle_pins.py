@@ -854,3 +854,72 @@ def test_guided_sampling_reweights_to_the_trial_distribution():
     e1, _, _ = o.vmc(xz, 5, seed=7)
     e2, _, _, _ = o.vmc_guided(xz2, 5, eps=0.0, seed=7)
     assert np.array_equal(xz, xz2) and np.array_equal(e1, e2)
+
+
+# ----------------------------------------------------------------------------
+# three/four-body Jastrow (Eq. threebody_jastrow)
+# ----------------------------------------------------------------------------
+
+def test_jastrow3_single_function_closed_form():
+    """One s Gaussian chi on one atom and scalar couplings m_p, m_a: the pair sum
+    is m_p/2 (U_u^2 - sum_u chi^2 + U_d^2 - sum_d chi^2) + m_a U_u U_d with U_s the
+    spin sums of chi."""
+    s = synth.small_random(n_atoms=1, n_up=2, n_dn=2, per_atom=6, seed=120, use_j1=False, use_j2=False)
+    zeta, mp, ma = 0.7, 0.3, -0.45
+    s.j3 = {"shell_atom": [0], "shell_l": [0], "shell_radial": [0], "shell_zeta": [zeta],
+            "para": np.array([[mp]]), "anti": np.array([[ma]])}
+    s.check()
+    o = oracle.Oracle(s)
+    x = _rand_cfg(s, 121)
+    chi = np.exp(-zeta * np.sum((x - s.R[0]) ** 2, axis=1))
+    u, d = chi[:2], chi[2:]
+    ref = mp / 2 * (u.sum() ** 2 - (u ** 2).sum() + d.sum() ** 2 - (d ** 2).sum()) + ma * u.sum() * d.sum()
+    assert abs(o.jastrow(x) - ref) < 1e-14 * (1 + abs(ref))
+
+
+def test_jastrow3_kinetic_gradient_translation_antisymmetry():
+    """With J3 on (s and p Jastrow functions on every atom): grad log|Psi| and the
+    kinetic energy against central differences, the translation sum of the
+    nuclear and electronic derivatives, and same-spin exchange symmetry."""
+    s = synth.with_j3(synth.small_random(n_atoms=3, n_up=3, n_dn=2, per_atom=6, seed=122, slater_fraction=0.3),
+                      seed=122, sd=0.2)
+    o = oracle.Oracle(s)
+    x = _rand_cfg(s, 123)
+    g = o.grad_logpsi(x, want_lam=False)
+    e, kin, vee, vei, vii, gD, lD = o.local_energy(x, parts=True)
+    la0, sg0 = _logpsi_signed(o, x)
+    h1, h2 = 1e-4, 1e-3
+    lap_sum = 0.0
+    for i in range(s.N):
+        for q in range(3):
+            xp, xm = x.copy(), x.copy()
+            xp[i, q] += h1
+            xm[i, q] -= h1
+            fd = (_logpsi_signed(o, xp)[0] - _logpsi_signed(o, xm)[0]) / (2 * h1)
+            assert abs(fd - g["r"][i, q]) < 1e-7 * (1 + abs(g["r"][i, q]))
+            xp, xm = x.copy(), x.copy()
+            xp[i, q] += h2
+            xm[i, q] -= h2
+            lp, sp = _logpsi_signed(o, xp)
+            lm, sm = _logpsi_signed(o, xm)
+            lap_sum += (sp * sg0 * math.exp(lp - la0) + sm * sg0 * math.exp(lm - la0) - 2.0) / h2 ** 2
+    assert abs(-0.5 * lap_sum - kin) < 1e-5 * (1 + abs(kin))
+    assert np.allclose(g["R"].sum(0) + g["r"].sum(0), 0.0, atol=1e-9)
+    # J3 moves with the nuclei: d log|Psi| / d R_a against central differences
+    h = 1e-5
+    for a in range(3):
+        for q in range(3):
+            vals = []
+            for sgn in (1, -1):
+                t = synth.with_j3(synth.small_random(n_atoms=3, n_up=3, n_dn=2, per_atom=6, seed=122,
+                                                     slater_fraction=0.3), seed=122, sd=0.2)
+                t.R = t.R.copy()
+                t.R[a, q] += sgn * h
+                t.check()
+                vals.append(oracle.Oracle(t).logpsi(x)[0])
+            assert abs((vals[0] - vals[1]) / (2 * h) - g["R"][a, q]) < 1e-6 * (1 + abs(g["R"][a, q]))
+    la, sg, _, J = o.logpsi(x)
+    y = x.copy()
+    y[[0, 2]] = y[[2, 0]]
+    la2, sg2, _, J2 = o.logpsi(y)
+    assert abs(la2 - la) < 1e-12 and sg2 == -sg and abs(J2 - J) < 1e-13
