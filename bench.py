@@ -353,12 +353,13 @@ FORCES_WORKLOAD = ("adjoint gradients: 64 He atoms in a 16 bohr cube, N=128 (64 
                    "d log|Psi|/d b")
 
 
-def forces_bench(pg, torch, dist, args, dev, rank, ws, local, fp64_tc=False):
+def forces_bench(pg, torch, dist, args, dev, rank, ws, local, fp64_tc=False, steps=None):
     """E_L + forces per second: one step = jagp_grad over all walkers with the
     force-estimator seeds (sE = 1/M, sL = 2 (e_L - <e_L>)/M from the walkers'
     local energies), producing e_L, dE/dR, d log|Psi|/d lambda and d/d b."""
     import numpy as np
     import synth
+    steps = args.force_steps if steps is None else steps
     sysm = synth.config4()
     W = args.force_walkers
     x0 = np.ascontiguousarray(synth.init_walkers(sysm, W * ws, seed=0)[rank * W:(rank + 1) * W])
@@ -392,7 +393,7 @@ def forces_bench(pg, torch, dist, args, dev, rank, ws, local, fp64_tc=False):
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_push("forces")
     e0.record()
-    for _ in range(args.force_steps):
+    for _ in range(steps):
         call()
     e1.record()
     torch.cuda.nvtx.range_pop()
@@ -409,8 +410,9 @@ def forces_bench(pg, torch, dist, args, dev, rank, ws, local, fp64_tc=False):
     ecall()
     torch.cuda.synchronize()
     e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    esteps = max(3, steps // 4)
     e2.record()
-    for _ in range(args.force_steps):
+    for _ in range(esteps):
         ecall()
     e3.record()
     torch.cuda.synchronize()
@@ -422,7 +424,7 @@ def forces_bench(pg, torch, dist, args, dev, rank, ws, local, fp64_tc=False):
     g.close()
     n, nd = sysm.n_up, sysm.n_dn
     flops = 2.0 * L * L * W * (n + nd)  # the two lambda-product launches: 2 L^2 per orbital row
-    achieved = flops * args.force_steps / (lam_ms / 1e3) / 1e12 if lam_ms > 0 else None
+    achieved = flops * steps / (lam_ms / 1e3) / 1e12 if lam_ms > 0 else None
     if fp64_tc:
         kp = (L + 63) // 64 * 64
         nsl = 7 if L <= 512 else 8
@@ -435,14 +437,73 @@ def forces_bench(pg, torch, dist, args, dev, rank, ws, local, fp64_tc=False):
                 "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS if achieved else None,
                 "traffic": None, "work": "2 L^2 flop per orbital row of the two adjoint lambda products",
                 "launches": lam_n, "share_of_step": lam_ms / ms if ms > 0 else None}
-    return {"metric": "E_L+forces/s", "value": W * ws * args.force_steps / (ms_max / 1e3), "unit": "configurations/s",
-            "ms_per_step": ms_max / args.force_steps, "steps": args.force_steps, "warmup": args.force_warmup,
+    return {"metric": "E_L+forces/s", "value": W * ws * steps / (ms_max / 1e3), "unit": "configurations/s",
+            "ms_per_step": ms_max / steps, "steps": steps, "warmup": args.force_warmup,
             "dtype": "f64", "workload": FORCES_WORKLOAD, "walkers_per_gpu": W, "gpu_launches": launches,
-            "energy_only": {"metric": "E_L/s", "value": W * ws * args.force_steps / (ems_max / 1e3),
-                            "unit": "configurations/s", "ms_per_step": ems_max / args.force_steps,
+            "energy_only": {"metric": "E_L/s", "value": W * ws * esteps / (ems_max / 1e3),
+                            "unit": "configurations/s", "ms_per_step": ems_max / esteps, "steps": esteps,
                             "note": "jagp_eval + local_energy on the same configurations"},
-            "forces_to_energy_cost": ms_max / ems_max if ems_max > 0 else None,
+            "forces_to_energy_cost": (ms_max / steps) / (ems_max / esteps) if ems_max > 0 else None,
             "roofline": roof}
+
+
+REWEIGHTED_WORKLOAD = ("finite-variance forces on the adjoint workload's system (64 He, N=128, L=1536): walkers "
+                       "sampled from the guiding function (theta = 3/8, eps tuned to <W> = 0.8), reweighting factors "
+                       "W = (R / max(R, eps))^2, reweighted force seeds, adjoint and space warp")
+
+
+def reweighted_forces_bench(pg, torch, dist, args, dev, rank, ws, local):
+    """The full finite-variance force estimator of Sec. "Atomic forces": guided
+    sampling (eps tuned so that <W> is near 0.8), the weights, the reweighted
+    seeds, the FP64 adjoint and the space warp; one step = weights + seeds +
+    adjoint + warp on all walkers."""
+    import numpy as np
+    import synth
+    sysm = synth.config4()
+    W = args.reweighted_walkers
+    x0 = np.ascontiguousarray(synth.init_walkers(sysm, W * ws, seed=1)[rank * W:(rank + 1) * W])
+    g = pg.JAGP(sysm, W, seed=1)
+    r = g.positions(x0)
+    g.eval(r)
+    g.sweep(r, 4, walker0=rank * W, energies=False)
+    eps = pg.tune_guiding_eps(g, r, target=0.8, rounds=6, sweeps=2, walker0=rank * W, sweep0=10)
+    eL, _ = g.sweep(r, 2, walker0=rank * W, sweep0=100)
+    e = eL[-1].contiguous()
+    f64 = dict(dtype=torch.float64, device=dev)
+    na = sysm.n_atoms
+    wts = torch.empty(W, **f64)
+    work = torch.empty(pg.jagp_grad_workspace_bytes(g.h, W), dtype=torch.uint8, device=dev)
+    Rw, rb, dR = torch.empty((W, na, 3), **f64), torch.empty((W, sysm.N, 3), **f64), torch.empty((na, 3), **f64)
+    jas = torch.empty(3, **f64)
+
+    def step():
+        pg.jagp_guiding_weights(g.h, g.state, W, 0.375, eps, weights=wts)
+        sL, sE, mean = pg.jagp_force_seeds(e, wts)
+        pg.jagp_grad(g.h, r, g.state, W, work, sL, sE, None, None, jas, None, Rw, rb)
+        pg.jagp_space_warp(g.h, r, W, rb, Rw, seed_logpsi=sL, dR=dR)
+        return mean
+    step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.nvtx.range_push("forces_reweighted")
+    e0.record()
+    for _ in range(args.reweighted_steps):
+        mean = step()
+    e1.record()
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    mw = float(mean[1].item())
+    g.close()
+    return {"metric": "E_L+forces/s", "value": W * ws * args.reweighted_steps / (ms / 1e3), "unit": "configurations/s",
+            "ms_per_step": ms / args.reweighted_steps, "steps": args.reweighted_steps, "walkers_per_gpu": W,
+            "eps": eps, "mean_weight": mw, "dtype": "f64", "workload": REWEIGHTED_WORKLOAD}
 
 
 BATCH_WORKLOAD = ("batched uneven systems, mixed precision: 64 independent neutral He systems, N uniform in "
@@ -901,7 +962,8 @@ def run_gpu(args):
     forces = None if args.no_forces else forces_bench(pg, torch, dist, args, dev, rank, ws, local)
     forces_tc = None
     if not args.no_forces and not args.no_fp64tc:
-        forces_tc = forces_bench(pg, torch, dist, args, dev, rank, ws, local, fp64_tc=True)
+        forces_tc = forces_bench(pg, torch, dist, args, dev, rank, ws, local, fp64_tc=True,
+                                 steps=args.force_tc_steps)
         forces_tc["dtype"] = "f64 (lambda products FP64-equivalent on tensor cores)"
     batched = None if args.no_batch else batch_bench(pg, torch, dist, args, dev, rank, ws)
     batched64 = None
@@ -911,6 +973,7 @@ def run_gpu(args):
     large = None if args.no_large else large_bench(pg, torch, dist, args, dev, rank, ws, local)
     pipeline = None if args.no_large else pipeline_bench(pg, torch, dist, args, dev, rank, ws, local)
     sr = None if args.no_sr else sr_bench(pg, torch, dist, args, dev, rank, ws, local)
+    reweighted = None if args.no_forces else reweighted_forces_bench(pg, torch, dist, args, dev, rank, ws, local)
     c1 = None if args.no_c1 else c1_bench(pg, torch, dist, args, dev, rank, ws, local)
 
     if rank != 0:
@@ -998,6 +1061,8 @@ def run_gpu(args):
         out["pipeline"] = pipeline
     if sr is not None:
         out["sr"] = sr
+    if reweighted is not None:
+        out["forces_reweighted"] = reweighted
     if c1 is not None:
         out["c1"] = c1
     out["energy"] = energy
@@ -1029,11 +1094,14 @@ def main():
     ap.add_argument("--force-walkers", type=int, default=2048)
     ap.add_argument("--force-steps", type=int, default=20)
     ap.add_argument("--force-warmup", type=int, default=1)
+    ap.add_argument("--force-tc-steps", type=int, default=8)
+    ap.add_argument("--reweighted-walkers", type=int, default=512)
+    ap.add_argument("--reweighted-steps", type=int, default=5)
     ap.add_argument("--no-batch", action="store_true", help="skip the batched uneven-systems measurement")
     ap.add_argument("--batch-systems", type=int, default=64)
     ap.add_argument("--batch-walkers", type=int, default=512)
     ap.add_argument("--batch-sweeps", type=int, default=50)
-    ap.add_argument("--batch-fp64-sweeps", type=int, default=20)
+    ap.add_argument("--batch-fp64-sweeps", type=int, default=5)
     ap.add_argument("--batch-streams", type=int, default=16)
     ap.add_argument("--no-large", action="store_true", help="skip the 512-electron mixed-precision measurement")
     ap.add_argument("--large-walkers", type=int, default=1024)

@@ -78,6 +78,16 @@ typedef struct jagp_system {
   double b_para, b_anti;      /* J2 parameters */
   int use_j1, use_j2;
   int j2_spin_independent;    /* 1: r/(2(1+b_anti r)) for every pair */
+  /* three/four-body Jastrow (Eq. threebody_jastrow), read only when use_j3:
+   *   J3 = sum_{i<j} sum_{mu,nu} M^{s_i s_j}_{mu,nu} chi_mu(r_i) chi_nu(r_j)
+   * with its own basis chi (shells in the format above, LJ functions) and the
+   * symmetric coupling matrices j3_para (equal spins) and j3_anti [LJ][LJ].
+   * FP64 handles only; jagp_grad and guided sampling reject it (UNSUPPORTED). */
+  int n_jshells;
+  const int *jshell_atom, *jshell_l, *jshell_radial;
+  const double *jshell_zeta;
+  const double *j3_para, *j3_anti;
+  int use_j3;
 } jagp_system_t;
 
 typedef struct jagp_options {

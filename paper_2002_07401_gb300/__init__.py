@@ -34,6 +34,9 @@ class _System(C.Structure):
         ("n_up", C.c_int), ("n_dn", C.c_int), ("unpaired", C.c_void_p),
         ("b_ea", C.c_double), ("b_para", C.c_double), ("b_anti", C.c_double),
         ("use_j1", C.c_int), ("use_j2", C.c_int), ("j2_spin_independent", C.c_int),
+        ("n_jshells", C.c_int), ("jshell_atom", C.c_void_p), ("jshell_l", C.c_void_p),
+        ("jshell_radial", C.c_void_p), ("jshell_zeta", C.c_void_p), ("j3_para", C.c_void_p),
+        ("j3_anti", C.c_void_p), ("use_j3", C.c_int),
     ]
 
 
@@ -194,6 +197,13 @@ def jagp_create(sysm, precision: int = JAGP_PREC_FP64, max_walkers: int = 1, del
     s.b_ea, s.b_para, s.b_anti = float(sysm.b_ea), float(sysm.b_para), float(sysm.b_anti)
     s.use_j1, s.use_j2 = int(sysm.use_j1), int(sysm.use_j2)
     s.j2_spin_independent = int(sysm.j2_spin_independent)
+    j3 = getattr(sysm, "j3", None)
+    if j3 is not None:
+        s.n_jshells = int(len(j3["shell_l"]))
+        s.jshell_atom, s.jshell_l = arr(j3["shell_atom"], np.int32), arr(j3["shell_l"], np.int32)
+        s.jshell_radial, s.jshell_zeta = arr(j3["shell_radial"], np.int32), arr(j3["shell_zeta"], np.float64)
+        s.j3_para, s.j3_anti = arr(j3["para"], np.float64), arr(j3["anti"], np.float64)
+        s.use_j3 = 1
     o = _Options()
     o.precision, o.max_walkers = int(precision), int(max_walkers)
     o.delta = float(sysm.delta if delta is None else delta)

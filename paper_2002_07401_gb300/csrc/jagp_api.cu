@@ -71,7 +71,8 @@ bool tc_refresh(const jagp_ctx *h) { return h->precision == JAGP_PREC_MIXED && h
 Layout layout_of(const jagp_ctx *h, int W) {
   const bool mixed = h->precision == JAGP_PREC_MIXED;
   return make_layout((size_t)W, (size_t)h->ds.n_up, (size_t)h->ds.N, (size_t)h->ds.L, mixed ? 4 : 8,
-                     h->tc_lambda ? (size_t)h->kp : 0, (size_t)h->tc_slices, tc_refresh(h));
+                     h->tc_lambda ? (size_t)h->kp : 0, (size_t)h->tc_slices, tc_refresh(h),
+                     h->ds.use_j3 ? (size_t)h->ds.LJ : 0);
 }
 
 // the fifteen slice pairs (a, b) with a + b <= 4 of the five-slice fixed-point
@@ -203,6 +204,10 @@ float *lo_table(const jagp_ctx *h, void *state, size_t off) {
 // where the refresh keeps G~ (its own array: the proposed rows in gprop stay
 // valid across refreshes within a half-sweep)
 double *refresh_g(const Layout &L, void *state) { return at<double>(state, L.g64); }
+// the three-body Jastrow's per-walker vectors (null without it)
+double *j3_vectors(const jagp_ctx *h, const Layout &L, void *state) {
+  return h->ds.use_j3 ? at<double>(state, L.j3buf) : nullptr;
+}
 
 // the local-energy sequence on a current state
 // Mixed path: the M vectors of the kinetic energy as exact fixed-point
@@ -265,6 +270,7 @@ jagp_status_t run_local_energy(jagp_ctx *h, const double *r, void *state, int W,
     const jagp_status_t s = run_kinetic_mixed(h, r, state, W, st);
     if (s != JAGP_OK) return s;
   } else {
+    if (h->ds.use_j3) LAUNCH(0, 1, launch_j3_prep(h->ds, r, j3_vectors(h, L, state), W, st));
     LAUNCH(JAGP_KERNEL_ENERGY, 1,
            launch_mmat<T>(h->ds, at<T>(state, L.ginv), at<T>(state, L.bt), at<T>(state, L.a_up), at<T>(state, L.mbuf),
                           W, st));
@@ -275,7 +281,8 @@ jagp_status_t run_local_energy(jagp_ctx *h, const double *r, void *state, int W,
   if (std::is_same<T, float>::value)
     LAUNCH(JAGP_KERNEL_ENERGY, 1, launch_elocal_dw(h->ds, r, at<double>(state, L.kin), eL, parts, W, st, sc));
   else
-    LAUNCH(JAGP_KERNEL_ENERGY, 1, launch_elocal(h->ds, r, at<double>(state, L.kin), eL, parts, W, st, sc));
+    LAUNCH(JAGP_KERNEL_ENERGY, 1,
+           launch_elocal(h->ds, r, at<double>(state, L.kin), eL, parts, W, st, sc, j3_vectors(h, L, state)));
   return JAGP_OK;
 }
 
@@ -311,7 +318,10 @@ jagp_status_t run_refresh(jagp_ctx *h, const double *r, void *state, int W, int 
   LAUNCH(0, 1,
          launch_refresh_inverse<T>(gm, at<T>(state, L.ginv), at<double>(state, L.scal), at<int>(state, L.status), n,
                                    W, check_drift, h->drift_tol, st, gi64));
-  if (jastrow) LAUNCH(0, 1, launch_jastrow_full(h->ds, r, at<double>(state, L.scal), W, st));
+  if (jastrow) {
+    if (h->ds.use_j3) LAUNCH(0, 1, launch_j3_prep(h->ds, r, j3_vectors(h, L, state), W, st));
+    LAUNCH(0, 1, launch_jastrow_full(h->ds, r, at<double>(state, L.scal), W, st, j3_vectors(h, L, state)));
+  }
   return JAGP_OK;
 }
 
@@ -398,7 +408,7 @@ jagp_status_t run_sweeps(jagp_ctx *h, double *d_r, void *d_state, int W, int nsw
       if (!guided)
         LAUNCH(JAGP_KERNEL_METROPOLIS, 1,
                launch_metropolis<T>(d, up, d_r, rprop, gprop, ginv, scal, status, pprop, phi_up, list, chunk, W, st,
-                                    pprop_lo, phi_lo, m0, m1, total));
+                                    pprop_lo, phi_lo, m0, m1, total, j3_vectors(h, L, d_state)));
       jagp_status_t q =
           lambda_products(h, pprop, pprop_lo, up ? a_up : bt, up, list, chunk, 0, 1, 0, W * n, d_state, W, st);
       if (q != JAGP_OK) return q;
@@ -409,6 +419,8 @@ jagp_status_t run_sweeps(jagp_ctx *h, double *d_r, void *d_state, int W, int nsw
     }
     return JAGP_OK;
   };
+  // the three-body Jastrow's vectors from the positions (the acceptance kernels keep them current)
+  if (d.use_j3 && nsweeps > 0) LAUNCH(0, 1, launch_j3_prep(d, d_r, j3_vectors(h, L, d_state), W, st));
   for (int t = 0; t < nsweeps; ++t) {
     const uint32_t sw = (uint32_t)(sweep0 + (uint64_t)t);
     JAGP_CU(cudaMemsetAsync(count, 0, 2 * sizeof(int), st));
@@ -507,6 +519,10 @@ static jagp_status_t jagp_grad_impl(jagp_handle_t h, const double *d_r, void *d_
   if (s != JAGP_OK) return s;
   if (!d_r || !d_work || (reinterpret_cast<uintptr_t>(d_work) & 255u)) return JAGP_ERR_INVALID_ARG;
   if (h->precision != JAGP_PREC_FP64) return JAGP_ERR_UNSUPPORTED;
+  if (h->ds.use_j3) {
+    jagp_set_detail("the adjoint does not carry the three-body Jastrow");
+    return JAGP_ERR_UNSUPPORTED;
+  }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const DevSystem &d = h->ds;
   const int n = d.n_up, nd = d.n_dn, N = d.N, Lb = d.L;
@@ -643,6 +659,40 @@ jagp_status_t jagp_create(jagp_handle_t *out, const jagp_system_t *sys, const ja
   for (int i = 0; i < L; ++i)
     for (int j = 0; j < L; ++j) lamT[(size_t)j * L + i] = sys->lambda[(size_t)i * L + j];
 
+  // three/four-body Jastrow: its shell table (caller order) and couplings
+  int LJ = 0;
+  std::vector<double4> jgeo;
+  std::vector<int> jinfo;
+  if (sys->use_j3) {
+    if (opt->precision != JAGP_PREC_FP64) {
+      jagp_set_detail("the three-body Jastrow runs in the FP64 path only");
+      return JAGP_ERR_UNSUPPORTED;
+    }
+    if (sys->n_jshells <= 0 || !sys->jshell_atom || !sys->jshell_l || !sys->jshell_radial || !sys->jshell_zeta ||
+        !sys->j3_para || !sys->j3_anti)
+      return JAGP_ERR_INVALID_ARG;
+    for (int k = 0; k < sys->n_jshells; ++k) {
+      const int l = sys->jshell_l[k], a = sys->jshell_atom[k], rad = sys->jshell_radial[k];
+      if (l < 0 || l > 2 || rad < 0 || rad > 1) return JAGP_ERR_UNSUPPORTED;
+      if (a < 0 || a >= sys->n_atoms || !(sys->jshell_zeta[k] >= 0.0)) return JAGP_ERR_INVALID_ARG;
+      jgeo.push_back(make_double4(sys->R[3 * a], sys->R[3 * a + 1], sys->R[3 * a + 2], sys->jshell_zeta[k]));
+      jinfo.push_back(l | (rad << 2) | (LJ << 8));
+      LJ += 2 * l + 1;
+    }
+    for (int i = 0; i < LJ; ++i)
+      for (int j = 0; j < LJ; ++j)
+        if (sys->j3_para[i * LJ + j] != sys->j3_para[j * LJ + i] || sys->j3_anti[i * LJ + j] != sys->j3_anti[j * LJ + i]) {
+          jagp_set_detail("the three-body couplings must be symmetric");
+          return JAGP_ERR_INVALID_ARG;
+        }
+    // the sequential acceptance keeps G~^{-1} and the Jastrow vectors in shared memory
+    const size_t n = sys->n_up, N = sys->n_up + sys->n_dn;
+    if ((N * 3 + n * n + 3 * n + 9 * (size_t)LJ) * 8 > 200 * 1024) {
+      jagp_set_detail("three-body Jastrow with N_up = %d and LJ = %d does not fit the acceptance kernel", sys->n_up,
+                      LJ);
+      return JAGP_ERR_UNSUPPORTED;
+    }
+  }
   jagp_ctx *h = new jagp_ctx();
   if (cudaGetDevice(&h->device) != cudaSuccess) {
     delete h;
@@ -683,6 +733,8 @@ jagp_status_t jagp_create(jagp_handle_t *out, const jagp_system_t *sys, const ja
   const size_t exp_bytes = tc ? (size_t)L * 4 : 0;
   const size_t oSA = take(split_bytes), oSB = take(split_bytes), oXA = take(exp_bytes), oXB = take(exp_bytes);
   const size_t oE = take(16);
+  const size_t oJG = take((size_t)jgeo.size() * sizeof(double4)), oJI = take(jinfo.size() * sizeof(int));
+  const size_t oJP = take((size_t)LJ * LJ * 8), oJA = take((size_t)LJ * LJ * 8);
   std::vector<uint16_t> sA(split_bytes / 2, 0), sB(split_bytes / 2, 0);
   std::vector<int> xA(tc ? L : 0), xB(tc ? L : 0);
   if (tc) {
@@ -718,7 +770,12 @@ jagp_status_t jagp_create(jagp_handle_t *out, const jagp_system_t *sys, const ja
                         cudaMemcpy(b + oSB, sB.data(), split_bytes, cudaMemcpyHostToDevice) == cudaSuccess &&
                         cudaMemcpy(b + oXA, xA.data(), exp_bytes, cudaMemcpyHostToDevice) == cudaSuccess &&
                         cudaMemcpy(b + oXB, xB.data(), exp_bytes, cudaMemcpyHostToDevice) == cudaSuccess)) &&
-            cudaMemset(b + oE, 0, 16) == cudaSuccess;
+            cudaMemset(b + oE, 0, 16) == cudaSuccess &&
+            (LJ == 0 ||
+             (cudaMemcpy(b + oJG, jgeo.data(), jgeo.size() * sizeof(double4), cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemcpy(b + oJI, jinfo.data(), jinfo.size() * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemcpy(b + oJP, sys->j3_para, (size_t)LJ * LJ * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemcpy(b + oJA, sys->j3_anti, (size_t)LJ * LJ * 8, cudaMemcpyHostToDevice) == cudaSuccess));
   if (!ok) {
     cudaFree(h->d_mem);
     delete h;
@@ -755,6 +812,13 @@ jagp_status_t jagp_create(jagp_handle_t *out, const jagp_system_t *sys, const ja
   d.delta = opt->delta;
   d.key0 = (uint32_t)(opt->seed & 0xffffffffu);
   d.key1 = (uint32_t)(opt->seed >> 32);
+  d.use_j3 = LJ > 0 ? 1 : 0;
+  d.n_jshells = LJ > 0 ? sys->n_jshells : 0;
+  d.LJ = LJ;
+  d.jshell_geo = reinterpret_cast<const double4 *>(b + oJG);
+  d.jshell_info = reinterpret_cast<const int *>(b + oJI);
+  d.j3p = reinterpret_cast<const double *>(b + oJP);
+  d.j3a = reinterpret_cast<const double *>(b + oJA);
   h->precision = opt->precision;
   h->kp = kp;
   h->split_lamT = tc ? reinterpret_cast<const uint16_t *>(b + oSA) : nullptr;
@@ -1460,8 +1524,8 @@ jagp_status_t jagp_set_guiding(jagp_handle_t h, double theta, double eps) {
     jagp_set_detail("theta = %g, eps = %g (theta > 0, eps >= 0)", theta, eps);
     return jagp_note(h, "jagp_set_guiding", JAGP_ERR_INVALID_ARG);
   }
-  if (eps > 0.0 && (h->precision != JAGP_PREC_FP64 || h->ds.n_up > kGuidedMaxUp)) {
-    jagp_set_detail("guided sampling needs an FP64 handle with N_up <= %d", kGuidedMaxUp);
+  if (eps > 0.0 && (h->precision != JAGP_PREC_FP64 || h->ds.n_up > kGuidedMaxUp || h->ds.use_j3)) {
+    jagp_set_detail("guided sampling needs an FP64 handle with N_up <= %d and no three-body Jastrow", kGuidedMaxUp);
     return jagp_note(h, "jagp_set_guiding", JAGP_ERR_UNSUPPORTED);
   }
   h->guide_theta = theta;

@@ -44,6 +44,11 @@ struct DevSystem {
   double v_ii;              // ion-ion repulsion (a constant of the system)
   double delta;
   uint32_t key0, key1;      // Philox key
+  // three/four-body Jastrow (FP64 path): its shells, LJ functions, couplings [LJ][LJ]
+  int use_j3, n_jshells, LJ;
+  const double4 *jshell_geo;
+  const int *jshell_info;
+  const double *j3p, *j3a;
 };
 
 // Byte offsets of the per-walker arrays inside the caller's state buffer.
@@ -86,6 +91,8 @@ struct Layout {
   size_t mexp_a;   // int    [W n_up]        their exponents
   size_t mexp_b;   // int    [W L]
   size_t mrows;    // int    [W n_up]        destination rows of the M product
+  size_t j3buf;    // double [W][6][LJ]      three-body Jastrow: U_up, U_dn (spin sums of chi), M_p U_up,
+                   //                        M_p U_dn, M_a U_up, M_a U_dn
   size_t total;
 };
 
@@ -95,7 +102,7 @@ inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // esz: bytes per table element (8 or 4); kp: padded K of the packed operand (0 = none)
 inline Layout make_layout(size_t W, size_t nu, size_t N, size_t L, size_t esz = 8, size_t kp = 0,
-                          size_t nsl = kFixedSlices, bool tc_refresh = false) {
+                          size_t nsl = kFixedSlices, bool tc_refresh = false, size_t lj = 0) {
   Layout l;
   size_t o = 0;
   auto take = [&](size_t bytes) { size_t r = o; o = align256(o + bytes); return r; };
@@ -135,6 +142,7 @@ inline Layout make_layout(size_t W, size_t nu, size_t N, size_t L, size_t esz = 
   l.mexp_a = take(mx ? W * nu * 4 : 0);
   l.mexp_b = take(mx ? W * L * 4 : 0);
   l.mrows = take(mx ? W * nu * 4 : 0);
+  l.j3buf = take(W * 6 * lj * 8);
   l.total = o;
   return l;
 }

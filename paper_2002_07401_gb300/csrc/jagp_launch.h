@@ -26,7 +26,8 @@ template <typename T>
 cudaError_t launch_metropolis(const DevSystem &s, bool up, double *r, const double *rprop, const T *gprop,
                               T *ginv, double *scal, int *status, const T *pprop, T *phi_up, int *list,
                               int *count, int W, cudaStream_t st, const float *pprop_lo = nullptr,
-                              float *phi_lo = nullptr, int m_begin = 0, int m_end = -1, int *total = nullptr);
+                              float *phi_lo = nullptr, int m_begin = 0, int m_end = -1, int *total = nullptr,
+                              double *j3buf = nullptr);
 
 // The Metropolis half-sweep (FP64, N_up <= kGuidedMaxUp) sampling the guiding
 // function: acceptance |Psi_T'/Psi_T|^2 W / W', W = (R / max(R, eps))^2; gmat
@@ -69,8 +70,11 @@ template <typename T>
 cudaError_t launch_refresh_inverse(double *gm, T *ginv, double *scal, int *status, int n, int W,
                                    int check_drift, double drift_tol, cudaStream_t st, double *ginv64 = nullptr);
 
+// J = J1 + J2 (+ J3 from the walker's j3 vectors j3buf [W][6][LJ], when the system has it)
 cudaError_t launch_jastrow_full(const DevSystem &s, const double *r, double *scal, int W,
-                                cudaStream_t st);
+                                cudaStream_t st, const double *j3buf = nullptr);
+// the three-body Jastrow's per-walker vectors (U_s and M U_s, see j3.cuh) from the positions
+cudaError_t launch_j3_prep(const DevSystem &s, const double *r, double *buf, int W, cudaStream_t st);
 
 // M vectors of the kinetic energy (see k_linalg.cu), then the orbital
 // derivative contractions and the final per-walker local energy.
@@ -88,7 +92,8 @@ cudaError_t launch_mmat_dw(const DevSystem &s, const double *ginv64, const float
 cudaError_t launch_kinetic_m2(const DevSystem &s, const double *r, const float *mbuf, const float *mlo, double *kin,
                               int W, cudaStream_t st);
 cudaError_t launch_elocal(const DevSystem &s, const double *r, const double *kin, double *eL,
-                          double *parts, int W, cudaStream_t st, double *scal = nullptr);
+                          double *parts, int W, cudaStream_t st, double *scal = nullptr,
+                          const double *j3buf = nullptr);
 // the FP32 path's version (double-word distances, Coulomb sums and Jastrow values)
 cudaError_t launch_elocal_dw(const DevSystem &s, const double *r, const double *kin, double *eL,
                              double *parts, int W, cudaStream_t st, double *scal = nullptr);

@@ -100,6 +100,10 @@ jagp_status_t scratch_address(int device, void **out) {
 jagp_status_t eval_noalloc(jagp_handle_t h, const double *d_r, int W, double *d_logabs, double *d_sign,
                            void *stream) {
   if (!h || !d_r || W <= 0 || W > h->max_walkers) return JAGP_ERR_INVALID_ARG;
+  if (h->ds.use_j3) {
+    jagp_set_detail("the fixed scratch holds no three-body Jastrow vectors");
+    return JAGP_ERR_UNSUPPORTED;
+  }
   const DevSystem &d = h->ds;
   const int n = d.n_up, Lb = d.L;
   const EvalScratch S = eval_scratch_layout((size_t)W, (size_t)n, (size_t)Lb);

@@ -6,6 +6,7 @@
 
 #include <type_traits>
 
+#include "j3.cuh"
 #include "jagp_launch.h"
 
 namespace jagp {
@@ -289,7 +290,8 @@ cudaError_t launch_kinetic_m2(const DevSystem &s, const double *r, const float *
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(128) k_elocal(DevSystem s, const double *__restrict__ r,
                                                 const double *__restrict__ kin, double *__restrict__ eL,
-                                                double *__restrict__ parts, double *__restrict__ scal) {
+                                                double *__restrict__ parts, double *__restrict__ scal,
+                                                const double *__restrict__ j3buf) {
   const int w = blockIdx.x, N = s.N, tid = threadIdx.x;
   extern __shared__ double xs[];
   for (int t = tid; t < N * 3; t += blockDim.x) xs[t] = r[(size_t)w * N * 3 + t];
@@ -345,6 +347,14 @@ __global__ void __launch_bounds__(128) k_elocal(DevSystem s, const double *__res
         gJz += q * dz;
         lJ += vpp + 2.0 * q;
       }
+    }
+    if (s.use_j3 && j3buf) {
+      // three/four-body Jastrow: 1/2 chi^T Q to J, (grad chi)^T Q, (lap chi)^T Q
+      double g3[3] = {0.0, 0.0, 0.0};
+      j3_electron(s, j3buf + (size_t)w * 6 * s.LJ, e < s.n_up, ex, ey, ez, &jv, g3, &lJ);
+      gJx += g3[0];
+      gJy += g3[1];
+      gJz += g3[2];
     }
     const double *kd = kin + ((size_t)w * N + e) * 4;
     const double t = kd[3] + lJ + 2.0 * (kd[0] * gJx + kd[1] * gJy + kd[2] * gJz) +
@@ -577,9 +587,10 @@ cudaError_t launch_elocal_dw(const DevSystem &s, const double *r, const double *
 }
 
 cudaError_t launch_elocal(const DevSystem &s, const double *r, const double *kin, double *eL, double *parts, int W,
-                          cudaStream_t st, double *scal) {
+                          cudaStream_t st, double *scal, const double *j3buf) {
   if (W <= 0) return cudaSuccess;
-  k_elocal<<<W, 128, (size_t)s.N * 3 * sizeof(double), st>>>(s, r, kin, eL, parts, scal);
+  if (s.use_j3 && !j3buf) return cudaErrorInvalidValue;
+  k_elocal<<<W, 128, (size_t)s.N * 3 * sizeof(double), st>>>(s, r, kin, eL, parts, scal, j3buf);
   return cudaGetLastError();
 }
 

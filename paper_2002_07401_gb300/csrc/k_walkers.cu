@@ -5,6 +5,7 @@
 
 #include <type_traits>
 
+#include "j3.cuh"
 #include "jagp_launch.h"
 
 namespace jagp {
@@ -231,7 +232,7 @@ __global__ void __launch_bounds__(512) k_metropolis(DevSystem s, double *__restr
                                                     int *__restrict__ count,
                                                     const float *__restrict__ pprop_lo,
                                                     float *__restrict__ phi_lo, int m_begin, int m_end,
-                                                    int *__restrict__ total) {
+                                                    int *__restrict__ total, double *__restrict__ j3buf) {
   extern __shared__ double sm[];
   const int n = s.n_up, N = s.N, tid = threadIdx.x, bs = blockDim.x;
   const int w = blockIdx.x;
@@ -245,6 +246,14 @@ __global__ void __launch_bounds__(512) k_metropolis(DevSystem s, double *__restr
   T *cc = vv + n;                                   // n
   float *xf = reinterpret_cast<float *>(cc + n);    // mixed path: N * 3 positions rounded to FP32
   constexpr bool kF32 = std::is_same<T, float>::value;
+  // three-body Jastrow (FP64 path, G~^{-1} in shared memory): the walker's j3
+  // vectors [6][LJ] and chi at the old and the proposed position, chi change
+  const bool j3 = !kF32 && !GLOB && s.use_j3 && j3buf;
+  const int LJ = s.LJ;
+  double *j3v = reinterpret_cast<double *>(cc + n);  // 6 LJ (no FP32 mirror in the FP64 path)
+  double *chi_o = j3v + 6 * LJ, *chi_n = chi_o + LJ, *dchi = chi_n + LJ;
+  if (j3)
+    for (int t = tid; t < 6 * LJ; t += bs) j3v[t] = j3buf[(size_t)w * 6 * LJ + t];
   __shared__ double red[64];
   __shared__ int s_acc;
   __shared__ double s_R;
@@ -284,6 +293,28 @@ __global__ void __launch_bounds__(512) k_metropolis(DevSystem s, double *__restr
         pj += static_cast<double>(j2_move_change_f<UP>(s, xf, e, pf, of, tid, bs));
       } else {
         pj += j2_move_change<T, UP>(s, xs, e, px, py, pz, ox, oy, oz, tid, bs);
+      }
+    }
+    if (j3) {
+      // chi at the old and the proposed position (threads over the Jastrow's shells)
+      for (int k = tid; k < s.n_jshells; k += bs) {
+        const double4 g = s.jshell_geo[k];
+        const int info = s.jshell_info[k], off = shell_off(info);
+        double vo[5], vn[5];
+        const int nc = shell_values(info, g.w, ox - g.x, oy - g.y, oz - g.z, vo);
+        shell_values(info, g.w, px - g.x, py - g.y, pz - g.z, vn);
+        for (int c = 0; c < nc; ++c) {
+          chi_o[off + c] = vo[c];
+          chi_n[off + c] = vn[c];
+        }
+      }
+      __syncthreads();
+      // d J3 = (chi' - chi)^T Q, Q = M_p U_s + M_a U_s' - M_p chi
+      const double *Vs = j3v + (UP ? 2 : 3) * LJ, *Va = j3v + (UP ? 5 : 4) * LJ;
+      for (int mu = tid; mu < LJ; mu += bs) {
+        double mc = 0.0;
+        for (int nu = 0; nu < LJ; ++nu) mc = fma(s.j3p[(size_t)mu * LJ + nu], chi_o[nu], mc);
+        pj = fma(chi_n[mu] - chi_o[mu], Vs[mu] + Va[mu] - mc, pj);
       }
     }
     block_sum2(pr, pj, red);
@@ -354,9 +385,27 @@ __global__ void __launch_bounds__(512) k_metropolis(DevSystem s, double *__restr
         if (phi_lo)
           for (int t = tid; t < s.L; t += bs) phi_lo[row + t] = pprop_lo[row + t];
       }
+      if (j3) {
+        // the spin sum and its two products follow the moved electron
+        for (int t = tid; t < LJ; t += bs) dchi[t] = chi_n[t] - chi_o[t];
+        __syncthreads();
+        double *U = j3v + (UP ? 0 : 1) * LJ, *Up = j3v + (UP ? 2 : 3) * LJ, *Ua = j3v + (UP ? 4 : 5) * LJ;
+        for (int mu = tid; mu < LJ; mu += bs) {
+          double ap = 0.0, aa = 0.0;
+          for (int nu = 0; nu < LJ; ++nu) {
+            ap = fma(s.j3p[(size_t)mu * LJ + nu], dchi[nu], ap);
+            aa = fma(s.j3a[(size_t)mu * LJ + nu], dchi[nu], aa);
+          }
+          U[mu] += dchi[mu];
+          Up[mu] += ap;
+          Ua[mu] += aa;
+        }
+      }
     }
     __syncthreads();
   }
+  if (j3)
+    for (int t = tid; t < 6 * LJ; t += bs) j3buf[(size_t)w * 6 * LJ + t] = j3v[t];
   if (!GLOB)
     for (int t = tid; t < n * n; t += bs) gw[t] = Gi[t];
   for (int t = tid; t < N * 3; t += bs) r[(size_t)w * N * 3 + t] = xs[t];
@@ -757,11 +806,27 @@ template <typename T>
 cudaError_t launch_metropolis(const DevSystem &s, bool up, double *r, const double *rprop, const T *gprop, T *ginv,
                               double *scal, int *status, const T *pprop, T *phi_up, int *list, int *count, int W,
                               cudaStream_t st, const float *pprop_lo, float *phi_lo, int m_begin, int m_end,
-                              int *total) {
+                              int *total, double *j3buf) {
   if (W <= 0 || (!up && s.n_dn == 0)) return cudaSuccess;
   if (m_end < 0) m_end = up ? s.n_up : s.n_dn;
   if (m_begin >= m_end) return cudaSuccess;
   const int n = s.n_up;
+  const bool j3 = s.use_j3 && std::is_same<T, double>::value;
+  if (j3) {
+    // the three-body Jastrow's change is formed in the CTA-per-walker kernel
+    const size_t per3 = metro_smem_per_walker<T>(n, s.N) + (size_t)9 * s.LJ * sizeof(double);
+    if (!j3buf || per3 > kMetroSmemMax) return cudaErrorInvalidValue;
+    const int threads = n <= 64 ? 128 : 256;
+    if (up)
+      k_metropolis<true, T, false><<<W, threads, per3, st>>>(s, r, rprop, gprop, ginv, scal, status, pprop, phi_up,
+                                                              list, count, pprop_lo, phi_lo, m_begin, m_end, total,
+                                                              j3buf);
+    else
+      k_metropolis<false, T, false><<<W, threads, per3, st>>>(s, r, rprop, gprop, ginv, scal, status, pprop, phi_up,
+                                                               list, count, pprop_lo, phi_lo, m_begin, m_end, total,
+                                                               j3buf);
+    return cudaGetLastError();
+  }
   const size_t per = metro_smem_per_walker<T>(n, s.N);
   if (n <= 32) {
     const int blocks = (W + kMetroWarps - 1) / kMetroWarps;
@@ -777,34 +842,35 @@ cudaError_t launch_metropolis(const DevSystem &s, bool up, double *r, const doub
     const int threads = n <= 64 ? 128 : 256;
     if (up)
       k_metropolis<true, T, false><<<W, threads, per, st>>>(s, r, rprop, gprop, ginv, scal, status, pprop, phi_up,
-                                                             list, count, pprop_lo, phi_lo, m_begin, m_end, total);
+                                                             list, count, pprop_lo, phi_lo, m_begin, m_end, total, nullptr);
     else
       k_metropolis<false, T, false><<<W, threads, per, st>>>(s, r, rprop, gprop, ginv, scal, status, pprop, phi_up,
-                                                              list, count, pprop_lo, phi_lo, m_begin, m_end, total);
+                                                              list, count, pprop_lo, phi_lo, m_begin, m_end, total,
+                                                              nullptr);
     return cudaGetLastError();
   }
   const size_t glob = (size_t)s.N * 3 * sizeof(double) + (size_t)3 * n * sizeof(T) +
                       (std::is_same<T, float>::value ? (size_t)s.N * 3 * sizeof(float) : 0);
   if (up)
     k_metropolis<true, T, true><<<W, 512, glob, st>>>(s, r, rprop, gprop, ginv, scal, status, pprop, phi_up, list,
-                                                       count, pprop_lo, phi_lo, m_begin, m_end, total);
+                                                       count, pprop_lo, phi_lo, m_begin, m_end, total, nullptr);
   else
     k_metropolis<false, T, true><<<W, 512, glob, st>>>(s, r, rprop, gprop, ginv, scal, status, pprop, phi_up, list,
-                                                        count, pprop_lo, phi_lo, m_begin, m_end, total);
+                                                        count, pprop_lo, phi_lo, m_begin, m_end, total, nullptr);
   return cudaGetLastError();
 }
 template cudaError_t launch_metropolis<double>(const DevSystem &, bool, double *, const double *, const double *,
                                                double *, double *, int *, const double *, double *, int *, int *,
-                                               int, cudaStream_t, const float *, float *, int, int, int *);
+                                               int, cudaStream_t, const float *, float *, int, int, int *, double *);
 template cudaError_t launch_metropolis<float>(const DevSystem &, bool, double *, const double *, const float *,
                                               float *, double *, int *, const float *, float *, int *, int *, int,
-                                              cudaStream_t, const float *, float *, int, int, int *);
+                                              cudaStream_t, const float *, float *, int, int, int *, double *);
 
 // ---------------------------------------------------------------------------
 // J = J1 + J2 of each walker from scratch (one CTA per walker).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(128) k_jastrow_full(DevSystem s, const double *__restrict__ r,
-                                                      double *__restrict__ scal) {
+                                                      double *__restrict__ scal, const double *__restrict__ j3buf) {
   const int w = blockIdx.x, N = s.N;
   const double *x = r + (size_t)w * N * 3;
   __shared__ double red[64];
@@ -824,13 +890,20 @@ __global__ void __launch_bounds__(128) k_jastrow_full(DevSystem s, const double 
       const double dx = x[3 * i] - x[3 * j], dy = x[3 * i + 1] - x[3 * j + 1], dz = x[3 * i + 2] - x[3 * j + 2];
       j2 += j2_val(kk, bb, sqrt(dx * dx + dy * dy + dz * dz));
     }
+  if (s.use_j3 && j3buf)
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+      double g3[3] = {0.0, 0.0, 0.0}, l3 = 0.0;
+      j3_electron(s, j3buf + (size_t)w * 6 * s.LJ, i < s.n_up, x[3 * i], x[3 * i + 1], x[3 * i + 2], &j2, g3, &l3);
+    }
   block_sum2(j1, j2, red);
   if (threadIdx.x == 0) scal[(size_t)w * S_STRIDE + S_J] = j1 + j2;
 }
 
-cudaError_t launch_jastrow_full(const DevSystem &s, const double *r, double *scal, int W, cudaStream_t st) {
+cudaError_t launch_jastrow_full(const DevSystem &s, const double *r, double *scal, int W, cudaStream_t st,
+                                const double *j3buf) {
   if (W <= 0) return cudaSuccess;
-  k_jastrow_full<<<W, 128, 0, st>>>(s, r, scal);
+  if (s.use_j3 && !j3buf) return cudaErrorInvalidValue;
+  k_jastrow_full<<<W, 128, 0, st>>>(s, r, scal, j3buf);
   return cudaGetLastError();
 }
 
