@@ -89,6 +89,17 @@ def lib():
         L.orc_elocal_grad_fd.restype = i
         L.orc_elocal_dlambda_fd.argtypes = [vp, vp, i, i, d]
         L.orc_elocal_dlambda_fd.restype = d
+        L.orc_elocal_fd_select.argtypes = [vp, vp, d, i, vp, vp, vp]
+        L.orc_elocal_fd_select.restype = i
+        L.orc_lrdmc_hops.argtypes = [vp, vp, d, d, vp, vp, vp, vp]
+        L.orc_lrdmc_hops.restype = i
+        L.orc_lrdmc_project.argtypes = [vp, vp, i, C.c_longlong, C.c_uint64, C.c_longlong, d, d, d, d, i, vp, vp,
+                                        vp, vp, i]
+        L.orc_lrdmc_project.restype = i
+        L.orc_lrdmc_branch.argtypes = [i, C.c_uint64, C.c_longlong, vp, vp, vp, vp, vp]
+        L.orc_lrdmc_branch.restype = None
+        L.orc_lrdmc_energy.argtypes = [i, vp, vp, i]
+        L.orc_lrdmc_energy.restype = d
         L.orc_reblock_levels.argtypes = [i]
         L.orc_reblock_levels.restype = i
         L.orc_reblock.argtypes = [vp, i, i, vp, vp]
@@ -176,6 +187,25 @@ def sr(O, e, eps=1e-3, delta=1.0, want_S=True):
     if not ok:
         raise ValueError("singular regularised S matrix")
     return {"Obar": Ob, "S": S, "f": f, "dalpha": da}
+
+
+def lrdmc_branch(w, eL, seed=0, gen=0):
+    """Reconfiguration after an LRDMC projection (Eqs. branching-1, -2):
+    (parent indices [W], wbar, ebar)."""
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    eL = np.ascontiguousarray(eL, dtype=np.float64)
+    W = int(w.shape[0])
+    parent = np.zeros(W, dtype=np.int32)
+    wb, eb = C.c_double(), C.c_double()
+    lib().orc_lrdmc_branch(W, int(seed), int(gen), _p(w), _p(eL), _p(parent), C.addressof(wb), C.addressof(eb))
+    return parent, wb.value, eb.value
+
+
+def lrdmc_energy(wbar, ebar, p):
+    """LRDMC energy with the correcting factor of p generations."""
+    wbar = np.ascontiguousarray(wbar, dtype=np.float64)
+    ebar = np.ascontiguousarray(ebar, dtype=np.float64)
+    return float(lib().orc_lrdmc_energy(int(wbar.shape[0]), _p(wbar), _p(ebar), int(p)))
 
 
 def max_threads() -> int:
@@ -293,6 +323,73 @@ class Oracle:
         dr = np.zeros((self.N, 3)) if want_r else None
         lib().orc_elocal_grad_fd(self._ps, _p(x), float(h), _p(dR), _p(dr))
         return dR, dr
+
+    def elocal_fd_select(self, x, R=(), r=(), lam=(), h=1e-4):
+        """Selected components of the same Richardson-extrapolated central
+        differences, in parallel: R and r are lists of (atom or electron, axis),
+        lam a list of (mu, nu).  Returns the values in the order R, r, lam."""
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        kind = [0] * len(R) + [1] * len(r) + [2] * len(lam)
+        index = [3 * a + q for a, q in R] + [3 * i + q for i, q in r] + [mu * self.L + nu for mu, nu in lam]
+        kind = np.array(kind, dtype=np.int32)
+        index = np.array(index, dtype=np.int64)
+        out = np.zeros(len(kind))
+        if not lib().orc_elocal_fd_select(self._ps, _p(x), float(h), len(kind), _p(kind), _p(index), _p(out)):
+            raise ValueError("bad component")
+        return out
+
+    def lrdmc_hops(self, x, a, gamma=0.0):
+        """Hop ratios rho [6N], rates t [6N], Gamma and e_L of one configuration
+        (Sec. "Lattice regularized Monte Carlo"); hop k = 6 i + 2 d + s."""
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        rho, t = np.zeros(6 * self.N), np.zeros(6 * self.N)
+        G, e = C.c_double(), C.c_double()
+        if not lib().orc_lrdmc_hops(self._ps, _p(x), float(a), float(gamma), _p(rho), _p(t), C.addressof(G),
+                                    C.addressof(e)):
+            raise ValueError("singular geminal matrix")
+        return rho, t, G.value, e.value
+
+    def lrdmc_project(self, x, weight, seed=0, gen=0, a=0.2, gamma=0.0, tau=0.1, e_ref=0.0, max_hops=1 << 20,
+                      walker0=0, nthreads=0):
+        """One continuous-time projection of length tau per walker; x [W][N][3]
+        and weight [W] are updated in place.  Returns (e_L [W], hops [W], flags [W])."""
+        assert x.flags.c_contiguous and x.dtype == np.float64
+        assert weight.flags.c_contiguous and weight.dtype == np.float64
+        W = x.shape[0]
+        eL, hops, flags = np.zeros(W), np.zeros(W, dtype=np.int32), np.zeros(W, dtype=np.int32)
+        ok = lib().orc_lrdmc_project(self._ps, _p(x), W, int(walker0), int(seed), int(gen), float(a), float(gamma),
+                                     float(tau), float(e_ref), int(max_hops), _p(weight), _p(eL), _p(hops),
+                                     _p(flags), int(nthreads))
+        if not ok:
+            raise ValueError("singular geminal matrix")
+        return eL, hops, flags
+
+    def lrdmc(self, x, ngen, seed=0, a=0.2, gamma=0.0, tau=0.1, e_ref=0.0, max_hops=1 << 20, gen0=0,
+              branch=True, nthreads=0):
+        """ngen generations (projection, then reconfiguration); x [W][N][3] in
+        place.  Returns per-generation wbar, ebar [ngen], e_L, hops, parents,
+        weights [ngen][W] (weights before the reconfiguration)."""
+        W = x.shape[0]
+        out = {k: [] for k in ("wbar", "ebar", "eL", "hops", "parent", "weight", "flags")}
+        w = np.ones(W)
+        for gi in range(ngen):
+            g = gen0 + gi
+            eL, hops, flags = self.lrdmc_project(x, w, seed, g, a, gamma, tau, e_ref, max_hops, 0, nthreads)
+            out["eL"].append(eL)
+            out["hops"].append(hops)
+            out["flags"].append(flags)
+            out["weight"].append(w.copy())
+            if branch:
+                parent, wb, eb = lrdmc_branch(w, eL, seed, g)
+                x[:] = x[parent]
+                w = np.ones(W)
+            else:
+                parent = np.arange(W, dtype=np.int32)
+                wb, eb = w.mean(), float((w * eL).sum() / w.sum())
+            out["parent"].append(parent)
+            out["wbar"].append(wb)
+            out["ebar"].append(eb)
+        return {k: np.array(v) for k, v in out.items()}
 
     def guiding_R(self, x, theta=0.375):
         """R(x) = (S sum |G~^{-1}|^2)^-theta of one configuration (Eq. R_r)."""

@@ -1057,6 +1057,53 @@ double orc_elocal_dlambda_fd(const orc_system *s, const double *x, int mu, int n
   return (4.0 * D[1] - D[0]) / 3.0;
 }
 
+/* Selected components of the same central differences, one component per  */
+/* thread, each on its own copies of x, R and lambda (so that full-size      */
+/* systems can be checked at a few components): kind[c] = 0 for             */
+/* d e_L / d R (index[c] = 3 a + q), 1 for d e_L / d r (index[c] = 3 i + q), */
+/* 2 for d e_L / d lambda (index[c] = mu L + nu).  out[c] is the value      */
+/* orc_elocal_grad_fd or orc_elocal_dlambda_fd gives for that component     */
+/* (the same steps in the same order).  Returns 0 for a bad kind or index.  */
+int orc_elocal_fd_select(const orc_system *s, const double *x, double h, int n, const int *kind,
+                         const long long *index, double *out) {
+  const int N = s->n_up + s->n_dn, L = s->L;
+  for (int c = 0; c < n; ++c) {
+    const long long lim = kind[c] == 0 ? 3LL * s->n_atoms : kind[c] == 1 ? 3LL * N : (long long)L * L;
+    if (kind[c] < 0 || kind[c] > 2 || index[c] < 0 || index[c] >= lim) return 0;
+  }
+#pragma omp parallel for schedule(dynamic)
+  for (int c = 0; c < n; ++c) {
+    orc_system t = *s;
+    double *xx = (double *)malloc(sizeof(double) * 3 * N);
+    double *RR = (double *)malloc(sizeof(double) * 3 * s->n_atoms);
+    double *lam = kind[c] == 2 ? (double *)malloc(sizeof(double) * (size_t)L * L) : NULL;
+    memcpy(xx, x, sizeof(double) * 3 * N);
+    memcpy(RR, s->R, sizeof(double) * 3 * s->n_atoms);
+    t.R = RR;
+    if (lam) {
+      memcpy(lam, s->lam, sizeof(double) * (size_t)L * L);
+      t.lam = lam;
+    }
+    double *v = kind[c] == 0 ? RR : kind[c] == 1 ? xx : lam;
+    const double v0 = v[index[c]];
+    const double hs[2] = {h, 0.5 * h};
+    double D[2];
+    for (int k = 0; k < 2; ++k) {
+      v[index[c]] = v0 + hs[k];
+      const double ep = el_at(&t, xx);
+      v[index[c]] = v0 - hs[k];
+      const double em = el_at(&t, xx);
+      v[index[c]] = v0;
+      D[k] = (ep - em) / (2.0 * hs[k]);
+    }
+    out[c] = (4.0 * D[1] - D[0]) / 3.0;
+    free(xx);
+    free(RR);
+    free(lam);
+  }
+  return 1;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Error bar of the VMC mean from correlated samples by reblocking (Sec.    */
 /* VMC: blocks of growing size until the estimate of the error plateaus).   */
@@ -1250,4 +1297,190 @@ int orc_swct_derivs(const orc_system *s, const double *x, double h, double *dEL,
   }
   free(eR); free(er); free(lR); free(lr); free(om); free(dom);
   return ok;
+}
+
+/* ======================================================================== */
+/* Lattice-regularised diffusion Monte Carlo (Sec. "Lattice regularized     */
+/* Monte Carlo"), guiding function Psi_G = Psi_T, continuous time.          */
+/* ======================================================================== */
+/* Hops of one configuration.  Hop k = 6 i + 2 d + s moves electron i by     */
+/* +a (s = 0) or -a (s = 1) along axis d.  rho_k = Psi_G(x'_k) / Psi_G(x),    */
+/* from log|det G~|, its sign and J recomputed at x'_k (definition; 0 if     */
+/* G~ is singular there).  The discretised kinetic energy has the element    */
+/* -1/(2 a^2) for every hop; the fixed-node Hamiltonian keeps it where       */
+/* s_{x',x} = rho_k H_{x',x} < 0 (rho_k > 0) and multiplies it by -gamma     */
+/* where s_{x',x} > 0 (rho_k < 0, a hop across the node), moving (1 + gamma) */
+/* V_sf to the diagonal.  The importance-sampled Green's function then      */
+/* leaves x for x'_k with the rate                                           */
+/*   t_k = (rho_k > 0 ? rho_k : gamma |rho_k|) / (2 a^2),                    */
+/* Gamma = sum_k t_k (k = 0 .. 6N-1 in order).  With the regularised         */
+/* potential V^a (Eq. lrdmc_potential) sum_x' H^FN_{x',x} Psi_G(x')/Psi_G(x)  */
+/* is the continuous local energy e_L(x) for every gamma (the V_sf terms     */
+/* cancel), which is what weights the walker.                                */
+int orc_lrdmc_hops(const orc_system *s, const double *x, double a, double gamma, double *rho, double *t,
+                   double *Gamma, double *eL) {
+  const int N = s->n_up + s->n_dn;
+  double o0[4], o1[4], e[5];
+  if (!orc_logpsi(s, x, o0)) return 0;
+  double *xp = (double *)malloc(sizeof(double) * 3 * N);
+  const double c = 1.0 / (2.0 * a * a);
+  double G = 0.0;
+  for (int k = 0; k < 6 * N; ++k) {
+    const int i = k / 6, d = (k % 6) / 2, sg = k % 2;
+    memcpy(xp, x, sizeof(double) * 3 * N);
+    xp[3 * i + d] = sg ? x[3 * i + d] - a : x[3 * i + d] + a;
+    double r = 0.0;
+    if (orc_logpsi(s, xp, o1)) r = o1[1] * o0[1] * exp(o1[0] - o0[0]);
+    rho[k] = r;
+    t[k] = (r > 0.0 ? r : -gamma * r) * c;
+    G += t[k];
+  }
+  free(xp);
+  *Gamma = G;
+  orc_local_energy(s, x, e);
+  *eL = e[0];
+  return 1;
+}
+
+/* One projection of length tau for each of W walkers (continuous time): at  */
+/* x the walker waits tau_xi = -ln(1 - xi) / Gamma(x) and its log-weight     */
+/* falls by tau_xi (e_L(x) - e_ref); once the wait reaches the time left it  */
+/* falls by the time left times (e_L(x) - e_ref) instead and the projection  */
+/* ends; otherwise the walker hops to x'_k with probability t_k / Gamma.     */
+/* e_ref only shifts every log-weight by the same tau e_ref.  Hop h of       */
+/* walker w in generation g draws one Philox4x32-10 block, counter          */
+/* (w, g, h, 2) and the VMC key: xi = (x0 + 1/2) 2^-32, and hop k is the     */
+/* first whose running sum of t (k = 0, 1, ...) exceeds (x1 + 1/2) 2^-32     */
+/* Gamma (the last hop with t > 0 if rounding leaves none).  A walker that   */
+/* has made max_hops hops stays where it is for the rest of the time and    */
+/* gets flag bit 1; a singular G~ gives flag bit 2 and ends its projection.  */
+/* weight[w] *= exp(sum of its log-weight changes); eL_out[w] = e_L at the  */
+/* final configuration; hops_out[w] = hops made.                             */
+static void lrdmc_walker(const orc_system *s, double *x, uint32_t wid, uint64_t seed, uint32_t gen, double a,
+                         double gamma, double tau, double e_ref, int max_hops, double *weight, double *eL_out,
+                         int *hops_out, int *flags_out) {
+  const int N = s->n_up + s->n_dn;
+  double *rho = (double *)malloc(sizeof(double) * 6 * N), *t = (double *)malloc(sizeof(double) * 6 * N);
+  const uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+  double left = tau, lw = 0.0, Gamma = 0.0, eL = 0.0;
+  int h = 0, flags = 0;
+  for (;;) {
+    if (!orc_lrdmc_hops(s, x, a, gamma, rho, t, &Gamma, &eL)) {
+      flags |= 2;
+      break;
+    }
+    if (h >= max_hops) {
+      flags |= 1;
+      lw -= left * (eL - e_ref);
+      break;
+    }
+    const uint32_t ctr[4] = {wid, gen, (uint32_t)h, 2u};
+    uint32_t o[4];
+    orc_philox4x32_10(ctr, key, o);
+    const double xi = ((double)o[0] + 0.5) * 0x1p-32;
+    const double wait = Gamma > 0.0 ? -log(1.0 - xi) / Gamma : INFINITY;
+    if (wait >= left) {
+      lw -= left * (eL - e_ref);
+      break;
+    }
+    lw -= wait * (eL - e_ref);
+    left -= wait;
+    const double thr = ((double)o[1] + 0.5) * 0x1p-32 * Gamma;
+    double run = 0.0;
+    int k = -1;
+    for (int q = 0; q < 6 * N; ++q) {
+      run += t[q];
+      if (t[q] > 0.0) k = q;
+      if (run > thr) break;
+    }
+    const int i = k / 6, d = (k % 6) / 2;
+    x[3 * i + d] = (k % 2) ? x[3 * i + d] - a : x[3 * i + d] + a;
+    h++;
+  }
+  *weight *= exp(lw);
+  *eL_out = eL;
+  *hops_out = h;
+  *flags_out = flags;
+  free(rho);
+  free(t);
+}
+
+int orc_lrdmc_project(const orc_system *s, double *x, int W, long long walker0, uint64_t seed, long long gen,
+                      double a, double gamma, double tau, double e_ref, int max_hops, double *weight, double *eL_out,
+                      int *hops_out, int *flags_out, int nthreads) {
+  const int N = s->n_up + s->n_dn;
+  int bad = 0;
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+  (void)nthreads;
+#endif
+#pragma omp parallel for schedule(dynamic) reduction(+ : bad)
+  for (int w = 0; w < W; ++w) {
+    lrdmc_walker(s, x + (size_t)w * N * 3, (uint32_t)(walker0 + w), seed, (uint32_t)gen, a, gamma, tau, e_ref,
+                 max_hops, weight + w, eL_out + w, hops_out + w, flags_out + w);
+    if (flags_out[w] & 2) bad++;
+  }
+  return bad == 0;
+}
+
+/* Reconfiguration after a projection (Eqs. branching-1, branching-2): W new */
+/* walkers drawn from the old ones with probabilities w_a / sum_b w_b, by   */
+/* systematic resampling with one uniform per generation (Philox4x32-10,     */
+/* counter (0, g, 0, 3), the VMC key, z = (x0 + 1/2) 2^-32): new walker j    */
+/* takes the first old walker a whose running weight sum (a = 0, 1, ... in   */
+/* order) exceeds (j + z) sum w / W (the last walker with w > 0 if rounding  */
+/* leaves none).  wbar = sum w / W; ebar = sum w e_L / sum w (the mean local */
+/* energy before the reconfiguration); the new weights are all 1.            */
+void orc_lrdmc_branch(int W, uint64_t seed, long long gen, const double *w, const double *eL, int *parent,
+                      double *wbar, double *ebar) {
+  const uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+  const uint32_t ctr[4] = {0u, (uint32_t)gen, 0u, 3u};
+  uint32_t o[4];
+  if (W <= 0) return;
+  orc_philox4x32_10(ctr, key, o);
+  const double z = ((double)o[0] + 0.5) * 0x1p-32;
+  double S = 0.0, Se = 0.0;
+  int last = 0;
+  for (int b = 0; b < W; ++b) {
+    S += w[b];
+    Se += w[b] * eL[b];
+    if (w[b] > 0.0) last = b;
+  }
+  int b = 0;
+  double run = w[0];
+  for (int j = 0; j < W; ++j) {
+    const double thr = ((double)j + z) * S / W;
+    while (b < W && !(run > thr)) {
+      b++;
+      if (b < W) run += w[b];
+    }
+    parent[j] = b < W ? b : last;
+  }
+  *wbar = S / W;
+  *ebar = Se / S;
+}
+
+/* Energy with the correcting factor (Eq. many-walker-weight and the         */
+/* estimator after it): E = sum_{n=p}^{T-1} G_n ebar_n / sum_{n=p}^{T-1} G_n,  */
+/* G_n = prod_{j=1..p} wbar_{n-j}, the products taken as exponentials of     */
+/* sums of logarithms less their largest (the same ratio without overflow).  */
+double orc_lrdmc_energy(int T, const double *wbar, const double *ebar, int p) {
+  if (p < 0 || p >= T) return NAN;
+  double *lg = (double *)malloc(sizeof(double) * T);
+  double mx = -INFINITY;
+  for (int n = p; n < T; ++n) {
+    double l = 0.0;
+    for (int j = 1; j <= p; ++j) l += log(wbar[n - j]);
+    lg[n] = l;
+    if (l > mx) mx = l;
+  }
+  double num = 0.0, den = 0.0;
+  for (int n = p; n < T; ++n) {
+    const double g = exp(lg[n] - mx);
+    num += g * ebar[n];
+    den += g;
+  }
+  free(lg);
+  return num / den;
 }

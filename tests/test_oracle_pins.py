@@ -520,6 +520,24 @@ def test_elocal_grad_fd_translation_sum():
     assert np.allclose(dR.sum(0) + dr.sum(0), 0.0, atol=1e-8 * scale)
 
 
+def test_elocal_fd_select_equals_the_full_differences():
+    """The parallel selected-component differences (used at full size) give
+    exactly the components of the full nuclear, electronic and lambda
+    differences pinned above, including an unsymmetrised lambda entry; an
+    out-of-range component is refused."""
+    s = synth.small_random(n_atoms=3, n_up=3, n_dn=2, per_atom=20, seed=45, slater_fraction=0.2)
+    o = oracle.Oracle(s)
+    x = _rand_cfg(s, 46)
+    dR, dr = o.elocal_grad(x, h=1e-3)
+    Rc, rc, lc = [(0, 2), (2, 0), (1, 1)], [(4, 1), (0, 0)], [(3, 7), (7, 3)]
+    got = o.elocal_fd_select(x, R=Rc, r=rc, lam=lc, h=1e-3)
+    want = [dR[a, q] for a, q in Rc] + [dr[i, q] for i, q in rc] + \
+        [o.elocal_dlambda(x, mu, nu, h=1e-3) for mu, nu in lc]
+    assert np.array_equal(got, np.array(want))
+    with pytest.raises(ValueError):
+        o.elocal_fd_select(x, R=[(s.n_atoms, 0)])
+
+
 def test_agp_nonsymmetric_rank_n_lambda():
     """lambda = C D^T (non-symmetric, rank n): G~ = (Phi_up C)(Phi_dn D)^T, so
     det G~ = det(Phi_up C) det(Phi_dn D); a transposed lambda would give
