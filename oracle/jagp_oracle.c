@@ -1353,7 +1353,8 @@ int orc_lrdmc_hops(const orc_system *s, const double *x, double a, double gamma,
 /* first whose running sum of t (k = 0, 1, ...) exceeds (x1 + 1/2) 2^-32     */
 /* Gamma (the last hop with t > 0 if rounding leaves none).  A walker that   */
 /* has made max_hops hops stays where it is for the rest of the time and    */
-/* gets flag bit 1; a singular G~ gives flag bit 2 and ends its projection.  */
+/* gets flag bit 1; a singular G~ gives flag bit 2, a non-finite Gamma or   */
+/* e_L flag bit 4, and either ends its projection.                           */
 /* weight[w] *= exp(sum of its log-weight changes); eL_out[w] = e_L at the  */
 /* final configuration; hops_out[w] = hops made.                             */
 static void lrdmc_walker(const orc_system *s, double *x, uint32_t wid, uint64_t seed, uint32_t gen, double a,
@@ -1367,6 +1368,10 @@ static void lrdmc_walker(const orc_system *s, double *x, uint32_t wid, uint64_t 
   for (;;) {
     if (!orc_lrdmc_hops(s, x, a, gamma, rho, t, &Gamma, &eL)) {
       flags |= 2;
+      break;
+    }
+    if (!isfinite(Gamma) || !isfinite(eL)) {
+      flags |= 4;
       break;
     }
     if (h >= max_hops) {
