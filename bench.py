@@ -15,7 +15,7 @@ steps.  Under torchrun each rank runs its own 4096 walkers (weak scaling, no
 data-path collective; a barrier and a max-reduction of the timings only).
 
 Prints one JSON line (rank 0).  Each timed region is an NVTX push/pop range
-(fp64, mixed, fp64tc, batched, forces, large, large_forces), so that a profiler
+(fp64, mixed, fp64tc, batched, forces, large, large_forces, sr, lrdmc), so that a profiler
 can keep to it (ncu --nvtx --nvtx-include "batched/").
 """
 from __future__ import annotations
@@ -74,8 +74,8 @@ def _bf16_sustained_peak():
 BF16_SUSTAINED_TFLOPS, BF16_PEAK_SOURCE = _bf16_sustained_peak()
 # BF16 slice-pair products per element of the mixed path's lambda products:
 # both the up-spin rows (phi^T lambda) and the down-spin rows (lambda phi) take
-# all 15 pairs of the five-slice operands (two-float results)
-PAIRS_UP, PAIRS_DN = 15, 15
+# all 21 pairs of the six-slice operands (two-float results)
+PAIRS_UP, PAIRS_DN = 21, 21
 NO_AUTOTUNE = False  # --no-autotune: time the shape heuristics' tiles
 
 
@@ -576,9 +576,9 @@ def batch_bench(pg, torch, dist, args, dev, rank, ws, precision=None, sweeps=Non
     achieved = flops / (lam_ms / 1e3) / 1e12 if lam_ms > 0 else None
     if mixed:
         roof = tensor_roofline("k_umma_gemm (tcgen05, BF16 fixed-point slices), all member systems", achieved,
-                               achieved * 15 if achieved else None, lam_n, lam_ms, 0.0,
+                               achieved * PAIRS_UP if achieved else None, lam_n, lam_ms, 0.0,
                                "2 L^2 flop per accepted orbital row, summed over the systems of one sweep; issued: "
-                               "15 BF16 slice-pair products per flop (before padding K to 64)")
+                               "%d BF16 slice-pair products per flop (before padding K to 64)" % PAIRS_UP)
     else:
         roof = {"kernel": "k_lambda_rows, all member systems", "bound": "alu", "achieved": achieved,
                 "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS if achieved else None,
@@ -643,8 +643,8 @@ def large_bench(pg, torch, dist, args, dev, rank, ws, local):
             "roofline": tensor_roofline("k_umma_gemm (tcgen05, BF16 fixed-point slices)",
                                         2.0 * L * L * rr["accepted"] / secs / 1e12 if secs > 0 else None, tc,
                                         rr["prof_n"], rr["prof_ms"], rr["ms"],
-                                        "2 L^2 flop per accepted orbital row (the lambda product); issued: 15 BF16 "
-                                        "slice-pair products per flop"),
+                                        "2 L^2 flop per accepted orbital row (the lambda product); issued: %d BF16 "
+                                        "slice-pair products per flop" % PAIRS_UP),
             "forces": forces}
 
 
@@ -806,6 +806,87 @@ def sr_bench(pg, torch, dist, args, dev, rank, ws, local):
                                     "unit": "TFLOP/s",
                                     "frac": dflops / (d_ms / steps / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
                                     "work": "2 (N_up N_dn L + N_up L^2) flop per walker"}}
+
+
+LRDMC_WORKLOAD = ("lattice-regularised DMC on the C2 workload (16 He, N=32, L=320, 4096 walkers/GPU, FP64), "
+                  "continuous time, fixed node: lattice a = 0.2 bohr, gamma = 0, projection tau = 0.01 /Ha per "
+                  "generation, reconfiguration after each generation")
+
+
+def lrdmc_bench(pg, torch, dist, args, dev, rank, ws, local):
+    """LRDMC hops/s: one step = one generation (a continuous-time projection
+    of length tau, every walker hopping until its time is spent, then the
+    reconfiguration).  Each round of hops recomputes the moved rows' lambda
+    products, G~^{-1}, the kinetic vectors M and e_L of every walker, and the
+    6N hop ratios of every walker still moving."""
+    import numpy as np
+    import synth
+    sysm = synth.config2()
+    W = args.walkers
+    a, gamma, tau = 0.2, 0.0, 0.01
+    x0 = np.ascontiguousarray(synth.init_walkers(sysm, W * ws, seed=0)[rank * W:(rank + 1) * W])
+    g = pg.JAGP(sysm, W, seed=0)
+    r = g.positions(x0)
+    g.eval(r)
+    g.sweep(r, 4, walker0=rank * W, energies=False)
+    e_ref = float(g.local_energy(r).mean().item())
+    work = torch.empty(pg.jagp_lrdmc_workspace_bytes(g.h, W), dtype=torch.uint8, device=dev)
+    w = torch.ones(W, dtype=torch.float64, device=dev)
+    eL = torch.empty(W, dtype=torch.float64, device=dev)
+    hops = torch.empty(W, dtype=torch.int32, device=dev)
+    flags = torch.empty(W, dtype=torch.int32, device=dev)
+    stats = torch.empty(2, dtype=torch.float64, device=dev)
+    parent = torch.empty(W, dtype=torch.int32, device=dev)
+
+    def generation(gen):
+        pg.jagp_lrdmc_project(g.h, r, g.state, W, work, w, gen, a, gamma, tau, e_ref, 1 << 20, rank * W, eL, hops,
+                              flags)
+        h = hops.sum()
+        hm = hops.max()
+        pg.jagp_lrdmc_branch(g.h, r, W, work, w, eL, gen, parent, stats)
+        return h, hm
+
+    for gen in range(args.lrdmc_warmup):
+        generation(gen)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n0 = pg.jagp_launch_count(g.h)
+    tot_h, rounds, ebar = 0, 0, []
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.nvtx.range_push("lrdmc")
+    ev0.record()
+    for k in range(args.lrdmc_gens):
+        h, hm = generation(args.lrdmc_warmup + k)
+        tot_h += int(h.item())
+        rounds += int(hm.item()) + 1
+        ebar.append(float(stats[1].item()))
+    ev1.record()
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    ms = ev0.elapsed_time(ev1)
+    launches = pg.jagp_launch_count(g.h) - n0
+    t = torch.tensor([ms, tot_h], dtype=torch.float64, device=dev)
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t[0].item())
+    g.close()
+    K = args.lrdmc_gens
+    n, nd, N, L = sysm.n_up, sysm.n_dn, sysm.N, sysm.L
+    # dense FP64 work of one round per walker: the refresh product G~ = Phi_up Bt^T
+    # (2 n^2 L), the kinetic vectors M (2 N n L) and the 6N hop-ratio dots (12 N L),
+    # plus 2 L^2 per moved walker (its lambda row)
+    flops = rounds * W * (2.0 * n * n * L + 2.0 * N * n * L + 12.0 * N * L) + tot_h * 2.0 * L * L
+    tf = flops / (ms / 1e3) / 1e12
+    return {"metric": "LRDMC walker hops/s", "value": tot_h * ws / (ms / 1e3), "unit": "walker hops/s",
+            "ms_per_generation": ms / K, "generations": K, "warmup": args.lrdmc_warmup,
+            "hops_per_walker_per_generation": tot_h / (W * K), "rounds_per_generation": rounds / K,
+            "ebar": ebar, "e_ref": e_ref, "gpu_launches": launches, "dtype": "f64", "workload": LRDMC_WORKLOAD,
+            "roofline": {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": tf / FP64_PEAK_TFLOPS,
+                         "work": "per round and walker 2 N_up^2 L (G~) + 2 N N_up L (M) + 12 N L (hop ratios), "
+                                 "plus 2 L^2 per hop (lambda row), over the whole generation",
+                         "peak_source": "nominal FP64 of GB300 (152 SM x 2 DFMA/clk x 2.07 GHz)"}}
 
 
 C1_WORKLOAD = ("plain FP64 VMC, 4 H atoms in a 3 bohr cube, N=4 (2 up, 2 down), 6 s+p Gaussians/atom (L=24), "
@@ -973,6 +1054,7 @@ def run_gpu(args):
     large = None if args.no_large else large_bench(pg, torch, dist, args, dev, rank, ws, local)
     pipeline = None if args.no_large else pipeline_bench(pg, torch, dist, args, dev, rank, ws, local)
     sr = None if args.no_sr else sr_bench(pg, torch, dist, args, dev, rank, ws, local)
+    lrdmc = None if args.no_lrdmc else lrdmc_bench(pg, torch, dist, args, dev, rank, ws, local)
     reweighted = None if args.no_forces else reweighted_forces_bench(pg, torch, dist, args, dev, rank, ws, local)
     c1 = None if args.no_c1 else c1_bench(pg, torch, dist, args, dev, rank, ws, local)
 
@@ -999,7 +1081,7 @@ def run_gpu(args):
             d["roofline"] = tensor_roofline("k_umma_gemm (tcgen05, BF16 fixed-point slices)", achieved, tc,
                                             rr["prof_n"], rr["prof_ms"], rr["ms"],
                                             "2 L^2 flop per accepted orbital row (the lambda product); issued: "
-                                            "15 BF16 slice-pair products per flop on K padded to 64")
+                                            "%d BF16 slice-pair products per flop on K padded to 64" % PAIRS_UP)
         else:
             traffic_per_row, _ = profiled_traffic(kernel_source_hash())
             rows_per_launch = rr["accepted"] / max(rr["prof_n"], 1)
@@ -1061,6 +1143,8 @@ def run_gpu(args):
         out["pipeline"] = pipeline
     if sr is not None:
         out["sr"] = sr
+    if lrdmc is not None:
+        out["lrdmc"] = lrdmc
     if reweighted is not None:
         out["forces_reweighted"] = reweighted
     if c1 is not None:
@@ -1113,6 +1197,9 @@ def main():
     ap.add_argument("--sr-steps", type=int, default=3)
     ap.add_argument("--sr-iters", type=int, default=50)
     ap.add_argument("--no-c1", action="store_true", help="skip the 4-electron latency-bound line")
+    ap.add_argument("--no-lrdmc", action="store_true", help="skip the lattice-regularised DMC measurement")
+    ap.add_argument("--lrdmc-gens", type=int, default=3)
+    ap.add_argument("--lrdmc-warmup", type=int, default=1)
     ap.add_argument("--c1-sweeps", type=int, default=200)
     ap.add_argument("--large-only", action="store_true", help="run only the 512-electron measurement")
     ap.add_argument("--large-tuning", default=None,

@@ -298,6 +298,58 @@ jagp_status_t jagp_set_guiding(jagp_handle_t h, double theta, double eps);
 jagp_status_t jagp_force_seeds(const double *d_eL, const double *d_weight, int M, double *d_seed_logpsi,
                                double *d_seed_eL, double *d_mean, void *stream);
 
+/* ------------------------------------------------------------------------ */
+/* Lattice-regularised diffusion Monte Carlo (Sec. "Lattice regularized     */
+/* Monte Carlo"), continuous time, fixed node, guiding function = Psi_T.    */
+/* ------------------------------------------------------------------------ */
+/* One projection of imaginary-time length tau for W walkers at d_r [W][N][3]
+ * (device, updated in place).  Hop k = 6 i + 2 d + s moves electron i by +a
+ * (s = 0) or -a (s = 1) along axis d; rho_k = Psi(x') / Psi(x) and the
+ * fixed-node rate t_k = (rho_k > 0 ? rho_k : gamma |rho_k|) / (2 a^2),
+ * Gamma = sum_k t_k.  A walker at x waits tau_xi = -ln(1 - xi) / Gamma and
+ * its log-weight falls by tau_xi (e_L(x) - e_ref); when the wait reaches the
+ * time left it falls by the time left times (e_L(x) - e_ref) and the walker
+ * stops, else it hops to the first k whose running sum of t exceeds u Gamma.
+ * Hop h of walker walker0 + w in generation `generation` draws Philox4x32-10
+ * (counter (walker0 + w, generation, h, 2), the handle's seed as key):
+ * xi = (x0 + 1/2) 2^-32, u = (x1 + 1/2) 2^-32.  A walker stops after
+ * max_hops hops (flag bit 1); one whose G~ is singular or positions are not
+ * finite takes no part (flag bit 2); a non-finite rate sum or e_L ends the
+ * walker's projection (flag bit 4).
+ * d_weight [W] in/out: multiplied by exp(log-weight change).  d_eL [W]
+ * (or NULL): e_L at the final configuration.  d_hops, d_flags [W] (or NULL).
+ * d_state is evaluated at the start (jagp_eval) and is current at the end.
+ * d_work: jagp_lrdmc_workspace_bytes(h, W) bytes, 256-byte aligned, device.
+ * Synchronises the stream once per round of hops (every walker still moving
+ * takes one hop per round).  a > 0, gamma >= 0, tau >= 0, max_hops >= 0.
+ * Errors: INVALID_ARG; UNSUPPORTED for a mixed-precision handle or the
+ * three-body Jastrow. */
+size_t jagp_lrdmc_workspace_bytes(jagp_handle_t h, int W);
+jagp_status_t jagp_lrdmc_project(jagp_handle_t h, double *d_r, void *d_state, int W, uint64_t walker0,
+                                 uint64_t generation, double a, double gamma, double tau, double e_ref, int max_hops,
+                                 double *d_weight, double *d_eL, int *d_hops, int *d_flags, void *d_work,
+                                 void *stream);
+
+/* Reconfiguration after a projection (Eqs. branching-1, branching-2): W new
+ * walkers drawn from the old ones with probability w_a / sum w by systematic
+ * resampling with one uniform z per generation (Philox4x32-10, counter
+ * (0, generation, 0, 3), z = (x0 + 1/2) 2^-32): new walker j copies the first
+ * old walker whose running weight sum exceeds (j + z) sum w / W.  d_r [W][N][3]
+ * is replaced by the new population, d_weight [W] reset to 1, d_parent [W]
+ * (or NULL) receives the old indices, d_stats [2] = (wbar = sum w / W,
+ * ebar = sum w e_L / sum w) from d_eL [W].  The walkers' state must be
+ * re-evaluated (jagp_lrdmc_project does so).  d_work as for
+ * jagp_lrdmc_project.  Device pointers.  Errors: INVALID_ARG. */
+jagp_status_t jagp_lrdmc_branch(jagp_handle_t h, double *d_r, int W, uint64_t generation, double *d_weight,
+                                const double *d_eL, int *d_parent, double *d_stats, void *d_work, void *stream);
+
+/* Energy with the correcting factor (Eq. many-walker-weight and the estimator
+ * after it) from T generations' d_wbar, d_ebar [T]:
+ *   E = sum_{n=p}^{T-1} G_n ebar_n / sum_{n=p}^{T-1} G_n,
+ *   G_n = prod_{j=1..p} wbar_{n-j}  (formed as exponentials of log sums).
+ * d_E [1] device.  0 <= p < T.  Errors: INVALID_ARG. */
+jagp_status_t jagp_lrdmc_energy(const double *d_wbar, const double *d_ebar, int T, int p, double *d_E, void *stream);
+
 /* Copy per-walker bookkeeping to device arrays (each may be NULL):
  * log|Psi|, sign, accepted moves since jagp_eval, last drift, status bits. */
 jagp_status_t jagp_walker_info(jagp_handle_t h, const void *d_state, int W, double *d_logabs,
@@ -340,9 +392,9 @@ jagp_status_t jagp_autotune(jagp_handle_t h, void *d_state, int W, jagp_tuning_t
  * CUDA call; ms is ignored.  tile_proposals / tile_refresh: -1 (the shape
  * heuristics), 0, 32 or 64, and 16 for tile_refresh in the mixed path with
  * N_up <= 16.  umma_*: 0 without tensor-core lambda products (FP64 without
- * fp64_tensor_cores); else bn 0 (heuristic) or a multiple of 16 up to 128 (A_up
- * rows) / 96 (Bt rows) in the mixed path, 64 in the FP64 one, and stages -1
- * (chunk-major, only where two such stages fit in shared memory), 0 or 2..6.
+ * fp64_tensor_cores); else bn 0 (heuristic) or a multiple of 16 up to 64, and
+ * stages -1 (chunk-major, only where two such stages fit in shared memory:
+ * bn = 16 with the mixed path's six slices), 0 or 2..6.
  * Every choice changes the tiling only, so results stay as without tuning.
  * Returns JAGP_ERR_INVALID_ARG (and keeps the earlier choices) on any other value. */
 jagp_status_t jagp_set_tuning(jagp_handle_t h, const jagp_tuning_t *t);
@@ -355,14 +407,14 @@ jagp_status_t jagp_set_tuning(jagp_handle_t h, const jagp_tuning_t *t);
  *     C[rows[m]][n] = sum_{p < npairs} sum_{k < Kp} A[m][pair_a[p] Kp + k] * B[n][pair_b[p] Kp + k]
  *   fixed-point mode (both exponent arrays given): the terms are exact 8-bit
  *     integer slices, a = 2^(ea[m] - 7) sum_t A_t / 256^t (likewise b with
- *     eb[n]), pairs with equal pair_a + pair_b (<= 4) share an exactly summed
+ *     eb[n]), pairs with equal pair_a + pair_b (<= 5) share an exactly summed
  *     accumulator S_d, and C = 2^(ea + eb - 14) sum_d S_d / 256^d.
- * d_A: BF16 bits [M][a_terms Kp], d_B: BF16 bits [N][b_terms Kp] (up to five
+ * d_A: BF16 bits [M][a_terms Kp], d_B: BF16 bits [N][b_terms Kp] (up to six
  * terms per row side by side; Kp % 64 == 0; 16-byte aligned bases); d_C: FP32
  * with row pitch ldc >= N; d_rows: [M] destination rows or NULL (identity);
  * d_count: device int live row count (<= M) or NULL (= M); d_row_exp [M],
  * d_col_exp [N]: device ints or NULL.  h_pair_a/h_pair_b: host arrays of
- * npairs (1..16) term indices.  *d_err (device int) is set non-zero if a
+ * npairs (1..21) term indices.  *d_err (device int) is set non-zero if a
  * pipeline wait timed out.  Errors: INVALID_ARG for shapes, alignment or term
  * indices. */
 jagp_status_t jagp_gemm_bf16x(const uint16_t *d_A, int M, int a_terms, const uint16_t *d_B, int N, int b_terms,

@@ -124,6 +124,14 @@ def lib():
         L.jagp_reblock_levels.restype = i
         L.jagp_reblock.argtypes = [vp, i, i, vp, vp, vp, vp]
         L.jagp_reblock.restype = i
+        L.jagp_lrdmc_workspace_bytes.argtypes = [vp, i]
+        L.jagp_lrdmc_workspace_bytes.restype = C.c_size_t
+        L.jagp_lrdmc_project.argtypes = [vp, vp, vp, i, u64, u64, d, d, d, d, i, vp, vp, vp, vp, vp, vp]
+        L.jagp_lrdmc_project.restype = i
+        L.jagp_lrdmc_branch.argtypes = [vp, vp, i, u64, vp, vp, vp, vp, vp, vp]
+        L.jagp_lrdmc_branch.restype = i
+        L.jagp_lrdmc_energy.argtypes = [vp, vp, i, i, vp, vp]
+        L.jagp_lrdmc_energy.restype = i
         L.jagp_last_error.argtypes = [vp, C.c_char_p, C.c_size_t]
         L.jagp_last_error.restype = i
         L.jagp_status_string.argtypes = [i]
@@ -363,6 +371,39 @@ def jagp_reblock(eL, work=None, levels=None, stats=None, stream=None):
     return levels[:nlev], stats
 
 
+def jagp_lrdmc_workspace_bytes(h, W) -> int:
+    return int(lib().jagp_lrdmc_workspace_bytes(h, int(W)))
+
+
+def jagp_lrdmc_project(h, r, state, W, work, weight, generation=0, a=0.2, gamma=0.0, tau=0.1, e_ref=0.0,
+                       max_hops=1 << 20, walker0=0, eL=None, hops=None, flags=None, stream=None):
+    """One continuous-time LRDMC projection of length tau (see include/jagp.h);
+    r [W][N][3] and weight [W] (device FP64) are updated in place."""
+    _check(lib().jagp_lrdmc_project(h, _ptr(r), _ptr(state), int(W), int(walker0), int(generation), float(a),
+                                    float(gamma), float(tau), float(e_ref), int(max_hops), _ptr(weight), _ptr(eL),
+                                    _ptr(hops), _ptr(flags), _ptr(work), _stream(stream)), "jagp_lrdmc_project", h)
+
+
+def jagp_lrdmc_branch(h, r, W, work, weight, eL, generation=0, parent=None, stats=None, stream=None):
+    """Reconfiguration after a projection: r replaced by the new population,
+    weight reset to 1; returns (parent [W], stats [2] = (wbar, ebar)) device tensors."""
+    import torch
+    parent = torch.empty(W, dtype=torch.int32, device=r.device) if parent is None else parent
+    stats = torch.empty(2, dtype=torch.float64, device=r.device) if stats is None else stats
+    _check(lib().jagp_lrdmc_branch(h, _ptr(r), int(W), int(generation), _ptr(weight), _ptr(eL.contiguous()),
+                                   _ptr(parent), _ptr(stats), _ptr(work), _stream(stream)), "jagp_lrdmc_branch", h)
+    return parent, stats
+
+
+def jagp_lrdmc_energy(wbar, ebar, p, stream=None):
+    """LRDMC energy with the correcting factor of p generations (device tensor [1])."""
+    import torch
+    E = torch.empty(1, dtype=torch.float64, device=wbar.device)
+    _check(lib().jagp_lrdmc_energy(_ptr(wbar.contiguous()), _ptr(ebar.contiguous()), int(wbar.shape[0]), int(p),
+                                   _ptr(E), _stream(stream)), "jagp_lrdmc_energy")
+    return E
+
+
 def jagp_walker_info(h, state, W, logabs=None, sign=None, naccept=None, drift=None, status=None, stream=None):
     _check(lib().jagp_walker_info(h, _ptr(state), int(W), _ptr(logabs), _ptr(sign), _ptr(naccept), _ptr(drift),
                                   _ptr(status), _stream(stream)), "jagp_walker_info", h)
@@ -525,6 +566,33 @@ class JAGP:
         work = torch.empty(jagp_logpsi_derivs_workspace_bytes(self.h, W), dtype=torch.uint8, device=self.device)
         jagp_logpsi_derivs(self.h, r, self.state, W, work, O)
         return O
+
+    def lrdmc(self, r, ngen, a=0.2, gamma=0.0, tau=0.1, e_ref=0.0, max_hops=1 << 20, gen0=0, walker0=0):
+        """ngen LRDMC generations (projection, then reconfiguration) on r in
+        place (Sec. "Lattice regularized Monte Carlo").  Returns a dict of
+        device tensors: wbar, ebar [ngen]; eL, hops, flags, parent and the
+        weights before each reconfiguration, weight [ngen][W]."""
+        import torch
+        W = r.shape[0]
+        dev = dict(device=self.device)
+        work = torch.empty(jagp_lrdmc_workspace_bytes(self.h, W), dtype=torch.uint8, **dev)
+        w = torch.ones(W, dtype=torch.float64, **dev)
+        out = {"wbar": torch.empty(ngen, dtype=torch.float64, **dev),
+               "ebar": torch.empty(ngen, dtype=torch.float64, **dev),
+               "eL": torch.empty((ngen, W), dtype=torch.float64, **dev),
+               "weight": torch.empty((ngen, W), dtype=torch.float64, **dev),
+               "hops": torch.empty((ngen, W), dtype=torch.int32, **dev),
+               "flags": torch.empty((ngen, W), dtype=torch.int32, **dev),
+               "parent": torch.empty((ngen, W), dtype=torch.int32, **dev)}
+        stats = torch.empty(2, dtype=torch.float64, **dev)
+        for t in range(ngen):
+            jagp_lrdmc_project(self.h, r, self.state, W, work, w, gen0 + t, a, gamma, tau, e_ref, max_hops, walker0,
+                               out["eL"][t], out["hops"][t], out["flags"][t])
+            out["weight"][t].copy_(w)
+            jagp_lrdmc_branch(self.h, r, W, work, w, out["eL"][t], gen0 + t, out["parent"][t], stats)
+            out["wbar"][t] = stats[0]
+            out["ebar"][t] = stats[1]
+        return out
 
     def grad(self, r, seed_logpsi=None, seed_eL=None, want_lambda=True):
         """Vector-Jacobian products of (log|Psi|, e_L) at the current state (see

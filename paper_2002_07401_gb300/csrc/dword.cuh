@@ -85,13 +85,27 @@ __device__ __forceinline__ fdw dw_recip(fdw x) {
   return fast_two_sum(y, __fmul_rn(y, e));
 }
 
-// e^x for x <= 0 as a double-word, relative error ~1e-9:
+// 1/k! as a double-word (the FP32 rounding and the remainder, both formed at
+// compile time)
+struct DwConst {
+  float hi, lo;
+};
+constexpr DwConst dw_inv_fact(int k) {
+  double f = 1.0;
+  for (int i = 2; i <= k; ++i) f *= i;
+  const double v = 1.0 / f;
+  const float h = static_cast<float>(v);
+  return {h, static_cast<float>(v - static_cast<double>(h))};
+}
+
+// e^x for x <= 0 as a double-word, relative error a few units of 2^-46:
 // Cody-Waite reduction x = k ln2 + r, |r| <= ln2/2, with ln2 split into three
 // FP32 parts (the first with 16 significant bits, so that k * part1 and the
-// first subtraction are exact for |k| <= 150); then the Taylor series
-// e^r = 1 + r + r^2/2 + r^3 q(r), q(r) = sum_{n=3..8} r^(n-3)/n!, the first
-// three terms in double-word, the tail (< 0.0073) in FP32; the scaling by 2^k
-// is exact.  Arguments below -104 (where e^x is below the FP32 range) give 0.
+// first subtraction are exact for |k| <= 150); then the Taylor series of e^r
+// by Horner's rule in double-word arithmetic through r^6/6!, the terms
+// r^7/7! .. r^12/12! (together below 1.2e-7) in FP32, the truncation after
+// r^12/12! below 3e-16; the scaling by 2^k is exact.  Arguments below -104
+// (where e^x is below the FP32 range) give 0.
 __device__ __forceinline__ fdw dw_exp_neg(fdw x) {
   if (!(x.hi > -104.0f)) return {x.hi != x.hi ? x.hi : 0.0f, 0.0f};
   const float kLn2a = 0.693145751953125f;        // 16 significant bits
@@ -102,25 +116,28 @@ __device__ __forceinline__ fdw dw_exp_neg(fdw x) {
   r = dw_add(r, dw_neg(two_prod(k, kLn2b)));
   r = dw_add_f(r, __fmul_rn(-k, kLn2c));
   const float rh = r.hi;
-  float q = 1.0f / 40320.0f;
+  // FP32 tail: sum_{n=7..12} r^(n-7) / n!
+  float q = 1.0f / 479001600.0f;
+  q = __fmaf_rn(q, rh, 1.0f / 39916800.0f);
+  q = __fmaf_rn(q, rh, 1.0f / 3628800.0f);
+  q = __fmaf_rn(q, rh, 1.0f / 362880.0f);
+  q = __fmaf_rn(q, rh, 1.0f / 40320.0f);
   q = __fmaf_rn(q, rh, 1.0f / 5040.0f);
-  q = __fmaf_rn(q, rh, 1.0f / 720.0f);
-  q = __fmaf_rn(q, rh, 1.0f / 120.0f);
-  q = __fmaf_rn(q, rh, 1.0f / 24.0f);
-  q = __fmaf_rn(q, rh, 1.0f / 6.0f);
-  const float tail = __fmul_rn(q, __fmul_rn(__fmul_rn(rh, rh), rh));
-  fdw h = dw_mul(r, r);
-  h.hi = __fmul_rn(h.hi, 0.5f);
-  h.lo = __fmul_rn(h.lo, 0.5f);
-  fdw e = dw_add(r, h);
-  e = dw_add_f(e, tail);
-  e = dw_add_f(e, 1.0f);
+  // Horner in double-word: p = 1/6! + r q, then p = 1/n! + r p for n = 5 .. 0
+  constexpr DwConst c6 = dw_inv_fact(6), c5 = dw_inv_fact(5), c4 = dw_inv_fact(4), c3 = dw_inv_fact(3);
+  fdw p = dw_add(fdw{c6.hi, c6.lo}, dw_mul_f(r, q));
+  p = dw_add(fdw{c5.hi, c5.lo}, dw_mul(r, p));
+  p = dw_add(fdw{c4.hi, c4.lo}, dw_mul(r, p));
+  p = dw_add(fdw{c3.hi, c3.lo}, dw_mul(r, p));
+  p = dw_add_f(dw_mul(r, p), 0.5f);
+  p = dw_add_f(dw_mul(r, p), 1.0f);
+  p = dw_add_f(dw_mul(r, p), 1.0f);
   const int ki = static_cast<int>(k);
   if (ki >= -126) {
-    const float p = __int_as_float((127 + ki) << 23);
-    return {__fmul_rn(e.hi, p), __fmul_rn(e.lo, p)};
+    const float sc = __int_as_float((127 + ki) << 23);
+    return {__fmul_rn(p.hi, sc), __fmul_rn(p.lo, sc)};
   }
-  return {ldexpf(e.hi, ki), ldexpf(e.lo, ki)};
+  return {ldexpf(p.hi, ki), ldexpf(p.lo, ki)};
 }
 
 }  // namespace jagp

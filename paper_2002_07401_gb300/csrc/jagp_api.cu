@@ -75,13 +75,14 @@ Layout layout_of(const jagp_ctx *h, int W) {
                      h->ds.use_j3 ? (size_t)h->ds.LJ : 0);
 }
 
-// the fifteen slice pairs (a, b) with a + b <= 4 of the five-slice fixed-point
-// operands (each row kept to 2^-39 of its largest magnitude).  Both lambda
-// products take all fifteen: the rows lambda phi (Bt) enter G~ and the up
-// electrons' M vectors, the rows phi^T lambda (A_up) the down electrons' M
-// vectors, all as two-float numbers.
-const int kPairA[kFixedPairs] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3, 0, 1, 2, 3, 4};
-const int kPairB[kFixedPairs] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0, 4, 3, 2, 1, 0};
+// the twenty-one slice pairs (a, b) with a + b <= 5 of the six-slice
+// fixed-point operands (each row kept to 2^-47 of its largest magnitude, about
+// the precision of its two-float values).  Both lambda products take all of
+// them: the rows lambda phi (Bt) enter G~ and the up electrons' M vectors, the
+// rows phi^T lambda (A_up) the down electrons' M vectors, all as two-float
+// numbers; the kinetic term amplifies their relative error by about cond(G~).
+const int kPairA[kFixedPairs] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3, 0, 1, 2, 3, 4, 0, 1, 2, 3, 4, 5};
+const int kPairB[kFixedPairs] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0, 4, 3, 2, 1, 0, 5, 4, 3, 2, 1, 0};
 
 // all slice pairs (a, b) with a + b < nsl, ordered by a + b, then a
 int slice_pairs(int nsl, int *pa, int *pb) {
@@ -212,7 +213,7 @@ double *j3_vectors(const jagp_ctx *h, const Layout &L, void *state) {
 // the local-energy sequence on a current state
 // Mixed path: the M vectors of the kinetic energy as exact fixed-point
 // tensor-core products of the FP64 inverse of the last refresh with the
-// two-float tables (five 8-bit slices per element, fifteen slice pairs, a
+// two-float tables (six 8-bit slices per element, twenty-one slice pairs, a
 // two-float result M + M_lo; every accumulator sum exact for N_up <= 256 but
 // the last, whose rounding lies below 2^-55 of the leading term):
 //   up:   M[i][mu]        = sum_j Bt[j][mu] Ginv[j][i]    (columns of Bt against columns of G~^{-1})
@@ -295,7 +296,7 @@ jagp_status_t run_refresh(jagp_ctx *h, const double *r, void *state, int W, int 
   double *gm = refresh_g(L, state);
   if (tc_refresh(h)) {
     // G~ = (Phi_up + lo)(Bt + lo)^T per walker on the tensor cores: both tables
-    // cut into five fixed-point slices, fifteen pairs, FP64 epilogue
+    // cut into six fixed-point slices, twenty-one pairs, FP64 epilogue
     int *rows = at<int>(state, L.grows);
     uint16_t *pa = at<uint16_t>(state, L.gpack_a), *pb = at<uint16_t>(state, L.gpack_b);
     int *ea = at<int>(state, L.gexp_a), *eb = at<int>(state, L.gexp_b);
@@ -931,7 +932,7 @@ jagp_status_t tune_products(jagp_ctx *h, void *state, int W, cudaStream_t st, ja
   out->ms[1] = best;
   if (!h->tc_lambda) return JAGP_OK;
   // tensor-core lambda products of half the orbital rows (the accepted rows of
-  // a half-sweep at ~50% acceptance): mixed A_up (ten pairs) and Bt (fifteen),
+  // a half-sweep at ~50% acceptance): mixed A_up and Bt (twenty-one pairs each),
   // or the FP64-equivalent products (all pairs of 7 or 8 slices, FP64 result)
   const bool f64 = !std::is_same<T, float>::value;
   uint16_t *pack = at<uint16_t>(state, L.pack);
@@ -941,7 +942,7 @@ jagp_status_t tune_products(jagp_ctx *h, void *state, int W, cudaStream_t st, ja
   const int np64 = slice_pairs(h->tc_slices, pa64, pb64);
   for (int side = 0; side < 2; ++side) {
     const bool left = side == 0;
-    // tile widths; 16 lets four CTAs share an SM's tensor memory (5 x 16 columns each)
+    // tile widths; 16 lets several CTAs share an SM's tensor memory (6 x 16 columns each)
     const int cands[7] = {16, 32, 48, 64, 80, 96, 128};
     // stages: as many as fit (one CTA per SM), three or two (several CTAs per SM),
     // or chunk-major (-1: every slice of a K chunk per stage, each loaded once
@@ -949,7 +950,7 @@ jagp_status_t tune_products(jagp_ctx *h, void *state, int W, cudaStream_t st, ja
     const int stages[4] = {0, 3, 2, -1};
     const int npairs = f64 ? np64 : kFixedPairs;
     const int *tpa = f64 ? pa64 : kPairA, *tpb = f64 ? pb64 : kPairB;
-    const int limit = f64 ? 64 : 96;
+    const int limit = 64;  // six or more accumulators of bn columns in tensor memory
     float bs = 0.0f;
     int bbn = 0, bst = 0;
     for (int c = 0; c < 7; ++c)
@@ -1026,7 +1027,8 @@ static jagp_status_t jagp_set_tuning_impl(jagp_handle_t h, const jagp_tuning_t *
     const int np64 = slice_pairs(h->tc_slices, pa64, pb64);
     for (int side = 0; side < 2; ++side) {
       const bool left = side == 0;
-      const int limit = mixed ? 96 : 64;
+      // six accumulators (mixed) or up to eight (FP64-equivalent) of bn columns in tensor memory
+      const int limit = 64;
       if (bn[side] < 0 || bn[side] % 16 || bn[side] > limit) return JAGP_ERR_INVALID_ARG;
       if (stg[side] < -1 || stg[side] == 1 || stg[side] > 6) return JAGP_ERR_INVALID_ARG;
       const int npairs = mixed ? kFixedPairs : np64;
@@ -1072,12 +1074,13 @@ jagp_status_t jagp_gemm_bf16x(const uint16_t *d_A, int M, int a_terms, const uin
                               long long ldc, const int *d_rows, const int *d_count, const int *d_row_exp,
                               const int *d_col_exp, int *d_err, void *stream) {
   if (!d_A || !d_B || !d_C || !d_err || !h_pair_a || !h_pair_b) return JAGP_ERR_INVALID_ARG;
-  if (M <= 0 || N <= 0 || Kp <= 0 || Kp % 64 != 0 || ldc < N || npairs < 1 || npairs > 16) return JAGP_ERR_INVALID_ARG;
-  if (a_terms < 1 || a_terms > 5 || b_terms < 1 || b_terms > 5) return JAGP_ERR_INVALID_ARG;
+  if (M <= 0 || N <= 0 || Kp <= 0 || Kp % 64 != 0 || ldc < N || npairs < 1 || npairs > kFixedPairs)
+    return JAGP_ERR_INVALID_ARG;
+  if (a_terms < 1 || a_terms > kFixedSlices || b_terms < 1 || b_terms > kFixedSlices) return JAGP_ERR_INVALID_ARG;
   if ((d_row_exp == nullptr) != (d_col_exp == nullptr)) return JAGP_ERR_INVALID_ARG;
   if (d_row_exp)
     for (int p = 0; p < npairs; ++p)
-      if (h_pair_a[p] + h_pair_b[p] > 4) return JAGP_ERR_INVALID_ARG;
+      if (h_pair_a[p] + h_pair_b[p] > kFixedSlices - 1) return JAGP_ERR_INVALID_ARG;
   std::call_once(g_attr_once, [] {
     g_attr_err = setup_kernel_attributes();
     if (g_attr_err == cudaSuccess) g_attr_err = setup_walker_attributes();
@@ -1560,6 +1563,165 @@ jagp_status_t jagp_last_error(jagp_handle_t h, char *buf, size_t len) {
   if (!h) return JAGP_ERR_INVALID_ARG;
   if (buf && len > 0) snprintf(buf, len, "%s", h->last_error);
   return h->last_status;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Lattice-regularised diffusion Monte Carlo (Sec. "Lattice regularized Monte
+// Carlo"): the round loop of a projection and the reconfiguration.
+// ---------------------------------------------------------------------------
+namespace {
+
+LrdmcWork lrdmc_work(const jagp_ctx *h, int W, void *base, size_t *total) {
+  const size_t w = (size_t)W, N = h->ds.N;
+  size_t o = 0;
+  auto take = [&](size_t bytes) { size_t r = o; o = align256(o + bytes); return r; };
+  const size_t left = take(w * 8), lw = take(w * 8), eL = take(w * 8), rho = take(w * 6 * N * 8),
+               rt = take(w * N * 3 * 8), hops = take(w * 4), flags = take(w * 4), active = take(w * 4),
+               moved = take(w * 4), lu = take(w * 4), ld = take(w * 4), cnt = take(16);
+  if (total) *total = o;
+  LrdmcWork k;
+  char *b = static_cast<char *>(base);
+  k.left = reinterpret_cast<double *>(b + left);
+  k.lw = reinterpret_cast<double *>(b + lw);
+  k.eL = reinterpret_cast<double *>(b + eL);
+  k.rho = reinterpret_cast<double *>(b + rho);
+  k.r_tmp = reinterpret_cast<double *>(b + rt);
+  k.hops = reinterpret_cast<int *>(b + hops);
+  k.flags = reinterpret_cast<int *>(b + flags);
+  k.active = reinterpret_cast<int *>(b + active);
+  k.moved = reinterpret_cast<int *>(b + moved);
+  k.list_up = reinterpret_cast<int *>(b + lu);
+  k.list_dn = reinterpret_cast<int *>(b + ld);
+  k.cnt = reinterpret_cast<int *>(b + cnt);
+  return k;
+}
+
+jagp_status_t lrdmc_project(jagp_ctx *h, double *d_r, void *d_state, int W, uint64_t walker0, uint64_t gen,
+                            double a, double gamma, double tau, double e_ref, int max_hops, double *d_weight,
+                            double *d_eL, int *d_hops, int *d_flags, void *d_work, cudaStream_t st) {
+  const Layout L = layout_of(h, W);
+  const DevSystem &d = h->ds;
+  LrdmcWork k = lrdmc_work(h, W, d_work, nullptr);
+  double *phi_up = at<double>(d_state, L.phi_up), *pprop = at<double>(d_state, L.pprop);
+  int *status = at<int>(d_state, L.status);
+  // the walkers' tables, G~^{-1}, e_L and the kinetic vectors M at the start
+  jagp_status_t s = run_eval<double>(h, d_r, W, d_state, nullptr, nullptr, st);
+  if (s != JAGP_OK) return s;
+  s = run_local_energy<double>(h, d_r, d_state, W, k.eL, nullptr, st);
+  if (s != JAGP_OK) return s;
+  LAUNCH(0, 1, launch_lrdmc_start(status, W, tau, k, st));
+  for (;;) {
+    JAGP_CU(cudaMemsetAsync(k.cnt, 0, 4 * sizeof(int), st));
+    LAUNCH(JAGP_KERNEL_BASIS, 1, launch_lrdmc_ratios(d, d_r, at<double>(d_state, L.mbuf), k.active, a, k.rho, W, st));
+    LAUNCH(JAGP_KERNEL_METROPOLIS, 1,
+           launch_lrdmc_decide(d, d_r, k.eL, status, W, (uint32_t)walker0, (uint32_t)gen, a, gamma, e_ref, max_hops,
+                               k, st));
+    int h_cnt[4] = {0, 0, 0, 0};
+    JAGP_CU(cudaMemcpyAsync(h_cnt, k.cnt, sizeof(h_cnt), cudaMemcpyDeviceToHost, st));
+    JAGP_CU(cudaStreamSynchronize(st));
+    if (h_cnt[2] == 0) break;
+    // the moved electrons' orbital rows, their lambda products, G~^{-1}, J, e_L and M
+    LAUNCH(JAGP_KERNEL_BASIS, 1, launch_lrdmc_rows(d, d_r, k.moved, pprop, phi_up, W, st));
+    if (h_cnt[0] > 0) {
+      s = lambda_products(h, pprop, nullptr, at<double>(d_state, L.a_up), true, k.list_up, k.cnt, 0, 1, 0, h_cnt[0],
+                          d_state, W, st);
+      if (s != JAGP_OK) return s;
+    }
+    if (h_cnt[1] > 0) {
+      s = lambda_products(h, pprop, nullptr, at<double>(d_state, L.bt), false, k.list_dn, k.cnt + 1, 0, 1, 0,
+                          h_cnt[1], d_state, W, st);
+      if (s != JAGP_OK) return s;
+    }
+    s = run_refresh<double>(h, d_r, d_state, W, 0, true, st);
+    if (s != JAGP_OK) return s;
+    s = run_local_energy<double>(h, d_r, d_state, W, k.eL, nullptr, st);
+    if (s != JAGP_OK) return s;
+  }
+  LAUNCH(0, 1, launch_lrdmc_finish(W, k.lw, k.eL, d_weight, d_eL, st));
+  if (d_hops) JAGP_CU(cudaMemcpyAsync(d_hops, k.hops, (size_t)W * sizeof(int), cudaMemcpyDeviceToDevice, st));
+  if (d_flags) JAGP_CU(cudaMemcpyAsync(d_flags, k.flags, (size_t)W * sizeof(int), cudaMemcpyDeviceToDevice, st));
+  return JAGP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t jagp_lrdmc_workspace_bytes(jagp_handle_t h, int W) {
+  if (!h || W <= 0) return 0;
+  size_t total = 0;
+  lrdmc_work(h, W, nullptr, &total);
+  return total;
+}
+
+static jagp_status_t jagp_lrdmc_project_impl(jagp_handle_t h, double *d_r, void *d_state, int W, uint64_t walker0,
+                                             uint64_t generation, double a, double gamma, double tau, double e_ref,
+                                             int max_hops, double *d_weight, double *d_eL, int *d_hops, int *d_flags,
+                                             void *d_work, void *stream) {
+  jagp_status_t s = check_walkers(h, W, d_state);
+  if (s != JAGP_OK) return s;
+  if (!d_r || !d_weight || !d_work || (reinterpret_cast<uintptr_t>(d_work) & 255u)) {
+    jagp_set_detail("positions, weights or an aligned workspace missing");
+    return JAGP_ERR_INVALID_ARG;
+  }
+  if (!(a > 0.0) || !std::isfinite(a) || !(gamma >= 0.0) || !std::isfinite(gamma) || !(tau >= 0.0) ||
+      !std::isfinite(tau) || !std::isfinite(e_ref) || max_hops < 0) {
+    jagp_set_detail("a = %g, gamma = %g, tau = %g, e_ref = %g, max_hops = %d", a, gamma, tau, e_ref, max_hops);
+    return JAGP_ERR_INVALID_ARG;
+  }
+  if (h->precision != JAGP_PREC_FP64 || h->ds.use_j3) {
+    jagp_set_detail("lattice-regularised DMC runs on FP64 handles without the three-body Jastrow");
+    return JAGP_ERR_UNSUPPORTED;
+  }
+  if ((size_t)h->ds.N * 3 * sizeof(double) > 48 * 1024) {
+    jagp_set_detail("N = %d: the hop-ratio kernel keeps a walker's positions in 48 KB of shared memory", h->ds.N);
+    return JAGP_ERR_UNSUPPORTED;
+  }
+  return lrdmc_project(h, d_r, d_state, W, walker0, generation, a, gamma, tau, e_ref, max_hops, d_weight, d_eL,
+                       d_hops, d_flags, d_work, static_cast<cudaStream_t>(stream));
+}
+
+jagp_status_t jagp_lrdmc_project(jagp_handle_t h, double *d_r, void *d_state, int W, uint64_t walker0,
+                                 uint64_t generation, double a, double gamma, double tau, double e_ref, int max_hops,
+                                 double *d_weight, double *d_eL, int *d_hops, int *d_flags, void *d_work,
+                                 void *stream) {
+  return jagp_note(h, "jagp_lrdmc_project",
+                   jagp_lrdmc_project_impl(h, d_r, d_state, W, walker0, generation, a, gamma, tau, e_ref, max_hops,
+                                           d_weight, d_eL, d_hops, d_flags, d_work, stream));
+}
+
+static jagp_status_t jagp_lrdmc_branch_impl(jagp_handle_t h, double *d_r, int W, uint64_t generation,
+                                            double *d_weight, const double *d_eL, int *d_parent, double *d_stats,
+                                            void *d_work, void *stream) {
+  if (!h) return JAGP_ERR_INVALID_ARG;
+  if (W <= 0 || W > h->max_walkers || !d_r || !d_weight || !d_eL || !d_stats || !d_work ||
+      (reinterpret_cast<uintptr_t>(d_work) & 255u)) {
+    jagp_set_detail("W = %d (1..%d), positions, weights, energies, stats and an aligned workspace needed", W,
+                    h->max_walkers);
+    return JAGP_ERR_INVALID_ARG;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  LrdmcWork k = lrdmc_work(h, W, d_work, nullptr);
+  const size_t bytes = (size_t)W * h->ds.N * 3 * sizeof(double);
+  JAGP_CU(cudaMemcpyAsync(k.r_tmp, d_r, bytes, cudaMemcpyDeviceToDevice, st));
+  LAUNCH(0, 2,
+         launch_lrdmc_branch(W, h->ds.N, (uint32_t)generation, h->ds.key0, h->ds.key1, d_weight, d_eL,
+                             d_parent ? d_parent : k.moved, d_stats, k.r_tmp, d_r, st));
+  return JAGP_OK;
+}
+
+jagp_status_t jagp_lrdmc_branch(jagp_handle_t h, double *d_r, int W, uint64_t generation, double *d_weight,
+                                const double *d_eL, int *d_parent, double *d_stats, void *d_work, void *stream) {
+  return jagp_note(h, "jagp_lrdmc_branch",
+                   jagp_lrdmc_branch_impl(h, d_r, W, generation, d_weight, d_eL, d_parent, d_stats, d_work, stream));
+}
+
+jagp_status_t jagp_lrdmc_energy(const double *d_wbar, const double *d_ebar, int T, int p, double *d_E, void *stream) {
+  if (!d_wbar || !d_ebar || !d_E || T <= 0 || p < 0 || p >= T) return JAGP_ERR_INVALID_ARG;
+  JAGP_CU(launch_lrdmc_energy(d_wbar, d_ebar, T, p, d_E, static_cast<cudaStream_t>(stream)));
+  return JAGP_OK;
 }
 
 }  // extern "C"

@@ -15,8 +15,8 @@ constexpr int kMaxUp = 1024;        // largest N_up accepted (G~^{-1} leaves sha
 constexpr int kMaxUpGrad = 64;     // above this N_up the adjoint's G~-sized steps run as per-walker GEMMs
 constexpr int kWarp = 32;
 constexpr int kPropStride = 8;     // doubles per proposal record
-constexpr int kFixedSlices = 5;    // 8-bit slices per element of the fixed-point lambda products (mixed path)
-constexpr int kFixedPairs = 15;    // slice pairs (a, b) with a + b < kFixedSlices
+constexpr int kFixedSlices = 6;    // 8-bit slices per element of the fixed-point lambda products (mixed path)
+constexpr int kFixedPairs = 21;    // slice pairs (a, b) with a + b < kFixedSlices
 constexpr int kMaxPairs = 36;      // slice pairs of the FP64-equivalent products (eight slices)
 constexpr int kTcRefreshMinUp = 32;  // mixed path: G~ of a refresh on the tensor cores from this N_up on
 constexpr int kGuidedMaxUp = 64;     // guided sampling: G~ and G~^{-1} in shared memory up to this N_up
@@ -428,6 +428,21 @@ __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
+}
+
+// One-body Jastrow change when an electron moves from rr to rp, FP64
+// distances, summed over a warp (every lane gets the sum).
+__device__ __forceinline__ double j1_move_change(const DevSystem &s, const double *rp, const double *rr, int lane) {
+  double dj1 = 0.0;
+  // lane pairs: even lanes take the new position, odd lanes the old one
+  for (int q = lane; q < 2 * s.n_atoms; q += 32) {
+    const int a = q >> 1;
+    const double *pos = (q & 1) ? rr : rp;
+    const double ax = pos[0] - s.R[3 * a], ay = pos[1] - s.R[3 * a + 1], az = pos[2] - s.R[3 * a + 2];
+    const double v = j1_val(s.c1[a], s.b_ea, sqrt(ax * ax + ay * ay + az * az));
+    dj1 += (q & 1) ? -v : v;
+  }
+  return warp_sum(dj1);
 }
 
 }  // namespace jagp

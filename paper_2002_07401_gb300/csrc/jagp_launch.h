@@ -223,6 +223,35 @@ cudaError_t launch_force_seeds(const double *e, const double *u, int M, double *
                                cudaStream_t st);
 cudaError_t setup_forces_attributes();
 
+// Lattice-regularised diffusion Monte Carlo (k_lrdmc.cu), FP64 path.
+// Per-walker projection state in the caller's workspace.
+struct LrdmcWork {
+  double *left;    // [W] imaginary time left in this projection
+  double *lw;      // [W] log-weight gathered in this projection
+  double *eL;      // [W] local energy of the current configuration
+  double *rho;     // [W][6N] hop ratios Psi(x') / Psi(x)
+  double *r_tmp;   // [W][N][3] positions before a reconfiguration
+  int *hops, *flags, *active, *moved;  // [W]
+  int *list_up, *list_dn;              // [W] rows w n_up + row of this round's moves
+  int *cnt;                            // [4] up moves, down moves, walkers still active
+};
+cudaError_t launch_lrdmc_ratios(const DevSystem &s, const double *r, const double *mbuf, const int *active, double a,
+                                double *rho, int W, cudaStream_t st);
+cudaError_t launch_lrdmc_start(const int *status, int W, double tau, LrdmcWork &lw, cudaStream_t st);
+cudaError_t launch_lrdmc_decide(const DevSystem &s, double *r, const double *eL, const int *status, int W,
+                                uint32_t walker0, uint32_t gen, double a, double gamma, double e_ref, int max_hops,
+                                LrdmcWork &lw, cudaStream_t st);
+cudaError_t launch_lrdmc_rows(const DevSystem &s, const double *r, const int *moved, double *pprop, double *phi_up,
+                              int W, cudaStream_t st);
+cudaError_t launch_lrdmc_finish(int W, const double *lw, const double *eL_cur, double *weight, double *eL_out,
+                                cudaStream_t st);
+// parents by systematic resampling, (wbar, ebar) into stats, weights reset to
+// 1, r_new[j] = r_old[parent[j]]
+cudaError_t launch_lrdmc_branch(int W, int N, uint32_t gen, uint32_t key0, uint32_t key1, double *weight,
+                                const double *eL, int *parent, double *stats, const double *r_old, double *r_new,
+                                cudaStream_t st);
+cudaError_t launch_lrdmc_energy(const double *wbar, const double *ebar, int T, int p, double *E, cudaStream_t st);
+
 // one-time kernel attribute set-up (dynamic shared memory limits), per file
 cudaError_t setup_kernel_attributes();
 cudaError_t setup_walker_attributes();

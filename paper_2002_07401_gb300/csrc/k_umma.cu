@@ -12,7 +12,7 @@
 //   a = 2^(ea - 7) (t0 + t1 / 256 + t2 / 256^2 + ...),  |t_i| <= 128,
 // (exact in BF16), so every slice product is an integer below 2^14 and the
 // tensor cores sum them exactly while partial sums stay below 2^24.  Pairs of
-// equal weight d = a_p + b_p share an accumulator S_d (up to five), and the
+// equal weight d = a_p + b_p share an accumulator S_d (up to eight), and the
 // epilogue forms C = 2^(ea + eb - 14) (S_0 + S_1 / 256 + S_2 / 256^2 + ...) as
 // an unevaluated two-float sum: products of two-float rows far beyond FP32
 // accuracy, which the lossy FP32 accumulation inside the tensor cores would
@@ -797,7 +797,7 @@ cudaError_t launch_pack_cols(const double *X64, const float *X32, const float *X
 
 cudaError_t setup_umma_attributes() {
   // the largest opt-in shared memory per block (227 KB on this part), so that
-  // two chunk-major stages of five slices fit
+  // two chunk-major stages of six slices fit at the narrower tiles
   int dev = 0, optin = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);

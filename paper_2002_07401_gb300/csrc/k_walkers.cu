@@ -22,20 +22,6 @@ namespace jagp {
 // one-body Jastrow change of the move is taken here as well (FP32 distances in
 // the FP32 path: it only enters the acceptance test).
 // ---------------------------------------------------------------------------
-// FP64 path: the change from FP64 distances.
-__device__ __forceinline__ double j1_move_change(const DevSystem &s, const double *rp, const double *rr, int lane) {
-  double dj1 = 0.0;
-  // lane pairs: even lanes take the new position, odd lanes the old one
-  for (int q = lane; q < 2 * s.n_atoms; q += 32) {
-    const int a = q >> 1;
-    const double *pos = (q & 1) ? rr : rp;
-    const double ax = pos[0] - s.R[3 * a], ay = pos[1] - s.R[3 * a + 1], az = pos[2] - s.R[3 * a + 2];
-    const double v = j1_val(s.c1[a], s.b_ea, sqrt(ax * ax + ay * ay + az * az));
-    dj1 += (q & 1) ? -v : v;
-  }
-  return warp_sum(dj1);
-}
-
 // Mixed path: FP32 instructions only, from the positions and atoms rounded to
 // FP32 (the change only enters the acceptance test); every lane gets the sum.
 __device__ __forceinline__ double j1_move_change_f(const DevSystem &s, const float *rp, const float *rr, int lane) {

@@ -62,6 +62,12 @@ def test_status_strings_and_bad_args_without_gpu():
     assert L.jagp_sr_workspace_bytes(0, 5) == 0 and L.jagp_sr_workspace_bytes(10, 5) > 0
     assert L.jagp_sr_step(None, 5, None, 10, 5, 1e-3, 1.0, 10, 1e-10, None, None, None, None, None, None) == 1
     assert L.jagp_logpsi_derivs(None, None, None, 1, None, None, 1, None) == 1
+    # lattice-regularised DMC: a handle, sizes and the estimator's p are checked on the host
+    assert L.jagp_lrdmc_workspace_bytes(None, 4) == 0
+    assert L.jagp_lrdmc_project(None, None, None, 4, 0, 0, 0.2, 0.0, 0.1, 0.0, 10, None, None, None, None, None,
+                                None) == 1
+    assert L.jagp_lrdmc_branch(None, None, 4, 0, None, None, None, None, None, None) == 1
+    assert L.jagp_lrdmc_energy(None, None, 4, 0, None, None) == 1
 
 
 def test_oracle_and_product_share_no_code():

@@ -236,3 +236,45 @@ def test_full_size_c4_logpsi_gradients_sampled(torch_cuda):
         e_ref = o.local_energy(x)
         assert abs(eL.cpu().numpy()[0, w] - e_ref) <= 1e-10 * max(1.0, abs(e_ref)), (w, e_ref)
     g.close()
+
+
+@pytest.mark.parametrize("name", ["n121", "C4"])
+def test_large_local_energy_derivatives_match_fd(torch_cuda, name):
+    """The e_L half of the force at N_up = 121 (the adjoint's per-walker GEMM
+    branch) and at the full-size adjoint workload (64 He, N = 128, L = 1536,
+    2048 walkers, after one sweep as the bench runs it): for one sampled
+    walker, d e_L / d R_a at two nuclei, d e_L / d r_i at three electron
+    coordinates and d e_L / d lambda at two entries against the oracle's
+    Richardson-extrapolated central differences at h = 1e-4 bohr, tolerance
+    1e-6 relative to the largest of them."""
+    torch = torch_cuda
+    import paper_2002_07401_gb300 as pg
+    if name == "C4":
+        sysm, W = synth.config4(), 2048
+    else:
+        sysm, W = synth.small_random(n_atoms=60, n_up=121, n_dn=119, per_atom=6, seed=51, side=14.0, Z=2.0), 2
+    g = pg.JAGP(sysm, W, seed=0)
+    r = g.positions(synth.init_walkers(sysm, W, seed=0) if name == "C4" else _cfgs(sysm, W))
+    g.eval(r)
+    if name == "C4":
+        g.sweep(r, 1)
+        g.eval(r)
+    assert g.status() & (pg.WS_NONFINITE | pg.WS_SINGULAR) == 0
+    rng = np.random.default_rng(7)
+    w = int(rng.integers(W))
+    seeds = np.zeros(W)
+    seeds[w] = 1.0
+    out = g.grad(r, seed_eL=torch.tensor(seeds, device="cuda"))
+    x = np.ascontiguousarray(r.cpu().numpy()[w])
+    atoms = rng.choice(sysm.n_atoms, size=2, replace=False)
+    Rc = [(int(a), q) for a in atoms for q in range(3)]
+    rc = [(int(rng.integers(sysm.N)), int(rng.integers(3))) for _ in range(3)]
+    lc = [tuple(int(v) for v in rng.integers(sysm.L, size=2)) for _ in range(2)]
+    fd = oracle.Oracle(sysm).elocal_fd_select(x, R=Rc, r=rc, lam=lc, h=1e-4)
+    Rw, rr, lam = out["R_walker"].cpu().numpy(), out["r"].cpu().numpy(), out["lam"].cpu().numpy()
+    got = np.array([Rw[w, a, q] for a, q in Rc] + [rr[w, i, q] for i, q in rc] + [lam[mu, nu] for mu, nu in lc])
+    scale = max(1.0, float(np.abs(fd).max()))
+    err = np.abs(got - fd) / scale
+    print(name, "walker", w, "max rel err", err.max(), "components", np.abs(fd))
+    assert err.max() <= 1e-6, (Rc, rc, lc, got, fd)
+    g.close()

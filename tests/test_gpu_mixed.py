@@ -1,5 +1,5 @@
 """Mixed-precision path (double-word FP32 orbital tables, BF16 tensor-core
-lambda products on five-slice fixed-point operands, FP64 refresh / log-det /
+lambda products on six-slice fixed-point operands, FP64 refresh / log-det /
 energies, kinetic contraction from exact fixed-point M vectors in double-word
 arithmetic) against the FP64 oracle.
 
@@ -121,6 +121,47 @@ def test_mixed_vmc_mean_matches_oracle(torch_cuda):
     wo = eo[equil:].mean(0)
     err = math.sqrt(wm.var(ddof=1) / W + wo.var(ddof=1) / W)
     assert abs(wm.mean() - wo.mean()) < 4.5 * err, (wm.mean(), wo.mean(), err)
+
+
+@pytest.mark.parametrize("name", ["C2", "C3-median"])
+def test_mixed_vmc_mean_paired_with_the_fp64_chain(torch_cuda, name):
+    """VMC mean of the mixed chain at C2 (4096 walkers) and at the batched
+    workload's median system, against the FP64 chain driven by the same random
+    numbers.  The FP64 chain is the oracle's chain: the same proposals and
+    uniforms, positions identical move by move (the trajectory parity tests).
+    The mixed chain takes its accept decisions from FP32 ratios, so a walker
+    follows the FP64 chain until a decision flips.  Three checks:
+    * on the walkers that never left the FP64 trajectory the time-averaged
+      e_L differ only by the evaluation error: their mean difference is
+      within the per-configuration tolerance (1e-5 Ha);
+    * at least 99% of the walkers never leave it over 120 sweeps, so fewer
+      than about 3e-6 of the accept decisions differ (the only way the
+      sampled distribution could differ);
+    * over all walkers the mean difference lies within 4.5 paired error bars
+      plus the per-configuration tolerance."""
+    import paper_2002_07401_gb300 as pg
+    sysm = SYSTEMS[name]()
+    W, sweeps, equil = (4096, 120, 20) if name == "C2" else (2048, 120, 20)
+    x0 = synth.init_walkers(sysm, W, seed=3)
+    means, finals = {}, {}
+    for prec in (pg.JAGP_PREC_MIXED, pg.JAGP_PREC_FP64):
+        g = pg.JAGP(sysm, W, precision=prec, seed=11)
+        r = g.positions(x0)
+        g.eval(r)
+        eL, _ = g.sweep(r, sweeps)
+        assert g.status() & (pg.WS_NONFINITE | pg.WS_SINGULAR) == 0
+        means[prec] = eL.cpu().numpy()[equil:].mean(0)
+        finals[prec] = r.cpu().numpy()
+        g.close()
+    d = means[pg.JAGP_PREC_MIXED] - means[pg.JAGP_PREC_FP64]
+    se = d.std(ddof=1) / math.sqrt(W)
+    on = np.all(np.abs(finals[pg.JAGP_PREC_MIXED] - finals[pg.JAGP_PREC_FP64]) <= 1e-9, axis=(1, 2))
+    spread = means[pg.JAGP_PREC_FP64].std(ddof=1) / math.sqrt(W)
+    print(f"{name}: mean difference {d.mean():.3e} Ha, paired error {se:.3e} (unpaired {spread:.3e}), "
+          f"walkers on the FP64 trajectory {on.mean():.4f}, their mean difference {d[on].mean():.3e}")
+    assert on.mean() >= 0.99, on.mean()
+    assert abs(d[on].mean()) <= EL_TOL, d[on].mean()
+    assert abs(d.mean()) <= 4.5 * se + EL_TOL, (d.mean(), se)
 
 
 def test_mixed_hydrogen_zero_variance(torch_cuda):

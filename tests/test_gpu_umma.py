@@ -121,10 +121,12 @@ def slice_fixed4(torch, x, Kp, nsl=4):
 
 TEN = [(0, 0), (0, 1), (1, 0), (0, 2), (1, 1), (2, 0), (0, 3), (1, 2), (2, 1), (3, 0)]
 FIFTEEN = TEN + [(0, 4), (1, 3), (2, 2), (3, 1), (4, 0)]
+TWENTYONE = FIFTEEN + [(0, 5), (1, 4), (2, 3), (3, 2), (4, 1), (5, 0)]
 
 
 @pytest.mark.parametrize("M,N,K,nsl", [(300, 320, 320, 4), (129, 24, 24, 4), (200, 1536, 256, 4), (64, 100, 1000, 4),
-                                       (300, 320, 320, 5), (129, 200, 4096, 5)])
+                                       (300, 320, 320, 5), (129, 200, 4096, 5), (300, 320, 320, 6),
+                                       (129, 200, 4096, 6)])
 def test_umma_fixed_point_is_exact_up_to_fp32_rounding(torch_cuda, M, N, K, nsl):
     """Exact slice products summed exactly: the result equals the FP64 value
     reconstructed from the same slices to about one FP32 rounding, and the
@@ -138,7 +140,7 @@ def test_umma_fixed_point_is_exact_up_to_fp32_rounding(torch_cuda, M, N, K, nsl)
     y = torch.randn((N, K), device="cuda", dtype=torch.float64, generator=g) * 0.1
     y[:, :min(N, K)] += torch.eye(N, K, device="cuda", dtype=torch.float64)[:, :min(N, K)]
     Kp = (K + 63) // 64 * 64
-    pairs = TEN if nsl == 4 else FIFTEEN
+    pairs = {4: TEN, 5: FIFTEEN, 6: TWENTYONE}[nsl]
     A, ea = slice_fixed4(torch, x, Kp, nsl)
     B, eb = slice_fixed4(torch, y, Kp, nsl)
     C = torch.full((M, N), float("nan"), dtype=torch.float32, device="cuda")
