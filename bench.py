@@ -817,8 +817,8 @@ def lrdmc_bench(pg, torch, dist, args, dev, rank, ws, local):
     """LRDMC hops/s: one step = one generation (a continuous-time projection
     of length tau, every walker hopping until its time is spent, then the
     reconfiguration).  Each round of hops recomputes the moved rows' lambda
-    products, G~^{-1}, the kinetic vectors M and e_L of every walker, and the
-    6N hop ratios of every walker still moving."""
+    products, and G~^{-1}, the kinetic vectors M and e_L of the walkers that
+    moved, and the 6N hop ratios of every walker still moving."""
     import numpy as np
     import synth
     sysm = synth.config2()
@@ -873,10 +873,11 @@ def lrdmc_bench(pg, torch, dist, args, dev, rank, ws, local):
     g.close()
     K = args.lrdmc_gens
     n, nd, N, L = sysm.n_up, sysm.n_dn, sysm.N, sysm.L
-    # dense FP64 work of one round per walker: the refresh product G~ = Phi_up Bt^T
-    # (2 n^2 L), the kinetic vectors M (2 N n L) and the 6N hop-ratio dots (12 N L),
-    # plus 2 L^2 per moved walker (its lambda row)
-    flops = rounds * W * (2.0 * n * n * L + 2.0 * N * n * L + 12.0 * N * L) + tot_h * 2.0 * L * L
+    # dense FP64 work per hop: the moved row's lambda product (2 L^2), the
+    # refresh product G~ = Phi_up Bt^T (2 n^2 L) and the kinetic vectors M
+    # (2 N n L) of the walker that moved; per walker and round it is active
+    # (its hops plus its last round): the 6N hop-ratio dots (12 N L)
+    flops = tot_h * (2.0 * L * L + 2.0 * n * n * L + 2.0 * N * n * L) + (tot_h + W * K) * 12.0 * N * L
     tf = flops / (ms / 1e3) / 1e12
     return {"metric": "LRDMC walker hops/s", "value": tot_h * ws / (ms / 1e3), "unit": "walker hops/s",
             "ms_per_generation": ms / K, "generations": K, "warmup": args.lrdmc_warmup,
@@ -884,8 +885,8 @@ def lrdmc_bench(pg, torch, dist, args, dev, rank, ws, local):
             "ebar": ebar, "e_ref": e_ref, "gpu_launches": launches, "dtype": "f64", "workload": LRDMC_WORKLOAD,
             "roofline": {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": tf / FP64_PEAK_TFLOPS,
-                         "work": "per round and walker 2 N_up^2 L (G~) + 2 N N_up L (M) + 12 N L (hop ratios), "
-                                 "plus 2 L^2 per hop (lambda row), over the whole generation",
+                         "work": "per hop 2 L^2 (lambda row) + 2 N_up^2 L (G~) + 2 N N_up L (M); per active "
+                                 "walker and round 12 N L (hop ratios); over the whole generation",
                          "peak_source": "nominal FP64 of GB300 (152 SM x 2 DFMA/clk x 2.07 GHz)"}}
 
 

@@ -319,7 +319,9 @@ jagp_status_t jagp_force_seeds(const double *d_eL, const double *d_weight, int M
  * d_weight [W] in/out: multiplied by exp(log-weight change).  d_eL [W]
  * (or NULL): e_L at the final configuration.  d_hops, d_flags [W] (or NULL).
  * d_state is evaluated at the start (jagp_eval) and is current at the end.
- * d_work: jagp_lrdmc_workspace_bytes(h, W) bytes, 256-byte aligned, device.
+ * d_work: jagp_lrdmc_workspace_bytes(h, W) bytes, 256-byte aligned, device
+ * (it holds, besides the per-walker projection state, a compact walker state
+ * in which each round's moved walkers are refreshed).
  * Synchronises the stream once per round of hops (every walker still moving
  * takes one hop per round).  a > 0, gamma >= 0, tau >= 0, max_hops >= 0.
  * Errors: INVALID_ARG; UNSUPPORTED for a mixed-precision handle or the
@@ -392,9 +394,10 @@ jagp_status_t jagp_autotune(jagp_handle_t h, void *d_state, int W, jagp_tuning_t
  * CUDA call; ms is ignored.  tile_proposals / tile_refresh: -1 (the shape
  * heuristics), 0, 32 or 64, and 16 for tile_refresh in the mixed path with
  * N_up <= 16.  umma_*: 0 without tensor-core lambda products (FP64 without
- * fp64_tensor_cores); else bn 0 (heuristic) or a multiple of 16 up to 64, and
- * stages -1 (chunk-major, only where two such stages fit in shared memory:
- * bn = 16 with the mixed path's six slices), 0 or 2..6.
+ * fp64_tensor_cores); else bn 0 (heuristic) or a multiple of 16 up to 96 in
+ * the mixed path (five accumulators) and 64 in the FP64-equivalent one, and
+ * stages -1 (chunk-major, only where two such stages fit in shared memory,
+ * which the mixed path's 6 + 12 slice terms never do), 0 or 2..6.
  * Every choice changes the tiling only, so results stay as without tuning.
  * Returns JAGP_ERR_INVALID_ARG (and keeps the earlier choices) on any other value. */
 jagp_status_t jagp_set_tuning(jagp_handle_t h, const jagp_tuning_t *t);

@@ -83,6 +83,19 @@ Layout layout_of(const jagp_ctx *h, int W) {
 // numbers; the kinetic term amplifies their relative error by about cond(G~).
 const int kPairA[kFixedPairs] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3, 0, 1, 2, 3, 4, 0, 1, 2, 3, 4, 5};
 const int kPairB[kFixedPairs] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0, 4, 3, 2, 1, 0, 5, 4, 3, 2, 1, 0};
+// The lambda products take the same pairs with five accumulators instead of
+// six: the sliced lambda carries its six slices (terms 0..5) and copies scaled
+// by 2^-8 (terms 6..11), exact in BF16, so that the pairs of weight 256^-5 add
+// into the accumulator of weight 256^-4.  That accumulator's FP32 rounding
+// (about 2^-24 of its partial sums at every step along K) stays near 2^-48 of
+// the result, the precision of the six slices; merging one weight further
+// down (into 256^-3) measurably raised the error at an ill-conditioned
+// configuration.  Five accumulators leave room for 96-column tiles in tensor
+// memory (six: 64).
+constexpr int kLamTerms = 2 * kFixedSlices;
+const int kLamPairB[kFixedPairs] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0, 4, 3, 2, 1, 0, 11, 10, 9, 8, 7, 6};
+const int kLamGroup[kFixedPairs] = {0, 1, 1, 2, 2, 2, 3, 3, 3, 3, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4};
+constexpr int kLamBnMax = 96;  // tile width limit of the lambda products (five accumulators)
 
 // all slice pairs (a, b) with a + b < nsl, ordered by a + b, then a
 int slice_pairs(int nsl, int *pa, int *pb) {
@@ -124,6 +137,21 @@ int slice_row_fixed(const double *v, size_t vstride, int L, uint16_t *dst, size_
     }
   }
   return e;
+}
+
+// terms nsl..2nsl-1 of a sliced row: its slices times 2^-8 (exact: BF16 keeps
+// the 8-bit integers' bits, only the exponent moves)
+void scaled_slice_copies(uint16_t *row, size_t kp, int nsl) {
+  for (int t = 0; t < nsl; ++t)
+    for (size_t k = 0; k < kp; ++k) {
+      uint32_t u = static_cast<uint32_t>(row[t * kp + k]) << 16;
+      float f;
+      memcpy(&f, &u, 4);
+      const float g = std::ldexp(f, -8);
+      uint32_t v;
+      memcpy(&v, &g, 4);
+      row[(nsl + t) * kp + k] = static_cast<uint16_t>(v >> 16);
+    }
 }
 
 jagp_status_t check_walkers(const jagp_ctx *h, int W, const void *state) {
@@ -182,10 +210,10 @@ jagp_status_t lambda_products(jagp_ctx *h, const float *P, const float *P_lo, fl
   float *out_lo = at<float>(state, left ? L.a_up_lo : L.bt_lo);
   LAUNCH(JAGP_KERNEL_LAMBDA_ROWS, 1,
          launch_umma_gemm(pack, max_rows, count, kFixedSlices, left ? h->split_lamT : h->split_lam, h->ds.L,
-                          kFixedSlices, h->kp, kFixedPairs, kPairA, kPairB, out, h->ds.L,
+                          kLamTerms, h->kp, kFixedPairs, kPairA, kLamPairB, out, h->ds.L,
                           rows, h->d_err, st, exps, left ? h->exp_lamT : h->exp_lam, out_lo,
                           left ? h->tune_bn_left : h->tune_bn_right, nullptr, 8, 0, 0,
-                          left ? h->tune_st_left : h->tune_st_right));
+                          left ? h->tune_st_left : h->tune_st_right, 0, 0, 0, 0, kLamGroup));
   return JAGP_OK;
 }
 
@@ -726,11 +754,13 @@ jagp_status_t jagp_create(jagp_handle_t *out, const jagp_system_t *sys, const ja
   const bool tc64 = !mixed && opt->fp64_tensor_cores != 0;
   const bool tc = mixed || tc64;
   const int kp = (L + 63) / 64 * 64;
-  // slices per element: mixed 5 x 8 bits; FP64-equivalent 7 x 8 bits, or 8 x 7
-  // bits when L > 512 so that the leading accumulators stay exact
+  // slices per element: mixed 6 x 8 bits (stored with their copies scaled by
+  // 2^-8, 12 terms); FP64-equivalent 7 x 8 bits, or 8 x 7 bits when
+  // L > 512 so that the leading accumulators stay exact
   const int nsl = mixed ? kFixedSlices : (tc64 ? (L <= 512 ? 7 : 8) : 0);
+  const int nterms = mixed ? kLamTerms : nsl;
   const int bits = tc64 && L > 512 ? 7 : 8;
-  const size_t split_bytes = tc ? (size_t)L * nsl * kp * 2 : 0;
+  const size_t split_bytes = tc ? (size_t)L * nterms * kp * 2 : 0;
   const size_t exp_bytes = tc ? (size_t)L * 4 : 0;
   const size_t oSA = take(split_bytes), oSB = take(split_bytes), oXA = take(exp_bytes), oXB = take(exp_bytes);
   const size_t oE = take(16);
@@ -741,8 +771,13 @@ jagp_status_t jagp_create(jagp_handle_t *out, const jagp_system_t *sys, const ja
   if (tc) {
     for (int nn = 0; nn < L; ++nn) {
       // column nn, then row nn
-      xA[nn] = slice_row_fixed(sys->lambda + nn, (size_t)L, L, &sA[(size_t)nn * nsl * kp], (size_t)kp, nsl, bits);
-      xB[nn] = slice_row_fixed(sys->lambda + (size_t)nn * L, 1, L, &sB[(size_t)nn * nsl * kp], (size_t)kp, nsl, bits);
+      uint16_t *ra = &sA[(size_t)nn * nterms * kp], *rb = &sB[(size_t)nn * nterms * kp];
+      xA[nn] = slice_row_fixed(sys->lambda + nn, (size_t)L, L, ra, (size_t)kp, nsl, bits);
+      xB[nn] = slice_row_fixed(sys->lambda + (size_t)nn * L, 1, L, rb, (size_t)kp, nsl, bits);
+      if (mixed) {
+        scaled_slice_copies(ra, (size_t)kp, nsl);
+        scaled_slice_copies(rb, (size_t)kp, nsl);
+      }
     }
   }
   std::vector<float4> atom_f(na);
@@ -949,8 +984,9 @@ jagp_status_t tune_products(jagp_ctx *h, void *state, int W, cudaStream_t st, ja
     // for all pairs; two stages, where they fit)
     const int stages[4] = {0, 3, 2, -1};
     const int npairs = f64 ? np64 : kFixedPairs;
-    const int *tpa = f64 ? pa64 : kPairA, *tpb = f64 ? pb64 : kPairB;
-    const int limit = 64;  // six or more accumulators of bn columns in tensor memory
+    const int *tpa = f64 ? pa64 : kPairA, *tpb = f64 ? pb64 : kLamPairB;
+    // accumulators of bn columns in tensor memory: five (mixed) or up to eight
+    const int limit = f64 ? 64 : kLamBnMax;
     float bs = 0.0f;
     int bbn = 0, bst = 0;
     for (int c = 0; c < 7; ++c)
@@ -967,10 +1003,10 @@ jagp_status_t tune_products(jagp_ctx *h, void *state, int W, cudaStream_t st, ja
                                         exps, left ? h->exp_lamT : h->exp_lam, nullptr, cands[c],
                                         reinterpret_cast<double *>(dst), h->tc_bits, 0, 0, stages[q]);
               return launch_umma_gemm(pack, rows, nullptr, kFixedSlices, left ? h->split_lamT : h->split_lam, Lb,
-                                      kFixedSlices, h->kp, kFixedPairs, kPairA, kPairB,
+                                      kLamTerms, h->kp, kFixedPairs, kPairA, kLamPairB,
                                       reinterpret_cast<float *>(dst), Lb, nullptr, h->d_err, st, exps,
                                       left ? h->exp_lamT : h->exp_lam, at<float>(state, left ? L.a_up_lo : L.bt_lo),
-                                      cands[c], nullptr, 8, 0, 0, stages[q]);
+                                      cands[c], nullptr, 8, 0, 0, stages[q], 0, 0, 0, 0, kLamGroup);
             },
             st, &ms));
         if (bbn == 0 || ms < bs) {
@@ -1027,13 +1063,13 @@ static jagp_status_t jagp_set_tuning_impl(jagp_handle_t h, const jagp_tuning_t *
     const int np64 = slice_pairs(h->tc_slices, pa64, pb64);
     for (int side = 0; side < 2; ++side) {
       const bool left = side == 0;
-      // six accumulators (mixed) or up to eight (FP64-equivalent) of bn columns in tensor memory
-      const int limit = 64;
+      // five accumulators (mixed) or up to eight (FP64-equivalent) of bn columns in tensor memory
+      const int limit = mixed ? kLamBnMax : 64;
       if (bn[side] < 0 || bn[side] % 16 || bn[side] > limit) return JAGP_ERR_INVALID_ARG;
       if (stg[side] < -1 || stg[side] == 1 || stg[side] > 6) return JAGP_ERR_INVALID_ARG;
       const int npairs = mixed ? kFixedPairs : np64;
       const int actual = umma_pick_bn(h->ds.L, bn[side] ? bn[side] : limit);
-      if (stg[side] == -1 && !umma_chunk_fits(npairs, mixed ? kPairA : pa64, mixed ? kPairB : pb64, actual))
+      if (stg[side] == -1 && !umma_chunk_fits(npairs, mixed ? kPairA : pa64, mixed ? kLamPairB : pb64, actual))
         return JAGP_ERR_INVALID_ARG;
     }
   }
@@ -1579,7 +1615,8 @@ LrdmcWork lrdmc_work(const jagp_ctx *h, int W, void *base, size_t *total) {
   auto take = [&](size_t bytes) { size_t r = o; o = align256(o + bytes); return r; };
   const size_t left = take(w * 8), lw = take(w * 8), eL = take(w * 8), rho = take(w * 6 * N * 8),
                rt = take(w * N * 3 * 8), hops = take(w * 4), flags = take(w * 4), active = take(w * 4),
-               moved = take(w * 4), lu = take(w * 4), ld = take(w * 4), cnt = take(16);
+               moved = take(w * 4), lu = take(w * 4), ld = take(w * 4), lwk = take(w * 4), cnt = take(16),
+               rs = take(w * N * 3 * 8), es = take(w * 8), ss = take(layout_of(h, W).total);
   if (total) *total = o;
   LrdmcWork k;
   char *b = static_cast<char *>(base);
@@ -1594,7 +1631,11 @@ LrdmcWork lrdmc_work(const jagp_ctx *h, int W, void *base, size_t *total) {
   k.moved = reinterpret_cast<int *>(b + moved);
   k.list_up = reinterpret_cast<int *>(b + lu);
   k.list_dn = reinterpret_cast<int *>(b + ld);
+  k.list_w = reinterpret_cast<int *>(b + lwk);
   k.cnt = reinterpret_cast<int *>(b + cnt);
+  k.r_sub = reinterpret_cast<double *>(b + rs);
+  k.eL_sub = reinterpret_cast<double *>(b + es);
+  k.sub_state = b + ss;
   return k;
 }
 
@@ -1634,10 +1675,33 @@ jagp_status_t lrdmc_project(jagp_ctx *h, double *d_r, void *d_state, int W, uint
                           h_cnt[1], d_state, W, st);
       if (s != JAGP_OK) return s;
     }
-    s = run_refresh<double>(h, d_r, d_state, W, 0, true, st);
+    // only the moved walkers changed: their tables and positions into a
+    // compact state, G~^{-1}, J, e_L and M there, and back
+    const int Wc = h_cnt[2];
+    const Layout C = layout_of(h, Wc);
+    const size_t n = d.n_up, Lb = d.L, N = d.N;
+    WalkerCopies in{};
+    in.c[0] = {phi_up, at<double>(k.sub_state, C.phi_up), n * Lb * 8};
+    in.c[1] = {at<double>(d_state, L.a_up), at<double>(k.sub_state, C.a_up), n * Lb * 8};
+    in.c[2] = {at<double>(d_state, L.bt), at<double>(k.sub_state, C.bt), n * Lb * 8};
+    in.c[3] = {d_r, k.r_sub, N * 3 * 8};
+    in.c[4] = {at<double>(d_state, L.scal), at<double>(k.sub_state, C.scal), (size_t)S_STRIDE * 8};
+    in.c[5] = {status, at<int>(k.sub_state, C.status), 4};
+    in.n = 6;
+    LAUNCH(0, 1, launch_walker_copy(in, k.list_w, Wc, false, st));
+    s = run_refresh<double>(h, k.r_sub, k.sub_state, Wc, 0, true, st);
     if (s != JAGP_OK) return s;
-    s = run_local_energy<double>(h, d_r, d_state, W, k.eL, nullptr, st);
+    s = run_local_energy<double>(h, k.r_sub, k.sub_state, Wc, k.eL_sub, nullptr, st);
     if (s != JAGP_OK) return s;
+    WalkerCopies out{};
+    out.c[0] = {at<double>(k.sub_state, C.ginv), at<double>(d_state, L.ginv), n * n * 8};
+    out.c[1] = {at<double>(k.sub_state, C.scal), at<double>(d_state, L.scal), (size_t)S_STRIDE * 8};
+    out.c[2] = {at<int>(k.sub_state, C.status), status, 4};
+    out.c[3] = {at<double>(k.sub_state, C.mbuf), at<double>(d_state, L.mbuf), N * Lb * 8};
+    out.c[4] = {at<double>(k.sub_state, C.kin), at<double>(d_state, L.kin), N * 4 * 8};
+    out.c[5] = {k.eL_sub, k.eL, 8};
+    out.n = 6;
+    LAUNCH(0, 1, launch_walker_copy(out, k.list_w, Wc, true, st));
   }
   LAUNCH(0, 1, launch_lrdmc_finish(W, k.lw, k.eL, d_weight, d_eL, st));
   if (d_hops) JAGP_CU(cudaMemcpyAsync(d_hops, k.hops, (size_t)W * sizeof(int), cudaMemcpyDeviceToDevice, st));

@@ -130,7 +130,7 @@ cudaError_t launch_umma_gemm(const uint16_t *A, int m_max, const int *m_dev, int
                              const int *a_exp = nullptr, const int *b_exp = nullptr, float *out_lo = nullptr,
                              int bn_max = 0, double *out64 = nullptr, int slice_bits = 8, int batch_rows = 0,
                              int batches = 0, int stages_max = 0, int b_batch_rows = 0, long long o_bstride = 0,
-                             long long o_rstride = 0, long long o_cstride = 0);
+                             long long o_rstride = 0, long long o_cstride = 0, const int *pair_group = nullptr);
 // whether two chunk-major stages (stages_max = -1) of these pairs fit at tile width bn
 bool umma_chunk_fits(int npairs, const int *pair_a, const int *pair_b, int bn);
 // FP64 rows -> nsl exact slices of `bits` bits per element plus a row exponent;
@@ -233,8 +233,23 @@ struct LrdmcWork {
   double *r_tmp;   // [W][N][3] positions before a reconfiguration
   int *hops, *flags, *active, *moved;  // [W]
   int *list_up, *list_dn;              // [W] rows w n_up + row of this round's moves
+  int *list_w;                         // [W] walkers that moved this round
   int *cnt;                            // [4] up moves, down moves, walkers still active
+  void *sub_state;                     // walker state of the moved walkers, compacted
+  double *r_sub, *eL_sub;              // their positions [W][N][3] and local energies [W]
 };
+// per-walker arrays copied between a state and a compacted one
+struct WalkerCopy {
+  const void *src;
+  void *dst;
+  size_t bytes;  // per walker, a multiple of 4
+};
+struct WalkerCopies {
+  WalkerCopy c[10];
+  int n;
+};
+// gather (dst[j] = src[list[j]]) or scatter (dst[list[j]] = src[j]) for j < Wc
+cudaError_t launch_walker_copy(const WalkerCopies &cp, const int *list, int Wc, bool scatter, cudaStream_t st);
 cudaError_t launch_lrdmc_ratios(const DevSystem &s, const double *r, const double *mbuf, const int *active, double a,
                                 double *rho, int W, cudaStream_t st);
 cudaError_t launch_lrdmc_start(const int *status, int W, double tau, LrdmcWork &lw, cudaStream_t st);

@@ -17,9 +17,9 @@
 //
 // A projection runs in rounds: every walker with time left takes one hop
 // (or ends) per round, one thread deciding for each walker; then the moved
-// electrons' orbital rows, their lambda products, a refresh of G~^{-1} and
-// the local energy of the new configurations (jagp_api.cu) prepare the next
-// round.  Decisions read the Philox4x32-10 stream (walker, generation, hop, 2).
+// electrons' orbital rows and their lambda products, and, on a compact copy
+// of the moved walkers' state, a refresh of G~^{-1} and the local energy of
+// the new configurations (jagp_api.cu) prepare the next round.  Decisions read the Philox4x32-10 stream (walker, generation, hop, 2).
 #include "jagp_launch.h"
 
 namespace jagp {
@@ -87,13 +87,15 @@ __global__ void k_lrdmc_start(const int *__restrict__ status, int W, double tau,
 // left times e_L - e_ref) or hops to the first k whose running rate sum
 // exceeds u Gamma (a non-finite Gamma or e_L ends the walker with flag 4).
 // A moved electron's row goes to the up or down list
-// (w n_up + row) for the lambda products; cnt[2] counts walkers still active.
+// (w n_up + row) for the lambda products, the walker to list_w; cnt[2]
+// counts the walkers that moved (those still active).
 __global__ void k_lrdmc_decide(DevSystem s, double *__restrict__ r, const double *__restrict__ rho,
                                const double *__restrict__ eL, const int *__restrict__ status, int W, uint32_t walker0,
                                uint32_t gen, double a, double gamma, double e_ref, int max_hops,
                                double *__restrict__ left, double *__restrict__ lw, int *__restrict__ hops,
                                int *__restrict__ flags, int *__restrict__ active, int *__restrict__ moved,
-                               int *__restrict__ list_up, int *__restrict__ list_dn, int *__restrict__ cnt) {
+                               int *__restrict__ list_up, int *__restrict__ list_dn, int *__restrict__ list_w,
+                               int *__restrict__ cnt) {
   const int w = blockIdx.x * blockDim.x + threadIdx.x;
   if (w >= W) return;
   moved[w] = -1;
@@ -150,7 +152,20 @@ __global__ void k_lrdmc_decide(DevSystem s, double *__restrict__ r, const double
     list_up[atomicAdd(cnt, 1)] = w * n + i;
   else
     list_dn[atomicAdd(cnt + 1, 1)] = w * n + (i - n);
-  atomicAdd(cnt + 2, 1);
+  list_w[atomicAdd(cnt + 2, 1)] = w;
+}
+
+// Per-walker arrays between the state and the compact state of this round's
+// moved walkers: gather dst[j] = src[list[j]], scatter dst[list[j]] = src[j],
+// in 4-byte words (every per-walker size is a multiple of 4 bytes).
+__global__ void __launch_bounds__(256) k_walker_copy(WalkerCopies cp, const int *__restrict__ list, int scatter) {
+  const int j = blockIdx.x, w = list[j];
+  for (int a = 0; a < cp.n; ++a) {
+    const size_t words = cp.c[a].bytes / 4;
+    const uint32_t *s = reinterpret_cast<const uint32_t *>(cp.c[a].src) + (size_t)(scatter ? j : w) * words;
+    uint32_t *d = reinterpret_cast<uint32_t *>(cp.c[a].dst) + (size_t)(scatter ? w : j) * words;
+    for (size_t t = threadIdx.x; t < words; t += blockDim.x) d[t] = s[t];
+  }
 }
 
 // Orbital values of each moved electron at its new position into the
@@ -272,7 +287,7 @@ cudaError_t launch_lrdmc_decide(const DevSystem &s, double *r, const double *eL,
   if (W <= 0) return cudaSuccess;
   k_lrdmc_decide<<<(W + 127) / 128, 128, 0, st>>>(s, r, lw.rho, eL, status, W, walker0, gen, a, gamma, e_ref,
                                                    max_hops, lw.left, lw.lw, lw.hops, lw.flags, lw.active, lw.moved,
-                                                   lw.list_up, lw.list_dn, lw.cnt);
+                                                   lw.list_up, lw.list_dn, lw.list_w, lw.cnt);
   return cudaGetLastError();
 }
 
@@ -280,6 +295,14 @@ cudaError_t launch_lrdmc_rows(const DevSystem &s, const double *r, const int *mo
                               int W, cudaStream_t st) {
   if (W <= 0) return cudaSuccess;
   k_lrdmc_rows<<<W, 128, 0, st>>>(s, r, moved, pprop, phi_up);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_walker_copy(const WalkerCopies &cp, const int *list, int Wc, bool scatter, cudaStream_t st) {
+  if (Wc <= 0) return cudaSuccess;
+  for (int a = 0; a < cp.n; ++a)
+    if (cp.c[a].bytes % 4) return cudaErrorInvalidValue;
+  k_walker_copy<<<Wc, 256, 0, st>>>(cp, list, scatter ? 1 : 0);
   return cudaGetLastError();
 }
 

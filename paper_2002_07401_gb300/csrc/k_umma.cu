@@ -457,7 +457,7 @@ cudaError_t launch_umma_gemm(const uint16_t *A, int m_max, const int *m_dev, int
                              long long ldo, const int *out_rows, int *err, cudaStream_t st, const int *a_exp,
                              const int *b_exp, float *out_lo, int bn_max, double *out64, int slice_bits,
                              int batch_rows, int batches, int stages_max, int b_batch_rows, long long o_bstride,
-                             long long o_rstride, long long o_cstride) {
+                             long long o_rstride, long long o_cstride, const int *pair_group) {
   if (m_max <= 0 || n <= 0) return cudaSuccess;
   if (kp <= 0 || kp % 64 != 0 || npairs < 1 || npairs > kMaxPairs || a_terms < 1 || b_terms < 1)
     return cudaErrorInvalidValue;
@@ -470,7 +470,10 @@ cudaError_t launch_umma_gemm(const uint16_t *A, int m_max, const int *m_dev, int
     if (pair_a[p] < 0 || pair_a[p] >= a_terms || pair_b[p] < 0 || pair_b[p] >= b_terms) return cudaErrorInvalidValue;
     g.pair_a[p] = pair_a[p];
     g.pair_b[p] = pair_b[p];
-    g.pair_group[p] = a_exp ? pair_a[p] + pair_b[p] : 0;
+    // fixed-point mode: the accumulator of weight 256^-(a + b), or the one the
+    // caller names (terms pre-scaled by powers of 256 share an accumulator)
+    g.pair_group[p] = a_exp ? (pair_group ? pair_group[p] : pair_a[p] + pair_b[p]) : 0;
+    if (g.pair_group[p] < 0 || g.pair_group[p] >= 8) return cudaErrorInvalidValue;
     if (g.pair_group[p] + 1 > g.ngroups) g.ngroups = g.pair_group[p] + 1;
   }
   if (g.ngroups > 8) return cudaErrorInvalidValue;
