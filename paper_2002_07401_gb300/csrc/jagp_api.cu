@@ -296,6 +296,7 @@ jagp_status_t run_local_energy(jagp_ctx *h, const double *r, void *state, int W,
                                cudaStream_t st, bool write_jastrow = false) {
   const Layout L = layout_of(h, W);
   if (std::is_same<T, float>::value) {
+    if (h->ds.use_j3) LAUNCH(0, 1, launch_j3_prep(h->ds, r, j3_vectors(h, L, state), W, st));
     const jagp_status_t s = run_kinetic_mixed(h, r, state, W, st);
     if (s != JAGP_OK) return s;
   } else {
@@ -308,7 +309,8 @@ jagp_status_t run_local_energy(jagp_ctx *h, const double *r, void *state, int W,
   }
   double *sc = write_jastrow ? at<double>(state, L.scal) : nullptr;
   if (std::is_same<T, float>::value)
-    LAUNCH(JAGP_KERNEL_ENERGY, 1, launch_elocal_dw(h->ds, r, at<double>(state, L.kin), eL, parts, W, st, sc));
+    LAUNCH(JAGP_KERNEL_ENERGY, 1,
+           launch_elocal_dw(h->ds, r, at<double>(state, L.kin), eL, parts, W, st, sc, j3_vectors(h, L, state)));
   else
     LAUNCH(JAGP_KERNEL_ENERGY, 1,
            launch_elocal(h->ds, r, at<double>(state, L.kin), eL, parts, W, st, sc, j3_vectors(h, L, state)));
@@ -693,10 +695,6 @@ jagp_status_t jagp_create(jagp_handle_t *out, const jagp_system_t *sys, const ja
   std::vector<double4> jgeo;
   std::vector<int> jinfo;
   if (sys->use_j3) {
-    if (opt->precision != JAGP_PREC_FP64) {
-      jagp_set_detail("the three-body Jastrow runs in the FP64 path only");
-      return JAGP_ERR_UNSUPPORTED;
-    }
     if (sys->n_jshells <= 0 || !sys->jshell_atom || !sys->jshell_l || !sys->jshell_radial || !sys->jshell_zeta ||
         !sys->j3_para || !sys->j3_anti)
       return JAGP_ERR_INVALID_ARG;
@@ -1739,8 +1737,9 @@ static jagp_status_t jagp_lrdmc_project_impl(jagp_handle_t h, double *d_r, void 
     jagp_set_detail("lattice-regularised DMC runs on FP64 handles without the three-body Jastrow");
     return JAGP_ERR_UNSUPPORTED;
   }
-  if ((size_t)h->ds.N * 3 * sizeof(double) > 48 * 1024) {
-    jagp_set_detail("N = %d: the hop-ratio kernel keeps a walker's positions in 48 KB of shared memory", h->ds.N);
+  if ((size_t)h->ds.N * 3 * 16 > 48 * 1024) {
+    jagp_set_detail("N = %d: the hop-ratio kernel keeps a walker's positions (FP64 and double-word) in 48 KB of "
+                    "shared memory (N <= 1024)", h->ds.N);
     return JAGP_ERR_UNSUPPORTED;
   }
   return lrdmc_project(h, d_r, d_state, W, walker0, generation, a, gamma, tau, e_ref, max_hops, d_weight, d_eL,

@@ -237,13 +237,13 @@ __device__ __forceinline__ DwDisp dw_displacement(const fdw p[3], float4 geo_hi,
   return d;
 }
 
-// the radial factor as a double-word (relative error ~2e-9)
+// the radial factor as a double-word (relative error a few units of 2^-46)
 __device__ __forceinline__ fdw radial_dw(int rad, fdw zeta, fdw r2) {
   return dw_exp_neg(dw_neg(dw_mul(zeta, rad ? dw_sqrt(r2) : r2)));
 }
 
 // FP32 path: the shell's values as double-words; v[c] (hi) is the value
-// rounded to FP32 (within half an ulp plus ~2e-9 relative), vlo[c] the rest.
+// rounded to FP32 (within half an ulp plus a few units of 2^-46), vlo[c] the rest.
 __device__ __forceinline__ int shell_values_dw(int info, fdw zeta, const DwDisp &d, float v[5], float vlo[5]) {
   const int l = shell_l(info);
   const fdw g = radial_dw(shell_rad(info), zeta, d.r2);

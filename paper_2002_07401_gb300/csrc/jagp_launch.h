@@ -96,7 +96,8 @@ cudaError_t launch_elocal(const DevSystem &s, const double *r, const double *kin
                           const double *j3buf = nullptr);
 // the FP32 path's version (double-word distances, Coulomb sums and Jastrow values)
 cudaError_t launch_elocal_dw(const DevSystem &s, const double *r, const double *kin, double *eL,
-                             double *parts, int W, cudaStream_t st, double *scal = nullptr);
+                             double *parts, int W, cudaStream_t st, double *scal = nullptr,
+                             const double *j3buf = nullptr);
 
 // zero the per-walker counters; status = JAGP_WS_NONFINITE for a walker with a
 // non-finite coordinate in r [W][N][3] (when r is given), else 0

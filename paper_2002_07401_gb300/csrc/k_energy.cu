@@ -403,7 +403,8 @@ __global__ void __launch_bounds__(128) k_elocal(DevSystem s, const double *__res
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(128) k_elocal_dw(DevSystem s, const double *__restrict__ r,
                                                    const double *__restrict__ kin, double *__restrict__ eL,
-                                                   double *__restrict__ parts, double *__restrict__ scal) {
+                                                   double *__restrict__ parts, double *__restrict__ scal,
+                                                   const double *__restrict__ j3buf) {
   const int w = blockIdx.x, N = s.N, tid = threadIdx.x, na = s.n_atoms;
   const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   extern __shared__ float sf[];
@@ -524,6 +525,20 @@ __global__ void __launch_bounds__(128) k_elocal_dw(DevSystem s, const double *__
       gJz = dw_add(gJz, fdw{__shfl_xor_sync(0xffffffffu, gJz.hi, o), __shfl_xor_sync(0xffffffffu, gJz.lo, o)});
       lJ = dw_add(lJ, fdw{__shfl_xor_sync(0xffffffffu, lJ.hi, o), __shfl_xor_sync(0xffffffffu, lJ.lo, o)});
     }
+    if (s.use_j3 && j3buf) {
+      // three/four-body Jastrow of this electron in FP64 on one lane (its
+      // value to J, gradient and Laplacian to the Jastrow sums of every lane)
+      double v3 = 0.0, g3[3] = {0.0, 0.0, 0.0}, l3 = 0.0;
+      if (lane == 0) {
+        const double *pr = r + ((size_t)w * N + e) * 3;
+        j3_electron(s, j3buf + (size_t)w * 6 * s.LJ, eup, pr[0], pr[1], pr[2], &v3, g3, &l3);
+        jv = dw_add(jv, dw_of(v3));
+      }
+      gJx = dw_add(gJx, dw_of(__shfl_sync(0xffffffffu, g3[0], 0)));
+      gJy = dw_add(gJy, dw_of(__shfl_sync(0xffffffffu, g3[1], 0)));
+      gJz = dw_add(gJz, dw_of(__shfl_sync(0xffffffffu, g3[2], 0)));
+      lJ = dw_add(lJ, dw_of(__shfl_sync(0xffffffffu, l3, 0)));
+    }
     if (lane == slot) {
       kx = gJx;
       ky = gJy;
@@ -579,10 +594,11 @@ __global__ void __launch_bounds__(128) k_elocal_dw(DevSystem s, const double *__
 }
 
 cudaError_t launch_elocal_dw(const DevSystem &s, const double *r, const double *kin, double *eL, double *parts, int W,
-                             cudaStream_t st, double *scal) {
+                             cudaStream_t st, double *scal, const double *j3buf) {
   if (W <= 0) return cudaSuccess;
+  if (s.use_j3 && !j3buf) return cudaErrorInvalidValue;
   const size_t smem = ((size_t)(s.N + s.n_atoms) * 6 + (size_t)s.n_atoms * 8) * sizeof(float);
-  k_elocal_dw<<<W, 128, smem, st>>>(s, r, kin, eL, parts, scal);
+  k_elocal_dw<<<W, 128, smem, st>>>(s, r, kin, eL, parts, scal, j3buf);
   return cudaGetLastError();
 }
 

@@ -28,41 +28,121 @@ namespace {
 
 constexpr int kRatioThreads = 128;
 
-// rho[w][k] for every hop of every walker still active: one CTA per walker,
-// one warp per hop in turn (lanes over shells, atoms and electrons).
+// warp-wide double-word sum; dw_add is commutative, so every lane of the
+// butterfly ends with the same value
+__device__ __forceinline__ fdw warp_sum_dw(fdw v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const fdw u{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+    v = dw_add(v, u);
+  }
+  return v;
+}
+
+__device__ __forceinline__ fdw dw_dist(const fdw *p, const fdw *q) {
+  const fdw dx = dw_add(p[0], dw_neg(q[0])), dy = dw_add(p[1], dw_neg(q[1])), dz = dw_add(p[2], dw_neg(q[2]));
+  return dw_sqrt(dw_add(dw_add(dw_mul(dx, dx), dw_mul(dy, dy)), dw_mul(dz, dz)));
+}
+
+// one-body term of one atom, -c^3 u(c r), u(s) = (1 - e^{-b s}) / (2b) (s / 2 at b = 0)
+__device__ __forceinline__ fdw j1_term_dw(fdw c, fdw mc3, fdw b, fdw inv2b, bool b0, fdw r) {
+  const fdw sc = dw_mul(c, r);
+  const fdw u = b0 ? dw_mul_f(sc, 0.5f) : dw_mul(dw_add_f(dw_neg(dw_exp_neg(dw_neg(dw_mul(b, sc)))), 1.0f), inv2b);
+  return dw_mul(mc3, u);
+}
+
+// pair term r / (k (1 + b r)), 1/k = kinv (a power of two)
+__device__ __forceinline__ fdw j2_term_dw(fdw b, float kinv, fdw r) {
+  return dw_mul_f(dw_mul(r, dw_recip(dw_add_f(dw_mul(b, r), 1.0f))), kinv);
+}
+
+// rho[w][k] for every hop of every walker still active: one CTA per walker, a
+// warp per electron and its six hops (lanes over shells, atoms and electrons),
+// in double-word FP32 arithmetic (relative error a few units of 2^-46; FP64
+// instructions only to convert M, the positions and the atoms): GB300 issues
+// FP32 at ~64x its FP64 rate, and the 6N orbital evaluations per walker and
+// round are the bulk of the ratio work.
 __global__ void __launch_bounds__(kRatioThreads) k_lrdmc_ratios(DevSystem s, const double *__restrict__ r,
                                                                  const double *__restrict__ mbuf,
                                                                  const int *__restrict__ active, double a,
                                                                  double *__restrict__ rho) {
-  extern __shared__ double xs[];  // the walker's positions [N][3]
+  extern __shared__ double xs[];                         // the walker's positions [N][3]
+  fdw *xd = reinterpret_cast<fdw *>(xs + 3 * s.N);       // the same as double-words
   const int w = blockIdx.x, N = s.N, L = s.L;
   if (!active[w]) return;
-  for (int t = threadIdx.x; t < 3 * N; t += kRatioThreads) xs[t] = r[(size_t)w * N * 3 + t];
+  for (int t = threadIdx.x; t < 3 * N; t += kRatioThreads) {
+    const double v = r[(size_t)w * N * 3 + t];
+    xs[t] = v;
+    xd[t] = dw_of(v);
+  }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int k = warp; k < 6 * N; k += kRatioThreads / 32) {
-    const int i = k / 6, d = (k % 6) / 2;
+  const bool b0 = s.b_ea == 0.0;
+  const fdw bea = dw_of(s.b_ea), inv2b = dw_of(b0 ? 0.0 : 0.5 / s.b_ea);
+  for (int i = warp; i < N; i += kRatioThreads / 32) {
     const double *o = xs + 3 * i;
-    double p[3] = {o[0], o[1], o[2]};
-    p[d] = (k & 1) ? o[d] - a : o[d] + a;
+    const fdw *od = xd + 3 * i;
+    fdw pd[6][3];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const int d = k / 2;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) pd[k][q] = q == d ? dw_of((k & 1) ? o[d] - a : o[d] + a) : od[q];
+    }
+    fdw dot[6], dj[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) dot[k] = dj[k] = fdw{0.0f, 0.0f};
     const double *Mi = mbuf + ((size_t)w * N + i) * L;
-    double dot = 0.0;
     for (int sh = lane; sh < s.n_shells; sh += 32) {
-      const double4 g = s.shell_geo[sh];
-      const int info = s.shell_info[sh], off = shell_off(info);
-      double v[5];
-      const int nc = shell_values(info, g.w, p[0] - g.x, p[1] - g.y, p[2] - g.z, v);
-      for (int c = 0; c < nc; ++c) dot = fma(v[c], Mi[off + c], dot);
+      const float4 gh = s.shell_dw[2 * sh], gl = s.shell_dw[2 * sh + 1];
+      const int info = s.shell_info[sh], off = shell_off(info), nc = 2 * shell_l(info) + 1;
+      fdw m[5];
+#pragma unroll
+      for (int c = 0; c < 5; ++c) m[c] = c < nc ? dw_of(Mi[off + c]) : fdw{0.0f, 0.0f};
+      const fdw zeta{gh.w, gl.w};
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        const DwDisp dd = dw_displacement(pd[k], gh, gl);
+        float v[5], vl[5];
+        shell_values_dw(info, zeta, dd, v, vl);
+#pragma unroll
+        for (int c = 0; c < 5; ++c)
+          if (c < nc) dot[k] = dw_add(dot[k], dw_mul(fdw{v[c], vl[c]}, m[c]));
+      }
     }
-    dot = warp_sum(dot);
-    double dj = s.use_j1 ? j1_move_change(s, p, o, lane) : 0.0;
+    if (s.use_j1) {
+      for (int at = lane; at < s.n_atoms; at += 32) {
+        const fdw R[3] = {dw_of(s.R[3 * at]), dw_of(s.R[3 * at + 1]), dw_of(s.R[3 * at + 2])};
+        const double c = s.c1[at];
+        const fdw cd = dw_of(c), mc3 = dw_of(-c * c * c);
+        const fdw f0 = j1_term_dw(cd, mc3, bea, inv2b, b0, dw_dist(od, R));
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+          dj[k] = dw_add(dj[k], dw_add(j1_term_dw(cd, mc3, bea, inv2b, b0, dw_dist(pd[k], R)), dw_neg(f0)));
+      }
+    }
     if (s.use_j2) {
-      const double j2 = i < s.n_up ? j2_move_change<double, true>(s, xs, i, p[0], p[1], p[2], o[0], o[1], o[2], lane, 32)
-                                   : j2_move_change<double, false>(s, xs, i, p[0], p[1], p[2], o[0], o[1], o[2],
-                                                                   lane, 32);
-      dj += warp_sum(j2);
+      const bool up = i < s.n_up;
+      for (int q = lane; q < N; q += 32) {
+        if (q == i) continue;
+        double kk, bb;
+        j2_params(s, (q < s.n_up) == up, &kk, &bb);
+        const fdw b = dw_of(bb);
+        const float kinv = kk == 4.0 ? 0.25f : 0.5f;
+        const fdw f0 = j2_term_dw(b, kinv, dw_dist(od, xd + 3 * q));
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+          dj[k] = dw_add(dj[k], dw_add(j2_term_dw(b, kinv, dw_dist(pd[k], xd + 3 * q)), dw_neg(f0)));
+      }
     }
-    if (lane == 0) rho[(size_t)w * 6 * N + k] = dot * exp(dj);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const fdw dk = warp_sum_dw(dot[k]), jk = warp_sum_dw(dj[k]);
+      if (lane == k)
+        rho[(size_t)w * 6 * N + 6 * i + k] =
+            (static_cast<double>(dk.hi) + static_cast<double>(dk.lo)) *
+            exp(static_cast<double>(jk.hi) + static_cast<double>(jk.lo));
+    }
   }
 }
 
@@ -269,7 +349,7 @@ __global__ void k_lrdmc_energy(const double *__restrict__ wbar, const double *__
 cudaError_t launch_lrdmc_ratios(const DevSystem &s, const double *r, const double *mbuf, const int *active, double a,
                                 double *rho, int W, cudaStream_t st) {
   if (W <= 0) return cudaSuccess;
-  const size_t smem = (size_t)s.N * 3 * sizeof(double);
+  const size_t smem = (size_t)s.N * 3 * (sizeof(double) + sizeof(fdw));
   if (smem > 48 * 1024) return cudaErrorInvalidValue;
   k_lrdmc_ratios<<<W, kRatioThreads, smem, st>>>(s, r, mbuf, active, a, rho);
   return cudaGetLastError();

@@ -207,6 +207,14 @@ __device__ __forceinline__ double accept_prob(double pr, double pj) {
   return pr * pr * exp(2.0 * pj);
 }
 
+template <typename T>
+__host__ __device__ inline size_t metro_smem_per_walker(int n, int N) {
+  // positions (FP64), G~^{-1}, three n-vectors, and in the mixed path the FP32
+  // mirror of the positions
+  const size_t mirror = std::is_same<T, float>::value ? (size_t)N * 3 * sizeof(float) : 0;
+  return ((size_t)N * 3 * sizeof(double) + (size_t)(n * n + 3 * n) * sizeof(T) + mirror + 15) & ~size_t(15);
+}
+
 template <bool UP, typename T, bool GLOB>
 __global__ void __launch_bounds__(512) k_metropolis(DevSystem s, double *__restrict__ r,
                                                     const double *__restrict__ rprop,
@@ -232,11 +240,12 @@ __global__ void __launch_bounds__(512) k_metropolis(DevSystem s, double *__restr
   T *cc = vv + n;                                   // n
   float *xf = reinterpret_cast<float *>(cc + n);    // mixed path: N * 3 positions rounded to FP32
   constexpr bool kF32 = std::is_same<T, float>::value;
-  // three-body Jastrow (FP64 path, G~^{-1} in shared memory): the walker's j3
-  // vectors [6][LJ] and chi at the old and the proposed position, chi change
-  const bool j3 = !kF32 && !GLOB && s.use_j3 && j3buf;
+  // three-body Jastrow (G~^{-1} in shared memory; its change in FP64 in both
+  // paths): the walker's j3 vectors [6][LJ] and chi at the old and the
+  // proposed position, chi change, after the per-walker block
+  const bool j3 = !GLOB && s.use_j3 && j3buf;
   const int LJ = s.LJ;
-  double *j3v = reinterpret_cast<double *>(cc + n);  // 6 LJ (no FP32 mirror in the FP64 path)
+  double *j3v = reinterpret_cast<double *>(reinterpret_cast<char *>(sm) + metro_smem_per_walker<T>(n, N));
   double *chi_o = j3v + 6 * LJ, *chi_n = chi_o + LJ, *dchi = chi_n + LJ;
   if (j3)
     for (int t = tid; t < 6 * LJ; t += bs) j3v[t] = j3buf[(size_t)w * 6 * LJ + t];
@@ -659,13 +668,6 @@ cudaError_t launch_metropolis_guided(const DevSystem &s, bool up, double *r, con
 constexpr int kMetroWarps = 4;
 constexpr size_t kMetroSmemMax = 200 * 1024;  // G~^{-1} kept in shared memory up to this footprint
 
-template <typename T>
-__host__ __device__ inline size_t metro_smem_per_walker(int n, int N) {
-  // positions (FP64), G~^{-1}, three n-vectors, and in the mixed path the FP32
-  // mirror of the positions
-  const size_t mirror = std::is_same<T, float>::value ? (size_t)N * 3 * sizeof(float) : 0;
-  return ((size_t)N * 3 * sizeof(double) + (size_t)(n * n + 3 * n) * sizeof(T) + mirror + 15) & ~size_t(15);
-}
 
 template <bool UP, typename T>
 __global__ void __launch_bounds__(kMetroWarps * 32) k_metropolis_warp(
@@ -797,8 +799,7 @@ cudaError_t launch_metropolis(const DevSystem &s, bool up, double *r, const doub
   if (m_end < 0) m_end = up ? s.n_up : s.n_dn;
   if (m_begin >= m_end) return cudaSuccess;
   const int n = s.n_up;
-  const bool j3 = s.use_j3 && std::is_same<T, double>::value;
-  if (j3) {
+  if (s.use_j3) {
     // the three-body Jastrow's change is formed in the CTA-per-walker kernel
     const size_t per3 = metro_smem_per_walker<T>(n, s.N) + (size_t)9 * s.LJ * sizeof(double);
     if (!j3buf || per3 > kMetroSmemMax) return cudaErrorInvalidValue;

@@ -1,8 +1,9 @@
-"""GPU parity of the three/four-body Jastrow factor (Eq. threebody_jastrow,
-FP64 path): log|Psi| and e_L element by element, and Metropolis trajectories
+"""GPU parity of the three/four-body Jastrow factor (Eq. threebody_jastrow):
+FP64 path: log|Psi| and e_L element by element, and Metropolis trajectories
 move by move (the sequential acceptance keeps the spin sums of the Jastrow
 basis and their products with the couplings), against the oracle's plain
-pair sums."""
+pair sums.  Mixed path: log|Psi| and e_L within its stated targets (1e-6,
+1e-5 Ha) at seeded configurations and after sweeps."""
 import numpy as np
 import pytest
 
@@ -81,8 +82,6 @@ def test_j3_unsupported_paths(torch_cuda):
     torch = torch_cuda
     import paper_2002_07401_gb300 as pg
     sysm = SYSTEMS["small-unpaired"]()
-    with pytest.raises(pg.JagpError, match="unsupported"):
-        pg.JAGP(sysm, 4, precision=pg.JAGP_PREC_MIXED)
     g = pg.JAGP(sysm, 4)
     r = g.positions(synth.init_walkers(sysm, 4, seed=1))
     g.eval(r)
@@ -93,4 +92,36 @@ def test_j3_unsupported_paths(torch_cuda):
     la = torch.empty(4, dtype=torch.float64, device="cuda")
     with pytest.raises(pg.JagpError, match="three-body"):
         pg.jagp_eval_noalloc(g.h, r, 4, la, None)
+    g.close()
+
+
+@pytest.mark.parametrize("name", list(SYSTEMS))
+def test_j3_mixed_path(torch_cuda, name):
+    """The mixed path with the three-body Jastrow (its change in FP64 in the
+    acceptance kernel, its value, gradient and Laplacian in FP64 in the
+    double-word local energy): log|Psi| and e_L at seeded configurations,
+    then after two sweeps at the walkers' final positions, against the oracle
+    within 1e-6 and 1e-5 Ha."""
+    import paper_2002_07401_gb300 as pg
+    sysm = SYSTEMS[name]()
+    W = 8
+    x = synth.jitter_walkers(synth.init_walkers(sysm, W, seed=2), 3, 0.3)
+    o = oracle.Oracle(sysm)
+    g = pg.JAGP(sysm, W, precision=pg.JAGP_PREC_MIXED, seed=4)
+    r = g.positions(x)
+    la, sg = g.eval(r)
+    e = g.local_energy(r).cpu().numpy()
+    la_ref, sg_ref = o.logpsi_batch(x)
+    e_ref = o.local_energy_batch(x)
+    assert np.array_equal(sg.cpu().numpy(), sg_ref)
+    assert np.abs(la.cpu().numpy() - la_ref).max() <= 1e-6
+    assert np.abs(e - e_ref).max() <= 1e-5, np.abs(e - e_ref).max()
+    eL, acc = g.sweep(r, 2, acc=True)
+    assert g.status() & (pg.WS_NONFINITE | pg.WS_SINGULAR) == 0
+    assert acc.cpu().numpy()[:, 2].sum() > 0
+    xf = np.ascontiguousarray(r.cpu().numpy())
+    la_ref, _ = o.logpsi_batch(xf)
+    e_ref = o.local_energy_batch(xf)
+    assert np.abs(g.info()["logabs"].cpu().numpy() - la_ref).max() <= 1e-6
+    assert np.abs(eL.cpu().numpy()[-1] - e_ref).max() <= 1e-5
     g.close()
