@@ -384,8 +384,9 @@ typedef struct {
   int umma_bn_right;   /* mixed path: tensor-core tile width, Bt = lambda phi */
   float ms[4];
   int umma_stages_left;   /* pipeline stages of those products (0: as many as fit in 200 KB;
-                             -1: chunk-major, two stages each holding every slice of one
-                             64-wide K chunk, so that a slice is read once for all its pairs) */
+                             -1, -2, -3: chunk-major, two to four stages each holding every
+                             slice of one K chunk of 64, 32 or 16 elements, so that a slice
+                             is read once for all its pairs) */
   int umma_stages_right;
 } jagp_tuning_t;
 jagp_status_t jagp_autotune(jagp_handle_t h, void *d_state, int W, jagp_tuning_t *out, void *stream);
@@ -394,10 +395,10 @@ jagp_status_t jagp_autotune(jagp_handle_t h, void *d_state, int W, jagp_tuning_t
  * CUDA call; ms is ignored.  tile_proposals / tile_refresh: -1 (the shape
  * heuristics), 0, 32 or 64, and 16 for tile_refresh in the mixed path with
  * N_up <= 16.  umma_*: 0 without tensor-core lambda products (FP64 without
- * fp64_tensor_cores); else bn 0 (heuristic) or a multiple of 16 up to 96 in
- * the mixed path (five accumulators) and 64 in the FP64-equivalent one, and
- * stages -1 (chunk-major, only where two such stages fit in shared memory,
- * which the mixed path's 6 + 12 slice terms never do), 0 or 2..6.
+ * fp64_tensor_cores); else bn 0 (heuristic) or a multiple of 16 up to 64 (six
+ * or more tensor-memory accumulators), and stages -1, -2, -3 (chunk-major with
+ * K chunks of 64, 32, 16, only where two such stages fit in shared memory), 0
+ * or 2..6.
  * Every choice changes the tiling only, so results stay as without tuning.
  * Returns JAGP_ERR_INVALID_ARG (and keeps the earlier choices) on any other value. */
 jagp_status_t jagp_set_tuning(jagp_handle_t h, const jagp_tuning_t *t);

@@ -83,19 +83,6 @@ Layout layout_of(const jagp_ctx *h, int W) {
 // numbers; the kinetic term amplifies their relative error by about cond(G~).
 const int kPairA[kFixedPairs] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3, 0, 1, 2, 3, 4, 0, 1, 2, 3, 4, 5};
 const int kPairB[kFixedPairs] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0, 4, 3, 2, 1, 0, 5, 4, 3, 2, 1, 0};
-// The lambda products take the same pairs with five accumulators instead of
-// six: the sliced lambda carries its six slices (terms 0..5) and copies scaled
-// by 2^-8 (terms 6..11), exact in BF16, so that the pairs of weight 256^-5 add
-// into the accumulator of weight 256^-4.  That accumulator's FP32 rounding
-// (about 2^-24 of its partial sums at every step along K) stays near 2^-48 of
-// the result, the precision of the six slices; merging one weight further
-// down (into 256^-3) measurably raised the error at an ill-conditioned
-// configuration.  Five accumulators leave room for 96-column tiles in tensor
-// memory (six: 64).
-constexpr int kLamTerms = 2 * kFixedSlices;
-const int kLamPairB[kFixedPairs] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0, 4, 3, 2, 1, 0, 11, 10, 9, 8, 7, 6};
-const int kLamGroup[kFixedPairs] = {0, 1, 1, 2, 2, 2, 3, 3, 3, 3, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4};
-constexpr int kLamBnMax = 96;  // tile width limit of the lambda products (five accumulators)
 
 // all slice pairs (a, b) with a + b < nsl, ordered by a + b, then a
 int slice_pairs(int nsl, int *pa, int *pb) {
@@ -137,21 +124,6 @@ int slice_row_fixed(const double *v, size_t vstride, int L, uint16_t *dst, size_
     }
   }
   return e;
-}
-
-// terms nsl..2nsl-1 of a sliced row: its slices times 2^-8 (exact: BF16 keeps
-// the 8-bit integers' bits, only the exponent moves)
-void scaled_slice_copies(uint16_t *row, size_t kp, int nsl) {
-  for (int t = 0; t < nsl; ++t)
-    for (size_t k = 0; k < kp; ++k) {
-      uint32_t u = static_cast<uint32_t>(row[t * kp + k]) << 16;
-      float f;
-      memcpy(&f, &u, 4);
-      const float g = std::ldexp(f, -8);
-      uint32_t v;
-      memcpy(&v, &g, 4);
-      row[(nsl + t) * kp + k] = static_cast<uint16_t>(v >> 16);
-    }
 }
 
 jagp_status_t check_walkers(const jagp_ctx *h, int W, const void *state) {
@@ -210,10 +182,10 @@ jagp_status_t lambda_products(jagp_ctx *h, const float *P, const float *P_lo, fl
   float *out_lo = at<float>(state, left ? L.a_up_lo : L.bt_lo);
   LAUNCH(JAGP_KERNEL_LAMBDA_ROWS, 1,
          launch_umma_gemm(pack, max_rows, count, kFixedSlices, left ? h->split_lamT : h->split_lam, h->ds.L,
-                          kLamTerms, h->kp, kFixedPairs, kPairA, kLamPairB, out, h->ds.L,
+                          kFixedSlices, h->kp, kFixedPairs, kPairA, kPairB, out, h->ds.L,
                           rows, h->d_err, st, exps, left ? h->exp_lamT : h->exp_lam, out_lo,
                           left ? h->tune_bn_left : h->tune_bn_right, nullptr, 8, 0, 0,
-                          left ? h->tune_st_left : h->tune_st_right, 0, 0, 0, 0, kLamGroup));
+                          left ? h->tune_st_left : h->tune_st_right));
   return JAGP_OK;
 }
 
@@ -484,7 +456,13 @@ struct GradLayout {
   size_t jg, kbar, dnphi, h1, h2, gbar, btbar, abar, phibar_a, phibar_b, phibar_dn, part, rbar, rbar_at, jpar, eL,
       lam_part, total;
   int nparts, nz;
+  // lambda-bar on the tensor cores (FP64-equivalent handles, N_dn = N_up):
+  // segments of seg_w walkers (seg_w N_up <= 2048 rows of K each), the packed
+  // columns of both operands, their exponents and the per-segment products
+  int tc_lam, seg_w, nseg, kpseg;
+  size_t tc_u, tc_v, tc_eu, tc_ev, tc_part;
 };
+constexpr int kLamBarSlices = 8, kLamBarBits = 7;  // 7-bit slices: K <= 2048 sums stay below 2^24
 GradLayout grad_layout(const jagp_ctx *h, int W) {
   const size_t w = (size_t)W, n = h->ds.n_up, N = h->ds.N, L = h->ds.L, na = h->ds.n_atoms;
   GradLayout g;
@@ -510,6 +488,16 @@ GradLayout grad_layout(const jagp_ctx *h, int W) {
   g.jpar = take(w * 3 * 8);
   g.eL = take(w * 8);
   g.lam_part = take((size_t)g.nz * L * L * 8);
+  g.tc_lam = h->tc_lambda && h->ds.n_dn == h->ds.n_up && n > 0;
+  g.seg_w = g.tc_lam ? (int)std::max<size_t>(1, 2048 / n) : 0;
+  g.nseg = g.tc_lam ? 2 * ((W + g.seg_w - 1) / g.seg_w) : 0;
+  g.kpseg = g.tc_lam ? (int)((g.seg_w * n + 63) / 64 * 64) : 0;
+  const size_t pk = g.tc_lam ? (size_t)g.nseg * L * kLamBarSlices * g.kpseg * 2 : 0;
+  g.tc_u = take(pk);
+  g.tc_v = take(pk);
+  g.tc_eu = take(g.tc_lam ? (size_t)g.nseg * L * 4 : 0);
+  g.tc_ev = take(g.tc_lam ? (size_t)g.nseg * L * 4 : 0);
+  g.tc_part = take(g.tc_lam ? (size_t)g.nseg * L * L * 8 : 0);
   g.total = o;
   return g;
 }
@@ -603,10 +591,46 @@ static jagp_status_t jagp_grad_impl(jagp_handle_t h, const double *d_r, void *d_
          launch_adj_jastrow(d, d_r, d_seed_logpsi, d_seed_eL, wp(G.jg), at<double>(d_state, L.kin), wp(G.rbar),
                             wp(G.rbar_at), wp(G.jpar), W, st));
   LAUNCH(0, 1, launch_adj_reduce(wp(G.part), G.nparts, d.n_atoms, wp(G.rbar_at), wp(G.jpar), W, d_dR, d_djas, st));
-  if (d_dlambda)
+  if (d_dlambda && G.tc_lam) {
+    // lambda-bar = sum over rows of U^T V with (U, V) = (Btbar, dnphi) and
+    // (phi_up, Abar) on the tensor cores: the columns of each segment of
+    // seg_w walkers cut into eight exact 7-bit slices (K <= 2048 per segment,
+    // so every accumulator sum stays exact), the per-segment FP64 products,
+    // then their sum in segment order
+    uint16_t *pu = reinterpret_cast<uint16_t *>(wk + G.tc_u), *pv = reinterpret_cast<uint16_t *>(wk + G.tc_v);
+    int *eu = reinterpret_cast<int *>(wk + G.tc_eu), *ev = reinterpret_cast<int *>(wk + G.tc_ev);
+    const int full = W / G.seg_w, rest = W - full * G.seg_w, per = G.nseg / 2;
+    const size_t segk = (size_t)Lb * kLamBarSlices * G.kpseg;  // packed elements per segment
+    const double *U[2] = {wp(G.btbar), at<double>(d_state, L.phi_up)}, *V[2] = {dnphi, wp(G.abar)};
+    for (int set = 0; set < 2; ++set) {
+      const size_t s0 = (size_t)set * per;
+      const size_t xw = (size_t)G.seg_w * n * Lb;  // elements per segment of the [W][n][L] tables
+      for (int part = 0; part < 2; ++part) {
+        const int segs = part == 0 ? full : (rest > 0 ? 1 : 0);
+        if (segs == 0) continue;
+        const int rows = (part == 0 ? G.seg_w : rest) * n;
+        const size_t sg = s0 + (part == 0 ? 0 : full);
+        const size_t src = (part == 0 ? 0 : (size_t)full * xw);
+        LAUNCH(0, 1,
+               launch_pack_cols(U[set] + src, nullptr, nullptr, xw, rows, Lb, G.kpseg, segs, pu + sg * segk,
+                                eu + sg * Lb, nullptr, 0, 0, st, kLamBarSlices, kLamBarBits));
+        LAUNCH(0, 1,
+               launch_pack_cols(V[set] + src, nullptr, nullptr, xw, rows, Lb, G.kpseg, segs, pv + sg * segk,
+                                ev + sg * Lb, nullptr, 0, 0, st, kLamBarSlices, kLamBarBits));
+      }
+    }
+    int pa[kMaxPairs], pb[kMaxPairs];
+    const int np = slice_pairs(kLamBarSlices, pa, pb);
+    LAUNCH(JAGP_KERNEL_LAMBDA_ROWS, 1,
+           launch_umma_gemm(pu, G.nseg * Lb, nullptr, kLamBarSlices, pv, Lb, kLamBarSlices, G.kpseg, np, pa, pb,
+                            nullptr, 0, nullptr, h->d_err, st, eu, ev, nullptr, 0, wp(G.tc_part), kLamBarBits, Lb,
+                            G.nseg, 0, Lb, (long long)Lb * Lb, Lb, 1));
+    LAUNCH(0, 1, launch_adj_lambda_sum(wp(G.tc_part), G.nseg, Lb, d_dlambda, st));
+  } else if (d_dlambda) {
     LAUNCH(0, 1,
            launch_adj_lambda(wp(G.btbar), dnphi, at<double>(d_state, L.phi_up), wp(G.abar), W, n, nd, Lb,
                              wp(G.lam_part), G.nz, d_dlambda, st));
+  }
   if (d_dr) JAGP_CU(cudaMemcpyAsync(d_dr, wp(G.rbar), (size_t)W * N * 3 * 8, cudaMemcpyDeviceToDevice, st));
   if (d_dR_walker)
     JAGP_CU(cudaMemcpyAsync(d_dR_walker, wp(G.rbar_at), (size_t)W * d.n_atoms * 3 * 8, cudaMemcpyDeviceToDevice, st));
@@ -752,11 +776,10 @@ jagp_status_t jagp_create(jagp_handle_t *out, const jagp_system_t *sys, const ja
   const bool tc64 = !mixed && opt->fp64_tensor_cores != 0;
   const bool tc = mixed || tc64;
   const int kp = (L + 63) / 64 * 64;
-  // slices per element: mixed 6 x 8 bits (stored with their copies scaled by
-  // 2^-8, 12 terms); FP64-equivalent 7 x 8 bits, or 8 x 7 bits when
-  // L > 512 so that the leading accumulators stay exact
+  // slices per element: mixed 6 x 8 bits; FP64-equivalent 7 x 8 bits, or 8 x 7
+  // bits when L > 512 so that the leading accumulators stay exact
   const int nsl = mixed ? kFixedSlices : (tc64 ? (L <= 512 ? 7 : 8) : 0);
-  const int nterms = mixed ? kLamTerms : nsl;
+  const int nterms = nsl;
   const int bits = tc64 && L > 512 ? 7 : 8;
   const size_t split_bytes = tc ? (size_t)L * nterms * kp * 2 : 0;
   const size_t exp_bytes = tc ? (size_t)L * 4 : 0;
@@ -772,10 +795,6 @@ jagp_status_t jagp_create(jagp_handle_t *out, const jagp_system_t *sys, const ja
       uint16_t *ra = &sA[(size_t)nn * nterms * kp], *rb = &sB[(size_t)nn * nterms * kp];
       xA[nn] = slice_row_fixed(sys->lambda + nn, (size_t)L, L, ra, (size_t)kp, nsl, bits);
       xB[nn] = slice_row_fixed(sys->lambda + (size_t)nn * L, 1, L, rb, (size_t)kp, nsl, bits);
-      if (mixed) {
-        scaled_slice_copies(ra, (size_t)kp, nsl);
-        scaled_slice_copies(rb, (size_t)kp, nsl);
-      }
     }
   }
   std::vector<float4> atom_f(na);
@@ -978,19 +997,18 @@ jagp_status_t tune_products(jagp_ctx *h, void *state, int W, cudaStream_t st, ja
     // tile widths; 16 lets several CTAs share an SM's tensor memory (6 x 16 columns each)
     const int cands[7] = {16, 32, 48, 64, 80, 96, 128};
     // stages: as many as fit (one CTA per SM), three or two (several CTAs per SM),
-    // or chunk-major (-1: every slice of a K chunk per stage, each loaded once
-    // for all pairs; two stages, where they fit)
-    const int stages[4] = {0, 3, 2, -1};
+    // or chunk-major (every slice of a K chunk of 64, 32 or 16 per stage, each
+    // loaded once for all pairs; two to four stages, where they fit)
+    const int stages[6] = {0, 3, 2, -1, -2, -3};
     const int npairs = f64 ? np64 : kFixedPairs;
-    const int *tpa = f64 ? pa64 : kPairA, *tpb = f64 ? pb64 : kLamPairB;
-    // accumulators of bn columns in tensor memory: five (mixed) or up to eight
-    const int limit = f64 ? 64 : kLamBnMax;
+    const int *tpa = f64 ? pa64 : kPairA, *tpb = f64 ? pb64 : kPairB;
+    const int limit = 64;  // six or more accumulators of bn columns in tensor memory
     float bs = 0.0f;
     int bbn = 0, bst = 0;
     for (int c = 0; c < 7; ++c)
-      for (int q = 0; q < 4; ++q) {
+      for (int q = 0; q < 6; ++q) {
         if (cands[c] > limit) continue;
-        if (stages[q] < 0 && !umma_chunk_fits(npairs, tpa, tpb, cands[c])) continue;
+        if (stages[q] < 0 && !umma_chunk_fits(npairs, tpa, tpb, cands[c], stages[q])) continue;
         float ms = 0.0f;
         JAGP_CU(time_calls(
             [&] {
@@ -1001,10 +1019,10 @@ jagp_status_t tune_products(jagp_ctx *h, void *state, int W, cudaStream_t st, ja
                                         exps, left ? h->exp_lamT : h->exp_lam, nullptr, cands[c],
                                         reinterpret_cast<double *>(dst), h->tc_bits, 0, 0, stages[q]);
               return launch_umma_gemm(pack, rows, nullptr, kFixedSlices, left ? h->split_lamT : h->split_lam, Lb,
-                                      kLamTerms, h->kp, kFixedPairs, kPairA, kLamPairB,
+                                      kFixedSlices, h->kp, kFixedPairs, kPairA, kPairB,
                                       reinterpret_cast<float *>(dst), Lb, nullptr, h->d_err, st, exps,
                                       left ? h->exp_lamT : h->exp_lam, at<float>(state, left ? L.a_up_lo : L.bt_lo),
-                                      cands[c], nullptr, 8, 0, 0, stages[q], 0, 0, 0, 0, kLamGroup);
+                                      cands[c], nullptr, 8, 0, 0, stages[q]);
             },
             st, &ms));
         if (bbn == 0 || ms < bs) {
@@ -1061,13 +1079,13 @@ static jagp_status_t jagp_set_tuning_impl(jagp_handle_t h, const jagp_tuning_t *
     const int np64 = slice_pairs(h->tc_slices, pa64, pb64);
     for (int side = 0; side < 2; ++side) {
       const bool left = side == 0;
-      // five accumulators (mixed) or up to eight (FP64-equivalent) of bn columns in tensor memory
-      const int limit = mixed ? kLamBnMax : 64;
+      // six (mixed) or up to eight (FP64-equivalent) accumulators of bn columns in tensor memory
+      const int limit = 64;
       if (bn[side] < 0 || bn[side] % 16 || bn[side] > limit) return JAGP_ERR_INVALID_ARG;
-      if (stg[side] < -1 || stg[side] == 1 || stg[side] > 6) return JAGP_ERR_INVALID_ARG;
+      if (stg[side] < -3 || stg[side] == 1 || stg[side] > 6) return JAGP_ERR_INVALID_ARG;
       const int npairs = mixed ? kFixedPairs : np64;
       const int actual = umma_pick_bn(h->ds.L, bn[side] ? bn[side] : limit);
-      if (stg[side] == -1 && !umma_chunk_fits(npairs, mixed ? kPairA : pa64, mixed ? kLamPairB : pb64, actual))
+      if (stg[side] < 0 && !umma_chunk_fits(npairs, mixed ? kPairA : pa64, mixed ? kPairB : pb64, actual, stg[side]))
         return JAGP_ERR_INVALID_ARG;
     }
   }

@@ -132,20 +132,22 @@ cudaError_t launch_umma_gemm(const uint16_t *A, int m_max, const int *m_dev, int
                              int bn_max = 0, double *out64 = nullptr, int slice_bits = 8, int batch_rows = 0,
                              int batches = 0, int stages_max = 0, int b_batch_rows = 0, long long o_bstride = 0,
                              long long o_rstride = 0, long long o_cstride = 0, const int *pair_group = nullptr);
-// whether two chunk-major stages (stages_max = -1) of these pairs fit at tile width bn
-bool umma_chunk_fits(int npairs, const int *pair_a, const int *pair_b, int bn);
+// whether two chunk-major stages (stages_max = -1, -2, -3: K chunks of 64, 32,
+// 16) of these pairs fit at tile width bn
+bool umma_chunk_fits(int npairs, const int *pair_a, const int *pair_b, int bn, int stages_max);
 // FP64 rows -> nsl exact slices of `bits` bits per element plus a row exponent;
 // rows_out[m] = the source row, or (dst_stride > 0) (m / nsub) dst_stride + dst_off + m % nsub
 cudaError_t launch_pack_fixed64(const double *P, const int *list, const int *count, int nrows, int nsub, int stride,
                                 int L, int kp, int nsl, int bits, uint16_t *A, int *rows_out, int *exps,
                                 int max_rows, cudaStream_t st, long dst_stride = 0, long dst_off = 0);
 // columns c < C of the per-walker matrices X_w ([R][C], X_w = X + w xw; FP64 X64,
-// or two-float X32 + Xlo) -> operand rows w C + c of kFixedSlices exact 8-bit
-// slices over the R rows (K padded to kp), exponents exps[w C + c], and
-// rows_out[w C + c] = w dst_stride + dst_off + c (when given)
+// or two-float X32 + Xlo) -> operand rows w C + c of nsl exact slices of
+// `bits` bits (8, or 7 for FP64 X; nsl <= 8) over the R rows (K padded to kp),
+// exponents exps[w C + c], and rows_out[w C + c] = w dst_stride + dst_off + c
+// (when given)
 cudaError_t launch_pack_cols(const double *X64, const float *X32, const float *Xlo, size_t xw, int R, int C, int kp,
                              int W, uint16_t *A, int *exps, int *rows_out, long dst_stride, long dst_off,
-                             cudaStream_t st);
+                             cudaStream_t st, int nsl = kFixedSlices, int bits = 8);
 // FP32 rows (two-float rows P + P_lo when P_lo is given) -> kFixedSlices exact
 // 8-bit slices per element (BF16) plus a row exponent
 cudaError_t launch_pack_fixed(const float *P, const float *P_lo, const int *list, const int *count, int nrows,
@@ -178,6 +180,8 @@ cudaError_t launch_adj_reduce(const double *part, int nparts, int n_atoms, doubl
                               int W, double *dR, double *djas, cudaStream_t st);
 cudaError_t launch_adj_lambda(const double *btbar, const double *dnphi, const double *phi_up, const double *abar,
                               int W, int n, int nd, int L, double *part, int nz, double *dlam, cudaStream_t st);
+// dlam[i] = sum_{z < nz} part[z][i] (fixed order), i < L^2
+cudaError_t launch_adj_lambda_sum(const double *part, int nz, int L, double *dlam, cudaStream_t st);
 cudaError_t setup_adjoint_attributes();
 
 // Reblocking (k_stats.cu): walker means per sweep of eL [T][W] into work [T],

@@ -751,6 +751,14 @@ cudaError_t launch_adj_lambda(const double *btbar, const double *dnphi, const do
   return cudaGetLastError();
 }
 
+cudaError_t launch_adj_lambda_sum(const double *part, int nz, int L, double *dlam, cudaStream_t st) {
+  const long LL = (long)L * L;
+  long blocks = (LL + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  k_adj_lambda_sum<<<(int)blocks, 256, 0, st>>>(part, nz, (int)LL, dlam);
+  return cudaGetLastError();
+}
+
 cudaError_t setup_adjoint_attributes() {
   const int big = 200 * 1024;
   cudaError_t e;

@@ -88,14 +88,17 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
 }
 
 // Shared-memory matrix descriptor of a K-major tile written by TMA with the
-// 128-byte swizzle: rows of 128 bytes, 8-row groups 1024 bytes apart.
-__device__ __forceinline__ uint64_t desc_sw128_kmajor(uint32_t saddr) {
+// swizzle of its row width: rows of 128, 64 or 32 bytes (K chunks of 64, 32 or
+// 16 BF16 elements), 8-row groups 8 row widths apart; the PTX layout codes of
+// the 128-, 64- and 32-byte swizzles are 2, 4 and 6.
+__device__ __forceinline__ uint64_t desc_kmajor(uint32_t saddr, uint32_t row_bytes) {
+  const uint64_t layout = row_bytes == 128 ? 2 : (row_bytes == 64 ? 4 : 6);
   uint64_t d = 0;
-  d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);  // start address
-  d |= static_cast<uint64_t>(1) << 16;                  // leading byte offset (unused here)
-  d |= static_cast<uint64_t>(1024 >> 4) << 32;          // stride byte offset
-  d |= static_cast<uint64_t>(1) << 46;                  // descriptor version for tcgen05
-  d |= static_cast<uint64_t>(2) << 61;                  // 128-byte swizzle
+  d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);      // start address
+  d |= static_cast<uint64_t>(1) << 16;                      // leading byte offset (unused here)
+  d |= static_cast<uint64_t>((8u * row_bytes) >> 4) << 32;  // stride byte offset
+  d |= static_cast<uint64_t>(1) << 46;                      // descriptor version for tcgen05
+  d |= layout << 61;                                        // swizzle
   return d;
 }
 
@@ -144,8 +147,9 @@ struct UmmaArgs {
                          // rows; batch b's rows of A meet only batch b's rows of B
   int tiles_per_batch;   // batched mode: 128-row tiles per batch
   int b_batch_rows;      // batched mode: rows of B per batch (= batch_rows unless given)
-  int chunk_major;       // 1: one stage holds every slice of one 64-wide K chunk of A (na) and B (nb),
+  int chunk_major;       // 1: one stage holds every slice of one K chunk of A (na) and B (nb),
   int na, nb;            //    and the MMA thread issues all pairs from it (slices loaded once per chunk)
+  int cw;                // K chunk width in elements: 64, or 32 / 16 for chunk-major stages of many slices
   const int *a_exp;      // fixed-point mode: row exponents [m_max], else null
   const int *b_exp;      // fixed-point mode: column exponents [n]
   uint32_t idesc;
@@ -187,8 +191,10 @@ __global__ void __launch_bounds__(128) k_umma_gemm(const __grid_constant__ CUten
   const int bbase = bb * g.b_batch_rows;  // first B row (and column exponent) of this batch
   if (m0 >= M) return;  // whole CTA, before any barrier or tensor-memory use
   const int n0 = tile_x * g.bn;
-  const uint32_t a_bytes = 128u * 128u;
-  const uint32_t b_bytes = static_cast<uint32_t>(g.bn) * 128u;
+  const uint32_t row_bytes = static_cast<uint32_t>(g.cw) * 2u;  // 128, 64 or 32
+  const uint32_t a_bytes = 128u * row_bytes;
+  const uint32_t b_bytes = static_cast<uint32_t>(g.bn) * row_bytes;
+  const int ksteps = g.cw / 16;  // MMAs (K = 16) per chunk
   const uint32_t stage_bytes =
       g.chunk_major ? static_cast<uint32_t>(g.na) * a_bytes + static_cast<uint32_t>(g.nb) * b_bytes : a_bytes + b_bytes;
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + g.stages * stage_bytes);
@@ -213,7 +219,7 @@ __global__ void __launch_bounds__(128) k_umma_gemm(const __grid_constant__ CUten
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const int kchunks = g.kp / 64;
+  const int kchunks = g.kp / g.cw;
   const int iters = g.chunk_major ? kchunks : g.npairs * kchunks;
   const uint32_t tiles = smem_u32(smem);
 
@@ -228,12 +234,22 @@ __global__ void __launch_bounds__(128) k_umma_gemm(const __grid_constant__ CUten
       }
       const uint32_t full = full0 + 8u * s, base = tiles + s * stage_bytes;
       mbar_expect_tx(full, stage_bytes);
-      for (int a = 0; a < g.na; ++a) tma_load_2d(base + a * a_bytes, &tmA, a * g.kp + it * 64, m0, full);
+      for (int a = 0; a < g.na; ++a) tma_load_2d(base + a * a_bytes, &tmA, a * g.kp + it * g.cw, m0, full);
       for (int b = 0; b < g.nb; ++b)
-        tma_load_2d(base + g.na * a_bytes + b * b_bytes, &tmB, b * g.kp + it * 64, bbase + n0, full);
+        tma_load_2d(base + g.na * a_bytes + b * b_bytes, &tmB, b * g.kp + it * g.cw, bbase + n0, full);
     }
   } else if (warp == 1 && lane == 0 && g.chunk_major) {
-    // MMA issuer, chunk-major: all pairs of the chunk from the one stage
+    // MMA issuer, chunk-major: all pairs of the chunk from the one stage.  The
+    // descriptors differ from the stage's only in the start-address field
+    // (16-byte units, no carry out of it inside one CTA's shared memory), so
+    // each MMA adds precomputed offsets instead of rebuilding them; the first
+    // chunk initialises every accumulator, the rest accumulate.
+    uint32_t offa[kMaxPairs], offb[kMaxPairs], dtm[kMaxPairs];
+    for (int p = 0; p < g.npairs; ++p) {
+      offa[p] = (static_cast<uint32_t>(g.pair_a[p]) * a_bytes) >> 4;
+      offb[p] = (static_cast<uint32_t>(g.na) * a_bytes + static_cast<uint32_t>(g.pair_b[p]) * b_bytes) >> 4;
+      dtm[p] = tmem + static_cast<uint32_t>(g.pair_group[p] * g.bn);
+    }
     uint32_t started = 0;
     for (int it = 0; it < iters; ++it) {
       const int s = it % g.stages;
@@ -243,17 +259,19 @@ __global__ void __launch_bounds__(128) k_umma_gemm(const __grid_constant__ CUten
         break;
       }
       tc_fence_after();
-      const uint32_t base = tiles + s * stage_bytes;
-      for (int p = 0; p < g.npairs; ++p) {
-        const int grp = g.pair_group[p];
-        const uint32_t a0 = base + g.pair_a[p] * a_bytes, b0 = base + g.na * a_bytes + g.pair_b[p] * b_bytes;
-        const uint32_t d_tmem = tmem + static_cast<uint32_t>(grp * g.bn);
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-          umma_bf16(d_tmem, desc_sw128_kmajor(a0 + kk * 32), desc_sw128_kmajor(b0 + kk * 32), g.idesc,
-                    (started >> grp) & 1u);
-          started |= 1u << grp;
+      const uint64_t dstage = desc_kmajor(tiles + s * stage_bytes, row_bytes);
+      if (it == 0) {
+        for (int p = 0; p < g.npairs; ++p) {
+          const int grp = g.pair_group[p];
+          for (int kk = 0; kk < ksteps; ++kk) {
+            umma_bf16(dtm[p], dstage + offa[p] + 2u * kk, dstage + offb[p] + 2u * kk, g.idesc, (started >> grp) & 1u);
+            started |= 1u << grp;
+          }
         }
+      } else {
+        for (int p = 0; p < g.npairs; ++p)
+          for (int kk = 0; kk < ksteps; ++kk)
+            umma_bf16(dtm[p], dstage + offa[p] + 2u * kk, dstage + offb[p] + 2u * kk, g.idesc, 1u);
       }
       umma_commit(empty0 + 8u * s);
     }
@@ -289,7 +307,7 @@ __global__ void __launch_bounds__(128) k_umma_gemm(const __grid_constant__ CUten
       const uint32_t d_tmem = tmem + static_cast<uint32_t>(grp * g.bn);
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk) {
-        umma_bf16(d_tmem, desc_sw128_kmajor(a0 + kk * 32), desc_sw128_kmajor(b0 + kk * 32), g.idesc,
+        umma_bf16(d_tmem, desc_kmajor(a0 + kk * 32, 128u), desc_kmajor(b0 + kk * 32, 128u), g.idesc,
                   (started >> grp) & 1u);
         started |= 1u << grp;
       }
@@ -413,15 +431,19 @@ EncodeTiledFn encode_fn() {
 }
 
 // 2-D BF16 map with a 128-byte-swizzled box of 64 (inner) x box_rows
-bool make_map(CUtensorMap *m, const void *base, uint64_t inner, uint64_t rows, uint32_t box_rows) {
+// box of cw x box_rows BF16 elements, swizzled by its row width (cw = 64, 32
+// or 16: 128-, 64- or 32-byte rows)
+bool make_map(CUtensorMap *m, const void *base, uint64_t inner, uint64_t rows, uint32_t box_rows, uint32_t cw) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
   cuuint64_t dims[2] = {inner, rows};
   cuuint64_t strides[1] = {inner * 2};
-  cuuint32_t box[2] = {64, box_rows};
+  cuuint32_t box[2] = {cw, box_rows};
   cuuint32_t es[2] = {1, 1};
+  const CUtensorMapSwizzle sw =
+      cw == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : (cw == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B);
   return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, es,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -436,20 +458,22 @@ int umma_pick_bn(int n, int max_bn) {
 namespace {
 int g_smem_optin = 220 * 1024;  // the kernel's dynamic shared-memory limit, set once per process
 
-uint32_t chunk_stage_bytes(int na, int nb, int bn) {
-  return static_cast<uint32_t>(na) * 128u * 128u + static_cast<uint32_t>(nb * bn) * 128u;
+uint32_t chunk_stage_bytes(int na, int nb, int bn, int cw) {
+  return (static_cast<uint32_t>(na) * 128u + static_cast<uint32_t>(nb * bn)) * static_cast<uint32_t>(cw) * 2u;
 }
+// chunk width of the chunk-major modes: stages_max -1, -2, -3 -> 64, 32, 16
+int chunk_width(int stages_max) { return stages_max == -1 ? 64 : (stages_max == -2 ? 32 : 16); }
 // room for the stages: the limit less the 1 KB alignment slack and the barriers
 uint32_t chunk_budget() { return static_cast<uint32_t>(g_smem_optin - 1024 - 64); }
 }  // namespace
 
-bool umma_chunk_fits(int npairs, const int *pair_a, const int *pair_b, int bn) {
+bool umma_chunk_fits(int npairs, const int *pair_a, const int *pair_b, int bn, int stages_max) {
   int na = 0, nb = 0;
   for (int p = 0; p < npairs; ++p) {
     na = pair_a[p] + 1 > na ? pair_a[p] + 1 : na;
     nb = pair_b[p] + 1 > nb ? pair_b[p] + 1 : nb;
   }
-  return 2u * chunk_stage_bytes(na, nb, bn) <= chunk_budget();
+  return 2u * chunk_stage_bytes(na, nb, bn, chunk_width(stages_max)) <= chunk_budget();
 }
 
 cudaError_t launch_umma_gemm(const uint16_t *A, int m_max, const int *m_dev, int a_terms, const uint16_t *B, int n,
@@ -504,13 +528,16 @@ cudaError_t launch_umma_gemm(const uint16_t *A, int m_max, const int *m_dev, int
     g.nb = pair_b[p] + 1 > g.nb ? pair_b[p] + 1 : g.nb;
   }
   uint32_t stage_bytes = 128u * 128u + static_cast<uint32_t>(g.bn) * 128u;
-  if (stages_max < -1) return cudaErrorInvalidValue;
-  // stages_max = -1: chunk-major, two stages of every slice of a 64-wide K chunk
-  g.chunk_major = stages_max == -1 ? 1 : 0;
+  if (stages_max < -3) return cudaErrorInvalidValue;
+  // stages_max = -1, -2, -3: chunk-major, every slice of a 64-, 32- or 16-wide
+  // K chunk per stage, as many stages as fit (two to four)
+  g.chunk_major = stages_max < 0 ? 1 : 0;
+  g.cw = g.chunk_major ? chunk_width(stages_max) : 64;
   if (g.chunk_major) {
-    stage_bytes = chunk_stage_bytes(g.na, g.nb, g.bn);
+    stage_bytes = chunk_stage_bytes(g.na, g.nb, g.bn, g.cw);
     if (2u * stage_bytes > chunk_budget()) return cudaErrorInvalidValue;
-    g.stages = 2;
+    g.stages = static_cast<int>(chunk_budget() / stage_bytes);
+    if (g.stages > 4) g.stages = 4;
   } else {
     // pipeline depth: as many stages as fit in 200 KB, at most 6, or fewer
     // (stages_max, from the autotuner) so that several CTAs share an SM
@@ -538,8 +565,10 @@ cudaError_t launch_umma_gemm(const uint16_t *A, int m_max, const int *m_dev, int
   g.err = err;
   CUtensorMap ta, tb;
   const uint64_t b_rows = batch_rows > 0 ? static_cast<uint64_t>(b_batch_rows) * batches : static_cast<uint64_t>(n);
-  if (!make_map(&ta, A, static_cast<uint64_t>(a_terms) * kp, static_cast<uint64_t>(m_max), 128) ||
-      !make_map(&tb, B, static_cast<uint64_t>(b_terms) * kp, b_rows, static_cast<uint32_t>(g.bn)))
+  if (!make_map(&ta, A, static_cast<uint64_t>(a_terms) * kp, static_cast<uint64_t>(m_max), 128,
+                static_cast<uint32_t>(g.cw)) ||
+      !make_map(&tb, B, static_cast<uint64_t>(b_terms) * kp, b_rows, static_cast<uint32_t>(g.bn),
+                static_cast<uint32_t>(g.cw)))
     return cudaErrorInvalidValue;
   const size_t smem = 1024 + static_cast<size_t>(g.stages) * stage_bytes + 8 * (2 * g.stages + 1) + 16;
   dim3 grid((n + g.bn - 1) / g.bn, batch_rows > 0 ? batches * g.tiles_per_batch : (m_max + 127) / 128);
@@ -664,8 +693,9 @@ cudaError_t launch_pack_fixed64(const double *P, const int *list, const int *cou
 // Bt and A_up): for walker w < W and column c < C of X_w = X + w xw
 // ([R][C] row-major), operand row m = w C + c holds X_w[0..R)[c] (zero from R
 // to kp) relative to 2^e, e = 1 + the binary exponent of the column's largest
-// magnitude, cut into kFixedSlices exact 8-bit slices as k_pack_fixed cuts a
-// row (an FP64 X, or a two-float X + Xlo with the remainder carried exactly).
+// magnitude, cut into nsl exact slices of `bits` bits (FP64 X: 8 or 7 bits, up
+// to eight slices; two-float X + Xlo: 8 bits, the remainder carried exactly)
+// as k_pack_fixed cuts a row.
 // exps[m] = e; rows_out[m] = w dst_stride + dst_off + c when rows_out is given.
 // One CTA per (walker, 32 columns): the column maxima first, then tiles of 64
 // rows through shared memory, so that the reads (32 consecutive columns of a
@@ -676,7 +706,9 @@ template <bool kF64>
 __global__ void __launch_bounds__(256) k_pack_cols(const double *__restrict__ X64, const float *__restrict__ X32,
                                                    const float *__restrict__ Xlo, size_t xw, int R, int C, int kp,
                                                    __nv_bfloat16 *__restrict__ A, int *__restrict__ exps,
-                                                   int *__restrict__ rows_out, long dst_stride, long dst_off) {
+                                                   int *__restrict__ rows_out, long dst_stride, long dst_off,
+                                                   int nsl, int bits) {
+  constexpr int kMaxSl = 8;
   __shared__ double t64[kF64 ? 64 : 1][33];
   __shared__ float th[kF64 ? 1 : 64][33], tl[kF64 ? 1 : 64][33];
   __shared__ float cmax[8][32];
@@ -745,22 +777,25 @@ __global__ void __launch_bounds__(256) k_pack_cols(const double *__restrict__ X6
       const int col = jr + 8 * cc, cg = c0 + col;
       if (cg >= C) continue;
       const int e = cexp[col];
-      __nv_bfloat16 sl[2][kFixedSlices];
+      __nv_bfloat16 sl[2][kMaxSl];
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int jj = 2 * (tid & 31) + h;
         if constexpr (kF64) {
-          double x = ldexp(t64[jj][col], 7 - e);  // |x| < 128
+          const double step = ldexp(1.0, bits);
+          double x = ldexp(t64[jj][col], bits - 1 - e);  // |x| < 2^(bits - 1)
 #pragma unroll
-          for (int t = 0; t < kFixedSlices; ++t) {
+          for (int t = 0; t < kMaxSl; ++t) {
+            if (t >= nsl) break;
             const double q = rint(x);
             sl[h][t] = __float2bfloat16_rn(static_cast<float>(q));
-            x = (x - q) * 256.0;
+            x = (x - q) * step;
           }
         } else {
           float x = ldexpf(th[jj][col], 7 - e), xl = ldexpf(tl[jj][col], 7 - e);
 #pragma unroll
-          for (int t = 0; t < kFixedSlices; ++t) {
+          for (int t = 0; t < kMaxSl; ++t) {
+            if (t >= nsl) break;
             const float q = rintf(x);
             sl[h][t] = __float2bfloat16_rn(q);
             const fdw r = two_sum(__fsub_rn(x, q), xl);
@@ -769,9 +804,10 @@ __global__ void __launch_bounds__(256) k_pack_cols(const double *__restrict__ X6
           }
         }
       }
-      __nv_bfloat16 *dst = A + ((size_t)w * C + cg) * kFixedSlices * (size_t)kp + j0 + 2 * (tid & 31);
+      __nv_bfloat16 *dst = A + ((size_t)w * C + cg) * nsl * (size_t)kp + j0 + 2 * (tid & 31);
 #pragma unroll
-      for (int t = 0; t < kFixedSlices; ++t) {
+      for (int t = 0; t < kMaxSl; ++t) {
+        if (t >= nsl) break;
         __nv_bfloat162 v;
         v.x = sl[0][t];
         v.y = sl[1][t];
@@ -784,17 +820,19 @@ __global__ void __launch_bounds__(256) k_pack_cols(const double *__restrict__ X6
 
 cudaError_t launch_pack_cols(const double *X64, const float *X32, const float *Xlo, size_t xw, int R, int C, int kp,
                              int W, uint16_t *A, int *exps, int *rows_out, long dst_stride, long dst_off,
-                             cudaStream_t st) {
+                             cudaStream_t st, int nsl, int bits) {
   if (W <= 0 || C <= 0) return cudaSuccess;
   if (kp % 64 != 0 || kp < R || (X64 == nullptr) == (X32 == nullptr)) return cudaErrorInvalidValue;
+  if (nsl < 1 || nsl > 8 || (bits != 8 && (bits != 7 || !X64))) return cudaErrorInvalidValue;
   dim3 grid((C + 31) / 32, W);
   if (X64)
     k_pack_cols<true><<<grid, 256, 0, st>>>(X64, nullptr, nullptr, xw, R, C, kp,
-                                            reinterpret_cast<__nv_bfloat16 *>(A), exps, rows_out, dst_stride, dst_off);
+                                            reinterpret_cast<__nv_bfloat16 *>(A), exps, rows_out, dst_stride, dst_off,
+                                            nsl, bits);
   else
     k_pack_cols<false><<<grid, 256, 0, st>>>(nullptr, X32, Xlo, xw, R, C, kp,
                                              reinterpret_cast<__nv_bfloat16 *>(A), exps, rows_out, dst_stride,
-                                             dst_off);
+                                             dst_off, nsl, bits);
   return cudaGetLastError();
 }
 

@@ -44,9 +44,10 @@ def test_autotune_changes_no_result(torch_cuda, name, mode):
             t = g.autotune()
             assert t["tile_proposals"] in (0, 32, 64) and t["tile_refresh"] in (0, 16, 32, 64)
             if mixed:
-                assert t["umma_bn_left"] in (16, 32, 48, 64, 80, 96)
-                assert t["umma_bn_right"] in (16, 32, 48, 64, 80, 96)
-                assert t["umma_stages_left"] in (0, 2, 3) and t["umma_stages_right"] in (0, 2, 3)
+                assert t["umma_bn_left"] in (16, 32, 48, 64)
+                assert t["umma_bn_right"] in (16, 32, 48, 64)
+                assert t["umma_stages_left"] in (-3, -2, -1, 0, 2, 3)
+                assert t["umma_stages_right"] in (-3, -2, -1, 0, 2, 3)
                 assert all(m > 0 for m in t["ms"])
             elif mode == "fp64tc":
                 assert t["umma_bn_left"] in (16, 32, 48, 64) and t["umma_bn_right"] in (16, 32, 48, 64)
@@ -95,10 +96,13 @@ def _run(sysm, W, prec, tuning, fp64_tc=False):
 PINNED_MIXED = [
     {"tile_proposals": 0, "tile_refresh": 32, "umma_bn_left": 16, "umma_bn_right": 16,
      "umma_stages_left": 2, "umma_stages_right": 3},
-    {"tile_proposals": 64, "tile_refresh": 0, "umma_bn_left": 96, "umma_bn_right": 80,
-     "umma_stages_left": 0, "umma_stages_right": 3},
+    {"tile_proposals": 64, "tile_refresh": 0, "umma_bn_left": 16, "umma_bn_right": 16,
+     "umma_stages_left": -1, "umma_stages_right": 3},
     {"tile_proposals": 32, "tile_refresh": 64, "umma_bn_left": 64, "umma_bn_right": 48,
      "umma_stages_left": 0, "umma_stages_right": 2},
+    # chunk-major with K chunks of 32 and 16 (64- and 32-byte swizzled tiles)
+    {"tile_proposals": 0, "tile_refresh": 0, "umma_bn_left": 64, "umma_bn_right": 48,
+     "umma_stages_left": -2, "umma_stages_right": -3},
 ]
 
 
@@ -130,12 +134,12 @@ def test_set_tuning_rejects_bad_values(torch_cuda):
     fp64 = pg.JAGP(synth.config2(), 8)
     fp64tc = pg.JAGP(synth.config2(), 8, fp64_tc=True)
     bad_mixed = [{"tile_proposals": 16}, {"tile_refresh": 48}, {"umma_bn_left": 24}, {"umma_bn_left": 144},
-                 {"umma_bn_right": 88}, {"umma_stages_left": 1}, {"umma_stages_right": 7},
-                 {"umma_stages_left": -2},
-                 # five accumulators of more than 96 columns
-                 {"umma_bn_left": 112}, {"umma_bn_right": 128},
-                 # two chunk-major stages of the 6 + 12 slice terms never fit
-                 {"umma_bn_right": 16, "umma_stages_right": -1}, {"umma_bn_left": 64, "umma_stages_left": -1}]
+                 {"umma_bn_right": 72}, {"umma_stages_left": 1}, {"umma_stages_right": 7},
+                 # six accumulators of more than 64 columns
+                 {"umma_bn_left": 80}, {"umma_bn_right": 96},
+                 # two chunk-major stages of six slices with K chunks of 64 fit only at 16 columns
+                 {"umma_bn_right": 32, "umma_stages_right": -1}, {"umma_bn_left": 64, "umma_stages_left": -1},
+                 {"umma_stages_left": -4}]
     for t in bad_mixed:
         with pytest.raises(pg.JagpError):
             mixed.set_tuning(t)

@@ -101,16 +101,20 @@ def test_fp64tc_full_size_c2_matches_native_fp64(torch_cuda):
     assert np.all(_close(out[1][1], out[0][1]))
 
 
-def test_fp64tc_adjoint_matches_native(torch_cuda):
+@pytest.mark.parametrize("name,W", [("mid-n40", 4), ("C2", 4), ("n48-L576", 80)])
+def test_fp64tc_adjoint_matches_native(torch_cuda, name, W):
     """jagp_grad with the tensor-core FP64-equivalent lambda products equals the
-    native FP64 adjoint to 1e-9 (relative to the largest component)."""
+    native FP64 adjoint to 1e-9 (relative to the largest component).  With
+    N_dn = N_up (C2, the L = 576 system) lambda-bar runs on the tensor cores
+    as well, in segments of 2048 // N_up walkers (the 80 walkers of the L = 576
+    system make one full segment and a ragged one per row set)."""
     torch = torch_cuda
     import paper_2002_07401_gb300 as pg
-    sysm = SYSTEMS["mid-n40"]()
-    W = 4
+    sysm = SYSTEMS[name]()
     x = _walkers(sysm, W, seed=12)
-    sL = torch.tensor([0.3, -1.1, 0.7, 0.2], dtype=torch.float64, device="cuda")
-    sE = torch.tensor([0.25, 0.25, -0.5, 1.0], dtype=torch.float64, device="cuda")
+    rng = np.random.default_rng(W)
+    sL = torch.tensor(rng.normal(size=W), dtype=torch.float64, device="cuda")
+    sE = torch.tensor(rng.normal(size=W) / W, dtype=torch.float64, device="cuda")
     outs = []
     for tc in (False, True):
         g = pg.JAGP(sysm, W, fp64_tc=tc)
