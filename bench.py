@@ -655,7 +655,7 @@ PIPELINE_WORKLOAD = ("large system, full pipeline: the 512-electron system's 102
                      "and d/d b")
 
 
-def pipeline_bench(pg, torch, dist, args, dev, rank, ws, local):
+def pipeline_bench(pg, torch, dist, args, dev, rank, ws, local, pin=None):
     """Config 5 as one timed pipeline: args.pipeline_sweeps mixed sweeps of all
     walkers; after every args.pipeline_every sweeps the first
     args.pipeline_force_walkers walkers' configurations go (device to device)
@@ -670,7 +670,11 @@ def pipeline_bench(pg, torch, dist, args, dev, rank, ws, local):
     S, every = args.pipeline_sweeps, args.pipeline_every
     x0 = np.ascontiguousarray(synth.init_walkers(sysm, W * ws, seed=0)[rank * W:(rank + 1) * W])
     gm = pg.JAGP(sysm, W, seed=0, precision=pg.JAGP_PREC_MIXED)
-    tuning = None if NO_AUTOTUNE else gm.autotune()
+    if pin:  # the large line's choices for the same system and walker count
+        gm.set_tuning(pin)
+        tuning = pin
+    else:
+        tuning = None if NO_AUTOTUNE else gm.autotune()
     r = gm.positions(x0)
     gf = pg.JAGP(sysm, K, seed=0, fp64_tc=True)
     rf = torch.empty((K, sysm.N, 3), dtype=torch.float64, device=dev)
@@ -1053,7 +1057,8 @@ def run_gpu(args):
         batched64 = batch_bench(pg, torch, dist, args, dev, rank, ws, precision=pg.JAGP_PREC_FP64,
                                 sweeps=args.batch_fp64_sweeps)
     large = None if args.no_large else large_bench(pg, torch, dist, args, dev, rank, ws, local)
-    pipeline = None if args.no_large else pipeline_bench(pg, torch, dist, args, dev, rank, ws, local)
+    pipeline = None if args.no_large else pipeline_bench(pg, torch, dist, args, dev, rank, ws, local,
+                                                         pin=large.get("tuning") if large else None)
     sr = None if args.no_sr else sr_bench(pg, torch, dist, args, dev, rank, ws, local)
     lrdmc = None if args.no_lrdmc else lrdmc_bench(pg, torch, dist, args, dev, rank, ws, local)
     reweighted = None if args.no_forces else reweighted_forces_bench(pg, torch, dist, args, dev, rank, ws, local)

@@ -123,7 +123,7 @@ cudaError_t launch_increment(uint32_t *c, uint32_t by, cudaStream_t st);
 // aligned bases); rows m < *m_dev (or m_max) are written; out FP32, pitch ldo.
 // With a_exp/b_exp (row / column exponents) the terms are fixed-point slices and
 // pairs of equal a + b share an exact accumulator (see k_umma.cu).
-// stages_max: pipeline depth (0: as many as fit); -1: chunk-major stages.
+// stages_max: pipeline depth (0: as many as fit); -1, -2, -3: chunk-major stages (K chunks of 64, 32, 16).
 int umma_pick_bn(int n, int max_bn);
 cudaError_t launch_umma_gemm(const uint16_t *A, int m_max, const int *m_dev, int a_terms, const uint16_t *B, int n,
                              int b_terms, int kp, int npairs, const int *pair_a, const int *pair_b, float *out,

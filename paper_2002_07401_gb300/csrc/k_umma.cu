@@ -22,7 +22,7 @@
 // lane 0 issues the MMAs (one per 16-wide K slice), all four warps drain the
 // accumulator from tensor memory (warp w owns TMEM lanes 32w..32w+31 = rows).
 // Stages hold one A and one B slice of a 64-wide K chunk, pair after pair; in
-// chunk-major mode (stages_max = -1, for long K) a stage holds every slice of
+// chunk-major modes (stages_max = -1, -2, -3: K chunks of 64, 32, 16) a stage holds every slice of
 // the chunk and the MMA thread issues all pairs from it.  CTAs walk kGroupM row
 // tiles of one column tile before the next, so that a wave shares operand
 // tiles in L2.  Every wait is bounded by the global timer; a timeout sets *err.
@@ -239,17 +239,7 @@ __global__ void __launch_bounds__(128) k_umma_gemm(const __grid_constant__ CUten
         tma_load_2d(base + g.na * a_bytes + b * b_bytes, &tmB, b * g.kp + it * g.cw, bbase + n0, full);
     }
   } else if (warp == 1 && lane == 0 && g.chunk_major) {
-    // MMA issuer, chunk-major: all pairs of the chunk from the one stage.  The
-    // descriptors differ from the stage's only in the start-address field
-    // (16-byte units, no carry out of it inside one CTA's shared memory), so
-    // each MMA adds precomputed offsets instead of rebuilding them; the first
-    // chunk initialises every accumulator, the rest accumulate.
-    uint32_t offa[kMaxPairs], offb[kMaxPairs], dtm[kMaxPairs];
-    for (int p = 0; p < g.npairs; ++p) {
-      offa[p] = (static_cast<uint32_t>(g.pair_a[p]) * a_bytes) >> 4;
-      offb[p] = (static_cast<uint32_t>(g.na) * a_bytes + static_cast<uint32_t>(g.pair_b[p]) * b_bytes) >> 4;
-      dtm[p] = tmem + static_cast<uint32_t>(g.pair_group[p] * g.bn);
-    }
+    // MMA issuer, chunk-major: all pairs of the chunk from the one stage
     uint32_t started = 0;
     for (int it = 0; it < iters; ++it) {
       const int s = it % g.stages;
@@ -259,19 +249,16 @@ __global__ void __launch_bounds__(128) k_umma_gemm(const __grid_constant__ CUten
         break;
       }
       tc_fence_after();
-      const uint64_t dstage = desc_kmajor(tiles + s * stage_bytes, row_bytes);
-      if (it == 0) {
-        for (int p = 0; p < g.npairs; ++p) {
-          const int grp = g.pair_group[p];
-          for (int kk = 0; kk < ksteps; ++kk) {
-            umma_bf16(dtm[p], dstage + offa[p] + 2u * kk, dstage + offb[p] + 2u * kk, g.idesc, (started >> grp) & 1u);
-            started |= 1u << grp;
-          }
+      const uint32_t base = tiles + s * stage_bytes;
+      for (int p = 0; p < g.npairs; ++p) {
+        const int grp = g.pair_group[p];
+        const uint32_t a0 = base + g.pair_a[p] * a_bytes, b0 = base + g.na * a_bytes + g.pair_b[p] * b_bytes;
+        const uint32_t d_tmem = tmem + static_cast<uint32_t>(grp * g.bn);
+        for (int kk = 0; kk < ksteps; ++kk) {
+          umma_bf16(d_tmem, desc_kmajor(a0 + kk * 32, row_bytes), desc_kmajor(b0 + kk * 32, row_bytes), g.idesc,
+                    (started >> grp) & 1u);
+          started |= 1u << grp;
         }
-      } else {
-        for (int p = 0; p < g.npairs; ++p)
-          for (int kk = 0; kk < ksteps; ++kk)
-            umma_bf16(dtm[p], dstage + offa[p] + 2u * kk, dstage + offb[p] + 2u * kk, g.idesc, 1u);
       }
       umma_commit(empty0 + 8u * s);
     }
@@ -838,7 +825,7 @@ cudaError_t launch_pack_cols(const double *X64, const float *X32, const float *X
 
 cudaError_t setup_umma_attributes() {
   // the largest opt-in shared memory per block (227 KB on this part), so that
-  // two chunk-major stages of six slices fit at the narrower tiles
+  // two or more chunk-major stages of six slices fit (with K chunks of 32 or 16)
   int dev = 0, optin = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);

@@ -92,6 +92,10 @@ def test_j3_unsupported_paths(torch_cuda):
     la = torch.empty(4, dtype=torch.float64, device="cuda")
     with pytest.raises(pg.JagpError, match="three-body"):
         pg.jagp_eval_noalloc(g.h, r, 4, la, None)
+    work = torch.empty(pg.jagp_lrdmc_workspace_bytes(g.h, 4), dtype=torch.uint8, device="cuda")
+    w = torch.ones(4, dtype=torch.float64, device="cuda")
+    with pytest.raises(pg.JagpError, match="three-body"):
+        pg.jagp_lrdmc_project(g.h, r, g.state, 4, work, w, 0, 0.2, 0.0, 0.1, 0.0)
     g.close()
 
 
