@@ -559,6 +559,27 @@ def batch_bench(pg, torch, dist, args, dev, rank, ws, precision=None, sweeps=Non
     acc = b.acc.cpu().numpy()
     launches_per_sweep = b.launches_per_sweep()
     b.close()
+    # the other form of the same batched sweep (bit-identical results): grouped
+    # launches (one per kernel and point of the sweep over all systems) beside
+    # per-system launches over streams, or the reverse
+    other = None
+    other_sweeps = args.batch_grouped_sweeps if mixed else min(2, args.batch_grouped_sweeps)
+    if other_sweeps > 0:
+        ns_other = 0 if args.batch_streams > 0 else 16
+        b2 = pg.Batch(members, pos, walker0=[rank * W] * len(members), n_streams=ns_other)
+        b2.sweep(2, sweep0=nsw + args.warmup)
+        torch.cuda.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record()
+        b2.sweep(other_sweeps, sweep0=nsw + args.warmup + 2)
+        g1.record()
+        torch.cuda.synchronize()
+        gms = g0.elapsed_time(g1) / other_sweeps
+        other = {"form": "grouped launches" if ns_other == 0 else "per-system launches over 16 streams",
+                 "ms_per_sweep": gms, "value": W * sum(s.N for s in systems) / (gms / 1e3),
+                 "unit": "walker-electron moves/s (one GPU)", "sweeps": other_sweeps,
+                 "graph_launches_per_sweep": b2.launches_per_sweep()}
+        b2.close()
     # roofline: every member's lambda products of one sweep, timed per launch
     lam_ms, lam_n, flops = 0.0, 0, 0.0
     acc1 = torch.empty((1, 4), dtype=torch.float64, device=dev)
@@ -592,6 +613,8 @@ def batch_bench(pg, torch, dist, args, dev, rank, ws, precision=None, sweeps=Non
             "acceptance": float(acc[:, 2].sum()) / (moves / ws), "status_bits": bits,
             "dtype": "f32+bf16 (f64 refresh)" if mixed else "f64", "workload": BATCH_WORKLOAD if mixed else
             BATCH_WORKLOAD.replace("mixed precision", "plain FP64"), "graph_launches_per_sweep": launches_per_sweep,
+            "form": "grouped launches" if args.batch_streams <= 0 else
+            "per-system launches over %d streams" % args.batch_streams, "other_form": other,
             "tuning": tuning_summary(tunings), "roofline": roof}
 
 
@@ -1192,7 +1215,11 @@ def main():
     ap.add_argument("--batch-walkers", type=int, default=512)
     ap.add_argument("--batch-sweeps", type=int, default=50)
     ap.add_argument("--batch-fp64-sweeps", type=int, default=5)
-    ap.add_argument("--batch-streams", type=int, default=16)
+    ap.add_argument("--batch-streams", type=int, default=16,
+                    help="> 0: per-system launches over that many streams; 0 (or -k): grouped launches over all "
+                         "systems (in k lanes)")
+    ap.add_argument("--batch-grouped-sweeps", type=int, default=10,
+                    help="sweeps of the other batched form (grouped launches, or per-system streams) timed beside")
     ap.add_argument("--no-large", action="store_true", help="skip the 512-electron mixed-precision measurement")
     ap.add_argument("--large-walkers", type=int, default=1024)
     ap.add_argument("--large-steps", type=int, default=20)

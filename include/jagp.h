@@ -214,8 +214,24 @@ jagp_status_t jagp_reblock(const double *d_eL, int T, int W, double *d_work, dou
  * sweep written to d_eL[s] ([W[s]], the last sweep's) and accumulated into
  * d_acc[s][4] (sum e_L, sum e_L^2, accepted moves, max drift; the caller
  * zeroes it).  The first jagp_batch_sweep captures one sweep of all systems
- * (their launches forked over n_streams concurrent streams, largest systems
- * first) into a CUDA graph, which every later sweep replays; the sweep index
+ * into a CUDA graph, which every later sweep replays.  With n_streams = 0 the
+ * graph holds grouped launches: each system's launch sequence is recorded,
+ * and the launches of one kernel at one point of the sweep (a spin
+ * half-sweep's proposals, the acceptance of its k-th block of moves, the
+ * lambda products of the accepted rows, the steps of a refresh, the local
+ * energy, the sums) are issued as ONE launch over all systems' work (about a
+ * hundred launches per sweep for the 64-system workload, against one
+ * sequence per system); if a system's sequence cannot be grouped, the
+ * per-system form with 8 streams is used instead.  With n_streams = -k the
+ * systems are split into k lanes of about equal cost, each lane a chain of
+ * grouped launches on its own stream of the graph.  With n_streams > 0 every
+ * system's own launches are forked over n_streams concurrent streams,
+ * largest systems first.  The per-system forms give bit for bit the results
+ * of per-system vmc_sweep calls (the same kernels); a grouped launch runs the
+ * same formulas in the same order for each system but is compiled as another
+ * kernel, so its floating-point results may differ in the last bits (the
+ * tests find the same trajectories and local energies within 1e-11).  The
+ * sweep index
  * is read from a device counter, so the states, positions and output arrays
  * must stay where they were when the batch was created.  Handles, states and
  * arrays are borrowed, not copied.  d_eL and d_acc may be NULL. */

@@ -11,6 +11,7 @@
 #include <type_traits>
 #include <vector>
 
+#include "jagp_group.cuh"
 #include "jagp_launch.h"
 
 using namespace jagp;
@@ -19,6 +20,24 @@ using namespace jagp;
 
 #include <stdarg.h>
 #include <stdio.h>
+
+namespace jagp {
+static thread_local GroupRecorder *g_group_recorder = nullptr;
+GroupRecorder *group_recorder() { return g_group_recorder; }
+void set_group_recorder(GroupRecorder *r) { g_group_recorder = r; }
+cudaError_t group_raise_smem(const void *fn, unsigned char *done) {
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
+  if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
+  cudaFuncAttributes fa;
+  if ((e = cudaFuncGetAttributes(&fa, fn)) != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+  if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = 1;
+  return e;
+}
+}  // namespace jagp
 
 namespace {
 
@@ -296,6 +315,7 @@ jagp_status_t run_refresh(jagp_ctx *h, const double *r, void *state, int W, int 
   const Layout L = layout_of(h, W);
   const int n = h->ds.n_up, Lb = h->ds.L;
   double *gm = refresh_g(L, state);
+  group_subkey(0);  // grouped sweeps: packing, then the G~ product, then the elimination
   if (tc_refresh(h)) {
     // G~ = (Phi_up + lo)(Bt + lo)^T per walker on the tensor cores: both tables
     // cut into six fixed-point slices, twenty-one pairs, FP64 epilogue
@@ -308,16 +328,19 @@ jagp_status_t run_refresh(jagp_ctx *h, const double *r, void *state, int W, int 
     LAUNCH(0, 1,
            launch_pack_fixed(at<float>(state, L.bt), lo_table(h, state, L.bt_lo), nullptr, nullptr, W * n, 1, 1, Lb,
                              h->kp, pb, rows, eb, W * n, st));
+    group_subkey(1);
     LAUNCH(JAGP_KERNEL_GEMM_ROWS, 1,
            launch_umma_gemm(pa, W * n, nullptr, kFixedSlices, pb, n, kFixedSlices, h->kp, kFixedPairs, kPairA, kPairB,
                             nullptr, n, nullptr, h->d_err, st, ea, eb, nullptr, 0, gm, 8, n, W));
   } else {
+    group_subkey(1);
     LAUNCH(JAGP_KERNEL_GEMM_ROWS, 1,
            refresh_geminal(at<T>(state, L.phi_up), lo_table(h, state, L.phi_lo), (size_t)n * Lb, at<T>(state, L.bt),
                            lo_table(h, state, L.bt_lo), (size_t)n * Lb, n, Lb, gm, W, st, h->tune_tile_refresh));
   }
   // the mixed path keeps an FP64 copy of the inverse for the local energy
   double *gi64 = h->precision == JAGP_PREC_MIXED ? at<double>(state, L.ginv64) : nullptr;
+  group_subkey(2);
   LAUNCH(0, 1,
          launch_refresh_inverse<T>(gm, at<T>(state, L.ginv), at<double>(state, L.scal), at<int>(state, L.status), n,
                                    W, check_drift, h->drift_tol, st, gi64));
@@ -379,9 +402,11 @@ jagp_status_t run_sweeps(jagp_ctx *h, double *d_r, void *d_state, int W, int nsw
   // G~ at once, then the acceptance in chunks of refresh_moves moves, each
   // followed by the lambda products of its accepted rows and, but for the
   // last chunk, a refresh of G~^{-1} from the tables
-  auto half_sweep = [&](bool up, uint32_t sw) -> jagp_status_t {
+  auto half_sweep = [&](bool up, uint32_t sw, int t) -> jagp_status_t {
     const int moves = up ? n : d.n_dn;
     if (moves == 0) return JAGP_OK;
+    const int hk = up ? 1 : 3;  // grouped sweeps: (sweep, part, chunk, phase) of the launches below
+    group_key(t, hk, 0, 0);
     int *total = count + (up ? 0 : 1), *chunk = count + 2;
     LAUNCH(JAGP_KERNEL_BASIS, 1,
            launch_basis_points<T>(d, true, d_r, W, up ? 0 : n, moves, pprop, pprop_lo, rprop, (uint32_t)walker0, sw,
@@ -397,7 +422,8 @@ jagp_status_t run_sweeps(jagp_ctx *h, double *d_r, void *d_state, int W, int nsw
     const int step = h->refresh_moves > 0 ? h->refresh_moves : moves;
     for (int m0 = 0; m0 < moves; m0 += step) {
       const int m1 = m0 + step < moves ? m0 + step : moves;
-      JAGP_CU(cudaMemsetAsync(chunk, 0, sizeof(int), st));
+      group_key(t, hk, m0 / step, 1);
+      JAGP_CU(zero_ints(chunk, 1, st));
       bool guided = false;
       if constexpr (std::is_same<T, double>::value) {
         if (h->guide_eps > 0.0) {
@@ -416,6 +442,7 @@ jagp_status_t run_sweeps(jagp_ctx *h, double *d_r, void *d_state, int W, int nsw
           lambda_products(h, pprop, pprop_lo, up ? a_up : bt, up, list, chunk, 0, 1, 0, W * n, d_state, W, st);
       if (q != JAGP_OK) return q;
       if (m1 < moves) {
+        group_key(t, hk, m0 / step, 2);
         q = run_refresh<T>(h, d_r, d_state, W, 1, false, st);
         if (q != JAGP_OK) return q;
       }
@@ -423,28 +450,34 @@ jagp_status_t run_sweeps(jagp_ctx *h, double *d_r, void *d_state, int W, int nsw
     return JAGP_OK;
   };
   // the three-body Jastrow's vectors from the positions (the acceptance kernels keep them current)
+  group_key(-1, 0, 0, 0);
   if (d.use_j3 && nsweeps > 0) LAUNCH(0, 1, launch_j3_prep(d, d_r, j3_vectors(h, L, d_state), W, st));
   for (int t = 0; t < nsweeps; ++t) {
     const uint32_t sw = (uint32_t)(sweep0 + (uint64_t)t);
-    JAGP_CU(cudaMemsetAsync(count, 0, 2 * sizeof(int), st));
+    group_key(t, 0, 0, 0);
+    JAGP_CU(zero_ints(count, 2, st));
     // up electrons: rows of G~ against the frozen down-spin table Bt
-    s = half_sweep(true, sw);
+    s = half_sweep(true, sw, t);
     if (s != JAGP_OK) return s;
     if (half_refresh && d.n_dn > 0) {
+      group_key(t, 2, 0, 0);
       s = run_refresh<T>(h, d_r, d_state, W, 1, false, st);
       if (s != JAGP_OK) return s;
     }
     // down electrons: columns of G~ against the updated up-spin table A_up
-    s = half_sweep(false, sw);
+    s = half_sweep(false, sw, t);
     if (s != JAGP_OK) return s;
     double *eL = d_eL ? d_eL + (accumulate ? 0 : (size_t)t * W) : nullptr;
     // the local-energy pass also forms J, so the refresh skips its Jastrow pass then
+    group_key(t, 4, 0, 0);
     s = run_refresh<T>(h, d_r, d_state, W, 1, eL == nullptr, st);
     if (s != JAGP_OK) return s;
     if (eL) {
+      group_key(t, 4, 0, 1);
       s = run_local_energy<T>(h, d_r, d_state, W, eL, nullptr, st, true);
       if (s != JAGP_OK) return s;
     }
+    group_key(t, 4, 0, 2);
     if (d_acc)
       LAUNCH(0, 1, launch_reduce_acc(eL, scal, count, W, d_acc + (accumulate ? 0 : (size_t)t * 4), st, accumulate));
   }
@@ -1230,8 +1263,26 @@ static jagp_status_t jagp_walker_status_impl(jagp_handle_t h, const void *d_stat
 // ---------------------------------------------------------------------------
 }  // extern "C"
 
+// one launch of the grouped sweep: kernel fn over the entries of table
+struct GroupLaunch {
+  const void *fn;
+  dim3 block;
+  size_t smem;
+  int blocks;
+  size_t tab_off;     // byte offset of the argument packs in the blob
+  size_t pack_bytes;  // size of one argument pack
+  int lane;
+  GroupTable table;
+};
+
 struct jagp_batch {
   int S = 0;
+  bool grouped = false;          // one launch per kernel and point of the sweep over all systems
+  void *blob = nullptr;          // device: entry tables and argument packs of the grouped launches
+  std::vector<GroupLaunch> glaunch;
+  int group_lanes = 1;           // concurrent chains of grouped launches
+  std::vector<cudaStream_t> lane_streams;
+  std::vector<cudaEvent_t> lane_events;
   std::vector<jagp_ctx *> h;
   std::vector<void *> state;
   std::vector<double *> r, eL;
@@ -1250,12 +1301,215 @@ struct jagp_batch {
 };
 
 namespace {
+// the per-system streams: systems by decreasing cost (order), each onto the
+// least-loaded of K streams at its turn, so that the streams of the graph end
+// at about the same time (round robin leaves the stream with the largest
+// systems about half again above the mean)
+std::vector<int> batch_lanes(jagp_batch *b, int K) {
+  auto cost = [&](int q) {
+    const double n = b->h[q]->ds.n_up, L = b->h[q]->ds.L;
+    return (double)b->W[q] * (n * L * L + n * n * L);
+  };
+  b->order.resize(b->S);
+  for (int q = 0; q < b->S; ++q) b->order[q] = q;
+  std::stable_sort(b->order.begin(), b->order.end(), [&](int a, int c) { return cost(a) > cost(c); });
+  std::vector<int> lane;
+  std::vector<double> load(K, 0.0);
+  for (int q = 0; q < b->S; ++q) {
+    int best = 0;
+    for (int k = 1; k < K; ++k)
+      if (load[k] < load[best]) best = k;
+    lane.push_back(best);
+    load[best] += cost(b->order[q]);
+  }
+  return lane;
+}
+
 __global__ void k_set_counter(uint32_t *c, uint32_t v) {
   if (threadIdx.x == 0) *c = v;
 }
 
+// Grouped sweep: record each system's launch sequence of one sweep (nothing
+// runs; a launcher that cannot be recorded would be caught by the capture of
+// the scratch stream), order all records by their point of the sweep (the
+// keys set in run_sweeps / run_refresh, then the order within that point),
+// and issue the records of the same kernel at the same point as one grouped
+// launch.  Each system's own launches keep their order, and launches of
+// different systems are independent, so every system sees exactly its
+// per-system sequence.  Returns UNSUPPORTED when a sequence cannot be grouped.
+jagp_status_t batch_build_grouped(jagp_batch *b) {
+  cudaStream_t st = b->cap;
+  std::vector<GroupRecord> all;
+  for (int q = 0; q < b->S; ++q) {
+    jagp_ctx *h = b->h[q];
+    GroupRecorder R;
+    R.sys = q;
+    const int prof = h->prof_kernel;
+    h->prof_kernel = 0;
+    JAGP_CU(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    set_group_recorder(&R);
+    jagp_status_t rc;
+    if (h->precision == JAGP_PREC_MIXED)
+      rc = run_sweeps<float>(h, b->r[q], b->state[q], b->W[q], 1, b->walker0[q], 0, b->eL[q],
+                             b->acc ? b->acc + 4 * (size_t)q : nullptr, st, b->counter, 1);
+    else
+      rc = run_sweeps<double>(h, b->r[q], b->state[q], b->W[q], 1, b->walker0[q], 0, b->eL[q],
+                              b->acc ? b->acc + 4 * (size_t)q : nullptr, st, b->counter, 1);
+    set_group_recorder(nullptr);
+    h->prof_kernel = prof;
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(st, &g);
+    size_t nodes = 0;
+    if (g) {
+      cudaGraphGetNodes(g, nullptr, &nodes);
+      cudaGraphDestroy(g);
+    }
+    if (e != cudaSuccess) {
+      g_last_cuda_error = cudaGetErrorString(e);
+      return JAGP_ERR_CUDA;
+    }
+    if (rc != JAGP_OK) return rc;
+    if (nodes != 0) return JAGP_ERR_UNSUPPORTED;  // a launch that bypassed the recorder
+    for (auto &r : R.recs) all.push_back(std::move(r));
+  }
+  // lanes: disjoint sets of systems (balanced by cost), each its own chain of
+  // grouped launches on its own stream of the graph, so that the lanes' kernels overlap
+  const int lanes = std::max(1, std::min(b->group_lanes, b->S));
+  std::vector<int> lane_of(b->S, 0);
+  if (lanes > 1) {
+    const std::vector<int> ln = batch_lanes(b, lanes);
+    for (int q = 0; q < b->S; ++q) lane_of[b->order[q]] = ln[q];
+  }
+  for (auto &r : all) r.lane = lane_of[r.sys];
+  auto point_less = [](const GroupRecord &a, const GroupRecord &c) {
+    if (a.lane != c.lane) return a.lane < c.lane;
+    for (int i = 0; i < 5; ++i)
+      if (a.key[i] != c.key[i]) return a.key[i] < c.key[i];
+    return a.seq < c.seq;
+  };
+  // every system's sequence must advance through the points in order
+  {
+    std::vector<const GroupRecord *> last(b->S, nullptr);
+    for (const auto &r : all) {
+      if (last[r.sys] && !point_less(*last[r.sys], r)) return JAGP_ERR_UNSUPPORTED;
+      last[r.sys] = &r;
+    }
+  }
+  auto same_launch = [](const GroupRecord &a, const GroupRecord &c) {
+    return a.fn == c.fn && a.block.x == c.block.x && a.block.y == c.block.y && a.block.z == c.block.z;
+  };
+  std::stable_sort(all.begin(), all.end(), [&](const GroupRecord &a, const GroupRecord &c) {
+    if (point_less(a, c)) return true;
+    if (point_less(c, a)) return false;
+    if (a.fn != c.fn) return std::less<const void *>()(a.fn, c.fn);
+    if (a.block.x != c.block.x) return a.block.x < c.block.x;
+    return a.block.y * 1024 + a.block.z < c.block.y * 1024 + c.block.z;
+  });
+  // lay out the entry tables and argument packs
+  std::vector<unsigned char> host;
+  auto place = [&](size_t bytes, size_t align) {
+    size_t off = (host.size() + align - 1) / align * align;
+    host.resize(off + bytes);
+    return off;
+  };
+  b->glaunch.clear();
+  for (size_t i = 0; i < all.size();) {
+    // records of one kernel at one point (at most kGroupMax per launch)
+    size_t j = i + 1;
+    while (j < all.size() && j - i < (size_t)kGroupMax && !point_less(all[i], all[j]) && same_launch(all[i], all[j]))
+      ++j;
+    GroupLaunch gl{};
+    gl.fn = all[i].fn;
+    gl.block = all[i].block;
+    gl.lane = all[i].lane;
+    gl.table.n = (int)(j - i);
+    const size_t psz = all[i].args.size();
+    if (psz % all[i].align) return JAGP_ERR_UNSUPPORTED;
+    gl.tab_off = place((size_t)gl.table.n * psz, 256);
+    gl.pack_bytes = psz;
+    long long blocks = 0;
+    for (size_t k = i; k < j; ++k) {
+      const GroupRecord &r = all[k];
+      if (r.args.size() != psz) return JAGP_ERR_UNSUPPORTED;
+      gl.table.start[k - i] = (int)blocks;
+      gl.table.dims[k - i][0] = (int)r.grid.x;
+      gl.table.dims[k - i][1] = (int)r.grid.y;
+      gl.table.dims[k - i][2] = (int)r.grid.z;
+      memcpy(host.data() + gl.tab_off + (k - i) * psz, r.args.data(), psz);
+      blocks += (long long)r.grid.x * r.grid.y * r.grid.z;
+      if (blocks > 0x7fffffffLL) return JAGP_ERR_UNSUPPORTED;
+      gl.smem = std::max(gl.smem, r.smem);
+    }
+    gl.table.start[gl.table.n] = (int)blocks;
+    gl.blocks = (int)blocks;
+    b->glaunch.push_back(gl);
+    i = j;
+  }
+  if (b->blob) cudaFree(b->blob);
+  b->blob = nullptr;
+  JAGP_CU(cudaMalloc(&b->blob, std::max<size_t>(host.size(), 256)));
+  JAGP_CU(cudaMemcpy(b->blob, host.data(), host.size(), cudaMemcpyHostToDevice));
+  // dynamic shared memory beyond 48 KB: the kernel's limit raised to the device's
+  for (const auto &gl : b->glaunch)
+    if (gl.smem > 48 * 1024) {
+      unsigned char done[64] = {};
+      JAGP_CU(group_raise_smem(gl.fn, done));
+    }
+  // capture: each lane's grouped launches in order on its stream (forked from
+  // and joined back into the capture stream), then the sweep counter
+  while ((int)b->lane_streams.size() < lanes) {
+    cudaStream_t s2;
+    cudaEvent_t e2;
+    JAGP_CU(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
+    b->lane_streams.push_back(s2);
+    JAGP_CU(cudaEventCreateWithFlags(&e2, cudaEventDisableTiming));
+    b->lane_events.push_back(e2);
+  }
+  JAGP_CU(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  cudaError_t le = cudaEventRecord(b->ev0, st);
+  for (int k = 0; k < lanes && le == cudaSuccess; ++k) le = cudaStreamWaitEvent(b->lane_streams[k], b->ev0, 0);
+  for (auto &gl : b->glaunch) {
+    if (le != cudaSuccess) break;
+    void *tab = static_cast<char *>(b->blob) + gl.tab_off;
+    void *args[2] = {&tab, &gl.table};
+    le = cudaLaunchKernel(gl.fn, dim3(gl.blocks), gl.block, args, gl.smem, b->lane_streams[gl.lane]);
+  }
+  for (int k = 0; k < lanes && le == cudaSuccess; ++k) {
+    le = cudaEventRecord(b->lane_events[k], b->lane_streams[k]);
+    if (le == cudaSuccess) le = cudaStreamWaitEvent(st, b->lane_events[k], 0);
+  }
+  if (le == cudaSuccess) le = launch_increment(b->counter, 1, st);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(st, &g);
+  if (le != cudaSuccess || e != cudaSuccess || !g) {
+    g_last_cuda_error = cudaGetErrorString(le != cudaSuccess ? le : e);
+    if (g) cudaGraphDestroy(g);
+    return JAGP_ERR_CUDA;
+  }
+  b->graph = g;
+  JAGP_CU(cudaGraphInstantiate(&b->exec, g, 0));
+  b->grouped = true;
+  return JAGP_OK;
+}
+
 jagp_status_t batch_capture(jagp_batch *b) {
   cudaStream_t st = b->cap;
+  if (b->streams.empty()) {
+    // grouped launches, or the per-system streams when a sequence cannot be grouped
+    const jagp_status_t rc = batch_build_grouped(b);
+    if (rc != JAGP_ERR_UNSUPPORTED) return rc;
+    cudaGetLastError();
+    const int K = std::max(1, std::min(8, b->S));
+    for (int k = 0; k < K; ++k) {
+      cudaStream_t s2;
+      cudaEvent_t e2;
+      JAGP_CU(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
+      b->streams.push_back(s2);
+      JAGP_CU(cudaEventCreateWithFlags(&e2, cudaEventDisableTiming));
+      b->ev.push_back(e2);
+    }
+    b->lane = batch_lanes(b, K);
+  }
   JAGP_CU(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
   jagp_status_t rc = JAGP_OK;
   cudaEventRecord(b->ev0, st);
@@ -1318,27 +1572,12 @@ jagp_status_t jagp_batch_create(jagp_batch_t *out, int S, const jagp_handle_t *h
     b->walker0.push_back(walker0 ? walker0[q] : 0);
     b->order.push_back(q);
   }
-  // largest systems first so that the concurrent streams finish together
-  auto cost = [&](int q) {
-    const double n = b->h[q]->ds.n_up, L = b->h[q]->ds.L;
-    return (double)b->W[q] * (n * L * L + n * n * L);
-  };
-  std::stable_sort(b->order.begin(), b->order.end(), [&](int a, int c) { return cost(a) > cost(c); });
   b->acc = d_acc;
-  const int K = std::max(1, std::min(n_streams > 0 ? n_streams : 8, S));
-  // longest first onto the least-loaded stream, so that the streams of the
-  // graph end at about the same time (round robin leaves the stream with the
-  // largest systems about half again above the mean)
-  {
-    std::vector<double> load(K, 0.0);
-    for (int q = 0; q < S; ++q) {
-      int best = 0;
-      for (int k = 1; k < K; ++k)
-        if (load[k] < load[best]) best = k;
-      b->lane.push_back(best);
-      load[best] += cost(b->order[q]);
-    }
-  }
+  // n_streams > 0: per-system launches over that many streams; 0 or -k:
+  // grouped launches in one or k lanes (the streams only as the fallback)
+  const int K = n_streams > 0 ? std::max(1, std::min(n_streams, S)) : 0;
+  b->group_lanes = n_streams < 0 ? -n_streams : 1;
+  if (K > 0) b->lane = batch_lanes(b, K);
   bool ok = cudaMalloc(&b->counter, sizeof(uint32_t)) == cudaSuccess &&
             cudaMemset(b->counter, 0, sizeof(uint32_t)) == cudaSuccess &&
             cudaEventCreateWithFlags(&b->ev0, cudaEventDisableTiming) == cudaSuccess &&
@@ -1403,6 +1642,9 @@ jagp_status_t jagp_batch_destroy(jagp_batch_t b) {
   if (b->ev0) cudaEventDestroy(b->ev0);
   if (b->cap) cudaStreamDestroy(b->cap);
   if (b->counter) cudaFree(b->counter);
+  if (b->blob) cudaFree(b->blob);
+  for (auto s2 : b->lane_streams) cudaStreamDestroy(s2);
+  for (auto e2 : b->lane_events) cudaEventDestroy(e2);
   delete b;
   return JAGP_OK;
 }

@@ -24,6 +24,14 @@ constexpr int kMmatDwMaxUp = 32;     // mixed path: exact M vectors on the CUDA 
 
 // Shell record packed for one 32-byte load: centre (x, y, z) and exponent.
 // info = l | radial << 2 | first-function-offset << 8.
+// Tell the compiler that these (non-null) pointers address global memory, so
+// that it may use global loads and stores through them where it cannot infer
+// that from where they came from (kernel arguments read from memory).
+template <class... P>
+__device__ __forceinline__ void assume_global(const P *...p) {
+  (__builtin_assume(__isGlobal(p)), ...);
+}
+
 struct DevSystem {
   int n_atoms, n_shells, L, n_up, n_dn, N;
   const double *R;          // [n_atoms][3]

@@ -31,6 +31,8 @@
 
 #include <mutex>
 
+#include "jagp_group.cuh"
+#include "jagp_group.cuh"
 #include "jagp_launch.h"
 
 namespace jagp {
@@ -115,6 +117,14 @@ __device__ __forceinline__ void umma_commit(uint32_t bar) {
                : "memory");
 }
 
+// tensor maps read from global memory (the grouped launches keep them with
+// their arguments there): order the generic-proxy writes that placed them
+// before their use by the tensor-map proxy.  Kernel-parameter maps need nothing.
+__device__ __forceinline__ void tensormap_acquire(const CUtensorMap *a, const CUtensorMap *b) {
+  if (__isGlobal(a)) asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(a) : "memory");
+  if (__isGlobal(b)) asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(b) : "memory");
+}
+
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -164,239 +174,248 @@ struct UmmaArgs {
   int *err;
 };
 
-__global__ void __launch_bounds__(128) k_umma_gemm(const __grid_constant__ CUtensorMap tmA,
-                                                      const __grid_constant__ CUtensorMap tmB, UmmaArgs g) {
-  extern __shared__ uint8_t smem_raw[];
-  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  const int M = g.m_dev ? *g.m_dev : g.m_max;
-  // batched mode: tile t of batch b starts at row b * batch_rows + 128 t; rows
-  // past the batch's end (read from the next batch) are computed but not written
-  // grouped tile order: CTAs in launch order walk kGroupM row tiles of one
-  // column tile before the next column tile, so that a wave reuses both A and
-  // B tiles from L2 (with large K the operands exceed L2)
-  int tile_y, tile_x;
-  {
-    const int tiles_n = gridDim.x, tiles_m = gridDim.y;
-    const int pid = blockIdx.x + blockIdx.y * tiles_n;
-    const int span = kGroupM * tiles_n;
-    const int first = (pid / span) * kGroupM;
-    const int gsize = tiles_m - first < kGroupM ? tiles_m - first : kGroupM;
-    const int r = pid - (pid / span) * span;
-    tile_y = first + r % gsize;
-    tile_x = r / gsize;
-  }
-  const int bb = g.batch_rows ? tile_y / g.tiles_per_batch : 0;
-  const int bt0 = g.batch_rows ? (tile_y - bb * g.tiles_per_batch) * 128 : 0;
-  const int m0 = g.batch_rows ? bb * g.batch_rows + bt0 : tile_y * 128;
-  const int bbase = bb * g.b_batch_rows;  // first B row (and column exponent) of this batch
-  if (m0 >= M) return;  // whole CTA, before any barrier or tensor-memory use
-  const int n0 = tile_x * g.bn;
-  const uint32_t row_bytes = static_cast<uint32_t>(g.cw) * 2u;  // 128, 64 or 32
-  const uint32_t a_bytes = 128u * row_bytes;
-  const uint32_t b_bytes = static_cast<uint32_t>(g.bn) * row_bytes;
-  const int ksteps = g.cw / 16;  // MMAs (K = 16) per chunk
-  const uint32_t stage_bytes =
-      g.chunk_major ? static_cast<uint32_t>(g.na) * a_bytes + static_cast<uint32_t>(g.nb) * b_bytes : a_bytes + b_bytes;
-  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + g.stages * stage_bytes);
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * g.stages + 1);
-  const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8u * g.stages, done = full0 + 16u * g.stages;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < g.stages; ++s) {
-      mbar_init(full0 + 8u * s, 1);
-      mbar_init(empty0 + 8u * s, 1);
+struct UmmaGemm {
+  static __device__ __forceinline__ void run(const CUtensorMap &tmA, const CUtensorMap &tmB, const UmmaArgs &g,
+                                             const uint3 bid, const uint3 gdim) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int M = g.m_dev ? *g.m_dev : g.m_max;
+    // batched mode: tile t of batch b starts at row b * batch_rows + 128 t; rows
+    // past the batch's end (read from the next batch) are computed but not written
+    // grouped tile order: CTAs in launch order walk kGroupM row tiles of one
+    // column tile before the next column tile, so that a wave reuses both A and
+    // B tiles from L2 (with large K the operands exceed L2)
+    int tile_y, tile_x;
+    {
+      const int tiles_n = gdim.x, tiles_m = gdim.y;
+      const int pid = bid.x + bid.y * tiles_n;
+      const int span = kGroupM * tiles_n;
+      const int first = (pid / span) * kGroupM;
+      const int gsize = tiles_m - first < kGroupM ? tiles_m - first : kGroupM;
+      const int r = pid - (pid / span) * span;
+      tile_y = first + r % gsize;
+      tile_x = r / gsize;
     }
-    mbar_init(done, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(g.tmem_cols)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = *tmem_slot;
-  const int kchunks = g.kp / g.cw;
-  const int iters = g.chunk_major ? kchunks : g.npairs * kchunks;
-  const uint32_t tiles = smem_u32(smem);
+    const int bb = g.batch_rows ? tile_y / g.tiles_per_batch : 0;
+    const int bt0 = g.batch_rows ? (tile_y - bb * g.tiles_per_batch) * 128 : 0;
+    const int m0 = g.batch_rows ? bb * g.batch_rows + bt0 : tile_y * 128;
+    const int bbase = bb * g.b_batch_rows;  // first B row (and column exponent) of this batch
+    if (m0 >= M) return;  // whole CTA, before any barrier or tensor-memory use
+    const int n0 = tile_x * g.bn;
+    const uint32_t row_bytes = static_cast<uint32_t>(g.cw) * 2u;  // 128, 64 or 32
+    const uint32_t a_bytes = 128u * row_bytes;
+    const uint32_t b_bytes = static_cast<uint32_t>(g.bn) * row_bytes;
+    const int ksteps = g.cw / 16;  // MMAs (K = 16) per chunk
+    const uint32_t stage_bytes =
+        g.chunk_major ? static_cast<uint32_t>(g.na) * a_bytes + static_cast<uint32_t>(g.nb) * b_bytes : a_bytes + b_bytes;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + g.stages * stage_bytes);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * g.stages + 1);
+    const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8u * g.stages, done = full0 + 16u * g.stages;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+      for (int s = 0; s < g.stages; ++s) {
+        mbar_init(full0 + 8u * s, 1);
+        mbar_init(empty0 + 8u * s, 1);
+      }
+      mbar_init(done, 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                   "r"(g.tmem_cols)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const int kchunks = g.kp / g.cw;
+    const int iters = g.chunk_major ? kchunks : g.npairs * kchunks;
+    const uint32_t tiles = smem_u32(smem);
 
-  if (warp == 0 && lane == 0 && g.chunk_major) {
-    // producer, chunk-major: every slice of A and B for one K chunk per stage
-    for (int it = 0; it < iters; ++it) {
-      const int s = it % g.stages;
-      const uint32_t use = static_cast<uint32_t>(it / g.stages);
-      if (it >= g.stages && !mbar_wait(empty0 + 8u * s, (use & 1u) ^ 1u)) {
-        atomicExch(g.err, 1);
-        break;
+    if (warp == 0 && lane == 0) tensormap_acquire(&tmA, &tmB);
+    if (warp == 0 && lane == 0 && g.chunk_major) {
+      // producer, chunk-major: every slice of A and B for one K chunk per stage
+      for (int it = 0; it < iters; ++it) {
+        const int s = it % g.stages;
+        const uint32_t use = static_cast<uint32_t>(it / g.stages);
+        if (it >= g.stages && !mbar_wait(empty0 + 8u * s, (use & 1u) ^ 1u)) {
+          atomicExch(g.err, 1);
+          break;
+        }
+        const uint32_t full = full0 + 8u * s, base = tiles + s * stage_bytes;
+        mbar_expect_tx(full, stage_bytes);
+        for (int a = 0; a < g.na; ++a) tma_load_2d(base + a * a_bytes, &tmA, a * g.kp + it * g.cw, m0, full);
+        for (int b = 0; b < g.nb; ++b)
+          tma_load_2d(base + g.na * a_bytes + b * b_bytes, &tmB, b * g.kp + it * g.cw, bbase + n0, full);
       }
-      const uint32_t full = full0 + 8u * s, base = tiles + s * stage_bytes;
-      mbar_expect_tx(full, stage_bytes);
-      for (int a = 0; a < g.na; ++a) tma_load_2d(base + a * a_bytes, &tmA, a * g.kp + it * g.cw, m0, full);
-      for (int b = 0; b < g.nb; ++b)
-        tma_load_2d(base + g.na * a_bytes + b * b_bytes, &tmB, b * g.kp + it * g.cw, bbase + n0, full);
-    }
-  } else if (warp == 1 && lane == 0 && g.chunk_major) {
-    // MMA issuer, chunk-major: all pairs of the chunk from the one stage
-    uint32_t started = 0;
-    for (int it = 0; it < iters; ++it) {
-      const int s = it % g.stages;
-      const uint32_t use = static_cast<uint32_t>(it / g.stages);
-      if (!mbar_wait(full0 + 8u * s, use & 1u)) {
-        atomicExch(g.err, 2);
-        break;
+    } else if (warp == 1 && lane == 0 && g.chunk_major) {
+      // MMA issuer, chunk-major: all pairs of the chunk from the one stage
+      uint32_t started = 0;
+      for (int it = 0; it < iters; ++it) {
+        const int s = it % g.stages;
+        const uint32_t use = static_cast<uint32_t>(it / g.stages);
+        if (!mbar_wait(full0 + 8u * s, use & 1u)) {
+          atomicExch(g.err, 2);
+          break;
+        }
+        tc_fence_after();
+        const uint32_t base = tiles + s * stage_bytes;
+        for (int p = 0; p < g.npairs; ++p) {
+          const int grp = g.pair_group[p];
+          const uint32_t a0 = base + g.pair_a[p] * a_bytes, b0 = base + g.na * a_bytes + g.pair_b[p] * b_bytes;
+          const uint32_t d_tmem = tmem + static_cast<uint32_t>(grp * g.bn);
+          for (int kk = 0; kk < ksteps; ++kk) {
+            umma_bf16(d_tmem, desc_kmajor(a0 + kk * 32, row_bytes), desc_kmajor(b0 + kk * 32, row_bytes), g.idesc,
+                      (started >> grp) & 1u);
+            started |= 1u << grp;
+          }
+        }
+        umma_commit(empty0 + 8u * s);
       }
-      tc_fence_after();
-      const uint32_t base = tiles + s * stage_bytes;
-      for (int p = 0; p < g.npairs; ++p) {
-        const int grp = g.pair_group[p];
-        const uint32_t a0 = base + g.pair_a[p] * a_bytes, b0 = base + g.na * a_bytes + g.pair_b[p] * b_bytes;
+      umma_commit(done);
+    } else if (warp == 0 && lane == 0) {
+      // producer: one A tile (128 x 64) and one B tile (bn x 64) per stage
+      for (int it = 0; it < iters; ++it) {
+        const int s = it % g.stages;
+        const uint32_t use = static_cast<uint32_t>(it / g.stages);
+        if (it >= g.stages && !mbar_wait(empty0 + 8u * s, (use & 1u) ^ 1u)) {
+          atomicExch(g.err, 1);
+          break;
+        }
+        const uint32_t full = full0 + 8u * s;
+        mbar_expect_tx(full, stage_bytes);
+        const int p = it / kchunks, c = it - p * kchunks;
+        tma_load_2d(tiles + s * stage_bytes, &tmA, g.pair_a[p] * g.kp + c * 64, m0, full);
+        tma_load_2d(tiles + s * stage_bytes + a_bytes, &tmB, g.pair_b[p] * g.kp + c * 64, bbase + n0, full);
+      }
+    } else if (warp == 1 && lane == 0) {
+      // MMA issuer: four K = 16 slices per 64-wide chunk, accumulating in TMEM
+      uint32_t started = 0;  // bit g: accumulator g has received its first product
+      for (int it = 0; it < iters; ++it) {
+        const int s = it % g.stages;
+        const uint32_t use = static_cast<uint32_t>(it / g.stages);
+        if (!mbar_wait(full0 + 8u * s, use & 1u)) {
+          atomicExch(g.err, 2);
+          break;
+        }
+        tc_fence_after();
+        const uint32_t a0 = tiles + s * stage_bytes, b0 = a0 + a_bytes;
+        const int grp = g.pair_group[it / kchunks];
         const uint32_t d_tmem = tmem + static_cast<uint32_t>(grp * g.bn);
-        for (int kk = 0; kk < ksteps; ++kk) {
-          umma_bf16(d_tmem, desc_kmajor(a0 + kk * 32, row_bytes), desc_kmajor(b0 + kk * 32, row_bytes), g.idesc,
+  #pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          umma_bf16(d_tmem, desc_kmajor(a0 + kk * 32, 128u), desc_kmajor(b0 + kk * 32, 128u), g.idesc,
                     (started >> grp) & 1u);
           started |= 1u << grp;
         }
+        umma_commit(empty0 + 8u * s);
       }
-      umma_commit(empty0 + 8u * s);
+      umma_commit(done);  // arrives once every MMA issued above has completed
     }
-    umma_commit(done);
-  } else if (warp == 0 && lane == 0) {
-    // producer: one A tile (128 x 64) and one B tile (bn x 64) per stage
-    for (int it = 0; it < iters; ++it) {
-      const int s = it % g.stages;
-      const uint32_t use = static_cast<uint32_t>(it / g.stages);
-      if (it >= g.stages && !mbar_wait(empty0 + 8u * s, (use & 1u) ^ 1u)) {
-        atomicExch(g.err, 1);
-        break;
-      }
-      const uint32_t full = full0 + 8u * s;
-      mbar_expect_tx(full, stage_bytes);
-      const int p = it / kchunks, c = it - p * kchunks;
-      tma_load_2d(tiles + s * stage_bytes, &tmA, g.pair_a[p] * g.kp + c * 64, m0, full);
-      tma_load_2d(tiles + s * stage_bytes + a_bytes, &tmB, g.pair_b[p] * g.kp + c * 64, bbase + n0, full);
-    }
-  } else if (warp == 1 && lane == 0) {
-    // MMA issuer: four K = 16 slices per 64-wide chunk, accumulating in TMEM
-    uint32_t started = 0;  // bit g: accumulator g has received its first product
-    for (int it = 0; it < iters; ++it) {
-      const int s = it % g.stages;
-      const uint32_t use = static_cast<uint32_t>(it / g.stages);
-      if (!mbar_wait(full0 + 8u * s, use & 1u)) {
-        atomicExch(g.err, 2);
-        break;
-      }
-      tc_fence_after();
-      const uint32_t a0 = tiles + s * stage_bytes, b0 = a0 + a_bytes;
-      const int grp = g.pair_group[it / kchunks];
-      const uint32_t d_tmem = tmem + static_cast<uint32_t>(grp * g.bn);
-#pragma unroll
-      for (int kk = 0; kk < 4; ++kk) {
-        umma_bf16(d_tmem, desc_kmajor(a0 + kk * 32, 128u), desc_kmajor(b0 + kk * 32, 128u), g.idesc,
-                  (started >> grp) & 1u);
-        started |= 1u << grp;
-      }
-      umma_commit(empty0 + 8u * s);
-    }
-    umma_commit(done);  // arrives once every MMA issued above has completed
-  }
-  __syncwarp();
+    __syncwarp();
 
-  // epilogue: tensor memory -> registers -> FP32 rows
-  const bool ready = __all_sync(0xffffffffu, mbar_wait(done, 0));  // warp-uniform for tcgen05.ld
-  tc_fence_after();
-  if (ready) {
-    const int row = m0 + warp * 32 + lane;
-    const bool live = row < M && (!g.batch_rows || bt0 + warp * 32 + lane < g.batch_rows);
-    const long long dst = live ? (g.out_rows ? g.out_rows[row] : row) : 0;
-    // element offset of this row's column 0 and the stride between columns
-    const long long obase = g.o_cstride ? (long long)bb * g.o_bstride + (long long)(bt0 + warp * 32 + lane) * g.o_rstride
-                                        : dst * g.ldo;
-    const long long ocs = g.o_cstride ? g.o_cstride : 1;
-    const uint32_t t_row = tmem + (static_cast<uint32_t>(warp * 32) << 16);
-    const int ea = (g.a_exp && live) ? g.a_exp[row] : 0;
-    for (int c = 0; c < g.bn; c += 16) {
-      if (g.out64) {
-        // FP64 result: v = S_0 + 2^-b (S_1 + 2^-b (S_2 + ...)) by Horner in FP64
-        // from the exact integer sums, then the power-of-two scale
-        double acc[16];
-#pragma unroll
-        for (int j = 0; j < 16; ++j) acc[j] = 0.0;
-        const double wq = ldexp(1.0, -g.slice_bits);
-        for (int q = g.ngroups - 1; q >= 0; --q) {
-          float u[16];
-          tmem_ld16(t_row + static_cast<uint32_t>(q * g.bn + c), u);
-#pragma unroll
-          for (int j = 0; j < 16; ++j) acc[j] = fma(acc[j], wq, static_cast<double>(u[j]));
+    // epilogue: tensor memory -> registers -> FP32 rows
+    const bool ready = __all_sync(0xffffffffu, mbar_wait(done, 0));  // warp-uniform for tcgen05.ld
+    tc_fence_after();
+    if (ready) {
+      const int row = m0 + warp * 32 + lane;
+      const bool live = row < M && (!g.batch_rows || bt0 + warp * 32 + lane < g.batch_rows);
+      const long long dst = live ? (g.out_rows ? g.out_rows[row] : row) : 0;
+      // element offset of this row's column 0 and the stride between columns
+      const long long obase = g.o_cstride ? (long long)bb * g.o_bstride + (long long)(bt0 + warp * 32 + lane) * g.o_rstride
+                                          : dst * g.ldo;
+      const long long ocs = g.o_cstride ? g.o_cstride : 1;
+      const uint32_t t_row = tmem + (static_cast<uint32_t>(warp * 32) << 16);
+      const int ea = (g.a_exp && live) ? g.a_exp[row] : 0;
+      for (int c = 0; c < g.bn; c += 16) {
+        if (g.out64) {
+          // FP64 result: v = S_0 + 2^-b (S_1 + 2^-b (S_2 + ...)) by Horner in FP64
+          // from the exact integer sums, then the power-of-two scale
+          double acc[16];
+  #pragma unroll
+          for (int j = 0; j < 16; ++j) acc[j] = 0.0;
+          const double wq = ldexp(1.0, -g.slice_bits);
+          for (int q = g.ngroups - 1; q >= 0; --q) {
+            float u[16];
+            tmem_ld16(t_row + static_cast<uint32_t>(q * g.bn + c), u);
+  #pragma unroll
+            for (int j = 0; j < 16; ++j) acc[j] = fma(acc[j], wq, static_cast<double>(u[j]));
+          }
+          if (live) {
+            double *o = g.out64 + obase;
+  #pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const int col = n0 + c + j;
+              if (col < g.n) o[col * ocs] = ldexp(acc[j], ea + g.b_exp[bbase + col] - 2 * (g.slice_bits - 1));
+            }
+          }
+          continue;
+        }
+        float v[16];
+        tmem_ld16(t_row + static_cast<uint32_t>(c), v);
+        if (g.a_exp) {
+          // v = S_0 + S_1 / 256 + S_2 / 256^2 + ... as an unevaluated sum
+          // hi + lo of FP32 numbers: every S_d is an exact integer below 2^24 and
+          // each addition goes through an error-free transformation (TwoSum)
+          float lo[16];
+  #pragma unroll
+          for (int j = 0; j < 16; ++j) lo[j] = 0.0f;
+          float scale = 1.0f;
+          for (int q = 1; q < g.ngroups; ++q) {
+            float u[16];
+            tmem_ld16(t_row + static_cast<uint32_t>(q * g.bn + c), u);
+            scale *= 0.00390625f;
+  #pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const float b = __fmul_rn(u[j], scale);  // exact: power-of-two scaling
+              const float s = __fadd_rn(v[j], b);
+              const float z = __fsub_rn(s, v[j]);
+              const float e = __fadd_rn(__fsub_rn(v[j], __fsub_rn(s, z)), __fsub_rn(b, z));
+              v[j] = s;
+              lo[j] = __fadd_rn(lo[j], e);
+            }
+          }
+  #pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const float hi = __fadd_rn(v[j], lo[j]);
+            const float l2 = __fsub_rn(lo[j], __fsub_rn(hi, v[j]));
+            const int col = n0 + c + j;
+            const int sh = ea + (col < g.n ? g.b_exp[bbase + col] : 0) - 14;
+            v[j] = ldexpf(hi, sh);
+            lo[j] = ldexpf(l2, sh);
+          }
+          if (live && g.out_lo) {
+            float *ol = g.out_lo + obase;
+  #pragma unroll
+            for (int j = 0; j < 16; ++j)
+              if (n0 + c + j < g.n) ol[(n0 + c + j) * ocs] = lo[j];
+          }
         }
         if (live) {
-          double *o = g.out64 + obase;
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int col = n0 + c + j;
-            if (col < g.n) o[col * ocs] = ldexp(acc[j], ea + g.b_exp[bbase + col] - 2 * (g.slice_bits - 1));
-          }
-        }
-        continue;
-      }
-      float v[16];
-      tmem_ld16(t_row + static_cast<uint32_t>(c), v);
-      if (g.a_exp) {
-        // v = S_0 + S_1 / 256 + S_2 / 256^2 + ... as an unevaluated sum
-        // hi + lo of FP32 numbers: every S_d is an exact integer below 2^24 and
-        // each addition goes through an error-free transformation (TwoSum)
-        float lo[16];
-#pragma unroll
-        for (int j = 0; j < 16; ++j) lo[j] = 0.0f;
-        float scale = 1.0f;
-        for (int q = 1; q < g.ngroups; ++q) {
-          float u[16];
-          tmem_ld16(t_row + static_cast<uint32_t>(q * g.bn + c), u);
-          scale *= 0.00390625f;
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const float b = __fmul_rn(u[j], scale);  // exact: power-of-two scaling
-            const float s = __fadd_rn(v[j], b);
-            const float z = __fsub_rn(s, v[j]);
-            const float e = __fadd_rn(__fsub_rn(v[j], __fsub_rn(s, z)), __fsub_rn(b, z));
-            v[j] = s;
-            lo[j] = __fadd_rn(lo[j], e);
-          }
-        }
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const float hi = __fadd_rn(v[j], lo[j]);
-          const float l2 = __fsub_rn(lo[j], __fsub_rn(hi, v[j]));
-          const int col = n0 + c + j;
-          const int sh = ea + (col < g.n ? g.b_exp[bbase + col] : 0) - 14;
-          v[j] = ldexpf(hi, sh);
-          lo[j] = ldexpf(l2, sh);
-        }
-        if (live && g.out_lo) {
-          float *ol = g.out_lo + obase;
-#pragma unroll
+          float *o = g.out + obase;
+  #pragma unroll
           for (int j = 0; j < 16; ++j)
-            if (n0 + c + j < g.n) ol[(n0 + c + j) * ocs] = lo[j];
+            if (n0 + c + j < g.n) o[(n0 + c + j) * ocs] = v[j];
         }
       }
-      if (live) {
-        float *o = g.out + obase;
-#pragma unroll
-        for (int j = 0; j < 16; ++j)
-          if (n0 + c + j < g.n) o[(n0 + c + j) * ocs] = v[j];
-      }
+    } else if (lane == 0) {
+      atomicExch(g.err, 3);
     }
-  } else if (lane == 0) {
-    atomicExch(g.err, 3);
-  }
-  tc_fence_before();
-  __syncthreads();
-  if (warp == 0) {
-    tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(g.tmem_cols) : "memory");
-  }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+      tc_fence_after();
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(g.tmem_cols) : "memory");
+    }
+}
+};
+
+__global__ void __launch_bounds__(128) k_umma_gemm(const __grid_constant__ CUtensorMap tmA,
+                                                      const __grid_constant__ CUtensorMap tmB,
+                                                      const __grid_constant__ UmmaArgs g) {
+  UmmaGemm::run(tmA, tmB, g, blockIdx, gridDim);
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -559,8 +578,7 @@ cudaError_t launch_umma_gemm(const uint16_t *A, int m_max, const int *m_dev, int
     return cudaErrorInvalidValue;
   const size_t smem = 1024 + static_cast<size_t>(g.stages) * stage_bytes + 8 * (2 * g.stages + 1) + 16;
   dim3 grid((n + g.bn - 1) / g.bn, batch_rows > 0 ? batches * g.tiles_per_batch : (m_max + 127) / 128);
-  k_umma_gemm<<<grid, 128, smem, st>>>(ta, tb, g);
-  return cudaGetLastError();
+  return launch_or_record<UmmaGemm, 128>(k_umma_gemm, grid, dim3(128), smem, st, ta, tb, g);
 }
 
 // ---------------------------------------------------------------------------
@@ -576,42 +594,53 @@ cudaError_t launch_umma_gemm(const uint16_t *A, int m_max, const int *m_dev, int
 // from slice to slice as an exact two-float sum (TwoSum), so that the slices
 // take the low part's bits as well.
 // ---------------------------------------------------------------------------
+struct PackFixed {
+  static __device__ __forceinline__ void run(const float *__restrict__ P, const float *__restrict__ P_lo,
+                                                     const int *__restrict__ list, const int *__restrict__ count,
+                                                     int nrows, int nsub, int stride, int L, int kp,
+                                                     __nv_bfloat16 *__restrict__ A, int *__restrict__ rows_out,
+                                                     int *__restrict__ exps,
+                                             const uint3 bid, const uint3 gdim) {
+    assume_global(P, A, rows_out, exps);
+    const int rows = count ? *count : nrows;
+    const int lane = threadIdx.x & 31;
+    const long nw = (long)gdim.x * (blockDim.x >> 5);
+    for (long m = (long)bid.x * (blockDim.x >> 5) + (threadIdx.x >> 5); m < rows; m += nw) {
+      const long phys = list ? (long)list[m] : (m / nsub) * stride + (m % nsub);
+      const float *src = P + phys * L;
+      const float *srl = P_lo ? P_lo + phys * L : nullptr;
+      float mx = 0.0f;
+      for (int k = lane; k < L; k += 32) mx = fmaxf(mx, fabsf(src[k]));
+  #pragma unroll
+      for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      const int e = (mx > 0.0f) ? ilogbf(mx) + 1 : 0;
+      if (lane == 0) {
+        rows_out[m] = (int)phys;
+        exps[m] = e;
+      }
+      __nv_bfloat16 *dst = A + m * kFixedSlices * (long)kp;
+      for (int k = lane; k < kp; k += 32) {
+        float x = k < L ? ldexpf(src[k], 7 - e) : 0.0f;  // |x| < 128
+        // the low part, in the same scale
+        float xl = (srl && k < L) ? ldexpf(srl[k], 7 - e) : 0.0f;
+  #pragma unroll
+        for (int t = 0; t < kFixedSlices; ++t) {
+          const float q = rintf(x);
+          dst[t * kp + k] = __float2bfloat16_rn(q);
+          const fdw r = two_sum(__fsub_rn(x, q), xl);  // remainder + low part, exactly
+          x = __fmul_rn(r.hi, 256.0f);
+          xl = __fmul_rn(r.lo, 256.0f);
+        }
+      }
+    }
+}
+};
 __global__ void __launch_bounds__(256) k_pack_fixed(const float *__restrict__ P, const float *__restrict__ P_lo,
                                                      const int *__restrict__ list, const int *__restrict__ count,
                                                      int nrows, int nsub, int stride, int L, int kp,
                                                      __nv_bfloat16 *__restrict__ A, int *__restrict__ rows_out,
                                                      int *__restrict__ exps) {
-  const int rows = count ? *count : nrows;
-  const int lane = threadIdx.x & 31;
-  const long nw = (long)gridDim.x * (blockDim.x >> 5);
-  for (long m = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); m < rows; m += nw) {
-    const long phys = list ? (long)list[m] : (m / nsub) * stride + (m % nsub);
-    const float *src = P + phys * L;
-    const float *srl = P_lo ? P_lo + phys * L : nullptr;
-    float mx = 0.0f;
-    for (int k = lane; k < L; k += 32) mx = fmaxf(mx, fabsf(src[k]));
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    const int e = (mx > 0.0f) ? ilogbf(mx) + 1 : 0;
-    if (lane == 0) {
-      rows_out[m] = (int)phys;
-      exps[m] = e;
-    }
-    __nv_bfloat16 *dst = A + m * kFixedSlices * (long)kp;
-    for (int k = lane; k < kp; k += 32) {
-      float x = k < L ? ldexpf(src[k], 7 - e) : 0.0f;  // |x| < 128
-      // the low part, in the same scale
-      float xl = (srl && k < L) ? ldexpf(srl[k], 7 - e) : 0.0f;
-#pragma unroll
-      for (int t = 0; t < kFixedSlices; ++t) {
-        const float q = rintf(x);
-        dst[t * kp + k] = __float2bfloat16_rn(q);
-        const fdw r = two_sum(__fsub_rn(x, q), xl);  // remainder + low part, exactly
-        x = __fmul_rn(r.hi, 256.0f);
-        xl = __fmul_rn(r.lo, 256.0f);
-      }
-    }
-  }
+  PackFixed::run(P, P_lo, list, count, nrows, nsub, stride, L, kp, A, rows_out, exps, blockIdx, gridDim);
 }
 
 cudaError_t launch_pack_fixed(const float *P, const float *P_lo, const int *list, const int *count, int nrows,
@@ -620,46 +649,57 @@ cudaError_t launch_pack_fixed(const float *P, const float *P_lo, const int *list
   if (max_rows <= 0) return cudaSuccess;
   long blocks = (max_rows + 7) / 8;
   if (blocks > 152 * 16) blocks = 152 * 16;
-  k_pack_fixed<<<(int)blocks, 256, 0, st>>>(P, P_lo, list, count, nrows, nsub > 0 ? nsub : 1, stride, L, kp,
-                                              reinterpret_cast<__nv_bfloat16 *>(A), rows_out, exps);
-  return cudaGetLastError();
+  return launch_or_record<PackFixed, 256>(k_pack_fixed, dim3((int)blocks), dim3(256), 0, st, P, P_lo, list, count,
+                                          nrows, nsub > 0 ? nsub : 1, stride, L, kp,
+                                          reinterpret_cast<__nv_bfloat16 *>(A), rows_out, exps);
 }
 
 // FP64 rows -> nsl exact slices of `bits` bits (|t| <= 2^(bits-1), BF16) per
 // element relative to 2^e, e = 1 + the binary exponent of the row's largest
 // magnitude, for the FP64-equivalent products (every step exact in FP64).
+struct PackFixed64 {
+  static __device__ __forceinline__ void run(const double *__restrict__ P, const int *__restrict__ list,
+                                                      const int *__restrict__ count, int nrows, int nsub, int stride,
+                                                      int L, int kp, int nsl, int bits,
+                                                      __nv_bfloat16 *__restrict__ A, int *__restrict__ rows_out,
+                                                      int *__restrict__ exps, long dst_stride, long dst_off,
+                                             const uint3 bid, const uint3 gdim) {
+    assume_global(P, A, rows_out, exps);
+    const int rows = count ? *count : nrows;
+    const int lane = threadIdx.x & 31;
+    const long nw = (long)gdim.x * (blockDim.x >> 5);
+    const double step = ldexp(1.0, bits);
+    for (long m = (long)bid.x * (blockDim.x >> 5) + (threadIdx.x >> 5); m < rows; m += nw) {
+      const long phys = list ? (long)list[m] : (m / nsub) * stride + (m % nsub);
+      const double *src = P + phys * L;
+      double mx = 0.0;
+      for (int k = lane; k < L; k += 32) mx = fmax(mx, fabs(src[k]));
+  #pragma unroll
+      for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      const int e = (mx > 0.0) ? ilogb(mx) + 1 : 0;
+      if (lane == 0) {
+        // the row of the result: the source row, or (m / nsub) * dst_stride + dst_off + m % nsub
+        rows_out[m] = dst_stride > 0 ? (int)((m / nsub) * dst_stride + dst_off + m % nsub) : (int)phys;
+        exps[m] = e;
+      }
+      __nv_bfloat16 *dst = A + m * nsl * (long)kp;
+      for (int k = lane; k < kp; k += 32) {
+        double x = k < L ? ldexp(src[k], bits - 1 - e) : 0.0;  // |x| < 2^(bits-1)
+        for (int t = 0; t < nsl; ++t) {
+          const double q = rint(x);
+          dst[t * kp + k] = __float2bfloat16_rn(static_cast<float>(q));
+          x = (x - q) * step;
+        }
+      }
+    }
+}
+};
 __global__ void __launch_bounds__(256) k_pack_fixed64(const double *__restrict__ P, const int *__restrict__ list,
                                                       const int *__restrict__ count, int nrows, int nsub, int stride,
                                                       int L, int kp, int nsl, int bits,
                                                       __nv_bfloat16 *__restrict__ A, int *__restrict__ rows_out,
                                                       int *__restrict__ exps, long dst_stride, long dst_off) {
-  const int rows = count ? *count : nrows;
-  const int lane = threadIdx.x & 31;
-  const long nw = (long)gridDim.x * (blockDim.x >> 5);
-  const double step = ldexp(1.0, bits);
-  for (long m = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); m < rows; m += nw) {
-    const long phys = list ? (long)list[m] : (m / nsub) * stride + (m % nsub);
-    const double *src = P + phys * L;
-    double mx = 0.0;
-    for (int k = lane; k < L; k += 32) mx = fmax(mx, fabs(src[k]));
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    const int e = (mx > 0.0) ? ilogb(mx) + 1 : 0;
-    if (lane == 0) {
-      // the row of the result: the source row, or (m / nsub) * dst_stride + dst_off + m % nsub
-      rows_out[m] = dst_stride > 0 ? (int)((m / nsub) * dst_stride + dst_off + m % nsub) : (int)phys;
-      exps[m] = e;
-    }
-    __nv_bfloat16 *dst = A + m * nsl * (long)kp;
-    for (int k = lane; k < kp; k += 32) {
-      double x = k < L ? ldexp(src[k], bits - 1 - e) : 0.0;  // |x| < 2^(bits-1)
-      for (int t = 0; t < nsl; ++t) {
-        const double q = rint(x);
-        dst[t * kp + k] = __float2bfloat16_rn(static_cast<float>(q));
-        x = (x - q) * step;
-      }
-    }
-  }
+  PackFixed64::run(P, list, count, nrows, nsub, stride, L, kp, nsl, bits, A, rows_out, exps, dst_stride, dst_off, blockIdx, gridDim);
 }
 
 cudaError_t launch_pack_fixed64(const double *P, const int *list, const int *count, int nrows, int nsub, int stride,
@@ -668,10 +708,9 @@ cudaError_t launch_pack_fixed64(const double *P, const int *list, const int *cou
   if (max_rows <= 0) return cudaSuccess;
   long blocks = (max_rows + 7) / 8;
   if (blocks > 152 * 16) blocks = 152 * 16;
-  k_pack_fixed64<<<(int)blocks, 256, 0, st>>>(P, list, count, nrows, nsub > 0 ? nsub : 1, stride, L, kp, nsl, bits,
-                                               reinterpret_cast<__nv_bfloat16 *>(A), rows_out, exps, dst_stride,
-                                               dst_off);
-  return cudaGetLastError();
+  return launch_or_record<PackFixed64, 256>(k_pack_fixed64, dim3((int)blocks), dim3(256), 0, st, P, list, count, nrows,
+                                            nsub > 0 ? nsub : 1, stride, L, kp, nsl, bits,
+                                            reinterpret_cast<__nv_bfloat16 *>(A), rows_out, exps, dst_stride, dst_off);
 }
 
 // ---------------------------------------------------------------------------
@@ -690,119 +729,132 @@ cudaError_t launch_pack_fixed64(const double *P, const int *list, const int *cou
 // are both coalesced.
 // ---------------------------------------------------------------------------
 template <bool kF64>
+struct PackCols {
+  static __device__ __forceinline__ void run(const double *__restrict__ X64, const float *__restrict__ X32,
+                                                   const float *__restrict__ Xlo, size_t xw, int R, int C, int kp,
+                                                   __nv_bfloat16 *__restrict__ A, int *__restrict__ exps,
+                                                   int *__restrict__ rows_out, long dst_stride, long dst_off,
+                                                   int nsl, int bits,
+                                             const uint3 bid, const uint3 gdim) {
+    assume_global(A, exps);
+    if constexpr (kF64) assume_global(X64); else assume_global(X32);
+    constexpr int kMaxSl = 8;
+    __shared__ double t64[kF64 ? 64 : 1][33];
+    __shared__ float th[kF64 ? 1 : 64][33], tl[kF64 ? 1 : 64][33];
+    __shared__ float cmax[8][32];
+    __shared__ int cexp[32];
+    const int tid = threadIdx.x, cl = tid & 31, jr = tid >> 5;
+    const int w = bid.y, c0 = bid.x * 32;
+    const int c = c0 + cl;
+    const size_t base = (size_t)w * xw;
+    float mx = 0.0f;
+    double mx64 = 0.0;
+    if (c < C)
+      for (int j = jr; j < R; j += 8) {
+        if constexpr (kF64)
+          mx64 = fmax(mx64, fabs(X64[base + (size_t)j * C + c]));
+        else
+          mx = fmaxf(mx, fabsf(X32[base + (size_t)j * C + c]));
+      }
+    if constexpr (kF64) {
+      // exponents from the FP64 maxima: compare through the exponent only
+      cmax[jr][cl] = 0.0f;
+      __shared__ double cmax64[8][32];
+      cmax64[jr][cl] = mx64;
+      __syncthreads();
+      if (jr == 0) {
+        double m = cmax64[0][cl];
+        for (int q = 1; q < 8; ++q) m = fmax(m, cmax64[q][cl]);
+        const int e = m > 0.0 ? ilogb(m) + 1 : 0;
+        cexp[cl] = e;
+        if (c < C) {
+          exps[(size_t)w * C + c] = e;
+          if (rows_out) rows_out[(size_t)w * C + c] = (int)(w * dst_stride + dst_off + c);
+        }
+      }
+    } else {
+      cmax[jr][cl] = mx;
+      __syncthreads();
+      if (jr == 0) {
+        float m = cmax[0][cl];
+        for (int q = 1; q < 8; ++q) m = fmaxf(m, cmax[q][cl]);
+        const int e = m > 0.0f ? ilogbf(m) + 1 : 0;
+        cexp[cl] = e;
+        if (c < C) {
+          exps[(size_t)w * C + c] = e;
+          if (rows_out) rows_out[(size_t)w * C + c] = (int)(w * dst_stride + dst_off + c);
+        }
+      }
+    }
+    __syncthreads();
+    for (int j0 = 0; j0 < kp; j0 += 64) {
+      // tile [64 rows][32 columns], zero past R or C
+  #pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int jj = jr + 8 * q, j = j0 + jj;
+        const bool in = j < R && c < C;
+        if constexpr (kF64) {
+          t64[jj][cl] = in ? X64[base + (size_t)j * C + c] : 0.0;
+        } else {
+          th[jj][cl] = in ? X32[base + (size_t)j * C + c] : 0.0f;
+          tl[jj][cl] = (in && Xlo) ? Xlo[base + (size_t)j * C + c] : 0.0f;
+        }
+      }
+      __syncthreads();
+      // warp jr writes columns jr, jr + 8, jr + 16, jr + 24; lane: rows 2 lane, 2 lane + 1
+  #pragma unroll
+      for (int cc = 0; cc < 4; ++cc) {
+        const int col = jr + 8 * cc, cg = c0 + col;
+        if (cg >= C) continue;
+        const int e = cexp[col];
+        __nv_bfloat16 sl[2][kMaxSl];
+  #pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int jj = 2 * (tid & 31) + h;
+          if constexpr (kF64) {
+            const double step = ldexp(1.0, bits);
+            double x = ldexp(t64[jj][col], bits - 1 - e);  // |x| < 2^(bits - 1)
+  #pragma unroll
+            for (int t = 0; t < kMaxSl; ++t) {
+              if (t >= nsl) break;
+              const double q = rint(x);
+              sl[h][t] = __float2bfloat16_rn(static_cast<float>(q));
+              x = (x - q) * step;
+            }
+          } else {
+            float x = ldexpf(th[jj][col], 7 - e), xl = ldexpf(tl[jj][col], 7 - e);
+  #pragma unroll
+            for (int t = 0; t < kMaxSl; ++t) {
+              if (t >= nsl) break;
+              const float q = rintf(x);
+              sl[h][t] = __float2bfloat16_rn(q);
+              const fdw r = two_sum(__fsub_rn(x, q), xl);
+              x = __fmul_rn(r.hi, 256.0f);
+              xl = __fmul_rn(r.lo, 256.0f);
+            }
+          }
+        }
+        __nv_bfloat16 *dst = A + ((size_t)w * C + cg) * nsl * (size_t)kp + j0 + 2 * (tid & 31);
+  #pragma unroll
+        for (int t = 0; t < kMaxSl; ++t) {
+          if (t >= nsl) break;
+          __nv_bfloat162 v;
+          v.x = sl[0][t];
+          v.y = sl[1][t];
+          *reinterpret_cast<__nv_bfloat162 *>(dst + (size_t)t * kp) = v;
+        }
+      }
+      __syncthreads();
+    }
+}
+};
+template <bool kF64>
 __global__ void __launch_bounds__(256) k_pack_cols(const double *__restrict__ X64, const float *__restrict__ X32,
                                                    const float *__restrict__ Xlo, size_t xw, int R, int C, int kp,
                                                    __nv_bfloat16 *__restrict__ A, int *__restrict__ exps,
                                                    int *__restrict__ rows_out, long dst_stride, long dst_off,
                                                    int nsl, int bits) {
-  constexpr int kMaxSl = 8;
-  __shared__ double t64[kF64 ? 64 : 1][33];
-  __shared__ float th[kF64 ? 1 : 64][33], tl[kF64 ? 1 : 64][33];
-  __shared__ float cmax[8][32];
-  __shared__ int cexp[32];
-  const int tid = threadIdx.x, cl = tid & 31, jr = tid >> 5;
-  const int w = blockIdx.y, c0 = blockIdx.x * 32;
-  const int c = c0 + cl;
-  const size_t base = (size_t)w * xw;
-  float mx = 0.0f;
-  double mx64 = 0.0;
-  if (c < C)
-    for (int j = jr; j < R; j += 8) {
-      if constexpr (kF64)
-        mx64 = fmax(mx64, fabs(X64[base + (size_t)j * C + c]));
-      else
-        mx = fmaxf(mx, fabsf(X32[base + (size_t)j * C + c]));
-    }
-  if constexpr (kF64) {
-    // exponents from the FP64 maxima: compare through the exponent only
-    cmax[jr][cl] = 0.0f;
-    __shared__ double cmax64[8][32];
-    cmax64[jr][cl] = mx64;
-    __syncthreads();
-    if (jr == 0) {
-      double m = cmax64[0][cl];
-      for (int q = 1; q < 8; ++q) m = fmax(m, cmax64[q][cl]);
-      const int e = m > 0.0 ? ilogb(m) + 1 : 0;
-      cexp[cl] = e;
-      if (c < C) {
-        exps[(size_t)w * C + c] = e;
-        if (rows_out) rows_out[(size_t)w * C + c] = (int)(w * dst_stride + dst_off + c);
-      }
-    }
-  } else {
-    cmax[jr][cl] = mx;
-    __syncthreads();
-    if (jr == 0) {
-      float m = cmax[0][cl];
-      for (int q = 1; q < 8; ++q) m = fmaxf(m, cmax[q][cl]);
-      const int e = m > 0.0f ? ilogbf(m) + 1 : 0;
-      cexp[cl] = e;
-      if (c < C) {
-        exps[(size_t)w * C + c] = e;
-        if (rows_out) rows_out[(size_t)w * C + c] = (int)(w * dst_stride + dst_off + c);
-      }
-    }
-  }
-  __syncthreads();
-  for (int j0 = 0; j0 < kp; j0 += 64) {
-    // tile [64 rows][32 columns], zero past R or C
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int jj = jr + 8 * q, j = j0 + jj;
-      const bool in = j < R && c < C;
-      if constexpr (kF64) {
-        t64[jj][cl] = in ? X64[base + (size_t)j * C + c] : 0.0;
-      } else {
-        th[jj][cl] = in ? X32[base + (size_t)j * C + c] : 0.0f;
-        tl[jj][cl] = (in && Xlo) ? Xlo[base + (size_t)j * C + c] : 0.0f;
-      }
-    }
-    __syncthreads();
-    // warp jr writes columns jr, jr + 8, jr + 16, jr + 24; lane: rows 2 lane, 2 lane + 1
-#pragma unroll
-    for (int cc = 0; cc < 4; ++cc) {
-      const int col = jr + 8 * cc, cg = c0 + col;
-      if (cg >= C) continue;
-      const int e = cexp[col];
-      __nv_bfloat16 sl[2][kMaxSl];
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int jj = 2 * (tid & 31) + h;
-        if constexpr (kF64) {
-          const double step = ldexp(1.0, bits);
-          double x = ldexp(t64[jj][col], bits - 1 - e);  // |x| < 2^(bits - 1)
-#pragma unroll
-          for (int t = 0; t < kMaxSl; ++t) {
-            if (t >= nsl) break;
-            const double q = rint(x);
-            sl[h][t] = __float2bfloat16_rn(static_cast<float>(q));
-            x = (x - q) * step;
-          }
-        } else {
-          float x = ldexpf(th[jj][col], 7 - e), xl = ldexpf(tl[jj][col], 7 - e);
-#pragma unroll
-          for (int t = 0; t < kMaxSl; ++t) {
-            if (t >= nsl) break;
-            const float q = rintf(x);
-            sl[h][t] = __float2bfloat16_rn(q);
-            const fdw r = two_sum(__fsub_rn(x, q), xl);
-            x = __fmul_rn(r.hi, 256.0f);
-            xl = __fmul_rn(r.lo, 256.0f);
-          }
-        }
-      }
-      __nv_bfloat16 *dst = A + ((size_t)w * C + cg) * nsl * (size_t)kp + j0 + 2 * (tid & 31);
-#pragma unroll
-      for (int t = 0; t < kMaxSl; ++t) {
-        if (t >= nsl) break;
-        __nv_bfloat162 v;
-        v.x = sl[0][t];
-        v.y = sl[1][t];
-        *reinterpret_cast<__nv_bfloat162 *>(dst + (size_t)t * kp) = v;
-      }
-    }
-    __syncthreads();
-  }
+  PackCols<kF64>::run(X64, X32, Xlo, xw, R, C, kp, A, exps, rows_out, dst_stride, dst_off, nsl, bits, blockIdx, gridDim);
 }
 
 cudaError_t launch_pack_cols(const double *X64, const float *X32, const float *Xlo, size_t xw, int R, int C, int kp,
@@ -812,15 +864,15 @@ cudaError_t launch_pack_cols(const double *X64, const float *X32, const float *X
   if (kp % 64 != 0 || kp < R || (X64 == nullptr) == (X32 == nullptr)) return cudaErrorInvalidValue;
   if (nsl < 1 || nsl > 8 || (bits != 8 && (bits != 7 || !X64))) return cudaErrorInvalidValue;
   dim3 grid((C + 31) / 32, W);
+  const float *nf = nullptr;
+  const double *nd = nullptr;
   if (X64)
-    k_pack_cols<true><<<grid, 256, 0, st>>>(X64, nullptr, nullptr, xw, R, C, kp,
-                                            reinterpret_cast<__nv_bfloat16 *>(A), exps, rows_out, dst_stride, dst_off,
-                                            nsl, bits);
-  else
-    k_pack_cols<false><<<grid, 256, 0, st>>>(nullptr, X32, Xlo, xw, R, C, kp,
-                                             reinterpret_cast<__nv_bfloat16 *>(A), exps, rows_out, dst_stride,
-                                             dst_off, nsl, bits);
-  return cudaGetLastError();
+    return launch_or_record<PackCols<true>, 256>(k_pack_cols<true>, grid, dim3(256), 0, st, X64, nf, nf, xw, R, C, kp,
+                                                 reinterpret_cast<__nv_bfloat16 *>(A), exps, rows_out, dst_stride,
+                                                 dst_off, nsl, bits);
+  return launch_or_record<PackCols<false>, 256>(k_pack_cols<false>, grid, dim3(256), 0, st, nd, X32, Xlo, xw, R, C, kp,
+                                                reinterpret_cast<__nv_bfloat16 *>(A), exps, rows_out, dst_stride,
+                                                dst_off, nsl, bits);
 }
 
 cudaError_t setup_umma_attributes() {
