@@ -615,12 +615,13 @@ class JAGP:
 class Batch:
     """Independent systems swept together (jagp_batch_*): members are JAGP
     objects with their positions; every sweep is one replay of a captured CUDA
-    graph, of grouped launches over all members (n_streams = 0) or of each
-    member's own launches over n_streams streams.  eL[s] holds the last
-    sweep's local energies, acc[s] the running (sum e_L, sum e_L^2, accepted
-    moves, max drift)."""
+    graph, of each member's own launches over n_streams streams (bit for bit
+    the per-member sweeps), or of grouped launches over all members
+    (n_streams = 0, or -k for k lanes: about a hundred launches per sweep).
+    eL[s] holds the last sweep's local energies, acc[s] the running (sum e_L,
+    sum e_L^2, accepted moves, max drift)."""
 
-    def __init__(self, members, positions, walker0=None, n_streams=0):
+    def __init__(self, members, positions, walker0=None, n_streams=16):
         import torch
         self.members, self.r = list(members), list(positions)
         S = len(self.members)

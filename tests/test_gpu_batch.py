@@ -101,7 +101,7 @@ def test_batched_full_size_sampled(torch_cuda):
         m.autotune(p)
         members.append(m)
         pos.append(p)
-    b = pg.Batch(members, pos)
+    b = pg.Batch(members, pos, n_streams=0)
     b.sweep(1, sweep0=0)
     torch.cuda.synchronize()
     assert b.launches_per_sweep() < 150, b.launches_per_sweep()
