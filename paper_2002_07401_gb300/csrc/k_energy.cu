@@ -32,10 +32,8 @@ namespace jagp {
 // ---------------------------------------------------------------------------
 template <typename T>
 struct Kinetic {
-  static __device__ __forceinline__ void run(DevSystem s, const double *__restrict__ r,
-                                                 const T *__restrict__ mbuf, double *__restrict__ kin,
-                                                 int W,
-                                             const uint3 bid, const uint3 gdim) {
+  static __device__ __forceinline__ void run(DevSystem s, const double *__restrict__ r, const T *__restrict__ mbuf,
+                                             double *__restrict__ kin, int W, const uint3 bid, const uint3 gdim) {
     assume_global(r, mbuf, kin);
     constexpr bool kDw = std::is_same<T, float>::value;
     extern __shared__ double4 sh_geo[];
@@ -159,8 +157,7 @@ struct Kinetic {
 };
 template <typename T>
 __global__ void __launch_bounds__(256) k_kinetic(DevSystem s, const double *__restrict__ r,
-                                                 const T *__restrict__ mbuf, double *__restrict__ kin,
-                                                 int W) {
+                                                 const T *__restrict__ mbuf, double *__restrict__ kin, int W) {
   Kinetic<T>::run(s, r, mbuf, kin, W, blockIdx, gridDim);
 }
 
@@ -189,9 +186,8 @@ template cudaError_t launch_kinetic<float>(const DevSystem &, const double *, co
 // ---------------------------------------------------------------------------
 struct KineticM2 {
   static __device__ __forceinline__ void run(DevSystem s, const double *__restrict__ r,
-                                                    const float *__restrict__ mbuf, const float *__restrict__ mlo,
-                                                    double *__restrict__ kin, int W,
-                                             const uint3 bid, const uint3 gdim) {
+                                             const float *__restrict__ mbuf, const float *__restrict__ mlo,
+                                             double *__restrict__ kin, int W, const uint3 bid, const uint3 gdim) {
     assume_global(r, mbuf, mlo, kin);
     extern __shared__ double4 sh_geo[];
     int *sh_info = reinterpret_cast<int *>(sh_geo + s.n_shells);
@@ -309,10 +305,9 @@ cudaError_t launch_kinetic_m2(const DevSystem &s, const double *r, const float *
 // ---------------------------------------------------------------------------
 struct Elocal {
   static __device__ __forceinline__ void run(DevSystem s, const double *__restrict__ r,
-                                                const double *__restrict__ kin, double *__restrict__ eL,
-                                                double *__restrict__ parts, double *__restrict__ scal,
-                                                const double *__restrict__ j3buf,
-                                             const uint3 bid, const uint3 gdim) {
+                                             const double *__restrict__ kin, double *__restrict__ eL,
+                                             double *__restrict__ parts, double *__restrict__ scal,
+                                             const double *__restrict__ j3buf, const uint3 bid, const uint3 gdim) {
     assume_global(r, kin, eL);
     const int w = bid.x, N = s.N, tid = threadIdx.x;
     extern __shared__ double xs[];
@@ -432,10 +427,9 @@ __global__ void __launch_bounds__(128) k_elocal(DevSystem s, const double *__res
 // ---------------------------------------------------------------------------
 struct ElocalDw {
   static __device__ __forceinline__ void run(DevSystem s, const double *__restrict__ r,
-                                                   const double *__restrict__ kin, double *__restrict__ eL,
-                                                   double *__restrict__ parts, double *__restrict__ scal,
-                                                   const double *__restrict__ j3buf,
-                                             const uint3 bid, const uint3 gdim) {
+                                             const double *__restrict__ kin, double *__restrict__ eL,
+                                             double *__restrict__ parts, double *__restrict__ scal,
+                                             const double *__restrict__ j3buf, const uint3 bid, const uint3 gdim) {
     assume_global(r, kin, eL);
     const int w = bid.x, N = s.N, tid = threadIdx.x, na = s.n_atoms;
     const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;

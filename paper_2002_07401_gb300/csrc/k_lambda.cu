@@ -17,9 +17,8 @@ namespace jagp {
 // ---------------------------------------------------------------------------
 struct LambdaRows {
   static __device__ __forceinline__ void run(const double *__restrict__ P, const double *__restrict__ Lam,
-                                                     double *__restrict__ Out, const int *__restrict__ list,
-                                                     const int *__restrict__ count, int nrows, int nsub,
-                                                     int stride, int L,
+                                             double *__restrict__ Out, const int *__restrict__ list,
+                                             const int *__restrict__ count, int nrows, int nsub, int stride, int L,
                                              const uint3 bid, const uint3 gdim) {
     assume_global(P, Lam, Out);
     const int rows = count ? *count : nrows;
@@ -85,8 +84,8 @@ struct LambdaRows {
 };
 __global__ void __launch_bounds__(256) k_lambda_rows(const double *__restrict__ P, const double *__restrict__ Lam,
                                                      double *__restrict__ Out, const int *__restrict__ list,
-                                                     const int *__restrict__ count, int nrows, int nsub,
-                                                     int stride, int L) {
+                                                     const int *__restrict__ count, int nrows, int nsub, int stride,
+                                                     int L) {
   LambdaRows::run(P, Lam, Out, list, count, nrows, nsub, stride, L, blockIdx, gridDim);
 }
 

@@ -17,9 +17,8 @@ namespace jagp {
 // ---------------------------------------------------------------------------
 template <typename T>
 struct GemmRows {
-  static __device__ __forceinline__ void run(const T *__restrict__ X, size_t xw,
-                                                   const T *__restrict__ Y, size_t yw, int ma, int nb,
-                                                   int K, T *__restrict__ Out, size_t ow, int ldo,
+  static __device__ __forceinline__ void run(const T *__restrict__ X, size_t xw, const T *__restrict__ Y, size_t yw,
+                                             int ma, int nb, int K, T *__restrict__ Out, size_t ow, int ldo,
                                              const uint3 bid, const uint3 gdim) {
     assume_global(X, Y, Out);
     __shared__ T Xs[16][65];
@@ -47,9 +46,9 @@ struct GemmRows {
 }
 };
 template <typename T>
-__global__ void __launch_bounds__(256) k_gemm_rows(const T *__restrict__ X, size_t xw,
-                                                   const T *__restrict__ Y, size_t yw, int ma, int nb,
-                                                   int K, T *__restrict__ Out, size_t ow, int ldo) {
+__global__ void __launch_bounds__(256) k_gemm_rows(const T *__restrict__ X, size_t xw, const T *__restrict__ Y,
+                                                   size_t yw, int ma, int nb, int K, T *__restrict__ Out, size_t ow,
+                                                   int ldo) {
   GemmRows<T>::run(X, xw, Y, yw, ma, nb, K, Out, ow, ldo, blockIdx, gridDim);
 }
 
@@ -61,10 +60,9 @@ __global__ void __launch_bounds__(256) k_gemm_rows(const T *__restrict__ X, size
 // as accurate as the double-word tables rather than FP32.  The _rn intrinsics
 // keep the compiler from fusing the steps.
 struct GemmRowsDot2 {
-  static __device__ __forceinline__ void run(const float *__restrict__ X, const float *__restrict__ Xlo,
-                                                        size_t xw, const float *__restrict__ Y,
-                                                        const float *__restrict__ Ylo, size_t yw, int ma, int nb,
-                                                        int K, double *__restrict__ Out, size_t ow, int ldo,
+  static __device__ __forceinline__ void run(const float *__restrict__ X, const float *__restrict__ Xlo, size_t xw,
+                                             const float *__restrict__ Y, const float *__restrict__ Ylo, size_t yw,
+                                             int ma, int nb, int K, double *__restrict__ Out, size_t ow, int ldo,
                                              const uint3 bid, const uint3 gdim) {
     assume_global(X, Y, Out);
     __shared__ float Xs[16][65];
@@ -124,10 +122,9 @@ __global__ void __launch_bounds__(256) k_gemm_rows_dot2(const float *__restrict_
 // ---------------------------------------------------------------------------
 template <typename T, int TM, bool DOT2, typename OutT>
 struct GemmRowsBlk {
-  static __device__ __forceinline__ void run(const T *__restrict__ X, const float *__restrict__ Xlo,
-                                                       size_t xw, const T *__restrict__ Y,
-                                                       const float *__restrict__ Ylo, size_t yw, int ma, int nb,
-                                                       int K, OutT *__restrict__ Out, size_t ow, int ldo,
+  static __device__ __forceinline__ void run(const T *__restrict__ X, const float *__restrict__ Xlo, size_t xw,
+                                             const T *__restrict__ Y, const float *__restrict__ Ylo, size_t yw,
+                                             int ma, int nb, int K, OutT *__restrict__ Out, size_t ow, int ldo,
                                              const uint3 bid, const uint3 gdim) {
     assume_global(X, Y, Out);
     constexpr int KC = 32, R = TM / 16, PAD = TM + 1;
@@ -236,13 +233,10 @@ inline int gemm_rows_tile(int ma, int nb) {
 // CTA, 64 threads each with a 2 x 2 output block, so that every shared-memory
 // operand read serves two outputs instead of one; k order as above.
 struct GemmRowsDot2Small {
-  static __device__ __forceinline__ void run(const float *__restrict__ X,
-                                                              const float *__restrict__ Xlo, size_t xw,
-                                                              const float *__restrict__ Y,
-                                                              const float *__restrict__ Ylo, size_t yw, int ma,
-                                                              int nb, int K, double *__restrict__ Out, size_t ow,
-                                                              int ldo, int W,
-                                             const uint3 bid, const uint3 gdim) {
+  static __device__ __forceinline__ void run(const float *__restrict__ X, const float *__restrict__ Xlo, size_t xw,
+                                             const float *__restrict__ Y, const float *__restrict__ Ylo, size_t yw,
+                                             int ma, int nb, int K, double *__restrict__ Out, size_t ow, int ldo,
+                                             int W, const uint3 bid, const uint3 gdim) {
     assume_global(X, Y, Out);
     constexpr int KC = 32;
     __shared__ float Xs[4][KC][17], Xl[4][KC][17], Ys[4][KC][17], Yl[4][KC][17];
@@ -452,9 +446,8 @@ constexpr size_t kRefreshSmemMax = 200 * 1024;  // shared-memory rows of the in-
 template <typename T, int NM>
 struct RefreshInverseReg {
   static __device__ __forceinline__ void run(const double *__restrict__ gm, T *__restrict__ ginv,
-                                                             double *__restrict__ scal, int *__restrict__ status,
-                                                             int n, int W, int check_drift, double drift_tol,
-                                                             double *__restrict__ ginv64,
+                                             double *__restrict__ scal, int *__restrict__ status, int n, int W,
+                                             int check_drift, double drift_tol, double *__restrict__ ginv64,
                                              const uint3 bid, const uint3 gdim) {
     assume_global(gm, ginv, scal, status);
     constexpr int kGroups = 32 / NM;
@@ -575,9 +568,8 @@ __global__ void __launch_bounds__(128) k_refresh_inverse_reg(const double *__res
 template <typename T>
 struct RefreshInverseReg64 {
   static __device__ __forceinline__ void run(const double *__restrict__ gm, T *__restrict__ ginv,
-                                                               double *__restrict__ scal, int *__restrict__ status,
-                                                               int n, int W, int check_drift, double drift_tol,
-                                                               double *__restrict__ ginv64,
+                                             double *__restrict__ scal, int *__restrict__ status, int n, int W,
+                                             int check_drift, double drift_tol, double *__restrict__ ginv64,
                                              const uint3 bid, const uint3 gdim) {
     assume_global(gm, ginv, scal, status);
     constexpr unsigned kFull = 0xffffffffu;
@@ -770,11 +762,10 @@ __global__ void __launch_bounds__(128) k_refresh_inverse_reg64(const double *__r
 // CTAs together fit in L2).
 template <typename T>
 struct RefreshInverseInplace {
-  static __device__ __forceinline__ void run(double *__restrict__ gm, T *__restrict__ ginv,
-                                                                 double *__restrict__ scal, int *__restrict__ status,
-                                                                 int n, int rs, int check_drift, double drift_tol,
-                                                                 double *__restrict__ ginv64,
-                                             const uint3 bid, const uint3 gdim) {
+  static __device__ __forceinline__ void run(double *__restrict__ gm, T *__restrict__ ginv, double *__restrict__ scal,
+                                             int *__restrict__ status, int n, int rs, int check_drift,
+                                             double drift_tol, double *__restrict__ ginv64, const uint3 bid,
+                                             const uint3 gdim) {
     assume_global(gm, ginv, scal, status);
     extern __shared__ double sm[];
     const int ld = n + 1;
@@ -996,10 +987,9 @@ template cudaError_t launch_refresh_inverse<float>(double *, float *, double *, 
 // ---------------------------------------------------------------------------
 template <typename T>
 struct Mmat {
-  static __device__ __forceinline__ void run(DevSystem s, const T *__restrict__ ginv,
-                                              const T *__restrict__ bt, const T *__restrict__ a_up,
-                                              T *__restrict__ mbuf,
-                                             const uint3 bid, const uint3 gdim) {
+  static __device__ __forceinline__ void run(DevSystem s, const T *__restrict__ ginv, const T *__restrict__ bt,
+                                             const T *__restrict__ a_up, T *__restrict__ mbuf, const uint3 bid,
+                                             const uint3 gdim) {
     assume_global(ginv, bt, a_up, mbuf);
     extern __shared__ double smd[];
     T *sm = reinterpret_cast<T *>(smd);
@@ -1032,9 +1022,8 @@ struct Mmat {
 }
 };
 template <typename T>
-__global__ void __launch_bounds__(256) k_mmat(DevSystem s, const T *__restrict__ ginv,
-                                              const T *__restrict__ bt, const T *__restrict__ a_up,
-                                              T *__restrict__ mbuf) {
+__global__ void __launch_bounds__(256) k_mmat(DevSystem s, const T *__restrict__ ginv, const T *__restrict__ bt,
+                                              const T *__restrict__ a_up, T *__restrict__ mbuf) {
   Mmat<T>::run(s, ginv, bt, a_up, mbuf, blockIdx, gridDim);
 }
 
@@ -1044,10 +1033,9 @@ __global__ void __launch_bounds__(256) k_mmat(DevSystem s, const T *__restrict__
 // blockIdx.y, then down tiles, so that no tile mixes the two formulas.
 template <typename T>
 struct MmatTiled {
-  static __device__ __forceinline__ void run(DevSystem s, const T *__restrict__ ginv,
-                                                    const T *__restrict__ bt, const T *__restrict__ a_up,
-                                                    T *__restrict__ mbuf,
-                                             const uint3 bid, const uint3 gdim) {
+  static __device__ __forceinline__ void run(DevSystem s, const T *__restrict__ ginv, const T *__restrict__ bt,
+                                             const T *__restrict__ a_up, T *__restrict__ mbuf, const uint3 bid,
+                                             const uint3 gdim) {
     assume_global(ginv, bt, a_up, mbuf);
     __shared__ T Xs[16][64];  // Xs[k][e]: G~^{-1}[k][e] (up) or G~^{-1}[e][k] (down)
     __shared__ T Ys[16][64];  // Ys[k][c]: Bt[k][c] (up) or A_up[k][c] (down)
@@ -1109,9 +1097,8 @@ struct MmatTiled {
 }
 };
 template <typename T>
-__global__ void __launch_bounds__(256) k_mmat_tiled(DevSystem s, const T *__restrict__ ginv,
-                                                    const T *__restrict__ bt, const T *__restrict__ a_up,
-                                                    T *__restrict__ mbuf) {
+__global__ void __launch_bounds__(256) k_mmat_tiled(DevSystem s, const T *__restrict__ ginv, const T *__restrict__ bt,
+                                                    const T *__restrict__ a_up, T *__restrict__ mbuf) {
   MmatTiled<T>::run(s, ginv, bt, a_up, mbuf, blockIdx, gridDim);
 }
 
@@ -1123,10 +1110,10 @@ __global__ void __launch_bounds__(256) k_mmat_tiled(DevSystem s, const T *__rest
 // FP32 precision.  One CTA per (walker, 64 columns).
 struct MmatDw {
   static __device__ __forceinline__ void run(DevSystem s, const double *__restrict__ ginv64,
-                                                 const float *__restrict__ bt, const float *__restrict__ bt_lo,
-                                                 const float *__restrict__ a_up, const float *__restrict__ a_lo,
-                                                 float *__restrict__ mbuf, float *__restrict__ mlo,
-                                             const uint3 bid, const uint3 gdim) {
+                                             const float *__restrict__ bt, const float *__restrict__ bt_lo,
+                                             const float *__restrict__ a_up, const float *__restrict__ a_lo,
+                                             float *__restrict__ mbuf, float *__restrict__ mlo, const uint3 bid,
+                                             const uint3 gdim) {
     assume_global(ginv64, bt, bt_lo, a_up, a_lo, mbuf, mlo);
     extern __shared__ float smf[];
     const int n = s.n_up, N = s.N, L = s.L;

@@ -413,8 +413,8 @@ struct UmmaGemm {
 };
 
 __global__ void __launch_bounds__(128) k_umma_gemm(const __grid_constant__ CUtensorMap tmA,
-                                                      const __grid_constant__ CUtensorMap tmB,
-                                                      const __grid_constant__ UmmaArgs g) {
+                                                   const __grid_constant__ CUtensorMap tmB,
+                                                   const __grid_constant__ UmmaArgs g) {
   UmmaGemm::run(tmA, tmB, g, blockIdx, gridDim);
 }
 
@@ -596,11 +596,10 @@ cudaError_t launch_umma_gemm(const uint16_t *A, int m_max, const int *m_dev, int
 // ---------------------------------------------------------------------------
 struct PackFixed {
   static __device__ __forceinline__ void run(const float *__restrict__ P, const float *__restrict__ P_lo,
-                                                     const int *__restrict__ list, const int *__restrict__ count,
-                                                     int nrows, int nsub, int stride, int L, int kp,
-                                                     __nv_bfloat16 *__restrict__ A, int *__restrict__ rows_out,
-                                                     int *__restrict__ exps,
-                                             const uint3 bid, const uint3 gdim) {
+                                             const int *__restrict__ list, const int *__restrict__ count, int nrows,
+                                             int nsub, int stride, int L, int kp, __nv_bfloat16 *__restrict__ A,
+                                             int *__restrict__ rows_out, int *__restrict__ exps, const uint3 bid,
+                                             const uint3 gdim) {
     assume_global(P, A, rows_out, exps);
     const int rows = count ? *count : nrows;
     const int lane = threadIdx.x & 31;
@@ -636,10 +635,10 @@ struct PackFixed {
 }
 };
 __global__ void __launch_bounds__(256) k_pack_fixed(const float *__restrict__ P, const float *__restrict__ P_lo,
-                                                     const int *__restrict__ list, const int *__restrict__ count,
-                                                     int nrows, int nsub, int stride, int L, int kp,
-                                                     __nv_bfloat16 *__restrict__ A, int *__restrict__ rows_out,
-                                                     int *__restrict__ exps) {
+                                                    const int *__restrict__ list, const int *__restrict__ count,
+                                                    int nrows, int nsub, int stride, int L, int kp,
+                                                    __nv_bfloat16 *__restrict__ A, int *__restrict__ rows_out,
+                                                    int *__restrict__ exps) {
   PackFixed::run(P, P_lo, list, count, nrows, nsub, stride, L, kp, A, rows_out, exps, blockIdx, gridDim);
 }
 
@@ -659,11 +658,10 @@ cudaError_t launch_pack_fixed(const float *P, const float *P_lo, const int *list
 // magnitude, for the FP64-equivalent products (every step exact in FP64).
 struct PackFixed64 {
   static __device__ __forceinline__ void run(const double *__restrict__ P, const int *__restrict__ list,
-                                                      const int *__restrict__ count, int nrows, int nsub, int stride,
-                                                      int L, int kp, int nsl, int bits,
-                                                      __nv_bfloat16 *__restrict__ A, int *__restrict__ rows_out,
-                                                      int *__restrict__ exps, long dst_stride, long dst_off,
-                                             const uint3 bid, const uint3 gdim) {
+                                             const int *__restrict__ count, int nrows, int nsub, int stride, int L,
+                                             int kp, int nsl, int bits, __nv_bfloat16 *__restrict__ A,
+                                             int *__restrict__ rows_out, int *__restrict__ exps, long dst_stride,
+                                             long dst_off, const uint3 bid, const uint3 gdim) {
     assume_global(P, A, rows_out, exps);
     const int rows = count ? *count : nrows;
     const int lane = threadIdx.x & 31;
@@ -696,10 +694,11 @@ struct PackFixed64 {
 };
 __global__ void __launch_bounds__(256) k_pack_fixed64(const double *__restrict__ P, const int *__restrict__ list,
                                                       const int *__restrict__ count, int nrows, int nsub, int stride,
-                                                      int L, int kp, int nsl, int bits,
-                                                      __nv_bfloat16 *__restrict__ A, int *__restrict__ rows_out,
-                                                      int *__restrict__ exps, long dst_stride, long dst_off) {
-  PackFixed64::run(P, list, count, nrows, nsub, stride, L, kp, nsl, bits, A, rows_out, exps, dst_stride, dst_off, blockIdx, gridDim);
+                                                      int L, int kp, int nsl, int bits, __nv_bfloat16 *__restrict__ A,
+                                                      int *__restrict__ rows_out, int *__restrict__ exps,
+                                                      long dst_stride, long dst_off) {
+  PackFixed64::run(P, list, count, nrows, nsub, stride, L, kp, nsl, bits, A, rows_out, exps, dst_stride, dst_off,
+                   blockIdx, gridDim);
 }
 
 cudaError_t launch_pack_fixed64(const double *P, const int *list, const int *count, int nrows, int nsub, int stride,
@@ -731,11 +730,10 @@ cudaError_t launch_pack_fixed64(const double *P, const int *list, const int *cou
 template <bool kF64>
 struct PackCols {
   static __device__ __forceinline__ void run(const double *__restrict__ X64, const float *__restrict__ X32,
-                                                   const float *__restrict__ Xlo, size_t xw, int R, int C, int kp,
-                                                   __nv_bfloat16 *__restrict__ A, int *__restrict__ exps,
-                                                   int *__restrict__ rows_out, long dst_stride, long dst_off,
-                                                   int nsl, int bits,
-                                             const uint3 bid, const uint3 gdim) {
+                                             const float *__restrict__ Xlo, size_t xw, int R, int C, int kp,
+                                             __nv_bfloat16 *__restrict__ A, int *__restrict__ exps,
+                                             int *__restrict__ rows_out, long dst_stride, long dst_off, int nsl,
+                                             int bits, const uint3 bid, const uint3 gdim) {
     assume_global(A, exps);
     if constexpr (kF64) assume_global(X64); else assume_global(X32);
     constexpr int kMaxSl = 8;
@@ -852,9 +850,10 @@ template <bool kF64>
 __global__ void __launch_bounds__(256) k_pack_cols(const double *__restrict__ X64, const float *__restrict__ X32,
                                                    const float *__restrict__ Xlo, size_t xw, int R, int C, int kp,
                                                    __nv_bfloat16 *__restrict__ A, int *__restrict__ exps,
-                                                   int *__restrict__ rows_out, long dst_stride, long dst_off,
-                                                   int nsl, int bits) {
-  PackCols<kF64>::run(X64, X32, Xlo, xw, R, C, kp, A, exps, rows_out, dst_stride, dst_off, nsl, bits, blockIdx, gridDim);
+                                                   int *__restrict__ rows_out, long dst_stride, long dst_off, int nsl,
+                                                   int bits) {
+  PackCols<kF64>::run(X64, X32, Xlo, xw, R, C, kp, A, exps, rows_out, dst_stride, dst_off, nsl, bits, blockIdx,
+                      gridDim);
 }
 
 cudaError_t launch_pack_cols(const double *X64, const float *X32, const float *Xlo, size_t xw, int R, int C, int kp,

@@ -43,12 +43,11 @@ __device__ __forceinline__ double j1_move_change_f(const DevSystem &s, const flo
 
 template <bool PROPOSE, typename T>
 struct BasisPoints {
-  static __device__ __forceinline__ void run(DevSystem s, const double *__restrict__ r, int W,
-                                                      int e0, int npts, T *__restrict__ out,
-                                                      float *__restrict__ out_lo, double *__restrict__ rprop,
-                                                      uint32_t walker0, uint32_t sweep,
-                                                      const uint32_t *__restrict__ sweep_dev,
-                                             const uint3 bid, const uint3 gdim) {
+  static __device__ __forceinline__ void run(DevSystem s, const double *__restrict__ r, int W, int e0, int npts,
+                                             T *__restrict__ out, float *__restrict__ out_lo,
+                                             double *__restrict__ rprop, uint32_t walker0, uint32_t sweep,
+                                             const uint32_t *__restrict__ sweep_dev, const uint3 bid,
+                                             const uint3 gdim) {
     assume_global(r, out);
     constexpr bool kDw = std::is_same<T, float>::value;
     if (PROPOSE && sweep_dev) sweep += *sweep_dev;  // graph replays read the sweep index from the device
@@ -141,10 +140,9 @@ struct BasisPoints {
 }
 };
 template <bool PROPOSE, typename T>
-__global__ void __launch_bounds__(256) k_basis_points(DevSystem s, const double *__restrict__ r, int W,
-                                                      int e0, int npts, T *__restrict__ out,
-                                                      float *__restrict__ out_lo, double *__restrict__ rprop,
-                                                      uint32_t walker0, uint32_t sweep,
+__global__ void __launch_bounds__(256) k_basis_points(DevSystem s, const double *__restrict__ r, int W, int e0,
+                                                      int npts, T *__restrict__ out, float *__restrict__ out_lo,
+                                                      double *__restrict__ rprop, uint32_t walker0, uint32_t sweep,
                                                       const uint32_t *__restrict__ sweep_dev) {
   BasisPoints<PROPOSE, T>::run(s, r, W, e0, npts, out, out_lo, rprop, walker0, sweep, sweep_dev, blockIdx, gridDim);
 }
@@ -229,18 +227,14 @@ __host__ __device__ inline size_t metro_smem_per_walker(int n, int N) {
 
 template <bool UP, typename T, bool GLOB>
 struct Metropolis {
-  static __device__ __forceinline__ void run(DevSystem s, double *__restrict__ r,
-                                                    const double *__restrict__ rprop,
-                                                    const T *__restrict__ gprop,
-                                                    T *__restrict__ ginv, double *__restrict__ scal,
-                                                    int *__restrict__ status,
-                                                    const T *__restrict__ pprop,
-                                                    T *__restrict__ phi_up, int *__restrict__ list,
-                                                    int *__restrict__ count,
-                                                    const float *__restrict__ pprop_lo,
-                                                    float *__restrict__ phi_lo, int m_begin, int m_end,
-                                                    int *__restrict__ total, double *__restrict__ j3buf,
-                                             const uint3 bid, const uint3 gdim) {
+  static __device__ __forceinline__ void run(DevSystem s, double *__restrict__ r, const double *__restrict__ rprop,
+                                             const T *__restrict__ gprop, T *__restrict__ ginv,
+                                             double *__restrict__ scal, int *__restrict__ status,
+                                             const T *__restrict__ pprop, T *__restrict__ phi_up,
+                                             int *__restrict__ list, int *__restrict__ count,
+                                             const float *__restrict__ pprop_lo, float *__restrict__ phi_lo,
+                                             int m_begin, int m_end, int *__restrict__ total,
+                                             double *__restrict__ j3buf, const uint3 bid, const uint3 gdim) {
     assume_global(r, rprop, gprop, ginv, scal, status, pprop, phi_up, list, count);
     extern __shared__ double sm[];
     const int n = s.n_up, N = s.N, tid = threadIdx.x, bs = blockDim.x;
@@ -429,17 +423,15 @@ struct Metropolis {
 };
 template <bool UP, typename T, bool GLOB>
 __global__ void __launch_bounds__(512) k_metropolis(DevSystem s, double *__restrict__ r,
-                                                    const double *__restrict__ rprop,
-                                                    const T *__restrict__ gprop,
+                                                    const double *__restrict__ rprop, const T *__restrict__ gprop,
                                                     T *__restrict__ ginv, double *__restrict__ scal,
-                                                    int *__restrict__ status,
-                                                    const T *__restrict__ pprop,
+                                                    int *__restrict__ status, const T *__restrict__ pprop,
                                                     T *__restrict__ phi_up, int *__restrict__ list,
-                                                    int *__restrict__ count,
-                                                    const float *__restrict__ pprop_lo,
+                                                    int *__restrict__ count, const float *__restrict__ pprop_lo,
                                                     float *__restrict__ phi_lo, int m_begin, int m_end,
                                                     int *__restrict__ total, double *__restrict__ j3buf) {
-  Metropolis<UP, T, GLOB>::run(s, r, rprop, gprop, ginv, scal, status, pprop, phi_up, list, count, pprop_lo, phi_lo, m_begin, m_end, total, j3buf, blockIdx, gridDim);
+  Metropolis<UP, T, GLOB>::run(s, r, rprop, gprop, ginv, scal, status, pprop, phi_up, list, count, pprop_lo, phi_lo,
+                               m_begin, m_end, total, j3buf, blockIdx, gridDim);
 }
 
 // ---------------------------------------------------------------------------
@@ -704,12 +696,14 @@ struct MetropolisWarp {
   // latency-bound (one walker's sequential moves per warp): keep six CTAs of
   // four warps resident per SM
   static constexpr int kMinBlocks = 6;
-  static __device__ __forceinline__ void run(DevSystem s, double *__restrict__ r, const double *__restrict__ rprop, const T *__restrict__ gprop,
-    T *__restrict__ ginv, double *__restrict__ scal, int *__restrict__ status,
-    const T *__restrict__ pprop, T *__restrict__ phi_up, int *__restrict__ list,
-    int *__restrict__ count, int W, const float *__restrict__ pprop_lo, float *__restrict__ phi_lo, int m_begin,
-    int m_end, int *__restrict__ total,
-                                             const uint3 bid, const uint3 gdim) {
+  static __device__ __forceinline__ void run(DevSystem s, double *__restrict__ r, const double *__restrict__ rprop,
+                                             const T *__restrict__ gprop, T *__restrict__ ginv,
+                                             double *__restrict__ scal, int *__restrict__ status,
+                                             const T *__restrict__ pprop, T *__restrict__ phi_up,
+                                             int *__restrict__ list, int *__restrict__ count, int W,
+                                             const float *__restrict__ pprop_lo, float *__restrict__ phi_lo,
+                                             int m_begin, int m_end, int *__restrict__ total, const uint3 bid,
+                                             const uint3 gdim) {
     assume_global(r, rprop, gprop, ginv, scal, status, pprop, phi_up, list, count);
     extern __shared__ double sm[];
     const int n = s.n_up, N = s.N, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -826,12 +820,13 @@ struct MetropolisWarp {
 }
 };
 template <bool UP, typename T>
-__global__ void __launch_bounds__(kMetroWarps * 32) k_metropolis_warp(DevSystem s, double *__restrict__ r, const double *__restrict__ rprop, const T *__restrict__ gprop,
-    T *__restrict__ ginv, double *__restrict__ scal, int *__restrict__ status,
-    const T *__restrict__ pprop, T *__restrict__ phi_up, int *__restrict__ list,
+__global__ void __launch_bounds__(kMetroWarps * 32) k_metropolis_warp(DevSystem s, double *__restrict__ r,
+    const double *__restrict__ rprop, const T *__restrict__ gprop, T *__restrict__ ginv, double *__restrict__ scal,
+    int *__restrict__ status, const T *__restrict__ pprop, T *__restrict__ phi_up, int *__restrict__ list,
     int *__restrict__ count, int W, const float *__restrict__ pprop_lo, float *__restrict__ phi_lo, int m_begin,
     int m_end, int *__restrict__ total) {
-  MetropolisWarp<UP, T>::run(s, r, rprop, gprop, ginv, scal, status, pprop, phi_up, list, count, W, pprop_lo, phi_lo, m_begin, m_end, total, blockIdx, gridDim);
+  MetropolisWarp<UP, T>::run(s, r, rprop, gprop, ginv, scal, status, pprop, phi_up, list, count, W, pprop_lo, phi_lo,
+                             m_begin, m_end, total, blockIdx, gridDim);
 }
 
 template <typename T>
@@ -990,9 +985,8 @@ cudaError_t launch_walker_info(const double *scal, const int *status, int W, dou
 // Per-sweep accumulators in a fixed reduction order (bitwise reproducible):
 // acc = (sum e_L, sum e_L^2, accepted moves of this sweep, max drift).
 struct ReduceAcc {
-  static __device__ __forceinline__ void run(const double *eL, const double *scal, const int *count,
-                                                     int W, double *acc, int accumulate,
-                                             const uint3 bid, const uint3 gdim) {
+  static __device__ __forceinline__ void run(const double *eL, const double *scal, const int *count, int W,
+                                             double *acc, int accumulate, const uint3 bid, const uint3 gdim) {
     __shared__ double s1[1024], s2[1024], s3[1024];
     double a = 0.0, b = 0.0, d = 0.0;
     for (int w = threadIdx.x; w < W; w += blockDim.x) {
@@ -1031,8 +1025,8 @@ struct ReduceAcc {
     }
 }
 };
-__global__ void __launch_bounds__(1024) k_reduce_acc(const double *eL, const double *scal, const int *count,
-                                                     int W, double *acc, int accumulate) {
+__global__ void __launch_bounds__(1024) k_reduce_acc(const double *eL, const double *scal, const int *count, int W,
+                                                     double *acc, int accumulate) {
   ReduceAcc::run(eL, scal, count, W, acc, accumulate, blockIdx, gridDim);
 }
 
