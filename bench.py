@@ -933,10 +933,31 @@ def c1_bench(pg, torch, dist, args, dev, rank, ws, local):
                       dev, local, pg.KERNEL_LAMBDA_ROWS, label="c1")
     rr["g"].close()
     ms = rr["ms_max"]
+    # the same sweeps replayed as one captured CUDA graph per sweep (a one-system
+    # batch: the sweep index comes from a device counter), which removes the
+    # host's launch cost from every kernel
+    g = pg.JAGP(sysm, W, seed=0)
+    p = g.positions(x0)
+    g.eval(p)
+    b = pg.Batch([g], [p], walker0=[rank * W], n_streams=1)
+    b.sweep(args.warmup, sweep0=0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    b.sweep(args.c1_sweeps, sweep0=args.warmup)
+    e1.record()
+    torch.cuda.synchronize()
+    gms = e0.elapsed_time(e1)
+    graph = {"ms_per_sweep": gms / args.c1_sweeps, "value": W * sysm.N * args.c1_sweeps / (gms / 1e3),
+             "unit": "walker-electron moves/s (one GPU)", "graph_launches_per_sweep": b.launches_per_sweep(),
+             "note": "one CUDA graph replay per sweep (jagp_batch over this one system)"}
+    b.close()
+    g.close()
     return {"metric": "walker-electron moves/s", "value": W * sysm.N * args.c1_sweeps * ws / (ms / 1e3),
             "unit": "walker-electron moves/s", "ms_per_sweep": ms / args.c1_sweeps, "sweeps": args.c1_sweeps,
             "gpu_launches": rr["launches"], "launches_per_sweep": rr["launches"] / args.c1_sweeps,
-            "us_per_launch": ms * 1e3 / max(rr["launches"], 1), "dtype": "f64", "workload": C1_WORKLOAD,
+            "us_per_launch": ms * 1e3 / max(rr["launches"], 1), "graph": graph, "dtype": "f64",
+            "workload": C1_WORKLOAD,
             "roofline": {"bound": "latency", "note": "each launch carries microseconds of work: the sweep is bound "
                          "by launch latency and the sequential acceptance, not by a roofline", "frac": None}}
 

@@ -25,16 +25,16 @@ namespace jagp {
 static thread_local GroupRecorder *g_group_recorder = nullptr;
 GroupRecorder *group_recorder() { return g_group_recorder; }
 void set_group_recorder(GroupRecorder *r) { g_group_recorder = r; }
-cudaError_t group_raise_smem(const void *fn, unsigned char *done) {
+cudaError_t group_raise_smem(const void *fn, std::atomic<unsigned char> *done) {
   int dev = 0, optin = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
+  if (dev >= 0 && dev < 64 && done[dev].load(std::memory_order_acquire)) return cudaSuccess;
   if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
   cudaFuncAttributes fa;
   if ((e = cudaFuncGetAttributes(&fa, fn)) != cudaSuccess) return e;
   e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
-  if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = 1;
+  if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev].store(1, std::memory_order_release);
   return e;
 }
 }  // namespace jagp
@@ -1452,7 +1452,8 @@ jagp_status_t batch_build_grouped(jagp_batch *b) {
   // dynamic shared memory beyond 48 KB: the kernel's limit raised to the device's
   for (const auto &gl : b->glaunch)
     if (gl.smem > 48 * 1024) {
-      unsigned char done[64] = {};
+      std::atomic<unsigned char> done[64];
+      for (auto &d : done) d.store(0, std::memory_order_relaxed);
       JAGP_CU(group_raise_smem(gl.fn, done));
     }
   // capture: each lane's grouped launches in order on its stream (forked from

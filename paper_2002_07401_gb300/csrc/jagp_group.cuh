@@ -23,6 +23,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <atomic>
 #include <type_traits>
 #include <utility>
 #include <vector>
@@ -179,7 +180,8 @@ inline void group_subkey(int e) {
 
 // allow kernel fn dynamic shared memory up to the current device's opt-in
 // limit less its static shared memory; done[device] records that it was set
-cudaError_t group_raise_smem(const void *fn, unsigned char *done);
+// (setting it twice from two threads is harmless)
+cudaError_t group_raise_smem(const void *fn, std::atomic<unsigned char> *done);
 
 // kernel<<<grid, block, smem, st>>>(a...) (the per-system launch of functor
 // F, max. threads per block MT), or, while a recorder is installed, the
@@ -211,7 +213,7 @@ cudaError_t launch_or_record(K kernel, dim3 grid, dim3 block, size_t smem, cudaS
     return cudaSuccess;
   }
   if (smem > 48 * 1024) {
-    static unsigned char raised[64] = {};  // per device
+    static std::atomic<unsigned char> raised[64];  // per device (zero at start)
     const cudaError_t e = group_raise_smem(reinterpret_cast<const void *>(kernel), raised);
     if (e != cudaSuccess) return e;
   }
