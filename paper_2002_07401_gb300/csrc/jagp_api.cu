@@ -1270,7 +1270,6 @@ struct GroupLaunch {
   size_t smem;
   int blocks;
   size_t tab_off;     // byte offset of the argument packs in the blob
-  size_t pack_bytes;  // size of one argument pack
   int lane;
   GroupTable table;
 };
@@ -1426,7 +1425,6 @@ jagp_status_t batch_build_grouped(jagp_batch *b) {
     const size_t psz = all[i].args.size();
     if (psz % all[i].align) return JAGP_ERR_UNSUPPORTED;
     gl.tab_off = place((size_t)gl.table.n * psz, 256);
-    gl.pack_bytes = psz;
     long long blocks = 0;
     for (size_t k = i; k < j; ++k) {
       const GroupRecord &r = all[k];
